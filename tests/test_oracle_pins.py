@@ -1,0 +1,447 @@
+"""Pins for the CPU oracle: checks against what the paper and mathematics fix,
+not against the oracle itself.
+
+Each test names the plausible mistake it would catch.  The oracle is test
+infrastructure (plain FP64 C); these tests run on the CPU only.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.fft as sfft
+import scipy.sparse as sp
+
+import oracle
+import paris_inputs as pi
+
+P, W = pi.PERIODIC, pi.WALL
+
+
+# ----------------------------------------------------------- independent D, G ---
+
+def _face_offsets(grid):
+    sizes = [int(np.prod(grid.face_shape(a))) for a in range(3)]
+    return [0, sizes[0], sizes[0] + sizes[1]], sum(sizes)
+
+
+def incidence_matrices(grid):
+    """Dense-definition discrete gradient G (faces x cells) and divergence D
+    (cells x faces) built entry by entry from Eq. cont2 and the face-gradient
+    definition (p_R - p_L)/h; wall faces have no gradient and carry no flux."""
+    n = (grid.nx, grid.ny, grid.nz)
+    off, nf = _face_offsets(grid)
+    cidx = lambda i, j, k: (k * grid.ny + j) * grid.nx + i
+    gr, gc, gv = [], [], []
+    dr, dc, dv = [], [], []
+    h = grid.h
+    for a in range(3):
+        fs = grid.face_shape(a)  # (z, y, x)
+        fidx = lambda c, fs=fs, a=a: off[a] + (c[2] * fs[1] + c[1]) * fs[2] + c[0]
+        for k in range(fs[0]):
+            for j in range(fs[1]):
+                for i in range(fs[2]):
+                    c = [i, j, k]
+                    ia = c[a]
+                    if grid.bc[a] == W and (ia == 0 or ia == n[a]):
+                        continue
+                    left = list(c)
+                    left[a] = (ia - 1) % n[a]
+                    f = fidx(c)
+                    gr += [f, f]
+                    gc += [cidx(*c), cidx(*left)]
+                    gv += [1.0 / h, -1.0 / h]
+        for k in range(n[2]):
+            for j in range(n[1]):
+                for i in range(n[0]):
+                    c = [i, j, k]
+                    ia = c[a]
+                    cm = list(c)
+                    cp = list(c)
+                    cp[a] = ia + 1
+                    if grid.bc[a] == P:
+                        cp[a] %= n[a]
+                    if not (grid.bc[a] == W and ia + 1 == n[a]):
+                        dr.append(cidx(*c)); dc.append(fidx(cp)); dv.append(1.0 / h)
+                    if not (grid.bc[a] == W and ia == 0):
+                        dr.append(cidx(*c)); dc.append(fidx(cm)); dv.append(-1.0 / h)
+    N = grid.ncells
+    G = sp.coo_matrix((gv, (gr, gc)), shape=(nf, N)).tocsr()
+    D = sp.coo_matrix((dv, (dr, dc)), shape=(N, nf)).tocsr()
+    return G, D
+
+
+def flat_faces(*fs):
+    return np.concatenate([np.ravel(f) for f in fs])
+
+
+def csr_dense(op):
+    rowptr, col, val = op.csr()
+    return sp.csr_matrix((val, col, rowptr), shape=(op.n, op.n))
+
+
+SMALL_GRIDS = [
+    pi.Grid(2, 3, 4, 0.25, (P, P, P)),
+    pi.Grid(3, 2, 5, 0.5, (W, P, W)),
+    pi.Grid(4, 4, 3, 1.0 / 3, (P, W, P)),
+    pi.Grid(1, 4, 2, 0.5, (P, P, W)),
+    pi.Grid(5, 3, 2, 0.2, (W, W, W)),
+]
+
+
+def _rand_beta(grid, seed):
+    rng = np.random.default_rng(seed)
+    return [rng.uniform(0.001, 1.0, size=grid.face_shape(a)) for a in range(3)]
+
+
+# --------------------------------------------------------------- operator ---
+
+@pytest.mark.parametrize("grid", SMALL_GRIDS, ids=lambda g: f"{g.nx}x{g.ny}x{g.nz}_{g.bc}")
+def test_assembled_operator_equals_D_B_G(grid):
+    """-A == D diag(beta) G with D, G from their definitions.  Catches a wrong
+    neighbour index, a missing periodic wrap, a wall link left in, a duplicate
+    neighbour (n = 1, 2) not summed, a wrong 1/h^2 scale or sign."""
+    beta = _rand_beta(grid, 1)
+    # wall faces hold arbitrary values: the oracle must ignore them
+    op = oracle.Operator(grid, *beta)
+    G, D = incidence_matrices(grid)
+    Bf = sp.diags(flat_faces(*beta))
+    L = (D @ Bf @ G).toarray()
+    A = csr_dense(op).toarray()
+    np.testing.assert_allclose(-A, L, rtol=1e-14, atol=1e-14 * np.abs(L).max())
+
+
+@pytest.mark.parametrize("grid", SMALL_GRIDS, ids=lambda g: f"{g.nx}x{g.ny}x{g.nz}_{g.bc}")
+def test_divergence_and_gradient_match_definitions(grid):
+    """oracle.divergence == D u/dt and oracle.face_gradient == G p; D = -G^T on
+    the non-wall faces.  Catches a sign flip or a +/- face mix-up."""
+    rng = np.random.default_rng(2)
+    u = [rng.uniform(-1, 1, size=grid.face_shape(a)) for a in range(3)]
+    p = rng.uniform(-1, 1, size=grid.shape)
+    G, D = incidence_matrices(grid)
+    dt = 0.37
+    np.testing.assert_allclose(oracle.divergence(grid, *u, dt=dt).ravel(), D @ flat_faces(*u) / dt,
+                               rtol=1e-13, atol=1e-12)
+    np.testing.assert_allclose(flat_faces(*oracle.face_gradient(grid, p)), G @ p.ravel(),
+                               rtol=1e-13, atol=1e-12)
+    assert abs(D + G.T).max() < 1e-12 / grid.h
+
+
+def test_divergence_unit_impulses():
+    """Face i-1/2 is the - face of cell i and the + face of cell i-1, so a unit
+    velocity there gives -1/(h dt) in cell i and +1/(h dt) in cell i-1; a wall
+    face gives nothing.  Brute force over every face of a 3x3x3 grid with walls
+    in y."""
+    grid = pi.Grid(3, 3, 3, 0.5, (P, W, P))
+    for a in range(3):
+        fs = grid.face_shape(a)
+        for flat in range(int(np.prod(fs))):
+            u = [np.zeros(grid.face_shape(b)) for b in range(3)]
+            u[a].ravel()[flat] = 1.0
+            d = oracle.divergence(grid, *u, dt=2.0)
+            k, j, i = np.unravel_index(flat, fs)
+            c = [i, j, k]
+            n = [3, 3, 3]
+            expect = np.zeros(grid.shape)
+            wall = grid.bc[a] == W and (c[a] == 0 or c[a] == n[a])
+            if not wall:
+                right = list(c)
+                left = list(c)
+                left[a] = (c[a] - 1) % n[a]
+                expect[right[2], right[1], right[0]] -= 1.0 / (0.5 * 2.0)
+                expect[left[2], left[1], left[0]] += 1.0 / (0.5 * 2.0)
+            np.testing.assert_array_equal(d, expect)
+
+
+@pytest.mark.parametrize("grid", SMALL_GRIDS[:3], ids=lambda g: f"{g.nx}x{g.ny}x{g.nz}")
+def test_symmetry_null_space_psd(grid):
+    """A = A^T bitwise; A 1 = 0 to 4 ulp of the diagonal; A is positive
+    semi-definite with a one-dimensional null space (the constants)."""
+    beta = _rand_beta(grid, 3)
+    op = oracle.Operator(grid, *beta)
+    A = csr_dense(op)
+    assert (A != A.T).nnz == 0
+    diag = A.diagonal()
+    r = op.apply(np.ones(grid.shape)).ravel()
+    assert np.all(np.abs(r) <= 4 * np.finfo(float).eps * diag)
+    ev = np.linalg.eigvalsh(A.toarray())
+    assert ev[0] > -1e-12 * ev[-1]
+    assert ev[1] > 1e-8 * ev[-1]  # only one zero eigenvalue
+
+
+# ---------------------------------------------------------- face coefficients ---
+
+def test_face_coeffs_hand_values():
+    """beta = 1/rho_f with rho = rho1 C + rho2 (1-C) and rho_f the mean of the two
+    cells (Eq. muH); wall faces 0.  Values worked by hand for a 4x1x1 row with
+    walls in x: C = (1, 0.5, 0, 0.25), rho1 = 10, rho2 = 2."""
+    grid = pi.Grid(4, 1, 1, 1.0, (W, P, P))
+    C = np.array([1.0, 0.5, 0.0, 0.25]).reshape(1, 1, 4)
+    bx, by, bz = oracle.face_coeffs(grid, C, 10.0, 2.0)
+    rho = [10.0, 6.0, 2.0, 4.0]
+    expect = [0.0, 1 / 8.0, 1 / 4.0, 1 / 3.0, 0.0]
+    np.testing.assert_allclose(bx.ravel(), expect, rtol=1e-15)
+    # periodic y and z of length 1: the face sees the same cell on both sides
+    np.testing.assert_allclose(by.ravel(), [1.0 / r for r in rho], rtol=1e-15)
+    np.testing.assert_allclose(bz.ravel(), [1.0 / r for r in rho], rtol=1e-15)
+
+
+def test_face_coeffs_periodic_wrap():
+    """Face -1/2 of a periodic axis couples cell 0 with cell n-1."""
+    grid = pi.Grid(3, 1, 1, 1.0, (P, P, P))
+    C = np.array([1.0, 0.0, 0.0]).reshape(1, 1, 3)
+    bx, _, _ = oracle.face_coeffs(grid, C, 3.0, 1.0)
+    np.testing.assert_allclose(bx.ravel(), [0.5, 0.5, 1.0], rtol=1e-15)
+
+
+# ------------------------------------------------------------------- solves ---
+
+def _bordered_solve(A, rhs):
+    """Mean-free solution of A x = rhs via the bordered system [A 1; 1^T 0]."""
+    n = A.shape[0]
+    M = np.zeros((n + 1, n + 1))
+    M[:n, :n] = A
+    M[:n, n] = 1.0
+    M[n, :n] = 1.0
+    x = np.linalg.solve(M, np.concatenate([rhs, [0.0]]))
+    return x[:n]
+
+
+@pytest.mark.parametrize("bc", [(P, P, P), (P, P, W), (W, W, W)])
+def test_dense_lu_8cubed(bc):
+    """The oracle's projection matches a dense LU solve of the bordered system
+    on an 8^3 grid with a density ratio 1000 drop (relative 1e-11)."""
+    grid = pi.Grid(8, 8, 8, 1.0 / 8, bc)
+    pr = pi.random_problem(grid, seed=7, rho1=1000.0)
+    res = oracle.projection_step(grid, pr.C, pr.rho1, pr.rho2, pr.dt, pr.u, pr.v, pr.w, tol=1e-14)
+    A = csr_dense(res.op).toarray()
+    b = res.rhs.ravel() - res.rhs.mean()
+    p_lu = _bordered_solve(A, -b)
+    np.testing.assert_allclose(res.p.ravel(), p_lu, rtol=0, atol=1e-11 * np.abs(p_lu).max())
+
+
+def _const_coeff_solution(grid, beta, b):
+    """Mean-free solution of beta * lap_h p = b by diagonalising the 7-point
+    Laplacian: Fourier modes along periodic axes, eigenvalue
+    -(4/h^2) sin^2(pi k/n); DCT-II modes along wall (Neumann) axes,
+    eigenvalue -(4/h^2) sin^2(pi k/(2n))."""
+    n = (grid.nx, grid.ny, grid.nz)
+    axes_np = {0: 2, 1: 1, 2: 0}
+    B = b.astype(complex)
+    lam = np.zeros(grid.shape)
+    for a in range(3):
+        ax = axes_np[a]
+        k = np.arange(n[a])
+        if grid.bc[a] == P:
+            B = np.fft.fft(B, axis=ax)
+            la = -(4.0 / grid.h ** 2) * np.sin(np.pi * k / n[a]) ** 2
+        else:
+            B = sfft.dct(B.real, type=2, norm="ortho", axis=ax) + 1j * sfft.dct(B.imag, type=2, norm="ortho", axis=ax)
+            la = -(4.0 / grid.h ** 2) * np.sin(np.pi * k / (2 * n[a])) ** 2
+        shape = [1, 1, 1]
+        shape[ax] = n[a]
+        lam = lam + la.reshape(shape)
+    lam = beta * lam
+    X = np.zeros_like(B)
+    nz = np.abs(lam) > 0
+    X[nz] = B[nz] / lam[nz]
+    for a in range(3):
+        ax = axes_np[a]
+        if grid.bc[a] == P:
+            X = np.fft.ifft(X, axis=ax)
+        else:
+            X = sfft.idct(X.real, type=2, norm="ortho", axis=ax) + 1j * sfft.idct(X.imag, type=2, norm="ortho", axis=ax)
+    return X.real
+
+
+@pytest.mark.parametrize("bc,n", [((P, P, P), (16, 12, 8)), ((P, P, W), (16, 16, 16)),
+                                  ((W, P, W), (12, 8, 10)), ((W, W, W), (8, 8, 8))])
+def test_constant_coefficient_closed_form(bc, n):
+    """rho1 = rho2: the solve reduces to the constant-coefficient Laplacian,
+    diagonalised by FFT/DCT-II.  Match <= 1e-12 relative.  Catches any
+    operator or RHS error that survives the variable-coefficient tests."""
+    grid = pi.Grid(*n, 1.0 / n[0], bc)
+    pr = pi.random_problem(grid, seed=11, rho1=4.0, rho2=4.0)
+    res = oracle.projection_step(grid, pr.C, 4.0, 4.0, pr.dt, pr.u, pr.v, pr.w, tol=1e-15)
+    b = res.rhs - res.rhs.mean()
+    p_ref = _const_coeff_solution(grid, 0.25, b)
+    p_ref -= p_ref.mean()
+    np.testing.assert_allclose(res.p, p_ref, rtol=0, atol=1e-12 * np.abs(p_ref).max())
+
+
+def _numpy_face_gradient(grid, phi):
+    """(phi_R - phi_L)/h on every face, 0 on wall faces (numpy roll, independent
+    of the oracle)."""
+    out = []
+    for a in range(3):
+        ax = 2 - a
+        if grid.bc[a] == P:
+            g = (phi - np.roll(phi, 1, axis=ax)) / grid.h
+        else:
+            g = np.zeros(grid.face_shape(a))
+            sl_in = [slice(None)] * 3
+            sl_in[ax] = slice(1, -1)
+            g[tuple(sl_in)] = np.diff(phi, axis=ax) / grid.h
+        out.append(g)
+    return out
+
+
+@pytest.mark.parametrize("bc", [(P, P, W), (P, P, P)])
+def test_gradient_field_pin(bc):
+    """u* = dt B G phi has D u*/dt = L phi, so p = phi - mean(phi) and u = 0,
+    at density ratio 1000.  Catches a wrong sign or scale in the RHS, the
+    solve or the correction (no discretisation error involved)."""
+    grid = pi.Grid(24, 20, 16, 1.0 / 24, bc)
+    pr = pi.random_problem(grid, seed=5, rho1=1000.0, drops=3)
+    beta = oracle.face_coeffs(grid, pr.C, pr.rho1, pr.rho2)
+    phi = pi.random_field(grid.shape, seed=3)
+    g = _numpy_face_gradient(grid, phi)
+    ustar = [pr.dt * b * gg for b, gg in zip(beta, g)]
+    res = oracle.projection_step(grid, pr.C, pr.rho1, pr.rho2, pr.dt, *ustar, tol=1e-14)
+    lmin, lmax = res.cg.lanczos_extremes()
+    bound = (lmax / lmin) * max(res.cg.rel_res_l2, 1e-16) * np.linalg.norm(phi)
+    err = np.linalg.norm(res.p - phi)
+    assert err <= bound and err <= 1e-8 * np.linalg.norm(phi)
+    umax = max(np.abs(x).max() for x in ustar)
+    for uu in res.u:
+        assert np.abs(uu).max() <= 1e-8 * umax
+
+
+def test_divergence_free_pin():
+    """u* = discrete curl of an edge potential: b = 0 to round-off, p = 0, u = u*."""
+    grid = pi.Grid(16, 16, 16, 1.0 / 16)
+    rng = np.random.default_rng(9)
+    u = pi.edge_potential_curl(rng, grid, 6, 3)
+    C = np.zeros(grid.shape)
+    C[4:9, 5:11, 3:8] = 1.0
+    res = oracle.projection_step(grid, C, 50.0, 1.0, 1e-3, *u)
+    scale = max(np.abs(x).max() for x in u) / grid.h / 1e-3
+    assert np.abs(res.rhs).max() <= 1e-12 * scale
+    for a in range(3):
+        np.testing.assert_allclose(res.u[a], u[a], rtol=0, atol=1e-12 * np.abs(u[a]).max())
+
+
+def test_idempotence():
+    """Projecting a projected field again changes nothing and gives p ~ 0."""
+    grid = pi.Grid(16, 12, 16, 1.0 / 16, (P, W, P))
+    pr = pi.random_problem(grid, seed=21, rho1=100.0)
+    r1 = oracle.projection_step(grid, pr.C, pr.rho1, pr.rho2, pr.dt, pr.u, pr.v, pr.w, tol=1e-14)
+    r2 = oracle.projection_step(grid, pr.C, pr.rho1, pr.rho2, pr.dt, *r1.u, tol=1e-14)
+    for a in range(3):
+        np.testing.assert_allclose(r2.u[a], r1.u[a], rtol=0, atol=1e-9)
+    assert np.abs(r2.p).max() <= 1e-8 * np.abs(r1.p).max()
+
+
+def test_projection_divergence_roundoff():
+    """After the projection D u = dt (b - L p) exactly, so max|D u| <= dt ||r||inf
+    plus round-off, far below 1e-9 max|u*|/h."""
+    pr = pi.config2(n=32, drops=8)
+    res = oracle.projection_step(pr.grid, pr.C, pr.rho1, pr.rho2, pr.dt, pr.u, pr.v, pr.w)
+    d = oracle.divergence(pr.grid, *res.u, dt=1.0)
+    umax = max(np.abs(x).max() for x in (pr.u, pr.v, pr.w))
+    assert np.abs(d).max() <= 1e-9 * umax / pr.grid.h
+    # wall faces blocked
+    assert np.all(res.u[2][0] == 0) and np.all(res.u[2][-1] == 0)
+
+
+def test_second_order_manufactured():
+    """Manufactured p = cos(2 pi x) cos(2 pi y) cos(pi z) with walls in z and
+    beta = 1/rho, rho = 1 + sin(2 pi x) sin(2 pi y)/2 sampled on the faces,
+    b = div(beta grad p) exactly: the error falls ~4x per halving of h."""
+    errs = []
+    for n in (16, 32, 64):
+        grid = pi.Grid(n, n, n, 1.0 / n, (P, P, W))
+        beta = []
+        for a in range(3):
+            x, y, z = pi.face_positions(grid, a)
+            X, Y = np.meshgrid(x, y, indexing="xy")  # (y, x)
+            rho = 1.0 + 0.5 * np.sin(2 * np.pi * X) * np.sin(2 * np.pi * Y)
+            beta.append(np.broadcast_to(1.0 / rho, (z.size,) + rho.shape).copy())
+        c = (np.arange(n) + 0.5) / n
+        Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+        tp = 2 * np.pi
+        p = np.cos(tp * X) * np.cos(tp * Y) * np.cos(np.pi * Z)
+        px = -tp * np.sin(tp * X) * np.cos(tp * Y) * np.cos(np.pi * Z)
+        py = -tp * np.cos(tp * X) * np.sin(tp * Y) * np.cos(np.pi * Z)
+        rho = 1.0 + 0.5 * np.sin(tp * X) * np.sin(tp * Y)
+        rx = np.pi * np.cos(tp * X) * np.sin(tp * Y)
+        ry = np.pi * np.sin(tp * X) * np.cos(tp * Y)
+        lap = -(4 * np.pi ** 2 + 4 * np.pi ** 2 + np.pi ** 2) * p
+        b = lap / rho - (rx * px + ry * py) / rho ** 2
+        op = oracle.Operator(grid, *beta)
+        res = oracle.cg(op, -(b - b.mean()), tol=1e-13)
+        ph = res.x - res.x.mean()
+        errs.append(np.abs(ph - (p - p.mean())).max())
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.5 < r1 < 4.6 and 3.5 < r2 < 4.6, errs
+
+
+def test_lanczos_extremes_match_dense_eigenvalues():
+    """The Lanczos estimate from the CG coefficients brackets the spectrum:
+    lambda_max within 1 %, smallest non-zero eigenvalue within 5 %."""
+    grid = pi.Grid(8, 6, 8, 1.0 / 8, (P, W, P))
+    pr = pi.random_problem(grid, seed=4, rho1=30.0)
+    res = oracle.projection_step(grid, pr.C, pr.rho1, pr.rho2, pr.dt, pr.u, pr.v, pr.w, tol=1e-14)
+    ev = np.linalg.eigvalsh(csr_dense(res.op).toarray())
+    lmin, lmax = res.cg.lanczos_extremes()
+    assert abs(lmax - ev[-1]) <= 0.01 * ev[-1]
+    assert abs(lmin - ev[1]) <= 0.05 * ev[1]
+
+
+def test_cg_zero_rhs():
+    grid = pi.Grid(4, 4, 4, 0.25)
+    op = oracle.Operator(grid, *_rand_beta(grid, 0))
+    res = oracle.cg(op, np.zeros(grid.shape))
+    assert res.iters == 0 and np.all(res.x == 0)
+
+
+# ------------------------------------------------------------------ adjoint ---
+
+def _fd_dloss(grid, base_args, target, which, index, eps):
+    """Central difference of L = 1/2 ||u - t||^2 written as
+    sum (u+ - u-) * ((u+ + u-)/2 - t), which avoids cancellation."""
+    C, rho1, rho2, dt, u = base_args
+    vals = []
+    for s in (+1, -1):
+        Cs = C.copy()
+        us = [x.copy() for x in u]
+        if which == "C":
+            Cs.ravel()[index] += s * eps
+        else:
+            a, f = which, index
+            us[a].ravel()[f] += s * eps
+        res = oracle.projection_step(grid, Cs, rho1, rho2, dt, *us, tol=1e-15)
+        vals.append(res.u)
+    num = 0.0
+    for a in range(3):
+        up, um = vals[0][a], vals[1][a]
+        num += np.sum((up - um) * (0.5 * (up + um) - target[a]))
+    return num / (2 * eps)
+
+
+@pytest.mark.parametrize("bc", [(P, P, P), (P, W, P)])
+def test_adjoint_against_finite_differences(bc):
+    """dL/du* and dL/dC from the oracle adjoint agree with central finite
+    differences (1e-6 relative) for L = 1/2 ||u - t||^2 on a 6x6x6 grid."""
+    grid = pi.Grid(6, 6, 6, 1.0 / 6, bc)
+    rng = np.random.default_rng(31)
+    c = (np.arange(6) + 0.5) / 6 - 0.5
+    r = np.sqrt(c[:, None, None] ** 2 + c[None, :, None] ** 2 + c[None, None, :] ** 2)
+    C = 0.5 * (1 - np.tanh((r - 0.25) / 0.1))
+    u = [rng.uniform(-1, 1, size=grid.face_shape(a)) for a in range(3)]
+    pi.zero_wall_faces(grid, *u)
+    t = [rng.uniform(-1, 1, size=grid.face_shape(a)) for a in range(3)]
+    rho1, rho2, dt = 20.0, 1.0, 0.01
+    res = oracle.projection_step(grid, C, rho1, rho2, dt, *u, tol=1e-15)
+    g = [res.u[a] - t[a] for a in range(3)]
+    gstar, gbeta, q, st = oracle.project_adjoint(grid, res.op, res.beta, res.p, dt, *g, tol=1e-15)
+    gC = oracle.face_coeffs_adjoint(grid, rho1, rho2, res.beta, gbeta)
+    args = (C, rho1, rho2, dt, u)
+    for a in range(3):
+        for f in rng.choice(gstar[a].size, size=5, replace=False):
+            fd = _fd_dloss(grid, args, t, a, f, 1e-6)
+            ad = gstar[a].ravel()[f]
+            assert abs(fd - ad) <= 1e-6 * max(abs(ad), 1e-3 * np.abs(gstar[a]).max()), (a, f, fd, ad)
+    for cidx in rng.choice(C.size, size=8, replace=False):
+        fd = _fd_dloss(grid, args, t, "C", cidx, 1e-6)
+        ad = gC.ravel()[cidx]
+        assert abs(fd - ad) <= 1e-6 * max(abs(ad), 1e-3 * np.abs(gC).max()), (cidx, fd, ad)
