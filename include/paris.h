@@ -1,0 +1,197 @@
+/*
+ * paris.h -- C ABI of the GB300 (sm_103a) one-fluid pressure projection.
+ *
+ * The library computes one projection step of the PARIS one-fluid method
+ * (arXiv 2012.11744, Sec. 3.2 Eqs. fotm, cont-eq1 and poisson; Sec. 3.7 and
+ * 3.8) on a single GPU:
+ *
+ *   1. beta_f = 1/rho_f, rho = rho1 C + rho2 (1 - C) (Eq. muH), face density
+ *      the mean of the two cells, beta = 0 on wall faces      paris_face_coeffs
+ *   2. b = (grad^h . u*)/dt (Eqs. cont2, incompdisc3), mean removed
+ *                                                           paris_divergence
+ *   3. solve grad^h . (beta grad^h p) = b, mean(p) = 0      paris_poisson_solve
+ *   4. u = u* - dt beta_f (grad^h p)_f (Eq. fotm)            paris_project
+ *
+ * GRID AND LAYOUT.  A regular grid of nx*ny*nz cubic cells of edge h
+ * (Sec. 3.1: the VOF routines are limited to cubic cells).  Cell (i,j,k) is
+ * stored at (k*ny + j)*nx + i (x fastest).  Each axis is either periodic or
+ * bounded by walls (no-slip/no-penetration: zero normal velocity, homogeneous
+ * Neumann condition for p, Sec. 3.8).  Face arrays (u, beta_x on x-faces etc.)
+ * store face "i-1/2" of cell i at index i and have the cell layout with the
+ * face axis extended by one when that axis has walls:
+ *   x-faces: nz * ny * (nx + wall_x)     index (k*ny + j)*(nx+wall_x) + i
+ *   y-faces: nz * (ny + wall_y) * nx     index (k*(ny+wall_y) + j)*nx + i
+ *   z-faces: (nz + wall_z) * ny * nx     index (k*ny + j)*nx + i
+ * Along a wall axis the entries 0 and n are the wall faces.
+ *
+ * MEMORY.  Unless a name ends in _host, every array argument is a DEVICE
+ * pointer to IEEE double, owned by the caller, contiguous in the layout above
+ * and 8-byte aligned.  The context owns its workspace (multigrid hierarchy,
+ * Krylov vectors, reduction scratch), allocated in paris_create and released in
+ * paris_destroy; the compute calls allocate nothing.
+ *
+ * STREAMS.  Every call is enqueued on the context's CUDA stream (given to
+ * paris_create as a cudaStream_t cast to void*; NULL = the legacy default
+ * stream).  Calls returning only a status are asynchronous; calls that fill a
+ * host struct (paris_stats, the mean removed) synchronise the stream first.
+ * paris_poisson_solve always synchronises: the number of iterations it runs is
+ * decided from device-side residual norms.
+ *
+ * ERRORS.  Every call returns a paris_status; nothing is thrown across the ABI.
+ * Arguments are validated before any work is enqueued.  A CUDA error is
+ * reported as PARIS_ERR_CUDA and leaves the context unusable (destroy it).
+ */
+#ifndef PARIS_H
+#define PARIS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PARIS_OK = 0,
+    PARIS_ERR_INVALID_ARG = 1,   /* bad size, spacing, density, time step, null pointer */
+    PARIS_ERR_CUDA = 2,          /* a CUDA call failed (allocation, launch, copy) */
+    PARIS_ERR_NOT_CONVERGED = 3, /* solve hit max_iter; p holds the best iterate */
+    PARIS_ERR_NONFINITE = 4,     /* a NaN/Inf appeared in the right-hand side or the residual */
+    PARIS_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
+    PARIS_ERR_NO_MEMORY = 6      /* device allocation failed in paris_create */
+} paris_status;
+
+typedef enum { PARIS_PERIODIC = 0, PARIS_WALL = 1 } paris_bc;
+
+typedef enum {
+    PARIS_FP64 = 0,  /* FP64 multigrid-preconditioned CG, FP64 V-cycles */
+    PARIS_MIXED = 1  /* FP64 iterative refinement around FP32 V-cycle-preconditioned
+                        flexible CG; residuals, solution, dot products, mean removal
+                        and the coarsest solve in FP64 */
+} paris_precision;
+
+typedef enum {
+    PARIS_SMOOTH_RBGS = 0,   /* red-black Gauss-Seidel with over-relaxation (Sec. 3.7.1) */
+    PARIS_SMOOTH_JACOBI = 1  /* damped Jacobi, the paper's GPU iteration (Sec. 3.7.4) */
+} paris_smoother;
+
+typedef struct {
+    int nx, ny, nz;  /* cells per axis, each >= 2 */
+    double h;        /* cell edge, > 0 */
+    int bc[3];       /* paris_bc for the x, y, z axes */
+} paris_grid;
+
+typedef struct {
+    double tol;           /* stop when ||r||_2/||b||_2 <= tol AND ||r||_inf/||b||_inf <= tol (1e-10) */
+    int max_iter;         /* cap on preconditioned iterations (V-cycles) per solve (200) */
+    int precision;        /* paris_precision (PARIS_MIXED) */
+    int nu1, nu2;         /* pre/post smoothing sweeps per level (2, 2) */
+    double omega;         /* over-relaxation factor of the smoother (1.15; Jacobi: 0.8) */
+    int smoother;         /* paris_smoother (PARIS_SMOOTH_RBGS) */
+    int coarse_max_cells; /* coarsen until the coarsest grid has at most this many cells (64) */
+    double inner_tol;     /* MIXED: relative residual reduction of each FP32 inner solve (1e-5) */
+    int fallback;         /* MIXED: on failure redo the solve in FP64 (1) */
+} paris_opts;
+
+typedef struct {
+    int iters;             /* preconditioned iterations (V-cycles) in total */
+    int outer_iters;       /* MIXED: FP64 refinement steps; FP64: equals iters */
+    double rel_res_l2;     /* ||b - L p||_2 / ||b||_2 of the returned p, computed in FP64 */
+    double rel_res_linf;   /* ||b - L p||_inf / ||b||_inf */
+    double mean_b_removed; /* mean of the right-hand side removed before the solve */
+    int fell_back;         /* MIXED: 1 if the FP64 fallback produced the result */
+    int converged;         /* 1 if both tolerances were met */
+    int levels;            /* multigrid levels used */
+} paris_stats;
+
+typedef struct paris_ctx paris_ctx;
+
+/* Fill *o with the defaults listed above. */
+void paris_default_opts(paris_opts* o);
+
+/* Create a context for one grid: validates g (n >= 2 per axis, h > 0, bc in
+ * {0,1}) and o, builds the multigrid level plan and allocates all device
+ * workspace on the current device.  stream: a cudaStream_t (may be NULL).
+ * Errors: INVALID_ARG, NO_MEMORY, CUDA.  On error *ctx is NULL. */
+paris_status paris_create(paris_ctx** ctx, const paris_grid* g, const paris_opts* o, void* stream);
+
+/* Release the context and its device workspace (synchronises its stream). */
+paris_status paris_destroy(paris_ctx* ctx);
+
+/* Replace the options (same grid); no reallocation unless the level plan changes. */
+paris_status paris_set_opts(paris_ctx* ctx, const paris_opts* o);
+
+/* Step 1 -- Eq. muH and Sec. 3.7.1: from the cell volume fraction C (cells,
+ * values normally in [0,1]) and the densities rho1 (fluid C=1), rho2 (C=0),
+ * both > 0, write beta_f = 2/(rho_L + rho_R) on every face, 0 on wall faces
+ * (Sec. 3.8 coefficient zeroing).  beta_x/y/z: face arrays (see layout).
+ * Errors: INVALID_ARG (null pointer, rho <= 0). */
+paris_status paris_face_coeffs(paris_ctx* ctx, const double* C, double rho1, double rho2,
+                               double* beta_x, double* beta_y, double* beta_z);
+
+/* Step 2 -- Eqs. cont2/incompdisc3: rhs_c = sum over the axes of
+ * (u_{+face} - u_{-face})/(h dt); wall faces contribute no flux whatever they
+ * hold.  The mean of rhs is then removed (the compatibility condition of the
+ * singular Neumann/periodic problem) and returned in *mean_removed when that
+ * pointer (host) is not NULL, which synchronises the stream.
+ * Errors: INVALID_ARG (null pointer, dt <= 0). */
+paris_status paris_divergence(paris_ctx* ctx, const double* u, const double* v, const double* w,
+                              double dt, double* rhs, double* mean_removed);
+
+/* Step 3 -- Eq. poisson with tau folded into b: solve
+ *   sum_f beta_f (p_nb - p_c)/h^2 = rhs_c
+ * (the paper's A1..A7 form of Sec. 3.7.1 divided by -tau) for p with
+ * mean(p) = 0.  rhs is read only; its mean is removed internally.  p: in =
+ * initial guess, out = solution.  Multigrid-preconditioned CG (FP64 form) or
+ * FP64 iterative refinement around FP32 multigrid-preconditioned flexible CG
+ * (MIXED), per the context options; st (host, optional) receives the stats.
+ * Errors: INVALID_ARG, NOT_CONVERGED (p holds the last iterate), NONFINITE
+ * (NaN/Inf in rhs or during the solve), CUDA. */
+paris_status paris_poisson_solve(paris_ctx* ctx, const double* beta_x, const double* beta_y,
+                                 const double* beta_z, const double* rhs, double* p,
+                                 paris_stats* st);
+
+/* Step 4 -- Eq. fotm: on every non-wall face u_f <- u_f - dt beta_f (p_R - p_L)/h,
+ * in place on u, v, w (in: u*, out: u); wall faces are set to 0 (Sec. 3.8 velocity
+ * blocking).  Errors: INVALID_ARG (null pointer, dt <= 0). */
+paris_status paris_project(paris_ctx* ctx, const double* beta_x, const double* beta_y,
+                           const double* beta_z, const double* p, double dt,
+                           double* u, double* v, double* w);
+
+/* Steps 1-4 in order on device arrays: C (cells) -> beta (context scratch),
+ * b, p (in: initial guess, out: mean-free solution), u/v/w in place.
+ * Errors: as the four calls. */
+paris_status paris_projection_step(paris_ctx* ctx, const double* C, double rho1, double rho2,
+                                   double dt, double* u, double* v, double* w, double* p,
+                                   paris_stats* st);
+
+/* paris_projection_step on HOST arrays: C_host, u/v/w_host (in: u*, out: u)
+ * and p_host (in: initial guess, out: p) are copied to and from device
+ * buffers the context owns (allocated on the first call of this function,
+ * which should therefore not be the one being timed).  Pinned host memory
+ * gives the fastest copies.  Synchronises the stream before returning. */
+paris_status paris_projection_step_host(paris_ctx* ctx, const double* C_host, double rho1,
+                                        double rho2, double dt, double* u_host, double* v_host,
+                                        double* w_host, double* p_host, paris_stats* st);
+
+/* Diagnostics on device arrays, FP64: r = rhs - L p, returning (host) the
+ * relative residual norms with respect to rhs (rhs taken as given, mean not
+ * removed) and the maximum absolute discrete divergence max|grad^h . u| of a
+ * face field (u may be NULL to skip).  Synchronises the stream. */
+paris_status paris_residual_norms(paris_ctx* ctx, const double* beta_x, const double* beta_y,
+                                  const double* beta_z, const double* rhs, const double* p,
+                                  double* rel_l2, double* rel_linf);
+paris_status paris_max_divergence(paris_ctx* ctx, const double* u, const double* v,
+                                  const double* w, double* max_abs_div);
+
+/* Face-array sizes (number of doubles) of the context's grid; axis 0, 1, 2. */
+int64_t paris_face_count(const paris_ctx* ctx, int axis);
+int64_t paris_cell_count(const paris_ctx* ctx);
+
+/* Human-readable name of a status code (static string). */
+const char* paris_status_string(paris_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PARIS_H */

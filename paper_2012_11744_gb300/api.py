@@ -1,0 +1,240 @@
+"""Python binding of the projection library: torch tensors in, C ABI calls out.
+
+Only argument marshalling happens here (shape/dtype/device checks, data
+pointers, the current CUDA stream); every step of the projection runs in the
+CUDA kernels of libparis.so.  The call names follow include/paris.h.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import MIXED, FP64, PERIODIC, WALL, SMOOTH_JACOBI, SMOOTH_RBGS, ParisError  # noqa: F401
+
+
+@dataclass
+class Grid:
+    """nx*ny*nz cubic cells of edge h; bc per axis: PERIODIC (0) or WALL (1)."""
+    nx: int
+    ny: int
+    nz: int
+    h: float
+    bc: tuple = (PERIODIC, PERIODIC, PERIODIC)
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    def face_shape(self, axis: int):
+        n = [self.nz, self.ny, self.nx]
+        n[2 - axis] += 1 if self.bc[axis] == WALL else 0
+        return tuple(n)
+
+
+def default_opts(**kw) -> _abi.Opts:
+    lib = _abi.load()
+    o = _abi.Opts()
+    lib.paris_default_opts(ct.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def _grid_struct(g) -> _abi.Grid:
+    s = _abi.Grid()
+    s.nx, s.ny, s.nz, s.h = int(g.nx), int(g.ny), int(g.nz), float(g.h)
+    for a in range(3):
+        s.bc[a] = int(g.bc[a])
+    return s
+
+
+class Context:
+    """One paris_ctx: a grid, solver options, device workspace and a stream.
+
+    ``stream``: a torch.cuda.Stream (default: the current stream at creation).
+    All tensors passed to the methods must be float64, contiguous and on the
+    context's device.
+    """
+
+    def __init__(self, grid, opts: _abi.Opts | None = None, device=None, stream=None, **kw):
+        self.lib = _abi.load()
+        self.grid = Grid(grid.nx, grid.ny, grid.nz, grid.h, tuple(grid.bc))
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.opts = opts if opts is not None else default_opts(**kw)
+        self._ptr = ct.c_void_p()
+        gs = _grid_struct(self.grid)
+        with torch.cuda.device(self.device):
+            _abi.check(self.lib.paris_create(ct.byref(self._ptr), ct.byref(gs), ct.byref(self.opts),
+                                             ct.c_void_p(self.stream.cuda_stream)), "paris_create")
+
+    # ------------------------------------------------------------ lifetime
+    def close(self):
+        if getattr(self, "_ptr", None) and self._ptr.value:
+            self.lib.paris_destroy(self._ptr)
+            self._ptr = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_opts(self, opts=None, **kw):
+        o = opts if opts is not None else self.opts
+        for k, v in kw.items():
+            setattr(o, k, v)
+        _abi.check(self.lib.paris_set_opts(self._ptr, ct.byref(o)), "paris_set_opts")
+        self.opts = o
+
+    # ------------------------------------------------------------- helpers
+    def _t(self, x: torch.Tensor, shape, name: str) -> ct.c_void_p:
+        if not isinstance(x, torch.Tensor):
+            raise TypeError(f"{name}: expected a torch.Tensor")
+        if x.dtype != torch.float64 or not x.is_contiguous() or x.device != self.device:
+            raise ValueError(f"{name}: need a contiguous float64 tensor on {self.device}")
+        if tuple(x.shape) != tuple(shape) and x.numel() != int(np.prod(shape)):
+            raise ValueError(f"{name}: shape {tuple(x.shape)} != {tuple(shape)}")
+        return ct.c_void_p(x.data_ptr())
+
+    def empty_cells(self):
+        return torch.empty(self.grid.shape, dtype=torch.float64, device=self.device)
+
+    def empty_faces(self):
+        return tuple(torch.empty(self.grid.face_shape(a), dtype=torch.float64, device=self.device)
+                     for a in range(3))
+
+    # --------------------------------------------------------------- steps
+    def face_coeffs(self, C, rho1, rho2, out=None):
+        """beta_f = 1/rho_f (Eq. muH, arithmetic face density), 0 on walls."""
+        bx, by, bz = out if out is not None else self.empty_faces()
+        g = self.grid
+        _abi.check(self.lib.paris_face_coeffs(self._ptr, self._t(C, g.shape, "C"), float(rho1),
+                                              float(rho2), self._t(bx, g.face_shape(0), "beta_x"),
+                                              self._t(by, g.face_shape(1), "beta_y"),
+                                              self._t(bz, g.face_shape(2), "beta_z")),
+                   "paris_face_coeffs")
+        return bx, by, bz
+
+    def divergence(self, u, v, w, dt, out=None, want_mean=True):
+        """rhs = (grad^h . u)/dt with its mean removed; returns (rhs, mean)."""
+        g = self.grid
+        rhs = out if out is not None else self.empty_cells()
+        mean = ct.c_double(0.0)
+        _abi.check(self.lib.paris_divergence(self._ptr, self._t(u, g.face_shape(0), "u"),
+                                             self._t(v, g.face_shape(1), "v"),
+                                             self._t(w, g.face_shape(2), "w"), float(dt),
+                                             self._t(rhs, g.shape, "rhs"),
+                                             ct.byref(mean) if want_mean else None),
+                   "paris_divergence")
+        return rhs, mean.value
+
+    def poisson_solve(self, bx, by, bz, rhs, p, check=True):
+        """Solve grad^h.(beta grad^h p) = rhs (mean(p) = 0); p in/out. Returns stats dict."""
+        g = self.grid
+        st = _abi.Stats()
+        s = self.lib.paris_poisson_solve(self._ptr, self._t(bx, g.face_shape(0), "beta_x"),
+                                         self._t(by, g.face_shape(1), "beta_y"),
+                                         self._t(bz, g.face_shape(2), "beta_z"),
+                                         self._t(rhs, g.shape, "rhs"), self._t(p, g.shape, "p"),
+                                         ct.byref(st))
+        if check:
+            _abi.check(s, "paris_poisson_solve", st.as_dict())
+        d = st.as_dict()
+        d["status"] = s
+        return d
+
+    def project(self, bx, by, bz, p, dt, u, v, w):
+        """u <- u - dt beta grad^h p on non-wall faces (Eq. fotm), wall faces 0."""
+        g = self.grid
+        _abi.check(self.lib.paris_project(self._ptr, self._t(bx, g.face_shape(0), "beta_x"),
+                                          self._t(by, g.face_shape(1), "beta_y"),
+                                          self._t(bz, g.face_shape(2), "beta_z"),
+                                          self._t(p, g.shape, "p"), float(dt),
+                                          self._t(u, g.face_shape(0), "u"),
+                                          self._t(v, g.face_shape(1), "v"),
+                                          self._t(w, g.face_shape(2), "w")), "paris_project")
+
+    def projection_step(self, C, rho1, rho2, dt, u, v, w, p, check=True):
+        """The four steps on device tensors; u, v, w, p updated in place."""
+        g = self.grid
+        st = _abi.Stats()
+        s = self.lib.paris_projection_step(self._ptr, self._t(C, g.shape, "C"), float(rho1),
+                                           float(rho2), float(dt),
+                                           self._t(u, g.face_shape(0), "u"),
+                                           self._t(v, g.face_shape(1), "v"),
+                                           self._t(w, g.face_shape(2), "w"),
+                                           self._t(p, g.shape, "p"), ct.byref(st))
+        if check:
+            _abi.check(s, "paris_projection_step", st.as_dict())
+        d = st.as_dict()
+        d["status"] = s
+        return d
+
+    def projection_step_host(self, C, rho1, rho2, dt, u, v, w, p, check=True):
+        """The four steps on HOST arrays (numpy float64 or CPU torch tensors,
+        ideally pinned); u, v, w, p updated in place."""
+        g = self.grid
+
+        def hp(x, shape, name):
+            if isinstance(x, torch.Tensor):
+                if x.device.type != "cpu" or x.dtype != torch.float64 or not x.is_contiguous():
+                    raise ValueError(f"{name}: need a contiguous float64 CPU tensor")
+                ptr = x.data_ptr()
+                n = x.numel()
+            else:
+                if x.dtype != np.float64 or not x.flags.c_contiguous:
+                    raise ValueError(f"{name}: need a contiguous float64 array")
+                ptr = x.ctypes.data
+                n = x.size
+            if n != int(np.prod(shape)):
+                raise ValueError(f"{name}: size {n} != {shape}")
+            return ct.c_void_p(ptr)
+
+        st = _abi.Stats()
+        s = self.lib.paris_projection_step_host(self._ptr, hp(C, g.shape, "C"), float(rho1),
+                                                float(rho2), float(dt), hp(u, g.face_shape(0), "u"),
+                                                hp(v, g.face_shape(1), "v"),
+                                                hp(w, g.face_shape(2), "w"), hp(p, g.shape, "p"),
+                                                ct.byref(st))
+        if check:
+            _abi.check(s, "paris_projection_step_host", st.as_dict())
+        d = st.as_dict()
+        d["status"] = s
+        return d
+
+    def residual_norms(self, bx, by, bz, rhs, p):
+        """FP64 (||rhs - L p||_2/||rhs||_2, ||.||_inf/||rhs||_inf) on the device."""
+        g = self.grid
+        a, b = ct.c_double(), ct.c_double()
+        _abi.check(self.lib.paris_residual_norms(self._ptr, self._t(bx, g.face_shape(0), "beta_x"),
+                                                 self._t(by, g.face_shape(1), "beta_y"),
+                                                 self._t(bz, g.face_shape(2), "beta_z"),
+                                                 self._t(rhs, g.shape, "rhs"),
+                                                 self._t(p, g.shape, "p"), ct.byref(a), ct.byref(b)),
+                   "paris_residual_norms")
+        return a.value, b.value
+
+    def max_divergence(self, u, v, w):
+        """max |grad^h . u| over the cells, computed on the device."""
+        g = self.grid
+        m = ct.c_double()
+        _abi.check(self.lib.paris_max_divergence(self._ptr, self._t(u, g.face_shape(0), "u"),
+                                                 self._t(v, g.face_shape(1), "v"),
+                                                 self._t(w, g.face_shape(2), "w"), ct.byref(m)),
+                   "paris_max_divergence")
+        return m.value

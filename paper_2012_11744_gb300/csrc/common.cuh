@@ -1,0 +1,145 @@
+// Shared device-side definitions of the projection library: grid geometry,
+// face indexing, the 7-point variable-coefficient stencil and deterministic
+// block reductions.  Internal header (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace paris {
+
+constexpr int kRedThreads = 256;  // threads of every reducing kernel's block
+
+// One grid level: cells per axis and wall flags.  Cell (i,j,k) lives at
+// (k*ny + j)*nx + i; face arrays extend the face axis by one when that axis
+// has walls (entries 0 and n are the wall faces).
+struct Geo {
+    int nx, ny, nz;
+    int wx, wy, wz;
+
+    __host__ __device__ int64_t ncell() const { return (int64_t)nx * ny * nz; }
+    __host__ __device__ int64_t nface(int axis) const {
+        return (int64_t)(nx + (axis == 0 ? wx : 0)) * (ny + (axis == 1 ? wy : 0)) *
+               (nz + (axis == 2 ? wz : 0));
+    }
+    __host__ __device__ int64_t cidx(int i, int j, int k) const {
+        return ((int64_t)k * ny + j) * nx + i;
+    }
+    __host__ __device__ int64_t fx(int i, int j, int k) const {
+        return ((int64_t)k * ny + j) * (nx + wx) + i;
+    }
+    __host__ __device__ int64_t fy(int i, int j, int k) const {
+        return ((int64_t)k * (ny + wy) + j) * nx + i;
+    }
+    __host__ __device__ int64_t fz(int i, int j, int k) const {
+        return ((int64_t)k * ny + j) * nx + i;
+    }
+};
+
+// Coefficient set of one level: face arrays and a uniform scale (1/h^2 for
+// arrays holding beta itself, 1 for arrays that are already scaled).
+template <typename T>
+struct Coef {
+    const T* bx;
+    const T* by;
+    const T* bz;
+    T scale;
+};
+
+// Neighbour indices and + face index along one axis of length n.  Along a
+// wall axis the missing neighbour is clamped onto the cell itself; its face
+// coefficient is forced to zero (Neumann by coefficient zeroing).
+struct AxisNb {
+    int m, p, fp;   // minus neighbour, plus neighbour, index of the + face
+    bool wm, wp;    // minus / plus face is a wall
+};
+
+__host__ __device__ inline AxisNb axis_nb(int i, int n, int wall) {
+    AxisNb a;
+    a.wm = wall && i == 0;
+    a.wp = wall && i == n - 1;
+    a.m = i > 0 ? i - 1 : (wall ? 0 : n - 1);
+    a.p = i + 1 < n ? i + 1 : (wall ? n - 1 : 0);
+    a.fp = (i + 1 < n || wall) ? i + 1 : 0;
+    return a;
+}
+
+// The six face coefficients (unscaled) around cell (i,j,k) and the neighbour
+// cell indices, in the order x-, x+, y-, y+, z-, z+.
+template <typename T>
+struct Stencil {
+    T b[6];
+    int64_t nb[6];
+};
+
+template <typename T>
+__device__ inline void load_stencil(const Geo& g, const Coef<T>& cf, int i, int j, int k,
+                                    Stencil<T>& s) {
+    AxisNb ax = axis_nb(i, g.nx, g.wx);
+    AxisNb ay = axis_nb(j, g.ny, g.wy);
+    AxisNb az = axis_nb(k, g.nz, g.wz);
+    s.b[0] = ax.wm ? T(0) : cf.bx[g.fx(i, j, k)];
+    s.b[1] = ax.wp ? T(0) : cf.bx[g.fx(ax.fp, j, k)];
+    s.b[2] = ay.wm ? T(0) : cf.by[g.fy(i, j, k)];
+    s.b[3] = ay.wp ? T(0) : cf.by[g.fy(i, ay.fp, k)];
+    s.b[4] = az.wm ? T(0) : cf.bz[g.fz(i, j, k)];
+    s.b[5] = az.wp ? T(0) : cf.bz[g.fz(i, j, az.fp)];
+    s.nb[0] = g.cidx(ax.m, j, k);
+    s.nb[1] = g.cidx(ax.p, j, k);
+    s.nb[2] = g.cidx(i, ay.m, k);
+    s.nb[3] = g.cidx(i, ay.p, k);
+    s.nb[4] = g.cidx(i, j, az.m);
+    s.nb[5] = g.cidx(i, j, az.p);
+}
+
+// (A x)_c with A = -L: scale * sum_f beta_f (x_c - x_nb)  (difference form,
+// which keeps the FP64 residual accurate when x is smooth).
+template <typename T>
+__device__ inline T apply_A(const Stencil<T>& s, const T* __restrict__ x, T xc, T scale) {
+    T acc = s.b[0] * (xc - x[s.nb[0]]);
+#pragma unroll
+    for (int q = 1; q < 6; ++q) acc = fma(s.b[q], xc - x[s.nb[q]], acc);
+    return scale * acc;
+}
+
+// ------------------------------------------------------------ reductions ---
+
+__device__ inline double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ inline double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Reduce NV values over a block of kRedThreads threads (ops: 0 = sum,
+// 1 = max) in a fixed order and store them as this block's partials at
+// partials[NV*block + q].  Deterministic: the order depends only on the
+// thread layout.
+template <int NV>
+__device__ inline void block_reduce_store(double (&v)[NV], const int (&op)[NV], double* partials,
+                                          int64_t block, int tid) {
+    __shared__ double sh[kRedThreads / 32][NV];
+    const int lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = op[q] ? warp_max(v[q]) : warp_sum(v[q]);
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) sh[wid][q] = v[q];
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double t = lane < kRedThreads / 32 ? sh[lane][q] : (op[q] ? 0.0 : 0.0);
+            t = op[q] ? warp_max(t) : warp_sum(t);
+            if (lane == 0) partials[NV * block + q] = t;
+        }
+    }
+}
+
+}  // namespace paris

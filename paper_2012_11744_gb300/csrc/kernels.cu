@@ -1,0 +1,804 @@
+// CUDA kernels of the one-fluid pressure projection (sm_103a).
+//
+// Paper references: PARIS, arXiv 2012.11744.  Eq. muH (one-fluid density),
+// Eqs. cont2/incompdisc3 (divergence on the staggered grid), Eq. poisson and
+// the A1..A8 system form with its over-relaxed red-black Gauss-Seidel update
+// (Eq. eq:beta_pressure, Sec. 3.7.1), the V-cycle of Sec. 3.7.3, the Jacobi
+// iteration of Sec. 3.7.4, the link-flag coefficient zeroing at walls
+// (Sec. 3.8) and the velocity correction Eq. fotm.
+//
+// Stencil kernels work in the SPD form A = -L, A x = f with f = -b:
+//   (A x)_c = scale * sum_f beta_f (x_c - x_nb),
+// i.e. the paper's A7 p - sum A_nb p_nb with A_nb = beta_f scale.
+#include <math.h>
+
+#include "kernels.cuh"
+
+namespace paris {
+
+namespace {
+
+constexpr int kTX = 32, kTY = 8;  // 2-D tile of the stencil kernels (x fastest)
+constexpr int kZ = 8;             // cells per thread along z in reducing stencil kernels
+
+inline dim3 tile_grid(const Geo& g, int zper) {
+    return dim3((g.nx + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, (g.nz + zper - 1) / zper);
+}
+
+inline int64_t nblocks_of(dim3 gr) { return (int64_t)gr.x * gr.y * gr.z; }
+
+__device__ inline int64_t flat_block() {
+    return ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+}
+
+__device__ inline int flat_tid() { return threadIdx.y * blockDim.x + threadIdx.x; }
+
+__device__ inline double nonfinite(double v) { return isfinite(v) ? 0.0 : 1.0; }
+
+}  // namespace
+
+int elementwise_blocks(int64_t n) {
+    int64_t b = (n + kRedThreads - 1) / kRedThreads;
+    const int64_t cap = 152 * 8;  // 8 resident 256-thread blocks on each of the 152 SMs
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+// ---------------------------------------------------------------- finalize ---
+
+// Deterministic second stage of every reduction: one CTA folds the block
+// partials in a fixed order, then thread 0 applies the scalar update `mode`.
+__global__ void finalize_kernel(const double* __restrict__ partials, int64_t nblocks, int nv,
+                                int maxmask, Scal* s, int mode, double param) {
+    __shared__ double sh[kRedThreads / 32][4];
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    const int tid = threadIdx.x;
+    for (int64_t b = tid; b < nblocks; b += kRedThreads)
+        for (int q = 0; q < nv; ++q) {
+            double t = partials[(int64_t)nv * b + q];
+            v[q] = ((maxmask >> q) & 1) ? fmax(v[q], t) : v[q] + t;
+        }
+    const int lane = tid & 31, wid = tid >> 5;
+    for (int q = 0; q < 4; ++q) {
+        v[q] = ((maxmask >> q) & 1) ? warp_max(v[q]) : warp_sum(v[q]);
+        if (lane == 0) sh[wid][q] = v[q];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double r[4];
+        for (int q = 0; q < 4; ++q) {
+            double t = 0.0;
+            for (int w = 0; w < kRedThreads / 32; ++w)
+                t = ((maxmask >> q) & 1) ? fmax(t, sh[w][q]) : t + sh[w][q];
+            r[q] = t;
+            s->red[q] = t;
+        }
+        switch (mode) {
+            case FIN_MEAN_B: s->mean_b = r[0] / param; s->nonfinite += r[2]; break;
+            case FIN_BNORMS:  // the first residual of a solve is f itself: seed rinf with |f|inf
+                s->bnorm2 = r[0]; s->binf = r[1]; s->rinf = r[1]; s->nonfinite += r[2]; break;
+            case FIN_RNORMS: s->rr = r[0]; s->rinf = r[1]; s->nonfinite += r[2]; break;
+            case FIN_ALPHA: s->alpha = (r[0] > 0.0) ? s->rho / r[0] : 0.0; break;
+            case FIN_RHO_BETA: s->beta = (s->rho != 0.0) ? r[0] / s->rho : 0.0; s->rho = r[0]; break;
+            case FIN_RHO_INIT: s->rho = r[0]; s->beta = 0.0; break;
+            case FIN_FCG_BETA:
+                s->beta = (s->rho != 0.0) ? -s->alpha * r[1] / s->rho : 0.0;
+                s->rho = r[0];
+                break;
+            case FIN_SCALE: {
+                // r32 = scale * r64 keeps the FP32 inner problem O(1)
+                double m = s->rinf > 1e-300 ? s->rinf : 1.0;
+                s->scale = 1.0 / m;
+                s->inv_scale = m;
+                break;
+            }
+            case FIN_INNER_INIT: s->rr0 = r[0]; s->rr = r[0]; s->rinf = r[1]; break;
+            default: break;
+        }
+    }
+}
+
+void finalize(const double* partials, int64_t nblocks, int nv, int maxmask, Scal* s, int mode,
+              double param, cudaStream_t st) {
+    finalize_kernel<<<1, kRedThreads, 0, st>>>(partials, nblocks, nv, maxmask, s, mode, param);
+}
+
+// ------------------------------------------------------- face coefficients ---
+
+// Eq. muH: rho = rho1 C + rho2 (1 - C); beta_f = 1/rho_f with rho_f the mean
+// of the two cells (the paper's "interpolation of 1/rho" read as the mean of
+// rho, then inverted); wall faces 0 (Sec. 3.8).  One thread per cell writes
+// the - face of each axis, and the last cell of a wall axis also writes the
+// + wall face.
+__global__ void face_coeffs_kernel(Geo g, const double* __restrict__ C, double rho1, double rho2,
+                                   double* __restrict__ bx, double* __restrict__ by,
+                                   double* __restrict__ bz) {
+    const int i = blockIdx.x * kTX + threadIdx.x;
+    const int j = blockIdx.y * kTY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    const double drho = rho1 - rho2;
+    const double rc = fma(drho, C[g.cidx(i, j, k)], rho2);
+    AxisNb ax = axis_nb(i, g.nx, g.wx), ay = axis_nb(j, g.ny, g.wy), az = axis_nb(k, g.nz, g.wz);
+    {
+        double rl = fma(drho, C[g.cidx(ax.m, j, k)], rho2);
+        bx[g.fx(i, j, k)] = ax.wm ? 0.0 : 2.0 / (rl + rc);
+        if (g.wx && i == g.nx - 1) bx[g.fx(g.nx, j, k)] = 0.0;
+    }
+    {
+        double rl = fma(drho, C[g.cidx(i, ay.m, k)], rho2);
+        by[g.fy(i, j, k)] = ay.wm ? 0.0 : 2.0 / (rl + rc);
+        if (g.wy && j == g.ny - 1) by[g.fy(i, g.ny, k)] = 0.0;
+    }
+    {
+        double rl = fma(drho, C[g.cidx(i, j, az.m)], rho2);
+        bz[g.fz(i, j, k)] = az.wm ? 0.0 : 2.0 / (rl + rc);
+        if (g.wz && k == g.nz - 1) bz[g.fz(i, j, g.nz)] = 0.0;
+    }
+}
+
+void launch_face_coeffs(const Geo& g, const double* C, double rho1, double rho2, double* bx,
+                        double* by, double* bz, cudaStream_t st) {
+    dim3 gr((g.nx + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, g.nz);
+    face_coeffs_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(g, C, rho1, rho2, bx, by, bz);
+}
+
+// -------------------------------------------------------------- divergence ---
+
+// Sum over the axes of (u_{+face} - u_{-face}) (Eqs. cont2, incompdisc3),
+// wall faces carrying no flux; times 1/(h dt).
+__device__ inline double cell_div(const Geo& g, const double* __restrict__ u,
+                                  const double* __restrict__ v, const double* __restrict__ w,
+                                  int i, int j, int k) {
+    AxisNb ax = axis_nb(i, g.nx, g.wx), ay = axis_nb(j, g.ny, g.wy), az = axis_nb(k, g.nz, g.wz);
+    double up = ax.wp ? 0.0 : u[g.fx(ax.fp, j, k)];
+    double um = ax.wm ? 0.0 : u[g.fx(i, j, k)];
+    double vp = ay.wp ? 0.0 : v[g.fy(i, ay.fp, k)];
+    double vm = ay.wm ? 0.0 : v[g.fy(i, j, k)];
+    double wp = az.wp ? 0.0 : w[g.fz(i, j, az.fp)];
+    double wm = az.wm ? 0.0 : w[g.fz(i, j, k)];
+    return ((up - um) + (vp - vm)) + (wp - wm);
+}
+
+__global__ void __launch_bounds__(kTX* kTY) divergence_kernel(Geo g, const double* __restrict__ u,
+                                                              const double* __restrict__ v,
+                                                              const double* __restrict__ w,
+                                                              double inv_hdt,
+                                                              double* __restrict__ rhs,
+                                                              double* partials) {
+    const int i = blockIdx.x * kTX + threadIdx.x;
+    const int j = blockIdx.y * kTY + threadIdx.y;
+    double acc[3] = {0.0, 0.0, 0.0};
+    if (i < g.nx && j < g.ny) {
+        const int k0 = blockIdx.z * kZ, k1 = min(k0 + kZ, g.nz);
+        for (int k = k0; k < k1; ++k) {
+            double b = cell_div(g, u, v, w, i, j, k) * inv_hdt;
+            rhs[g.cidx(i, j, k)] = b;
+            acc[0] += b;
+            acc[1] = fmax(acc[1], fabs(b));
+            acc[2] += nonfinite(b);
+        }
+    }
+    const int op[3] = {0, 1, 0};
+    block_reduce_store<3>(acc, op, partials, flat_block(), flat_tid());
+}
+
+int64_t launch_divergence(const Geo& g, const double* u, const double* v, const double* w,
+                          double inv_hdt, double* rhs, double* partials, cudaStream_t st) {
+    dim3 gr = tile_grid(g, kZ);
+    divergence_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(g, u, v, w, inv_hdt, rhs, partials);
+    return nblocks_of(gr);
+}
+
+__global__ void __launch_bounds__(kTX* kTY) max_div_kernel(Geo g, const double* __restrict__ u,
+                                                           const double* __restrict__ v,
+                                                           const double* __restrict__ w,
+                                                           double inv_h, double* partials) {
+    const int i = blockIdx.x * kTX + threadIdx.x;
+    const int j = blockIdx.y * kTY + threadIdx.y;
+    double acc[1] = {0.0};
+    if (i < g.nx && j < g.ny) {
+        const int k0 = blockIdx.z * kZ, k1 = min(k0 + kZ, g.nz);
+        for (int k = k0; k < k1; ++k) acc[0] = fmax(acc[0], fabs(cell_div(g, u, v, w, i, j, k) * inv_h));
+    }
+    const int op[1] = {1};
+    block_reduce_store<1>(acc, op, partials, flat_block(), flat_tid());
+}
+
+int64_t launch_max_divergence(const Geo& g, const double* u, const double* v, const double* w,
+                              double inv_h, double* partials, cudaStream_t st) {
+    dim3 gr = tile_grid(g, kZ);
+    max_div_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(g, u, v, w, inv_h, partials);
+    return nblocks_of(gr);
+}
+
+// f = -(rhs - mean_b): the right-hand side of the SPD system A p = f.
+__global__ void make_rhs_kernel(int64_t n, const double* __restrict__ rhs, const Scal* s,
+                                double* __restrict__ f, double* partials) {
+    const double mb = s->mean_b;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        double t = -(rhs[c] - mb);
+        f[c] = t;
+        acc[0] = fma(t, t, acc[0]);
+        acc[1] = fmax(acc[1], fabs(t));
+        acc[2] += nonfinite(t);
+    }
+    const int op[3] = {0, 1, 0};
+    block_reduce_store<3>(acc, op, partials, blockIdx.x, threadIdx.x);
+}
+
+int64_t launch_make_rhs(int64_t n, const double* rhs, const Scal* s, double* f, double* partials,
+                        cudaStream_t st) {
+    int nb = elementwise_blocks(n);
+    make_rhs_kernel<<<nb, kRedThreads, 0, st>>>(n, rhs, s, f, partials);
+    return nb;
+}
+
+__global__ void sub_mean_kernel(int64_t n, double* __restrict__ x, const Scal* s) {
+    const double m = s->red[0] / (double)n;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x)
+        x[c] -= m;
+}
+
+void launch_sub_mean(int64_t n, double* x, const Scal* s, cudaStream_t st) {
+    sub_mean_kernel<<<elementwise_blocks(n), kRedThreads, 0, st>>>(n, x, s);
+}
+
+__global__ void sum_kernel(int64_t n, const double* __restrict__ x, double* partials) {
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        acc[0] += x[c];
+        acc[1] = fmax(acc[1], fabs(x[c]));
+        acc[2] += nonfinite(x[c]);
+    }
+    const int op[3] = {0, 1, 0};
+    block_reduce_store<3>(acc, op, partials, blockIdx.x, threadIdx.x);
+}
+
+int64_t launch_sum(int64_t n, const double* x, double* partials, cudaStream_t st) {
+    int nb = elementwise_blocks(n);
+    sum_kernel<<<nb, kRedThreads, 0, st>>>(n, x, partials);
+    return nb;
+}
+
+// ------------------------------------------------------ velocity correction ---
+
+// Eq. fotm: u_f -= dt beta_f (p_R - p_L)/h on non-wall faces; wall faces
+// blocked to 0 (Sec. 3.8).  Thread per cell, handling its - faces (and the
+// + wall face of the last cell of a wall axis).
+__global__ void project_kernel(Geo g, const double* __restrict__ bx, const double* __restrict__ by,
+                               const double* __restrict__ bz, const double* __restrict__ p,
+                               double dt_over_h, double* __restrict__ u, double* __restrict__ v,
+                               double* __restrict__ w) {
+    const int i = blockIdx.x * kTX + threadIdx.x;
+    const int j = blockIdx.y * kTY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    const double pc = p[g.cidx(i, j, k)];
+    AxisNb ax = axis_nb(i, g.nx, g.wx), ay = axis_nb(j, g.ny, g.wy), az = axis_nb(k, g.nz, g.wz);
+    {
+        int64_t f = g.fx(i, j, k);
+        u[f] = ax.wm ? 0.0 : u[f] - dt_over_h * bx[f] * (pc - p[g.cidx(ax.m, j, k)]);
+        if (g.wx && i == g.nx - 1) u[g.fx(g.nx, j, k)] = 0.0;
+    }
+    {
+        int64_t f = g.fy(i, j, k);
+        v[f] = ay.wm ? 0.0 : v[f] - dt_over_h * by[f] * (pc - p[g.cidx(i, ay.m, k)]);
+        if (g.wy && j == g.ny - 1) v[g.fy(i, g.ny, k)] = 0.0;
+    }
+    {
+        int64_t f = g.fz(i, j, k);
+        w[f] = az.wm ? 0.0 : w[f] - dt_over_h * bz[f] * (pc - p[g.cidx(i, j, az.m)]);
+        if (g.wz && k == g.nz - 1) w[g.fz(i, j, g.nz)] = 0.0;
+    }
+}
+
+void launch_project(const Geo& g, const double* bx, const double* by, const double* bz,
+                    const double* p, double dt_over_h, double* u, double* v, double* w,
+                    cudaStream_t st) {
+    dim3 gr((g.nx + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, g.nz);
+    project_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(g, bx, by, bz, p, dt_over_h, u, v, w);
+}
+
+// ------------------------------------------------------------ level set-up ---
+
+// Level-0 coefficient copy in the solver's precision, pre-multiplied by scale.
+template <typename T>
+__global__ void convert_beta_kernel(int64_t n, const double* __restrict__ b, double scale,
+                                    T* __restrict__ out) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x)
+        out[c] = (T)(b[c] * scale);
+}
+
+template <typename T>
+void launch_convert_beta(const Geo& g, const double* b64[3], double scale, T* out[3],
+                         cudaStream_t st) {
+    for (int a = 0; a < 3; ++a) {
+        int64_t n = g.nface(a);
+        convert_beta_kernel<T><<<elementwise_blocks(n), kRedThreads, 0, st>>>(n, b64[a], scale,
+                                                                              out[a]);
+    }
+}
+
+// Rediscretised coarse coefficients (the paper gives no coarsening rule,
+// Sec. 3.7.3): a coarse face normal to axis a is covered by the fine faces
+// at fine index f_a*I_a along a and f_b*I_b + {0..f_b-1} along the other
+// axes b; its coefficient is their mean times (h_fine/h_coarse)^2 along a
+// (the arrays hold beta/h_a^2).  Wall faces stay 0.
+template <typename T>
+__global__ void coarse_beta_kernel(Geo fg, Coef<T> cf, Geo cg, int fa0, int fa1, int fa2,
+                                   int axis, double ratio, T* __restrict__ out) {
+    const int n0 = cg.nx + (axis == 0 ? cg.wx : 0);
+    const int n1 = cg.ny + (axis == 1 ? cg.wy : 0);
+    const int n2 = cg.nz + (axis == 2 ? cg.wz : 0);
+    const int64_t total = (int64_t)n0 * n1 * n2;
+    const int fac[3] = {fa0, fa1, fa2};
+    const T* src = axis == 0 ? cf.bx : (axis == 1 ? cf.by : cf.bz);
+    const int fn0 = fg.nx + (axis == 0 ? fg.wx : 0);
+    const int fn1 = fg.ny + (axis == 1 ? fg.wy : 0);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int I = (int)(t % n0);
+        const int J = (int)((t / n0) % n1);
+        const int K = (int)(t / ((int64_t)n0 * n1));
+        const int C3[3] = {I, J, K};
+        int lo[3], cnt[3];
+        for (int b = 0; b < 3; ++b) {
+            if (b == axis) { lo[b] = C3[b] * fac[b]; cnt[b] = 1; }
+            else { lo[b] = C3[b] * fac[b]; cnt[b] = fac[b]; }
+        }
+        double sum = 0.0;
+        for (int dk = 0; dk < cnt[2]; ++dk)
+            for (int dj = 0; dj < cnt[1]; ++dj)
+                for (int di = 0; di < cnt[0]; ++di) {
+                    int64_t fi = ((int64_t)(lo[2] + dk) * fn1 + (lo[1] + dj)) * fn0 + (lo[0] + di);
+                    sum += (double)src[fi];
+                }
+        double mean = sum / (double)(cnt[0] * cnt[1] * cnt[2]);
+        out[t] = (T)(mean * ratio * (double)cf.scale);
+    }
+}
+
+template <typename T>
+void launch_coarse_beta(const Geo& fine, const Coef<T>& cf, const Geo& coarse, const int f[3],
+                        const double hc2_over_hf2[3], T* out[3], cudaStream_t st) {
+    for (int a = 0; a < 3; ++a) {
+        int64_t n = coarse.nface(a);
+        coarse_beta_kernel<T><<<elementwise_blocks(n), kRedThreads, 0, st>>>(
+            fine, cf, coarse, f[0], f[1], f[2], a, 1.0 / hc2_over_hf2[a], out[a]);
+    }
+}
+
+// w = 1 / sum_f beta_f (unscaled inverse diagonal; the smoother divides the
+// right-hand side by the level's scale).
+template <typename T>
+__global__ void inv_diag_kernel(Geo g, Coef<T> cf, T* __restrict__ w) {
+    const int i = blockIdx.x * kTX + threadIdx.x;
+    const int j = blockIdx.y * kTY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    Stencil<T> s;
+    load_stencil(g, cf, i, j, k, s);
+    T d = ((s.b[0] + s.b[1]) + (s.b[2] + s.b[3])) + (s.b[4] + s.b[5]);
+    w[g.cidx(i, j, k)] = d > T(0) ? T(1) / d : T(0);
+}
+
+template <typename T>
+void launch_inv_diag(const Geo& g, const Coef<T>& cf, T* w, cudaStream_t st) {
+    dim3 gr((g.nx + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, g.nz);
+    inv_diag_kernel<T><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, w);
+}
+
+// Dense inverse of the coarsest operator regularised on its null space:
+// (A + a 1 1^T)^{-1} with a = mean(diag)/n, which maps a mean-free f to the
+// mean-free solution of A x = f.  FP64 Gauss-Jordan without pivoting (the
+// regularised matrix is SPD) by one CTA; n <= 128.
+template <typename T>
+__global__ void coarse_inverse_kernel(Geo g, Coef<T> cf, double* __restrict__ M) {
+    const int n = (int)g.ncell();
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < n * n; e += nt) M[e] = 0.0;
+    __syncthreads();
+    __shared__ double dsum;
+    if (tid == 0) dsum = 0.0;
+    __syncthreads();
+    for (int c = tid; c < n; c += nt) {
+        const int i = c % g.nx, j = (c / g.nx) % g.ny, k = c / (g.nx * g.ny);
+        Stencil<T> s;
+        load_stencil(g, cf, i, j, k, s);
+        for (int q = 0; q < 6; ++q) {
+            double b = (double)s.b[q] * (double)cf.scale;
+            M[(int64_t)c * n + c] += b;
+            M[(int64_t)c * n + s.nb[q]] -= b;  // a self-neighbour (n = 1) cancels
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int c = 0; c < n; ++c) t += M[(int64_t)c * n + c];
+        dsum = t;
+    }
+    __syncthreads();
+    const double a = dsum / ((double)n * (double)n);
+    for (int e = tid; e < n * n; e += nt) M[e] += a;
+    __syncthreads();
+    // in-place Gauss-Jordan inversion
+    __shared__ double piv;
+    extern __shared__ double col[];  // n entries: column k before the pivot step
+    for (int kk = 0; kk < n; ++kk) {
+        if (tid == 0) piv = 1.0 / M[(int64_t)kk * n + kk];
+        __syncthreads();
+        for (int r = tid; r < n; r += nt) col[r] = M[(int64_t)r * n + kk];
+        __syncthreads();
+        // scale the pivot row
+        for (int c = tid; c < n; c += nt)
+            M[(int64_t)kk * n + c] = (c == kk) ? piv : M[(int64_t)kk * n + c] * piv;
+        __syncthreads();
+        // eliminate column kk from the other rows
+        for (int e = tid; e < n * n; e += nt) {
+            int r = e / n, c = e % n;
+            if (r == kk) continue;
+            double f = col[r];
+            if (c == kk) M[e] = -f * piv;
+            else M[e] -= f * M[(int64_t)kk * n + c];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+void launch_coarse_inverse(const Geo& g, const Coef<T>& cf, double* inv, cudaStream_t st) {
+    int n = (int)g.ncell();
+    coarse_inverse_kernel<T><<<1, 256, sizeof(double) * n, st>>>(g, cf, inv);
+}
+
+// x = M (f - mean f) on the coarsest level (FP64 arithmetic).
+template <typename T>
+__global__ void coarse_solve_kernel(int n, const double* __restrict__ M, const T* __restrict__ f,
+                                    T* __restrict__ x) {
+    extern __shared__ double fs[];
+    __shared__ double mean;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int c = tid; c < n; c += nt) fs[c] = (double)f[c];
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int c = 0; c < n; ++c) t += fs[c];
+        mean = t / (double)n;
+    }
+    __syncthreads();
+    for (int r = tid; r < n; r += nt) {
+        double acc = 0.0;
+        for (int c = 0; c < n; ++c) acc = fma(M[(int64_t)r * n + c], fs[c] - mean, acc);
+        x[r] = (T)acc;
+    }
+}
+
+template <typename T>
+void launch_coarse_solve(const Geo& g, const double* inv, const T* f, T* x, cudaStream_t st) {
+    int n = (int)g.ncell();
+    coarse_solve_kernel<T><<<1, 128, sizeof(double) * n, st>>>(n, inv, f, x);
+}
+
+// ------------------------------------------------------------------ smoothers ---
+
+// Over-relaxed Gauss-Seidel update of Eq. eq:beta_pressure in the SPD form:
+//   x_c <- x_c + omega ( w_c (f_c/scale + sum_f beta_f x_nb) - x_c ),
+// w_c = 1/sum_f beta_f.  One thread per x-pair (2t, 2t+1) of a row updates
+// the member of colour `color` ((i+j+k) even = red = 0).  With zero_init the
+// incoming x is taken as zero and the other member of the pair is zeroed.
+template <typename T>
+__global__ void __launch_bounds__(kTX* kTY) rbgs_kernel(Geo g, Coef<T> cf, const T* __restrict__ w,
+                                                       const T* __restrict__ f, T* __restrict__ x,
+                                                       int color, T omega, int zero_init) {
+    const int t = blockIdx.x * kTX + threadIdx.x;
+    const int j = blockIdx.y * kTY + threadIdx.y;
+    const int k = blockIdx.z;
+    const int i0 = 2 * t;
+    if (i0 >= g.nx || j >= g.ny) return;
+    const int i = i0 + ((i0 + j + k + color) & 1);
+    const int io = i0 + 1 - (i - i0);  // the other member of the pair
+    const T hs = T(1) / cf.scale;
+    if (i < g.nx) {
+        const int64_t c = g.cidx(i, j, k);
+        T xn;
+        if (zero_init) {
+            xn = omega * w[c] * (f[c] * hs);
+        } else {
+            Stencil<T> s;
+            load_stencil(g, cf, i, j, k, s);
+            T acc = f[c] * hs;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) acc = fma(s.b[q], x[s.nb[q]], acc);
+            const T xc = x[c];
+            xn = fma(omega, fma(w[c], acc, -xc), xc);
+        }
+        x[c] = xn;
+    }
+    if (zero_init && io < g.nx) x[g.cidx(io, j, k)] = T(0);
+}
+
+template <typename T>
+void launch_rbgs(const Geo& g, const Coef<T>& cf, const T* w, const T* f, T* x, int color,
+                 double omega, bool zero_init, cudaStream_t st) {
+    const int npair = (g.nx + 1) / 2;
+    dim3 gr((npair + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, g.nz);
+    rbgs_kernel<T><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, w, f, x, color, (T)omega,
+                                                  zero_init ? 1 : 0);
+}
+
+// Damped Jacobi (the paper's GPU iteration, Sec. 3.7.4), double-buffered:
+//   x_out = x + omega (w (f/scale + sum beta x_nb) - x).
+template <typename T>
+__global__ void __launch_bounds__(kTX* kTY) jacobi_kernel(Geo g, Coef<T> cf,
+                                                         const T* __restrict__ w,
+                                                         const T* __restrict__ f,
+                                                         const T* __restrict__ x,
+                                                         T* __restrict__ xo, T omega,
+                                                         int zero_init) {
+    const int i = blockIdx.x * kTX + threadIdx.x;
+    const int j = blockIdx.y * kTY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    const int64_t c = g.cidx(i, j, k);
+    const T hs = T(1) / cf.scale;
+    if (zero_init) {
+        xo[c] = omega * w[c] * (f[c] * hs);
+        return;
+    }
+    Stencil<T> s;
+    load_stencil(g, cf, i, j, k, s);
+    T acc = f[c] * hs;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) acc = fma(s.b[q], x[s.nb[q]], acc);
+    const T xc = x[c];
+    xo[c] = fma(omega, fma(w[c], acc, -xc), xc);
+}
+
+template <typename T>
+void launch_jacobi(const Geo& g, const Coef<T>& cf, const T* w, const T* f, const T* x, T* xout,
+                   double omega, bool zero_init, cudaStream_t st) {
+    dim3 gr((g.nx + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, g.nz);
+    jacobi_kernel<T><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, w, f, x, xout, (T)omega,
+                                                    zero_init ? 1 : 0);
+}
+
+// ------------------------------------------------- restriction / prolongation ---
+
+// Coarse right-hand side: the average over the children of the fine residual
+// f - A x (restriction R = P^T / #children for the piecewise-constant P).
+template <typename T>
+__global__ void restrict_residual_kernel(Geo fg, Coef<T> cf, const T* __restrict__ f,
+                                         const T* __restrict__ x, Geo cg, int fa0, int fa1,
+                                         int fa2, T* __restrict__ fc) {
+    const int I = blockIdx.x * kTX + threadIdx.x;
+    const int J = blockIdx.y * kTY + threadIdx.y;
+    const int K = blockIdx.z;
+    if (I >= cg.nx || J >= cg.ny) return;
+    T sum = T(0);
+    for (int dk = 0; dk < fa2; ++dk)
+        for (int dj = 0; dj < fa1; ++dj)
+            for (int di = 0; di < fa0; ++di) {
+                const int i = I * fa0 + di, j = J * fa1 + dj, k = K * fa2 + dk;
+                const int64_t c = fg.cidx(i, j, k);
+                Stencil<T> s;
+                load_stencil(fg, cf, i, j, k, s);
+                sum += f[c] - apply_A(s, x, x[c], cf.scale);
+            }
+    fc[cg.cidx(I, J, K)] = sum / T(fa0 * fa1 * fa2);
+}
+
+template <typename T>
+void launch_restrict_residual(const Geo& fine, const Coef<T>& cf, const T* f, const T* x,
+                             const Geo& coarse, const int fac[3], T* fc, cudaStream_t st) {
+    dim3 gr((coarse.nx + kTX - 1) / kTX, (coarse.ny + kTY - 1) / kTY, coarse.nz);
+    restrict_residual_kernel<T><<<gr, dim3(kTX, kTY), 0, st>>>(fine, cf, f, x, coarse, fac[0],
+                                                               fac[1], fac[2], fc);
+}
+
+template <typename T>
+__global__ void prolong_add_kernel(Geo fg, Geo cg, int fa0, int fa1, int fa2,
+                                   const T* __restrict__ xc, T* __restrict__ x) {
+    const int i = blockIdx.x * kTX + threadIdx.x;
+    const int j = blockIdx.y * kTY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= fg.nx || j >= fg.ny) return;
+    x[fg.cidx(i, j, k)] += xc[cg.cidx(i / fa0, j / fa1, k / fa2)];
+}
+
+template <typename T>
+void launch_prolong_add(const Geo& fine, const Geo& coarse, const int fac[3], const T* xc, T* x,
+                        cudaStream_t st) {
+    dim3 gr((fine.nx + kTX - 1) / kTX, (fine.ny + kTY - 1) / kTY, fine.nz);
+    prolong_add_kernel<T><<<gr, dim3(kTX, kTY), 0, st>>>(fine, coarse, fac[0], fac[1], fac[2], xc,
+                                                         x);
+}
+
+// ------------------------------------------------------------------ Krylov ---
+
+// FP64 residual r = f - A x with fused norms; the mixed form also writes the
+// scaled FP32 copy r32 = scale * r that the inner solve starts from.
+__global__ void __launch_bounds__(kTX* kTY) residual64_kernel(Geo g, Coef<double> cf,
+                                                              const double* __restrict__ f,
+                                                              const double* __restrict__ x,
+                                                              double* __restrict__ r64,
+                                                              float* __restrict__ r32,
+                                                              const Scal* s, double* partials) {
+    const int i = blockIdx.x * kTX + threadIdx.x;
+    const int j = blockIdx.y * kTY + threadIdx.y;
+    double acc[3] = {0.0, 0.0, 0.0};
+    if (i < g.nx && j < g.ny) {
+        const double sc = r32 ? s->scale : 0.0;
+        const int k0 = blockIdx.z * kZ, k1 = min(k0 + kZ, g.nz);
+        for (int k = k0; k < k1; ++k) {
+            const int64_t c = g.cidx(i, j, k);
+            Stencil<double> st;
+            load_stencil(g, cf, i, j, k, st);
+            double r = f[c] - apply_A(st, x, x[c], cf.scale);
+            if (r64) r64[c] = r;
+            if (r32) r32[c] = (float)(r * sc);
+            acc[0] = fma(r, r, acc[0]);
+            acc[1] = fmax(acc[1], fabs(r));
+            acc[2] += nonfinite(r);
+        }
+    }
+    const int op[3] = {0, 1, 0};
+    block_reduce_store<3>(acc, op, partials, flat_block(), flat_tid());
+}
+
+int64_t launch_residual64(const Geo& g, const Coef<double>& cf, const double* f, const double* x,
+                          double* r64, float* r32, const Scal* s, double* partials,
+                          cudaStream_t st) {
+    dim3 gr = tile_grid(g, kZ);
+    residual64_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, f, x, r64, r32, s, partials);
+    return nblocks_of(gr);
+}
+
+// q = A d and the partial sums of d . q (accumulated per thread in T,
+// across threads and blocks in FP64).
+template <typename T>
+__global__ void __launch_bounds__(kTX* kTY) matvec_dot_kernel(Geo g, Coef<T> cf,
+                                                             const T* __restrict__ d,
+                                                             T* __restrict__ q,
+                                                             double* partials) {
+    const int i = blockIdx.x * kTX + threadIdx.x;
+    const int j = blockIdx.y * kTY + threadIdx.y;
+    T loc = T(0);
+    if (i < g.nx && j < g.ny) {
+        const int k0 = blockIdx.z * kZ, k1 = min(k0 + kZ, g.nz);
+        for (int k = k0; k < k1; ++k) {
+            const int64_t c = g.cidx(i, j, k);
+            Stencil<T> st;
+            load_stencil(g, cf, i, j, k, st);
+            const T dc = d[c];
+            const T qc = apply_A(st, d, dc, cf.scale);
+            q[c] = qc;
+            loc = fma(dc, qc, loc);
+        }
+    }
+    double acc[1] = {(double)loc};
+    const int op[1] = {0};
+    block_reduce_store<1>(acc, op, partials, flat_block(), flat_tid());
+}
+
+template <typename T>
+int64_t launch_matvec_dot(const Geo& g, const Coef<T>& cf, const T* d, T* q, double* partials,
+                          cudaStream_t st) {
+    dim3 gr = tile_grid(g, kZ);
+    matvec_dot_kernel<T><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, d, q, partials);
+    return nblocks_of(gr);
+}
+
+template <typename T>
+__global__ void update_xr_kernel(int64_t n, const Scal* s, const T* __restrict__ d,
+                                 const T* __restrict__ q, T* __restrict__ x, T* __restrict__ r,
+                                 double* partials) {
+    const T alpha = (T)s->alpha;
+    T l2 = T(0), li = T(0);
+    double nf = 0.0;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        x[c] = fma(alpha, d[c], x[c]);
+        const T rc = fma(-alpha, q[c], r[c]);
+        r[c] = rc;
+        l2 = fma(rc, rc, l2);
+        li = fmax(li, fabs(rc));
+        nf += isfinite(rc) ? 0.0 : 1.0;
+    }
+    double acc[3] = {(double)l2, (double)li, nf};
+    const int op[3] = {0, 1, 0};
+    block_reduce_store<3>(acc, op, partials, blockIdx.x, threadIdx.x);
+}
+
+template <typename T>
+int64_t launch_update_xr(int64_t n, const Scal* s, const T* d, const T* q, T* x, T* r,
+                         double* partials, cudaStream_t st) {
+    int nb = elementwise_blocks(n);
+    update_xr_kernel<T><<<nb, kRedThreads, 0, st>>>(n, s, d, q, x, r, partials);
+    return nb;
+}
+
+template <typename T>
+__global__ void dot2_kernel(int64_t n, const T* __restrict__ a, const T* __restrict__ b,
+                            const T* __restrict__ c, double* partials) {
+    T s0 = T(0), s1 = T(0);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const T av = a[e];
+        s0 = fma(av, b[e], s0);
+        if (c) s1 = fma(av, c[e], s1);
+    }
+    double acc[2] = {(double)s0, (double)s1};
+    const int op[2] = {0, 0};
+    block_reduce_store<2>(acc, op, partials, blockIdx.x, threadIdx.x);
+}
+
+template <typename T>
+int64_t launch_dot2(int64_t n, const T* a, const T* b, const T* c, double* partials,
+                    cudaStream_t st) {
+    int nb = elementwise_blocks(n);
+    dot2_kernel<T><<<nb, kRedThreads, 0, st>>>(n, a, b, c, partials);
+    return nb;
+}
+
+template <typename T>
+__global__ void xpby_kernel(int64_t n, const Scal* s, const T* __restrict__ z, T* __restrict__ d) {
+    const T beta = (T)s->beta;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        d[e] = fma(beta, d[e], z[e]);
+}
+
+template <typename T>
+void launch_xpby(int64_t n, const Scal* s, const T* z, T* d, cudaStream_t st) {
+    xpby_kernel<T><<<elementwise_blocks(n), kRedThreads, 0, st>>>(n, s, z, d);
+}
+
+__global__ void accumulate_kernel(int64_t n, const Scal* s, const float* __restrict__ e,
+                                  double* __restrict__ x) {
+    const double is = s->inv_scale;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x)
+        x[c] = fma((double)e[c], is, x[c]);
+}
+
+void launch_accumulate(int64_t n, const Scal* s, const float* e, double* x, cudaStream_t st) {
+    accumulate_kernel<<<elementwise_blocks(n), kRedThreads, 0, st>>>(n, s, e, x);
+}
+
+// ------------------------------------------------------ explicit instances ---
+
+#define PARIS_INSTANTIATE(T)                                                                  \
+    template void launch_convert_beta<T>(const Geo&, const double* [3], double, T* [3],        \
+                                         cudaStream_t);                                        \
+    template void launch_coarse_beta<T>(const Geo&, const Coef<T>&, const Geo&, const int[3],  \
+                                        const double[3], T* [3], cudaStream_t);                \
+    template void launch_inv_diag<T>(const Geo&, const Coef<T>&, T*, cudaStream_t);            \
+    template void launch_coarse_inverse<T>(const Geo&, const Coef<T>&, double*, cudaStream_t); \
+    template void launch_coarse_solve<T>(const Geo&, const double*, const T*, T*, cudaStream_t); \
+    template void launch_rbgs<T>(const Geo&, const Coef<T>&, const T*, const T*, T*, int,     \
+                                 double, bool, cudaStream_t);                                  \
+    template void launch_jacobi<T>(const Geo&, const Coef<T>&, const T*, const T*, const T*,  \
+                                   T*, double, bool, cudaStream_t);                            \
+    template void launch_restrict_residual<T>(const Geo&, const Coef<T>&, const T*, const T*,  \
+                                              const Geo&, const int[3], T*, cudaStream_t);     \
+    template void launch_prolong_add<T>(const Geo&, const Geo&, const int[3], const T*, T*,   \
+                                        cudaStream_t);                                         \
+    template int64_t launch_matvec_dot<T>(const Geo&, const Coef<T>&, const T*, T*, double*,   \
+                                          cudaStream_t);                                       \
+    template int64_t launch_update_xr<T>(int64_t, const Scal*, const T*, const T*, T*, T*,     \
+                                         double*, cudaStream_t);                               \
+    template int64_t launch_dot2<T>(int64_t, const T*, const T*, const T*, double*,            \
+                                    cudaStream_t);                                             \
+    template void launch_xpby<T>(int64_t, const Scal*, const T*, T*, cudaStream_t);
+
+PARIS_INSTANTIATE(float)
+PARIS_INSTANTIATE(double)
+
+}  // namespace paris

@@ -1,0 +1,119 @@
+// Host-side launchers of the projection kernels (internal to the library).
+#pragma once
+
+#include "common.cuh"
+
+namespace paris {
+
+// Device-resident scalars of one solve; written by finalize_kernel, read by
+// the kernels that need them (no host round trip inside an iteration).
+struct Scal {
+    double red[4];       // last finalized reduction results
+    double mean_b;       // mean removed from the right-hand side
+    double bnorm2;       // ||f||_2^2 of the mean-free right-hand side
+    double binf;         // ||f||_inf
+    double rho;          // (F)CG: r . z
+    double alpha;        // (F)CG step length
+    double beta;         // (F)CG direction update coefficient
+    double rr;           // current residual ||r||_2^2
+    double rinf;         // current residual ||r||_inf
+    double scale;        // MIXED: r32 = scale * r64; correction e64 = e32 / scale
+    double inv_scale;
+    double rr0;          // MIXED: ||r32||_2^2 at the start of the inner solve
+    double nonfinite;    // > 0 if a NaN/Inf was seen
+};
+
+enum FinalizeMode {
+    FIN_STORE = 0,      // red[q] = result q
+    FIN_MEAN_B = 1,     // mean_b = result0 / param
+    FIN_BNORMS = 2,     // bnorm2 = result0, binf = result1
+    FIN_RNORMS = 3,     // rr = result0, rinf = result1
+    FIN_ALPHA = 4,      // alpha = rho / result0
+    FIN_RHO_BETA = 5,   // beta = result0 / rho, rho = result0 (PCG)
+    FIN_RHO_INIT = 6,   // rho = result0 (first direction)
+    FIN_FCG_BETA = 7,   // beta = -alpha * result1 / rho, rho = result0 (flexible CG)
+    FIN_SCALE = 8,      // scale = 1/max(result1, tiny), rr0 = rr*scale^2 ... (mixed)
+    FIN_INNER_INIT = 9  // rr0 = result0, rr = result0
+};
+
+// Generic grid for element-wise kernels.
+int elementwise_blocks(int64_t n);
+
+void finalize(const double* partials, int64_t nblocks, int nv, int maxmask, Scal* s, int mode,
+              double param, cudaStream_t st);
+
+// ---------------------------------------------------------- field steps ---
+void launch_face_coeffs(const Geo& g, const double* C, double rho1, double rho2, double* bx,
+                        double* by, double* bz, cudaStream_t st);
+// rhs = div(u)/(h dt); partials: (sum rhs, max |rhs|, nonfinite count)
+int64_t launch_divergence(const Geo& g, const double* u, const double* v, const double* w,
+                          double inv_hdt, double* rhs, double* partials, cudaStream_t st);
+// f = -(rhs - mean_b), partials: (||f||^2, max|f|, nonfinite)
+int64_t launch_make_rhs(int64_t n, const double* rhs, const Scal* s, double* f, double* partials,
+                        cudaStream_t st);
+void launch_sub_mean(int64_t n, double* x, const Scal* s, cudaStream_t st);
+int64_t launch_sum(int64_t n, const double* x, double* partials, cudaStream_t st);
+void launch_project(const Geo& g, const double* bx, const double* by, const double* bz,
+                    const double* p, double dt_over_h, double* u, double* v, double* w,
+                    cudaStream_t st);
+int64_t launch_max_divergence(const Geo& g, const double* u, const double* v, const double* w,
+                              double inv_h, double* partials, cudaStream_t st);
+
+// ---------------------------------------------------- level set-up --------
+template <typename T>
+void launch_convert_beta(const Geo& g, const double* b64[3], double scale, T* out[3],
+                         cudaStream_t st);
+template <typename T>
+void launch_coarse_beta(const Geo& fine, const Coef<T>& cf, const Geo& coarse, const int f[3],
+                        const double hc2_over_hf2[3], T* out[3], cudaStream_t st);
+template <typename T>
+void launch_inv_diag(const Geo& g, const Coef<T>& cf, T* w, cudaStream_t st);
+// dense (A + a 1 1^T)^{-1} of the coarsest operator, FP64, one CTA
+template <typename T>
+void launch_coarse_inverse(const Geo& g, const Coef<T>& cf, double* inv, cudaStream_t st);
+template <typename T>
+void launch_coarse_solve(const Geo& g, const double* inv, const T* f, T* x, cudaStream_t st);
+
+// ------------------------------------------------------------ V-cycle -----
+// One red-black colour pass of over-relaxed Gauss-Seidel on A x = f.
+// zero_init: x is taken as 0 on entry (the pass also zeroes the other colour).
+template <typename T>
+void launch_rbgs(const Geo& g, const Coef<T>& cf, const T* w, const T* f, T* x, int color,
+                 double omega, bool zero_init, cudaStream_t st);
+// One damped-Jacobi sweep x_out = x + omega D^{-1} (f - A x).
+template <typename T>
+void launch_jacobi(const Geo& g, const Coef<T>& cf, const T* w, const T* f, const T* x, T* xout,
+                   double omega, bool zero_init, cudaStream_t st);
+// coarse f = average over the children of (f - A x) on the fine level
+template <typename T>
+void launch_restrict_residual(const Geo& fine, const Coef<T>& cf, const T* f, const T* x,
+                             const Geo& coarse, const int fac[3], T* fc, cudaStream_t st);
+// x_fine += x_coarse[parent]
+template <typename T>
+void launch_prolong_add(const Geo& fine, const Geo& coarse, const int fac[3], const T* xc,
+                        T* x, cudaStream_t st);
+
+// ------------------------------------------------------------ Krylov ------
+// r = f - A x (FP64), optional r32 = scale * r; partials (||r||^2, max|r|, nonfinite)
+int64_t launch_residual64(const Geo& g, const Coef<double>& cf, const double* f, const double* x,
+                          double* r64, float* r32, const Scal* s, double* partials,
+                          cudaStream_t st);
+// q = A d; partials (d . q)
+template <typename T>
+int64_t launch_matvec_dot(const Geo& g, const Coef<T>& cf, const T* d, T* q, double* partials,
+                          cudaStream_t st);
+// x += alpha d; r -= alpha q; partials (||r||^2, max|r|, nonfinite)
+template <typename T>
+int64_t launch_update_xr(int64_t n, const Scal* s, const T* d, const T* q, T* x, T* r,
+                         double* partials, cudaStream_t st);
+// partials (a . b, a . c)  (c may be null -> 0)
+template <typename T>
+int64_t launch_dot2(int64_t n, const T* a, const T* b, const T* c, double* partials,
+                    cudaStream_t st);
+// d = z + beta d
+template <typename T>
+void launch_xpby(int64_t n, const Scal* s, const T* z, T* d, cudaStream_t st);
+// x64 += e32 * inv_scale
+void launch_accumulate(int64_t n, const Scal* s, const float* e, double* x, cudaStream_t st);
+
+}  // namespace paris

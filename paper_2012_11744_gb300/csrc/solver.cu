@@ -1,0 +1,713 @@
+// Host runtime of the projection library: context, multigrid level plan,
+// workspace, the FP64 and mixed-precision Krylov drivers and the C ABI.
+//
+// Solver (Sec. 3.7 of the PARIS paper describes red-black SOR, Hypre's
+// multigrid, an in-code V-cycle and a GPU Jacobi iteration; this library
+// combines them as a preconditioner):
+//   FP64  : conjugate gradients on A p = f (A = -L, f = -b, both mean-free)
+//           preconditioned by one symmetric FP64 V-cycle (red-black SOR
+//           smoother, 8-child averaging restriction, piecewise-constant
+//           prolongation, rediscretised coarse coefficients, dense FP64 solve
+//           on the coarsest grid).
+//   MIXED : FP64 iterative refinement.  Each step computes the true residual
+//           in FP64, solves A e = r approximately with flexible CG in FP32
+//           preconditioned by the same V-cycle in FP32, and accumulates
+//           p += e in FP64.  Dot products are summed across threads in FP64.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/paris.h"
+#include "kernels.cuh"
+
+using namespace paris;
+
+namespace {
+
+struct Level {
+    Geo g;
+    int fac[3] = {1, 1, 1};      // coarsening factor from the previous level
+    double hrel[3] = {1, 1, 1};  // h_a of this level / h of level 0
+    float* b32[3] = {nullptr, nullptr, nullptr};
+    double* b64[3] = {nullptr, nullptr, nullptr};
+    float* w32 = nullptr;
+    double* w64 = nullptr;
+    float* x32 = nullptr;
+    float* f32 = nullptr;
+    float* t32 = nullptr;  // Jacobi second buffer
+    double* x64 = nullptr;
+    double* f64 = nullptr;
+    double* t64 = nullptr;
+};
+
+struct Alloc {
+    std::vector<void*> ptrs;
+    cudaError_t err = cudaSuccess;
+    template <typename T>
+    T* get(int64_t n) {
+        if (err != cudaSuccess) return nullptr;
+        void* p = nullptr;
+        size_t bytes = (size_t)std::max<int64_t>(n, 1) * sizeof(T);
+        err = cudaMalloc(&p, bytes);
+        if (err != cudaSuccess) return nullptr;
+        ptrs.push_back(p);
+        return (T*)p;
+    }
+    void release() {
+        for (void* p : ptrs) cudaFree(p);
+        ptrs.clear();
+    }
+};
+
+constexpr int kMaxDense = 128;
+
+}  // namespace
+
+struct paris_ctx {
+    paris_grid grid;
+    paris_opts opts;
+    Geo g0;
+    int64_t N = 0;
+    cudaStream_t st = nullptr;
+    std::vector<Level> lv;
+    bool dense_coarse = false;
+    Alloc mem;
+    double* coarse_inv = nullptr;
+    // FP64 Krylov vectors
+    double *f = nullptr, *r = nullptr, *z = nullptr, *d = nullptr, *q = nullptr;
+    // FP32 inner vectors
+    float *r32 = nullptr, *z32 = nullptr, *d32 = nullptr, *q32 = nullptr, *e32 = nullptr;
+    // level-0 FP32 coefficient copies
+    float* b32_0[3] = {nullptr, nullptr, nullptr};
+    double* partials = nullptr;
+    Scal* scal = nullptr;
+    Scal* scal_h = nullptr;  // pinned host mirror
+    // projection-step scratch
+    double* beta[3] = {nullptr, nullptr, nullptr};
+    double* rhs = nullptr;
+    // host-call staging (allocated on first use)
+    double *hC = nullptr, *hu = nullptr, *hv = nullptr, *hw = nullptr, *hp = nullptr;
+    double last_mean_b = 0.0;
+};
+
+namespace {
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return PARIS_ERR_CUDA;              \
+    } while (0)
+
+bool valid_grid(const paris_grid* g) {
+    if (!g) return false;
+    if (g->nx < 2 || g->ny < 2 || g->nz < 2) return false;
+    if (!(g->h > 0.0) || !std::isfinite(g->h)) return false;
+    for (int a = 0; a < 3; ++a)
+        if (g->bc[a] != PARIS_PERIODIC && g->bc[a] != PARIS_WALL) return false;
+    return true;
+}
+
+bool valid_opts(const paris_opts* o) {
+    if (!o) return false;
+    if (!(o->tol > 0.0) || o->max_iter < 1) return false;
+    if (o->precision != PARIS_FP64 && o->precision != PARIS_MIXED) return false;
+    if (o->nu1 < 0 || o->nu2 < 0 || o->nu1 + o->nu2 < 1 || o->nu1 > 16 || o->nu2 > 16) return false;
+    if (!(o->omega > 0.0 && o->omega < 2.0)) return false;
+    if (o->smoother != PARIS_SMOOTH_RBGS && o->smoother != PARIS_SMOOTH_JACOBI) return false;
+    if (o->coarse_max_cells < 1 || o->coarse_max_cells > kMaxDense) return false;
+    if (!(o->inner_tol > 0.0 && o->inner_tol < 1.0)) return false;
+    return true;
+}
+
+// Level plan: halve every axis while all are even and >= 4; once that stops,
+// halve the axes that still can (semi-coarsening) while the level has more
+// than coarse_max_cells cells.  The paper's in-code multigrid (Sec. 3.7.3)
+// needs 2^n points per direction; this plan also covers sizes such as 48 or 96.
+std::vector<Level> plan_levels(const paris_grid& gr, int coarse_max) {
+    std::vector<Level> out;
+    Level l0;
+    l0.g = Geo{gr.nx, gr.ny, gr.nz, gr.bc[0] == PARIS_WALL, gr.bc[1] == PARIS_WALL,
+               gr.bc[2] == PARIS_WALL};
+    out.push_back(l0);
+    for (;;) {
+        const Level& c = out.back();
+        if (c.g.ncell() <= coarse_max) break;
+        int n[3] = {c.g.nx, c.g.ny, c.g.nz};
+        bool can[3];
+        bool all = true, any = false;
+        for (int a = 0; a < 3; ++a) {
+            can[a] = (n[a] % 2 == 0) && n[a] >= 4;
+            all = all && can[a];
+            any = any || can[a];
+        }
+        if (!any) break;
+        Level nl;
+        nl.g = c.g;
+        for (int a = 0; a < 3; ++a) {
+            int f = (all || can[a]) ? 2 : 1;
+            nl.fac[a] = f;
+            nl.hrel[a] = c.hrel[a] * f;
+            n[a] /= f;
+        }
+        nl.g.nx = n[0];
+        nl.g.ny = n[1];
+        nl.g.nz = n[2];
+        out.push_back(nl);
+    }
+    return out;
+}
+
+paris_status alloc_ctx(paris_ctx* c) {
+    Alloc& m = c->mem;
+    const int64_t N = c->N;
+    c->lv = plan_levels(c->grid, c->opts.coarse_max_cells);
+    const Level& last = c->lv.back();
+    c->dense_coarse = last.g.ncell() <= kMaxDense;
+    for (size_t l = 0; l < c->lv.size(); ++l) {
+        Level& L = c->lv[l];
+        const int64_t n = L.g.ncell();
+        if (l > 0) {
+            for (int a = 0; a < 3; ++a) {
+                L.b32[a] = m.get<float>(L.g.nface(a));
+                L.b64[a] = m.get<double>(L.g.nface(a));
+            }
+            L.x32 = m.get<float>(n);
+            L.f32 = m.get<float>(n);
+            L.x64 = m.get<double>(n);
+            L.f64 = m.get<double>(n);
+        }
+        L.w32 = m.get<float>(n);
+        L.w64 = m.get<double>(n);
+        L.t32 = m.get<float>(n);
+        L.t64 = m.get<double>(n);
+    }
+    if (c->dense_coarse) c->coarse_inv = m.get<double>(last.g.ncell() * last.g.ncell());
+    c->f = m.get<double>(N);
+    c->r = m.get<double>(N);
+    c->z = m.get<double>(N);
+    c->d = m.get<double>(N);
+    c->q = m.get<double>(N);
+    c->r32 = m.get<float>(N);
+    c->z32 = m.get<float>(N);
+    c->d32 = m.get<float>(N);
+    c->q32 = m.get<float>(N);
+    c->e32 = m.get<float>(N);
+    for (int a = 0; a < 3; ++a) {
+        c->b32_0[a] = m.get<float>(c->g0.nface(a));
+        c->beta[a] = m.get<double>(c->g0.nface(a));
+    }
+    c->rhs = m.get<double>(N);
+    // block partials: the largest reduction grid is the z-tiled stencil grid
+    int64_t tiles = (int64_t)((c->g0.nx + 31) / 32) * ((c->g0.ny + 7) / 8) * ((c->g0.nz + 7) / 8);
+    int64_t np = std::max<int64_t>(tiles, 152 * 8) * 4;
+    c->partials = m.get<double>(np);
+    c->scal = m.get<Scal>(1);
+    if (m.err != cudaSuccess) return m.err == cudaErrorMemoryAllocation ? PARIS_ERR_NO_MEMORY : PARIS_ERR_CUDA;
+    if (cudaMallocHost(&c->scal_h, sizeof(Scal)) != cudaSuccess) return PARIS_ERR_NO_MEMORY;
+    CK(cudaMemsetAsync(c->scal, 0, sizeof(Scal), c->st));
+    return PARIS_OK;
+}
+
+paris_status read_scal(paris_ctx* c) {
+    CK(cudaMemcpyAsync(c->scal_h, c->scal, sizeof(Scal), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return PARIS_OK;
+}
+
+// ------------------------------------------------------------- V-cycle ---
+
+template <typename T>
+struct Prec;
+template <>
+struct Prec<float> {
+    static float* b(Level& L, int a) { return L.b32[a]; }
+    static float* w(Level& L) { return L.w32; }
+    static float* x(Level& L) { return L.x32; }
+    static float* f(Level& L) { return L.f32; }
+    static float* t(Level& L) { return L.t32; }
+};
+template <>
+struct Prec<double> {
+    static double* b(Level& L, int a) { return L.b64[a]; }
+    static double* w(Level& L) { return L.w64; }
+    static double* x(Level& L) { return L.x64; }
+    static double* f(Level& L) { return L.f64; }
+    static double* t(Level& L) { return L.t64; }
+};
+
+template <typename T>
+Coef<T> level_coef(paris_ctx* c, int l, const Coef<T>& c0) {
+    if (l == 0) return c0;
+    Level& L = c->lv[l];
+    return Coef<T>{Prec<T>::b(L, 0), Prec<T>::b(L, 1), Prec<T>::b(L, 2), T(1)};
+}
+
+// Per-solve set-up of the hierarchy in precision T: coarse coefficients,
+// inverse diagonals, dense coarsest inverse.
+template <typename T>
+void setup_hierarchy(paris_ctx* c, const Coef<T>& c0) {
+    const int nl = (int)c->lv.size();
+    for (int l = 1; l < nl; ++l) {
+        Level& L = c->lv[l];
+        Level& F = c->lv[l - 1];
+        Coef<T> cf = level_coef<T>(c, l - 1, c0);
+        double ratio2[3];
+        for (int a = 0; a < 3; ++a) ratio2[a] = (double)L.fac[a] * L.fac[a];
+        T* out[3] = {Prec<T>::b(L, 0), Prec<T>::b(L, 1), Prec<T>::b(L, 2)};
+        launch_coarse_beta<T>(F.g, cf, L.g, L.fac, ratio2, out, c->st);
+    }
+    for (int l = 0; l < nl; ++l) launch_inv_diag<T>(c->lv[l].g, level_coef<T>(c, l, c0), Prec<T>::w(c->lv[l]), c->st);
+    if (c->dense_coarse)
+        launch_coarse_inverse<T>(c->lv[nl - 1].g, level_coef<T>(c, nl - 1, c0), c->coarse_inv, c->st);
+}
+
+template <typename T>
+void smooth(paris_ctx* c, int l, const Coef<T>& cf, const T* f, T* x, int sweeps, bool first_zero,
+            bool reverse) {
+    Level& L = c->lv[l];
+    const paris_opts& o = c->opts;
+    for (int s = 0; s < sweeps; ++s) {
+        const bool z0 = first_zero && s == 0;
+        if (o.smoother == PARIS_SMOOTH_JACOBI) {
+            // x -> t -> copy back keeps x as the output buffer
+            launch_jacobi<T>(L.g, cf, Prec<T>::w(L), f, x, Prec<T>::t(L), o.omega, z0, c->st);
+            cudaMemcpyAsync(x, Prec<T>::t(L), sizeof(T) * L.g.ncell(), cudaMemcpyDeviceToDevice, c->st);
+        } else {
+            const int c0 = reverse ? 1 : 0;
+            launch_rbgs<T>(L.g, cf, Prec<T>::w(L), f, x, c0, o.omega, z0, c->st);
+            launch_rbgs<T>(L.g, cf, Prec<T>::w(L), f, x, 1 - c0, o.omega, false, c->st);
+        }
+    }
+}
+
+// x0 = V(f0): one symmetric V-cycle for A x = f on level 0 (x0 overwritten).
+template <typename T>
+void vcycle(paris_ctx* c, const Coef<T>& c0, const T* f0, T* x0) {
+    const int nl = (int)c->lv.size();
+    const paris_opts& o = c->opts;
+    for (int l = 0; l < nl - 1; ++l) {
+        const T* f = l == 0 ? f0 : Prec<T>::f(c->lv[l]);
+        T* x = l == 0 ? x0 : Prec<T>::x(c->lv[l]);
+        Coef<T> cf = level_coef<T>(c, l, c0);
+        if (o.nu1 > 0) smooth<T>(c, l, cf, f, x, o.nu1, true, false);
+        else cudaMemsetAsync(x, 0, sizeof(T) * c->lv[l].g.ncell(), c->st);
+        Level& C = c->lv[l + 1];
+        launch_restrict_residual<T>(c->lv[l].g, cf, f, x, C.g, C.fac, Prec<T>::f(C), c->st);
+    }
+    {
+        Level& C = c->lv[nl - 1];
+        const T* f = nl == 1 ? f0 : Prec<T>::f(C);
+        T* x = nl == 1 ? x0 : Prec<T>::x(C);
+        if (c->dense_coarse) {
+            launch_coarse_solve<T>(C.g, c->coarse_inv, f, x, c->st);
+        } else {
+            Coef<T> cf = level_coef<T>(c, nl - 1, c0);
+            smooth<T>(c, nl - 1, cf, f, x, 8, true, false);
+            smooth<T>(c, nl - 1, cf, f, x, 8, false, true);
+        }
+    }
+    for (int l = nl - 2; l >= 0; --l) {
+        const T* f = l == 0 ? f0 : Prec<T>::f(c->lv[l]);
+        T* x = l == 0 ? x0 : Prec<T>::x(c->lv[l]);
+        Coef<T> cf = level_coef<T>(c, l, c0);
+        Level& C = c->lv[l + 1];
+        launch_prolong_add<T>(c->lv[l].g, C.g, C.fac, Prec<T>::x(C), x, c->st);
+        if (o.nu2 > 0) smooth<T>(c, l, cf, f, x, o.nu2, false, true);
+    }
+}
+
+// ------------------------------------------------------------- drivers ---
+
+struct SolveOut {
+    int iters = 0, outer = 0;
+    bool converged = false, nonfinite = false;
+};
+
+bool meets(const paris_ctx* c, const Scal& s) {
+    const double t = c->opts.tol;
+    return s.rr <= t * t * s.bnorm2 && s.rinf <= t * s.binf;
+}
+
+// Common prologue: mean of rhs, f = -(rhs - mean), norms of f.
+paris_status prologue(paris_ctx* c, const double* rhs) {
+    int64_t nb = launch_sum(c->N, rhs, c->partials, c->st);
+    finalize(c->partials, nb, 3, 2, c->scal, FIN_MEAN_B, (double)c->N, c->st);
+    nb = launch_make_rhs(c->N, rhs, c->scal, c->f, c->partials, c->st);
+    finalize(c->partials, nb, 3, 2, c->scal, FIN_BNORMS, 0.0, c->st);
+    CK(cudaGetLastError());
+    return PARIS_OK;
+}
+
+paris_status true_residual(paris_ctx* c, const Coef<double>& c64, const double* x, float* r32) {
+    if (r32) finalize(c->partials, 0, 1, 0, c->scal, FIN_SCALE, 0.0, c->st);
+    int64_t nb = launch_residual64(c->g0, c64, c->f, x, r32 ? nullptr : c->r, r32, c->scal,
+                                   c->partials, c->st);
+    finalize(c->partials, nb, 3, 2, c->scal, FIN_RNORMS, 0.0, c->st);
+    CK(cudaGetLastError());
+    return read_scal(c);
+}
+
+// FP64 multigrid-preconditioned CG from the initial guess in x.
+paris_status solve_fp64(paris_ctx* c, const Coef<double>& c64, double* x, SolveOut& out,
+                        int max_iter) {
+    setup_hierarchy<double>(c, c64);
+    paris_status s = true_residual(c, c64, x, nullptr);  // r = f - A x
+    if (s != PARIS_OK) return s;
+    if (c->scal_h->nonfinite > 0) { out.nonfinite = true; return PARIS_OK; }
+    if (c->scal_h->bnorm2 == 0.0 || meets(c, *c->scal_h)) { out.converged = true; return PARIS_OK; }
+    const int64_t N = c->N;
+    int restarts = 0;
+    while (out.iters < max_iter) {
+        vcycle<double>(c, c64, c->r, c->z);
+        int64_t nb = launch_dot2<double>(N, c->r, c->z, nullptr, c->partials, c->st);
+        finalize(c->partials, nb, 2, 0, c->scal, FIN_RHO_INIT, 0.0, c->st);
+        CK(cudaMemcpyAsync(c->d, c->z, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->st));
+        bool conv = false;
+        while (out.iters < max_iter) {
+            nb = launch_matvec_dot<double>(c->g0, c64, c->d, c->q, c->partials, c->st);
+            finalize(c->partials, nb, 1, 0, c->scal, FIN_ALPHA, 0.0, c->st);
+            nb = launch_update_xr<double>(N, c->scal, c->d, c->q, x, c->r, c->partials, c->st);
+            finalize(c->partials, nb, 3, 2, c->scal, FIN_RNORMS, 0.0, c->st);
+            ++out.iters;
+            s = read_scal(c);
+            if (s != PARIS_OK) return s;
+            if (c->scal_h->nonfinite > 0) { out.nonfinite = true; return PARIS_OK; }
+            if (meets(c, *c->scal_h)) { conv = true; break; }
+            vcycle<double>(c, c64, c->r, c->z);
+            nb = launch_dot2<double>(N, c->r, c->z, nullptr, c->partials, c->st);
+            finalize(c->partials, nb, 2, 0, c->scal, FIN_RHO_BETA, 0.0, c->st);
+            launch_xpby<double>(N, c->scal, c->z, c->d, c->st);
+        }
+        // verify with the true residual; restart from it if the recurrence drifted
+        s = true_residual(c, c64, x, nullptr);
+        if (s != PARIS_OK) return s;
+        if (meets(c, *c->scal_h)) { out.converged = true; return PARIS_OK; }
+        if (!conv || ++restarts > 3) return PARIS_OK;
+    }
+    return PARIS_OK;
+}
+
+// Mixed precision: FP64 iterative refinement around FP32 flexible CG.
+paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, SolveOut& out,
+                         int max_iter) {
+    const int64_t N = c->N;
+    const double ih2 = 1.0 / (c->grid.h * c->grid.h);
+    {
+        const double* b64[3] = {c64.bx, c64.by, c64.bz};
+        launch_convert_beta<float>(c->g0, b64, ih2, c->b32_0, c->st);
+    }
+    Coef<float> c32{c->b32_0[0], c->b32_0[1], c->b32_0[2], 1.0f};
+    setup_hierarchy<float>(c, c32);
+    double prev_rr = INFINITY;
+    int stalls = 0;
+    for (;;) {
+        paris_status s = true_residual(c, c64, x, c->r32);  // r32 = scale * (f - A x)
+        if (s != PARIS_OK) return s;
+        const Scal& h = *c->scal_h;
+        if (h.nonfinite > 0) { out.nonfinite = true; return PARIS_OK; }
+        if (h.bnorm2 == 0.0 || meets(c, h)) { out.converged = true; return PARIS_OK; }
+        if (out.iters >= max_iter) return PARIS_OK;
+        if (h.rr > 0.25 * prev_rr) { if (++stalls >= 2) return PARIS_OK; } else stalls = 0;
+        prev_rr = h.rr;
+        ++out.outer;
+        // inner solve of A e = r32 to a relative reduction inner_tol (not below
+        // what the outer tolerance still needs, with a safety factor 0.1)
+        const double rr32 = h.rr * h.scale * h.scale;
+        double need2 = (c->opts.tol * c->opts.tol * h.bnorm2) / std::max(h.rr, 1e-300) * 1e-2;
+        double it2 = c->opts.inner_tol * c->opts.inner_tol;
+        const double target = rr32 * std::max(it2, std::min(need2, 1.0));
+        CK(cudaMemsetAsync(c->e32, 0, sizeof(float) * N, c->st));
+        vcycle<float>(c, c32, c->r32, c->z32);
+        int64_t nb = launch_dot2<float>(N, c->r32, c->z32, nullptr, c->partials, c->st);
+        finalize(c->partials, nb, 2, 0, c->scal, FIN_RHO_INIT, 0.0, c->st);
+        CK(cudaMemcpyAsync(c->d32, c->z32, sizeof(float) * N, cudaMemcpyDeviceToDevice, c->st));
+        for (int j = 0; j < 50 && out.iters < max_iter; ++j) {
+            nb = launch_matvec_dot<float>(c->g0, c32, c->d32, c->q32, c->partials, c->st);
+            finalize(c->partials, nb, 1, 0, c->scal, FIN_ALPHA, 0.0, c->st);
+            nb = launch_update_xr<float>(N, c->scal, c->d32, c->q32, c->e32, c->r32, c->partials, c->st);
+            finalize(c->partials, nb, 3, 2, c->scal, FIN_STORE, 0.0, c->st);
+            ++out.iters;
+            s = read_scal(c);
+            if (s != PARIS_OK) return s;
+            const double in_rr = c->scal_h->red[0];
+            if (!(in_rr == in_rr) || c->scal_h->red[2] > 0) break;  // non-finite: let the outer step judge
+            if (in_rr <= target || in_rr > 1e6 * rr32) break;
+            vcycle<float>(c, c32, c->r32, c->z32);
+            nb = launch_dot2<float>(N, c->z32, c->r32, c->q32, c->partials, c->st);  // (z.r, z.q)
+            finalize(c->partials, nb, 2, 0, c->scal, FIN_FCG_BETA, 0.0, c->st);
+            launch_xpby<float>(N, c->scal, c->z32, c->d32, c->st);
+        }
+        launch_accumulate(N, c->scal, c->e32, x, c->st);
+        CK(cudaGetLastError());
+    }
+}
+
+paris_status remove_mean(paris_ctx* c, double* x, int64_t n) {
+    int64_t nb = launch_sum(n, x, c->partials, c->st);
+    finalize(c->partials, nb, 3, 2, c->scal, FIN_STORE, 0.0, c->st);
+    launch_sub_mean(n, x, c->scal, c->st);
+    CK(cudaGetLastError());
+    return PARIS_OK;
+}
+
+}  // namespace
+
+// ================================================================== C ABI ===
+
+extern "C" {
+
+void paris_default_opts(paris_opts* o) {
+    if (!o) return;
+    o->tol = 1e-10;
+    o->max_iter = 200;
+    o->precision = PARIS_MIXED;
+    o->nu1 = 2;
+    o->nu2 = 2;
+    o->omega = 1.15;
+    o->smoother = PARIS_SMOOTH_RBGS;
+    o->coarse_max_cells = 64;
+    o->inner_tol = 1e-5;
+    o->fallback = 1;
+}
+
+const char* paris_status_string(paris_status s) {
+    switch (s) {
+        case PARIS_OK: return "ok";
+        case PARIS_ERR_INVALID_ARG: return "invalid argument";
+        case PARIS_ERR_CUDA: return "CUDA error";
+        case PARIS_ERR_NOT_CONVERGED: return "not converged";
+        case PARIS_ERR_NONFINITE: return "non-finite value";
+        case PARIS_ERR_TIMEOUT: return "device wait timed out";
+        case PARIS_ERR_NO_MEMORY: return "out of device memory";
+    }
+    return "unknown status";
+}
+
+paris_status paris_create(paris_ctx** out, const paris_grid* g, const paris_opts* o, void* stream) {
+    if (!out) return PARIS_ERR_INVALID_ARG;
+    *out = nullptr;
+    paris_opts def;
+    paris_default_opts(&def);
+    if (!o) o = &def;
+    if (!valid_grid(g) || !valid_opts(o)) return PARIS_ERR_INVALID_ARG;
+    paris_ctx* c = new (std::nothrow) paris_ctx();
+    if (!c) return PARIS_ERR_NO_MEMORY;
+    c->grid = *g;
+    c->opts = *o;
+    c->g0 = Geo{g->nx, g->ny, g->nz, g->bc[0] == PARIS_WALL, g->bc[1] == PARIS_WALL,
+                g->bc[2] == PARIS_WALL};
+    c->N = c->g0.ncell();
+    c->st = (cudaStream_t)stream;
+    paris_status s = alloc_ctx(c);
+    if (s != PARIS_OK) {
+        paris_destroy(c);
+        return s;
+    }
+    *out = c;
+    return PARIS_OK;
+}
+
+paris_status paris_destroy(paris_ctx* c) {
+    if (!c) return PARIS_ERR_INVALID_ARG;
+    cudaStreamSynchronize(c->st);
+    c->mem.release();
+    if (c->scal_h) cudaFreeHost(c->scal_h);
+    delete c;
+    return PARIS_OK;
+}
+
+paris_status paris_set_opts(paris_ctx* c, const paris_opts* o) {
+    if (!c || !valid_opts(o)) return PARIS_ERR_INVALID_ARG;
+    if (o->coarse_max_cells != c->opts.coarse_max_cells) {
+        // the level plan depends on coarse_max_cells: rebuild the workspace
+        CK(cudaStreamSynchronize(c->st));
+        c->mem.release();
+        if (c->scal_h) cudaFreeHost(c->scal_h);
+        c->scal_h = nullptr;
+        c->hC = c->hu = c->hv = c->hw = c->hp = nullptr;
+        c->opts = *o;
+        return alloc_ctx(c);
+    }
+    c->opts = *o;
+    return PARIS_OK;
+}
+
+int64_t paris_face_count(const paris_ctx* c, int axis) {
+    if (!c || axis < 0 || axis > 2) return -1;
+    return c->g0.nface(axis);
+}
+
+int64_t paris_cell_count(const paris_ctx* c) { return c ? c->N : -1; }
+
+paris_status paris_face_coeffs(paris_ctx* c, const double* C, double rho1, double rho2,
+                               double* bx, double* by, double* bz) {
+    if (!c || !C || !bx || !by || !bz) return PARIS_ERR_INVALID_ARG;
+    if (!(rho1 > 0.0) || !(rho2 > 0.0) || !std::isfinite(rho1) || !std::isfinite(rho2))
+        return PARIS_ERR_INVALID_ARG;
+    launch_face_coeffs(c->g0, C, rho1, rho2, bx, by, bz, c->st);
+    CK(cudaGetLastError());
+    return PARIS_OK;
+}
+
+paris_status paris_divergence(paris_ctx* c, const double* u, const double* v, const double* w,
+                              double dt, double* rhs, double* mean_removed) {
+    if (!c || !u || !v || !w || !rhs) return PARIS_ERR_INVALID_ARG;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return PARIS_ERR_INVALID_ARG;
+    int64_t nb = launch_divergence(c->g0, u, v, w, 1.0 / (c->grid.h * dt), rhs, c->partials, c->st);
+    finalize(c->partials, nb, 3, 2, c->scal, FIN_MEAN_B, (double)c->N, c->st);
+    launch_sub_mean(c->N, rhs, c->scal, c->st);
+    CK(cudaGetLastError());
+    if (mean_removed) {
+        paris_status s = read_scal(c);
+        if (s != PARIS_OK) return s;
+        *mean_removed = c->scal_h->mean_b;
+        c->last_mean_b = c->scal_h->mean_b;
+    }
+    return PARIS_OK;
+}
+
+paris_status paris_poisson_solve(paris_ctx* c, const double* bx, const double* by,
+                                 const double* bz, const double* rhs, double* p,
+                                 paris_stats* st) {
+    if (!c || !bx || !by || !bz || !rhs || !p) return PARIS_ERR_INVALID_ARG;
+    const double ih2 = 1.0 / (c->grid.h * c->grid.h);
+    Coef<double> c64{bx, by, bz, ih2};
+    CK(cudaMemsetAsync(c->scal, 0, sizeof(Scal), c->st));
+    paris_status s = prologue(c, rhs);
+    if (s != PARIS_OK) return s;
+    SolveOut out;
+    int fell_back = 0;
+    if (c->opts.precision == PARIS_MIXED) {
+        s = solve_mixed(c, c64, p, out, c->opts.max_iter);
+        if (s != PARIS_OK) return s;
+        if (!out.converged && !out.nonfinite && c->opts.fallback) {
+            SolveOut o2;
+            s = solve_fp64(c, c64, p, o2, c->opts.max_iter);
+            if (s != PARIS_OK) return s;
+            o2.iters += out.iters;
+            o2.outer += out.outer;
+            out = o2;
+            fell_back = 1;
+        }
+    } else {
+        s = solve_fp64(c, c64, p, out, c->opts.max_iter);
+        if (s != PARIS_OK) return s;
+        out.outer = out.iters;
+    }
+    s = remove_mean(c, p, c->N);
+    if (s != PARIS_OK) return s;
+    s = read_scal(c);
+    if (s != PARIS_OK) return s;
+    const Scal& h = *c->scal_h;
+    if (st) {
+        st->iters = out.iters;
+        st->outer_iters = out.outer;
+        st->rel_res_l2 = h.bnorm2 > 0 ? std::sqrt(h.rr / h.bnorm2) : 0.0;
+        st->rel_res_linf = h.binf > 0 ? h.rinf / h.binf : 0.0;
+        st->mean_b_removed = h.mean_b;
+        st->fell_back = fell_back;
+        st->converged = out.converged ? 1 : 0;
+        st->levels = (int)c->lv.size();
+    }
+    if (out.nonfinite) return PARIS_ERR_NONFINITE;
+    return out.converged ? PARIS_OK : PARIS_ERR_NOT_CONVERGED;
+}
+
+paris_status paris_project(paris_ctx* c, const double* bx, const double* by, const double* bz,
+                           const double* p, double dt, double* u, double* v, double* w) {
+    if (!c || !bx || !by || !bz || !p || !u || !v || !w) return PARIS_ERR_INVALID_ARG;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return PARIS_ERR_INVALID_ARG;
+    launch_project(c->g0, bx, by, bz, p, dt / c->grid.h, u, v, w, c->st);
+    CK(cudaGetLastError());
+    return PARIS_OK;
+}
+
+paris_status paris_projection_step(paris_ctx* c, const double* C, double rho1, double rho2,
+                                   double dt, double* u, double* v, double* w, double* p,
+                                   paris_stats* st) {
+    if (!c || !C || !u || !v || !w || !p) return PARIS_ERR_INVALID_ARG;
+    paris_status s = paris_face_coeffs(c, C, rho1, rho2, c->beta[0], c->beta[1], c->beta[2]);
+    if (s != PARIS_OK) return s;
+    s = paris_divergence(c, u, v, w, dt, c->rhs, nullptr);
+    if (s != PARIS_OK) return s;
+    double mb = 0.0;
+    {
+        // the divergence's removed mean is the one worth reporting
+        CK(cudaMemcpyAsync(&c->scal_h->mean_b, &c->scal->mean_b, sizeof(double),
+                           cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        mb = c->scal_h->mean_b;
+    }
+    paris_status solve = paris_poisson_solve(c, c->beta[0], c->beta[1], c->beta[2], c->rhs, p, st);
+    if (solve != PARIS_OK && solve != PARIS_ERR_NOT_CONVERGED) return solve;
+    if (st) st->mean_b_removed = mb;
+    s = paris_project(c, c->beta[0], c->beta[1], c->beta[2], p, dt, u, v, w);
+    if (s != PARIS_OK) return s;
+    return solve;
+}
+
+paris_status paris_projection_step_host(paris_ctx* c, const double* C_host, double rho1,
+                                        double rho2, double dt, double* u_host, double* v_host,
+                                        double* w_host, double* p_host, paris_stats* st) {
+    if (!c || !C_host || !u_host || !v_host || !w_host || !p_host) return PARIS_ERR_INVALID_ARG;
+    const int64_t N = c->N;
+    const int64_t nf[3] = {c->g0.nface(0), c->g0.nface(1), c->g0.nface(2)};
+    if (!c->hC) {
+        c->hC = c->mem.get<double>(N);
+        c->hu = c->mem.get<double>(nf[0]);
+        c->hv = c->mem.get<double>(nf[1]);
+        c->hw = c->mem.get<double>(nf[2]);
+        c->hp = c->mem.get<double>(N);
+        if (c->mem.err != cudaSuccess) return PARIS_ERR_NO_MEMORY;
+    }
+    CK(cudaMemcpyAsync(c->hC, C_host, sizeof(double) * N, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->hu, u_host, sizeof(double) * nf[0], cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->hv, v_host, sizeof(double) * nf[1], cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->hw, w_host, sizeof(double) * nf[2], cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->hp, p_host, sizeof(double) * N, cudaMemcpyHostToDevice, c->st));
+    paris_status s = paris_projection_step(c, c->hC, rho1, rho2, dt, c->hu, c->hv, c->hw, c->hp, st);
+    if (s != PARIS_OK && s != PARIS_ERR_NOT_CONVERGED) return s;
+    CK(cudaMemcpyAsync(u_host, c->hu, sizeof(double) * nf[0], cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(v_host, c->hv, sizeof(double) * nf[1], cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(w_host, c->hw, sizeof(double) * nf[2], cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(p_host, c->hp, sizeof(double) * N, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return s;
+}
+
+paris_status paris_residual_norms(paris_ctx* c, const double* bx, const double* by,
+                                  const double* bz, const double* rhs, const double* p,
+                                  double* rel_l2, double* rel_linf) {
+    if (!c || !bx || !by || !bz || !rhs || !p || !rel_l2 || !rel_linf) return PARIS_ERR_INVALID_ARG;
+    const double ih2 = 1.0 / (c->grid.h * c->grid.h);
+    Coef<double> c64{bx, by, bz, ih2};
+    // f = -rhs as given (no mean removal): norms of rhs and of rhs - L p
+    CK(cudaMemsetAsync(c->scal, 0, sizeof(Scal), c->st));
+    int64_t nb = launch_make_rhs(c->N, rhs, c->scal, c->f, c->partials, c->st);
+    finalize(c->partials, nb, 3, 2, c->scal, FIN_BNORMS, 0.0, c->st);
+    paris_status s = true_residual(c, c64, p, nullptr);
+    if (s != PARIS_OK) return s;
+    const Scal& h = *c->scal_h;
+    *rel_l2 = h.bnorm2 > 0 ? std::sqrt(h.rr / h.bnorm2) : std::sqrt(h.rr);
+    *rel_linf = h.binf > 0 ? h.rinf / h.binf : h.rinf;
+    return PARIS_OK;
+}
+
+paris_status paris_max_divergence(paris_ctx* c, const double* u, const double* v,
+                                  const double* w, double* max_abs_div) {
+    if (!c || !u || !v || !w || !max_abs_div) return PARIS_ERR_INVALID_ARG;
+    int64_t nb = launch_max_divergence(c->g0, u, v, w, 1.0 / c->grid.h, c->partials, c->st);
+    finalize(c->partials, nb, 1, 1, c->scal, FIN_STORE, 0.0, c->st);
+    CK(cudaGetLastError());
+    paris_status s = read_scal(c);
+    if (s != PARIS_OK) return s;
+    *max_abs_div = c->scal_h->red[0];
+    return PARIS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,140 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bars (from the method's statement): FP64 relative residual <= 1e-10 in the L2
+and L-infinity norms, ||p - p_oracle||_inf / ||p_oracle||_inf <= 1e-8 after
+mean removal, max|div u| <= 1e-9 max|u*|/h.  Face coefficients, divergence
+and the velocity correction are element-wise checks at a few ulp.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paris_inputs as pi
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+P, W = pi.PERIODIC, pi.WALL
+
+
+@pytest.fixture(scope="module")
+def paris():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2012_11744_gb300 as m
+    m.build()
+    return m
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def ctx_for(paris, grid, **opts):
+    return paris.Context(grid, opts=paris.default_opts(**opts))
+
+
+GRIDS = [
+    pi.Grid(32, 32, 32, 1 / 32, (P, P, P)),
+    pi.Grid(24, 20, 16, 1 / 24, (P, P, W)),
+    pi.Grid(17, 9, 12, 0.05, (W, P, W)),
+    pi.Grid(6, 5, 3, 0.2, (W, W, W)),
+    pi.Grid(2, 2, 2, 0.5, (P, P, P)),
+    pi.Grid(48, 2, 10, 1 / 48, (P, W, P)),
+]
+GID = [f"{g.nx}x{g.ny}x{g.nz}_{''.join('pw'[b] for b in g.bc)}" for g in GRIDS]
+
+
+@pytest.mark.parametrize("grid", GRIDS, ids=GID)
+def test_face_coeffs_match_oracle(paris, grid):
+    pr = pi.random_problem(grid, seed=1, rho1=1000.0)
+    ref = oracle.face_coeffs(grid, pr.C, pr.rho1, pr.rho2)
+    with ctx_for(paris, grid) as ctx:
+        got = ctx.face_coeffs(dev(pr.C), pr.rho1, pr.rho2)
+        for a in range(3):
+            np.testing.assert_allclose(host(got[a]), ref[a], rtol=4e-16, atol=0)
+
+
+@pytest.mark.parametrize("grid", GRIDS, ids=GID)
+def test_divergence_matches_oracle(paris, grid):
+    pr = pi.random_problem(grid, seed=2)
+    ref = oracle.divergence(grid, pr.u, pr.v, pr.w, pr.dt)
+    mref = ref.mean()
+    with ctx_for(paris, grid) as ctx:
+        rhs, mean = ctx.divergence(dev(pr.u), dev(pr.v), dev(pr.w), pr.dt)
+        scale = np.abs(ref).max()
+        np.testing.assert_allclose(host(rhs), ref - mref, rtol=0, atol=1e-14 * scale)
+        assert abs(mean - mref) <= 1e-14 * scale
+
+
+@pytest.mark.parametrize("grid", GRIDS, ids=GID)
+def test_project_matches_oracle(paris, grid):
+    pr = pi.random_problem(grid, seed=3, rho1=50.0)
+    beta = oracle.face_coeffs(grid, pr.C, pr.rho1, pr.rho2)
+    p = pi.random_field(grid.shape, seed=4)
+    ref = oracle.project(grid, *beta, p, pr.dt, pr.u, pr.v, pr.w)
+    with ctx_for(paris, grid) as ctx:
+        u, v, w = dev(pr.u), dev(pr.v), dev(pr.w)
+        ctx.project(*(dev(b) for b in beta), dev(p), pr.dt, u, v, w)
+        for a, x in enumerate((u, v, w)):
+            np.testing.assert_allclose(host(x), ref[a], rtol=0, atol=1e-14 * np.abs(ref[a]).max())
+
+
+def _check_solution(grid, pr, ref, p_gpu, u_gpu, st, tol=1e-10, perr=1e-8):
+    # residual of the GPU pressure under the ORACLE's operator (FP64 CSR)
+    b = ref.rhs - ref.rhs.mean()
+    r = b - ref.op.apply_L(p_gpu)
+    assert np.linalg.norm(r) <= tol * np.linalg.norm(b) * 1.01, (np.linalg.norm(r) / np.linalg.norm(b), st)
+    assert np.abs(r).max() <= tol * np.abs(b).max() * 1.01, (np.abs(r).max() / np.abs(b).max(), st)
+    assert abs(p_gpu.mean()) <= 1e-12 * np.abs(p_gpu).max()
+    e = np.abs(p_gpu - ref.p).max() / np.abs(ref.p).max()
+    assert e <= perr, (e, st)
+    umax = max(np.abs(x).max() for x in (pr.u, pr.v, pr.w))
+    d = oracle.divergence(grid, *u_gpu, dt=1.0)
+    assert np.abs(d).max() <= 1e-9 * umax / grid.h
+    for a in range(3):
+        np.testing.assert_allclose(u_gpu[a], ref.u[a], rtol=0, atol=1e-7 * umax)
+
+
+@pytest.mark.parametrize("precision", ["FP64", "MIXED"])
+@pytest.mark.parametrize("grid", GRIDS, ids=GID)
+def test_projection_step_matches_oracle(paris, grid, precision):
+    pr = pi.random_problem(grid, seed=5, rho1=1000.0)
+    ref = oracle.projection_step(grid, pr.C, pr.rho1, pr.rho2, pr.dt, pr.u, pr.v, pr.w)
+    with ctx_for(paris, grid, precision=getattr(paris, precision)) as ctx:
+        u, v, w = dev(pr.u), dev(pr.v), dev(pr.w)
+        p = torch.zeros(grid.shape, dtype=torch.float64, device="cuda")
+        st = ctx.projection_step(dev(pr.C), pr.rho1, pr.rho2, pr.dt, u, v, w, p)
+        assert st["converged"] == 1 and st["fell_back"] == 0, st
+        _check_solution(grid, pr, ref, host(p), (host(u), host(v), host(w)), st)
+
+
+@pytest.mark.parametrize("precision", ["FP64", "MIXED"])
+def test_config1_drop32(paris, precision):
+    """The 32^3 drop (rho 10/1, u* from seed 0): full parity."""
+    pr = pi.config1()
+    g = pr.grid
+    ref = oracle.projection_step(g, pr.C, pr.rho1, pr.rho2, pr.dt, pr.u, pr.v, pr.w)
+    with ctx_for(paris, g, precision=getattr(paris, precision)) as ctx:
+        u, v, w = dev(pr.u), dev(pr.v), dev(pr.w)
+        p = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+        st = ctx.projection_step(dev(pr.C), pr.rho1, pr.rho2, pr.dt, u, v, w, p)
+        _check_solution(g, pr, ref, host(p), (host(u), host(v), host(w)), st)
+
+
+@pytest.mark.parametrize("precision", ["FP64", "MIXED"])
+def test_drops_walls_64(paris, precision):
+    """The 256^3 drop-field recipe at 64^3: walls in z, ratio 1000, 64 drops."""
+    pr = pi.config2(n=64)
+    g = pr.grid
+    ref = oracle.projection_step(g, pr.C, pr.rho1, pr.rho2, pr.dt, pr.u, pr.v, pr.w)
+    with ctx_for(paris, g, precision=getattr(paris, precision)) as ctx:
+        u, v, w = dev(pr.u), dev(pr.v), dev(pr.w)
+        p = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+        st = ctx.projection_step(dev(pr.C), pr.rho1, pr.rho2, pr.dt, u, v, w, p)
+        assert st["iters"] <= 30, st
+        _check_solution(g, pr, ref, host(p), (host(u), host(v), host(w)), st)
