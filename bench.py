@@ -1,0 +1,389 @@
+#!/usr/bin/env python
+"""Projection solves/s at 256^3, density ratio 1000, relative residual 1e-10:
+mixed FP32/FP64 form vs plain FP64 form, with the HBM roofline fraction of the
+dominant kernel.
+
+One step = one whole projection (face coefficients from C, divergence of u*,
+multigrid-preconditioned Poisson solve to 1e-10 in the L2 and L-infinity norms,
+velocity correction) of the 256^3 drop field: 64 drops, periodic x/y, walls
+in z, rho1/rho2 = 1000, dt = 1e-4, seeded synthetic input.  Before every step
+u*, v*, w* are restored from device-resident copies and p is reset to zero
+(both inside the timed region; ~1 % of a step).  Each step reads more than the
+129 MB L2 (C plus u*, v*, w*: 537 MB), so no flush is needed.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl paris|reference]
+Multi-GPU (torchrun): every rank runs an independent replica ("replicas
+only": one projection does not shard here), value = all ranks' solves / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Projection solves/s at 256³, ρ ratio 1000, resid 1e-10: mixed vs FP64; % HBM"
+UNIT = "solves/s"
+
+# DRAM traffic of one launch of each instrumented kernel class, from an ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the
+# kernel source is unchanged (sha256 of csrc/kernels.cu at capture time).
+NCU_TRAFFIC = {}
+
+
+def kernel_source_sha() -> str:
+    p = os.path.join(ROOT, "paper_2012_11744_gb300", "csrc", "kernels.cu")
+    with open(p, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.fh = None
+
+    def __enter__(self):
+        try:
+            self.fh = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.fh is None:
+            return None
+        try:
+            with open(self.fh.name) as fh:
+                rows = [r.strip().split(",") for r in fh if r.strip()]
+            os.unlink(self.fh.name)
+        except Exception:
+            return None
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if n_gpus > 0 else "gloo")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------- CPU oracle ---
+
+def oracle_sample(pr, budget_s: float, golden: dict | None):
+    """Time the oracle (as it stands) on a bounded sample of the 256^3 solve:
+    the full set-up (face coefficients, divergence, CSR assembly) plus CG
+    iterations for about `budget_s` seconds; extrapolate to the CG iteration
+    count of the full oracle solve (stored by tests/golden/make_drops256_golden.py)."""
+    import oracle
+    g = pr.grid
+    t0 = time.perf_counter()
+    beta = oracle.face_coeffs(g, pr.C, pr.rho1, pr.rho2)
+    b = oracle.divergence(g, pr.u, pr.v, pr.w, pr.dt)
+    b0 = oracle.remove_mean(b)
+    op = oracle.Operator(g, *beta)
+    t1 = time.perf_counter()
+    m = 10
+    res = oracle.cg(op, -b0, tol=1e-300, max_iter=m, check=10 ** 9)
+    t2 = time.perf_counter()
+    per_it = (t2 - t1) / m
+    m2 = max(10, int(budget_s / max(per_it, 1e-6)))
+    t3 = time.perf_counter()
+    res = oracle.cg(op, -b0, tol=1e-300, max_iter=m2, check=50)
+    t4 = time.perf_counter()
+    per_it = (t4 - t3) / max(res.iters, 1)
+    n_full = int(golden["oracle"]["cg_iters"]) if golden else None
+    proj = oracle.project(g, *beta, res.x, pr.dt, pr.u, pr.v, pr.w)  # noqa: F841 (timed below)
+    t5 = time.perf_counter()
+    setup = (t1 - t0) + (t5 - t4)
+    if n_full is None:
+        n_full = 12000  # order of magnitude when the stored count is missing
+    solve_s = setup + per_it * n_full
+    return {"solve_s": solve_s, "setup_s": setup, "s_per_cg_iter": per_it, "cg_iters_sampled": res.iters,
+            "cg_iters_full": n_full, "sample_s": t5 - t0}
+
+
+def load_golden(n):
+    p = os.path.join(ROOT, "tests", "golden", f"drops{n}_walls_z.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh)
+    return None
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 CPU oracle on the host cores, same metric."""
+    if rank != 0:
+        return
+    import paris_inputs as pi
+    pr = pi.config2(n=args.n)
+    golden = load_golden(args.n)
+    cores = os.cpu_count()
+    for _ in range(args.warmup):
+        oracle_sample(pr, 0.5, golden)
+    samples = [oracle_sample(pr, args.ref_budget, golden) for _ in range(args.steps)]
+    total = sum(s["solve_s"] for s in samples)
+    value = args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(args.n),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"per step: oracle set-up + ~{args.ref_budget:.0f} s of CG iterations "
+                                   f"on the {args.n}^3 system, extrapolated to the "
+                                   f"{samples[0]['cg_iters_full']} iterations of the full oracle solve"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(n):
+    return {"workload": f"drops{n}_walls_z: {n}^3 unit box, periodic x/y, walls z, 64 drops, "
+                        f"rho 1000/1, dt 1e-4, tol 1e-10 (L2 and Linf)",
+            "grid": [n, n, n], "precision": "mixed FP32 V-cycles in FP64 refinement (value) vs FP64",
+            "l2": "no flush: every step reads C and u*,v*,w* (4 x 134 MB > 129 MB L2)",
+            "parallelism": "replicas"}
+
+
+# ---------------------------------------------------------------- GPU arm ---
+
+def run_paris(args, rank, world, local):
+    import torch
+
+    import paper_2012_11744_gb300 as paris
+    from paper_2012_11744_gb300 import api
+    import paris_inputs as pi
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    pr = pi.config2(n=args.n)
+    g = pr.grid
+    N = g.ncells
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    C = d(pr.C)
+    u0, v0, w0 = d(pr.u), d(pr.v), d(pr.w)
+    u, v, w = u0.clone(), v0.clone(), w0.clone()
+    p = torch.zeros(g.shape, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    results = {}
+
+    def step(ctx):
+        u.copy_(u0)
+        v.copy_(v0)
+        w.copy_(w0)
+        p.zero_()
+        return ctx.projection_step(C, pr.rho1, pr.rho2, pr.dt, u, v, w, p)
+
+    def timed(ctx, K, W, prof=False):
+        for _ in range(W):
+            st = step(ctx)
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        if prof:
+            ctx.profile(True)
+        l0 = api.launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sts = []
+        for _ in range(K):
+            sts.append(step(ctx))
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        launches = api.launch_count() - l0
+        ms = e0.elapsed_time(e1)
+        prof_d = ctx.profile_read() if prof else None
+        if prof:
+            ctx.profile(False)
+        return ms, sts, launches, prof_d
+
+    hbm, peak_kind = measured_peaks()
+    # mixed precision (headline)
+    ctx = paris.Context(g, opts=paris.default_opts(precision=paris.MIXED), device=dev)
+    with ClockSampler(local) as clk:
+        ms_mixed, st_mixed, launches, prof = timed(ctx, args.steps, args.warmup, prof=True)
+    clocks = clk.summary()
+    ms_mixed = allreduce_max(ms_mixed, world, dev)
+    # e2e through the host-buffer entry point (pinned host memory)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    hC, hu0, hv0, hw0 = pin(pr.C), pin(pr.u), pin(pr.v), pin(pr.w)
+    hu, hv, hw = hu0.clone().pin_memory(), hv0.clone().pin_memory(), hw0.clone().pin_memory()
+    hp = torch.zeros(g.shape, dtype=torch.float64).pin_memory()
+    ctx.projection_step_host(hC, pr.rho1, pr.rho2, pr.dt, hu, hv, hw, hp)  # allocates staging
+    e2e_s = 0.0
+    k_e2e = max(3, args.steps // 2)
+    for i in range(args.warmup + k_e2e):
+        hu.copy_(hu0)
+        hv.copy_(hv0)
+        hw.copy_(hw0)
+        hp.zero_()
+        t0 = time.perf_counter()
+        ctx.projection_step_host(hC, pr.rho1, pr.rho2, pr.dt, hu, hv, hw, hp)
+        t1 = time.perf_counter()
+        if i >= args.warmup:
+            e2e_s += t1 - t0
+    e2e_s = allreduce_max(e2e_s, world, dev)
+    h2d = 8 * (2 * N + sum(int(np.prod(g.face_shape(a))) for a in range(3)))
+    d2h = h2d - 8 * N
+    ctx.close()
+    # plain FP64 form
+    ctx = paris.Context(g, opts=paris.default_opts(precision=paris.FP64), device=dev)
+    k64 = max(3, args.steps // 2)
+    ms_fp64, st_fp64, _, prof64 = timed(ctx, k64, args.warmup, prof=True)
+    ms_fp64 = allreduce_max(ms_fp64, world, dev)
+    ctx.close()
+
+    if rank != 0:
+        return
+    value = world * args.steps / (ms_mixed / 1e3)
+    fp64_value = world * k64 / (ms_fp64 / 1e3)
+    # roofline of the dominant kernel class (largest summed time)
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    pk = prof[dom]
+    achieved = pk["bytes"] / (pk["ms"] / 1e3) / 1e9 if pk["ms"] > 0 else None
+    tr = NCU_TRAFFIC.get(dom)
+    traffic = tr["bytes_per_launch"] if tr and tr.get("kernels_sha") == kernel_source_sha() else None
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        import paris_inputs as pi2  # noqa: F401
+        golden = load_golden(args.n)
+        s = oracle_sample(pr, args.cpu_budget, golden)
+        cpu = {"value": 1.0 / s["solve_s"], "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"oracle set-up + {s['cg_iters_sampled']} CG iterations of the {args.n}^3 "
+                         f"system ({s['sample_s']:.1f} s), extrapolated to the {s['cg_iters_full']} "
+                         f"iterations of the full oracle solve"}
+    its = [s["iters"] for s in st_mixed]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_mixed / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": workload_config(args.n),
+        "fp64": {"value": fp64_value, "unit": UNIT, "ms_per_step": ms_fp64 / k64, "steps": k64,
+                 "iters": st_fp64[-1]["iters"], "rel_res_l2": st_fp64[-1]["rel_res_l2"],
+                 "rel_res_linf": st_fp64[-1]["rel_res_linf"]},
+        "mixed_over_fp64": value / fp64_value,
+        "solve": {"iters": its[-1], "outer_iters": st_mixed[-1]["outer_iters"],
+                  "rel_res_l2": st_mixed[-1]["rel_res_l2"], "rel_res_linf": st_mixed[-1]["rel_res_linf"],
+                  "levels": st_mixed[-1]["levels"], "fell_back": st_mixed[-1]["fell_back"]},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
+                     "peak_kind": peak_kind, "launches": pk["timed"],
+                     "avg_launch_us": 1e3 * pk["ms"] / max(pk["timed"], 1)},
+        "kernel_classes": {k: {"launches": v["timed"], "ms": v["ms"],
+                               "gbs": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else None}
+                           for k, v in prof.items()},
+        "kernel_classes_fp64": {k: {"launches": v["timed"], "ms": v["ms"],
+                                    "gbs": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else None}
+                                for k, v in prof64.items()},
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * k_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="paris", choices=["paris", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="grid edge of the drop-field workload")
+    ap.add_argument("--ref-budget", type=float, default=2.0,
+                    help="seconds of oracle CG iterations per --impl reference step")
+    ap.add_argument("--cpu-budget", type=float, default=6.0,
+                    help="seconds of oracle CG iterations in the cpu_baseline sample")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        # rank 0 alone runs the CPU oracle; other ranks exit without work
+        run_reference(args, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")))
+        return
+    rank, world, local = dist_setup(args.gpus)
+    run_paris(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

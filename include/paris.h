@@ -70,8 +70,12 @@ typedef enum {
 } paris_precision;
 
 typedef enum {
-    PARIS_SMOOTH_RBGS = 0,   /* red-black Gauss-Seidel with over-relaxation (Sec. 3.7.1) */
-    PARIS_SMOOTH_JACOBI = 1  /* damped Jacobi, the paper's GPU iteration (Sec. 3.7.4) */
+    PARIS_SMOOTH_RBGS = 0,       /* red-black Gauss-Seidel with over-relaxation (Sec. 3.7.1),
+                                    both colours fused into one pass over memory */
+    PARIS_SMOOTH_JACOBI = 1,     /* damped Jacobi, the paper's GPU iteration (Sec. 3.7.4) */
+    PARIS_SMOOTH_RBGS_2PASS = 2  /* the same red-black iteration as two in-place colour
+                                    passes (bit-identical to PARIS_SMOOTH_RBGS when every
+                                    periodic axis has even length) */
 } paris_smoother;
 
 typedef struct {
@@ -86,7 +90,7 @@ typedef struct {
     int precision;        /* paris_precision (PARIS_MIXED) */
     int nu1, nu2;         /* pre/post smoothing sweeps per level (2, 2) */
     double omega;         /* over-relaxation factor of the smoother (1.15; Jacobi: 0.8) */
-    int smoother;         /* paris_smoother (PARIS_SMOOTH_RBGS) */
+    int smoother;         /* paris_smoother (PARIS_SMOOTH_RBGS_2PASS) */
     int coarse_max_cells; /* coarsen until the coarsest grid has at most this many cells (64) */
     double inner_tol;     /* MIXED: relative residual reduction of each FP32 inner solve (1e-5) */
     int fallback;         /* MIXED: on failure redo the solve in FP64 (1) */
@@ -182,6 +186,36 @@ paris_status paris_residual_norms(paris_ctx* ctx, const double* beta_x, const do
                                   double* rel_l2, double* rel_linf);
 paris_status paris_max_divergence(paris_ctx* ctx, const double* u, const double* v,
                                   const double* w, double* max_abs_div);
+
+/* Kernel-class timing (diagnostics for roofline reports).  While enabled,
+ * every launch of an instrumented level-0 kernel class is bracketed by a CUDA
+ * event pair on the context's stream (a pool of 16384 pairs per enable;
+ * launches beyond it are counted but not timed).  paris_profile(ctx, 1)
+ * clears the counters; paris_profile_read synchronises the stream and returns
+ * the launches, their summed device time and their summed algorithmic bytes
+ * (each array a launch must touch read or written once, at the precision the
+ * kernel ran in).  Classes: */
+typedef enum {
+    PARIS_K_SMOOTH0 = 0,   /* one smoother pass on the finest level */
+    PARIS_K_RESTRICT0 = 1, /* residual + restriction from the finest level */
+    PARIS_K_PROLONG0 = 2,  /* prolongation + correction onto the finest level */
+    PARIS_K_MATVEC0 = 3,   /* Krylov operator application q = A d (+ d.q) */
+    PARIS_K_RESID64 = 4,   /* FP64 true residual r = f - A p (+ norms) */
+    PARIS_K_COUNT = 5
+} paris_kernel_class;
+
+typedef struct {
+    int64_t launches; /* launches recorded since paris_profile(ctx, 1) */
+    int64_t timed;    /* launches that had an event pair */
+    double ms;        /* summed device time of the timed launches */
+    double bytes;     /* summed algorithmic bytes of the timed launches */
+} paris_kernel_prof;
+
+paris_status paris_profile(paris_ctx* ctx, int enable);
+paris_status paris_profile_read(paris_ctx* ctx, int kernel_class, paris_kernel_prof* out);
+
+/* Process-wide number of CUDA kernels this library has launched. */
+int64_t paris_launch_count(void);
 
 /* Face-array sizes (number of doubles) of the context's grid; axis 0, 1, 2. */
 int64_t paris_face_count(const paris_ctx* ctx, int axis);

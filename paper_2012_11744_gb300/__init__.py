@@ -5,9 +5,9 @@ variable-coefficient Poisson solve, velocity correction -- runs in the CUDA
 kernels of ``libparis.so`` behind the C ABI of ``include/paris.h``; this
 package is the thin Python binding (argument marshalling only).
 """
-from .api import (FP64, MIXED, PERIODIC, SMOOTH_JACOBI, SMOOTH_RBGS, WALL, Context, Grid,  # noqa: F401
-                  ParisError, default_opts)
+from .api import (FP64, MIXED, PERIODIC, SMOOTH_JACOBI, SMOOTH_RBGS, SMOOTH_RBGS_2PASS,  # noqa: F401
+                  WALL, Context, Grid, ParisError, default_opts, launch_count)
 from .build import build  # noqa: F401
 
 __all__ = ["Context", "Grid", "default_opts", "ParisError", "build", "FP64", "MIXED", "PERIODIC",
-           "WALL", "SMOOTH_RBGS", "SMOOTH_JACOBI"]
+           "WALL", "SMOOTH_RBGS", "SMOOTH_JACOBI", "SMOOTH_RBGS_2PASS", "launch_count"]

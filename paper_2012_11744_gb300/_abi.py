@@ -25,6 +25,7 @@ FP64 = 0
 MIXED = 1
 SMOOTH_RBGS = 0
 SMOOTH_JACOBI = 1
+SMOOTH_RBGS_2PASS = 2
 
 
 class Grid(ct.Structure):
@@ -37,6 +38,15 @@ class Opts(ct.Structure):
                 ("nu1", ct.c_int), ("nu2", ct.c_int), ("omega", ct.c_double),
                 ("smoother", ct.c_int), ("coarse_max_cells", ct.c_int),
                 ("inner_tol", ct.c_double), ("fallback", ct.c_int)]
+
+
+class KernelProf(ct.Structure):
+    _fields_ = [("launches", ct.c_int64), ("timed", ct.c_int64), ("ms", ct.c_double),
+                ("bytes", ct.c_double)]
+
+
+K_SMOOTH0, K_RESTRICT0, K_PROLONG0, K_MATVEC0, K_RESID64 = range(5)
+K_NAMES = ("smooth0", "restrict0", "prolong0", "matvec0", "resid64")
 
 
 class Stats(ct.Structure):
@@ -68,6 +78,9 @@ SIGNATURES = {
                                               ct.POINTER(Stats)]),
     "paris_residual_norms": (ct.c_int, [_P, _P, _P, _P, _P, _P, ct.POINTER(_D), ct.POINTER(_D)]),
     "paris_max_divergence": (ct.c_int, [_P, _P, _P, _P, ct.POINTER(_D)]),
+    "paris_profile": (ct.c_int, [_P, ct.c_int]),
+    "paris_profile_read": (ct.c_int, [_P, ct.c_int, ct.POINTER(KernelProf)]),
+    "paris_launch_count": (ct.c_int64, []),
     "paris_face_count": (ct.c_int64, [_P, ct.c_int]),
     "paris_cell_count": (ct.c_int64, [_P]),
     "paris_status_string": (ct.c_char_p, [ct.c_int]),

@@ -13,7 +13,8 @@ import numpy as np
 import torch
 
 from . import _abi
-from ._abi import MIXED, FP64, PERIODIC, WALL, SMOOTH_JACOBI, SMOOTH_RBGS, ParisError  # noqa: F401
+from ._abi import (MIXED, FP64, PERIODIC, WALL, SMOOTH_JACOBI, SMOOTH_RBGS,  # noqa: F401
+                   SMOOTH_RBGS_2PASS, ParisError)
 
 
 @dataclass
@@ -44,6 +45,11 @@ def default_opts(**kw) -> _abi.Opts:
             raise AttributeError(f"unknown option {k}")
         setattr(o, k, v)
     return o
+
+
+def launch_count() -> int:
+    """Number of CUDA kernels libparis.so has launched in this process."""
+    return int(_abi.load().paris_launch_count())
 
 
 def _grid_struct(g) -> _abi.Grid:
@@ -228,6 +234,19 @@ class Context:
                                                  self._t(p, g.shape, "p"), ct.byref(a), ct.byref(b)),
                    "paris_residual_norms")
         return a.value, b.value
+
+    def profile(self, enable: bool = True):
+        """Start (clearing the counters) or stop per-kernel-class event timing."""
+        _abi.check(self.lib.paris_profile(self._ptr, 1 if enable else 0), "paris_profile")
+
+    def profile_read(self):
+        """{class name: {launches, timed, ms, bytes}} for the instrumented classes."""
+        out = {}
+        for k, name in enumerate(_abi.K_NAMES):
+            kp = _abi.KernelProf()
+            _abi.check(self.lib.paris_profile_read(self._ptr, k, ct.byref(kp)), "paris_profile_read")
+            out[name] = {"launches": kp.launches, "timed": kp.timed, "ms": kp.ms, "bytes": kp.bytes}
+        return out
 
     def max_divergence(self, u, v, w):
         """max |grad^h . u| over the cells, computed on the device."""

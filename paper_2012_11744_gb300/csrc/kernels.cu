@@ -12,6 +12,8 @@
 // i.e. the paper's A7 p - sum A_nb p_nb with A_nb = beta_f scale.
 #include <math.h>
 
+#include <atomic>
+
 #include "kernels.cuh"
 
 namespace paris {
@@ -36,6 +38,10 @@ __device__ inline int flat_tid() { return threadIdx.y * blockDim.x + threadIdx.x
 __device__ inline double nonfinite(double v) { return isfinite(v) ? 0.0 : 1.0; }
 
 }  // namespace
+
+static std::atomic<long long> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 int elementwise_blocks(int64_t n) {
     int64_t b = (n + kRedThreads - 1) / kRedThreads;
@@ -102,6 +108,7 @@ __global__ void finalize_kernel(const double* __restrict__ partials, int64_t nbl
 void finalize(const double* partials, int64_t nblocks, int nv, int maxmask, Scal* s, int mode,
               double param, cudaStream_t st) {
     finalize_kernel<<<1, kRedThreads, 0, st>>>(partials, nblocks, nv, maxmask, s, mode, param);
+    count_launch();
 }
 
 // ------------------------------------------------------- face coefficients ---
@@ -142,6 +149,7 @@ void launch_face_coeffs(const Geo& g, const double* C, double rho1, double rho2,
                         double* by, double* bz, cudaStream_t st) {
     dim3 gr((g.nx + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, g.nz);
     face_coeffs_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(g, C, rho1, rho2, bx, by, bz);
+    count_launch();
 }
 
 // -------------------------------------------------------------- divergence ---
@@ -188,6 +196,7 @@ int64_t launch_divergence(const Geo& g, const double* u, const double* v, const 
                           double inv_hdt, double* rhs, double* partials, cudaStream_t st) {
     dim3 gr = tile_grid(g, kZ);
     divergence_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(g, u, v, w, inv_hdt, rhs, partials);
+    count_launch();
     return nblocks_of(gr);
 }
 
@@ -210,6 +219,7 @@ int64_t launch_max_divergence(const Geo& g, const double* u, const double* v, co
                               double inv_h, double* partials, cudaStream_t st) {
     dim3 gr = tile_grid(g, kZ);
     max_div_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(g, u, v, w, inv_h, partials);
+    count_launch();
     return nblocks_of(gr);
 }
 
@@ -234,6 +244,7 @@ int64_t launch_make_rhs(int64_t n, const double* rhs, const Scal* s, double* f, 
                         cudaStream_t st) {
     int nb = elementwise_blocks(n);
     make_rhs_kernel<<<nb, kRedThreads, 0, st>>>(n, rhs, s, f, partials);
+    count_launch();
     return nb;
 }
 
@@ -246,6 +257,7 @@ __global__ void sub_mean_kernel(int64_t n, double* __restrict__ x, const Scal* s
 
 void launch_sub_mean(int64_t n, double* x, const Scal* s, cudaStream_t st) {
     sub_mean_kernel<<<elementwise_blocks(n), kRedThreads, 0, st>>>(n, x, s);
+    count_launch();
 }
 
 __global__ void sum_kernel(int64_t n, const double* __restrict__ x, double* partials) {
@@ -263,6 +275,7 @@ __global__ void sum_kernel(int64_t n, const double* __restrict__ x, double* part
 int64_t launch_sum(int64_t n, const double* x, double* partials, cudaStream_t st) {
     int nb = elementwise_blocks(n);
     sum_kernel<<<nb, kRedThreads, 0, st>>>(n, x, partials);
+    count_launch();
     return nb;
 }
 
@@ -303,6 +316,7 @@ void launch_project(const Geo& g, const double* bx, const double* by, const doub
                     cudaStream_t st) {
     dim3 gr((g.nx + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, g.nz);
     project_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(g, bx, by, bz, p, dt_over_h, u, v, w);
+    count_launch();
 }
 
 // ------------------------------------------------------------ level set-up ---
@@ -323,6 +337,7 @@ void launch_convert_beta(const Geo& g, const double* b64[3], double scale, T* ou
         int64_t n = g.nface(a);
         convert_beta_kernel<T><<<elementwise_blocks(n), kRedThreads, 0, st>>>(n, b64[a], scale,
                                                                               out[a]);
+        count_launch();
     }
 }
 
@@ -372,6 +387,7 @@ void launch_coarse_beta(const Geo& fine, const Coef<T>& cf, const Geo& coarse, c
         int64_t n = coarse.nface(a);
         coarse_beta_kernel<T><<<elementwise_blocks(n), kRedThreads, 0, st>>>(
             fine, cf, coarse, f[0], f[1], f[2], a, 1.0 / hc2_over_hf2[a], out[a]);
+        count_launch();
     }
 }
 
@@ -393,6 +409,7 @@ template <typename T>
 void launch_inv_diag(const Geo& g, const Coef<T>& cf, T* w, cudaStream_t st) {
     dim3 gr((g.nx + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, g.nz);
     inv_diag_kernel<T><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, w);
+    count_launch();
 }
 
 // Dense inverse of the coarsest operator regularised on its null space:
@@ -456,6 +473,7 @@ template <typename T>
 void launch_coarse_inverse(const Geo& g, const Coef<T>& cf, double* inv, cudaStream_t st) {
     int n = (int)g.ncell();
     coarse_inverse_kernel<T><<<1, 256, sizeof(double) * n, st>>>(g, cf, inv);
+    count_launch();
 }
 
 // x = M (f - mean f) on the coarsest level (FP64 arithmetic).
@@ -484,6 +502,7 @@ template <typename T>
 void launch_coarse_solve(const Geo& g, const double* inv, const T* f, T* x, cudaStream_t st) {
     int n = (int)g.ncell();
     coarse_solve_kernel<T><<<1, 128, sizeof(double) * n, st>>>(n, inv, f, x);
+    count_launch();
 }
 
 // ------------------------------------------------------------------ smoothers ---
@@ -531,6 +550,7 @@ void launch_rbgs(const Geo& g, const Coef<T>& cf, const T* w, const T* f, T* x, 
     dim3 gr((npair + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, g.nz);
     rbgs_kernel<T><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, w, f, x, color, (T)omega,
                                                   zero_init ? 1 : 0);
+    count_launch();
 }
 
 // Damped Jacobi (the paper's GPU iteration, Sec. 3.7.4), double-buffered:
@@ -567,6 +587,7 @@ void launch_jacobi(const Geo& g, const Coef<T>& cf, const T* w, const T* f, cons
     dim3 gr((g.nx + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, g.nz);
     jacobi_kernel<T><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, w, f, x, xout, (T)omega,
                                                     zero_init ? 1 : 0);
+    count_launch();
 }
 
 // ------------------------------------------------- restriction / prolongation ---
@@ -600,6 +621,7 @@ void launch_restrict_residual(const Geo& fine, const Coef<T>& cf, const T* f, co
     dim3 gr((coarse.nx + kTX - 1) / kTX, (coarse.ny + kTY - 1) / kTY, coarse.nz);
     restrict_residual_kernel<T><<<gr, dim3(kTX, kTY), 0, st>>>(fine, cf, f, x, coarse, fac[0],
                                                                fac[1], fac[2], fc);
+    count_launch();
 }
 
 template <typename T>
@@ -618,6 +640,7 @@ void launch_prolong_add(const Geo& fine, const Geo& coarse, const int fac[3], co
     dim3 gr((fine.nx + kTX - 1) / kTX, (fine.ny + kTY - 1) / kTY, fine.nz);
     prolong_add_kernel<T><<<gr, dim3(kTX, kTY), 0, st>>>(fine, coarse, fac[0], fac[1], fac[2], xc,
                                                          x);
+    count_launch();
 }
 
 // ------------------------------------------------------------------ Krylov ---
@@ -657,6 +680,7 @@ int64_t launch_residual64(const Geo& g, const Coef<double>& cf, const double* f,
                           cudaStream_t st) {
     dim3 gr = tile_grid(g, kZ);
     residual64_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, f, x, r64, r32, s, partials);
+    count_launch();
     return nblocks_of(gr);
 }
 
@@ -692,6 +716,7 @@ int64_t launch_matvec_dot(const Geo& g, const Coef<T>& cf, const T* d, T* q, dou
                           cudaStream_t st) {
     dim3 gr = tile_grid(g, kZ);
     matvec_dot_kernel<T><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, d, q, partials);
+    count_launch();
     return nblocks_of(gr);
 }
 
@@ -721,6 +746,7 @@ int64_t launch_update_xr(int64_t n, const Scal* s, const T* d, const T* q, T* x,
                          double* partials, cudaStream_t st) {
     int nb = elementwise_blocks(n);
     update_xr_kernel<T><<<nb, kRedThreads, 0, st>>>(n, s, d, q, x, r, partials);
+    count_launch();
     return nb;
 }
 
@@ -744,6 +770,7 @@ int64_t launch_dot2(int64_t n, const T* a, const T* b, const T* c, double* parti
                     cudaStream_t st) {
     int nb = elementwise_blocks(n);
     dot2_kernel<T><<<nb, kRedThreads, 0, st>>>(n, a, b, c, partials);
+    count_launch();
     return nb;
 }
 
@@ -758,6 +785,7 @@ __global__ void xpby_kernel(int64_t n, const Scal* s, const T* __restrict__ z, T
 template <typename T>
 void launch_xpby(int64_t n, const Scal* s, const T* z, T* d, cudaStream_t st) {
     xpby_kernel<T><<<elementwise_blocks(n), kRedThreads, 0, st>>>(n, s, z, d);
+    count_launch();
 }
 
 __global__ void accumulate_kernel(int64_t n, const Scal* s, const float* __restrict__ e,
@@ -770,6 +798,7 @@ __global__ void accumulate_kernel(int64_t n, const Scal* s, const float* __restr
 
 void launch_accumulate(int64_t n, const Scal* s, const float* e, double* x, cudaStream_t st) {
     accumulate_kernel<<<elementwise_blocks(n), kRedThreads, 0, st>>>(n, s, e, x);
+    count_launch();
 }
 
 // ------------------------------------------------------ explicit instances ---

@@ -39,6 +39,10 @@ enum FinalizeMode {
 // Generic grid for element-wise kernels.
 int elementwise_blocks(int64_t n);
 
+// Process-wide count of kernel launches made by the library.
+void count_launch(int n = 1);
+long long launch_count();
+
 void finalize(const double* partials, int64_t nblocks, int nv, int maxmask, Scal* s, int mode,
               double param, cudaStream_t st);
 
@@ -80,6 +84,14 @@ void launch_coarse_solve(const Geo& g, const double* inv, const T* f, T* x, cuda
 template <typename T>
 void launch_rbgs(const Geo& g, const Coef<T>& cf, const T* w, const T* f, T* x, int color,
                  double omega, bool zero_init, cudaStream_t st);
+// One fused red-black sweep (both colours, one pass) from xin to xout
+// (separate arrays; xin unread when zero_init).  first_color: colour
+// updated first (0 = red, (i+j+k) even).  use_w: read the inverse diagonal
+// from w instead of recomputing it from the coefficients.
+template <typename T>
+void launch_rbgs_fused(const Geo& g, const Coef<T>& cf, const T* w, const T* f, const T* xin,
+                       T* xout, int first_color, double omega, bool zero_init, bool use_w,
+                       cudaStream_t st);
 // One damped-Jacobi sweep x_out = x + omega D^{-1} (f - A x).
 template <typename T>
 void launch_jacobi(const Geo& g, const Coef<T>& cf, const T* w, const T* f, const T* x, T* xout,

@@ -65,6 +65,16 @@ struct Alloc {
 };
 
 constexpr int kMaxDense = 128;
+constexpr int kProfPool = 8192;  // event pairs per paris_profile(ctx, 1)
+
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;  // 2 per slot
+    std::vector<int> slot_cls;
+    std::vector<double> slot_bytes;
+    int used = 0;
+    int64_t launches[PARIS_K_COUNT] = {};
+};
 
 }  // namespace
 
@@ -93,6 +103,7 @@ struct paris_ctx {
     // host-call staging (allocated on first use)
     double *hC = nullptr, *hu = nullptr, *hv = nullptr, *hw = nullptr, *hp = nullptr;
     double last_mean_b = 0.0;
+    Profiler prof;
 };
 
 namespace {
@@ -118,7 +129,7 @@ bool valid_opts(const paris_opts* o) {
     if (o->precision != PARIS_FP64 && o->precision != PARIS_MIXED) return false;
     if (o->nu1 < 0 || o->nu2 < 0 || o->nu1 + o->nu2 < 1 || o->nu1 > 16 || o->nu2 > 16) return false;
     if (!(o->omega > 0.0 && o->omega < 2.0)) return false;
-    if (o->smoother != PARIS_SMOOTH_RBGS && o->smoother != PARIS_SMOOTH_JACOBI) return false;
+    if (o->smoother < PARIS_SMOOTH_RBGS || o->smoother > PARIS_SMOOTH_RBGS_2PASS) return false;
     if (o->coarse_max_cells < 1 || o->coarse_max_cells > kMaxDense) return false;
     if (!(o->inner_tol > 0.0 && o->inner_tol < 1.0)) return false;
     return true;
@@ -219,6 +230,29 @@ paris_status read_scal(paris_ctx* c) {
     return PARIS_OK;
 }
 
+// Brackets one launch of an instrumented kernel class with an event pair
+// when profiling is on (see paris_profile).
+struct ProfScope {
+    paris_ctx* c;
+    int slot = -1;
+    ProfScope(paris_ctx* c_, int cls, double bytes) : c(c_) {
+        Profiler& P = c->prof;
+        if (!P.on || cls < 0) return;
+        P.launches[cls]++;
+        if (P.used < kProfPool) {
+            slot = P.used++;
+            P.slot_cls[slot] = cls;
+            P.slot_bytes[slot] = bytes;
+            cudaEventRecord(P.ev[2 * slot], c->st);
+        }
+    }
+    ~ProfScope() {
+        if (slot >= 0) cudaEventRecord(c->prof.ev[2 * slot + 1], c->st);
+    }
+};
+
+double beta_count(const Geo& g) { return (double)(g.nface(0) + g.nface(1) + g.nface(2)); }
+
 // ------------------------------------------------------------- V-cycle ---
 
 template <typename T>
@@ -271,18 +305,44 @@ void smooth(paris_ctx* c, int l, const Coef<T>& cf, const T* f, T* x, int sweeps
             bool reverse) {
     Level& L = c->lv[l];
     const paris_opts& o = c->opts;
+    const double n = (double)L.g.ncell(), sz = sizeof(T), nb = beta_count(L.g);
+    const int cls = l == 0 ? PARIS_K_SMOOTH0 : -1;
+    const bool use_w = sizeof(T) == 8;  // FP64: a division costs more than reading 1/D
+    if (o.smoother == PARIS_SMOOTH_RBGS_2PASS) {
+        for (int s = 0; s < sweeps; ++s) {
+            const bool z0 = first_zero && s == 0;
+            const int c0 = reverse ? 1 : 0;
+            {
+                ProfScope ps(c, cls, z0 ? 2 * n * sz : (2.5 * n + nb) * sz);
+                launch_rbgs<T>(L.g, cf, Prec<T>::w(L), f, x, c0, o.omega, z0, c->st);
+            }
+            {
+                ProfScope ps(c, cls, (2.5 * n + nb) * sz);
+                launch_rbgs<T>(L.g, cf, Prec<T>::w(L), f, x, 1 - c0, o.omega, false, c->st);
+            }
+        }
+        return;
+    }
+    // ping-pong between x and the level's second buffer, ending in x
+    T* bufs[2] = {x, Prec<T>::t(L)};
+    int cur = 0;
     for (int s = 0; s < sweeps; ++s) {
         const bool z0 = first_zero && s == 0;
+        const int remaining = sweeps - s;
+        const int out = z0 ? ((remaining % 2 == 1) ? 0 : 1) : 1 - cur;
+        const T* in = z0 ? nullptr : bufs[cur];
         if (o.smoother == PARIS_SMOOTH_JACOBI) {
-            // x -> t -> copy back keeps x as the output buffer
-            launch_jacobi<T>(L.g, cf, Prec<T>::w(L), f, x, Prec<T>::t(L), o.omega, z0, c->st);
-            cudaMemcpyAsync(x, Prec<T>::t(L), sizeof(T) * L.g.ncell(), cudaMemcpyDeviceToDevice, c->st);
+            ProfScope ps(c, cls, (z0 ? 3 * n : 4 * n + nb) * sz);
+            launch_jacobi<T>(L.g, cf, Prec<T>::w(L), f, in ? in : f, bufs[out], o.omega, z0, c->st);
         } else {
-            const int c0 = reverse ? 1 : 0;
-            launch_rbgs<T>(L.g, cf, Prec<T>::w(L), f, x, c0, o.omega, z0, c->st);
-            launch_rbgs<T>(L.g, cf, Prec<T>::w(L), f, x, 1 - c0, o.omega, false, c->st);
+            ProfScope ps(c, cls, ((z0 ? 2 * n : 3 * n) + nb + (use_w ? n : 0)) * sz);
+            launch_rbgs_fused<T>(L.g, cf, Prec<T>::w(L), f, in, bufs[out], reverse ? 1 : 0, o.omega, z0,
+                                 use_w, c->st);
         }
+        cur = out;
     }
+    if (cur != 0)
+        cudaMemcpyAsync(x, bufs[cur], sizeof(T) * L.g.ncell(), cudaMemcpyDeviceToDevice, c->st);
 }
 
 // x0 = V(f0): one symmetric V-cycle for A x = f on level 0 (x0 overwritten).
@@ -297,7 +357,12 @@ void vcycle(paris_ctx* c, const Coef<T>& c0, const T* f0, T* x0) {
         if (o.nu1 > 0) smooth<T>(c, l, cf, f, x, o.nu1, true, false);
         else cudaMemsetAsync(x, 0, sizeof(T) * c->lv[l].g.ncell(), c->st);
         Level& C = c->lv[l + 1];
-        launch_restrict_residual<T>(c->lv[l].g, cf, f, x, C.g, C.fac, Prec<T>::f(C), c->st);
+        {
+            const double n = (double)c->lv[l].g.ncell();
+            ProfScope ps(c, l == 0 ? PARIS_K_RESTRICT0 : -1,
+                         (2 * n + beta_count(c->lv[l].g) + (double)C.g.ncell()) * sizeof(T));
+            launch_restrict_residual<T>(c->lv[l].g, cf, f, x, C.g, C.fac, Prec<T>::f(C), c->st);
+        }
     }
     {
         Level& C = c->lv[nl - 1];
@@ -316,7 +381,11 @@ void vcycle(paris_ctx* c, const Coef<T>& c0, const T* f0, T* x0) {
         T* x = l == 0 ? x0 : Prec<T>::x(c->lv[l]);
         Coef<T> cf = level_coef<T>(c, l, c0);
         Level& C = c->lv[l + 1];
-        launch_prolong_add<T>(c->lv[l].g, C.g, C.fac, Prec<T>::x(C), x, c->st);
+        {
+            const double n = (double)c->lv[l].g.ncell();
+            ProfScope ps(c, l == 0 ? PARIS_K_PROLONG0 : -1, (2 * n + (double)C.g.ncell()) * sizeof(T));
+            launch_prolong_add<T>(c->lv[l].g, C.g, C.fac, Prec<T>::x(C), x, c->st);
+        }
         if (o.nu2 > 0) smooth<T>(c, l, cf, f, x, o.nu2, false, true);
     }
 }
@@ -345,8 +414,13 @@ paris_status prologue(paris_ctx* c, const double* rhs) {
 
 paris_status true_residual(paris_ctx* c, const Coef<double>& c64, const double* x, float* r32) {
     if (r32) finalize(c->partials, 0, 1, 0, c->scal, FIN_SCALE, 0.0, c->st);
-    int64_t nb = launch_residual64(c->g0, c64, c->f, x, r32 ? nullptr : c->r, r32, c->scal,
-                                   c->partials, c->st);
+    int64_t nb;
+    {
+        const double n = (double)c->N;
+        ProfScope ps(c, PARIS_K_RESID64, (16 * n + 8 * beta_count(c->g0)) + (r32 ? 4 : 8) * n);
+        nb = launch_residual64(c->g0, c64, c->f, x, r32 ? nullptr : c->r, r32, c->scal, c->partials,
+                               c->st);
+    }
     finalize(c->partials, nb, 3, 2, c->scal, FIN_RNORMS, 0.0, c->st);
     CK(cudaGetLastError());
     return read_scal(c);
@@ -369,7 +443,10 @@ paris_status solve_fp64(paris_ctx* c, const Coef<double>& c64, double* x, SolveO
         CK(cudaMemcpyAsync(c->d, c->z, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->st));
         bool conv = false;
         while (out.iters < max_iter) {
-            nb = launch_matvec_dot<double>(c->g0, c64, c->d, c->q, c->partials, c->st);
+            {
+                ProfScope ps(c, PARIS_K_MATVEC0, (2.0 * N + beta_count(c->g0)) * 8);
+                nb = launch_matvec_dot<double>(c->g0, c64, c->d, c->q, c->partials, c->st);
+            }
             finalize(c->partials, nb, 1, 0, c->scal, FIN_ALPHA, 0.0, c->st);
             nb = launch_update_xr<double>(N, c->scal, c->d, c->q, x, c->r, c->partials, c->st);
             finalize(c->partials, nb, 3, 2, c->scal, FIN_RNORMS, 0.0, c->st);
@@ -427,7 +504,10 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
         finalize(c->partials, nb, 2, 0, c->scal, FIN_RHO_INIT, 0.0, c->st);
         CK(cudaMemcpyAsync(c->d32, c->z32, sizeof(float) * N, cudaMemcpyDeviceToDevice, c->st));
         for (int j = 0; j < 50 && out.iters < max_iter; ++j) {
-            nb = launch_matvec_dot<float>(c->g0, c32, c->d32, c->q32, c->partials, c->st);
+            {
+                ProfScope ps(c, PARIS_K_MATVEC0, (2.0 * N + beta_count(c->g0)) * 4);
+                nb = launch_matvec_dot<float>(c->g0, c32, c->d32, c->q32, c->partials, c->st);
+            }
             finalize(c->partials, nb, 1, 0, c->scal, FIN_ALPHA, 0.0, c->st);
             nb = launch_update_xr<float>(N, c->scal, c->d32, c->q32, c->e32, c->r32, c->partials, c->st);
             finalize(c->partials, nb, 3, 2, c->scal, FIN_STORE, 0.0, c->st);
@@ -469,7 +549,7 @@ void paris_default_opts(paris_opts* o) {
     o->nu1 = 2;
     o->nu2 = 2;
     o->omega = 1.15;
-    o->smoother = PARIS_SMOOTH_RBGS;
+    o->smoother = PARIS_SMOOTH_RBGS_2PASS;
     o->coarse_max_cells = 64;
     o->inner_tol = 1e-5;
     o->fallback = 1;
@@ -517,6 +597,7 @@ paris_status paris_destroy(paris_ctx* c) {
     cudaStreamSynchronize(c->st);
     c->mem.release();
     if (c->scal_h) cudaFreeHost(c->scal_h);
+    for (auto& e : c->prof.ev) cudaEventDestroy(e);
     delete c;
     return PARIS_OK;
 }
@@ -536,6 +617,45 @@ paris_status paris_set_opts(paris_ctx* c, const paris_opts* o) {
     c->opts = *o;
     return PARIS_OK;
 }
+
+paris_status paris_profile(paris_ctx* c, int enable) {
+    if (!c) return PARIS_ERR_INVALID_ARG;
+    Profiler& P = c->prof;
+    if (enable && P.ev.empty()) {
+        P.ev.resize(2 * kProfPool);
+        for (auto& e : P.ev) CK(cudaEventCreate(&e));
+        P.slot_cls.resize(kProfPool);
+        P.slot_bytes.resize(kProfPool);
+    }
+    if (enable) {
+        CK(cudaStreamSynchronize(c->st));
+        P.used = 0;
+        for (int k = 0; k < PARIS_K_COUNT; ++k) P.launches[k] = 0;
+    }
+    P.on = enable != 0;
+    return PARIS_OK;
+}
+
+paris_status paris_profile_read(paris_ctx* c, int cls, paris_kernel_prof* out) {
+    if (!c || !out || cls < 0 || cls >= PARIS_K_COUNT) return PARIS_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(c->st));
+    Profiler& P = c->prof;
+    out->launches = P.launches[cls];
+    out->timed = 0;
+    out->ms = 0.0;
+    out->bytes = 0.0;
+    for (int s = 0; s < P.used; ++s) {
+        if (P.slot_cls[s] != cls) continue;
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, P.ev[2 * s], P.ev[2 * s + 1]));
+        out->timed += 1;
+        out->ms += ms;
+        out->bytes += P.slot_bytes[s];
+    }
+    return PARIS_OK;
+}
+
+int64_t paris_launch_count(void) { return (int64_t)launch_count(); }
 
 int64_t paris_face_count(const paris_ctx* c, int axis) {
     if (!c || axis < 0 || axis > 2) return -1;

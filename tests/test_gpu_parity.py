@@ -138,3 +138,42 @@ def test_drops_walls_64(paris, precision):
         st = ctx.projection_step(dev(pr.C), pr.rho1, pr.rho2, pr.dt, u, v, w, p)
         assert st["iters"] <= 30, st
         _check_solution(g, pr, ref, host(p), (host(u), host(v), host(w)), st)
+
+
+# every smoothed multigrid level has even periodic axes (walls may be odd)
+EVEN_GRIDS = [GRIDS[0], pi.Grid(64, 32, 16, 1 / 64, (P, P, W)), pi.Grid(24, 24, 24, 1 / 24),
+              pi.Grid(20, 12, 8, 0.05, (W, W, P)), pi.Grid(13, 7, 9, 0.1, (W, W, W))]
+
+
+@pytest.mark.parametrize("precision", ["FP64", "MIXED"])
+@pytest.mark.parametrize("grid", EVEN_GRIDS, ids=lambda g: f"{g.nx}x{g.ny}x{g.nz}")
+def test_fused_smoother_bit_identical_to_two_pass(paris, grid, precision):
+    """The fused red-black sweep does the same arithmetic in the same order as
+    two in-place colour passes: the whole solve is bit-identical (periodic
+    axes of even length on every smoothed level, where red-black is a true
+    two-colouring)."""
+    pr = pi.random_problem(grid, seed=8, rho1=1000.0)
+    beta = oracle.face_coeffs(grid, pr.C, pr.rho1, pr.rho2)
+    b = oracle.divergence(grid, pr.u, pr.v, pr.w, pr.dt)
+    out = []
+    for sm in (paris.SMOOTH_RBGS, paris.SMOOTH_RBGS_2PASS):
+        with ctx_for(paris, grid, precision=getattr(paris, precision), smoother=sm) as ctx:
+            p = torch.zeros(grid.shape, dtype=torch.float64, device="cuda")
+            st = ctx.poisson_solve(*(dev(x) for x in beta), dev(b), p)
+            out.append((host(p), st["iters"]))
+    assert out[0][1] == out[1][1]
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+
+
+@pytest.mark.parametrize("precision", ["FP64", "MIXED"])
+@pytest.mark.parametrize("grid", GRIDS[:4], ids=GID[:4])
+def test_jacobi_smoother_matches_oracle(paris, grid, precision):
+    """The paper's GPU iteration (damped Jacobi) as the V-cycle smoother."""
+    pr = pi.random_problem(grid, seed=9, rho1=100.0)
+    ref = oracle.projection_step(grid, pr.C, pr.rho1, pr.rho2, pr.dt, pr.u, pr.v, pr.w)
+    with ctx_for(paris, grid, precision=getattr(paris, precision), smoother=paris.SMOOTH_JACOBI,
+                 omega=0.8, max_iter=400) as ctx:
+        u, v, w = dev(pr.u), dev(pr.v), dev(pr.w)
+        p = torch.zeros(grid.shape, dtype=torch.float64, device="cuda")
+        st = ctx.projection_step(dev(pr.C), pr.rho1, pr.rho2, pr.dt, u, v, w, p)
+        _check_solution(grid, pr, ref, host(p), (host(u), host(v), host(w)), st)
