@@ -141,6 +141,28 @@ paris_status paris_face_coeffs(paris_ctx* ctx, const double* C, double rho1, dou
 paris_status paris_divergence(paris_ctx* ctx, const double* u, const double* v, const double* w,
                               double dt, double* rhs, double* mean_removed);
 
+/* Step 2 without a context, for callers that cannot allocate device memory
+ * (for example a solver embedded in an application whose own allocator owns
+ * all device memory, or a time loop held to a fixed memory budget).  The
+ * paper has no counterpart: this is an interface variant of paris_divergence
+ * with the same result.  g describes the grid; u, v, w (face arrays), rhs
+ * (cells, output) and mean_removed (one double, output, may be NULL) are
+ * DEVICE pointers owned by the caller; work is enqueued on `stream` and the
+ * call returns without synchronising.  No device memory is allocated: the
+ * block partial sums live in one static device array of 384 KB (16384 blocks
+ * of 32x8x8 cells) that every GPU loading the library holds until the process
+ * exits.  Grids needing more blocks than that (beyond 512x256x256 cells, i.e.
+ * ceil(nx/32)*ceil(ny/8)*ceil(nz/8) > 16384) are rejected with
+ * PARIS_ERR_INVALID_ARG before any work is enqueued.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  Every call
+ * overwrites the whole scratch it reads, so nothing needs clearing, but all
+ * calls share the one array: calls that overlap on the GPU (other streams,
+ * other threads) race and must be serialised by the caller. */
+paris_status paris_divergence_noalloc(const paris_grid* g, const double* u, const double* v,
+                                      const double* w, double dt, double* rhs,
+                                      double* mean_removed, void* stream);
+
 /* Step 3 -- Eq. poisson with tau folded into b: solve
  *   sum_f beta_f (p_nb - p_c)/h^2 = rhs_c
  * (the paper's A1..A7 form of Sec. 3.7.1 divided by -tau) for p with

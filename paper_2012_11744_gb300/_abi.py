@@ -71,6 +71,7 @@ SIGNATURES = {
     "paris_set_opts": (ct.c_int, [_P, ct.POINTER(Opts)]),
     "paris_face_coeffs": (ct.c_int, [_P, _P, _D, _D, _P, _P, _P]),
     "paris_divergence": (ct.c_int, [_P, _P, _P, _P, _D, _P, ct.POINTER(_D)]),
+    "paris_divergence_noalloc": (ct.c_int, [ct.POINTER(Grid), _P, _P, _P, _D, _P, _P, _P]),
     "paris_poisson_solve": (ct.c_int, [_P, _P, _P, _P, _P, _P, ct.POINTER(Stats)]),
     "paris_project": (ct.c_int, [_P, _P, _P, _P, _P, _D, _P, _P, _P]),
     "paris_projection_step": (ct.c_int, [_P, _P, _D, _D, _D, _P, _P, _P, _P, ct.POINTER(Stats)]),
