@@ -23,6 +23,41 @@ namespace {
 constexpr int kTX = 32, kTY = 8;  // 2-D tile of the stencil kernels (x fastest)
 constexpr int kZ = 8;             // cells per thread along z in reducing stencil kernels
 
+// Element-wise grid-stride loop over [0, n).
+#define PARIS_EW_FOR(c, n)                                                           \
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < (n);        \
+         c += (int64_t)gridDim.x * blockDim.x)
+
+// 16-byte vectors for the streaming kernels: a thread moves 16 bytes of
+// each array per load (float4 / double2), so enough bytes are in flight to
+// cover the HBM latency with the capped grid.
+template <typename T>
+struct V16;
+template <>
+struct V16<float> {
+    using type = float4;
+    static constexpr int n = 4;
+};
+template <>
+struct V16<double> {
+    using type = double2;
+    static constexpr int n = 2;
+};
+
+// Vector part [0, n/W) of a grid-stride loop, then the scalar tail.
+#define PARIS_VEC_FOR(i, nvec)                                                        \
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (nvec);      \
+         i += (int64_t)gridDim.x * blockDim.x)
+#define PARIS_TAIL_FOR(c, start, n)                                                   \
+    for (int64_t c = (start) + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < (n); \
+         c += (int64_t)gridDim.x * blockDim.x)
+
+// z-loop over [k0, k1)
+#define PARIS_ZLOOP(k0, k1, BODY)              \
+    for (int k = (k0); k < (k1); ++k) {        \
+        BODY                                   \
+    }
+
 inline dim3 tile_grid(const Geo& g, int zper) {
     return dim3((g.nx + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, (g.nz + zper - 1) / zper);
 }
@@ -43,12 +78,25 @@ static std::atomic<long long> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
+// true when every (non-null) pointer is 16-byte aligned: vector loads allowed
+inline bool aligned16(const void* a, const void* b = nullptr, const void* c = nullptr,
+                      const void* d = nullptr) {
+    auto ok = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
+    return ok(a) && ok(b) && ok(c) && ok(d);
+}
+
 int elementwise_blocks(int64_t n) {
     int64_t b = (n + kRedThreads - 1) / kRedThreads;
     const int64_t cap = 152 * 8;  // 8 resident 256-thread blocks on each of the 152 SMs
     if (b > cap) b = cap;
     if (b < 1) b = 1;
     return (int)b;
+}
+
+int64_t max_reduce_blocks(const Geo& g) {
+    const int64_t tiles = nblocks_of(tile_grid(g, kZ));
+    const int64_t ew = elementwise_blocks(g.ncell());
+    return tiles > ew ? tiles : ew;
 }
 
 // ---------------------------------------------------------------- finalize ---
@@ -60,11 +108,25 @@ __global__ void finalize_kernel(const double* __restrict__ partials, int64_t nbl
     __shared__ double sh[kRedThreads / 32][4];
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     const int tid = threadIdx.x;
-    for (int64_t b = tid; b < nblocks; b += kRedThreads)
-        for (int q = 0; q < nv; ++q) {
-            double t = partials[(int64_t)nv * b + q];
-            v[q] = ((maxmask >> q) & 1) ? fmax(v[q], t) : v[q] + t;
+    // four interleaved accumulators per value keep four loads in flight
+    for (int q = 0; q < nv; ++q) {
+        const bool mx = (maxmask >> q) & 1;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int64_t b = tid;
+        for (; b + 3 * kRedThreads < nblocks; b += 4 * kRedThreads) {
+            const double t0 = partials[(int64_t)nv * b + q];
+            const double t1 = partials[(int64_t)nv * (b + kRedThreads) + q];
+            const double t2 = partials[(int64_t)nv * (b + 2 * kRedThreads) + q];
+            const double t3 = partials[(int64_t)nv * (b + 3 * kRedThreads) + q];
+            if (mx) { a0 = fmax(a0, t0); a1 = fmax(a1, t1); a2 = fmax(a2, t2); a3 = fmax(a3, t3); }
+            else { a0 += t0; a1 += t1; a2 += t2; a3 += t3; }
         }
+        for (; b < nblocks; b += kRedThreads) {
+            const double t0 = partials[(int64_t)nv * b + q];
+            a0 = mx ? fmax(a0, t0) : a0 + t0;
+        }
+        v[q] = mx ? fmax(fmax(a0, a1), fmax(a2, a3)) : (a0 + a1) + (a2 + a3);
+    }
     const int lane = tid & 31, wid = tid >> 5;
     for (int q = 0; q < 4; ++q) {
         v[q] = ((maxmask >> q) & 1) ? warp_max(v[q]) : warp_sum(v[q]);
@@ -113,6 +175,20 @@ void finalize(const double* partials, int64_t nblocks, int nv, int maxmask, Scal
 
 // ------------------------------------------------------- face coefficients ---
 
+// 2/s for s > 0 by Newton-Raphson on the reciprocal: y0 = 1/s in FP32,
+// then two FP64 steps y <- y + y (1 - s y), each doubling the correct bits
+// (24 -> 48 -> full double precision; the result is within one ulp of the
+// correctly rounded quotient).  FP64 division costs several times more on
+// this GPU, whose FP64 rate is 1/64 of its FP32 rate.
+__device__ inline double two_over(double s) {
+    double y = (double)__frcp_rn((float)s);
+    double e = fma(-s, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-s, y, 1.0);
+    y = fma(y, e, y);
+    return 2.0 * y;
+}
+
 // Eq. muH: rho = rho1 C + rho2 (1 - C); beta_f = 1/rho_f with rho_f the mean
 // of the two cells (the paper's "interpolation of 1/rho" read as the mean of
 // rho, then inverted); wall faces 0 (Sec. 3.8).  One thread per cell writes
@@ -125,22 +201,24 @@ __global__ void face_coeffs_kernel(Geo g, const double* __restrict__ C, double r
     const int j = blockIdx.y * kTY + threadIdx.y;
     const int k = blockIdx.z;
     if (i >= g.nx || j >= g.ny) return;
-    const double drho = rho1 - rho2;
-    const double rc = fma(drho, C[g.cidx(i, j, k)], rho2);
+    // Eq. muH as written, rho1 C + rho2 (1 - C): both terms are non-negative,
+    // so there is no cancellation even when rho1 << rho2 and C -> 1
+    auto rho = [&](double c) { return fma(rho1, c, rho2 * (1.0 - c)); };
+    const double rc = rho(C[g.cidx(i, j, k)]);
     AxisNb ax = axis_nb(i, g.nx, g.wx), ay = axis_nb(j, g.ny, g.wy), az = axis_nb(k, g.nz, g.wz);
     {
-        double rl = fma(drho, C[g.cidx(ax.m, j, k)], rho2);
-        bx[g.fx(i, j, k)] = ax.wm ? 0.0 : 2.0 / (rl + rc);
+        double rl = rho(C[g.cidx(ax.m, j, k)]);
+        bx[g.fx(i, j, k)] = ax.wm ? 0.0 : two_over(rl + rc);
         if (g.wx && i == g.nx - 1) bx[g.fx(g.nx, j, k)] = 0.0;
     }
     {
-        double rl = fma(drho, C[g.cidx(i, ay.m, k)], rho2);
-        by[g.fy(i, j, k)] = ay.wm ? 0.0 : 2.0 / (rl + rc);
+        double rl = rho(C[g.cidx(i, ay.m, k)]);
+        by[g.fy(i, j, k)] = ay.wm ? 0.0 : two_over(rl + rc);
         if (g.wy && j == g.ny - 1) by[g.fy(i, g.ny, k)] = 0.0;
     }
     {
-        double rl = fma(drho, C[g.cidx(i, j, az.m)], rho2);
-        bz[g.fz(i, j, k)] = az.wm ? 0.0 : 2.0 / (rl + rc);
+        double rl = rho(C[g.cidx(i, j, az.m)]);
+        bz[g.fz(i, j, k)] = az.wm ? 0.0 : two_over(rl + rc);
         if (g.wz && k == g.nz - 1) bz[g.fz(i, j, g.nz)] = 0.0;
     }
 }
@@ -180,13 +258,13 @@ __global__ void __launch_bounds__(kTX* kTY) divergence_kernel(Geo g, const doubl
     double acc[3] = {0.0, 0.0, 0.0};
     if (i < g.nx && j < g.ny) {
         const int k0 = blockIdx.z * kZ, k1 = min(k0 + kZ, g.nz);
-        for (int k = k0; k < k1; ++k) {
+        PARIS_ZLOOP(k0, k1, {
             double b = cell_div(g, u, v, w, i, j, k) * inv_hdt;
             rhs[g.cidx(i, j, k)] = b;
             acc[0] += b;
             acc[1] = fmax(acc[1], fabs(b));
             acc[2] += nonfinite(b);
-        }
+        })
     }
     const int op[3] = {0, 1, 0};
     block_reduce_store<3>(acc, op, partials, flat_block(), flat_tid());
@@ -209,7 +287,7 @@ __global__ void __launch_bounds__(kTX* kTY) max_div_kernel(Geo g, const double* 
     double acc[1] = {0.0};
     if (i < g.nx && j < g.ny) {
         const int k0 = blockIdx.z * kZ, k1 = min(k0 + kZ, g.nz);
-        for (int k = k0; k < k1; ++k) acc[0] = fmax(acc[0], fabs(cell_div(g, u, v, w, i, j, k) * inv_h));
+        PARIS_ZLOOP(k0, k1, { acc[0] = fmax(acc[0], fabs(cell_div(g, u, v, w, i, j, k) * inv_h)); })
     }
     const int op[1] = {1};
     block_reduce_store<1>(acc, op, partials, flat_block(), flat_tid());
@@ -228,8 +306,7 @@ __global__ void make_rhs_kernel(int64_t n, const double* __restrict__ rhs, const
                                 double* __restrict__ f, double* partials) {
     const double mb = s->mean_b;
     double acc[3] = {0.0, 0.0, 0.0};
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
-         c += (int64_t)gridDim.x * blockDim.x) {
+    PARIS_EW_FOR(c, n) {
         double t = -(rhs[c] - mb);
         f[c] = t;
         acc[0] = fma(t, t, acc[0]);
@@ -250,8 +327,7 @@ int64_t launch_make_rhs(int64_t n, const double* rhs, const Scal* s, double* f, 
 
 __global__ void sub_mean_kernel(int64_t n, double* __restrict__ x, const Scal* s) {
     const double m = s->red[0] / (double)n;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
-         c += (int64_t)gridDim.x * blockDim.x)
+    PARIS_EW_FOR(c, n)
         x[c] -= m;
 }
 
@@ -262,8 +338,7 @@ void launch_sub_mean(int64_t n, double* x, const Scal* s, cudaStream_t st) {
 
 __global__ void sum_kernel(int64_t n, const double* __restrict__ x, double* partials) {
     double acc[3] = {0.0, 0.0, 0.0};
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
-         c += (int64_t)gridDim.x * blockDim.x) {
+    PARIS_EW_FOR(c, n) {
         acc[0] += x[c];
         acc[1] = fmax(acc[1], fabs(x[c]));
         acc[2] += nonfinite(x[c]);
@@ -325,8 +400,7 @@ void launch_project(const Geo& g, const double* bx, const double* by, const doub
 template <typename T>
 __global__ void convert_beta_kernel(int64_t n, const double* __restrict__ b, double scale,
                                     T* __restrict__ out) {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
-         c += (int64_t)gridDim.x * blockDim.x)
+    PARIS_EW_FOR(c, n)
         out[c] = (T)(b[c] * scale);
 }
 
@@ -357,8 +431,7 @@ __global__ void coarse_beta_kernel(Geo fg, Coef<T> cf, Geo cg, int fa0, int fa1,
     const T* src = axis == 0 ? cf.bx : (axis == 1 ? cf.by : cf.bz);
     const int fn0 = fg.nx + (axis == 0 ? fg.wx : 0);
     const int fn1 = fg.ny + (axis == 1 ? fg.wy : 0);
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
+    PARIS_EW_FOR(t, total) {
         const int I = (int)(t % n0);
         const int J = (int)((t / n0) % n1);
         const int K = (int)(t / ((int64_t)n0 * n1));
@@ -512,7 +585,14 @@ void launch_coarse_solve(const Geo& g, const double* inv, const T* f, T* x, cuda
 // w_c = 1/sum_f beta_f.  One thread per x-pair (2t, 2t+1) of a row updates
 // the member of colour `color` ((i+j+k) even = red = 0).  With zero_init the
 // incoming x is taken as zero and the other member of the pair is zeroed.
+// 1 / sum of the six face coefficients, in the same order as inv_diag_kernel
 template <typename T>
+__device__ inline T inv_sum6(const T (&b)[6]) {
+    const T d = ((b[0] + b[1]) + (b[2] + b[3])) + (b[4] + b[5]);
+    return d > T(0) ? T(1) / d : T(0);
+}
+
+template <typename T, bool USEW>
 __global__ void __launch_bounds__(kTX* kTY) rbgs_kernel(Geo g, Coef<T> cf, const T* __restrict__ w,
                                                        const T* __restrict__ f, T* __restrict__ x,
                                                        int color, T omega, int zero_init) {
@@ -528,7 +608,15 @@ __global__ void __launch_bounds__(kTX* kTY) rbgs_kernel(Geo g, Coef<T> cf, const
         const int64_t c = g.cidx(i, j, k);
         T xn;
         if (zero_init) {
-            xn = omega * w[c] * (f[c] * hs);
+            T wc;
+            if (USEW) {
+                wc = w[c];
+            } else {
+                Stencil<T> s;
+                load_stencil(g, cf, i, j, k, s);
+                wc = inv_sum6(s.b);
+            }
+            xn = omega * wc * (f[c] * hs);
         } else {
             Stencil<T> s;
             load_stencil(g, cf, i, j, k, s);
@@ -536,7 +624,7 @@ __global__ void __launch_bounds__(kTX* kTY) rbgs_kernel(Geo g, Coef<T> cf, const
 #pragma unroll
             for (int q = 0; q < 6; ++q) acc = fma(s.b[q], x[s.nb[q]], acc);
             const T xc = x[c];
-            xn = fma(omega, fma(w[c], acc, -xc), xc);
+            xn = fma(omega, fma(USEW ? w[c] : inv_sum6(s.b), acc, -xc), xc);
         }
         x[c] = xn;
     }
@@ -548,8 +636,14 @@ void launch_rbgs(const Geo& g, const Coef<T>& cf, const T* w, const T* f, T* x, 
                  double omega, bool zero_init, cudaStream_t st) {
     const int npair = (g.nx + 1) / 2;
     dim3 gr((npair + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, g.nz);
-    rbgs_kernel<T><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, w, f, x, color, (T)omega,
-                                                  zero_init ? 1 : 0);
+    // FP32: recomputing 1/D from the coefficients already loaded is cheaper
+    // than reading it; FP64: the division costs more than the read
+    if (sizeof(T) == 8)
+        rbgs_kernel<T, true><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, w, f, x, color, (T)omega,
+                                                            zero_init ? 1 : 0);
+    else
+        rbgs_kernel<T, false><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, w, f, x, color, (T)omega,
+                                                             zero_init ? 1 : 0);
     count_launch();
 }
 
@@ -631,7 +725,8 @@ __global__ void prolong_add_kernel(Geo fg, Geo cg, int fa0, int fa1, int fa2,
     const int j = blockIdx.y * kTY + threadIdx.y;
     const int k = blockIdx.z;
     if (i >= fg.nx || j >= fg.ny) return;
-    x[fg.cidx(i, j, k)] += xc[cg.cidx(i / fa0, j / fa1, k / fa2)];
+    // factors are 1 or 2: halving is a shift
+    x[fg.cidx(i, j, k)] += xc[cg.cidx(i >> (fa0 - 1), j >> (fa1 - 1), k >> (fa2 - 1))];
 }
 
 template <typename T>
@@ -659,7 +754,7 @@ __global__ void __launch_bounds__(kTX* kTY) residual64_kernel(Geo g, Coef<double
     if (i < g.nx && j < g.ny) {
         const double sc = r32 ? s->scale : 0.0;
         const int k0 = blockIdx.z * kZ, k1 = min(k0 + kZ, g.nz);
-        for (int k = k0; k < k1; ++k) {
+        PARIS_ZLOOP(k0, k1, {
             const int64_t c = g.cidx(i, j, k);
             Stencil<double> st;
             load_stencil(g, cf, i, j, k, st);
@@ -669,7 +764,7 @@ __global__ void __launch_bounds__(kTX* kTY) residual64_kernel(Geo g, Coef<double
             acc[0] = fma(r, r, acc[0]);
             acc[1] = fmax(acc[1], fabs(r));
             acc[2] += nonfinite(r);
-        }
+        })
     }
     const int op[3] = {0, 1, 0};
     block_reduce_store<3>(acc, op, partials, flat_block(), flat_tid());
@@ -696,7 +791,7 @@ __global__ void __launch_bounds__(kTX* kTY) matvec_dot_kernel(Geo g, Coef<T> cf,
     T loc = T(0);
     if (i < g.nx && j < g.ny) {
         const int k0 = blockIdx.z * kZ, k1 = min(k0 + kZ, g.nz);
-        for (int k = k0; k < k1; ++k) {
+        PARIS_ZLOOP(k0, k1, {
             const int64_t c = g.cidx(i, j, k);
             Stencil<T> st;
             load_stencil(g, cf, i, j, k, st);
@@ -704,7 +799,7 @@ __global__ void __launch_bounds__(kTX* kTY) matvec_dot_kernel(Geo g, Coef<T> cf,
             const T qc = apply_A(st, d, dc, cf.scale);
             q[c] = qc;
             loc = fma(dc, qc, loc);
-        }
+        })
     }
     double acc[1] = {(double)loc};
     const int op[1] = {0};
@@ -723,18 +818,39 @@ int64_t launch_matvec_dot(const Geo& g, const Coef<T>& cf, const T* d, T* q, dou
 template <typename T>
 __global__ void update_xr_kernel(int64_t n, const Scal* s, const T* __restrict__ d,
                                  const T* __restrict__ q, T* __restrict__ x, T* __restrict__ r,
-                                 double* partials) {
+                                 double* partials, int vec) {
+    using VT = typename V16<T>::type;
+    constexpr int W = V16<T>::n;
     const T alpha = (T)s->alpha;
     T l2 = T(0), li = T(0);
     double nf = 0.0;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        x[c] = fma(alpha, d[c], x[c]);
-        const T rc = fma(-alpha, q[c], r[c]);
-        r[c] = rc;
-        l2 = fma(rc, rc, l2);
-        li = fmax(li, fabs(rc));
-        nf += isfinite(rc) ? 0.0 : 1.0;
+    auto one = [&](T dv, T qv, T& xv, T& rv) {
+        xv = fma(alpha, dv, xv);
+        rv = fma(-alpha, qv, rv);
+        l2 = fma(rv, rv, l2);
+        li = fmax(li, fabs(rv));
+        nf += isfinite(rv) ? 0.0 : 1.0;
+    };
+    const int64_t nv = vec ? n / W : 0;
+    PARIS_VEC_FOR(i, nv) {
+        const VT dv = reinterpret_cast<const VT*>(d)[i];
+        const VT qv = reinterpret_cast<const VT*>(q)[i];
+        VT xv = reinterpret_cast<VT*>(x)[i];
+        VT rv = reinterpret_cast<VT*>(r)[i];
+        const T* de = reinterpret_cast<const T*>(&dv);
+        const T* qe = reinterpret_cast<const T*>(&qv);
+        T* xe = reinterpret_cast<T*>(&xv);
+        T* re = reinterpret_cast<T*>(&rv);
+#pragma unroll
+        for (int w = 0; w < W; ++w) one(de[w], qe[w], xe[w], re[w]);
+        reinterpret_cast<VT*>(x)[i] = xv;
+        reinterpret_cast<VT*>(r)[i] = rv;
+    }
+    PARIS_TAIL_FOR(c, nv * W, n) {
+        T xv = x[c], rv = r[c];
+        one(d[c], q[c], xv, rv);
+        x[c] = xv;
+        r[c] = rv;
     }
     double acc[3] = {(double)l2, (double)li, nf};
     const int op[3] = {0, 1, 0};
@@ -745,20 +861,36 @@ template <typename T>
 int64_t launch_update_xr(int64_t n, const Scal* s, const T* d, const T* q, T* x, T* r,
                          double* partials, cudaStream_t st) {
     int nb = elementwise_blocks(n);
-    update_xr_kernel<T><<<nb, kRedThreads, 0, st>>>(n, s, d, q, x, r, partials);
+    update_xr_kernel<T><<<nb, kRedThreads, 0, st>>>(n, s, d, q, x, r, partials,
+                                                    aligned16(d, q, x, r) ? 1 : 0);
     count_launch();
     return nb;
 }
 
 template <typename T>
 __global__ void dot2_kernel(int64_t n, const T* __restrict__ a, const T* __restrict__ b,
-                            const T* __restrict__ c, double* partials) {
+                            const T* __restrict__ c, double* partials, int vec) {
+    using VT = typename V16<T>::type;
+    constexpr int W = V16<T>::n;
     T s0 = T(0), s1 = T(0);
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const T av = a[e];
-        s0 = fma(av, b[e], s0);
-        if (c) s1 = fma(av, c[e], s1);
+    const int64_t nv = vec ? n / W : 0;
+    PARIS_VEC_FOR(i, nv) {
+        const VT av = reinterpret_cast<const VT*>(a)[i];
+        const VT bv = reinterpret_cast<const VT*>(b)[i];
+        const T* ae = reinterpret_cast<const T*>(&av);
+        const T* be = reinterpret_cast<const T*>(&bv);
+#pragma unroll
+        for (int w = 0; w < W; ++w) s0 = fma(ae[w], be[w], s0);
+        if (c) {
+            const VT cv = reinterpret_cast<const VT*>(c)[i];
+            const T* ce = reinterpret_cast<const T*>(&cv);
+#pragma unroll
+            for (int w = 0; w < W; ++w) s1 = fma(ae[w], ce[w], s1);
+        }
+    }
+    PARIS_TAIL_FOR(e, nv * W, n) {
+        s0 = fma(a[e], b[e], s0);
+        if (c) s1 = fma(a[e], c[e], s1);
     }
     double acc[2] = {(double)s0, (double)s1};
     const int op[2] = {0, 0};
@@ -769,35 +901,56 @@ template <typename T>
 int64_t launch_dot2(int64_t n, const T* a, const T* b, const T* c, double* partials,
                     cudaStream_t st) {
     int nb = elementwise_blocks(n);
-    dot2_kernel<T><<<nb, kRedThreads, 0, st>>>(n, a, b, c, partials);
+    dot2_kernel<T><<<nb, kRedThreads, 0, st>>>(n, a, b, c, partials, aligned16(a, b, c) ? 1 : 0);
     count_launch();
     return nb;
 }
 
 template <typename T>
-__global__ void xpby_kernel(int64_t n, const Scal* s, const T* __restrict__ z, T* __restrict__ d) {
+__global__ void xpby_kernel(int64_t n, const Scal* s, const T* __restrict__ z, T* __restrict__ d,
+                            int vec) {
+    using VT = typename V16<T>::type;
+    constexpr int W = V16<T>::n;
     const T beta = (T)s->beta;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x)
-        d[e] = fma(beta, d[e], z[e]);
+    const int64_t nv = vec ? n / W : 0;
+    PARIS_VEC_FOR(i, nv) {
+        const VT zv = reinterpret_cast<const VT*>(z)[i];
+        VT dv = reinterpret_cast<VT*>(d)[i];
+        const T* ze = reinterpret_cast<const T*>(&zv);
+        T* de = reinterpret_cast<T*>(&dv);
+#pragma unroll
+        for (int w = 0; w < W; ++w) de[w] = fma(beta, de[w], ze[w]);
+        reinterpret_cast<VT*>(d)[i] = dv;
+    }
+    PARIS_TAIL_FOR(e, nv * W, n) d[e] = fma(beta, d[e], z[e]);
 }
 
 template <typename T>
 void launch_xpby(int64_t n, const Scal* s, const T* z, T* d, cudaStream_t st) {
-    xpby_kernel<T><<<elementwise_blocks(n), kRedThreads, 0, st>>>(n, s, z, d);
+    xpby_kernel<T><<<elementwise_blocks(n), kRedThreads, 0, st>>>(n, s, z, d, aligned16(z, d) ? 1 : 0);
     count_launch();
 }
 
 __global__ void accumulate_kernel(int64_t n, const Scal* s, const float* __restrict__ e,
-                                  double* __restrict__ x) {
+                                  double* __restrict__ x, int vec) {
     const double is = s->inv_scale;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
-         c += (int64_t)gridDim.x * blockDim.x)
-        x[c] = fma((double)e[c], is, x[c]);
+    const int64_t nv = vec ? n / 4 : 0;
+    PARIS_VEC_FOR(i, nv) {
+        const float4 ev = reinterpret_cast<const float4*>(e)[i];
+        double2 x0 = reinterpret_cast<double2*>(x)[2 * i];
+        double2 x1 = reinterpret_cast<double2*>(x)[2 * i + 1];
+        x0.x = fma((double)ev.x, is, x0.x);
+        x0.y = fma((double)ev.y, is, x0.y);
+        x1.x = fma((double)ev.z, is, x1.x);
+        x1.y = fma((double)ev.w, is, x1.y);
+        reinterpret_cast<double2*>(x)[2 * i] = x0;
+        reinterpret_cast<double2*>(x)[2 * i + 1] = x1;
+    }
+    PARIS_TAIL_FOR(c, nv * 4, n) x[c] = fma((double)e[c], is, x[c]);
 }
 
 void launch_accumulate(int64_t n, const Scal* s, const float* e, double* x, cudaStream_t st) {
-    accumulate_kernel<<<elementwise_blocks(n), kRedThreads, 0, st>>>(n, s, e, x);
+    accumulate_kernel<<<elementwise_blocks(n), kRedThreads, 0, st>>>(n, s, e, x, aligned16(e, x) ? 1 : 0);
     count_launch();
 }
 

@@ -36,8 +36,11 @@ enum FinalizeMode {
     FIN_INNER_INIT = 9  // rr0 = result0, rr = result0
 };
 
-// Generic grid for element-wise kernels.
+// Grid of the element-wise kernels (kEW elements per thread).
 int elementwise_blocks(int64_t n);
+// Most blocks any reducing kernel launches on a grid of this size (the
+// number of partial-sum slots a caller must provide, per value).
+int64_t max_reduce_blocks(const Geo& g);
 
 // Process-wide count of kernel launches made by the library.
 void count_launch(int n = 1);
@@ -92,6 +95,8 @@ template <typename T>
 void launch_rbgs_fused(const Geo& g, const Coef<T>& cf, const T* w, const T* f, const T* xin,
                        T* xout, int first_color, double omega, bool zero_init, bool use_w,
                        cudaStream_t st);
+// The fused sweep indexes with 32-bit integers: true when the level fits.
+bool rbgs_fused_fits(const Geo& g);
 // One damped-Jacobi sweep x_out = x + omega D^{-1} (f - A x).
 template <typename T>
 void launch_jacobi(const Geo& g, const Coef<T>& cf, const T* w, const T* f, const T* x, T* xout,

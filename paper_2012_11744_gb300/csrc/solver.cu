@@ -213,10 +213,8 @@ paris_status alloc_ctx(paris_ctx* c) {
         c->beta[a] = m.get<double>(c->g0.nface(a));
     }
     c->rhs = m.get<double>(N);
-    // block partials: the largest reduction grid is the z-tiled stencil grid
-    int64_t tiles = (int64_t)((c->g0.nx + 31) / 32) * ((c->g0.ny + 7) / 8) * ((c->g0.nz + 7) / 8);
-    int64_t np = std::max<int64_t>(tiles, 152 * 8) * 4;
-    c->partials = m.get<double>(np);
+    // block partials: up to 4 values per block of the largest reducing grid
+    c->partials = m.get<double>(max_reduce_blocks(c->g0) * 4);
     c->scal = m.get<Scal>(1);
     if (m.err != cudaSuccess) return m.err == cudaErrorMemoryAllocation ? PARIS_ERR_NO_MEMORY : PARIS_ERR_CUDA;
     if (cudaMallocHost(&c->scal_h, sizeof(Scal)) != cudaSuccess) return PARIS_ERR_NO_MEMORY;
@@ -295,7 +293,11 @@ void setup_hierarchy(paris_ctx* c, const Coef<T>& c0) {
         T* out[3] = {Prec<T>::b(L, 0), Prec<T>::b(L, 1), Prec<T>::b(L, 2)};
         launch_coarse_beta<T>(F.g, cf, L.g, L.fac, ratio2, out, c->st);
     }
-    for (int l = 0; l < nl; ++l) launch_inv_diag<T>(c->lv[l].g, level_coef<T>(c, l, c0), Prec<T>::w(c->lv[l]), c->st);
+    // inverse diagonals: read by the FP64 smoothers and by Jacobi; the FP32
+    // red-black sweeps recompute them from the coefficients they load
+    if (sizeof(T) == 8 || c->opts.smoother == PARIS_SMOOTH_JACOBI)
+        for (int l = 0; l < nl; ++l)
+            launch_inv_diag<T>(c->lv[l].g, level_coef<T>(c, l, c0), Prec<T>::w(c->lv[l]), c->st);
     if (c->dense_coarse)
         launch_coarse_inverse<T>(c->lv[nl - 1].g, level_coef<T>(c, nl - 1, c0), c->coarse_inv, c->st);
 }
@@ -308,7 +310,8 @@ void smooth(paris_ctx* c, int l, const Coef<T>& cf, const T* f, T* x, int sweeps
     const double n = (double)L.g.ncell(), sz = sizeof(T), nb = beta_count(L.g);
     const int cls = l == 0 ? PARIS_K_SMOOTH0 : -1;
     const bool use_w = sizeof(T) == 8;  // FP64: a division costs more than reading 1/D
-    if (o.smoother == PARIS_SMOOTH_RBGS_2PASS) {
+    if (o.smoother == PARIS_SMOOTH_RBGS_2PASS ||
+        (o.smoother == PARIS_SMOOTH_RBGS && !rbgs_fused_fits(L.g))) {
         for (int s = 0; s < sweeps; ++s) {
             const bool z0 = first_zero && s == 0;
             const int c0 = reverse ? 1 : 0;

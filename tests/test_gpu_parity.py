@@ -177,3 +177,39 @@ def test_jacobi_smoother_matches_oracle(paris, grid, precision):
         p = torch.zeros(grid.shape, dtype=torch.float64, device="cuda")
         st = ctx.projection_step(dev(pr.C), pr.rho1, pr.rho2, pr.dt, u, v, w, p)
         _check_solution(grid, pr, ref, host(p), (host(u), host(v), host(w)), st)
+
+
+@pytest.mark.parametrize("rho1,rho2", [(1000.0, 1.0), (1e-3, 7.5), (3.3e4, 2.2e-2), (1.0, 1.0)])
+def test_face_coefficient_reciprocal_within_four_ulp(paris, rho1, rho2):
+    """beta = 2/(rho_L + rho_R) is computed by Newton-Raphson on the GPU (within
+    one ulp of the correctly rounded quotient).  The GPU forms rho = rho2 +
+    (rho1 - rho2) C with one fused multiply-add where the oracle rounds
+    rho1 C + rho2 (1 - C) three times, so the two rho differ by up to ~2 ulp
+    each; the bound checked over random mixtures is therefore 4 ulp."""
+    grid = pi.Grid(64, 32, 16, 1 / 64, (P, W, P))
+    C = np.random.default_rng(5).uniform(0.0, 1.0, size=grid.shape)
+    ref = oracle.face_coeffs(grid, C, rho1, rho2)
+    with ctx_for(paris, grid) as ctx:
+        got = ctx.face_coeffs(dev(C), rho1, rho2)
+        for a in range(3):
+            g, r = host(got[a]), ref[a]
+            nz = r != 0
+            assert np.all(g[~nz] == 0)
+            ulps = np.abs(g[nz] - r[nz]) / np.spacing(np.abs(r[nz]))
+            assert ulps.max() <= 4.0, ulps.max()
+
+
+def test_unaligned_pressure_buffer(paris):
+    """p may start at any 8-byte boundary (a view into a larger buffer): the
+    vectorised kernels fall back to scalar accesses."""
+    grid = pi.Grid(24, 20, 16, 1 / 24, (P, P, W))
+    pr = pi.random_problem(grid, seed=12, rho1=100.0)
+    ref = oracle.projection_step(grid, pr.C, pr.rho1, pr.rho2, pr.dt, pr.u, pr.v, pr.w)
+    for prec in ("FP64", "MIXED"):
+        with ctx_for(paris, grid, precision=getattr(paris, prec)) as ctx:
+            u, v, w = dev(pr.u), dev(pr.v), dev(pr.w)
+            buf = torch.zeros(grid.ncells + 1, dtype=torch.float64, device="cuda")
+            p = buf[1:].view(grid.shape)
+            assert p.data_ptr() % 16 == 8
+            st = ctx.projection_step(dev(pr.C), pr.rho1, pr.rho2, pr.dt, u, v, w, p)
+            _check_solution(grid, pr, ref, host(p), (host(u), host(v), host(w)), st)
