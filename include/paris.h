@@ -199,6 +199,31 @@ paris_status paris_projection_step_host(paris_ctx* ctx, const double* C_host, do
                                         double rho2, double dt, double* u_host, double* v_host,
                                         double* w_host, double* p_host, paris_stats* st);
 
+/* Adjoint of steps 2-4 (the paper has no adjoint; derived from Eqs. fotm and
+ * poisson).  Given beta, the forward pressure p and g = dLoss/du on the faces
+ * (gu, gv, gw), solve the adjoint problem L q = D (B g) with the same operator
+ * and options as paris_poisson_solve (q: in = initial guess, out = mean-free
+ * adjoint pressure) and write, on every face,
+ *   gus   = dLoss/du*   = g - G q
+ *   gbeta = dLoss/dbeta = dt (G p) (G q - g)
+ * with (G x)_f = (x_R - x_L)/h; both are 0 on wall faces.  Face arrays in,
+ * face arrays out (device).  st (host, optional): stats of the adjoint solve.
+ * Errors: INVALID_ARG, NOT_CONVERGED (outputs still written), NONFINITE, CUDA. */
+paris_status paris_project_adjoint(paris_ctx* ctx, const double* beta_x, const double* beta_y,
+                                   const double* beta_z, const double* p, double dt,
+                                   const double* gu, const double* gv, const double* gw,
+                                   double* gus, double* gvs, double* gws, double* gbeta_x,
+                                   double* gbeta_y, double* gbeta_z, double* q, paris_stats* st);
+
+/* Adjoint of step 1: dLoss/dC_c = -(rho1 - rho2)/2 * sum over the non-wall
+ * faces f of cell c of gbeta_f beta_f^2, from beta_f = 2/(rho_L + rho_R) and
+ * rho = rho1 C + rho2 (1 - C).  beta and gbeta: face arrays; gC: cells.
+ * Errors: INVALID_ARG (null pointer, rho <= 0). */
+paris_status paris_face_coeffs_adjoint(paris_ctx* ctx, double rho1, double rho2,
+                                       const double* beta_x, const double* beta_y,
+                                       const double* beta_z, const double* gbeta_x,
+                                       const double* gbeta_y, const double* gbeta_z, double* gC);
+
 /* Diagnostics on device arrays, FP64: r = rhs - L p, returning (host) the
  * relative residual norms with respect to rhs (rhs taken as given, mean not
  * removed) and the maximum absolute discrete divergence max|grad^h . u| of a

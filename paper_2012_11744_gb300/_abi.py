@@ -77,6 +77,9 @@ SIGNATURES = {
     "paris_projection_step": (ct.c_int, [_P, _P, _D, _D, _D, _P, _P, _P, _P, ct.POINTER(Stats)]),
     "paris_projection_step_host": (ct.c_int, [_P, _P, _D, _D, _D, _P, _P, _P, _P,
                                               ct.POINTER(Stats)]),
+    "paris_project_adjoint": (ct.c_int, [_P, _P, _P, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P, _P,
+                                         _P, _P, ct.POINTER(Stats)]),
+    "paris_face_coeffs_adjoint": (ct.c_int, [_P, _D, _D, _P, _P, _P, _P, _P, _P, _P]),
     "paris_residual_norms": (ct.c_int, [_P, _P, _P, _P, _P, _P, ct.POINTER(_D), ct.POINTER(_D)]),
     "paris_max_divergence": (ct.c_int, [_P, _P, _P, _P, ct.POINTER(_D)]),
     "paris_profile": (ct.c_int, [_P, ct.c_int]),

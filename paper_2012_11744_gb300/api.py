@@ -223,6 +223,40 @@ class Context:
         d["status"] = s
         return d
 
+    def project_adjoint(self, bx, by, bz, p, dt, gu, gv, gw, q=None, check=True):
+        """Adjoint of the projection: returns ((gus, gvs, gws), (gbx, gby, gbz), q, stats)
+        with gus = dLoss/du* and gb = dLoss/dbeta for g = dLoss/du."""
+        g = self.grid
+        gus, gbt = self.empty_faces(), self.empty_faces()
+        if q is None:
+            q = torch.zeros(g.shape, dtype=torch.float64, device=self.device)
+        st = _abi.Stats()
+        fs = [g.face_shape(a) for a in range(3)]
+        s = self.lib.paris_project_adjoint(
+            self._ptr, self._t(bx, fs[0], "beta_x"), self._t(by, fs[1], "beta_y"),
+            self._t(bz, fs[2], "beta_z"), self._t(p, g.shape, "p"), float(dt),
+            self._t(gu, fs[0], "gu"), self._t(gv, fs[1], "gv"), self._t(gw, fs[2], "gw"),
+            *(self._t(x, fs[a], "gus") for a, x in enumerate(gus)),
+            *(self._t(x, fs[a], "gbeta") for a, x in enumerate(gbt)),
+            self._t(q, g.shape, "q"), ct.byref(st))
+        if check:
+            _abi.check(s, "paris_project_adjoint", st.as_dict())
+        d = st.as_dict()
+        d["status"] = s
+        return gus, gbt, q, d
+
+    def face_coeffs_adjoint(self, rho1, rho2, bx, by, bz, gbx, gby, gbz, out=None):
+        """dLoss/dC from dLoss/dbeta (cells)."""
+        g = self.grid
+        gC = out if out is not None else self.empty_cells()
+        fs = [g.face_shape(a) for a in range(3)]
+        _abi.check(self.lib.paris_face_coeffs_adjoint(
+            self._ptr, float(rho1), float(rho2), self._t(bx, fs[0], "beta_x"),
+            self._t(by, fs[1], "beta_y"), self._t(bz, fs[2], "beta_z"),
+            self._t(gbx, fs[0], "gbeta_x"), self._t(gby, fs[1], "gbeta_y"),
+            self._t(gbz, fs[2], "gbeta_z"), self._t(gC, g.shape, "gC")), "paris_face_coeffs_adjoint")
+        return gC
+
     def residual_norms(self, bx, by, bz, rhs, p):
         """FP64 (||rhs - L p||_2/||rhs||_2, ||.||_inf/||rhs||_inf) on the device."""
         g = self.grid

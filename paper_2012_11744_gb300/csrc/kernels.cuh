@@ -133,4 +133,19 @@ void launch_xpby(int64_t n, const Scal* s, const T* z, T* d, cudaStream_t st);
 // x64 += e32 * inv_scale
 void launch_accumulate(int64_t n, const Scal* s, const float* e, double* x, cudaStream_t st);
 
+// ------------------------------------------------------------ adjoint -----
+// out = D (B g) (walls carry no flux); partials (sum, max|out|, nonfinite)
+int64_t launch_weighted_div(const Geo& g, const double* bx, const double* by, const double* bz,
+                            const double* gx, const double* gy, const double* gz, double inv_h,
+                            double* out, double* partials, cudaStream_t st);
+// dLoss/du* = g - G q and dLoss/dbeta = dt (G p)(G q - g) on non-wall faces
+void launch_adjoint_faces(const Geo& g, const double* p, const double* q, double inv_h, double dt,
+                          const double* gx, const double* gy, const double* gz, double* usx,
+                          double* usy, double* usz, double* bbx, double* bby, double* bbz,
+                          cudaStream_t st);
+// dLoss/dC from dLoss/dbeta through beta = 2/(rho_L + rho_R)
+void launch_face_coeffs_adjoint(const Geo& g, double rho1, double rho2, const double* bx,
+                                const double* by, const double* bz, const double* gbx,
+                                const double* gby, const double* gbz, double* gC, cudaStream_t st);
+
 }  // namespace paris

@@ -803,6 +803,38 @@ paris_status paris_projection_step_host(paris_ctx* c, const double* C_host, doub
     return s;
 }
 
+paris_status paris_project_adjoint(paris_ctx* c, const double* bx, const double* by,
+                                   const double* bz, const double* p, double dt, const double* gu,
+                                   const double* gv, const double* gw, double* gus, double* gvs,
+                                   double* gws, double* gbx, double* gby, double* gbz, double* q,
+                                   paris_stats* st) {
+    if (!c || !bx || !by || !bz || !p || !gu || !gv || !gw || !gus || !gvs || !gws || !gbx || !gby ||
+        !gbz || !q)
+        return PARIS_ERR_INVALID_ARG;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return PARIS_ERR_INVALID_ARG;
+    const double inv_h = 1.0 / c->grid.h;
+    // right-hand side of the adjoint solve: D (B g)
+    launch_weighted_div(c->g0, bx, by, bz, gu, gv, gw, inv_h, c->rhs, c->partials, c->st);
+    CK(cudaGetLastError());
+    // the adjoint solve uses the same symmetric operator L = D B G
+    paris_status solve = paris_poisson_solve(c, bx, by, bz, c->rhs, q, st);
+    if (solve != PARIS_OK && solve != PARIS_ERR_NOT_CONVERGED) return solve;
+    launch_adjoint_faces(c->g0, p, q, inv_h, dt, gu, gv, gw, gus, gvs, gws, gbx, gby, gbz, c->st);
+    CK(cudaGetLastError());
+    return solve;
+}
+
+paris_status paris_face_coeffs_adjoint(paris_ctx* c, double rho1, double rho2, const double* bx,
+                                       const double* by, const double* bz, const double* gbx,
+                                       const double* gby, const double* gbz, double* gC) {
+    if (!c || !bx || !by || !bz || !gbx || !gby || !gbz || !gC) return PARIS_ERR_INVALID_ARG;
+    if (!(rho1 > 0.0) || !(rho2 > 0.0) || !std::isfinite(rho1) || !std::isfinite(rho2))
+        return PARIS_ERR_INVALID_ARG;
+    launch_face_coeffs_adjoint(c->g0, rho1, rho2, bx, by, bz, gbx, gby, gbz, gC, c->st);
+    CK(cudaGetLastError());
+    return PARIS_OK;
+}
+
 paris_status paris_residual_norms(paris_ctx* c, const double* bx, const double* by,
                                   const double* bz, const double* rhs, const double* p,
                                   double* rel_l2, double* rel_linf) {
