@@ -224,6 +224,54 @@ paris_status paris_face_coeffs_adjoint(paris_ctx* ctx, double rho1, double rho2,
                                        const double* beta_z, const double* gbeta_x,
                                        const double* gbeta_y, const double* gbeta_z, double* gC);
 
+/* ---------------------------------------------------------------------------
+ * BATCHED PROJECTIONS.  Many independent projection steps of uneven grid
+ * sizes in one persistent cooperative launch (captured in a CUDA graph on the
+ * first call and replayed afterwards).  Every instance runs the same step as
+ * paris_projection_step with the mixed-precision solver, starting from p = 0,
+ * on a group of CTAs sized in proportion to its cells; the groups never wait
+ * for one another.  Group barriers spin with an iteration limit: if one gives
+ * up (it should not, since a cooperative launch keeps every CTA resident) the
+ * step returns PARIS_ERR_TIMEOUT instead of hanging.
+ *
+ * POOLED LAYOUT.  All instances' arrays of one kind are concatenated in
+ * instance order into one device buffer: C and p (cells), u (x-faces), v
+ * (y-faces), w (z-faces); paris_batch_layout returns the n+1 offsets (in
+ * doubles) of each pool.  Each instance's slice uses the single-grid layout. */
+typedef struct paris_batch paris_batch;
+
+/* n grids (host array), options (precision is always mixed; smoother must be
+ * PARIS_SMOOTH_RBGS or PARIS_SMOOTH_RBGS_2PASS, both run as red-black colour
+ * passes here), stream.  Allocates all workspace.  INVALID_ARG also when n
+ * exceeds the number of CTAs the GPU can keep resident. */
+paris_status paris_batch_create(paris_batch** b, int n, const paris_grid* grids,
+                                const paris_opts* o, void* stream);
+paris_status paris_batch_destroy(paris_batch* b);
+/* Offsets of the pools (host arrays of n+1 int64, in doubles). */
+paris_status paris_batch_layout(const paris_batch* b, int64_t* cell_off, int64_t* xf_off,
+                                int64_t* yf_off, int64_t* zf_off);
+/* CTAs in the persistent launch (all co-resident). */
+int paris_batch_launch_ctas(const paris_batch* b);
+/* One projection step of every instance: C (cell pool), rho1/rho2/dt (host
+ * arrays of n), u/v/w (face pools, in: u*, out: u), p (cell pool, out: the
+ * mean-free pressure), st (host array of n, optional).  Returns the first
+ * failure (NONFINITE, NOT_CONVERGED) or TIMEOUT; synchronises the stream. */
+paris_status paris_batch_projection_step(paris_batch* b, const double* C, const double* rho1,
+                                         const double* rho2, const double* dt, double* u,
+                                         double* v, double* w, double* p, paris_stats* st);
+/* Autotuner: times the step for every candidate (sweeps nu1 = nu2 in {1,2,3},
+ * omega in {1.0, 1.15, 1.3}, CTAs per SM in {1,2,4,8} up to the resident
+ * limit) on scratch copies of u*, v*, w* (inputs are not modified), keeps the
+ * fastest converged one and appends it to cache_path (one JSON object per
+ * line keyed by GPU name, instance shapes and tolerance; may be NULL).  An
+ * existing entry for the same key is applied without timing.  Allocates its
+ * scratch (not a hot call).  best_ms (host, optional): the winner's time. */
+paris_status paris_batch_autotune(paris_batch* b, const double* C, const double* rho1,
+                                  const double* rho2, const double* dt, const double* u,
+                                  const double* v, const double* w, const char* cache_path,
+                                  double* best_ms);
+paris_status paris_batch_get_tuning(const paris_batch* b, int* nu, double* omega, int* ctas_per_sm);
+
 /* Diagnostics on device arrays, FP64: r = rhs - L p, returning (host) the
  * relative residual norms with respect to rhs (rhs taken as given, mean not
  * removed) and the maximum absolute discrete divergence max|grad^h . u| of a
@@ -267,6 +315,10 @@ int64_t paris_launch_count(void);
 /* Face-array sizes (number of doubles) of the context's grid; axis 0, 1, 2. */
 int64_t paris_face_count(const paris_ctx* ctx, int axis);
 int64_t paris_cell_count(const paris_ctx* ctx);
+
+/* The last CUDA error the library saw in this thread, as "name: description"
+ * (static thread-local string), to explain a PARIS_ERR_CUDA. */
+const char* paris_last_cuda_error(void);
 
 /* Human-readable name of a status code (static string). */
 const char* paris_status_string(paris_status s);

@@ -80,6 +80,17 @@ SIGNATURES = {
     "paris_project_adjoint": (ct.c_int, [_P, _P, _P, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P, _P,
                                          _P, _P, ct.POINTER(Stats)]),
     "paris_face_coeffs_adjoint": (ct.c_int, [_P, _D, _D, _P, _P, _P, _P, _P, _P, _P]),
+    "paris_batch_create": (ct.c_int, [ct.POINTER(_P), ct.c_int, ct.POINTER(Grid), ct.POINTER(Opts), _P]),
+    "paris_batch_destroy": (ct.c_int, [_P]),
+    "paris_batch_layout": (ct.c_int, [_P, ct.POINTER(ct.c_int64), ct.POINTER(ct.c_int64),
+                                      ct.POINTER(ct.c_int64), ct.POINTER(ct.c_int64)]),
+    "paris_batch_launch_ctas": (ct.c_int, [_P]),
+    "paris_batch_projection_step": (ct.c_int, [_P, _P, ct.POINTER(_D), ct.POINTER(_D), ct.POINTER(_D),
+                                               _P, _P, _P, _P, ct.POINTER(Stats)]),
+    "paris_batch_autotune": (ct.c_int, [_P, _P, ct.POINTER(_D), ct.POINTER(_D), ct.POINTER(_D), _P, _P,
+                                        _P, ct.c_char_p, ct.POINTER(_D)]),
+    "paris_batch_get_tuning": (ct.c_int, [_P, ct.POINTER(ct.c_int), ct.POINTER(_D),
+                                          ct.POINTER(ct.c_int)]),
     "paris_residual_norms": (ct.c_int, [_P, _P, _P, _P, _P, _P, ct.POINTER(_D), ct.POINTER(_D)]),
     "paris_max_divergence": (ct.c_int, [_P, _P, _P, _P, ct.POINTER(_D)]),
     "paris_profile": (ct.c_int, [_P, ct.c_int]),
@@ -88,6 +99,7 @@ SIGNATURES = {
     "paris_face_count": (ct.c_int64, [_P, ct.c_int]),
     "paris_cell_count": (ct.c_int64, [_P]),
     "paris_status_string": (ct.c_char_p, [ct.c_int]),
+    "paris_last_cuda_error": (ct.c_char_p, []),
 }
 
 
@@ -118,7 +130,10 @@ class ParisError(RuntimeError):
     def __init__(self, status: int, where: str, stats=None):
         self.status = status
         self.stats = stats
-        msg = load().paris_status_string(status).decode()
+        lib = load()
+        msg = lib.paris_status_string(status).decode()
+        if status == PARIS_ERR_CUDA:
+            msg += " [" + lib.paris_last_cuda_error().decode() + "]"
         super().__init__(f"{where}: {msg} (status {status})")
 
 

@@ -291,3 +291,103 @@ class Context:
                                                  self._t(w, g.face_shape(2), "w"), ct.byref(m)),
                    "paris_max_divergence")
         return m.value
+
+
+class Batch:
+    """Many independent projections of uneven grid sizes in one persistent
+    launch (paris_batch_*).  Arrays are pooled: one device buffer per kind
+    (C, p: cells; u, v, w: faces), instances concatenated in order."""
+
+    def __init__(self, grids, opts: _abi.Opts | None = None, device=None, stream=None, **kw):
+        self.lib = _abi.load()
+        self.grids = [Grid(g.nx, g.ny, g.nz, g.h, tuple(g.bc)) for g in grids]
+        self.n = len(self.grids)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.opts = opts if opts is not None else default_opts(**kw)
+        arr = (_abi.Grid * self.n)(*[_grid_struct(g) for g in self.grids])
+        self._ptr = ct.c_void_p()
+        with torch.cuda.device(self.device):
+            _abi.check(self.lib.paris_batch_create(ct.byref(self._ptr), self.n, arr, ct.byref(self.opts),
+                                                   ct.c_void_p(self.stream.cuda_stream)),
+                       "paris_batch_create")
+        offs = [(ct.c_int64 * (self.n + 1))() for _ in range(4)]
+        _abi.check(self.lib.paris_batch_layout(self._ptr, *offs), "paris_batch_layout")
+        self.offsets = {k: np.array(o[:], dtype=np.int64) for k, o in zip(("cells", "u", "v", "w"), offs)}
+
+    def close(self):
+        if getattr(self, "_ptr", None) and self._ptr.value:
+            self.lib.paris_batch_destroy(self._ptr)
+            self._ptr = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def launch_ctas(self):
+        return int(self.lib.paris_batch_launch_ctas(self._ptr))
+
+    def pack(self, arrays, kind):
+        """Concatenate per-instance numpy/torch arrays of one kind into a device pool."""
+        off = self.offsets["cells" if kind in ("C", "p") else kind]
+        pool = torch.empty(int(off[-1]), dtype=torch.float64, device=self.device)
+        for i, a in enumerate(arrays):
+            t = a if isinstance(a, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(a))
+            pool[off[i]:off[i + 1]] = t.reshape(-1).to(self.device, torch.float64)
+        return pool
+
+    def unpack(self, pool, kind):
+        """Views of a pool as per-instance arrays (numpy shape conventions)."""
+        off = self.offsets["cells" if kind in ("C", "p") else kind]
+        out = []
+        for i, g in enumerate(self.grids):
+            shape = g.shape if kind in ("C", "p") else g.face_shape("uvw".index(kind))
+            out.append(pool[off[i]:off[i + 1]].view(shape))
+        return out
+
+    def _check_pool(self, x, kind):
+        off = self.offsets["cells" if kind in ("C", "p") else kind]
+        if (not isinstance(x, torch.Tensor) or x.dtype != torch.float64 or not x.is_contiguous()
+                or x.device != self.device or x.numel() != int(off[-1])):
+            raise ValueError(f"{kind}: need a contiguous float64 pool of {int(off[-1])} on {self.device}")
+        return ct.c_void_p(x.data_ptr())
+
+    def projection_step(self, C, rho1, rho2, dt, u, v, w, p, check=True):
+        """One step of every instance; u, v, w, p pools updated in place.
+        rho1, rho2, dt: sequences of n values.  Returns a list of stats dicts."""
+        st = (_abi.Stats * self.n)()
+        arr = lambda x: (ct.c_double * self.n)(*[float(a) for a in x])
+        s = self.lib.paris_batch_projection_step(self._ptr, self._check_pool(C, "C"), arr(rho1), arr(rho2),
+                                                 arr(dt), self._check_pool(u, "u"), self._check_pool(v, "v"),
+                                                 self._check_pool(w, "w"), self._check_pool(p, "p"), st)
+        stats = [x.as_dict() for x in st]
+        if check:
+            _abi.check(s, "paris_batch_projection_step", stats)
+        return stats
+
+    def autotune(self, C, rho1, rho2, dt, u, v, w, cache_path=None):
+        """Pick sweeps, omega and CTAs per SM by timing; returns the best time (ms)."""
+        arr = lambda x: (ct.c_double * self.n)(*[float(a) for a in x])
+        best = ct.c_double(0.0)
+        _abi.check(self.lib.paris_batch_autotune(
+            self._ptr, self._check_pool(C, "C"), arr(rho1), arr(rho2), arr(dt), self._check_pool(u, "u"),
+            self._check_pool(v, "v"), self._check_pool(w, "w"),
+            cache_path.encode() if cache_path else None, ct.byref(best)), "paris_batch_autotune")
+        return best.value
+
+    def tuning(self):
+        nu, om, bps = ct.c_int(), ct.c_double(), ct.c_int()
+        _abi.check(self.lib.paris_batch_get_tuning(self._ptr, ct.byref(nu), ct.byref(om), ct.byref(bps)),
+                   "paris_batch_get_tuning")
+        return nu.value, om.value, bps.value

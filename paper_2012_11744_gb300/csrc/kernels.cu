@@ -13,6 +13,7 @@
 #include <math.h>
 
 #include <atomic>
+#include <cstdio>
 
 #include "kernels.cuh"
 
@@ -73,6 +74,13 @@ __device__ inline int flat_tid() { return threadIdx.y * blockDim.x + threadIdx.x
 __device__ inline double nonfinite(double v) { return isfinite(v) ? 0.0 : 1.0; }
 
 }  // namespace
+
+static thread_local char g_last_cuda_error[256] = "no CUDA error recorded";
+void paris_internal_note_cuda_error(cudaError_t e) {
+    snprintf(g_last_cuda_error, sizeof g_last_cuda_error, "%s: %s", cudaGetErrorName(e),
+             cudaGetErrorString(e));
+}
+const char* last_cuda_error() { return g_last_cuda_error; }
 
 static std::atomic<long long> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }

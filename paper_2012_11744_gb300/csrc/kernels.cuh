@@ -42,6 +42,10 @@ int elementwise_blocks(int64_t n);
 // number of partial-sum slots a caller must provide, per value).
 int64_t max_reduce_blocks(const Geo& g);
 
+// Remember the last CUDA error seen by the library (for paris_last_cuda_error).
+void paris_internal_note_cuda_error(cudaError_t e);
+const char* last_cuda_error();
+
 // Process-wide count of kernel launches made by the library.
 void count_launch(int n = 1);
 long long launch_count();

@@ -108,10 +108,13 @@ struct paris_ctx {
 
 namespace {
 
-#define CK(call)                                                   \
-    do {                                                           \
-        cudaError_t e_ = (call);                                   \
-        if (e_ != cudaSuccess) return PARIS_ERR_CUDA;              \
+#define CK(call)                                       \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) {                       \
+            paris_internal_note_cuda_error(e_);        \
+            return PARIS_ERR_CUDA;                     \
+        }                                              \
     } while (0)
 
 bool valid_grid(const paris_grid* g) {
@@ -659,6 +662,8 @@ paris_status paris_profile_read(paris_ctx* c, int cls, paris_kernel_prof* out) {
 }
 
 int64_t paris_launch_count(void) { return (int64_t)launch_count(); }
+
+const char* paris_last_cuda_error(void) { return last_cuda_error(); }
 
 int64_t paris_face_count(const paris_ctx* c, int axis) {
     if (!c || axis < 0 || axis > 2) return -1;
