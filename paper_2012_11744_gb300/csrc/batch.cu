@@ -1092,7 +1092,10 @@ paris_status paris_batch_autotune(paris_batch* b, const double* C, const double*
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     for (int bps : bpss) {
+        if (sms * bps < b->n) continue;  // needs at least one CTA per instance
         b->bps = bps;
         if ((ret = build_descriptors(b)) != PARIS_OK) break;
         b->graph_key[0] = nullptr;

@@ -127,3 +127,24 @@ def test_jet_512x256x256(paris):
     p, u, st = run_gpu(paris, pr, paris.MIXED)
     assert st["converged"] == 1, st
     check_properties(pr, p, u)
+
+
+def test_batch_256_uneven_instances(paris):
+    """The full batch: 256 periodic instances, axes from {32,48,64,96,128}
+    (1.07e8 cells), one persistent launch: every instance converges; 12
+    sampled instances are checked under the oracle's operator and divergence."""
+    probs = pi.config4(count=256)
+    with paris.Batch([p.grid for p in probs]) as b:
+        C = b.pack([p.C for p in probs], "C")
+        u = b.pack([p.u for p in probs], "u")
+        v = b.pack([p.v for p in probs], "v")
+        w = b.pack([p.w for p in probs], "w")
+        pp = torch.zeros_like(C)
+        st = b.projection_step(C, [p.rho1 for p in probs], [p.rho2 for p in probs],
+                               [p.dt for p in probs], u, v, w, pp)
+        assert all(s["converged"] == 1 for s in st)
+        rng = np.random.default_rng(256)
+        for i in rng.choice(len(probs), size=12, replace=False):
+            p = b.unpack(pp, "p")[i].cpu().numpy()
+            uvw = tuple(b.unpack(x, k)[i].cpu().numpy() for x, k in ((u, "u"), (v, "v"), (w, "w")))
+            check_properties(probs[i], p, uvw)
