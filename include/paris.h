@@ -94,6 +94,9 @@ typedef struct {
     int coarse_max_cells; /* coarsen until the coarsest grid has at most this many cells (64) */
     double inner_tol;     /* MIXED: relative residual reduction of each FP32 inner solve (1e-5) */
     int fallback;         /* MIXED: on failure redo the solve in FP64 (1) */
+    int slab_planes;      /* two-pass red-black: run each colour pass in z-slabs of this
+                             many planes so the second colour finds the slab in L2
+                             (0 = whole-grid passes) (0) */
 } paris_opts;
 
 typedef struct {

@@ -603,10 +603,10 @@ __device__ inline T inv_sum6(const T (&b)[6]) {
 template <typename T, bool USEW>
 __global__ void __launch_bounds__(kTX* kTY) rbgs_kernel(Geo g, Coef<T> cf, const T* __restrict__ w,
                                                        const T* __restrict__ f, T* __restrict__ x,
-                                                       int color, T omega, int zero_init) {
+                                                       int color, T omega, int zero_init, int k0) {
     const int t = blockIdx.x * kTX + threadIdx.x;
     const int j = blockIdx.y * kTY + threadIdx.y;
-    const int k = blockIdx.z;
+    const int k = k0 + blockIdx.z;
     const int i0 = 2 * t;
     if (i0 >= g.nx || j >= g.ny) return;
     const int i = i0 + ((i0 + j + k + color) & 1);
@@ -641,17 +641,18 @@ __global__ void __launch_bounds__(kTX* kTY) rbgs_kernel(Geo g, Coef<T> cf, const
 
 template <typename T>
 void launch_rbgs(const Geo& g, const Coef<T>& cf, const T* w, const T* f, T* x, int color,
-                 double omega, bool zero_init, cudaStream_t st) {
+                 double omega, bool zero_init, cudaStream_t st, int k0, int k1) {
+    if (k1 < 0) k1 = g.nz;
     const int npair = (g.nx + 1) / 2;
-    dim3 gr((npair + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, g.nz);
+    dim3 gr((npair + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, k1 - k0);
     // FP32: recomputing 1/D from the coefficients already loaded is cheaper
     // than reading it; FP64: the division costs more than the read
     if (sizeof(T) == 8)
         rbgs_kernel<T, true><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, w, f, x, color, (T)omega,
-                                                            zero_init ? 1 : 0);
+                                                            zero_init ? 1 : 0, k0);
     else
         rbgs_kernel<T, false><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, w, f, x, color, (T)omega,
-                                                             zero_init ? 1 : 0);
+                                                             zero_init ? 1 : 0, k0);
     count_launch();
 }
 
@@ -973,7 +974,7 @@ void launch_accumulate(int64_t n, const Scal* s, const float* e, double* x, cuda
     template void launch_coarse_inverse<T>(const Geo&, const Coef<T>&, double*, cudaStream_t); \
     template void launch_coarse_solve<T>(const Geo&, const double*, const T*, T*, cudaStream_t); \
     template void launch_rbgs<T>(const Geo&, const Coef<T>&, const T*, const T*, T*, int,     \
-                                 double, bool, cudaStream_t);                                  \
+                                 double, bool, cudaStream_t, int, int);                        \
     template void launch_jacobi<T>(const Geo&, const Coef<T>&, const T*, const T*, const T*,  \
                                    T*, double, bool, cudaStream_t);                            \
     template void launch_restrict_residual<T>(const Geo&, const Coef<T>&, const T*, const T*,  \

@@ -86,11 +86,12 @@ template <typename T>
 void launch_coarse_solve(const Geo& g, const double* inv, const T* f, T* x, cudaStream_t st);
 
 // ------------------------------------------------------------ V-cycle -----
-// One red-black colour pass of over-relaxed Gauss-Seidel on A x = f.
+// One red-black colour pass of over-relaxed Gauss-Seidel on A x = f, in
+// place, on the z-planes [k0, k1) (k1 < 0: all planes).
 // zero_init: x is taken as 0 on entry (the pass also zeroes the other colour).
 template <typename T>
 void launch_rbgs(const Geo& g, const Coef<T>& cf, const T* w, const T* f, T* x, int color,
-                 double omega, bool zero_init, cudaStream_t st);
+                 double omega, bool zero_init, cudaStream_t st, int k0 = 0, int k1 = -1);
 // One fused red-black sweep (both colours, one pass) from xin to xout
 // (separate arrays; xin unread when zero_init).  first_color: colour
 // updated first (0 = red, (i+j+k) even).  use_w: read the inverse diagonal

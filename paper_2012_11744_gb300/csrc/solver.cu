@@ -65,7 +65,7 @@ struct Alloc {
 };
 
 constexpr int kMaxDense = 128;
-constexpr int kProfPool = 8192;  // event pairs per paris_profile(ctx, 1)
+constexpr int kProfPool = 16384;  // event pairs per paris_profile(ctx, 1)
 
 struct Profiler {
     bool on = false;
@@ -104,6 +104,11 @@ struct paris_ctx {
     double *hC = nullptr, *hu = nullptr, *hv = nullptr, *hw = nullptr, *hp = nullptr;
     double last_mean_b = 0.0;
     Profiler prof;
+    // CUDA graphs of the coarse part of the V-cycle (index 0: FP32, 1: FP64)
+    cudaStream_t cap_stream = nullptr;
+    bool cap_stream_broken = false;
+    cudaGraphExec_t cg_exec[2] = {nullptr, nullptr};
+    int cg_kernels[2] = {0, 0};
 };
 
 namespace {
@@ -135,6 +140,7 @@ bool valid_opts(const paris_opts* o) {
     if (o->smoother < PARIS_SMOOTH_RBGS || o->smoother > PARIS_SMOOTH_RBGS_2PASS) return false;
     if (o->coarse_max_cells < 1 || o->coarse_max_cells > kMaxDense) return false;
     if (!(o->inner_tol > 0.0 && o->inner_tol < 1.0)) return false;
+    if (o->slab_planes < 0) return false;
     return true;
 }
 
@@ -223,6 +229,14 @@ paris_status alloc_ctx(paris_ctx* c) {
     if (cudaMallocHost(&c->scal_h, sizeof(Scal)) != cudaSuccess) return PARIS_ERR_NO_MEMORY;
     CK(cudaMemsetAsync(c->scal, 0, sizeof(Scal), c->st));
     return PARIS_OK;
+}
+
+void drop_graphs(paris_ctx* c) {
+    for (auto& g : c->cg_exec)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
 }
 
 paris_status read_scal(paris_ctx* c) {
@@ -315,17 +329,43 @@ void smooth(paris_ctx* c, int l, const Coef<T>& cf, const T* f, T* x, int sweeps
     const bool use_w = sizeof(T) == 8;  // FP64: a division costs more than reading 1/D
     if (o.smoother == PARIS_SMOOTH_RBGS_2PASS ||
         (o.smoother == PARIS_SMOOTH_RBGS && !rbgs_fused_fits(L.g))) {
+        // Large levels run each colour pass slab by slab: the second colour of
+        // slab s follows the first colour of slab s+1, while slab s is still
+        // in L2, so a sweep reads the level from HBM about once instead of
+        // twice.  The last slab's first colour runs early because with a
+        // periodic z axis it needs plane 0's second colour not yet updated.
+        // Every cell sees the same values as in two full passes.
+        const int nz = L.g.nz;
+        const int S = o.slab_planes > 0 ? o.slab_planes : nz;
+        const int m = (nz + S - 1) / S;
+        const bool slabs = o.slab_planes > 0 && m >= 4;
+        const double per_plane = 1.0 / nz;
         for (int s = 0; s < sweeps; ++s) {
             const bool z0 = first_zero && s == 0;
             const int c0 = reverse ? 1 : 0;
-            {
-                ProfScope ps(c, cls, z0 ? 2 * n * sz : (2.5 * n + nb) * sz);
-                launch_rbgs<T>(L.g, cf, Prec<T>::w(L), f, x, c0, o.omega, z0, c->st);
+            auto first = [&](int a, int b) {
+                ProfScope ps(c, cls, (z0 ? 2 * n * sz : (2.5 * n + nb) * sz) * (b - a) * per_plane);
+                launch_rbgs<T>(L.g, cf, Prec<T>::w(L), f, x, c0, o.omega, z0, c->st, a, b);
+            };
+            auto second = [&](int a, int b) {
+                ProfScope ps(c, cls, (2.5 * n + nb) * sz * (b - a) * per_plane);
+                launch_rbgs<T>(L.g, cf, Prec<T>::w(L), f, x, 1 - c0, o.omega, false, c->st, a, b);
+            };
+            if (!slabs) {
+                first(0, nz);
+                second(0, nz);
+                continue;
             }
-            {
-                ProfScope ps(c, cls, (2.5 * n + nb) * sz);
-                launch_rbgs<T>(L.g, cf, Prec<T>::w(L), f, x, 1 - c0, o.omega, false, c->st);
+            auto lo = [&](int q) { return q * S; };
+            auto hi = [&](int q) { return std::min(nz, (q + 1) * S); };
+            first(lo(0), hi(0));
+            first(lo(m - 1), hi(m - 1));
+            for (int q = 1; q <= m - 2; ++q) {
+                first(lo(q), hi(q));
+                second(lo(q - 1), hi(q - 1));
             }
+            second(lo(m - 2), hi(m - 2));
+            second(lo(m - 1), hi(m - 1));
         }
         return;
     }
@@ -351,49 +391,110 @@ void smooth(paris_ctx* c, int l, const Coef<T>& cf, const T* f, T* x, int sweeps
         cudaMemcpyAsync(x, bufs[cur], sizeof(T) * L.g.ncell(), cudaMemcpyDeviceToDevice, c->st);
 }
 
+// Pre-smoothing on level l and restriction of its residual to level l+1.
+template <typename T>
+void vdown(paris_ctx* c, const Coef<T>& c0, const T* f0, T* x0, int l) {
+    const paris_opts& o = c->opts;
+    const T* f = l == 0 ? f0 : Prec<T>::f(c->lv[l]);
+    T* x = l == 0 ? x0 : Prec<T>::x(c->lv[l]);
+    Coef<T> cf = level_coef<T>(c, l, c0);
+    if (o.nu1 > 0) smooth<T>(c, l, cf, f, x, o.nu1, true, false);
+    else cudaMemsetAsync(x, 0, sizeof(T) * c->lv[l].g.ncell(), c->st);
+    Level& C = c->lv[l + 1];
+    const double n = (double)c->lv[l].g.ncell();
+    ProfScope ps(c, l == 0 ? PARIS_K_RESTRICT0 : -1,
+                 (2 * n + beta_count(c->lv[l].g) + (double)C.g.ncell()) * sizeof(T));
+    launch_restrict_residual<T>(c->lv[l].g, cf, f, x, C.g, C.fac, Prec<T>::f(C), c->st);
+}
+
+// Exact (dense) or smoothed solve on the coarsest level.
+template <typename T>
+void vcoarse(paris_ctx* c, const Coef<T>& c0, const T* f0, T* x0) {
+    const int nl = (int)c->lv.size();
+    Level& C = c->lv[nl - 1];
+    const T* f = nl == 1 ? f0 : Prec<T>::f(C);
+    T* x = nl == 1 ? x0 : Prec<T>::x(C);
+    if (c->dense_coarse) {
+        launch_coarse_solve<T>(C.g, c->coarse_inv, f, x, c->st);
+    } else {
+        Coef<T> cf = level_coef<T>(c, nl - 1, c0);
+        smooth<T>(c, nl - 1, cf, f, x, 8, true, false);
+        smooth<T>(c, nl - 1, cf, f, x, 8, false, true);
+    }
+}
+
+// Prolongation from level l+1 onto level l and post-smoothing on level l.
+template <typename T>
+void vup(paris_ctx* c, const Coef<T>& c0, const T* f0, T* x0, int l) {
+    const paris_opts& o = c->opts;
+    const T* f = l == 0 ? f0 : Prec<T>::f(c->lv[l]);
+    T* x = l == 0 ? x0 : Prec<T>::x(c->lv[l]);
+    Coef<T> cf = level_coef<T>(c, l, c0);
+    Level& C = c->lv[l + 1];
+    {
+        const double n = (double)c->lv[l].g.ncell();
+        ProfScope ps(c, l == 0 ? PARIS_K_PROLONG0 : -1, (2 * n + (double)C.g.ncell()) * sizeof(T));
+        launch_prolong_add<T>(c->lv[l].g, C.g, C.fac, Prec<T>::x(C), x, c->st);
+    }
+    if (o.nu2 > 0) smooth<T>(c, l, cf, f, x, o.nu2, false, true);
+}
+
+// The part of the V-cycle below level 0 (levels 1 .. L-1) only reads and
+// writes the context's own level arrays, so it is captured once per
+// precision into a CUDA graph and replayed: dozens of small launches on the
+// coarse levels become one graph launch.  Captured on the context's private
+// stream (the legacy default stream cannot be captured), launched on the
+// context's stream.
+template <typename T>
+bool coarse_graph_launch(paris_ctx* c, const Coef<T>& c0) {
+    const int nl = (int)c->lv.size();
+    const int slot = sizeof(T) == 8 ? 1 : 0;
+    if (nl < 3 || !c->cap_stream) return false;
+    if (!c->cg_exec[slot]) {
+        cudaStream_t user = c->st;
+        c->st = c->cap_stream;
+        const long long before = launch_count();
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            for (int l = 1; l < nl - 1; ++l) vdown<T>(c, c0, nullptr, nullptr, l);
+            vcoarse<T>(c, c0, nullptr, nullptr);
+            for (int l = nl - 2; l >= 1; --l) vup<T>(c, c0, nullptr, nullptr, l);
+            e = cudaStreamEndCapture(c->st, &g);
+        }
+        c->st = user;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&c->cg_exec[slot], g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c->cg_exec[slot] = nullptr;
+            c->cap_stream_broken = true;  // fall back to direct launches
+            return false;
+        }
+        c->cg_kernels[slot] = (int)(launch_count() - before);
+        count_launch(-c->cg_kernels[slot]);  // counted when replayed instead
+    }
+    if (cudaGraphLaunch(c->cg_exec[slot], c->st) != cudaSuccess) return false;
+    count_launch(c->cg_kernels[slot]);
+    return true;
+}
+
 // x0 = V(f0): one symmetric V-cycle for A x = f on level 0 (x0 overwritten).
 template <typename T>
 void vcycle(paris_ctx* c, const Coef<T>& c0, const T* f0, T* x0) {
     const int nl = (int)c->lv.size();
-    const paris_opts& o = c->opts;
-    for (int l = 0; l < nl - 1; ++l) {
-        const T* f = l == 0 ? f0 : Prec<T>::f(c->lv[l]);
-        T* x = l == 0 ? x0 : Prec<T>::x(c->lv[l]);
-        Coef<T> cf = level_coef<T>(c, l, c0);
-        if (o.nu1 > 0) smooth<T>(c, l, cf, f, x, o.nu1, true, false);
-        else cudaMemsetAsync(x, 0, sizeof(T) * c->lv[l].g.ncell(), c->st);
-        Level& C = c->lv[l + 1];
-        {
-            const double n = (double)c->lv[l].g.ncell();
-            ProfScope ps(c, l == 0 ? PARIS_K_RESTRICT0 : -1,
-                         (2 * n + beta_count(c->lv[l].g) + (double)C.g.ncell()) * sizeof(T));
-            launch_restrict_residual<T>(c->lv[l].g, cf, f, x, C.g, C.fac, Prec<T>::f(C), c->st);
+    if (nl >= 3 && !c->cap_stream_broken) {
+        vdown<T>(c, c0, f0, x0, 0);
+        if (coarse_graph_launch<T>(c, c0)) {
+            vup<T>(c, c0, f0, x0, 0);
+            return;
         }
+        for (int l = 1; l < nl - 1; ++l) vdown<T>(c, c0, f0, x0, l);
+    } else {
+        for (int l = 0; l < nl - 1; ++l) vdown<T>(c, c0, f0, x0, l);
     }
-    {
-        Level& C = c->lv[nl - 1];
-        const T* f = nl == 1 ? f0 : Prec<T>::f(C);
-        T* x = nl == 1 ? x0 : Prec<T>::x(C);
-        if (c->dense_coarse) {
-            launch_coarse_solve<T>(C.g, c->coarse_inv, f, x, c->st);
-        } else {
-            Coef<T> cf = level_coef<T>(c, nl - 1, c0);
-            smooth<T>(c, nl - 1, cf, f, x, 8, true, false);
-            smooth<T>(c, nl - 1, cf, f, x, 8, false, true);
-        }
-    }
-    for (int l = nl - 2; l >= 0; --l) {
-        const T* f = l == 0 ? f0 : Prec<T>::f(c->lv[l]);
-        T* x = l == 0 ? x0 : Prec<T>::x(c->lv[l]);
-        Coef<T> cf = level_coef<T>(c, l, c0);
-        Level& C = c->lv[l + 1];
-        {
-            const double n = (double)c->lv[l].g.ncell();
-            ProfScope ps(c, l == 0 ? PARIS_K_PROLONG0 : -1, (2 * n + (double)C.g.ncell()) * sizeof(T));
-            launch_prolong_add<T>(c->lv[l].g, C.g, C.fac, Prec<T>::x(C), x, c->st);
-        }
-        if (o.nu2 > 0) smooth<T>(c, l, cf, f, x, o.nu2, false, true);
-    }
+    vcoarse<T>(c, c0, f0, x0);
+    for (int l = nl - 2; l >= 0; --l) vup<T>(c, c0, f0, x0, l);
 }
 
 // ------------------------------------------------------------- drivers ---
@@ -559,6 +660,7 @@ void paris_default_opts(paris_opts* o) {
     o->coarse_max_cells = 64;
     o->inner_tol = 1e-5;
     o->fallback = 1;
+    o->slab_planes = 0;
 }
 
 const char* paris_status_string(paris_status s) {
@@ -589,6 +691,10 @@ paris_status paris_create(paris_ctx** out, const paris_grid* g, const paris_opts
                 g->bc[2] == PARIS_WALL};
     c->N = c->g0.ncell();
     c->st = (cudaStream_t)stream;
+    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        c->cap_stream = nullptr;
+    }
     paris_status s = alloc_ctx(c);
     if (s != PARIS_OK) {
         paris_destroy(c);
@@ -601,6 +707,8 @@ paris_status paris_create(paris_ctx** out, const paris_grid* g, const paris_opts
 paris_status paris_destroy(paris_ctx* c) {
     if (!c) return PARIS_ERR_INVALID_ARG;
     cudaStreamSynchronize(c->st);
+    drop_graphs(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     c->mem.release();
     if (c->scal_h) cudaFreeHost(c->scal_h);
     for (auto& e : c->prof.ev) cudaEventDestroy(e);
@@ -610,6 +718,8 @@ paris_status paris_destroy(paris_ctx* c) {
 
 paris_status paris_set_opts(paris_ctx* c, const paris_opts* o) {
     if (!c || !valid_opts(o)) return PARIS_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(c->st));
+    drop_graphs(c);  // sweeps and omega are baked into the captured V-cycle
     if (o->coarse_max_cells != c->opts.coarse_max_cells) {
         // the level plan depends on coarse_max_cells: rebuild the workspace
         CK(cudaStreamSynchronize(c->st));

@@ -142,7 +142,9 @@ def test_drops_walls_64(paris, precision):
 
 # every smoothed multigrid level has even periodic axes (walls may be odd)
 EVEN_GRIDS = [GRIDS[0], pi.Grid(64, 32, 16, 1 / 64, (P, P, W)), pi.Grid(24, 24, 24, 1 / 24),
-              pi.Grid(20, 12, 8, 0.05, (W, W, P)), pi.Grid(13, 7, 9, 0.1, (W, W, W))]
+              pi.Grid(20, 12, 8, 0.05, (W, W, P)), pi.Grid(13, 7, 9, 0.1, (W, W, W)),
+              # tall grids: the two-pass sweep runs slab by slab (periodic and wall z)
+              pi.Grid(16, 24, 80, 1 / 16), pi.Grid(24, 16, 72, 1 / 24, (P, W, W))]
 
 
 @pytest.mark.parametrize("precision", ["FP64", "MIXED"])
@@ -156,13 +158,14 @@ def test_fused_smoother_bit_identical_to_two_pass(paris, grid, precision):
     beta = oracle.face_coeffs(grid, pr.C, pr.rho1, pr.rho2)
     b = oracle.divergence(grid, pr.u, pr.v, pr.w, pr.dt)
     out = []
-    for sm in (paris.SMOOTH_RBGS, paris.SMOOTH_RBGS_2PASS):
-        with ctx_for(paris, grid, precision=getattr(paris, precision), smoother=sm) as ctx:
+    for sm, slab in ((paris.SMOOTH_RBGS, 0), (paris.SMOOTH_RBGS_2PASS, 0), (paris.SMOOTH_RBGS_2PASS, 16)):
+        with ctx_for(paris, grid, precision=getattr(paris, precision), smoother=sm, slab_planes=slab) as ctx:
             p = torch.zeros(grid.shape, dtype=torch.float64, device="cuda")
             st = ctx.poisson_solve(*(dev(x) for x in beta), dev(b), p)
             out.append((host(p), st["iters"]))
-    assert out[0][1] == out[1][1]
-    np.testing.assert_array_equal(out[0][0], out[1][0])
+    for q in (1, 2):
+        assert out[0][1] == out[q][1]
+        np.testing.assert_array_equal(out[0][0], out[q][0])
 
 
 @pytest.mark.parametrize("precision", ["FP64", "MIXED"])
