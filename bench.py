@@ -38,7 +38,10 @@ UNIT = "solves/s"
 # DRAM traffic of one launch of each instrumented kernel class, from an ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the
 # kernel source is unchanged (sha256 of csrc/kernels.cu at capture time).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # two-pass FP32 colour pass on the 256^3 drop field (profiles/rbgs_2pass_drops256.md)
+    "smooth0": {"bytes_per_launch": 335.311e6 + 51.845e6, "kernels_sha": "0dbf60bf644221de"},
+}
 
 
 def kernel_source_sha() -> str:
