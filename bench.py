@@ -394,6 +394,25 @@ def run_paris(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_single(args):
+    """One projection of the workload, untimed: the target of ncu captures."""
+    import torch
+
+    import paper_2012_11744_gb300 as paris
+    import paris_inputs as pi
+    pr = pi.config2(n=args.n)
+    g = pr.grid
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    prec = paris.MIXED if args.single == "mixed" else paris.FP64
+    kw = {} if args.smoother is None else {"smoother": args.smoother}
+    ctx = paris.Context(g, opts=paris.default_opts(precision=prec, **kw))
+    u, v, w = d(pr.u), d(pr.v), d(pr.w)
+    p = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+    st = ctx.projection_step(d(pr.C), pr.rho1, pr.rho2, pr.dt, u, v, w, p)
+    torch.cuda.synchronize()
+    print(json.dumps({"single": args.single, "smoother": args.smoother, "stats": st}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -407,9 +426,16 @@ def main():
                     help="seconds of oracle CG iterations in the cpu_baseline sample")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-mode measurement")
+    ap.add_argument("--single", choices=["mixed", "fp64"], default=None,
+                    help="run one untimed projection (the target of ncu captures) and exit")
+    ap.add_argument("--smoother", type=int, default=None,
+                    help="with --single: 0 fused red-black, 1 Jacobi, 2 two-pass red-black")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.single:
+        run_single(args)
+        return
     if args.impl == "reference":
         # rank 0 alone runs the CPU oracle; other ranks exit without work
         run_reference(args, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")))

@@ -97,6 +97,9 @@ typedef struct {
     int slab_planes;      /* two-pass red-black: run each colour pass in z-slabs of this
                              many planes so the second colour finds the slab in L2
                              (0 = whole-grid passes) (0) */
+    int half_coefficients; /* MIXED: the finest-level V-cycle passes read FP16 copies of
+                              beta (the FP32 inner operator and the FP64 residual keep full
+                              precision, so this changes speed, not the converged p) (0) */
 } paris_opts;
 
 typedef struct {

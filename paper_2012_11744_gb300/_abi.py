@@ -37,7 +37,8 @@ class Opts(ct.Structure):
     _fields_ = [("tol", ct.c_double), ("max_iter", ct.c_int), ("precision", ct.c_int),
                 ("nu1", ct.c_int), ("nu2", ct.c_int), ("omega", ct.c_double),
                 ("smoother", ct.c_int), ("coarse_max_cells", ct.c_int),
-                ("inner_tol", ct.c_double), ("fallback", ct.c_int), ("slab_planes", ct.c_int)]
+                ("inner_tol", ct.c_double), ("fallback", ct.c_int), ("slab_planes", ct.c_int),
+                ("half_coefficients", ct.c_int)]
 
 
 class KernelProf(ct.Structure):

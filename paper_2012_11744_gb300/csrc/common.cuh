@@ -3,6 +3,7 @@
 // block reductions.  Internal header (not part of the C ABI).
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -90,6 +91,62 @@ __device__ inline void load_stencil(const Geo& g, const Coef<T>& cf, int i, int 
     s.nb[3] = g.cidx(i, ay.p, k);
     s.nb[4] = g.cidx(i, j, az.m);
     s.nb[5] = g.cidx(i, j, az.p);
+}
+
+// Coefficient loads from FP16, FP32 or FP64 storage.
+__device__ inline float ldc(const __half* p) { return __half2float(*p); }
+__device__ inline float ldc(const float* p) { return *p; }
+__device__ inline double ldc(const double* p) { return *p; }
+
+// load_stencil for coefficient arrays stored in another type TB (converted to T)
+template <typename T, typename TB>
+__device__ inline void load_stencil_as(const Geo& g, const TB* bx, const TB* by, const TB* bz,
+                                       int i, int j, int k, Stencil<T>& s) {
+    AxisNb ax = axis_nb(i, g.nx, g.wx);
+    AxisNb ay = axis_nb(j, g.ny, g.wy);
+    AxisNb az = axis_nb(k, g.nz, g.wz);
+    s.b[0] = ax.wm ? T(0) : (T)ldc(bx + g.fx(i, j, k));
+    s.b[1] = ax.wp ? T(0) : (T)ldc(bx + g.fx(ax.fp, j, k));
+    s.b[2] = ay.wm ? T(0) : (T)ldc(by + g.fy(i, j, k));
+    s.b[3] = ay.wp ? T(0) : (T)ldc(by + g.fy(i, ay.fp, k));
+    s.b[4] = az.wm ? T(0) : (T)ldc(bz + g.fz(i, j, k));
+    s.b[5] = az.wp ? T(0) : (T)ldc(bz + g.fz(i, j, az.fp));
+    s.nb[0] = g.cidx(ax.m, j, k);
+    s.nb[1] = g.cidx(ax.p, j, k);
+    s.nb[2] = g.cidx(i, ay.m, k);
+    s.nb[3] = g.cidx(i, ay.p, k);
+    s.nb[4] = g.cidx(i, j, az.m);
+    s.nb[5] = g.cidx(i, j, az.p);
+}
+
+// Same result as load_stencil_as with 32-bit index arithmetic (valid while
+// every face array of the level holds fewer than 2^31 entries): the cell and
+// face offsets of the six neighbours follow from the cell offset by
+// additions, with wrap-around or clamping at the domain edges.
+template <typename T, typename TB>
+__device__ inline void load_stencil_fast(const Geo& g, const TB* bx, const TB* by, const TB* bz,
+                                         int i, int j, int k, Stencil<T>& s, int& cell) {
+    const int nx = g.nx, ny = g.ny, nz = g.nz, pl = nx * ny;
+    const int row = k * ny + j;
+    const int c = row * nx + i;
+    cell = c;
+    const bool xlo = i == 0, xhi = i == nx - 1;
+    const int fx = row * (nx + g.wx) + i;
+    s.b[0] = (g.wx && xlo) ? T(0) : (T)ldc(bx + fx);
+    s.b[1] = (g.wx && xhi) ? T(0) : (T)ldc(bx + ((!xhi || g.wx) ? fx + 1 : fx - (nx - 1)));
+    s.nb[0] = !xlo ? c - 1 : (g.wx ? c : c + (nx - 1));
+    s.nb[1] = !xhi ? c + 1 : (g.wx ? c : c - (nx - 1));
+    const bool ylo = j == 0, yhi = j == ny - 1;
+    const int fy = (k * (ny + g.wy) + j) * nx + i;
+    s.b[2] = (g.wy && ylo) ? T(0) : (T)ldc(by + fy);
+    s.b[3] = (g.wy && yhi) ? T(0) : (T)ldc(by + ((!yhi || g.wy) ? fy + nx : fy - (ny - 1) * nx));
+    s.nb[2] = !ylo ? c - nx : (g.wy ? c : c + (ny - 1) * nx);
+    s.nb[3] = !yhi ? c + nx : (g.wy ? c : c - (ny - 1) * nx);
+    const bool zlo = k == 0, zhi = k == nz - 1;
+    s.b[4] = (g.wz && zlo) ? T(0) : (T)ldc(bz + c);
+    s.b[5] = (g.wz && zhi) ? T(0) : (T)ldc(bz + ((!zhi || g.wz) ? c + pl : c - (nz - 1) * pl));
+    s.nb[4] = !zlo ? c - pl : (g.wz ? c : c + (nz - 1) * pl);
+    s.nb[5] = !zhi ? c + pl : (g.wz ? c : c - (nz - 1) * pl);
 }
 
 // (A x)_c with A = -L: scale * sum_f beta_f (x_c - x_nb)  (difference form,

@@ -93,6 +93,12 @@ inline bool aligned16(const void* a, const void* b = nullptr, const void* c = nu
     return ok(a) && ok(b) && ok(c) && ok(d);
 }
 
+// 32-bit offsets suffice for every array of the level
+inline bool fits_i32(const Geo& g) {
+    const int64_t big = ((int64_t)1 << 31) - 1;
+    return g.nface(0) < big && g.nface(1) < big && g.nface(2) < big;
+}
+
 int elementwise_blocks(int64_t n) {
     int64_t b = (n + kRedThreads - 1) / kRedThreads;
     const int64_t cap = 152 * 8;  // 8 resident 256-thread blocks on each of the 152 SMs
@@ -600,8 +606,11 @@ __device__ inline T inv_sum6(const T (&b)[6]) {
     return d > T(0) ? T(1) / d : T(0);
 }
 
-template <typename T, bool USEW>
-__global__ void __launch_bounds__(kTX* kTY) rbgs_kernel(Geo g, Coef<T> cf, const T* __restrict__ w,
+template <typename T, typename TB, bool USEW, bool I32>
+__global__ void __launch_bounds__(kTX* kTY) rbgs_kernel(Geo g, const TB* __restrict__ bx,
+                                                       const TB* __restrict__ by,
+                                                       const TB* __restrict__ bz, T scale,
+                                                       const T* __restrict__ w,
                                                        const T* __restrict__ f, T* __restrict__ x,
                                                        int color, T omega, int zero_init, int k0) {
     const int t = blockIdx.x * kTX + threadIdx.x;
@@ -611,23 +620,23 @@ __global__ void __launch_bounds__(kTX* kTY) rbgs_kernel(Geo g, Coef<T> cf, const
     if (i0 >= g.nx || j >= g.ny) return;
     const int i = i0 + ((i0 + j + k + color) & 1);
     const int io = i0 + 1 - (i - i0);  // the other member of the pair
-    const T hs = T(1) / cf.scale;
+    const T hs = T(1) / scale;
     if (i < g.nx) {
-        const int64_t c = g.cidx(i, j, k);
+        Stencil<T> s;
+        int64_t c;
+        if (I32) {
+            int c32;
+            load_stencil_fast<T>(g, bx, by, bz, i, j, k, s, c32);
+            c = c32;
+        } else {
+            c = g.cidx(i, j, k);
+            load_stencil_as<T>(g, bx, by, bz, i, j, k, s);
+        }
         T xn;
         if (zero_init) {
-            T wc;
-            if (USEW) {
-                wc = w[c];
-            } else {
-                Stencil<T> s;
-                load_stencil(g, cf, i, j, k, s);
-                wc = inv_sum6(s.b);
-            }
+            const T wc = USEW ? w[c] : inv_sum6(s.b);
             xn = omega * wc * (f[c] * hs);
         } else {
-            Stencil<T> s;
-            load_stencil(g, cf, i, j, k, s);
             T acc = f[c] * hs;
 #pragma unroll
             for (int q = 0; q < 6; ++q) acc = fma(s.b[q], x[s.nb[q]], acc);
@@ -647,12 +656,36 @@ void launch_rbgs(const Geo& g, const Coef<T>& cf, const T* w, const T* f, T* x, 
     dim3 gr((npair + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, k1 - k0);
     // FP32: recomputing 1/D from the coefficients already loaded is cheaper
     // than reading it; FP64: the division costs more than the read
-    if (sizeof(T) == 8)
-        rbgs_kernel<T, true><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, w, f, x, color, (T)omega,
-                                                            zero_init ? 1 : 0, k0);
+    const bool i32 = fits_i32(g);
+    if (sizeof(T) == 8) {
+        if (i32)
+            rbgs_kernel<T, T, true, true><<<gr, dim3(kTX, kTY), 0, st>>>(
+                g, cf.bx, cf.by, cf.bz, cf.scale, w, f, x, color, (T)omega, zero_init ? 1 : 0, k0);
+        else
+            rbgs_kernel<T, T, true, false><<<gr, dim3(kTX, kTY), 0, st>>>(
+                g, cf.bx, cf.by, cf.bz, cf.scale, w, f, x, color, (T)omega, zero_init ? 1 : 0, k0);
+    } else {
+        if (i32)
+            rbgs_kernel<T, T, false, true><<<gr, dim3(kTX, kTY), 0, st>>>(
+                g, cf.bx, cf.by, cf.bz, cf.scale, w, f, x, color, (T)omega, zero_init ? 1 : 0, k0);
+        else
+            rbgs_kernel<T, T, false, false><<<gr, dim3(kTX, kTY), 0, st>>>(
+                g, cf.bx, cf.by, cf.bz, cf.scale, w, f, x, color, (T)omega, zero_init ? 1 : 0, k0);
+    }
+    count_launch();
+}
+
+void launch_rbgs_h(const Geo& g, const __half* const b[3], float scale, const float* f, float* x,
+                   int color, double omega, bool zero_init, cudaStream_t st, int k0, int k1) {
+    if (k1 < 0) k1 = g.nz;
+    const int npair = (g.nx + 1) / 2;
+    dim3 gr((npair + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, k1 - k0);
+    if (fits_i32(g))
+        rbgs_kernel<float, __half, false, true><<<gr, dim3(kTX, kTY), 0, st>>>(
+            g, b[0], b[1], b[2], scale, nullptr, f, x, color, (float)omega, zero_init ? 1 : 0, k0);
     else
-        rbgs_kernel<T, false><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, w, f, x, color, (T)omega,
-                                                             zero_init ? 1 : 0, k0);
+        rbgs_kernel<float, __half, false, false><<<gr, dim3(kTX, kTY), 0, st>>>(
+            g, b[0], b[1], b[2], scale, nullptr, f, x, color, (float)omega, zero_init ? 1 : 0, k0);
     count_launch();
 }
 
@@ -697,8 +730,9 @@ void launch_jacobi(const Geo& g, const Coef<T>& cf, const T* w, const T* f, cons
 
 // Coarse right-hand side: the average over the children of the fine residual
 // f - A x (restriction R = P^T / #children for the piecewise-constant P).
-template <typename T>
-__global__ void restrict_residual_kernel(Geo fg, Coef<T> cf, const T* __restrict__ f,
+template <typename T, typename TB, bool I32>
+__global__ void restrict_residual_kernel(Geo fg, const TB* __restrict__ bx, const TB* __restrict__ by,
+                                         const TB* __restrict__ bz, T scale, const T* __restrict__ f,
                                          const T* __restrict__ x, Geo cg, int fa0, int fa1,
                                          int fa2, T* __restrict__ fc) {
     const int I = blockIdx.x * kTX + threadIdx.x;
@@ -710,10 +744,17 @@ __global__ void restrict_residual_kernel(Geo fg, Coef<T> cf, const T* __restrict
         for (int dj = 0; dj < fa1; ++dj)
             for (int di = 0; di < fa0; ++di) {
                 const int i = I * fa0 + di, j = J * fa1 + dj, k = K * fa2 + dk;
-                const int64_t c = fg.cidx(i, j, k);
                 Stencil<T> s;
-                load_stencil(fg, cf, i, j, k, s);
-                sum += f[c] - apply_A(s, x, x[c], cf.scale);
+                int64_t c;
+                if (I32) {
+                    int c32;
+                    load_stencil_fast<T>(fg, bx, by, bz, i, j, k, s, c32);
+                    c = c32;
+                } else {
+                    c = fg.cidx(i, j, k);
+                    load_stencil_as<T>(fg, bx, by, bz, i, j, k, s);
+                }
+                sum += f[c] - apply_A(s, x, x[c], scale);
             }
     fc[cg.cidx(I, J, K)] = sum / T(fa0 * fa1 * fa2);
 }
@@ -722,9 +763,40 @@ template <typename T>
 void launch_restrict_residual(const Geo& fine, const Coef<T>& cf, const T* f, const T* x,
                              const Geo& coarse, const int fac[3], T* fc, cudaStream_t st) {
     dim3 gr((coarse.nx + kTX - 1) / kTX, (coarse.ny + kTY - 1) / kTY, coarse.nz);
-    restrict_residual_kernel<T><<<gr, dim3(kTX, kTY), 0, st>>>(fine, cf, f, x, coarse, fac[0],
-                                                               fac[1], fac[2], fc);
+    if (fits_i32(fine))
+        restrict_residual_kernel<T, T, true><<<gr, dim3(kTX, kTY), 0, st>>>(
+            fine, cf.bx, cf.by, cf.bz, cf.scale, f, x, coarse, fac[0], fac[1], fac[2], fc);
+    else
+        restrict_residual_kernel<T, T, false><<<gr, dim3(kTX, kTY), 0, st>>>(
+            fine, cf.bx, cf.by, cf.bz, cf.scale, f, x, coarse, fac[0], fac[1], fac[2], fc);
     count_launch();
+}
+
+void launch_restrict_residual_h(const Geo& fine, const __half* const b[3], float scale, const float* f,
+                                const float* x, const Geo& coarse, const int fac[3], float* fc,
+                                cudaStream_t st) {
+    dim3 gr((coarse.nx + kTX - 1) / kTX, (coarse.ny + kTY - 1) / kTY, coarse.nz);
+    if (fits_i32(fine))
+        restrict_residual_kernel<float, __half, true><<<gr, dim3(kTX, kTY), 0, st>>>(
+            fine, b[0], b[1], b[2], scale, f, x, coarse, fac[0], fac[1], fac[2], fc);
+    else
+        restrict_residual_kernel<float, __half, false><<<gr, dim3(kTX, kTY), 0, st>>>(
+            fine, b[0], b[1], b[2], scale, f, x, coarse, fac[0], fac[1], fac[2], fc);
+    count_launch();
+}
+
+// FP16 copies of the (unscaled) face coefficients for the level-0 V-cycle
+__global__ void convert_beta_half_kernel(int64_t n, const double* __restrict__ b, __half* __restrict__ out) {
+    PARIS_EW_FOR(c, n) out[c] = __double2half(b[c]);
+}
+
+void launch_convert_beta_half(const Geo& g, const double* const b64[3], __half* const out[3],
+                              cudaStream_t st) {
+    for (int a = 0; a < 3; ++a) {
+        const int64_t n = g.nface(a);
+        convert_beta_half_kernel<<<elementwise_blocks(n), kRedThreads, 0, st>>>(n, b64[a], out[a]);
+        count_launch();
+    }
 }
 
 template <typename T>
@@ -751,6 +823,7 @@ void launch_prolong_add(const Geo& fine, const Geo& coarse, const int fac[3], co
 
 // FP64 residual r = f - A x with fused norms; the mixed form also writes the
 // scaled FP32 copy r32 = scale * r that the inner solve starts from.
+template <bool I32>
 __global__ void __launch_bounds__(kTX* kTY) residual64_kernel(Geo g, Coef<double> cf,
                                                               const double* __restrict__ f,
                                                               const double* __restrict__ x,
@@ -764,9 +837,16 @@ __global__ void __launch_bounds__(kTX* kTY) residual64_kernel(Geo g, Coef<double
         const double sc = r32 ? s->scale : 0.0;
         const int k0 = blockIdx.z * kZ, k1 = min(k0 + kZ, g.nz);
         PARIS_ZLOOP(k0, k1, {
-            const int64_t c = g.cidx(i, j, k);
             Stencil<double> st;
-            load_stencil(g, cf, i, j, k, st);
+            int64_t c;
+            if (I32) {
+                int c32;
+                load_stencil_fast<double>(g, cf.bx, cf.by, cf.bz, i, j, k, st, c32);
+                c = c32;
+            } else {
+                c = g.cidx(i, j, k);
+                load_stencil(g, cf, i, j, k, st);
+            }
             double r = f[c] - apply_A(st, x, x[c], cf.scale);
             if (r64) r64[c] = r;
             if (r32) r32[c] = (float)(r * sc);
@@ -783,14 +863,17 @@ int64_t launch_residual64(const Geo& g, const Coef<double>& cf, const double* f,
                           double* r64, float* r32, const Scal* s, double* partials,
                           cudaStream_t st) {
     dim3 gr = tile_grid(g, kZ);
-    residual64_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, f, x, r64, r32, s, partials);
+    if (fits_i32(g))
+        residual64_kernel<true><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, f, x, r64, r32, s, partials);
+    else
+        residual64_kernel<false><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, f, x, r64, r32, s, partials);
     count_launch();
     return nblocks_of(gr);
 }
 
 // q = A d and the partial sums of d . q (accumulated per thread in T,
 // across threads and blocks in FP64).
-template <typename T>
+template <typename T, bool I32>
 __global__ void __launch_bounds__(kTX* kTY) matvec_dot_kernel(Geo g, Coef<T> cf,
                                                              const T* __restrict__ d,
                                                              T* __restrict__ q,
@@ -801,9 +884,16 @@ __global__ void __launch_bounds__(kTX* kTY) matvec_dot_kernel(Geo g, Coef<T> cf,
     if (i < g.nx && j < g.ny) {
         const int k0 = blockIdx.z * kZ, k1 = min(k0 + kZ, g.nz);
         PARIS_ZLOOP(k0, k1, {
-            const int64_t c = g.cidx(i, j, k);
             Stencil<T> st;
-            load_stencil(g, cf, i, j, k, st);
+            int64_t c;
+            if (I32) {
+                int c32;
+                load_stencil_fast<T>(g, cf.bx, cf.by, cf.bz, i, j, k, st, c32);
+                c = c32;
+            } else {
+                c = g.cidx(i, j, k);
+                load_stencil(g, cf, i, j, k, st);
+            }
             const T dc = d[c];
             const T qc = apply_A(st, d, dc, cf.scale);
             q[c] = qc;
@@ -819,7 +909,10 @@ template <typename T>
 int64_t launch_matvec_dot(const Geo& g, const Coef<T>& cf, const T* d, T* q, double* partials,
                           cudaStream_t st) {
     dim3 gr = tile_grid(g, kZ);
-    matvec_dot_kernel<T><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, d, q, partials);
+    if (fits_i32(g))
+        matvec_dot_kernel<T, true><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, d, q, partials);
+    else
+        matvec_dot_kernel<T, false><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, d, q, partials);
     count_launch();
     return nblocks_of(gr);
 }

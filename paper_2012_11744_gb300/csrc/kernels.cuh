@@ -110,6 +110,15 @@ void launch_jacobi(const Geo& g, const Coef<T>& cf, const T* w, const T* f, cons
 template <typename T>
 void launch_restrict_residual(const Geo& fine, const Coef<T>& cf, const T* f, const T* x,
                              const Geo& coarse, const int fac[3], T* fc, cudaStream_t st);
+// FP32 V-cycle with FP16 storage of the (unscaled) level-0 coefficients:
+// the colour pass and the residual restriction of the finest level.
+void launch_rbgs_h(const Geo& g, const __half* const b[3], float scale, const float* f, float* x,
+                   int color, double omega, bool zero_init, cudaStream_t st, int k0 = 0, int k1 = -1);
+void launch_restrict_residual_h(const Geo& fine, const __half* const b[3], float scale, const float* f,
+                                const float* x, const Geo& coarse, const int fac[3], float* fc,
+                                cudaStream_t st);
+void launch_convert_beta_half(const Geo& g, const double* const b64[3], __half* const out[3],
+                              cudaStream_t st);
 // x_fine += x_coarse[parent]
 template <typename T>
 void launch_prolong_add(const Geo& fine, const Geo& coarse, const int fac[3], const T* xc,

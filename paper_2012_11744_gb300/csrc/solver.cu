@@ -92,8 +92,11 @@ struct paris_ctx {
     double *f = nullptr, *r = nullptr, *z = nullptr, *d = nullptr, *q = nullptr;
     // FP32 inner vectors
     float *r32 = nullptr, *z32 = nullptr, *d32 = nullptr, *q32 = nullptr, *e32 = nullptr;
-    // level-0 FP32 coefficient copies
+    // level-0 FP32 coefficient copies (beta/h^2) and FP16 copies (beta) for
+    // the V-cycle's finest-level passes
     float* b32_0[3] = {nullptr, nullptr, nullptr};
+    __half* b16_0[3] = {nullptr, nullptr, nullptr};
+    bool half0 = false;  // the current solve reads b16_0 in the level-0 V-cycle passes
     double* partials = nullptr;
     Scal* scal = nullptr;
     Scal* scal_h = nullptr;  // pinned host mirror
@@ -219,6 +222,7 @@ paris_status alloc_ctx(paris_ctx* c) {
     c->e32 = m.get<float>(N);
     for (int a = 0; a < 3; ++a) {
         c->b32_0[a] = m.get<float>(c->g0.nface(a));
+        c->b16_0[a] = m.get<__half>(c->g0.nface(a));
         c->beta[a] = m.get<double>(c->g0.nface(a));
     }
     c->rhs = m.get<double>(N);
@@ -343,13 +347,27 @@ void smooth(paris_ctx* c, int l, const Coef<T>& cf, const T* f, T* x, int sweeps
         for (int s = 0; s < sweeps; ++s) {
             const bool z0 = first_zero && s == 0;
             const int c0 = reverse ? 1 : 0;
+            // FP32 solve, finest level: coefficients from the FP16 copies
+            const bool h16 = sizeof(T) == 4 && l == 0 && c->half0;
+            const double bsz = h16 ? 2.0 : (double)sz;
+            auto pass = [&](int color, bool zero, int a, int b) {
+                if constexpr (sizeof(T) == 4) {
+                    if (h16) {
+                        // FP16 arrays hold beta itself: scale by 1/h^2 in the kernel
+                        launch_rbgs_h(L.g, c->b16_0, (float)(1.0 / (c->grid.h * c->grid.h)), f, x, color,
+                                      o.omega, zero, c->st, a, b);
+                        return;
+                    }
+                }
+                launch_rbgs<T>(L.g, cf, Prec<T>::w(L), f, x, color, o.omega, zero, c->st, a, b);
+            };
             auto first = [&](int a, int b) {
-                ProfScope ps(c, cls, (z0 ? 2 * n * sz : (2.5 * n + nb) * sz) * (b - a) * per_plane);
-                launch_rbgs<T>(L.g, cf, Prec<T>::w(L), f, x, c0, o.omega, z0, c->st, a, b);
+                ProfScope ps(c, cls, (z0 ? 2 * n * sz : 2.5 * n * sz + nb * bsz) * (b - a) * per_plane);
+                pass(c0, z0, a, b);
             };
             auto second = [&](int a, int b) {
-                ProfScope ps(c, cls, (2.5 * n + nb) * sz * (b - a) * per_plane);
-                launch_rbgs<T>(L.g, cf, Prec<T>::w(L), f, x, 1 - c0, o.omega, false, c->st, a, b);
+                ProfScope ps(c, cls, (2.5 * n * sz + nb * bsz) * (b - a) * per_plane);
+                pass(1 - c0, false, a, b);
             };
             if (!slabs) {
                 first(0, nz);
@@ -402,8 +420,16 @@ void vdown(paris_ctx* c, const Coef<T>& c0, const T* f0, T* x0, int l) {
     else cudaMemsetAsync(x, 0, sizeof(T) * c->lv[l].g.ncell(), c->st);
     Level& C = c->lv[l + 1];
     const double n = (double)c->lv[l].g.ncell();
+    const bool h16 = sizeof(T) == 4 && l == 0 && c->half0;
     ProfScope ps(c, l == 0 ? PARIS_K_RESTRICT0 : -1,
-                 (2 * n + beta_count(c->lv[l].g) + (double)C.g.ncell()) * sizeof(T));
+                 (2 * n + (double)C.g.ncell()) * sizeof(T) + beta_count(c->lv[l].g) * (h16 ? 2 : sizeof(T)));
+    if constexpr (sizeof(T) == 4) {
+        if (h16) {
+            launch_restrict_residual_h(c->lv[l].g, c->b16_0, (float)(1.0 / (c->grid.h * c->grid.h)), f, x, C.g,
+                                       C.fac, Prec<T>::f(C), c->st);
+            return;
+        }
+    }
     launch_restrict_residual<T>(c->lv[l].g, cf, f, x, C.g, C.fac, Prec<T>::f(C), c->st);
 }
 
@@ -581,10 +607,10 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
                          int max_iter) {
     const int64_t N = c->N;
     const double ih2 = 1.0 / (c->grid.h * c->grid.h);
-    {
-        const double* b64[3] = {c64.bx, c64.by, c64.bz};
-        launch_convert_beta<float>(c->g0, b64, ih2, c->b32_0, c->st);
-    }
+    const double* b64[3] = {c64.bx, c64.by, c64.bz};
+    launch_convert_beta<float>(c->g0, b64, ih2, c->b32_0, c->st);
+    c->half0 = c->opts.half_coefficients != 0;
+    if (c->half0) launch_convert_beta_half(c->g0, b64, c->b16_0, c->st);
     Coef<float> c32{c->b32_0[0], c->b32_0[1], c->b32_0[2], 1.0f};
     setup_hierarchy<float>(c, c32);
     double prev_rr = INFINITY;
@@ -661,6 +687,7 @@ void paris_default_opts(paris_opts* o) {
     o->inner_tol = 1e-5;
     o->fallback = 1;
     o->slab_planes = 0;
+    o->half_coefficients = 0;
 }
 
 const char* paris_status_string(paris_status s) {

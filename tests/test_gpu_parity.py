@@ -159,7 +159,8 @@ def test_fused_smoother_bit_identical_to_two_pass(paris, grid, precision):
     b = oracle.divergence(grid, pr.u, pr.v, pr.w, pr.dt)
     out = []
     for sm, slab in ((paris.SMOOTH_RBGS, 0), (paris.SMOOTH_RBGS_2PASS, 0), (paris.SMOOTH_RBGS_2PASS, 16)):
-        with ctx_for(paris, grid, precision=getattr(paris, precision), smoother=sm, slab_planes=slab) as ctx:
+        with ctx_for(paris, grid, precision=getattr(paris, precision), smoother=sm, slab_planes=slab,
+                     half_coefficients=0) as ctx:
             p = torch.zeros(grid.shape, dtype=torch.float64, device="cuda")
             st = ctx.poisson_solve(*(dev(x) for x in beta), dev(b), p)
             out.append((host(p), st["iters"]))
@@ -216,3 +217,18 @@ def test_unaligned_pressure_buffer(paris):
             assert p.data_ptr() % 16 == 8
             st = ctx.projection_step(dev(pr.C), pr.rho1, pr.rho2, pr.dt, u, v, w, p)
             _check_solution(grid, pr, ref, host(p), (host(u), host(v), host(w)), st)
+
+
+@pytest.mark.parametrize("half", [0, 1])
+def test_mixed_with_and_without_fp16_coefficients(paris, half):
+    """FP16 copies of beta in the finest-level V-cycle passes change the
+    preconditioner only: the solve still meets every bar."""
+    pr = pi.config2(n=64)
+    g = pr.grid
+    ref = oracle.projection_step(g, pr.C, pr.rho1, pr.rho2, pr.dt, pr.u, pr.v, pr.w)
+    with ctx_for(paris, g, precision=paris.MIXED, half_coefficients=half) as ctx:
+        u, v, w = dev(pr.u), dev(pr.v), dev(pr.w)
+        p = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+        st = ctx.projection_step(dev(pr.C), pr.rho1, pr.rho2, pr.dt, u, v, w, p)
+        assert st["fell_back"] == 0 and st["iters"] <= 30, st
+        _check_solution(g, pr, ref, host(p), (host(u), host(v), host(w)), st)
