@@ -54,9 +54,9 @@ struct V16<double> {
          c += (int64_t)gridDim.x * blockDim.x)
 
 // z-loop over [k0, k1)
-#define PARIS_ZLOOP(k0, k1, BODY)              \
+#define PARIS_ZLOOP(k0, k1, ...)               \
     for (int k = (k0); k < (k1); ++k) {        \
-        BODY                                   \
+        __VA_ARGS__                            \
     }
 
 inline dim3 tile_grid(const Geo& g, int zper) {
@@ -478,6 +478,16 @@ void launch_coarse_beta(const Geo& fine, const Coef<T>& cf, const Geo& coarse, c
     }
 }
 
+// 1 / sum of the six face coefficients (the red-black sweeps' inverse diagonal)
+__device__ inline float rcp_rn(float d) { return __frcp_rn(d); }  // == 1.0f / d
+__device__ inline double rcp_rn(double d) { return 1.0 / d; }
+
+template <typename T>
+__device__ inline T inv_sum6(const T (&b)[6]) {
+    const T d = ((b[0] + b[1]) + (b[2] + b[3])) + (b[4] + b[5]);
+    return d > T(0) ? rcp_rn(d) : T(0);
+}
+
 // w = 1 / sum_f beta_f (unscaled inverse diagonal; the smoother divides the
 // right-hand side by the level's scale).
 template <typename T>
@@ -488,8 +498,7 @@ __global__ void inv_diag_kernel(Geo g, Coef<T> cf, T* __restrict__ w) {
     if (i >= g.nx || j >= g.ny) return;
     Stencil<T> s;
     load_stencil(g, cf, i, j, k, s);
-    T d = ((s.b[0] + s.b[1]) + (s.b[2] + s.b[3])) + (s.b[4] + s.b[5]);
-    w[g.cidx(i, j, k)] = d > T(0) ? T(1) / d : T(0);
+    w[g.cidx(i, j, k)] = inv_sum6(s.b);
 }
 
 template <typename T>
@@ -599,12 +608,6 @@ void launch_coarse_solve(const Geo& g, const double* inv, const T* f, T* x, cuda
 // w_c = 1/sum_f beta_f.  One thread per x-pair (2t, 2t+1) of a row updates
 // the member of colour `color` ((i+j+k) even = red = 0).  With zero_init the
 // incoming x is taken as zero and the other member of the pair is zeroed.
-// 1 / sum of the six face coefficients, in the same order as inv_diag_kernel
-template <typename T>
-__device__ inline T inv_sum6(const T (&b)[6]) {
-    const T d = ((b[0] + b[1]) + (b[2] + b[3])) + (b[4] + b[5]);
-    return d > T(0) ? T(1) / d : T(0);
-}
 
 template <typename T, typename TB, bool USEW, bool I32>
 __global__ void __launch_bounds__(kTX* kTY) rbgs_kernel(Geo g, const TB* __restrict__ bx,
@@ -810,9 +813,35 @@ __global__ void prolong_add_kernel(Geo fg, Geo cg, int fa0, int fa1, int fa2,
     x[fg.cidx(i, j, k)] += xc[cg.cidx(i >> (fa0 - 1), j >> (fa1 - 1), k >> (fa2 - 1))];
 }
 
+// x_fine += x_coarse[parent] for four x-consecutive fine cells per thread
+// (all axes halved, nx % 4 == 0, 16-byte aligned x)
+__global__ void prolong_add4_kernel(Geo fg, Geo cg, const float* __restrict__ xc, float* __restrict__ x) {
+    const int q = blockIdx.x * kTX + threadIdx.x;  // quad index along x
+    const int j = blockIdx.y * kTY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (4 * q >= fg.nx || j >= fg.ny) return;
+    const int64_t c = fg.cidx(4 * q, j, k);
+    const int64_t cc = cg.cidx(2 * q, j >> 1, k >> 1);
+    float4 v = *reinterpret_cast<const float4*>(x + c);
+    const float a = xc[cc], b = xc[cc + 1];
+    v.x += a;
+    v.y += a;
+    v.z += b;
+    v.w += b;
+    *reinterpret_cast<float4*>(x + c) = v;
+}
+
 template <typename T>
 void launch_prolong_add(const Geo& fine, const Geo& coarse, const int fac[3], const T* xc, T* x,
                         cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        if (fac[0] == 2 && fac[1] == 2 && fac[2] == 2 && fine.nx % 4 == 0 && aligned16(x)) {
+            dim3 gr((fine.nx / 4 + kTX - 1) / kTX, (fine.ny + kTY - 1) / kTY, fine.nz);
+            prolong_add4_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(fine, coarse, (const float*)xc, (float*)x);
+            count_launch();
+            return;
+        }
+    }
     dim3 gr((fine.nx + kTX - 1) / kTX, (fine.ny + kTY - 1) / kTY, fine.nz);
     prolong_add_kernel<T><<<gr, dim3(kTX, kTY), 0, st>>>(fine, coarse, fac[0], fac[1], fac[2], xc,
                                                          x);
