@@ -100,6 +100,15 @@ typedef struct {
     int half_coefficients; /* MIXED: the finest-level V-cycle passes read FP16 copies of
                               beta (the FP32 inner operator and the FP64 residual keep full
                               precision, so this changes speed, not the converged p) (0) */
+    int level0_density;   /* MIXED, paris_projection_step only: the finest level's FP32
+                             operator (colour passes, residual restriction, inner CG
+                             product, level-1 coefficients) is rebuilt in registers from an
+                             FP32 array of rho/2 (Eq. muH) instead of being read from three
+                             FP32 face arrays: 4 instead of 12 bytes per cell and pass.  Used
+                             when nx, ny, nz are even, the second level halves every axis,
+                             the smoother is PARIS_SMOOTH_RBGS_2PASS and half_coefficients is
+                             0; otherwise ignored.  The FP64 residual, the converged p and
+                             the projection keep the FP64 beta (1) */
 } paris_opts;
 
 typedef struct {

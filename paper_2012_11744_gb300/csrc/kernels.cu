@@ -189,58 +189,91 @@ void finalize(const double* partials, int64_t nblocks, int nv, int maxmask, Scal
 
 // ------------------------------------------------------- face coefficients ---
 
-// 2/s for s > 0 by Newton-Raphson on the reciprocal: y0 = 1/s in FP32,
-// then two FP64 steps y <- y + y (1 - s y), each doubling the correct bits
-// (24 -> 48 -> full double precision; the result is within one ulp of the
-// correctly rounded quotient).  FP64 division costs several times more on
-// this GPU, whose FP64 rate is 1/64 of its FP32 rate.
-__device__ inline double two_over(double s) {
-    double y = (double)__frcp_rn((float)s);
-    double e = fma(-s, y, 1.0);
-    y = fma(y, e, y);
-    e = fma(-s, y, 1.0);
-    y = fma(y, e, y);
-    return 2.0 * y;
+// 1/s for s > 0 without an FP64 division and without FP64<->FP32
+// conversions (both run at the FP64 rate, 1/64 of the FP32 rate on this
+// GPU): an FP32 estimate is formed from the leading bits of s by re-biasing
+// the exponent in integer arithmetic (20 of the 52 fraction bits kept, so
+// the estimate is within 2^-20 of s), inverted with the FP32 approximate
+// reciprocal (1 ulp), re-biased back into an FP64 y0 with |1 - s y0| < 2^-19.
+// One third-order Newton-Raphson step y0 (1 + e + e^2), e = 1 - s y0,
+// leaves a truncation error e^3 < 2^-57 relative, below half an ulp, so the
+// result is within one ulp of the correctly rounded 1/s.  Values of s
+// outside the exponent window [2^-123, 2^117) (or s <= 0, NaN) take the
+// FP64 division.
+__device__ inline double recip64(double s) {
+    const int hi = __double2hiint(s);
+    if (hi < (900 << 20) || hi >= (1140 << 20)) return 1.0 / s;
+    const float sf = __int_as_float((hi - (896 << 20)) << 3);
+    float yf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(sf));
+    const unsigned yb = (unsigned)__float_as_int(yf);
+    const double y0 = __hiloint2double((int)((yb >> 3) + (896u << 20)), (int)(yb << 29));
+    const double e = fma(-s, y0, 1.0);
+    return fma(y0, fma(e, e, e), y0);
 }
+
+constexpr int kFSeg = 16;  // planes per thread of the face-coefficient kernel
 
 // Eq. muH: rho = rho1 C + rho2 (1 - C); beta_f = 1/rho_f with rho_f the mean
 // of the two cells (the paper's "interpolation of 1/rho" read as the mean of
-// rho, then inverted); wall faces 0 (Sec. 3.8).  One thread per cell writes
-// the - face of each axis, and the last cell of a wall axis also writes the
-// + wall face.
-__global__ void face_coeffs_kernel(Geo g, const double* __restrict__ C, double rho1, double rho2,
-                                   double* __restrict__ bx, double* __restrict__ by,
-                                   double* __restrict__ bz) {
-    const int i = blockIdx.x * kTX + threadIdx.x;
-    const int j = blockIdx.y * kTY + threadIdx.y;
-    const int k = blockIdx.z;
-    if (i >= g.nx || j >= g.ny) return;
-    // Eq. muH as written, rho1 C + rho2 (1 - C): both terms are non-negative,
-    // so there is no cancellation even when rho1 << rho2 and C -> 1
-    auto rho = [&](double c) { return fma(rho1, c, rho2 * (1.0 - c)); };
-    const double rc = rho(C[g.cidx(i, j, k)]);
-    AxisNb ax = axis_nb(i, g.nx, g.wx), ay = axis_nb(j, g.ny, g.wy), az = axis_nb(k, g.nz, g.wz);
-    {
-        double rl = rho(C[g.cidx(ax.m, j, k)]);
-        bx[g.fx(i, j, k)] = ax.wm ? 0.0 : two_over(rl + rc);
-        if (g.wx && i == g.nx - 1) bx[g.fx(g.nx, j, k)] = 0.0;
-    }
-    {
-        double rl = rho(C[g.cidx(i, ay.m, k)]);
-        by[g.fy(i, j, k)] = ay.wm ? 0.0 : two_over(rl + rc);
-        if (g.wy && j == g.ny - 1) by[g.fy(i, g.ny, k)] = 0.0;
-    }
-    {
-        double rl = rho(C[g.cidx(i, j, az.m)]);
-        bz[g.fz(i, j, k)] = az.wm ? 0.0 : two_over(rl + rc);
-        if (g.wz && k == g.nz - 1) bz[g.fz(i, j, g.nz)] = 0.0;
+// rho, then inverted); wall faces 0 (Sec. 3.8).  Computed as rh = rho/2 from
+// rho1/2 and rho2/2 (exact scalings), beta_f = 1/(rh_L + rh_R).
+// A thread owns the column (i, j) over a segment of planes and writes the -
+// face of each axis (the last cell of a wall axis also writes the + wall
+// face).  Each cell's rh is evaluated once: the z-neighbour's is carried in
+// a register, the x- and y-neighbours' come through a shared-memory tile
+// whose halo row and column are evaluated by one warp each.  Optionally
+// writes the FP32 copy of rho/2 that the mixed solve's finest level reads.
+__global__ void __launch_bounds__(kTX* kTY) face_coeffs_kernel(Geo g, const double* __restrict__ C,
+                                                              double r1h, double r2h,
+                                                              double* __restrict__ bx,
+                                                              double* __restrict__ by,
+                                                              double* __restrict__ bz,
+                                                              float* __restrict__ rh32) {
+    __shared__ double sh[2][kTY + 1][kTX + 1];  // [plane parity][1 + row][1 + column]
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int i = blockIdx.x * kTX + tx, j = blockIdx.y * kTY + ty;
+    const bool in = i < nx && j < ny;
+    const int ic = min(i, nx - 1), jc = min(j, ny - 1);  // idle threads shadow a cell
+    const int kb = blockIdx.z * kFSeg, ke = min(kb + kFSeg, nz);
+    const int64_t pl = (int64_t)nx * ny;
+    auto rho = [&](double c) { return fma(r1h, c, r2h * (1.0 - c)); };
+    // halo cells: row j0-1 (warp 0) and column i0-1 (lanes 0..7 of warp 1)
+    const int i0 = blockIdx.x * kTX, j0 = blockIdx.y * kTY;
+    const int hx = i0 > 0 ? i0 - 1 : nx - 1;  // periodic wrap (walls: beta 0, value unused)
+    const int hy = j0 > 0 ? j0 - 1 : ny - 1;
+    const int hrow = min(j0 + tx, ny - 1);       // row of the column-halo cell of lane tx
+    const int hcol = min(i0 + tx, nx - 1);       // column of the row-halo cell of lane tx
+    const bool xw = g.wx && i == 0, yw = g.wy && j == 0;
+    double rzm = rho(C[(int64_t)(kb > 0 ? kb - 1 : nz - 1) * pl + (int64_t)jc * nx + ic]);
+    for (int k = kb; k < ke; ++k) {
+        const int64_t plane = (int64_t)k * pl;
+        const int64_t c = plane + (int64_t)jc * nx + ic;
+        const double rc = rho(C[c]);
+        const int b = k & 1;
+        sh[b][ty + 1][tx + 1] = rc;
+        if (ty == 0) sh[b][0][tx + 1] = rho(C[plane + (int64_t)hy * nx + hcol]);
+        if (ty == 1 && tx < kTY) sh[b][tx + 1][0] = rho(C[plane + (int64_t)hrow * nx + hx]);
+        __syncthreads();
+        const double rxm = sh[b][ty + 1][tx], rym = sh[b][ty][tx + 1];
+        if (in) {
+            bx[g.fx(i, j, k)] = xw ? 0.0 : recip64(rxm + rc);
+            by[g.fy(i, j, k)] = yw ? 0.0 : recip64(rym + rc);
+            bz[g.fz(i, j, k)] = (g.wz && k == 0) ? 0.0 : recip64(rzm + rc);
+            if (g.wx && i == nx - 1) bx[g.fx(nx, j, k)] = 0.0;
+            if (g.wy && j == ny - 1) by[g.fy(i, ny, k)] = 0.0;
+            if (g.wz && k == nz - 1) bz[g.fz(i, j, nz)] = 0.0;
+            if (rh32) rh32[c] = (float)rc;
+        }
+        rzm = rc;
     }
 }
 
 void launch_face_coeffs(const Geo& g, const double* C, double rho1, double rho2, double* bx,
-                        double* by, double* bz, cudaStream_t st) {
-    dim3 gr((g.nx + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, g.nz);
-    face_coeffs_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(g, C, rho1, rho2, bx, by, bz);
+                        double* by, double* bz, float* rh32, cudaStream_t st) {
+    dim3 gr((g.nx + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, (g.nz + kFSeg - 1) / kFSeg);
+    face_coeffs_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(g, C, 0.5 * rho1, 0.5 * rho2, bx, by, bz, rh32);
     count_launch();
 }
 

@@ -54,8 +54,9 @@ void finalize(const double* partials, int64_t nblocks, int nv, int maxmask, Scal
               double param, cudaStream_t st);
 
 // ---------------------------------------------------------- field steps ---
+// beta = 2/(rho_L + rho_R) (FP64); rh32 (may be null): FP32 copy of rho/2
 void launch_face_coeffs(const Geo& g, const double* C, double rho1, double rho2, double* bx,
-                        double* by, double* bz, cudaStream_t st);
+                        double* by, double* bz, float* rh32, cudaStream_t st);
 // rhs = div(u)/(h dt); partials: (sum rhs, max |rhs|, nonfinite count)
 int64_t launch_divergence(const Geo& g, const double* u, const double* v, const double* w,
                           double inv_hdt, double* rhs, double* partials, cudaStream_t st);
@@ -123,6 +124,24 @@ void launch_convert_beta_half(const Geo& g, const double* const b64[3], __half* 
 template <typename T>
 void launch_prolong_add(const Geo& fine, const Geo& coarse, const int fac[3], const T* xc,
                         T* x, cudaStream_t st);
+
+// ------------------------------------- level 0 rebuilt from the cell densities ---
+// rh: FP32 half-densities rho/2 of the finest level (Eq. muH); the kernels
+// form beta_f = 1/(rh_L + rh_R) in registers and apply 1/h^2 themselves.
+// even nx, ny, nz and 32-bit offsets
+bool rho0_fits(const Geo& g);
+void launch_rbgs_rho(const Geo& g, const float* rh, double h, const float* f, float* x, int color,
+                     double omega, bool zero_init, cudaStream_t st, int k0 = 0, int k1 = -1);
+// q = A d; partials (d . q); returns the number of blocks
+int64_t launch_matvec_rho(const Geo& g, const float* rh, double h, const float* d, float* q,
+                          double* partials, cudaStream_t st);
+int64_t rho0_matvec_blocks(const Geo& g);
+// coarse f = mean over the 2x2x2 children of (f - A x); coarse = every axis halved
+void launch_restrict_rho(const Geo& g, const float* rh, double h, const float* f, const float* x,
+                         const Geo& coarse, float* fc, cudaStream_t st);
+// scaled FP32 coefficients of the level with every axis halved
+void launch_coarse_beta_rho(const Geo& fine, const float* rh, double h, const Geo& coarse, float* out[3],
+                            cudaStream_t st);
 
 // ------------------------------------------------------------ Krylov ------
 // r = f - A x (FP64), optional r32 = scale * r; partials (||r||^2, max|r|, nonfinite)

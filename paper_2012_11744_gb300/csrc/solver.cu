@@ -97,6 +97,10 @@ struct paris_ctx {
     float* b32_0[3] = {nullptr, nullptr, nullptr};
     __half* b16_0[3] = {nullptr, nullptr, nullptr};
     bool half0 = false;  // the current solve reads b16_0 in the level-0 V-cycle passes
+    // FP32 half-densities rho/2 from which the finest level's FP32 kernels
+    // rebuild their coefficients (paris_opts.level0_density)
+    float* rh32 = nullptr;
+    bool rho0 = false;  // the current solve's level-0 FP32 kernels read rh32 instead of b32_0
     double* partials = nullptr;
     Scal* scal = nullptr;
     Scal* scal_h = nullptr;  // pinned host mirror
@@ -144,6 +148,7 @@ bool valid_opts(const paris_opts* o) {
     if (o->coarse_max_cells < 1 || o->coarse_max_cells > kMaxDense) return false;
     if (!(o->inner_tol > 0.0 && o->inner_tol < 1.0)) return false;
     if (o->slab_planes < 0) return false;
+    if (o->level0_density != 0 && o->level0_density != 1) return false;
     return true;
 }
 
@@ -226,8 +231,9 @@ paris_status alloc_ctx(paris_ctx* c) {
         c->beta[a] = m.get<double>(c->g0.nface(a));
     }
     c->rhs = m.get<double>(N);
+    if (rho0_fits(c->g0)) c->rh32 = m.get<float>(N);
     // block partials: up to 4 values per block of the largest reducing grid
-    c->partials = m.get<double>(max_reduce_blocks(c->g0) * 4);
+    c->partials = m.get<double>(std::max(max_reduce_blocks(c->g0), rho0_matvec_blocks(c->g0)) * 4);
     c->scal = m.get<Scal>(1);
     if (m.err != cudaSuccess) return m.err == cudaErrorMemoryAllocation ? PARIS_ERR_NO_MEMORY : PARIS_ERR_CUDA;
     if (cudaMallocHost(&c->scal_h, sizeof(Scal)) != cudaSuccess) return PARIS_ERR_NO_MEMORY;
@@ -312,6 +318,12 @@ void setup_hierarchy(paris_ctx* c, const Coef<T>& c0) {
         double ratio2[3];
         for (int a = 0; a < 3; ++a) ratio2[a] = (double)L.fac[a] * L.fac[a];
         T* out[3] = {Prec<T>::b(L, 0), Prec<T>::b(L, 1), Prec<T>::b(L, 2)};
+        if constexpr (sizeof(T) == 4) {
+            if (l == 1 && c->rho0) {
+                launch_coarse_beta_rho(F.g, c->rh32, c->grid.h, L.g, out, c->st);
+                continue;
+            }
+        }
         launch_coarse_beta<T>(F.g, cf, L.g, L.fac, ratio2, out, c->st);
     }
     // inverse diagonals: read by the FP64 smoothers and by Jacobi; the FP32
@@ -347,11 +359,24 @@ void smooth(paris_ctx* c, int l, const Coef<T>& cf, const T* f, T* x, int sweeps
         for (int s = 0; s < sweeps; ++s) {
             const bool z0 = first_zero && s == 0;
             const int c0 = reverse ? 1 : 0;
-            // FP32 solve, finest level: coefficients from the FP16 copies
+            // FP32 solve, finest level: coefficients from the FP16 copies or
+            // rebuilt from the cell densities
             const bool h16 = sizeof(T) == 4 && l == 0 && c->half0;
+            const bool v0 = sizeof(T) == 4 && l == 0 && c->rho0;
             const double bsz = h16 ? 2.0 : (double)sz;
+            // bytes per pass: x at every cell (neighbours and the updated colour),
+            // f and the write of the updated colour, plus the coefficients
+            // (three face arrays, or rho/2 once); a zero-initial pass reads no x
+            // and writes both colours
+            const double b_first = v0 ? (z0 ? 2.5 : 3.0) * n * sz : (z0 ? 2 * n * sz : 2.5 * n * sz + nb * bsz);
+            const double b_second = v0 ? 3.0 * n * sz : 2.5 * n * sz + nb * bsz;
             auto pass = [&](int color, bool zero, int a, int b) {
                 if constexpr (sizeof(T) == 4) {
+                    if (v0) {
+                        launch_rbgs_rho(L.g, c->rh32, c->grid.h, (const float*)f, (float*)x, color, o.omega,
+                                        zero, c->st, a, b);
+                        return;
+                    }
                     if (h16) {
                         // FP16 arrays hold beta itself: scale by 1/h^2 in the kernel
                         launch_rbgs_h(L.g, c->b16_0, (float)(1.0 / (c->grid.h * c->grid.h)), f, x, color,
@@ -362,11 +387,11 @@ void smooth(paris_ctx* c, int l, const Coef<T>& cf, const T* f, T* x, int sweeps
                 launch_rbgs<T>(L.g, cf, Prec<T>::w(L), f, x, color, o.omega, zero, c->st, a, b);
             };
             auto first = [&](int a, int b) {
-                ProfScope ps(c, cls, (z0 ? 2 * n * sz : 2.5 * n * sz + nb * bsz) * (b - a) * per_plane);
+                ProfScope ps(c, cls, b_first * (b - a) * per_plane);
                 pass(c0, z0, a, b);
             };
             auto second = [&](int a, int b) {
-                ProfScope ps(c, cls, (2.5 * n * sz + nb * bsz) * (b - a) * per_plane);
+                ProfScope ps(c, cls, b_second * (b - a) * per_plane);
                 pass(1 - c0, false, a, b);
             };
             if (!slabs) {
@@ -421,9 +446,16 @@ void vdown(paris_ctx* c, const Coef<T>& c0, const T* f0, T* x0, int l) {
     Level& C = c->lv[l + 1];
     const double n = (double)c->lv[l].g.ncell();
     const bool h16 = sizeof(T) == 4 && l == 0 && c->half0;
+    const bool v0 = sizeof(T) == 4 && l == 0 && c->rho0;
     ProfScope ps(c, l == 0 ? PARIS_K_RESTRICT0 : -1,
-                 (2 * n + (double)C.g.ncell()) * sizeof(T) + beta_count(c->lv[l].g) * (h16 ? 2 : sizeof(T)));
+                 (2 * n + (double)C.g.ncell()) * sizeof(T) +
+                     (v0 ? n * sizeof(T) : beta_count(c->lv[l].g) * (h16 ? 2 : sizeof(T))));
     if constexpr (sizeof(T) == 4) {
+        if (v0) {
+            launch_restrict_rho(c->lv[l].g, c->rh32, c->grid.h, (const float*)f, (const float*)x, C.g,
+                                (float*)Prec<T>::f(C), c->st);
+            return;
+        }
         if (h16) {
             launch_restrict_residual_h(c->lv[l].g, c->b16_0, (float)(1.0 / (c->grid.h * c->grid.h)), f, x, C.g,
                                        C.fac, Prec<T>::f(C), c->st);
@@ -603,14 +635,38 @@ paris_status solve_fp64(paris_ctx* c, const Coef<double>& c64, double* x, SolveO
 }
 
 // Mixed precision: FP64 iterative refinement around FP32 flexible CG.
+// The level-0 FP32 kernels can rebuild their coefficients from the cell
+// densities (paris_opts.level0_density) when the grid and the smoother allow it.
+bool rho0_usable(const paris_ctx* c) {
+    const paris_opts& o = c->opts;
+    if (!o.level0_density || o.precision != PARIS_MIXED || o.smoother != PARIS_SMOOTH_RBGS_2PASS ||
+        o.half_coefficients || !c->rh32 || c->lv.size() < 3)
+        return false;
+    const Level& L1 = c->lv[1];
+    return L1.fac[0] == 2 && L1.fac[1] == 2 && L1.fac[2] == 2;
+}
+
+// Clears the per-solve level-0 mode flags on every exit path.
+struct Level0Mode {
+    paris_ctx* c;
+    ~Level0Mode() {
+        c->rho0 = false;
+        c->half0 = false;
+    }
+};
+
 paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, SolveOut& out,
-                         int max_iter) {
+                         int max_iter, bool rho0) {
     const int64_t N = c->N;
     const double ih2 = 1.0 / (c->grid.h * c->grid.h);
     const double* b64[3] = {c64.bx, c64.by, c64.bz};
-    launch_convert_beta<float>(c->g0, b64, ih2, c->b32_0, c->st);
-    c->half0 = c->opts.half_coefficients != 0;
-    if (c->half0) launch_convert_beta_half(c->g0, b64, c->b16_0, c->st);
+    Level0Mode mode_guard{c};
+    c->rho0 = rho0;
+    if (!rho0) {
+        launch_convert_beta<float>(c->g0, b64, ih2, c->b32_0, c->st);
+        c->half0 = c->opts.half_coefficients != 0;
+        if (c->half0) launch_convert_beta_half(c->g0, b64, c->b16_0, c->st);
+    }
     Coef<float> c32{c->b32_0[0], c->b32_0[1], c->b32_0[2], 1.0f};
     setup_hierarchy<float>(c, c32);
     double prev_rr = INFINITY;
@@ -637,7 +693,10 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
         finalize(c->partials, nb, 2, 0, c->scal, FIN_RHO_INIT, 0.0, c->st);
         CK(cudaMemcpyAsync(c->d32, c->z32, sizeof(float) * N, cudaMemcpyDeviceToDevice, c->st));
         for (int j = 0; j < 50 && out.iters < max_iter; ++j) {
-            {
+            if (c->rho0) {
+                ProfScope ps(c, PARIS_K_MATVEC0, 3.0 * N * 4);
+                nb = launch_matvec_rho(c->g0, c->rh32, c->grid.h, c->d32, c->q32, c->partials, c->st);
+            } else {
                 ProfScope ps(c, PARIS_K_MATVEC0, (2.0 * N + beta_count(c->g0)) * 4);
                 nb = launch_matvec_dot<float>(c->g0, c32, c->d32, c->q32, c->partials, c->st);
             }
@@ -688,6 +747,7 @@ void paris_default_opts(paris_opts* o) {
     o->fallback = 1;
     o->slab_planes = 0;
     o->half_coefficients = 0;
+    o->level0_density = 1;
 }
 
 const char* paris_status_string(paris_status s) {
@@ -814,7 +874,7 @@ paris_status paris_face_coeffs(paris_ctx* c, const double* C, double rho1, doubl
     if (!c || !C || !bx || !by || !bz) return PARIS_ERR_INVALID_ARG;
     if (!(rho1 > 0.0) || !(rho2 > 0.0) || !std::isfinite(rho1) || !std::isfinite(rho2))
         return PARIS_ERR_INVALID_ARG;
-    launch_face_coeffs(c->g0, C, rho1, rho2, bx, by, bz, c->st);
+    launch_face_coeffs(c->g0, C, rho1, rho2, bx, by, bz, nullptr, c->st);
     CK(cudaGetLastError());
     return PARIS_OK;
 }
@@ -836,10 +896,14 @@ paris_status paris_divergence(paris_ctx* c, const double* u, const double* v, co
     return PARIS_OK;
 }
 
-paris_status paris_poisson_solve(paris_ctx* c, const double* bx, const double* by,
-                                 const double* bz, const double* rhs, double* p,
-                                 paris_stats* st) {
-    if (!c || !bx || !by || !bz || !rhs || !p) return PARIS_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+
+// The solve behind paris_poisson_solve; rho0: the mixed form's level-0 FP32
+// kernels rebuild their coefficients from rh32 (filled by the caller).
+paris_status poisson_solve(paris_ctx* c, const double* bx, const double* by, const double* bz,
+                           const double* rhs, double* p, paris_stats* st, bool rho0) {
     const double ih2 = 1.0 / (c->grid.h * c->grid.h);
     Coef<double> c64{bx, by, bz, ih2};
     CK(cudaMemsetAsync(c->scal, 0, sizeof(Scal), c->st));
@@ -848,7 +912,7 @@ paris_status paris_poisson_solve(paris_ctx* c, const double* bx, const double* b
     SolveOut out;
     int fell_back = 0;
     if (c->opts.precision == PARIS_MIXED) {
-        s = solve_mixed(c, c64, p, out, c->opts.max_iter);
+        s = solve_mixed(c, c64, p, out, c->opts.max_iter, rho0);
         if (s != PARIS_OK) return s;
         if (!out.converged && !out.nonfinite && c->opts.fallback) {
             SolveOut o2;
@@ -883,6 +947,17 @@ paris_status paris_poisson_solve(paris_ctx* c, const double* bx, const double* b
     return out.converged ? PARIS_OK : PARIS_ERR_NOT_CONVERGED;
 }
 
+}  // namespace
+
+extern "C" {
+
+paris_status paris_poisson_solve(paris_ctx* c, const double* bx, const double* by,
+                                 const double* bz, const double* rhs, double* p,
+                                 paris_stats* st) {
+    if (!c || !bx || !by || !bz || !rhs || !p) return PARIS_ERR_INVALID_ARG;
+    return poisson_solve(c, bx, by, bz, rhs, p, st, false);
+}
+
 paris_status paris_project(paris_ctx* c, const double* bx, const double* by, const double* bz,
                            const double* p, double dt, double* u, double* v, double* w) {
     if (!c || !bx || !by || !bz || !p || !u || !v || !w) return PARIS_ERR_INVALID_ARG;
@@ -896,8 +971,13 @@ paris_status paris_projection_step(paris_ctx* c, const double* C, double rho1, d
                                    double dt, double* u, double* v, double* w, double* p,
                                    paris_stats* st) {
     if (!c || !C || !u || !v || !w || !p) return PARIS_ERR_INVALID_ARG;
-    paris_status s = paris_face_coeffs(c, C, rho1, rho2, c->beta[0], c->beta[1], c->beta[2]);
-    if (s != PARIS_OK) return s;
+    if (!(rho1 > 0.0) || !(rho2 > 0.0) || !std::isfinite(rho1) || !std::isfinite(rho2))
+        return PARIS_ERR_INVALID_ARG;
+    const bool use_rho0 = rho0_usable(c);
+    launch_face_coeffs(c->g0, C, rho1, rho2, c->beta[0], c->beta[1], c->beta[2],
+                       use_rho0 ? c->rh32 : nullptr, c->st);
+    CK(cudaGetLastError());
+    paris_status s;
     s = paris_divergence(c, u, v, w, dt, c->rhs, nullptr);
     if (s != PARIS_OK) return s;
     double mb = 0.0;
@@ -908,7 +988,8 @@ paris_status paris_projection_step(paris_ctx* c, const double* C, double rho1, d
         CK(cudaStreamSynchronize(c->st));
         mb = c->scal_h->mean_b;
     }
-    paris_status solve = paris_poisson_solve(c, c->beta[0], c->beta[1], c->beta[2], c->rhs, p, st);
+    paris_status solve =
+        poisson_solve(c, c->beta[0], c->beta[1], c->beta[2], c->rhs, p, st, use_rho0);
     if (solve != PARIS_OK && solve != PARIS_ERR_NOT_CONVERGED) return solve;
     if (st) st->mean_b_removed = mb;
     s = paris_project(c, c->beta[0], c->beta[1], c->beta[2], p, dt, u, v, w);

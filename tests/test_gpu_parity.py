@@ -186,10 +186,10 @@ def test_jacobi_smoother_matches_oracle(paris, grid, precision):
 @pytest.mark.parametrize("rho1,rho2", [(1000.0, 1.0), (1e-3, 7.5), (3.3e4, 2.2e-2), (1.0, 1.0)])
 def test_face_coefficient_reciprocal_within_four_ulp(paris, rho1, rho2):
     """beta = 2/(rho_L + rho_R) is computed by Newton-Raphson on the GPU (within
-    one ulp of the correctly rounded quotient).  The GPU forms rho = rho2 +
-    (rho1 - rho2) C with one fused multiply-add where the oracle rounds
-    rho1 C + rho2 (1 - C) three times, so the two rho differ by up to ~2 ulp
-    each; the bound checked over random mixtures is therefore 4 ulp."""
+    one ulp of the correctly rounded quotient).  The GPU forms rho/2 =
+    (rho1/2) C + (rho2/2)(1 - C) with one fused multiply-add where the oracle
+    rounds rho1 C + rho2 (1 - C) three times, so the two rho differ by up to
+    ~2 ulp each; the bound checked over random mixtures is therefore 4 ulp."""
     grid = pi.Grid(64, 32, 16, 1 / 64, (P, W, P))
     C = np.random.default_rng(5).uniform(0.0, 1.0, size=grid.shape)
     ref = oracle.face_coeffs(grid, C, rho1, rho2)
@@ -232,3 +232,51 @@ def test_mixed_with_and_without_fp16_coefficients(paris, half):
         st = ctx.projection_step(dev(pr.C), pr.rho1, pr.rho2, pr.dt, u, v, w, p)
         assert st["fell_back"] == 0 and st["iters"] <= 30, st
         _check_solution(g, pr, ref, host(p), (host(u), host(v), host(w)), st)
+
+
+# even grids whose second level halves every axis: the mixed projection step
+# rebuilds the finest level's FP32 operator from the volume fraction there
+VOF_GRIDS = [pi.Grid(32, 32, 32, 1 / 32), pi.Grid(64, 32, 16, 1 / 64, (P, P, W)),
+             pi.Grid(24, 20, 16, 1 / 24, (W, P, W)), pi.Grid(20, 12, 8, 0.05, (W, W, P)),
+             pi.Grid(132, 20, 36, 1 / 132, (P, W, P)), pi.Grid(16, 8, 8, 1 / 16, (W, W, W))]
+
+
+@pytest.mark.parametrize("vof", [0, 1])
+@pytest.mark.parametrize("grid", VOF_GRIDS, ids=lambda g: f"{g.nx}x{g.ny}x{g.nz}_{''.join('pw'[b] for b in g.bc)}")
+def test_level0_from_volume_fraction(paris, grid, vof):
+    """The mixed projection step with the finest level's FP32 operator read
+    from FP32 face arrays (vof=0) or rebuilt from an FP32 copy of C in the
+    colour passes, restriction and inner CG product (vof=1): both meet every
+    bar.  The profiler's byte counts show which path ran (a vof colour pass
+    moves 10-12 bytes per cell, a face-array pass 20-22)."""
+    pr = pi.random_problem(grid, seed=21, rho1=1000.0)
+    ref = oracle.projection_step(grid, pr.C, pr.rho1, pr.rho2, pr.dt, pr.u, pr.v, pr.w)
+    with ctx_for(paris, grid, precision=paris.MIXED, level0_density=vof) as ctx:
+        u, v, w = dev(pr.u), dev(pr.v), dev(pr.w)
+        p = torch.zeros(grid.shape, dtype=torch.float64, device="cuda")
+        ctx.profile(True)
+        st = ctx.projection_step(dev(pr.C), pr.rho1, pr.rho2, pr.dt, u, v, w, p)
+        prof = ctx.profile_read()["smooth0"]
+        ctx.profile(False)
+        assert st["converged"] == 1 and st["fell_back"] == 0, st
+        per_cell = prof["bytes"] / prof["timed"] / grid.ncells
+        assert (per_cell <= 12.01) if vof else (per_cell >= 20.0), per_cell
+        _check_solution(grid, pr, ref, host(p), (host(u), host(v), host(w)), st)
+
+
+@pytest.mark.parametrize("grid", [pi.Grid(16, 24, 80, 1 / 16), pi.Grid(24, 16, 72, 1 / 24, (P, W, W))],
+                         ids=["16x24x80_ppp", "24x16x72_pww"])
+def test_level0_density_slabs_bit_identical(paris, grid):
+    """Slab-ordered colour passes see the same values as whole-grid passes,
+    also when the finest level is rebuilt from the volume fraction."""
+    pr = pi.random_problem(grid, seed=22, rho1=300.0)
+    out = []
+    for slab in (0, 16):
+        with ctx_for(paris, grid, precision=paris.MIXED, slab_planes=slab) as ctx:
+            u, v, w = dev(pr.u), dev(pr.v), dev(pr.w)
+            p = torch.zeros(grid.shape, dtype=torch.float64, device="cuda")
+            st = ctx.projection_step(dev(pr.C), pr.rho1, pr.rho2, pr.dt, u, v, w, p)
+            assert st["converged"] == 1
+            out.append((host(p), st["iters"]))
+    assert out[0][1] == out[1][1]
+    np.testing.assert_array_equal(out[0][0], out[1][0])
