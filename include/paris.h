@@ -297,6 +297,19 @@ paris_status paris_residual_norms(paris_ctx* ctx, const double* beta_x, const do
 paris_status paris_max_divergence(paris_ctx* ctx, const double* u, const double* v,
                                   const double* w, double* max_abs_div);
 
+/* Self-check of the arithmetic the kernels build from integer operations, on
+ * n device values v (FP64), against the GPU's own conversion and division
+ * instructions: for each value the FP64->FP32 conversion of v * 2^shift
+ * (round to nearest even; results below the FP32 normal range are flushed to
+ * zero and not counted), the FP32->FP64 conversion back with 2^-shift, and
+ * for 0 < v in [2^-123, 2^117) the FP64 reciprocal formed by Newton-Raphson
+ * (Eq. muH's 1/rho_f), which must be within one ulp of 1.0/v.  *mismatches
+ * (host) receives the number of disagreements.  stream: a cudaStream_t (may
+ * be NULL); the call allocates 8 bytes of device memory and synchronises it.
+ * Errors: INVALID_ARG (n < 0, |shift| > 60, null pointers), CUDA. */
+paris_status paris_check_arithmetic(const double* v, int64_t n, int shift, int64_t* mismatches,
+                                    void* stream);
+
 /* Kernel-class timing (diagnostics for roofline reports).  While enabled,
  * every launch of an instrumented level-0 kernel class is bracketed by a CUDA
  * event pair on the context's stream (a pool of 16384 pairs per enable;

@@ -94,6 +94,7 @@ SIGNATURES = {
                                           ct.POINTER(ct.c_int)]),
     "paris_residual_norms": (ct.c_int, [_P, _P, _P, _P, _P, _P, ct.POINTER(_D), ct.POINTER(_D)]),
     "paris_max_divergence": (ct.c_int, [_P, _P, _P, _P, ct.POINTER(_D)]),
+    "paris_check_arithmetic": (ct.c_int, [_P, ct.c_int64, ct.c_int, ct.POINTER(ct.c_int64), _P]),
     "paris_profile": (ct.c_int, [_P, ct.c_int]),
     "paris_profile_read": (ct.c_int, [_P, ct.c_int, ct.POINTER(KernelProf)]),
     "paris_launch_count": (ct.c_int64, []),

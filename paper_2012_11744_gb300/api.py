@@ -52,6 +52,20 @@ def launch_count() -> int:
     return int(_abi.load().paris_launch_count())
 
 
+def check_arithmetic(v, shift: int = 0) -> int:
+    """paris_check_arithmetic on a contiguous FP64 CUDA tensor: the number of
+    values where the library's integer FP64<->FP32 conversions (scaled by
+    2^shift) or its FP64 reciprocal disagree with the GPU's instructions."""
+    if not (isinstance(v, torch.Tensor) and v.is_cuda and v.dtype == torch.float64 and v.is_contiguous()):
+        raise TypeError("v must be a contiguous float64 CUDA tensor")
+    out = ct.c_int64(-1)
+    stream = torch.cuda.current_stream(v.device).cuda_stream
+    _abi.check(_abi.load().paris_check_arithmetic(ct.c_void_p(v.data_ptr()), v.numel(), int(shift),
+                                                  ct.byref(out), ct.c_void_p(stream)),
+               "paris_check_arithmetic")
+    return int(out.value)
+
+
 def _grid_struct(g) -> _abi.Grid:
     s = _abi.Grid()
     s.nx, s.ny, s.nz, s.h = int(g.nx), int(g.ny), int(g.nz), float(g.h)

@@ -73,6 +73,54 @@ __device__ inline int flat_tid() { return threadIdx.y * blockDim.x + threadIdx.x
 
 __device__ inline double nonfinite(double v) { return isfinite(v) ? 0.0 : 1.0; }
 
+// |v| as an integer key: for non-negative doubles (infinities and NaNs
+// included) the order of the bit patterns is the numeric order, so running
+// maxima of magnitudes and the non-finite test need no FP64 instruction (the
+// FP64 pipe runs at 1/64 of the FP32 rate on this GPU).
+__device__ inline unsigned long long abs_key(double v) {
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
+}
+__device__ inline unsigned key_nonfinite(unsigned long long k) { return k >= 0x7ff0000000000000ULL ? 1u : 0u; }
+__device__ inline double key_value(unsigned long long k) { return __longlong_as_double((long long)k); }
+
+// Conversions between FP64 and FP32 with a power-of-two scaling, written
+// with integer operations on the IEEE-754 fields: the hardware conversions
+// run on the FP64 pipe at about a fifth of its FMA rate on this GPU.
+//
+// float(v * 2^s): round to nearest, ties to even, for results in the FP32
+// normal range; smaller results flush to a signed zero, larger ones give a
+// signed infinity; infinities stay infinite and NaN stays NaN.
+__device__ inline float d2f_scaled(double v, int s) {
+    const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    if (e == 0x7ff) return __int_as_float((int)(sign | 0x7f800000u | (((hi & 0xfffffu) | lo) ? 0x400000u : 0u)));
+    const int fe = e - 896 + s;  // FP32 biased exponent (FP64 bias 1023, FP32 bias 127)
+    if (e == 0 || fe <= 0) return __int_as_float((int)sign);
+    if (fe >= 255) return __int_as_float((int)(sign | 0x7f800000u));
+    // the 23 leading fraction bits; round on the 29 dropped ones (a carry out
+    // of the fraction correctly increments the exponent)
+    const unsigned frac = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rem = lo & 0x1fffffffu;
+    unsigned bits = ((unsigned)fe << 23) | frac;
+    if (rem > 0x10000000u || (rem == 0x10000000u && (frac & 1u))) bits += 1u;
+    return __int_as_float((int)(sign | bits));
+}
+
+// (double)v * 2^s, exact for normal v whose scaled value is an FP64 normal
+// number; FP32 subnormals flush to a signed zero; infinities and NaN are kept.
+__device__ inline double f2d_scaled(float v, int s) {
+    const unsigned b = (unsigned)__float_as_int(v);
+    const unsigned sign = b & 0x80000000u;
+    const int e = (int)((b >> 23) & 0xffu);
+    const unsigned frac = b & 0x7fffffu;
+    if (e == 0xff) return __hiloint2double((int)(sign | 0x7ff00000u | (frac ? 0x80000u : 0u)), 0);
+    const int de = e + 896 + s;  // FP64 biased exponent
+    if (e == 0 || de <= 0) return __hiloint2double((int)sign, 0);
+    if (de >= 0x7ff) return __hiloint2double((int)(sign | 0x7ff00000u), 0);
+    return __hiloint2double((int)(sign | ((unsigned)de << 20) | (frac >> 3)), (int)(frac << 29));
+}
+
 }  // namespace
 
 static thread_local char g_last_cuda_error[256] = "no CUDA error recorded";
@@ -159,7 +207,9 @@ __global__ void finalize_kernel(const double* __restrict__ partials, int64_t nbl
         switch (mode) {
             case FIN_MEAN_B: s->mean_b = r[0] / param; s->nonfinite += r[2]; break;
             case FIN_BNORMS:  // the first residual of a solve is f itself: seed rinf with |f|inf
-                s->bnorm2 = r[0]; s->binf = r[1]; s->rinf = r[1]; s->nonfinite += r[2]; break;
+                s->bnorm2 = r[0]; s->binf = r[1]; s->rinf = r[1]; s->nonfinite += r[2];
+                s->xmax = r[3];
+                break;
             case FIN_RNORMS: s->rr = r[0]; s->rinf = r[1]; s->nonfinite += r[2]; break;
             case FIN_ALPHA: s->alpha = (r[0] > 0.0) ? s->rho / r[0] : 0.0; break;
             case FIN_RHO_BETA: s->beta = (s->rho != 0.0) ? r[0] / s->rho : 0.0; s->rho = r[0]; break;
@@ -169,10 +219,15 @@ __global__ void finalize_kernel(const double* __restrict__ partials, int64_t nbl
                 s->rho = r[0];
                 break;
             case FIN_SCALE: {
-                // r32 = scale * r64 keeps the FP32 inner problem O(1)
-                double m = s->rinf > 1e-300 ? s->rinf : 1.0;
-                s->scale = 1.0 / m;
-                s->inv_scale = m;
+                // r32 = scale * r64 keeps the FP32 inner problem O(1): scale is
+                // the power of two that maps max |r| into [0.5, 1), so scaling
+                // is an exact exponent shift in both directions
+                const double m = s->rinf > 1e-300 && isfinite(s->rinf) ? s->rinf : 1.0;
+                int ex = 0;
+                frexp(m, &ex);
+                s->scale = ldexp(1.0, -ex);
+                s->inv_scale = ldexp(1.0, ex);
+                s->scale_exp = (double)(-ex);
                 break;
             }
             case FIN_INNER_INIT: s->rr0 = r[0]; s->rr = r[0]; s->rinf = r[1]; break;
@@ -264,7 +319,7 @@ __global__ void __launch_bounds__(kTX* kTY) face_coeffs_kernel(Geo g, const doub
             if (g.wx && i == nx - 1) bx[g.fx(nx, j, k)] = 0.0;
             if (g.wy && j == ny - 1) by[g.fy(i, ny, k)] = 0.0;
             if (g.wz && k == nz - 1) bz[g.fz(i, j, nz)] = 0.0;
-            if (rh32) rh32[c] = (float)rc;
+            if (rh32) rh32[c] = d2f_scaled(rc, 0);
         }
         rzm = rc;
     }
@@ -302,17 +357,21 @@ __global__ void __launch_bounds__(kTX* kTY) divergence_kernel(Geo g, const doubl
                                                               double* partials) {
     const int i = blockIdx.x * kTX + threadIdx.x;
     const int j = blockIdx.y * kTY + threadIdx.y;
-    double acc[3] = {0.0, 0.0, 0.0};
+    double sum = 0.0;
+    unsigned long long bmax_k = 0;
+    unsigned nf = 0;
     if (i < g.nx && j < g.ny) {
         const int k0 = blockIdx.z * kZ, k1 = min(k0 + kZ, g.nz);
         PARIS_ZLOOP(k0, k1, {
-            double b = cell_div(g, u, v, w, i, j, k) * inv_hdt;
+            const double b = cell_div(g, u, v, w, i, j, k) * inv_hdt;
             rhs[g.cidx(i, j, k)] = b;
-            acc[0] += b;
-            acc[1] = fmax(acc[1], fabs(b));
-            acc[2] += nonfinite(b);
+            sum += b;
+            const unsigned long long kb = abs_key(b);
+            bmax_k = kb > bmax_k ? kb : bmax_k;
+            nf += key_nonfinite(kb);
         })
     }
+    double acc[3] = {sum, key_value(bmax_k), (double)nf};
     const int op[3] = {0, 1, 0};
     block_reduce_store<3>(acc, op, partials, flat_block(), flat_tid());
 }
@@ -331,11 +390,16 @@ __global__ void __launch_bounds__(kTX* kTY) max_div_kernel(Geo g, const double* 
                                                            double inv_h, double* partials) {
     const int i = blockIdx.x * kTX + threadIdx.x;
     const int j = blockIdx.y * kTY + threadIdx.y;
-    double acc[1] = {0.0};
+    unsigned long long dmax_k = 0;
     if (i < g.nx && j < g.ny) {
         const int k0 = blockIdx.z * kZ, k1 = min(k0 + kZ, g.nz);
-        PARIS_ZLOOP(k0, k1, { acc[0] = fmax(acc[0], fabs(cell_div(g, u, v, w, i, j, k) * inv_h)); })
+        PARIS_ZLOOP(k0, k1, {
+            const unsigned long long kd = abs_key(cell_div(g, u, v, w, i, j, k));
+            dmax_k = kd > dmax_k ? kd : dmax_k;
+        })
     }
+    // max |div| h^-1 = h^-1 max |div| (h > 0)
+    double acc[1] = {key_value(dmax_k) * inv_h};
     const int op[1] = {1};
     block_reduce_store<1>(acc, op, partials, flat_block(), flat_tid());
 }
@@ -350,24 +414,34 @@ int64_t launch_max_divergence(const Geo& g, const double* u, const double* v, co
 
 // f = -(rhs - mean_b): the right-hand side of the SPD system A p = f.
 __global__ void make_rhs_kernel(int64_t n, const double* __restrict__ rhs, const Scal* s,
-                                double* __restrict__ f, double* partials) {
+                                double* __restrict__ f, const double* __restrict__ x0,
+                                double* partials) {
     const double mb = s->mean_b;
-    double acc[3] = {0.0, 0.0, 0.0};
+    double l2 = 0.0;
+    unsigned long long fmax_k = 0, xmax_k = 0;
+    unsigned nf = 0;
     PARIS_EW_FOR(c, n) {
-        double t = -(rhs[c] - mb);
+        const double t = -(rhs[c] - mb);
         f[c] = t;
-        acc[0] = fma(t, t, acc[0]);
-        acc[1] = fmax(acc[1], fabs(t));
-        acc[2] += nonfinite(t);
+        l2 = fma(t, t, l2);
+        const unsigned long long k = abs_key(t);
+        fmax_k = k > fmax_k ? k : fmax_k;
+        nf += key_nonfinite(k);
+        if (x0) {
+            const unsigned long long kx = abs_key(x0[c]);
+            xmax_k = kx > xmax_k ? kx : xmax_k;
+        }
     }
-    const int op[3] = {0, 1, 0};
-    block_reduce_store<3>(acc, op, partials, blockIdx.x, threadIdx.x);
+    // without an initial guess the fourth value reads "not known to be zero"
+    double acc[4] = {l2, key_value(fmax_k), (double)nf, x0 ? key_value(xmax_k) : 1.0};
+    const int op[4] = {0, 1, 0, 1};
+    block_reduce_store<4>(acc, op, partials, blockIdx.x, threadIdx.x);
 }
 
-int64_t launch_make_rhs(int64_t n, const double* rhs, const Scal* s, double* f, double* partials,
-                        cudaStream_t st) {
+int64_t launch_make_rhs(int64_t n, const double* rhs, const Scal* s, double* f, const double* x0,
+                        double* partials, cudaStream_t st) {
     int nb = elementwise_blocks(n);
-    make_rhs_kernel<<<nb, kRedThreads, 0, st>>>(n, rhs, s, f, partials);
+    make_rhs_kernel<<<nb, kRedThreads, 0, st>>>(n, rhs, s, f, x0, partials);
     count_launch();
     return nb;
 }
@@ -544,64 +618,69 @@ void launch_inv_diag(const Geo& g, const Coef<T>& cf, T* w, cudaStream_t st) {
 // Dense inverse of the coarsest operator regularised on its null space:
 // (A + a 1 1^T)^{-1} with a = mean(diag)/n, which maps a mean-free f to the
 // mean-free solution of A x = f.  FP64 Gauss-Jordan without pivoting (the
-// regularised matrix is SPD) by one CTA; n <= 128.
+// regularised matrix is SPD) by one CTA of 32 x 32 threads on a copy of the
+// matrix in shared memory (n <= 128: at most 129 KB); the elimination step
+// maps rows to threadIdx.y and columns to threadIdx.x.
 template <typename T>
-__global__ void coarse_inverse_kernel(Geo g, Coef<T> cf, double* __restrict__ M) {
+__global__ void __launch_bounds__(1024) coarse_inverse_kernel(Geo g, Coef<T> cf, double* __restrict__ Mout) {
+    extern __shared__ double smem[];
     const int n = (int)g.ncell();
-    const int tid = threadIdx.x, nt = blockDim.x;
+    double* M = smem;         // n x n, row-major
+    double* col = smem + n * n;  // column kk before the pivot step
+    __shared__ double dsum, piv;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * blockDim.x + tx, nt = blockDim.x * blockDim.y;
     for (int e = tid; e < n * n; e += nt) M[e] = 0.0;
     __syncthreads();
-    __shared__ double dsum;
-    if (tid == 0) dsum = 0.0;
-    __syncthreads();
+    // each row is assembled by one thread
     for (int c = tid; c < n; c += nt) {
         const int i = c % g.nx, j = (c / g.nx) % g.ny, k = c / (g.nx * g.ny);
         Stencil<T> s;
         load_stencil(g, cf, i, j, k, s);
         for (int q = 0; q < 6; ++q) {
-            double b = (double)s.b[q] * (double)cf.scale;
-            M[(int64_t)c * n + c] += b;
-            M[(int64_t)c * n + s.nb[q]] -= b;  // a self-neighbour (n = 1) cancels
+            const double b = (double)s.b[q] * (double)cf.scale;
+            M[c * n + c] += b;
+            M[c * n + (int)s.nb[q]] -= b;  // a self-neighbour (n = 1) cancels
         }
     }
     __syncthreads();
     if (tid == 0) {
         double t = 0.0;
-        for (int c = 0; c < n; ++c) t += M[(int64_t)c * n + c];
+        for (int c = 0; c < n; ++c) t += M[c * n + c];
         dsum = t;
     }
     __syncthreads();
     const double a = dsum / ((double)n * (double)n);
     for (int e = tid; e < n * n; e += nt) M[e] += a;
     __syncthreads();
-    // in-place Gauss-Jordan inversion
-    __shared__ double piv;
-    extern __shared__ double col[];  // n entries: column k before the pivot step
     for (int kk = 0; kk < n; ++kk) {
-        if (tid == 0) piv = 1.0 / M[(int64_t)kk * n + kk];
+        if (tid == 0) piv = 1.0 / M[kk * n + kk];
+        for (int r = tid; r < n; r += nt) col[r] = M[r * n + kk];
         __syncthreads();
-        for (int r = tid; r < n; r += nt) col[r] = M[(int64_t)r * n + kk];
+        for (int c = tid; c < n; c += nt) M[kk * n + c] = (c == kk) ? piv : M[kk * n + c] * piv;
         __syncthreads();
-        // scale the pivot row
-        for (int c = tid; c < n; c += nt)
-            M[(int64_t)kk * n + c] = (c == kk) ? piv : M[(int64_t)kk * n + c] * piv;
-        __syncthreads();
-        // eliminate column kk from the other rows
-        for (int e = tid; e < n * n; e += nt) {
-            int r = e / n, c = e % n;
+        for (int r = ty; r < n; r += blockDim.y) {
             if (r == kk) continue;
-            double f = col[r];
-            if (c == kk) M[e] = -f * piv;
-            else M[e] -= f * M[(int64_t)kk * n + c];
+            const double fr = col[r];
+            for (int c = tx; c < n; c += blockDim.x)
+                M[r * n + c] = (c == kk) ? -fr * piv : fma(-fr, M[kk * n + c], M[r * n + c]);
         }
         __syncthreads();
     }
+    for (int e = tid; e < n * n; e += nt) Mout[e] = M[e];
 }
 
 template <typename T>
 void launch_coarse_inverse(const Geo& g, const Coef<T>& cf, double* inv, cudaStream_t st) {
-    int n = (int)g.ncell();
-    coarse_inverse_kernel<T><<<1, 256, sizeof(double) * n, st>>>(g, cf, inv);
+    const int n = (int)g.ncell();
+    const size_t bytes = sizeof(double) * ((size_t)n * n + n);
+    static bool opted = false;  // one opt-in per instantiation for more than 48 KB
+    if (!opted) {
+        cudaFuncSetAttribute(coarse_inverse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(double) * (128 * 128 + 128)));
+        opted = true;
+    }
+    coarse_inverse_kernel<T><<<1, dim3(32, 32), bytes, st>>>(g, cf, inv);
     count_launch();
 }
 
@@ -884,51 +963,72 @@ void launch_prolong_add(const Geo& fine, const Geo& coarse, const int fac[3], co
 // ------------------------------------------------------------------ Krylov ---
 
 // FP64 residual r = f - A x with fused norms; the mixed form also writes the
-// scaled FP32 copy r32 = scale * r that the inner solve starts from.
+// scaled FP32 copy r32 = scale * r that the inner solve starts from.  With
+// zero_ok and an initial guess that is zero everywhere (s->xmax == 0, a value
+// every thread reads alike) A x vanishes and r = f is copied.
 template <bool I32>
 __global__ void __launch_bounds__(kTX* kTY) residual64_kernel(Geo g, Coef<double> cf,
                                                               const double* __restrict__ f,
                                                               const double* __restrict__ x,
                                                               double* __restrict__ r64,
                                                               float* __restrict__ r32,
-                                                              const Scal* s, double* partials) {
+                                                              const Scal* s, double* partials,
+                                                              int zero_ok) {
     const int i = blockIdx.x * kTX + threadIdx.x;
     const int j = blockIdx.y * kTY + threadIdx.y;
-    double acc[3] = {0.0, 0.0, 0.0};
+    double l2 = 0.0;
+    unsigned long long rmax_k = 0;
+    unsigned nf = 0;
     if (i < g.nx && j < g.ny) {
-        const double sc = r32 ? s->scale : 0.0;
+        const int se = r32 ? (int)s->scale_exp : 0;
+        const bool zero = zero_ok && s->xmax == 0.0;
         const int k0 = blockIdx.z * kZ, k1 = min(k0 + kZ, g.nz);
         PARIS_ZLOOP(k0, k1, {
-            Stencil<double> st;
             int64_t c;
-            if (I32) {
-                int c32;
-                load_stencil_fast<double>(g, cf.bx, cf.by, cf.bz, i, j, k, st, c32);
-                c = c32;
-            } else {
+            double r;
+            if (zero) {
                 c = g.cidx(i, j, k);
-                load_stencil(g, cf, i, j, k, st);
+                r = f[c];
+            } else {
+                Stencil<double> st;
+                if (I32) {
+                    int c32;
+                    load_stencil_fast<double>(g, cf.bx, cf.by, cf.bz, i, j, k, st, c32);
+                    c = c32;
+                } else {
+                    c = g.cidx(i, j, k);
+                    load_stencil(g, cf, i, j, k, st);
+                }
+                // (A x)/scale in the difference form, then one fused step
+                const double xc = x[c];
+                double a = st.b[0] * (xc - x[st.nb[0]]);
+#pragma unroll
+                for (int q = 1; q < 6; ++q) a = fma(st.b[q], xc - x[st.nb[q]], a);
+                r = fma(-cf.scale, a, f[c]);
             }
-            double r = f[c] - apply_A(st, x, x[c], cf.scale);
             if (r64) r64[c] = r;
-            if (r32) r32[c] = (float)(r * sc);
-            acc[0] = fma(r, r, acc[0]);
-            acc[1] = fmax(acc[1], fabs(r));
-            acc[2] += nonfinite(r);
+            if (r32) r32[c] = d2f_scaled(r, se);
+            l2 = fma(r, r, l2);
+            const unsigned long long kr = abs_key(r);
+            rmax_k = kr > rmax_k ? kr : rmax_k;
+            nf += key_nonfinite(kr);
         })
     }
+    double acc[3] = {l2, key_value(rmax_k), (double)nf};
     const int op[3] = {0, 1, 0};
     block_reduce_store<3>(acc, op, partials, flat_block(), flat_tid());
 }
 
 int64_t launch_residual64(const Geo& g, const Coef<double>& cf, const double* f, const double* x,
-                          double* r64, float* r32, const Scal* s, double* partials,
+                          double* r64, float* r32, const Scal* s, double* partials, bool zero_ok,
                           cudaStream_t st) {
     dim3 gr = tile_grid(g, kZ);
     if (fits_i32(g))
-        residual64_kernel<true><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, f, x, r64, r32, s, partials);
+        residual64_kernel<true><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, f, x, r64, r32, s, partials,
+                                                               zero_ok ? 1 : 0);
     else
-        residual64_kernel<false><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, f, x, r64, r32, s, partials);
+        residual64_kernel<false><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, f, x, r64, r32, s, partials,
+                                                                zero_ok ? 1 : 0);
     count_launch();
     return nblocks_of(gr);
 }
@@ -1095,26 +1195,63 @@ void launch_xpby(int64_t n, const Scal* s, const T* z, T* d, cudaStream_t st) {
     count_launch();
 }
 
+// x += e * inv_scale, inv_scale a power of two: the product is the exact
+// conversion with an exponent shift, then one FP64 addition.
 __global__ void accumulate_kernel(int64_t n, const Scal* s, const float* __restrict__ e,
                                   double* __restrict__ x, int vec) {
-    const double is = s->inv_scale;
+    const int sh = -(int)s->scale_exp;
     const int64_t nv = vec ? n / 4 : 0;
     PARIS_VEC_FOR(i, nv) {
         const float4 ev = reinterpret_cast<const float4*>(e)[i];
         double2 x0 = reinterpret_cast<double2*>(x)[2 * i];
         double2 x1 = reinterpret_cast<double2*>(x)[2 * i + 1];
-        x0.x = fma((double)ev.x, is, x0.x);
-        x0.y = fma((double)ev.y, is, x0.y);
-        x1.x = fma((double)ev.z, is, x1.x);
-        x1.y = fma((double)ev.w, is, x1.y);
+        x0.x += f2d_scaled(ev.x, sh);
+        x0.y += f2d_scaled(ev.y, sh);
+        x1.x += f2d_scaled(ev.z, sh);
+        x1.y += f2d_scaled(ev.w, sh);
         reinterpret_cast<double2*>(x)[2 * i] = x0;
         reinterpret_cast<double2*>(x)[2 * i + 1] = x1;
     }
-    PARIS_TAIL_FOR(c, nv * 4, n) x[c] = fma((double)e[c], is, x[c]);
+    PARIS_TAIL_FOR(c, nv * 4, n) x[c] += f2d_scaled(e[c], sh);
 }
 
 void launch_accumulate(int64_t n, const Scal* s, const float* e, double* x, cudaStream_t st) {
     accumulate_kernel<<<elementwise_blocks(n), kRedThreads, 0, st>>>(n, s, e, x, aligned16(e, x) ? 1 : 0);
+    count_launch();
+}
+
+// ------------------------------------------------------------- self-check ---
+
+__global__ void check_arithmetic_kernel(const double* __restrict__ v, int64_t n, int shift, double p2,
+                                        unsigned long long* bad) {
+    unsigned long long cnt = 0;
+    PARIS_EW_FOR(i, n) {
+        const double x = v[i];
+        // FP64 -> FP32 with the scaling 2^shift (the product by p2 = 2^shift is exact)
+        const float hw = __double2float_rn(x * p2);
+        const float sw = d2f_scaled(x, shift);
+        const bool hw_sub = hw != 0.0f && fabsf(hw) < 1.17549435e-38f;  // flushed by design
+        if (isnan(hw)) cnt += isnan(sw) ? 0 : 1;
+        else if (hw_sub) cnt += (sw == 0.0f) ? 0 : 1;
+        else cnt += (__float_as_int(hw) == __float_as_int(sw)) ? 0 : 1;
+        // FP32 -> FP64 with 2^-shift (exact in both)
+        if (!isnan(hw) && !hw_sub) {
+            const double hw2 = (double)hw / p2;
+            const double sw2 = f2d_scaled(hw, -shift);
+            cnt += (__double_as_longlong(hw2) == __double_as_longlong(sw2)) ? 0 : 1;
+        }
+        // reciprocal within one ulp of the correctly rounded quotient
+        if (x > 0.0 && x >= 0x1p-123 && x < 0x1p117) {
+            const long long a = __double_as_longlong(recip64(x)), b = __double_as_longlong(1.0 / x);
+            cnt += (a - b <= 1 && b - a <= 1) ? 0 : 1;
+        }
+    }
+    if (cnt) atomicAdd(bad, cnt);
+}
+
+void launch_check_arithmetic(const double* v, int64_t n, int shift, unsigned long long* bad,
+                             cudaStream_t st) {
+    check_arithmetic_kernel<<<elementwise_blocks(n), kRedThreads, 0, st>>>(v, n, shift, ldexp(1.0, shift), bad);
     count_launch();
 }
 

@@ -17,10 +17,12 @@ struct Scal {
     double beta;         // (F)CG direction update coefficient
     double rr;           // current residual ||r||_2^2
     double rinf;         // current residual ||r||_inf
-    double scale;        // MIXED: r32 = scale * r64; correction e64 = e32 / scale
+    double scale;        // MIXED: r32 = scale * r64; correction e64 = e32 / scale (a power of 2)
     double inv_scale;
+    double scale_exp;    // log2(scale), an integer
     double rr0;          // MIXED: ||r32||_2^2 at the start of the inner solve
     double nonfinite;    // > 0 if a NaN/Inf was seen
+    double xmax;         // max |x| of the initial guess (0: the first residual is f)
 };
 
 enum FinalizeMode {
@@ -60,9 +62,10 @@ void launch_face_coeffs(const Geo& g, const double* C, double rho1, double rho2,
 // rhs = div(u)/(h dt); partials: (sum rhs, max |rhs|, nonfinite count)
 int64_t launch_divergence(const Geo& g, const double* u, const double* v, const double* w,
                           double inv_hdt, double* rhs, double* partials, cudaStream_t st);
-// f = -(rhs - mean_b), partials: (||f||^2, max|f|, nonfinite)
-int64_t launch_make_rhs(int64_t n, const double* rhs, const Scal* s, double* f, double* partials,
-                        cudaStream_t st);
+// f = -(rhs - mean_b), partials: (||f||^2, max|f|, nonfinite, max|x0|); x0 (the
+// initial guess) may be null
+int64_t launch_make_rhs(int64_t n, const double* rhs, const Scal* s, double* f, const double* x0,
+                        double* partials, cudaStream_t st);
 void launch_sub_mean(int64_t n, double* x, const Scal* s, cudaStream_t st);
 int64_t launch_sum(int64_t n, const double* x, double* partials, cudaStream_t st);
 void launch_project(const Geo& g, const double* bx, const double* by, const double* bz,
@@ -144,9 +147,11 @@ void launch_coarse_beta_rho(const Geo& fine, const float* rh, double h, const Ge
                             cudaStream_t st);
 
 // ------------------------------------------------------------ Krylov ------
-// r = f - A x (FP64), optional r32 = scale * r; partials (||r||^2, max|r|, nonfinite)
+// r = f - A x (FP64), optional r32 = scale * r; partials (||r||^2, max|r|, nonfinite).
+// zero_ok: x is the initial guess whose max |x| the prologue stored in s->xmax;
+// when that is 0 the kernel copies r = f instead of applying A.
 int64_t launch_residual64(const Geo& g, const Coef<double>& cf, const double* f, const double* x,
-                          double* r64, float* r32, const Scal* s, double* partials,
+                          double* r64, float* r32, const Scal* s, double* partials, bool zero_ok,
                           cudaStream_t st);
 // q = A d; partials (d . q)
 template <typename T>
@@ -165,6 +170,12 @@ template <typename T>
 void launch_xpby(int64_t n, const Scal* s, const T* z, T* d, cudaStream_t st);
 // x64 += e32 * inv_scale
 void launch_accumulate(int64_t n, const Scal* s, const float* e, double* x, cudaStream_t st);
+
+// ------------------------------------------------------------ self-check ---
+// counts disagreements of the integer conversions and the FP64 reciprocal
+// with the hardware instructions on n values (see paris_check_arithmetic)
+void launch_check_arithmetic(const double* v, int64_t n, int shift, unsigned long long* bad,
+                             cudaStream_t st);
 
 // ------------------------------------------------------------ adjoint -----
 // out = D (B g) (walls carry no flux); partials (sum, max|out|, nonfinite)

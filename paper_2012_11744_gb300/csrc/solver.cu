@@ -567,24 +567,31 @@ bool meets(const paris_ctx* c, const Scal& s) {
     return s.rr <= t * t * s.bnorm2 && s.rinf <= t * s.binf;
 }
 
-// Common prologue: mean of rhs, f = -(rhs - mean), norms of f.
-paris_status prologue(paris_ctx* c, const double* rhs) {
-    int64_t nb = launch_sum(c->N, rhs, c->partials, c->st);
-    finalize(c->partials, nb, 3, 2, c->scal, FIN_MEAN_B, (double)c->N, c->st);
-    nb = launch_make_rhs(c->N, rhs, c->scal, c->f, c->partials, c->st);
-    finalize(c->partials, nb, 3, 2, c->scal, FIN_BNORMS, 0.0, c->st);
+// Common prologue: mean of rhs (unless the caller already left it in
+// scal->mean_b), f = -(rhs - mean), norms of f and max |x0| of the initial guess.
+paris_status prologue(paris_ctx* c, const double* rhs, const double* x0, bool mean_known) {
+    int64_t nb;
+    if (!mean_known) {
+        nb = launch_sum(c->N, rhs, c->partials, c->st);
+        finalize(c->partials, nb, 3, 2, c->scal, FIN_MEAN_B, (double)c->N, c->st);
+    }
+    nb = launch_make_rhs(c->N, rhs, c->scal, c->f, x0, c->partials, c->st);
+    finalize(c->partials, nb, 4, 0xA, c->scal, FIN_BNORMS, 0.0, c->st);
     CK(cudaGetLastError());
     return PARIS_OK;
 }
 
-paris_status true_residual(paris_ctx* c, const Coef<double>& c64, const double* x, float* r32) {
+// r = f - A x in FP64 (r32: the scaled FP32 copy only); zero_ok: x is still
+// the initial guess the prologue measured.
+paris_status true_residual(paris_ctx* c, const Coef<double>& c64, const double* x, float* r32,
+                           bool zero_ok = false) {
     if (r32) finalize(c->partials, 0, 1, 0, c->scal, FIN_SCALE, 0.0, c->st);
     int64_t nb;
     {
         const double n = (double)c->N;
         ProfScope ps(c, PARIS_K_RESID64, (16 * n + 8 * beta_count(c->g0)) + (r32 ? 4 : 8) * n);
         nb = launch_residual64(c->g0, c64, c->f, x, r32 ? nullptr : c->r, r32, c->scal, c->partials,
-                               c->st);
+                               zero_ok, c->st);
     }
     finalize(c->partials, nb, 3, 2, c->scal, FIN_RNORMS, 0.0, c->st);
     CK(cudaGetLastError());
@@ -593,9 +600,9 @@ paris_status true_residual(paris_ctx* c, const Coef<double>& c64, const double* 
 
 // FP64 multigrid-preconditioned CG from the initial guess in x.
 paris_status solve_fp64(paris_ctx* c, const Coef<double>& c64, double* x, SolveOut& out,
-                        int max_iter) {
+                        int max_iter, bool fresh) {
     setup_hierarchy<double>(c, c64);
-    paris_status s = true_residual(c, c64, x, nullptr);  // r = f - A x
+    paris_status s = true_residual(c, c64, x, nullptr, fresh);  // r = f - A x
     if (s != PARIS_OK) return s;
     if (c->scal_h->nonfinite > 0) { out.nonfinite = true; return PARIS_OK; }
     if (c->scal_h->bnorm2 == 0.0 || meets(c, *c->scal_h)) { out.converged = true; return PARIS_OK; }
@@ -671,8 +678,9 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
     setup_hierarchy<float>(c, c32);
     double prev_rr = INFINITY;
     int stalls = 0;
-    for (;;) {
-        paris_status s = true_residual(c, c64, x, c->r32);  // r32 = scale * (f - A x)
+    for (bool first = true;; first = false) {
+        // r32 = scale * (f - A x); x is the untouched initial guess on the first pass
+        paris_status s = true_residual(c, c64, x, c->r32, first);
         if (s != PARIS_OK) return s;
         const Scal& h = *c->scal_h;
         if (h.nonfinite > 0) { out.nonfinite = true; return PARIS_OK; }
@@ -901,13 +909,15 @@ paris_status paris_divergence(paris_ctx* c, const double* u, const double* v, co
 namespace {
 
 // The solve behind paris_poisson_solve; rho0: the mixed form's level-0 FP32
-// kernels rebuild their coefficients from rh32 (filled by the caller).
+// kernels rebuild their coefficients from rh32 (filled by the caller);
+// mean_known: the caller reset scal and left the mean of rhs in scal->mean_b.
 paris_status poisson_solve(paris_ctx* c, const double* bx, const double* by, const double* bz,
-                           const double* rhs, double* p, paris_stats* st, bool rho0) {
+                           const double* rhs, double* p, paris_stats* st, bool rho0,
+                           bool mean_known) {
     const double ih2 = 1.0 / (c->grid.h * c->grid.h);
     Coef<double> c64{bx, by, bz, ih2};
-    CK(cudaMemsetAsync(c->scal, 0, sizeof(Scal), c->st));
-    paris_status s = prologue(c, rhs);
+    if (!mean_known) CK(cudaMemsetAsync(c->scal, 0, sizeof(Scal), c->st));
+    paris_status s = prologue(c, rhs, p, mean_known);
     if (s != PARIS_OK) return s;
     SolveOut out;
     int fell_back = 0;
@@ -916,7 +926,7 @@ paris_status poisson_solve(paris_ctx* c, const double* bx, const double* by, con
         if (s != PARIS_OK) return s;
         if (!out.converged && !out.nonfinite && c->opts.fallback) {
             SolveOut o2;
-            s = solve_fp64(c, c64, p, o2, c->opts.max_iter);
+            s = solve_fp64(c, c64, p, o2, c->opts.max_iter, false);
             if (s != PARIS_OK) return s;
             o2.iters += out.iters;
             o2.outer += out.outer;
@@ -924,7 +934,7 @@ paris_status poisson_solve(paris_ctx* c, const double* bx, const double* by, con
             fell_back = 1;
         }
     } else {
-        s = solve_fp64(c, c64, p, out, c->opts.max_iter);
+        s = solve_fp64(c, c64, p, out, c->opts.max_iter, true);
         if (s != PARIS_OK) return s;
         out.outer = out.iters;
     }
@@ -955,7 +965,7 @@ paris_status paris_poisson_solve(paris_ctx* c, const double* bx, const double* b
                                  const double* bz, const double* rhs, double* p,
                                  paris_stats* st) {
     if (!c || !bx || !by || !bz || !rhs || !p) return PARIS_ERR_INVALID_ARG;
-    return poisson_solve(c, bx, by, bz, rhs, p, st, false);
+    return poisson_solve(c, bx, by, bz, rhs, p, st, false, false);
 }
 
 paris_status paris_project(paris_ctx* c, const double* bx, const double* by, const double* bz,
@@ -973,25 +983,21 @@ paris_status paris_projection_step(paris_ctx* c, const double* C, double rho1, d
     if (!c || !C || !u || !v || !w || !p) return PARIS_ERR_INVALID_ARG;
     if (!(rho1 > 0.0) || !(rho2 > 0.0) || !std::isfinite(rho1) || !std::isfinite(rho2))
         return PARIS_ERR_INVALID_ARG;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return PARIS_ERR_INVALID_ARG;
     const bool use_rho0 = rho0_usable(c);
     launch_face_coeffs(c->g0, C, rho1, rho2, c->beta[0], c->beta[1], c->beta[2],
                        use_rho0 ? c->rh32 : nullptr, c->st);
     CK(cudaGetLastError());
+    // rhs = div u*/dt and its mean; the solve's prologue forms the mean-free
+    // f = -(rhs - mean) directly (no separate mean removal pass)
+    CK(cudaMemsetAsync(c->scal, 0, sizeof(Scal), c->st));
+    const int64_t nb = launch_divergence(c->g0, u, v, w, 1.0 / (c->grid.h * dt), c->rhs, c->partials, c->st);
+    finalize(c->partials, nb, 3, 2, c->scal, FIN_MEAN_B, (double)c->N, c->st);
+    CK(cudaGetLastError());
     paris_status s;
-    s = paris_divergence(c, u, v, w, dt, c->rhs, nullptr);
-    if (s != PARIS_OK) return s;
-    double mb = 0.0;
-    {
-        // the divergence's removed mean is the one worth reporting
-        CK(cudaMemcpyAsync(&c->scal_h->mean_b, &c->scal->mean_b, sizeof(double),
-                           cudaMemcpyDeviceToHost, c->st));
-        CK(cudaStreamSynchronize(c->st));
-        mb = c->scal_h->mean_b;
-    }
     paris_status solve =
-        poisson_solve(c, c->beta[0], c->beta[1], c->beta[2], c->rhs, p, st, use_rho0);
+        poisson_solve(c, c->beta[0], c->beta[1], c->beta[2], c->rhs, p, st, use_rho0, true);
     if (solve != PARIS_OK && solve != PARIS_ERR_NOT_CONVERGED) return solve;
-    if (st) st->mean_b_removed = mb;
     s = paris_project(c, c->beta[0], c->beta[1], c->beta[2], p, dt, u, v, w);
     if (s != PARIS_OK) return s;
     return solve;
@@ -1066,13 +1072,36 @@ paris_status paris_residual_norms(paris_ctx* c, const double* bx, const double* 
     Coef<double> c64{bx, by, bz, ih2};
     // f = -rhs as given (no mean removal): norms of rhs and of rhs - L p
     CK(cudaMemsetAsync(c->scal, 0, sizeof(Scal), c->st));
-    int64_t nb = launch_make_rhs(c->N, rhs, c->scal, c->f, c->partials, c->st);
-    finalize(c->partials, nb, 3, 2, c->scal, FIN_BNORMS, 0.0, c->st);
+    int64_t nb = launch_make_rhs(c->N, rhs, c->scal, c->f, nullptr, c->partials, c->st);
+    finalize(c->partials, nb, 4, 0xA, c->scal, FIN_BNORMS, 0.0, c->st);
     paris_status s = true_residual(c, c64, p, nullptr);
     if (s != PARIS_OK) return s;
     const Scal& h = *c->scal_h;
     *rel_l2 = h.bnorm2 > 0 ? std::sqrt(h.rr / h.bnorm2) : std::sqrt(h.rr);
     *rel_linf = h.binf > 0 ? h.rinf / h.binf : h.rinf;
+    return PARIS_OK;
+}
+
+paris_status paris_check_arithmetic(const double* v, int64_t n, int shift, int64_t* mismatches,
+                                    void* stream) {
+    if (!v || !mismatches || n < 0 || shift > 60 || shift < -60) return PARIS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long* bad = nullptr;
+    CK(cudaMalloc(&bad, sizeof(unsigned long long)));
+    unsigned long long h = 0;
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess && n > 0) {
+        launch_check_arithmetic(v, n, shift, bad, st);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, bad, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(bad);
+    if (e != cudaSuccess) {
+        paris_internal_note_cuda_error(e);
+        return PARIS_ERR_CUDA;
+    }
+    *mismatches = (int64_t)h;
     return PARIS_OK;
 }
 

@@ -280,3 +280,21 @@ def test_level0_density_slabs_bit_identical(paris, grid):
             out.append((host(p), st["iters"]))
     assert out[0][1] == out[1][1]
     np.testing.assert_array_equal(out[0][0], out[1][0])
+
+
+@pytest.mark.parametrize("shift", [0, -3, 7, -40, 40])
+def test_integer_conversions_and_reciprocal_match_the_gpu(paris, shift):
+    """The kernels convert FP64 <-> FP32 (with a power-of-two scaling) by
+    integer operations on the IEEE fields and form FP64 reciprocals by
+    Newton-Raphson; the self-check compares both with the GPU's conversion
+    and division instructions over values spanning the exponent range, exact
+    rounding ties and special values."""
+    rng = np.random.default_rng(17)
+    v = rng.standard_normal(200000) * 10.0 ** rng.integers(-45, 45, 200000)
+    # values exactly at and next to the FP32 rounding boundary
+    f = rng.standard_normal(20000).astype(np.float32).astype(np.float64)
+    bits = f.view(np.uint64)
+    ties = np.concatenate([(bits + d).view(np.float64) for d in (0x10000000, 0x0FFFFFFF, 0x10000001, 0x30000000)])
+    special = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 3.4028234663852886e38, 1.1754943508222875e-38, 1e-320])
+    x = np.concatenate([v, ties, special, np.abs(v)])
+    assert paris.check_arithmetic(dev(x), shift) == 0
