@@ -38,14 +38,19 @@ UNIT = "solves/s"
 # DRAM traffic of one launch of each instrumented kernel class, from an ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the
 # kernel source is unchanged (sha256 of csrc/kernels.cu at capture time).
+# DRAM bytes (read + write) per launch of the dominant kernel class, from one
+# ncu capture of "python bench.py --single mixed", valid while the source file
+# holding that kernel is unchanged (sha256 prefix); otherwise traffic is null.
 NCU_TRAFFIC = {
-    # two-pass FP32 colour pass on the 256^3 drop field (profiles/rbgs_2pass_drops256.md)
-    "smooth0": {"bytes_per_launch": 335.311e6 + 51.845e6, "kernels_sha": "0dbf60bf644221de"},
+    # finest-level colour pass, "ncu --set full -k regex:rbgs_rho -c 4" of the
+    # command above: 11 zero passes of 177.4 MB and 77 regular passes of 242.9 MB
+    # per solve
+    "smooth0": {"bytes_per_launch": 234.6e6, "source": "rho0.cu", "sha": "4ec254564df83070"},
 }
 
 
-def kernel_source_sha() -> str:
-    p = os.path.join(ROOT, "paper_2012_11744_gb300", "csrc", "kernels.cu")
+def kernel_source_sha(name: str) -> str:
+    p = os.path.join(ROOT, "paper_2012_11744_gb300", "csrc", name)
     with open(p, "rb") as fh:
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
@@ -347,11 +352,13 @@ def run_paris(args, rank, world, local):
     value = world * args.steps / (ms_mixed / 1e3)
     fp64_value = world * k64 / (ms_fp64 / 1e3)
     # roofline of the dominant kernel class (largest summed time)
-    dom = max(prof, key=lambda k: prof[k]["ms"])
+    from paper_2012_11744_gb300 import _abi as pabi
+    dom = max(pabi.K_BYTES, key=lambda k: prof[k]["ms"])
     pk = prof[dom]
     achieved = pk["bytes"] / (pk["ms"] / 1e3) / 1e9 if pk["ms"] > 0 else None
     tr = NCU_TRAFFIC.get(dom)
-    traffic = tr["bytes_per_launch"] if tr and tr.get("kernels_sha") == kernel_source_sha() else None
+    traffic = (tr["bytes_per_launch"] if tr and tr["bytes_per_launch"] and tr["sha"] == kernel_source_sha(tr["source"])
+               else None)
     cpu = None
     if world == 1 and not args.no_cpu:
         import paris_inputs as pi2  # noqa: F401

@@ -324,7 +324,12 @@ typedef enum {
     PARIS_K_PROLONG0 = 2,  /* prolongation + correction onto the finest level */
     PARIS_K_MATVEC0 = 3,   /* Krylov operator application q = A d (+ d.q) */
     PARIS_K_RESID64 = 4,   /* FP64 true residual r = f - A p (+ norms) */
-    PARIS_K_COUNT = 5
+    PARIS_K_COARSE = 5,    /* the V-cycle below the finest level (one timing per V-cycle) */
+    PARIS_K_FIELD = 6,     /* projection step: face coefficients and divergence */
+    PARIS_K_SETUP = 7,     /* per solve: right-hand side, level coefficients, coarsest inverse */
+    PARIS_K_KRYLOV = 8,    /* Krylov vector updates, dot products, reductions, scalar reads */
+    PARIS_K_PROJECT = 9,   /* velocity correction and the mean removal of p */
+    PARIS_K_COUNT = 10
 } paris_kernel_class;
 
 typedef struct {

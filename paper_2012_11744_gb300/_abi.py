@@ -47,7 +47,10 @@ class KernelProf(ct.Structure):
 
 
 K_SMOOTH0, K_RESTRICT0, K_PROLONG0, K_MATVEC0, K_RESID64 = range(5)
-K_NAMES = ("smooth0", "restrict0", "prolong0", "matvec0", "resid64")
+K_NAMES = ("smooth0", "restrict0", "prolong0", "matvec0", "resid64", "coarse", "field", "setup", "krylov",
+           "project")
+# classes of single kernels with an algorithmic byte count (the others group many launches)
+K_BYTES = ("smooth0", "restrict0", "prolong0", "matvec0", "resid64")
 
 
 class Stats(ct.Structure):

@@ -159,6 +159,16 @@ __device__ inline T apply_A(const Stencil<T>& s, const T* __restrict__ x, T xc, 
     return scale * acc;
 }
 
+// 1 / sum of the six face coefficients (the red-black sweeps' inverse diagonal)
+__device__ inline float rcp_rn(float d) { return __frcp_rn(d); }  // == 1.0f / d
+__device__ inline double rcp_rn(double d) { return 1.0 / d; }
+
+template <typename T>
+__device__ inline T inv_sum6(const T (&b)[6]) {
+    const T d = ((b[0] + b[1]) + (b[2] + b[3])) + (b[4] + b[5]);
+    return d > T(0) ? rcp_rn(d) : T(0);
+}
+
 // ------------------------------------------------------------ reductions ---
 
 __device__ inline double warp_sum(double v) {

@@ -458,12 +458,17 @@ void launch_sub_mean(int64_t n, double* x, const Scal* s, cudaStream_t st) {
 }
 
 __global__ void sum_kernel(int64_t n, const double* __restrict__ x, double* partials) {
-    double acc[3] = {0.0, 0.0, 0.0};
+    double sum = 0.0;
+    unsigned long long xmax_k = 0;
+    unsigned nf = 0;
     PARIS_EW_FOR(c, n) {
-        acc[0] += x[c];
-        acc[1] = fmax(acc[1], fabs(x[c]));
-        acc[2] += nonfinite(x[c]);
+        const double v = x[c];
+        sum += v;
+        const unsigned long long k = abs_key(v);
+        xmax_k = k > xmax_k ? k : xmax_k;
+        nf += key_nonfinite(k);
     }
+    double acc[3] = {sum, key_value(xmax_k), (double)nf};
     const int op[3] = {0, 1, 0};
     block_reduce_store<3>(acc, op, partials, blockIdx.x, threadIdx.x);
 }
@@ -585,15 +590,6 @@ void launch_coarse_beta(const Geo& fine, const Coef<T>& cf, const Geo& coarse, c
     }
 }
 
-// 1 / sum of the six face coefficients (the red-black sweeps' inverse diagonal)
-__device__ inline float rcp_rn(float d) { return __frcp_rn(d); }  // == 1.0f / d
-__device__ inline double rcp_rn(double d) { return 1.0 / d; }
-
-template <typename T>
-__device__ inline T inv_sum6(const T (&b)[6]) {
-    const T d = ((b[0] + b[1]) + (b[2] + b[3])) + (b[4] + b[5]);
-    return d > T(0) ? rcp_rn(d) : T(0);
-}
 
 // w = 1 / sum_f beta_f (unscaled inverse diagonal; the smoother divides the
 // right-hand side by the level's scale).

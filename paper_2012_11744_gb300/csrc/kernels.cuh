@@ -146,6 +146,30 @@ void launch_restrict_rho(const Geo& g, const float* rh, double h, const float* f
 void launch_coarse_beta_rho(const Geo& fine, const float* rh, double h, const Geo& coarse, float* out[3],
                             cudaStream_t st);
 
+// ------------------------------------------------ single-launch V-cycle tail ---
+// One level of the tail: coefficients (scaled by `scale`), inverse diagonal
+// (FP64 V-cycles; null: recomputed), solution and right-hand side, and the
+// coarsening factors from the level above.
+template <typename T>
+struct TailLevel {
+    Geo g;
+    int fac[3];
+    T scale;
+    const T* bx;
+    const T* by;
+    const T* bz;
+    const T* w;
+    T* x;
+    T* f;
+};
+constexpr int kMaxTail = 16;         // levels in one tail launch
+constexpr int kMaxDenseCells = 128;  // cells of a dense coarsest level
+// The V-cycle from levels[0] (its f already restricted from above) down to
+// the dense coarsest levels[n-1] (inverse Minv) and back: one block.
+template <typename T>
+void launch_tail_vcycle(const TailLevel<T>* levels, int n, const double* Minv, double omega, int nu1,
+                        int nu2, bool use_w, cudaStream_t st);
+
 // ------------------------------------------------------------ Krylov ------
 // r = f - A x (FP64), optional r32 = scale * r; partials (||r||^2, max|r|, nonfinite).
 // zero_ok: x is the initial guess whose max |x| the prologue stored in s->xmax;

@@ -497,6 +497,58 @@ void vup(paris_ctx* c, const Coef<T>& c0, const T* f0, T* x0, int l) {
     if (o.nu2 > 0) smooth<T>(c, l, cf, f, x, o.nu2, false, true);
 }
 
+// Levels with at most this many cells, down to the dense coarsest level,
+// run as one single-block launch (launch_tail_vcycle).
+constexpr int64_t kTailCells = 4096;
+
+// First level of that tail, or -1 (the tail needs the two-pass red-black
+// smoother, a dense coarsest level and at least one level above it).
+int tail_start(const paris_ctx* c) {
+    const int nl = (int)c->lv.size();
+    if (!c->dense_coarse || c->opts.smoother != PARIS_SMOOTH_RBGS_2PASS || nl < 3) return -1;
+    int t = nl - 1;
+    while (t - 1 >= 1 && c->lv[t - 1].g.ncell() <= kTailCells) --t;
+    if (t >= nl - 1 || nl - t > kMaxTail) return -1;
+    return t;
+}
+
+template <typename T>
+void launch_tail(paris_ctx* c, int t) {
+    const int nl = (int)c->lv.size();
+    TailLevel<T> tl[kMaxTail];
+    for (int l = t; l < nl; ++l) {
+        Level& L = c->lv[l];
+        TailLevel<T>& d = tl[l - t];
+        d.g = L.g;
+        for (int a = 0; a < 3; ++a) d.fac[a] = L.fac[a];
+        d.scale = T(1);
+        d.bx = Prec<T>::b(L, 0);
+        d.by = Prec<T>::b(L, 1);
+        d.bz = Prec<T>::b(L, 2);
+        d.w = sizeof(T) == 8 ? Prec<T>::w(L) : nullptr;
+        d.x = Prec<T>::x(L);
+        d.f = Prec<T>::f(L);
+    }
+    launch_tail_vcycle<T>(tl, nl - t, c->coarse_inv, c->opts.omega, c->opts.nu1, c->opts.nu2, sizeof(T) == 8,
+                          c->st);
+}
+
+// Levels 1 .. L-1 of the V-cycle (level 0's restriction already done).
+template <typename T>
+void coarse_part(paris_ctx* c, const Coef<T>& c0) {
+    const int nl = (int)c->lv.size();
+    const int t = tail_start(c);
+    if (t > 0) {
+        for (int l = 1; l < t; ++l) vdown<T>(c, c0, nullptr, nullptr, l);
+        launch_tail<T>(c, t);
+        for (int l = t - 1; l >= 1; --l) vup<T>(c, c0, nullptr, nullptr, l);
+        return;
+    }
+    for (int l = 1; l < nl - 1; ++l) vdown<T>(c, c0, nullptr, nullptr, l);
+    vcoarse<T>(c, c0, nullptr, nullptr);
+    for (int l = nl - 2; l >= 1; --l) vup<T>(c, c0, nullptr, nullptr, l);
+}
+
 // The part of the V-cycle below level 0 (levels 1 .. L-1) only reads and
 // writes the context's own level arrays, so it is captured once per
 // precision into a CUDA graph and replayed: dozens of small launches on the
@@ -515,9 +567,7 @@ bool coarse_graph_launch(paris_ctx* c, const Coef<T>& c0) {
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            for (int l = 1; l < nl - 1; ++l) vdown<T>(c, c0, nullptr, nullptr, l);
-            vcoarse<T>(c, c0, nullptr, nullptr);
-            for (int l = nl - 2; l >= 1; --l) vup<T>(c, c0, nullptr, nullptr, l);
+            coarse_part<T>(c, c0);
             e = cudaStreamEndCapture(c->st, &g);
         }
         c->st = user;
@@ -543,11 +593,12 @@ void vcycle(paris_ctx* c, const Coef<T>& c0, const T* f0, T* x0) {
     const int nl = (int)c->lv.size();
     if (nl >= 3 && !c->cap_stream_broken) {
         vdown<T>(c, c0, f0, x0, 0);
-        if (coarse_graph_launch<T>(c, c0)) {
-            vup<T>(c, c0, f0, x0, 0);
-            return;
+        {
+            ProfScope ps(c, PARIS_K_COARSE, 0.0);
+            if (!coarse_graph_launch<T>(c, c0)) coarse_part<T>(c, c0);
         }
-        for (int l = 1; l < nl - 1; ++l) vdown<T>(c, c0, f0, x0, l);
+        vup<T>(c, c0, f0, x0, 0);
+        return;
     } else {
         for (int l = 0; l < nl - 1; ++l) vdown<T>(c, c0, f0, x0, l);
     }
@@ -593,6 +644,7 @@ paris_status true_residual(paris_ctx* c, const Coef<double>& c64, const double* 
         nb = launch_residual64(c->g0, c64, c->f, x, r32 ? nullptr : c->r, r32, c->scal, c->partials,
                                zero_ok, c->st);
     }
+    ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
     finalize(c->partials, nb, 3, 2, c->scal, FIN_RNORMS, 0.0, c->st);
     CK(cudaGetLastError());
     return read_scal(c);
@@ -601,7 +653,10 @@ paris_status true_residual(paris_ctx* c, const Coef<double>& c64, const double* 
 // FP64 multigrid-preconditioned CG from the initial guess in x.
 paris_status solve_fp64(paris_ctx* c, const Coef<double>& c64, double* x, SolveOut& out,
                         int max_iter, bool fresh) {
-    setup_hierarchy<double>(c, c64);
+    {
+        ProfScope ps(c, PARIS_K_SETUP, 0.0);
+        setup_hierarchy<double>(c, c64);
+    }
     paris_status s = true_residual(c, c64, x, nullptr, fresh);  // r = f - A x
     if (s != PARIS_OK) return s;
     if (c->scal_h->nonfinite > 0) { out.nonfinite = true; return PARIS_OK; }
@@ -610,24 +665,32 @@ paris_status solve_fp64(paris_ctx* c, const Coef<double>& c64, double* x, SolveO
     int restarts = 0;
     while (out.iters < max_iter) {
         vcycle<double>(c, c64, c->r, c->z);
-        int64_t nb = launch_dot2<double>(N, c->r, c->z, nullptr, c->partials, c->st);
-        finalize(c->partials, nb, 2, 0, c->scal, FIN_RHO_INIT, 0.0, c->st);
-        CK(cudaMemcpyAsync(c->d, c->z, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->st));
+        int64_t nb;
+        {
+            ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
+            nb = launch_dot2<double>(N, c->r, c->z, nullptr, c->partials, c->st);
+            finalize(c->partials, nb, 2, 0, c->scal, FIN_RHO_INIT, 0.0, c->st);
+            CK(cudaMemcpyAsync(c->d, c->z, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->st));
+        }
         bool conv = false;
         while (out.iters < max_iter) {
             {
                 ProfScope ps(c, PARIS_K_MATVEC0, (2.0 * N + beta_count(c->g0)) * 8);
                 nb = launch_matvec_dot<double>(c->g0, c64, c->d, c->q, c->partials, c->st);
             }
-            finalize(c->partials, nb, 1, 0, c->scal, FIN_ALPHA, 0.0, c->st);
-            nb = launch_update_xr<double>(N, c->scal, c->d, c->q, x, c->r, c->partials, c->st);
-            finalize(c->partials, nb, 3, 2, c->scal, FIN_RNORMS, 0.0, c->st);
+            {
+                ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
+                finalize(c->partials, nb, 1, 0, c->scal, FIN_ALPHA, 0.0, c->st);
+                nb = launch_update_xr<double>(N, c->scal, c->d, c->q, x, c->r, c->partials, c->st);
+                finalize(c->partials, nb, 3, 2, c->scal, FIN_RNORMS, 0.0, c->st);
+                s = read_scal(c);
+            }
             ++out.iters;
-            s = read_scal(c);
             if (s != PARIS_OK) return s;
             if (c->scal_h->nonfinite > 0) { out.nonfinite = true; return PARIS_OK; }
             if (meets(c, *c->scal_h)) { conv = true; break; }
             vcycle<double>(c, c64, c->r, c->z);
+            ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
             nb = launch_dot2<double>(N, c->r, c->z, nullptr, c->partials, c->st);
             finalize(c->partials, nb, 2, 0, c->scal, FIN_RHO_BETA, 0.0, c->st);
             launch_xpby<double>(N, c->scal, c->z, c->d, c->st);
@@ -669,13 +732,16 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
     const double* b64[3] = {c64.bx, c64.by, c64.bz};
     Level0Mode mode_guard{c};
     c->rho0 = rho0;
-    if (!rho0) {
-        launch_convert_beta<float>(c->g0, b64, ih2, c->b32_0, c->st);
-        c->half0 = c->opts.half_coefficients != 0;
-        if (c->half0) launch_convert_beta_half(c->g0, b64, c->b16_0, c->st);
-    }
     Coef<float> c32{c->b32_0[0], c->b32_0[1], c->b32_0[2], 1.0f};
-    setup_hierarchy<float>(c, c32);
+    {
+        ProfScope ps(c, PARIS_K_SETUP, 0.0);
+        if (!rho0) {
+            launch_convert_beta<float>(c->g0, b64, ih2, c->b32_0, c->st);
+            c->half0 = c->opts.half_coefficients != 0;
+            if (c->half0) launch_convert_beta_half(c->g0, b64, c->b16_0, c->st);
+        }
+        setup_hierarchy<float>(c, c32);
+    }
     double prev_rr = INFINITY;
     int stalls = 0;
     for (bool first = true;; first = false) {
@@ -695,11 +761,18 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
         double need2 = (c->opts.tol * c->opts.tol * h.bnorm2) / std::max(h.rr, 1e-300) * 1e-2;
         double it2 = c->opts.inner_tol * c->opts.inner_tol;
         const double target = rr32 * std::max(it2, std::min(need2, 1.0));
-        CK(cudaMemsetAsync(c->e32, 0, sizeof(float) * N, c->st));
+        {
+            ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
+            CK(cudaMemsetAsync(c->e32, 0, sizeof(float) * N, c->st));
+        }
         vcycle<float>(c, c32, c->r32, c->z32);
-        int64_t nb = launch_dot2<float>(N, c->r32, c->z32, nullptr, c->partials, c->st);
-        finalize(c->partials, nb, 2, 0, c->scal, FIN_RHO_INIT, 0.0, c->st);
-        CK(cudaMemcpyAsync(c->d32, c->z32, sizeof(float) * N, cudaMemcpyDeviceToDevice, c->st));
+        int64_t nb;
+        {
+            ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
+            nb = launch_dot2<float>(N, c->r32, c->z32, nullptr, c->partials, c->st);
+            finalize(c->partials, nb, 2, 0, c->scal, FIN_RHO_INIT, 0.0, c->st);
+            CK(cudaMemcpyAsync(c->d32, c->z32, sizeof(float) * N, cudaMemcpyDeviceToDevice, c->st));
+        }
         for (int j = 0; j < 50 && out.iters < max_iter; ++j) {
             if (c->rho0) {
                 ProfScope ps(c, PARIS_K_MATVEC0, 3.0 * N * 4);
@@ -708,21 +781,28 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
                 ProfScope ps(c, PARIS_K_MATVEC0, (2.0 * N + beta_count(c->g0)) * 4);
                 nb = launch_matvec_dot<float>(c->g0, c32, c->d32, c->q32, c->partials, c->st);
             }
-            finalize(c->partials, nb, 1, 0, c->scal, FIN_ALPHA, 0.0, c->st);
-            nb = launch_update_xr<float>(N, c->scal, c->d32, c->q32, c->e32, c->r32, c->partials, c->st);
-            finalize(c->partials, nb, 3, 2, c->scal, FIN_STORE, 0.0, c->st);
+            {
+                ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
+                finalize(c->partials, nb, 1, 0, c->scal, FIN_ALPHA, 0.0, c->st);
+                nb = launch_update_xr<float>(N, c->scal, c->d32, c->q32, c->e32, c->r32, c->partials, c->st);
+                finalize(c->partials, nb, 3, 2, c->scal, FIN_STORE, 0.0, c->st);
+                s = read_scal(c);
+            }
             ++out.iters;
-            s = read_scal(c);
             if (s != PARIS_OK) return s;
             const double in_rr = c->scal_h->red[0];
             if (!(in_rr == in_rr) || c->scal_h->red[2] > 0) break;  // non-finite: let the outer step judge
             if (in_rr <= target || in_rr > 1e6 * rr32) break;
             vcycle<float>(c, c32, c->r32, c->z32);
+            ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
             nb = launch_dot2<float>(N, c->z32, c->r32, c->q32, c->partials, c->st);  // (z.r, z.q)
             finalize(c->partials, nb, 2, 0, c->scal, FIN_FCG_BETA, 0.0, c->st);
             launch_xpby<float>(N, c->scal, c->z32, c->d32, c->st);
         }
-        launch_accumulate(N, c->scal, c->e32, x, c->st);
+        {
+            ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
+            launch_accumulate(N, c->scal, c->e32, x, c->st);
+        }
         CK(cudaGetLastError());
     }
 }
@@ -917,7 +997,11 @@ paris_status poisson_solve(paris_ctx* c, const double* bx, const double* by, con
     const double ih2 = 1.0 / (c->grid.h * c->grid.h);
     Coef<double> c64{bx, by, bz, ih2};
     if (!mean_known) CK(cudaMemsetAsync(c->scal, 0, sizeof(Scal), c->st));
-    paris_status s = prologue(c, rhs, p, mean_known);
+    paris_status s;
+    {
+        ProfScope ps(c, PARIS_K_SETUP, 0.0);
+        s = prologue(c, rhs, p, mean_known);
+    }
     if (s != PARIS_OK) return s;
     SolveOut out;
     int fell_back = 0;
@@ -938,7 +1022,10 @@ paris_status poisson_solve(paris_ctx* c, const double* bx, const double* by, con
         if (s != PARIS_OK) return s;
         out.outer = out.iters;
     }
-    s = remove_mean(c, p, c->N);
+    {
+        ProfScope ps(c, PARIS_K_PROJECT, 0.0);
+        s = remove_mean(c, p, c->N);
+    }
     if (s != PARIS_OK) return s;
     s = read_scal(c);
     if (s != PARIS_OK) return s;
@@ -985,20 +1072,27 @@ paris_status paris_projection_step(paris_ctx* c, const double* C, double rho1, d
         return PARIS_ERR_INVALID_ARG;
     if (!(dt > 0.0) || !std::isfinite(dt)) return PARIS_ERR_INVALID_ARG;
     const bool use_rho0 = rho0_usable(c);
-    launch_face_coeffs(c->g0, C, rho1, rho2, c->beta[0], c->beta[1], c->beta[2],
-                       use_rho0 ? c->rh32 : nullptr, c->st);
-    CK(cudaGetLastError());
-    // rhs = div u*/dt and its mean; the solve's prologue forms the mean-free
-    // f = -(rhs - mean) directly (no separate mean removal pass)
-    CK(cudaMemsetAsync(c->scal, 0, sizeof(Scal), c->st));
-    const int64_t nb = launch_divergence(c->g0, u, v, w, 1.0 / (c->grid.h * dt), c->rhs, c->partials, c->st);
-    finalize(c->partials, nb, 3, 2, c->scal, FIN_MEAN_B, (double)c->N, c->st);
-    CK(cudaGetLastError());
+    {
+        ProfScope ps(c, PARIS_K_FIELD, 0.0);
+        launch_face_coeffs(c->g0, C, rho1, rho2, c->beta[0], c->beta[1], c->beta[2],
+                           use_rho0 ? c->rh32 : nullptr, c->st);
+        CK(cudaGetLastError());
+        // rhs = div u*/dt and its mean; the solve's prologue forms the mean-free
+        // f = -(rhs - mean) directly (no separate mean removal pass)
+        CK(cudaMemsetAsync(c->scal, 0, sizeof(Scal), c->st));
+        const int64_t nb =
+            launch_divergence(c->g0, u, v, w, 1.0 / (c->grid.h * dt), c->rhs, c->partials, c->st);
+        finalize(c->partials, nb, 3, 2, c->scal, FIN_MEAN_B, (double)c->N, c->st);
+        CK(cudaGetLastError());
+    }
     paris_status s;
     paris_status solve =
         poisson_solve(c, c->beta[0], c->beta[1], c->beta[2], c->rhs, p, st, use_rho0, true);
     if (solve != PARIS_OK && solve != PARIS_ERR_NOT_CONVERGED) return solve;
-    s = paris_project(c, c->beta[0], c->beta[1], c->beta[2], p, dt, u, v, w);
+    {
+        ProfScope ps(c, PARIS_K_PROJECT, 0.0);
+        s = paris_project(c, c->beta[0], c->beta[1], c->beta[2], p, dt, u, v, w);
+    }
     if (s != PARIS_OK) return s;
     return solve;
 }
