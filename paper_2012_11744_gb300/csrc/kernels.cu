@@ -71,56 +71,6 @@ __device__ inline int64_t flat_block() {
 
 __device__ inline int flat_tid() { return threadIdx.y * blockDim.x + threadIdx.x; }
 
-__device__ inline double nonfinite(double v) { return isfinite(v) ? 0.0 : 1.0; }
-
-// |v| as an integer key: for non-negative doubles (infinities and NaNs
-// included) the order of the bit patterns is the numeric order, so running
-// maxima of magnitudes and the non-finite test need no FP64 instruction (the
-// FP64 pipe runs at 1/64 of the FP32 rate on this GPU).
-__device__ inline unsigned long long abs_key(double v) {
-    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
-}
-__device__ inline unsigned key_nonfinite(unsigned long long k) { return k >= 0x7ff0000000000000ULL ? 1u : 0u; }
-__device__ inline double key_value(unsigned long long k) { return __longlong_as_double((long long)k); }
-
-// Conversions between FP64 and FP32 with a power-of-two scaling, written
-// with integer operations on the IEEE-754 fields: the hardware conversions
-// run on the FP64 pipe at about a fifth of its FMA rate on this GPU.
-//
-// float(v * 2^s): round to nearest, ties to even, for results in the FP32
-// normal range; smaller results flush to a signed zero, larger ones give a
-// signed infinity; infinities stay infinite and NaN stays NaN.
-__device__ inline float d2f_scaled(double v, int s) {
-    const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
-    const unsigned sign = hi & 0x80000000u;
-    const int e = (int)((hi >> 20) & 0x7ffu);
-    if (e == 0x7ff) return __int_as_float((int)(sign | 0x7f800000u | (((hi & 0xfffffu) | lo) ? 0x400000u : 0u)));
-    const int fe = e - 896 + s;  // FP32 biased exponent (FP64 bias 1023, FP32 bias 127)
-    if (e == 0 || fe <= 0) return __int_as_float((int)sign);
-    if (fe >= 255) return __int_as_float((int)(sign | 0x7f800000u));
-    // the 23 leading fraction bits; round on the 29 dropped ones (a carry out
-    // of the fraction correctly increments the exponent)
-    const unsigned frac = ((hi & 0xfffffu) << 3) | (lo >> 29);
-    const unsigned rem = lo & 0x1fffffffu;
-    unsigned bits = ((unsigned)fe << 23) | frac;
-    if (rem > 0x10000000u || (rem == 0x10000000u && (frac & 1u))) bits += 1u;
-    return __int_as_float((int)(sign | bits));
-}
-
-// (double)v * 2^s, exact for normal v whose scaled value is an FP64 normal
-// number; FP32 subnormals flush to a signed zero; infinities and NaN are kept.
-__device__ inline double f2d_scaled(float v, int s) {
-    const unsigned b = (unsigned)__float_as_int(v);
-    const unsigned sign = b & 0x80000000u;
-    const int e = (int)((b >> 23) & 0xffu);
-    const unsigned frac = b & 0x7fffffu;
-    if (e == 0xff) return __hiloint2double((int)(sign | 0x7ff00000u | (frac ? 0x80000u : 0u)), 0);
-    const int de = e + 896 + s;  // FP64 biased exponent
-    if (e == 0 || de <= 0) return __hiloint2double((int)sign, 0);
-    if (de >= 0x7ff) return __hiloint2double((int)(sign | 0x7ff00000u), 0);
-    return __hiloint2double((int)(sign | ((unsigned)de << 20) | (frac >> 3)), (int)(frac << 29));
-}
-
 }  // namespace
 
 static thread_local char g_last_cuda_error[256] = "no CUDA error recorded";
@@ -167,73 +117,7 @@ int64_t max_reduce_blocks(const Geo& g) {
 // partials in a fixed order, then thread 0 applies the scalar update `mode`.
 __global__ void finalize_kernel(const double* __restrict__ partials, int64_t nblocks, int nv,
                                 int maxmask, Scal* s, int mode, double param) {
-    __shared__ double sh[kRedThreads / 32][4];
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
-    const int tid = threadIdx.x;
-    // four interleaved accumulators per value keep four loads in flight
-    for (int q = 0; q < nv; ++q) {
-        const bool mx = (maxmask >> q) & 1;
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-        int64_t b = tid;
-        for (; b + 3 * kRedThreads < nblocks; b += 4 * kRedThreads) {
-            const double t0 = partials[(int64_t)nv * b + q];
-            const double t1 = partials[(int64_t)nv * (b + kRedThreads) + q];
-            const double t2 = partials[(int64_t)nv * (b + 2 * kRedThreads) + q];
-            const double t3 = partials[(int64_t)nv * (b + 3 * kRedThreads) + q];
-            if (mx) { a0 = fmax(a0, t0); a1 = fmax(a1, t1); a2 = fmax(a2, t2); a3 = fmax(a3, t3); }
-            else { a0 += t0; a1 += t1; a2 += t2; a3 += t3; }
-        }
-        for (; b < nblocks; b += kRedThreads) {
-            const double t0 = partials[(int64_t)nv * b + q];
-            a0 = mx ? fmax(a0, t0) : a0 + t0;
-        }
-        v[q] = mx ? fmax(fmax(a0, a1), fmax(a2, a3)) : (a0 + a1) + (a2 + a3);
-    }
-    const int lane = tid & 31, wid = tid >> 5;
-    for (int q = 0; q < 4; ++q) {
-        v[q] = ((maxmask >> q) & 1) ? warp_max(v[q]) : warp_sum(v[q]);
-        if (lane == 0) sh[wid][q] = v[q];
-    }
-    __syncthreads();
-    if (tid == 0) {
-        double r[4];
-        for (int q = 0; q < 4; ++q) {
-            double t = 0.0;
-            for (int w = 0; w < kRedThreads / 32; ++w)
-                t = ((maxmask >> q) & 1) ? fmax(t, sh[w][q]) : t + sh[w][q];
-            r[q] = t;
-            s->red[q] = t;
-        }
-        switch (mode) {
-            case FIN_MEAN_B: s->mean_b = r[0] / param; s->nonfinite += r[2]; break;
-            case FIN_BNORMS:  // the first residual of a solve is f itself: seed rinf with |f|inf
-                s->bnorm2 = r[0]; s->binf = r[1]; s->rinf = r[1]; s->nonfinite += r[2];
-                s->xmax = r[3];
-                break;
-            case FIN_RNORMS: s->rr = r[0]; s->rinf = r[1]; s->nonfinite += r[2]; break;
-            case FIN_ALPHA: s->alpha = (r[0] > 0.0) ? s->rho / r[0] : 0.0; break;
-            case FIN_RHO_BETA: s->beta = (s->rho != 0.0) ? r[0] / s->rho : 0.0; s->rho = r[0]; break;
-            case FIN_RHO_INIT: s->rho = r[0]; s->beta = 0.0; break;
-            case FIN_FCG_BETA:
-                s->beta = (s->rho != 0.0) ? -s->alpha * r[1] / s->rho : 0.0;
-                s->rho = r[0];
-                break;
-            case FIN_SCALE: {
-                // r32 = scale * r64 keeps the FP32 inner problem O(1): scale is
-                // the power of two that maps max |r| into [0.5, 1), so scaling
-                // is an exact exponent shift in both directions
-                const double m = s->rinf > 1e-300 && isfinite(s->rinf) ? s->rinf : 1.0;
-                int ex = 0;
-                frexp(m, &ex);
-                s->scale = ldexp(1.0, -ex);
-                s->inv_scale = ldexp(1.0, ex);
-                s->scale_exp = (double)(-ex);
-                break;
-            }
-            case FIN_INNER_INIT: s->rr0 = r[0]; s->rr = r[0]; s->rinf = r[1]; break;
-            default: break;
-        }
-    }
+    finalize_block(partials, nblocks, nv, maxmask, s, mode, param, threadIdx.x);
 }
 
 void finalize(const double* partials, int64_t nblocks, int nv, int maxmask, Scal* s, int mode,
@@ -284,7 +168,8 @@ __global__ void __launch_bounds__(kTX* kTY) face_coeffs_kernel(Geo g, const doub
                                                               double* __restrict__ bx,
                                                               double* __restrict__ by,
                                                               double* __restrict__ bz,
-                                                              float* __restrict__ rh32) {
+                                                              float* __restrict__ rh32,
+                                                              float2* __restrict__ rh2) {
     __shared__ double sh[2][kTY + 1][kTX + 1];  // [plane parity][1 + row][1 + column]
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -319,16 +204,22 @@ __global__ void __launch_bounds__(kTX* kTY) face_coeffs_kernel(Geo g, const doub
             if (g.wx && i == nx - 1) bx[g.fx(nx, j, k)] = 0.0;
             if (g.wy && j == ny - 1) by[g.fy(i, ny, k)] = 0.0;
             if (g.wz && k == nz - 1) bz[g.fz(i, j, nz)] = 0.0;
-            if (rh32) rh32[c] = d2f_scaled(rc, 0);
+            if (rh32) {
+                const float hi = d2f_scaled(rc, 0);
+                rh32[c] = hi;
+                // the remainder is exact in FP64; its FP32 rounding completes the pair
+                if (rh2) rh2[c] = make_float2(hi, d2f_scaled(rc - f2d_scaled(hi, 0), 0));
+            }
         }
         rzm = rc;
     }
 }
 
 void launch_face_coeffs(const Geo& g, const double* C, double rho1, double rho2, double* bx,
-                        double* by, double* bz, float* rh32, cudaStream_t st) {
+                        double* by, double* bz, float* rh32, float2* rh2, cudaStream_t st) {
     dim3 gr((g.nx + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, (g.nz + kFSeg - 1) / kFSeg);
-    face_coeffs_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(g, C, 0.5 * rho1, 0.5 * rho2, bx, by, bz, rh32);
+    face_coeffs_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(g, C, 0.5 * rho1, 0.5 * rho2, bx, by, bz, rh32,
+                                                      rh2);
     count_launch();
 }
 
@@ -354,7 +245,7 @@ __global__ void __launch_bounds__(kTX* kTY) divergence_kernel(Geo g, const doubl
                                                               const double* __restrict__ w,
                                                               double inv_hdt,
                                                               double* __restrict__ rhs,
-                                                              double* partials) {
+                                                              double* partials, FinSpec fin) {
     const int i = blockIdx.x * kTX + threadIdx.x;
     const int j = blockIdx.y * kTY + threadIdx.y;
     double sum = 0.0;
@@ -371,15 +262,14 @@ __global__ void __launch_bounds__(kTX* kTY) divergence_kernel(Geo g, const doubl
             nf += key_nonfinite(kb);
         })
     }
-    double acc[3] = {sum, key_value(bmax_k), (double)nf};
-    const int op[3] = {0, 1, 0};
-    block_reduce_store<3>(acc, op, partials, flat_block(), flat_tid());
+    block_reduce_skc<double>(sum, bmax_k, nf, partials, flat_block(), flat_tid());
+    finalize_last_block(partials, (int64_t)gridDim.x * gridDim.y * gridDim.z, fin, flat_tid());
 }
 
 int64_t launch_divergence(const Geo& g, const double* u, const double* v, const double* w,
-                          double inv_hdt, double* rhs, double* partials, cudaStream_t st) {
+                          double inv_hdt, double* rhs, double* partials, cudaStream_t st, FinSpec fin) {
     dim3 gr = tile_grid(g, kZ);
-    divergence_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(g, u, v, w, inv_hdt, rhs, partials);
+    divergence_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(g, u, v, w, inv_hdt, rhs, partials, fin);
     count_launch();
     return nblocks_of(gr);
 }
@@ -415,7 +305,7 @@ int64_t launch_max_divergence(const Geo& g, const double* u, const double* v, co
 // f = -(rhs - mean_b): the right-hand side of the SPD system A p = f.
 __global__ void make_rhs_kernel(int64_t n, const double* __restrict__ rhs, const Scal* s,
                                 double* __restrict__ f, const double* __restrict__ x0,
-                                double* partials) {
+                                double* partials, FinSpec fin) {
     const double mb = s->mean_b;
     double l2 = 0.0;
     unsigned long long fmax_k = 0, xmax_k = 0;
@@ -436,12 +326,13 @@ __global__ void make_rhs_kernel(int64_t n, const double* __restrict__ rhs, const
     double acc[4] = {l2, key_value(fmax_k), (double)nf, x0 ? key_value(xmax_k) : 1.0};
     const int op[4] = {0, 1, 0, 1};
     block_reduce_store<4>(acc, op, partials, blockIdx.x, threadIdx.x);
+    finalize_last_block(partials, gridDim.x, fin, threadIdx.x);
 }
 
 int64_t launch_make_rhs(int64_t n, const double* rhs, const Scal* s, double* f, const double* x0,
-                        double* partials, cudaStream_t st) {
+                        double* partials, cudaStream_t st, FinSpec fin) {
     int nb = elementwise_blocks(n);
-    make_rhs_kernel<<<nb, kRedThreads, 0, st>>>(n, rhs, s, f, x0, partials);
+    make_rhs_kernel<<<nb, kRedThreads, 0, st>>>(n, rhs, s, f, x0, partials, fin);
     count_launch();
     return nb;
 }
@@ -468,9 +359,7 @@ __global__ void sum_kernel(int64_t n, const double* __restrict__ x, double* part
         xmax_k = k > xmax_k ? k : xmax_k;
         nf += key_nonfinite(k);
     }
-    double acc[3] = {sum, key_value(xmax_k), (double)nf};
-    const int op[3] = {0, 1, 0};
-    block_reduce_store<3>(acc, op, partials, blockIdx.x, threadIdx.x);
+    block_reduce_skc<double>(sum, xmax_k, nf, partials, blockIdx.x, threadIdx.x);
 }
 
 int64_t launch_sum(int64_t n, const double* x, double* partials, cudaStream_t st) {
@@ -969,7 +858,7 @@ __global__ void __launch_bounds__(kTX* kTY) residual64_kernel(Geo g, Coef<double
                                                               double* __restrict__ r64,
                                                               float* __restrict__ r32,
                                                               const Scal* s, double* partials,
-                                                              int zero_ok) {
+                                                              int zero_ok, FinSpec fin) {
     const int i = blockIdx.x * kTX + threadIdx.x;
     const int j = blockIdx.y * kTY + threadIdx.y;
     double l2 = 0.0;
@@ -1010,21 +899,20 @@ __global__ void __launch_bounds__(kTX* kTY) residual64_kernel(Geo g, Coef<double
             nf += key_nonfinite(kr);
         })
     }
-    double acc[3] = {l2, key_value(rmax_k), (double)nf};
-    const int op[3] = {0, 1, 0};
-    block_reduce_store<3>(acc, op, partials, flat_block(), flat_tid());
+    block_reduce_skc<double>(l2, rmax_k, nf, partials, flat_block(), flat_tid());
+    finalize_last_block(partials, (int64_t)gridDim.x * gridDim.y * gridDim.z, fin, flat_tid());
 }
 
 int64_t launch_residual64(const Geo& g, const Coef<double>& cf, const double* f, const double* x,
                           double* r64, float* r32, const Scal* s, double* partials, bool zero_ok,
-                          cudaStream_t st) {
+                          cudaStream_t st, FinSpec fin) {
     dim3 gr = tile_grid(g, kZ);
     if (fits_i32(g))
         residual64_kernel<true><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, f, x, r64, r32, s, partials,
-                                                               zero_ok ? 1 : 0);
+                                                               zero_ok ? 1 : 0, fin);
     else
         residual64_kernel<false><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, f, x, r64, r32, s, partials,
-                                                                zero_ok ? 1 : 0);
+                                                                zero_ok ? 1 : 0, fin);
     count_launch();
     return nblocks_of(gr);
 }
@@ -1035,7 +923,7 @@ template <typename T, bool I32>
 __global__ void __launch_bounds__(kTX* kTY) matvec_dot_kernel(Geo g, Coef<T> cf,
                                                              const T* __restrict__ d,
                                                              T* __restrict__ q,
-                                                             double* partials) {
+                                                             double* partials, FinSpec fin) {
     const int i = blockIdx.x * kTX + threadIdx.x;
     const int j = blockIdx.y * kTY + threadIdx.y;
     T loc = T(0);
@@ -1061,16 +949,17 @@ __global__ void __launch_bounds__(kTX* kTY) matvec_dot_kernel(Geo g, Coef<T> cf,
     double acc[1] = {(double)loc};
     const int op[1] = {0};
     block_reduce_store<1>(acc, op, partials, flat_block(), flat_tid());
+    finalize_last_block(partials, (int64_t)gridDim.x * gridDim.y * gridDim.z, fin, flat_tid());
 }
 
 template <typename T>
 int64_t launch_matvec_dot(const Geo& g, const Coef<T>& cf, const T* d, T* q, double* partials,
-                          cudaStream_t st) {
+                          cudaStream_t st, FinSpec fin) {
     dim3 gr = tile_grid(g, kZ);
     if (fits_i32(g))
-        matvec_dot_kernel<T, true><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, d, q, partials);
+        matvec_dot_kernel<T, true><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, d, q, partials, fin);
     else
-        matvec_dot_kernel<T, false><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, d, q, partials);
+        matvec_dot_kernel<T, false><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, d, q, partials, fin);
     count_launch();
     return nblocks_of(gr);
 }
@@ -1078,7 +967,7 @@ int64_t launch_matvec_dot(const Geo& g, const Coef<T>& cf, const T* d, T* q, dou
 template <typename T>
 __global__ void update_xr_kernel(int64_t n, const Scal* s, const T* __restrict__ d,
                                  const T* __restrict__ q, T* __restrict__ x, T* __restrict__ r,
-                                 double* partials, int vec) {
+                                 double* partials, int vec, FinSpec fin) {
     using VT = typename V16<T>::type;
     constexpr int W = V16<T>::n;
     const T alpha = (T)s->alpha;
@@ -1115,21 +1004,22 @@ __global__ void update_xr_kernel(int64_t n, const Scal* s, const T* __restrict__
     double acc[3] = {(double)l2, (double)li, nf};
     const int op[3] = {0, 1, 0};
     block_reduce_store<3>(acc, op, partials, blockIdx.x, threadIdx.x);
+    finalize_last_block(partials, gridDim.x, fin, threadIdx.x);
 }
 
 template <typename T>
 int64_t launch_update_xr(int64_t n, const Scal* s, const T* d, const T* q, T* x, T* r,
-                         double* partials, cudaStream_t st) {
+                         double* partials, cudaStream_t st, FinSpec fin) {
     int nb = elementwise_blocks(n);
     update_xr_kernel<T><<<nb, kRedThreads, 0, st>>>(n, s, d, q, x, r, partials,
-                                                    aligned16(d, q, x, r) ? 1 : 0);
+                                                    aligned16(d, q, x, r) ? 1 : 0, fin);
     count_launch();
     return nb;
 }
 
 template <typename T>
 __global__ void dot2_kernel(int64_t n, const T* __restrict__ a, const T* __restrict__ b,
-                            const T* __restrict__ c, double* partials, int vec) {
+                            const T* __restrict__ c, double* partials, int vec, FinSpec fin) {
     using VT = typename V16<T>::type;
     constexpr int W = V16<T>::n;
     T s0 = T(0), s1 = T(0);
@@ -1155,13 +1045,14 @@ __global__ void dot2_kernel(int64_t n, const T* __restrict__ a, const T* __restr
     double acc[2] = {(double)s0, (double)s1};
     const int op[2] = {0, 0};
     block_reduce_store<2>(acc, op, partials, blockIdx.x, threadIdx.x);
+    finalize_last_block(partials, gridDim.x, fin, threadIdx.x);
 }
 
 template <typename T>
 int64_t launch_dot2(int64_t n, const T* a, const T* b, const T* c, double* partials,
-                    cudaStream_t st) {
+                    cudaStream_t st, FinSpec fin) {
     int nb = elementwise_blocks(n);
-    dot2_kernel<T><<<nb, kRedThreads, 0, st>>>(n, a, b, c, partials, aligned16(a, b, c) ? 1 : 0);
+    dot2_kernel<T><<<nb, kRedThreads, 0, st>>>(n, a, b, c, partials, aligned16(a, b, c) ? 1 : 0, fin);
     count_launch();
     return nb;
 }
@@ -1270,11 +1161,11 @@ void launch_check_arithmetic(const double* v, int64_t n, int shift, unsigned lon
     template void launch_prolong_add<T>(const Geo&, const Geo&, const int[3], const T*, T*,   \
                                         cudaStream_t);                                         \
     template int64_t launch_matvec_dot<T>(const Geo&, const Coef<T>&, const T*, T*, double*,   \
-                                          cudaStream_t);                                       \
+                                          cudaStream_t, FinSpec);                              \
     template int64_t launch_update_xr<T>(int64_t, const Scal*, const T*, const T*, T*, T*,     \
-                                         double*, cudaStream_t);                               \
+                                         double*, cudaStream_t, FinSpec);                      \
     template int64_t launch_dot2<T>(int64_t, const T*, const T*, const T*, double*,            \
-                                    cudaStream_t);                                             \
+                                    cudaStream_t, FinSpec);                                    \
     template void launch_xpby<T>(int64_t, const Scal*, const T*, T*, cudaStream_t);
 
 PARIS_INSTANTIATE(float)

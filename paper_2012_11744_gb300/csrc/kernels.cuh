@@ -23,6 +23,8 @@ struct Scal {
     double rr0;          // MIXED: ||r32||_2^2 at the start of the inner solve
     double nonfinite;    // > 0 if a NaN/Inf was seen
     double xmax;         // max |x| of the initial guess (0: the first residual is f)
+    unsigned ticket;     // blocks of the running reduction that stored their partials
+    unsigned pad_;
 };
 
 enum FinalizeMode {
@@ -35,8 +37,117 @@ enum FinalizeMode {
     FIN_RHO_INIT = 6,   // rho = result0 (first direction)
     FIN_FCG_BETA = 7,   // beta = -alpha * result1 / rho, rho = result0 (flexible CG)
     FIN_SCALE = 8,      // scale = 1/max(result1, tiny), rr0 = rr*scale^2 ... (mixed)
-    FIN_INNER_INIT = 9  // rr0 = result0, rr = result0
+    FIN_INNER_INIT = 9, // rr0 = result0, rr = result0
+    FIN_REFINE = 10     // scale from the current rinf, then rr = result0 / scale^2, rinf = result1
 };
+
+// Second stage of a reduction, by one block of kRedThreads threads: fold the
+// nv values of nblocks block partials in a fixed order (four interleaved
+// accumulators per thread, then the warps, then the block), store them in
+// s->red and apply `mode`.  Deterministic: the order depends only on nblocks.
+__device__ inline void finalize_block(const double* partials, int64_t nblocks, int nv, int maxmask, Scal* s,
+                                      int mode, double param, int tid) {
+    __shared__ double sh[kRedThreads / 32][4];
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int q = 0; q < nv; ++q) {
+        const bool mx = (maxmask >> q) & 1;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int64_t b = tid;
+        // partials written by other blocks of this launch: read past L1
+        for (; b + 3 * kRedThreads < nblocks; b += 4 * kRedThreads) {
+            const double t0 = __ldcg(partials + (int64_t)nv * b + q);
+            const double t1 = __ldcg(partials + (int64_t)nv * (b + kRedThreads) + q);
+            const double t2 = __ldcg(partials + (int64_t)nv * (b + 2 * kRedThreads) + q);
+            const double t3 = __ldcg(partials + (int64_t)nv * (b + 3 * kRedThreads) + q);
+            if (mx) { a0 = fmax(a0, t0); a1 = fmax(a1, t1); a2 = fmax(a2, t2); a3 = fmax(a3, t3); }
+            else { a0 += t0; a1 += t1; a2 += t2; a3 += t3; }
+        }
+        for (; b < nblocks; b += kRedThreads) {
+            const double t0 = __ldcg(partials + (int64_t)nv * b + q);
+            a0 = mx ? fmax(a0, t0) : a0 + t0;
+        }
+        v[q] = mx ? fmax(fmax(a0, a1), fmax(a2, a3)) : (a0 + a1) + (a2 + a3);
+    }
+    const int lane = tid & 31, wid = tid >> 5;
+    for (int q = 0; q < 4; ++q) {
+        v[q] = ((maxmask >> q) & 1) ? warp_max(v[q]) : warp_sum(v[q]);
+        if (lane == 0) sh[wid][q] = v[q];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double r[4];
+        for (int q = 0; q < 4; ++q) {
+            double t = 0.0;
+            for (int w = 0; w < kRedThreads / 32; ++w)
+                t = ((maxmask >> q) & 1) ? fmax(t, sh[w][q]) : t + sh[w][q];
+            r[q] = t;
+            s->red[q] = t;
+        }
+        // r32 = scale * r64 keeps the FP32 inner problem O(1): scale is the
+        // power of two that maps max |r| into [0.5, 1), so scaling is an exact
+        // exponent shift in both directions (taken from the previous residual,
+        // kept until its FP32 correction has been accumulated)
+        auto set_scale = [&]() {
+            const double m = s->rinf > 1e-300 && isfinite(s->rinf) ? s->rinf : 1.0;
+            int ex = 0;
+            frexp(m, &ex);
+            s->scale = ldexp(1.0, -ex);
+            s->inv_scale = ldexp(1.0, ex);
+            s->scale_exp = (double)(-ex);
+        };
+        switch (mode) {
+            case FIN_MEAN_B: s->mean_b = r[0] / param; s->nonfinite += r[2]; break;
+            case FIN_BNORMS:  // the first residual of a solve is f itself: seed rinf with |f|inf
+                s->bnorm2 = r[0]; s->binf = r[1]; s->rinf = r[1]; s->nonfinite += r[2];
+                s->xmax = r[3];
+                break;
+            case FIN_RNORMS: s->rr = r[0]; s->rinf = r[1]; s->nonfinite += r[2]; break;
+            case FIN_ALPHA: s->alpha = (r[0] > 0.0) ? s->rho / r[0] : 0.0; break;
+            case FIN_RHO_BETA: s->beta = (s->rho != 0.0) ? r[0] / s->rho : 0.0; s->rho = r[0]; break;
+            case FIN_RHO_INIT: s->rho = r[0]; s->beta = 0.0; break;
+            case FIN_FCG_BETA:
+                s->beta = (s->rho != 0.0) ? -s->alpha * r[1] / s->rho : 0.0;
+                s->rho = r[0];
+                break;
+            case FIN_SCALE: set_scale(); break;
+            case FIN_INNER_INIT: s->rr0 = r[0]; s->rr = r[0]; s->rinf = r[1]; break;
+            case FIN_REFINE:  // the refinement step scaled its r32 by max |r| before the
+                              // step and summed the squares of r32
+                set_scale();
+                s->rr = r[0] * s->inv_scale * s->inv_scale;
+                s->rinf = r[1];
+                s->nonfinite += r[2];
+                break;
+            default: break;
+        }
+    }
+}
+
+// A reduction's second stage fused into its first: `s` null means none (the
+// caller launches finalize).  Otherwise every block, after storing its
+// partials (thread 0 writes them), takes a ticket; the block that takes the
+// last one folds all partials (finalize_block) and resets the ticket.
+struct FinSpec {
+    Scal* s;
+    int nv, maxmask, mode;
+    double param;
+};
+inline FinSpec no_fin() { return FinSpec{nullptr, 0, 0, 0, 0.0}; }
+
+__device__ inline void finalize_last_block(const double* partials, int64_t nblocks, const FinSpec& f, int tid) {
+    if (!f.s) return;
+    __shared__ bool last;
+    if (tid == 0) {
+        __threadfence();  // this block's partials before its ticket
+        const unsigned t = atomicAdd(&f.s->ticket, 1u);
+        last = t == (unsigned)(nblocks - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();  // every other block's partials before the fold
+    finalize_block(partials, nblocks, f.nv, f.maxmask, f.s, f.mode, f.param, tid);
+    if (tid == 0) f.s->ticket = 0u;
+}
 
 // Grid of the element-wise kernels (kEW elements per thread).
 int elementwise_blocks(int64_t n);
@@ -56,16 +167,18 @@ void finalize(const double* partials, int64_t nblocks, int nv, int maxmask, Scal
               double param, cudaStream_t st);
 
 // ---------------------------------------------------------- field steps ---
-// beta = 2/(rho_L + rho_R) (FP64); rh32 (may be null): FP32 copy of rho/2
+// beta = 2/(rho_L + rho_R) (FP64); rh32 (may be null): FP32 copy of rho/2,
+// rh2 (may be null): rho/2 as (hi, lo) FP32 pairs, hi = rh32
 void launch_face_coeffs(const Geo& g, const double* C, double rho1, double rho2, double* bx,
-                        double* by, double* bz, float* rh32, cudaStream_t st);
+                        double* by, double* bz, float* rh32, float2* rh2, cudaStream_t st);
 // rhs = div(u)/(h dt); partials: (sum rhs, max |rhs|, nonfinite count)
 int64_t launch_divergence(const Geo& g, const double* u, const double* v, const double* w,
-                          double inv_hdt, double* rhs, double* partials, cudaStream_t st);
+                          double inv_hdt, double* rhs, double* partials, cudaStream_t st,
+                          FinSpec fin = no_fin());
 // f = -(rhs - mean_b), partials: (||f||^2, max|f|, nonfinite, max|x0|); x0 (the
 // initial guess) may be null
 int64_t launch_make_rhs(int64_t n, const double* rhs, const Scal* s, double* f, const double* x0,
-                        double* partials, cudaStream_t st);
+                        double* partials, cudaStream_t st, FinSpec fin = no_fin());
 void launch_sub_mean(int64_t n, double* x, const Scal* s, cudaStream_t st);
 int64_t launch_sum(int64_t n, const double* x, double* partials, cudaStream_t st);
 void launch_project(const Geo& g, const double* bx, const double* by, const double* bz,
@@ -137,7 +250,7 @@ void launch_rbgs_rho(const Geo& g, const float* rh, double h, const float* f, fl
                      double omega, bool zero_init, cudaStream_t st, int k0 = 0, int k1 = -1);
 // q = A d; partials (d . q); returns the number of blocks
 int64_t launch_matvec_rho(const Geo& g, const float* rh, double h, const float* d, float* q,
-                          double* partials, cudaStream_t st);
+                          double* partials, cudaStream_t st, FinSpec fin = no_fin());
 int64_t rho0_matvec_blocks(const Geo& g);
 // coarse f = mean over the 2x2x2 children of (f - A x); coarse = every axis halved
 void launch_restrict_rho(const Geo& g, const float* rh, double h, const float* f, const float* x,
@@ -145,6 +258,12 @@ void launch_restrict_rho(const Geo& g, const float* rh, double h, const float* f
 // scaled FP32 coefficients of the level with every axis halved
 void launch_coarse_beta_rho(const Geo& fine, const float* rh, double h, const Geo& coarse, float* out[3],
                             cudaStream_t st);
+
+// FP64 refinement step of the mixed form on the finest level, A d in
+// double-float from the rho/2 pairs rh2: x += 2^-a e, r_new = r_old - A 2^-a e,
+// r32 = 2^b r_new (2^a: s->scale, 2^b from s->rinf), norms (FIN_REFINE fused)
+void launch_refine_rho(const Geo& g, const float2* rh2, double h, const float* e, const double* r_old,
+                       double* r_new, double* x, float* r32, Scal* s, double* partials, cudaStream_t st);
 
 // ------------------------------------------------ single-launch V-cycle tail ---
 // One level of the tail: coefficients (scaled by `scale`), inverse diagonal
@@ -176,19 +295,19 @@ void launch_tail_vcycle(const TailLevel<T>* levels, int n, const double* Minv, d
 // when that is 0 the kernel copies r = f instead of applying A.
 int64_t launch_residual64(const Geo& g, const Coef<double>& cf, const double* f, const double* x,
                           double* r64, float* r32, const Scal* s, double* partials, bool zero_ok,
-                          cudaStream_t st);
+                          cudaStream_t st, FinSpec fin = no_fin());
 // q = A d; partials (d . q)
 template <typename T>
 int64_t launch_matvec_dot(const Geo& g, const Coef<T>& cf, const T* d, T* q, double* partials,
-                          cudaStream_t st);
+                          cudaStream_t st, FinSpec fin = no_fin());
 // x += alpha d; r -= alpha q; partials (||r||^2, max|r|, nonfinite)
 template <typename T>
 int64_t launch_update_xr(int64_t n, const Scal* s, const T* d, const T* q, T* x, T* r,
-                         double* partials, cudaStream_t st);
-// partials (a . b, a . c)  (c may be null -> 0)
+                         double* partials, cudaStream_t st, FinSpec fin = no_fin());
+// partials (a . b, a . c)  (c may be null -> 0); fin: fused second stage
 template <typename T>
 int64_t launch_dot2(int64_t n, const T* a, const T* b, const T* c, double* partials,
-                    cudaStream_t st);
+                    cudaStream_t st, FinSpec fin = no_fin());
 // d = z + beta d
 template <typename T>
 void launch_xpby(int64_t n, const Scal* s, const T* z, T* d, cudaStream_t st);

@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(kBX* kVY) op_rho_kernel(Geo g, const float* __
                                                         const float* __restrict__ x,
                                                         const float* __restrict__ f,
                                                         float* __restrict__ out, Geo cg,
-                                                        double* partials, int seg) {
+                                                        double* partials, int seg, FinSpec fin) {
     __shared__ float sh[2][kVY][kBX];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int j = blockIdx.y * kVY + ty;
@@ -506,6 +506,7 @@ __global__ void __launch_bounds__(kBX* kVY) op_rho_kernel(Geo g, const float* __
         const int op[1] = {0};
         const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
         block_reduce_store<1>(red, op, partials, blk, ty * kBX + tx);
+        finalize_last_block(partials, (int64_t)gridDim.x * gridDim.y * gridDim.z, fin, ty * kBX + tx);
     }
 }
 
@@ -515,11 +516,11 @@ int64_t rho0_matvec_blocks(const Geo& g) {
 }
 
 int64_t launch_matvec_rho(const Geo& g, const float* rh, double h, const float* d, float* q,
-                          double* partials, cudaStream_t st) {
+                          double* partials, cudaStream_t st, FinSpec fin) {
     const int seg = segment_planes(g, g.nz, (const void*)op_rho_kernel<false>);
     dim3 gr(pair_blocks_x(g), (g.ny + kVY - 1) / kVY, (g.nz + seg - 1) / seg);
     op_rho_kernel<false><<<gr, dim3(kBX, kVY), 0, st>>>(g, rh, (float)(1.0 / (h * h)), d, nullptr, q, g,
-                                                        partials, seg);
+                                                        partials, seg, fin);
     count_launch();
     return (int64_t)gr.x * gr.y * gr.z;
 }
@@ -529,7 +530,7 @@ void launch_restrict_rho(const Geo& g, const float* rh, double h, const float* f
     const int seg = segment_planes(g, g.nz, (const void*)op_rho_kernel<true>);
     dim3 gr(pair_blocks_x(g), (g.ny + kVY - 1) / kVY, (g.nz + seg - 1) / seg);
     op_rho_kernel<true><<<gr, dim3(kBX, kVY), 0, st>>>(g, rh, (float)(1.0 / (h * h)), x, f, fc, cg,
-                                                       nullptr, seg);
+                                                       nullptr, seg, no_fin());
     count_launch();
 }
 

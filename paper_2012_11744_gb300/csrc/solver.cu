@@ -100,6 +100,7 @@ struct paris_ctx {
     // FP32 half-densities rho/2 from which the finest level's FP32 kernels
     // rebuild their coefficients (paris_opts.level0_density)
     float* rh32 = nullptr;
+    float2* rh2 = nullptr;  // rho/2 as (hi, lo) FP32 pairs for the refinement step
     bool rho0 = false;  // the current solve's level-0 FP32 kernels read rh32 instead of b32_0
     double* partials = nullptr;
     Scal* scal = nullptr;
@@ -231,7 +232,10 @@ paris_status alloc_ctx(paris_ctx* c) {
         c->beta[a] = m.get<double>(c->g0.nface(a));
     }
     c->rhs = m.get<double>(N);
-    if (rho0_fits(c->g0)) c->rh32 = m.get<float>(N);
+    if (rho0_fits(c->g0)) {
+        c->rh32 = m.get<float>(N);
+        c->rh2 = m.get<float2>(N);
+    }
     // block partials: up to 4 values per block of the largest reducing grid
     c->partials = m.get<double>(std::max(max_reduce_blocks(c->g0), rho0_matvec_blocks(c->g0)) * 4);
     c->scal = m.get<Scal>(1);
@@ -626,8 +630,8 @@ paris_status prologue(paris_ctx* c, const double* rhs, const double* x0, bool me
         nb = launch_sum(c->N, rhs, c->partials, c->st);
         finalize(c->partials, nb, 3, 2, c->scal, FIN_MEAN_B, (double)c->N, c->st);
     }
-    nb = launch_make_rhs(c->N, rhs, c->scal, c->f, x0, c->partials, c->st);
-    finalize(c->partials, nb, 4, 0xA, c->scal, FIN_BNORMS, 0.0, c->st);
+    launch_make_rhs(c->N, rhs, c->scal, c->f, x0, c->partials, c->st,
+                    FinSpec{c->scal, 4, 0xA, FIN_BNORMS, 0.0});
     CK(cudaGetLastError());
     return PARIS_OK;
 }
@@ -635,17 +639,15 @@ paris_status prologue(paris_ctx* c, const double* rhs, const double* x0, bool me
 // r = f - A x in FP64 (r32: the scaled FP32 copy only); zero_ok: x is still
 // the initial guess the prologue measured.
 paris_status true_residual(paris_ctx* c, const Coef<double>& c64, const double* x, float* r32,
-                           bool zero_ok = false) {
+                           bool zero_ok = false, bool keep_r64 = false) {
     if (r32) finalize(c->partials, 0, 1, 0, c->scal, FIN_SCALE, 0.0, c->st);
-    int64_t nb;
     {
         const double n = (double)c->N;
         ProfScope ps(c, PARIS_K_RESID64, (16 * n + 8 * beta_count(c->g0)) + (r32 ? 4 : 8) * n);
-        nb = launch_residual64(c->g0, c64, c->f, x, r32 ? nullptr : c->r, r32, c->scal, c->partials,
-                               zero_ok, c->st);
+        launch_residual64(c->g0, c64, c->f, x, (r32 && !keep_r64) ? nullptr : c->r, r32, c->scal, c->partials,
+                          zero_ok, c->st, FinSpec{c->scal, 3, 2, FIN_RNORMS, 0.0});
     }
     ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
-    finalize(c->partials, nb, 3, 2, c->scal, FIN_RNORMS, 0.0, c->st);
     CK(cudaGetLastError());
     return read_scal(c);
 }
@@ -665,24 +667,23 @@ paris_status solve_fp64(paris_ctx* c, const Coef<double>& c64, double* x, SolveO
     int restarts = 0;
     while (out.iters < max_iter) {
         vcycle<double>(c, c64, c->r, c->z);
-        int64_t nb;
         {
             ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
-            nb = launch_dot2<double>(N, c->r, c->z, nullptr, c->partials, c->st);
-            finalize(c->partials, nb, 2, 0, c->scal, FIN_RHO_INIT, 0.0, c->st);
-            CK(cudaMemcpyAsync(c->d, c->z, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->st));
+            launch_dot2<double>(N, c->r, c->z, nullptr, c->partials, c->st,
+                                FinSpec{c->scal, 2, 0, FIN_RHO_INIT, 0.0});
+            std::swap(c->d, c->z);  // first direction d = z: exchange the buffers
         }
         bool conv = false;
         while (out.iters < max_iter) {
             {
                 ProfScope ps(c, PARIS_K_MATVEC0, (2.0 * N + beta_count(c->g0)) * 8);
-                nb = launch_matvec_dot<double>(c->g0, c64, c->d, c->q, c->partials, c->st);
+                launch_matvec_dot<double>(c->g0, c64, c->d, c->q, c->partials, c->st,
+                                          FinSpec{c->scal, 1, 0, FIN_ALPHA, 0.0});
             }
             {
                 ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
-                finalize(c->partials, nb, 1, 0, c->scal, FIN_ALPHA, 0.0, c->st);
-                nb = launch_update_xr<double>(N, c->scal, c->d, c->q, x, c->r, c->partials, c->st);
-                finalize(c->partials, nb, 3, 2, c->scal, FIN_RNORMS, 0.0, c->st);
+                launch_update_xr<double>(N, c->scal, c->d, c->q, x, c->r, c->partials, c->st,
+                                         FinSpec{c->scal, 3, 2, FIN_RNORMS, 0.0});
                 s = read_scal(c);
             }
             ++out.iters;
@@ -691,8 +692,8 @@ paris_status solve_fp64(paris_ctx* c, const Coef<double>& c64, double* x, SolveO
             if (meets(c, *c->scal_h)) { conv = true; break; }
             vcycle<double>(c, c64, c->r, c->z);
             ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
-            nb = launch_dot2<double>(N, c->r, c->z, nullptr, c->partials, c->st);
-            finalize(c->partials, nb, 2, 0, c->scal, FIN_RHO_BETA, 0.0, c->st);
+            launch_dot2<double>(N, c->r, c->z, nullptr, c->partials, c->st,
+                                FinSpec{c->scal, 2, 0, FIN_RHO_BETA, 0.0});
             launch_xpby<double>(N, c->scal, c->z, c->d, c->st);
         }
         // verify with the true residual; restart from it if the recurrence drifted
@@ -742,11 +743,14 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
         }
         setup_hierarchy<float>(c, c32);
     }
+    // With the finest level from rho/2 the refinement step updates r in
+    // double-float (launch_refine_rho) after the first FP64 residual.
+    const bool refine = c->rho0 && c->rh2;
     double prev_rr = INFINITY;
     int stalls = 0;
     for (bool first = true;; first = false) {
         // r32 = scale * (f - A x); x is the untouched initial guess on the first pass
-        paris_status s = true_residual(c, c64, x, c->r32, first);
+        paris_status s = (first || !refine) ? true_residual(c, c64, x, c->r32, first, refine) : read_scal(c);
         if (s != PARIS_OK) return s;
         const Scal& h = *c->scal_h;
         if (h.nonfinite > 0) { out.nonfinite = true; return PARIS_OK; }
@@ -766,26 +770,26 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
             CK(cudaMemsetAsync(c->e32, 0, sizeof(float) * N, c->st));
         }
         vcycle<float>(c, c32, c->r32, c->z32);
-        int64_t nb;
         {
             ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
-            nb = launch_dot2<float>(N, c->r32, c->z32, nullptr, c->partials, c->st);
-            finalize(c->partials, nb, 2, 0, c->scal, FIN_RHO_INIT, 0.0, c->st);
-            CK(cudaMemcpyAsync(c->d32, c->z32, sizeof(float) * N, cudaMemcpyDeviceToDevice, c->st));
+            launch_dot2<float>(N, c->r32, c->z32, nullptr, c->partials, c->st,
+                               FinSpec{c->scal, 2, 0, FIN_RHO_INIT, 0.0});
+            std::swap(c->d32, c->z32);  // first direction d = z: exchange the buffers
         }
         for (int j = 0; j < 50 && out.iters < max_iter; ++j) {
             if (c->rho0) {
                 ProfScope ps(c, PARIS_K_MATVEC0, 3.0 * N * 4);
-                nb = launch_matvec_rho(c->g0, c->rh32, c->grid.h, c->d32, c->q32, c->partials, c->st);
+                launch_matvec_rho(c->g0, c->rh32, c->grid.h, c->d32, c->q32, c->partials, c->st,
+                                  FinSpec{c->scal, 1, 0, FIN_ALPHA, 0.0});
             } else {
                 ProfScope ps(c, PARIS_K_MATVEC0, (2.0 * N + beta_count(c->g0)) * 4);
-                nb = launch_matvec_dot<float>(c->g0, c32, c->d32, c->q32, c->partials, c->st);
+                launch_matvec_dot<float>(c->g0, c32, c->d32, c->q32, c->partials, c->st,
+                                         FinSpec{c->scal, 1, 0, FIN_ALPHA, 0.0});
             }
             {
                 ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
-                finalize(c->partials, nb, 1, 0, c->scal, FIN_ALPHA, 0.0, c->st);
-                nb = launch_update_xr<float>(N, c->scal, c->d32, c->q32, c->e32, c->r32, c->partials, c->st);
-                finalize(c->partials, nb, 3, 2, c->scal, FIN_STORE, 0.0, c->st);
+                launch_update_xr<float>(N, c->scal, c->d32, c->q32, c->e32, c->r32, c->partials, c->st,
+                                        FinSpec{c->scal, 3, 2, FIN_STORE, 0.0});
                 s = read_scal(c);
             }
             ++out.iters;
@@ -795,11 +799,15 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
             if (in_rr <= target || in_rr > 1e6 * rr32) break;
             vcycle<float>(c, c32, c->r32, c->z32);
             ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
-            nb = launch_dot2<float>(N, c->z32, c->r32, c->q32, c->partials, c->st);  // (z.r, z.q)
-            finalize(c->partials, nb, 2, 0, c->scal, FIN_FCG_BETA, 0.0, c->st);
+            launch_dot2<float>(N, c->z32, c->r32, c->q32, c->partials, c->st,  // (z.r, z.q)
+                               FinSpec{c->scal, 2, 0, FIN_FCG_BETA, 0.0});
             launch_xpby<float>(N, c->scal, c->z32, c->d32, c->st);
         }
-        {
+        if (refine) {
+            ProfScope ps(c, PARIS_K_RESID64, 48.0 * N);
+            launch_refine_rho(c->g0, c->rh2, c->grid.h, c->e32, c->r, c->r, x, c->r32, c->scal, c->partials,
+                              c->st);
+        } else {
             ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
             launch_accumulate(N, c->scal, c->e32, x, c->st);
         }
@@ -962,7 +970,7 @@ paris_status paris_face_coeffs(paris_ctx* c, const double* C, double rho1, doubl
     if (!c || !C || !bx || !by || !bz) return PARIS_ERR_INVALID_ARG;
     if (!(rho1 > 0.0) || !(rho2 > 0.0) || !std::isfinite(rho1) || !std::isfinite(rho2))
         return PARIS_ERR_INVALID_ARG;
-    launch_face_coeffs(c->g0, C, rho1, rho2, bx, by, bz, nullptr, c->st);
+    launch_face_coeffs(c->g0, C, rho1, rho2, bx, by, bz, nullptr, nullptr, c->st);
     CK(cudaGetLastError());
     return PARIS_OK;
 }
@@ -1075,7 +1083,7 @@ paris_status paris_projection_step(paris_ctx* c, const double* C, double rho1, d
     {
         ProfScope ps(c, PARIS_K_FIELD, 0.0);
         launch_face_coeffs(c->g0, C, rho1, rho2, c->beta[0], c->beta[1], c->beta[2],
-                           use_rho0 ? c->rh32 : nullptr, c->st);
+                           use_rho0 ? c->rh32 : nullptr, use_rho0 ? c->rh2 : nullptr, c->st);
         CK(cudaGetLastError());
         // rhs = div u*/dt and its mean; the solve's prologue forms the mean-free
         // f = -(rhs - mean) directly (no separate mean removal pass)
