@@ -858,7 +858,7 @@ __global__ void __launch_bounds__(kTX* kTY) residual64_kernel(Geo g, Coef<double
                                                               double* __restrict__ r64,
                                                               float* __restrict__ r32,
                                                               const Scal* s, double* partials,
-                                                              int zero_ok, FinSpec fin) {
+                                                              int zero_ok, int split, FinSpec fin) {
     const int i = blockIdx.x * kTX + threadIdx.x;
     const int j = blockIdx.y * kTY + threadIdx.y;
     double l2 = 0.0;
@@ -892,7 +892,12 @@ __global__ void __launch_bounds__(kTX* kTY) residual64_kernel(Geo g, Coef<double
                 r = fma(-cf.scale, a, f[c]);
             }
             if (r64) r64[c] = r;
-            if (r32) r32[c] = d2f_scaled(r, se);
+            if (r32) {
+                // split: r32 in the colour-split layout (cell i of a row at
+                // i/2, plus nx/2 for colour (i+j+k) odd)
+                const int64_t cs = split ? c - i + (((i + j + k) & 1) ? g.nx / 2 : 0) + (i >> 1) : c;
+                r32[cs] = d2f_scaled(r, se);
+            }
             l2 = fma(r, r, l2);
             const unsigned long long kr = abs_key(r);
             rmax_k = kr > rmax_k ? kr : rmax_k;
@@ -905,14 +910,14 @@ __global__ void __launch_bounds__(kTX* kTY) residual64_kernel(Geo g, Coef<double
 
 int64_t launch_residual64(const Geo& g, const Coef<double>& cf, const double* f, const double* x,
                           double* r64, float* r32, const Scal* s, double* partials, bool zero_ok,
-                          cudaStream_t st, FinSpec fin) {
+                          cudaStream_t st, FinSpec fin, bool split) {
     dim3 gr = tile_grid(g, kZ);
     if (fits_i32(g))
         residual64_kernel<true><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, f, x, r64, r32, s, partials,
-                                                               zero_ok ? 1 : 0, fin);
+                                                               zero_ok ? 1 : 0, split ? 1 : 0, fin);
     else
         residual64_kernel<false><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, f, x, r64, r32, s, partials,
-                                                                zero_ok ? 1 : 0, fin);
+                                                                zero_ok ? 1 : 0, split ? 1 : 0, fin);
     count_launch();
     return nblocks_of(gr);
 }

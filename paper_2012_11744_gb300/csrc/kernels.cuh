@@ -244,6 +244,9 @@ void launch_prolong_add(const Geo& fine, const Geo& coarse, const int fac[3], co
 // ------------------------------------- level 0 rebuilt from the cell densities ---
 // rh: FP32 half-densities rho/2 of the finest level (Eq. muH); the kernels
 // form beta_f = 1/(rh_L + rh_R) in registers and apply 1/h^2 themselves.
+// The FP32 vectors of level 0 (x and f of the smoother, d and q of the inner
+// CG, r32 and e of the refinement) are in the colour-split layout: each row
+// holds its cells of colour (i+j+k) even in order of i, then the odd ones.
 // even nx, ny, nz and 32-bit offsets
 bool rho0_fits(const Geo& g);
 void launch_rbgs_rho(const Geo& g, const float* rh, double h, const float* f, float* x, int color,
@@ -255,13 +258,16 @@ int64_t rho0_matvec_blocks(const Geo& g);
 // coarse f = mean over the 2x2x2 children of (f - A x); coarse = every axis halved
 void launch_restrict_rho(const Geo& g, const float* rh, double h, const float* f, const float* x,
                          const Geo& coarse, float* fc, cudaStream_t st);
+// x += P xc (piecewise constant) onto the split level 0 from the level with every axis halved
+void launch_prolong_split(const Geo& fine, const Geo& coarse, const float* xc, float* x, cudaStream_t st);
 // scaled FP32 coefficients of the level with every axis halved
 void launch_coarse_beta_rho(const Geo& fine, const float* rh, double h, const Geo& coarse, float* out[3],
                             cudaStream_t st);
 
 // FP64 refinement step of the mixed form on the finest level, A d in
 // double-float from the rho/2 pairs rh2: x += 2^-a e, r_new = r_old - A 2^-a e,
-// r32 = 2^b r_new (2^a: s->scale, 2^b from s->rinf), norms (FIN_REFINE fused)
+// r32 = 2^b r_new (2^a: s->scale, 2^b from s->rinf), norms (FIN_REFINE fused);
+// e and r32 in the colour-split layout
 void launch_refine_rho(const Geo& g, const float2* rh2, double h, const float* e, const double* r_old,
                        double* r_new, double* x, float* r32, Scal* s, double* partials, cudaStream_t st);
 
@@ -292,10 +298,11 @@ void launch_tail_vcycle(const TailLevel<T>* levels, int n, const double* Minv, d
 // ------------------------------------------------------------ Krylov ------
 // r = f - A x (FP64), optional r32 = scale * r; partials (||r||^2, max|r|, nonfinite).
 // zero_ok: x is the initial guess whose max |x| the prologue stored in s->xmax;
-// when that is 0 the kernel copies r = f instead of applying A.
+// when that is 0 the kernel copies r = f instead of applying A.  split: r32
+// in the colour-split layout of level 0 (nx even).
 int64_t launch_residual64(const Geo& g, const Coef<double>& cf, const double* f, const double* x,
                           double* r64, float* r32, const Scal* s, double* partials, bool zero_ok,
-                          cudaStream_t st, FinSpec fin = no_fin());
+                          cudaStream_t st, FinSpec fin = no_fin(), bool split = false);
 // q = A d; partials (d . q)
 template <typename T>
 int64_t launch_matvec_dot(const Geo& g, const Coef<T>& cf, const T* d, T* q, double* partials,

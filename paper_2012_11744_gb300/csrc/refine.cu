@@ -98,24 +98,35 @@ __global__ void __launch_bounds__(kTX* kTY) refine_rho_kernel(Geo g, const float
         const int oxm = !xlo ? -1 : (g.wx ? 0 : nx - 1), oxp = !xhi ? 1 : (g.wx ? 0 : -(nx - 1));
         const int oym = !ylo ? -nx : (g.wy ? 0 : (ny - 1) * nx), oyp = !yhi ? nx : (g.wy ? 0 : -(ny - 1) * nx);
         const bool wxm = g.wx && xlo, wxp = g.wx && xhi, wym = g.wy && ylo, wyp = g.wy && yhi;
+        // e and r32 are colour-split: cell i of a row at i/2, plus nx/2 for
+        // colour (i+j+k) odd.  The x-neighbours' entries within the row (the
+        // other colour, so the half is fixed per plane below)
+        const int hx = nx / 2;
+        const int tx = i >> 1;
+        const int txm = (xlo ? nx - 1 : i - 1) >> 1, txp = (xhi ? 0 : i + 1) >> 1;
         const int k0 = blockIdx.z * kZ, k1 = min(k0 + kZ, nz);
         for (int k = k0; k < k1; ++k) {
             const int c = (k * ny + j) * nx + i;
             const bool zlo = k == 0, zhi = k == nz - 1;
             const int ozm = !zlo ? -pl : (g.wz ? 0 : (nz - 1) * pl), ozp = !zhi ? pl : (g.wz ? 0 : -(nz - 1) * pl);
             const bool wzm = g.wz && zlo, wzp = g.wz && zhi;
+            const int odd = (i + j + k) & 1;
+            const int rb = c - i;
+            const int sc = rb + (odd ? hx : 0) + tx;           // this cell
+            const int so = rb + (odd ? 0 : hx);                // other colour's half of this row
+            const int sn = so + tx;                            // y and z neighbours: same entry, other half
             const float2 rc = __ldg(rh2 + c);
-            const float ec = __ldg(e + c);
+            const float ec = __ldg(e + sc);
             // sum over the faces of beta_f (e_c - e_nb) as S + E: S the running
             // FP32 sum of the leading products (two-sum), E every rounding
             // error and low part (faces x-, x+, y-, y+, z-, z+)
             float S = 0.f, E = 0.f;
-            if (!wxm) face_term(rc, __ldg(rh2 + c + oxm), ec, __ldg(e + c + oxm), S, E);
-            if (!wxp) face_term(rc, __ldg(rh2 + c + oxp), ec, __ldg(e + c + oxp), S, E);
-            if (!wym) face_term(rc, __ldg(rh2 + c + oym), ec, __ldg(e + c + oym), S, E);
-            if (!wyp) face_term(rc, __ldg(rh2 + c + oyp), ec, __ldg(e + c + oyp), S, E);
-            if (!wzm) face_term(rc, __ldg(rh2 + c + ozm), ec, __ldg(e + c + ozm), S, E);
-            if (!wzp) face_term(rc, __ldg(rh2 + c + ozp), ec, __ldg(e + c + ozp), S, E);
+            if (!wxm) face_term(rc, __ldg(rh2 + c + oxm), ec, __ldg(e + so + txm), S, E);
+            if (!wxp) face_term(rc, __ldg(rh2 + c + oxp), ec, __ldg(e + so + txp), S, E);
+            if (!wym) face_term(rc, __ldg(rh2 + c + oym), ec, __ldg(e + sn + oym), S, E);
+            if (!wyp) face_term(rc, __ldg(rh2 + c + oyp), ec, __ldg(e + sn + oyp), S, E);
+            if (!wzm) face_term(rc, __ldg(rh2 + c + ozm), ec, __ldg(e + sn + ozm), S, E);
+            if (!wzp) face_term(rc, __ldg(rh2 + c + ozp), ec, __ldg(e + sn + ozp), S, E);
             // A d = 2^-sa (S + E) ih2, the product as a pair, the power of two
             // applied exactly on the FP64 side
             const float qh = __fmul_rn(S, ih2_hi);
@@ -126,7 +137,7 @@ __global__ void __launch_bounds__(kTX* kTY) refine_rho_kernel(Geo g, const float
             r_new[c] = rn;
             x[c] += f2d_scaled(ec, -sa);
             const float rs = d2f_scaled(rn, sb);
-            r32[c] = rs;
+            r32[sc] = rs;
             l2 = __fmaf_rn(rs, rs, l2);
             const unsigned long long kr = abs_key(rn);
             rmax_k = kr > rmax_k ? kr : rmax_k;

@@ -9,18 +9,25 @@
 // registers as beta_f = 1/(rh_L + rh_R) = 2/(rho_L + rho_R), the coefficient
 // the FP64 path stores.  Wall faces have beta = 0 (Sec. 3.8).
 //
-// Thread layout: a thread owns the x-pair of cells (2t, 2t+1) of one row and
-// walks a segment of z-planes (an even number chosen per launch).  The
-// pair's values of the planes above are loaded a few planes ahead into a
-// ring of registers, so each warp keeps
-// several planes of loads in flight while it computes; the values one plane
-// below are carried from the previous step.  The x-neighbours outside the
-// pair are held by the adjacent lanes and arrive by warp shuffles (the lanes
-// at the edges of the warp load theirs); the y-neighbours are loads of the
-// adjacent rows, mostly cache hits.  In a colour pass the updated member of a
-// pair alternates with the plane, and since 2t is even the colour of a plane
-// is the same across the warp: the loop is unrolled by two planes with the
-// member fixed at compile time.
+// Layout: the level-0 FP32 vectors of this mode (the smoother's x and f, the
+// inner CG's vectors) are stored colour-split: each row holds its cells of
+// colour 0 ((i+j+k) even) in order of i, then those of colour 1.  A colour
+// pass then reads and writes the updated colour as one contiguous half-row
+// and every neighbour it needs from the other half, instead of moving whole
+// rows of which it updates half.  rho/2 stays in cell order.
+//
+// Thread layout: a thread owns the x-pair of cells (2t, 2t+1) of one row
+// (entry t of both half-rows) and walks a segment of z-planes (an even number
+// chosen per launch).  The pair's values of the planes above are loaded a few
+// planes ahead into a ring of registers, so each warp keeps several planes of
+// loads in flight while it computes; the values one plane below are carried
+// from the previous step.  The x-neighbours outside the pair are held by the
+// adjacent lanes and arrive by warp shuffles (the lanes at the edges of the
+// warp load theirs); the y-neighbours are loads of the adjacent rows, mostly
+// cache hits.  In a colour pass the updated member of a pair alternates with
+// the plane, and since 2t is even the colour of a plane is the same across
+// the warp: the loop is unrolled by two planes with the member fixed at
+// compile time.
 //
 // Requirements (rho0_fits): nx, ny, nz even and 32-bit offsets; for the
 // restriction a coarse level with every axis halved.
@@ -50,12 +57,6 @@ __device__ __forceinline__ float bface(float a, float b) { return rcp_fast(a + b
 __device__ __forceinline__ float2 ldc2(const float* __restrict__ p, int c) {
     return __ldg(reinterpret_cast<const float2*>(p + c));
 }
-__device__ __forceinline__ float2 ld2(const float* p, int c) {
-    return *reinterpret_cast<const float2*>(p + c);
-}
-__device__ __forceinline__ void st2(float* p, int c, float2 v) {
-    *reinterpret_cast<float2*>(p + c) = v;
-}
 template <int M>
 __device__ __forceinline__ float mem(float2 v) {
     return M ? v.y : v.x;
@@ -77,6 +78,13 @@ struct PairCtx {
     bool xm_wall, xp_wall, ym_wall, yp_wall, wz;
     int xm_off, xp_off;  // offsets of those neighbours from cell i0 (periodic wrap)
     int ym, yp;          // offsets of rows j-1, j+1 from row j (periodic wrap)
+    // colour-split layout of the FP32 vectors: within a row, the cells of
+    // colour 0 ((i+j+k) even) at [0, nx/2), those of colour 1 at [nx/2, nx),
+    // each in order of i; pair t holds one cell of each colour, at index t
+    int hx;              // nx/2
+    int jt;              // j*nx + t: split offset of pair t's colour-0 cell within a plane
+    int tm, tp1;         // t-1 and t+1 wrapped around the row (periodic)
+    int jpar;            // j & 1: cell i0 of plane k has colour (j + k) & 1
 };
 
 __device__ __forceinline__ PairCtx pair_ctx(const Geo& g, int tp, int lane, int j) {
@@ -99,6 +107,12 @@ __device__ __forceinline__ PairCtx pair_ctx(const Geo& g, int tp, int lane, int 
     q.ym = j > 0 ? -g.nx : (g.ny - 1) * g.nx;
     q.yp = j < g.ny - 1 ? g.nx : -(g.ny - 1) * g.nx;
     q.wz = g.wz;
+    q.hx = g.nx / 2;
+    const int t = i0 / 2;
+    q.jt = j * g.nx + t;
+    q.tm = t > 0 ? -1 : q.hx - 1;
+    q.tp1 = t + 1 < q.hx ? 1 : 1 - q.hx;
+    q.jpar = j & 1;
     return q;
 }
 
@@ -198,52 +212,67 @@ bool rho0_fits(const Geo& g) {
 
 namespace {
 
-// One plane's values for a colour pass that updates member M of the pair.
+// One plane's values for a colour pass of colour `col` whose updated cell is
+// member M of the pair (the other member, of the other colour, is the
+// partner).  x and f are in the colour-split layout, rho/2 in cell order.
 struct PassSlot {
-    float2 X, R;                  // x and rh of the pair
-    float xym, xyp, rym, ryp, f;  // member M: x and rh in rows j-1, j+1; f
-    float xo, ro;                 // member M's x-neighbour outside the pair (edge lanes)
+    float xu, xo;           // x of the updated cell and of the partner
+    float2 R;               // rho/2 of the pair (members 0, 1)
+    float xym, xyp;         // x of the updated cell's y-neighbours (rows j-1, j+1)
+    float rym, ryp;         // and their rho/2
+    float f;                // f of the updated cell
+    float xe, re;           // x and rho/2 of its x-neighbour outside the pair (edge lanes)
 };
 
 template <bool ZERO, int M>
 __device__ __forceinline__ void pass_load(PassSlot& s, const PairCtx& q, const float* x,
                                           const float* __restrict__ rh, const float* __restrict__ f,
-                                          int k) {
-    const int o = plane_at(k, q.nz, q.pl, q.cj);
+                                          int col, int k) {
+    const int o = plane_at(k, q.nz, q.pl, q.cj);     // cell i0 (rho/2, cell order)
+    const int os = plane_at(k, q.nz, q.pl, q.jt);    // pair t, colour 0 (split layout)
+    const int ou = os + (col ? q.hx : 0), oo = os + (col ? 0 : q.hx);  // updated / other colour
     s.R = ldc2(rh, o);
     s.rym = __ldg(rh + o + q.ym + M);
     s.ryp = __ldg(rh + o + q.yp + M);
-    s.f = __ldg(f + o + M);
+    s.f = __ldg(f + ou);
     // every lane loads the neighbour outside its pair (a valid cell of the
     // same row; only the edge lanes use it): a conditional load would make
     // the selection wait for the load here instead of three planes later
-    const int oo = o + (M == 0 ? q.xm_off : q.xp_off);
-    s.ro = __ldg(rh + oo);
+    s.re = __ldg(rh + o + (M == 0 ? q.xm_off : q.xp_off));
     if (ZERO) {
-        s.X = make_float2(0.f, 0.f);
-        s.xym = s.xyp = s.xo = 0.f;
+        s.xu = s.xo = s.xym = s.xyp = s.xe = 0.f;
     } else {
-        s.X = ld2(x, o);
-        s.xym = x[o + q.ym + M];
-        s.xyp = x[o + q.yp + M];
+        s.xu = x[ou];
         s.xo = x[oo];
+        // the updated cell's neighbours all have the other colour
+        s.xym = x[oo + q.ym];
+        s.xyp = x[oo + q.yp];
+        s.xe = x[oo + (M == 0 ? q.tm : q.tp1)];
     }
 }
 
 // Over-relaxed Gauss-Seidel update (Eq. eq:beta_pressure, SPD form) of member
 // M of the pair in plane k:
 //   x_c <- x_c + omega ((h^2 f_c + sum_f beta_f x_nb) / sum_f beta_f - x_c);
-// S: this plane, S1: the plane above, xzm/rzm: member M one plane below.
+// S: this plane, S1: the plane above (its partner is the updated cell's
+// z-neighbour), xzm/rzm: x and rho/2 of the z-neighbour below.
 template <bool ZERO, int M>
-__device__ __forceinline__ void pass_plane(const PairCtx& q, float* x, float h2, float omega, int k,
-                                           const PassSlot& S,
-                                           const PassSlot& S1, float xzm, float rzm) {
-    const int c = k * q.pl + q.cj;
-    float2 vo, ro;
-    outer_x<M == 0, M == 1>(q, S.X, S.R, S.xo, S.ro, S.xo, S.ro, vo, ro);
-    const float xu = mem<M>(S.X), xin = mem<1 - M>(S.X);
+__device__ __forceinline__ void pass_plane(const PairCtx& q, float* x, float h2, float omega, int col, int k,
+                                           const PassSlot& S, const PassSlot& S1, float xzm, float rzm) {
+    // the x-neighbour outside the pair: the partner of lane -1 (M = 0) or of
+    // lane +1 (M = 1); edge lanes use their own loads
+    float vo, ro;
+    if (M == 0) {
+        vo = __shfl_up_sync(kAll, S.xo, 1);
+        ro = __shfl_up_sync(kAll, S.R.y, 1);
+        if (!q.xm_lane) { vo = S.xe; ro = S.re; }
+    } else {
+        vo = __shfl_down_sync(kAll, S.xo, 1);
+        ro = __shfl_down_sync(kAll, S.R.x, 1);
+        if (!q.xp_lane) { vo = S.xe; ro = S.re; }
+    }
     const float ru = mem<M>(S.R), rin = mem<1 - M>(S.R);
-    const float b0 = (M == 0 ? q.xm_wall : q.xp_wall) ? 0.f : bface(ru, mem<M>(ro));
+    const float b0 = (M == 0 ? q.xm_wall : q.xp_wall) ? 0.f : bface(ru, ro);
     const float b1 = bface(ru, rin);
     const float b2 = q.ym_wall ? 0.f : bface(ru, S.rym);
     const float b3 = q.yp_wall ? 0.f : bface(ru, S.ryp);
@@ -255,16 +284,19 @@ __device__ __forceinline__ void pass_plane(const PairCtx& q, float* x, float h2,
     if (ZERO) {
         xn = omega * w * fc;
     } else {
-        float acc = fmaf(b0, mem<M>(vo), fc);
-        acc = fmaf(b1, xin, acc);
+        float acc = fmaf(b0, vo, fc);
+        acc = fmaf(b1, S.xo, acc);
         acc = fmaf(b2, S.xym, acc);
         acc = fmaf(b3, S.xyp, acc);
         acc = fmaf(b4, xzm, acc);
-        acc = fmaf(b5, mem<M>(S1.X), acc);
-        xn = fmaf(omega, fmaf(w, acc, -xu), xu);
+        acc = fmaf(b5, S1.xo, acc);
+        xn = fmaf(omega, fmaf(w, acc, -S.xu), S.xu);
     }
-    const float other = ZERO ? 0.f : xin;
-    if (q.act) st2(x, c, M ? make_float2(other, xn) : make_float2(xn, other));
+    if (q.act) {
+        const int os = k * q.pl + q.jt;
+        x[os + (col ? q.hx : 0)] = xn;
+        if (ZERO) x[os + (col ? 0 : q.hx)] = 0.f;  // the other colour starts from zero
+    }
 }
 
 // A ring of R slots over the planes (R even: the updated member alternates
@@ -277,25 +309,26 @@ __device__ __forceinline__ void pass_plane(const PairCtx& q, float* x, float h2,
 template <bool ZERO, int M0, int R, int U>
 struct PassRing {
     __device__ __forceinline__ static bool run(const PairCtx& q, float* x, const float* __restrict__ rh,
-                                               const float* __restrict__ f, float h2, float omega, int k,
-                                               int ke, PassSlot (&S)[R], float& xzm, float& rzm) {
+                                               const float* __restrict__ f, float h2, float omega, int col,
+                                               int k, int ke, PassSlot (&S)[R], float& xzm, float& rzm) {
         constexpr int M = (M0 + U) & 1;  // member updated in plane k + U
         const int kk = k + U;
         if (kk >= ke) return false;
-        if (kk + R - 1 <= ke) pass_load<ZERO, (M0 + U + R - 1) & 1>(S[(U + R - 1) % R], q, x, rh, f, kk + R - 1);
+        if (kk + R - 1 <= ke)
+            pass_load<ZERO, (M0 + U + R - 1) & 1>(S[(U + R - 1) % R], q, x, rh, f, col, kk + R - 1);
         plane_barrier();
-        pass_plane<ZERO, M>(q, x, h2, omega, kk, S[U], S[(U + 1) % R], xzm, rzm);
+        pass_plane<ZERO, M>(q, x, h2, omega, col, kk, S[U], S[(U + 1) % R], xzm, rzm);
         // the next plane updates the other member; its z-neighbour below is
-        // that member of this plane, which this pass does not change
-        xzm = mem<1 - M>(S[U].X);
+        // this plane's partner, which this pass does not change
+        xzm = S[U].xo;
         rzm = mem<1 - M>(S[U].R);
-        return PassRing<ZERO, M0, R, U + 1>::run(q, x, rh, f, h2, omega, k, ke, S, xzm, rzm);
+        return PassRing<ZERO, M0, R, U + 1>::run(q, x, rh, f, h2, omega, col, k, ke, S, xzm, rzm);
     }
 };
 template <bool ZERO, int M0, int R>
 struct PassRing<ZERO, M0, R, R> {
     __device__ __forceinline__ static bool run(const PairCtx&, float*, const float* __restrict__,
-                                               const float* __restrict__, float, float, int, int,
+                                               const float* __restrict__, float, float, int, int, int,
                                                PassSlot (&)[R], float&, float&) {
         return true;
     }
@@ -303,23 +336,22 @@ struct PassRing<ZERO, M0, R, R> {
 
 template <bool ZERO, int M0, int R>
 __device__ __forceinline__ void pass_loop(const PairCtx& q, float* x, const float* __restrict__ rh,
-                                          const float* __restrict__ f, float h2, float omega, int kb,
-                                          int ke) {
+                                          const float* __restrict__ f, float h2, float omega, int col,
+                                          int kb, int ke) {
     static_assert(R % 2 == 0, "the ring length must be even");
     PassSlot S[R];
 #pragma unroll
     for (int u = 0; u < R - 1; ++u) {
-        if (u % 2 == 0) pass_load<ZERO, M0>(S[u], q, x, rh, f, kb + u);
-        else pass_load<ZERO, 1 - M0>(S[u], q, x, rh, f, kb + u);
+        if (u % 2 == 0) pass_load<ZERO, M0>(S[u], q, x, rh, f, col, kb + u);
+        else pass_load<ZERO, 1 - M0>(S[u], q, x, rh, f, col, kb + u);
     }
-    float xzm, rzm;  // the updated member's x and rh one plane below
+    float xzm, rzm;  // the updated cell's z-neighbour below (other colour): x, rho/2
     {
-        const int o = plane_at(kb - 1, q.nz, q.pl, q.cj);
-        rzm = __ldg(rh + o + M0);
-        xzm = ZERO ? 0.f : x[o + M0];
+        rzm = __ldg(rh + plane_at(kb - 1, q.nz, q.pl, q.cj) + M0);
+        xzm = ZERO ? 0.f : x[plane_at(kb - 1, q.nz, q.pl, q.jt) + (col ? 0 : q.hx)];
     }
     for (int k = kb; k < ke; k += R)
-        if (!PassRing<ZERO, M0, R, 0>::run(q, x, rh, f, h2, omega, k, ke, S, xzm, rzm)) break;
+        if (!PassRing<ZERO, M0, R, 0>::run(q, x, rh, f, h2, omega, col, k, ke, S, xzm, rzm)) break;
 }
 
 }  // namespace
@@ -341,9 +373,9 @@ __global__ void __launch_bounds__(kBX* kVY) rbgs_rho_kernel(Geo g, const float* 
     // member of the pair updated in plane kb: (i0 + j + kb) has the colour's
     // parity for i0, i0 even
     if (((j + kb + color) & 1) == 0)
-        pass_loop<ZERO, 0, kPassRing>(q, x, rh, f, h2, omega, kb, ke);
+        pass_loop<ZERO, 0, kPassRing>(q, x, rh, f, h2, omega, color, kb, ke);
     else
-        pass_loop<ZERO, 1, kPassRing>(q, x, rh, f, h2, omega, kb, ke);
+        pass_loop<ZERO, 1, kPassRing>(q, x, rh, f, h2, omega, color, kb, ke);
 }
 
 void launch_rbgs_rho(const Geo& g, const float* rh, double h, const float* f, float* x, int color,
@@ -366,39 +398,54 @@ void launch_rbgs_rho(const Geo& g, const float* rh, double h, const float* f, fl
 
 namespace {
 
-// One plane's values for a full application of A to the pair.
+// One plane's values for a full application of A to the pair.  x (or d) and
+// f are kept as loaded, as the entries of half-rows 0 and 1 (.x, .y); they
+// are put in cell order where they are used, so that no instruction waits
+// for a load before the plane that needs it.
 struct OpSlot {
-    float2 X, R;                // x (or d) and rh of the pair
+    float2 X, R;                // x of the pair (half-rows 0, 1) and rh (cell order)
     float2 Xym, Xyp, Rym, Ryp;  // rows j-1, j+1
-    float2 F;                   // restriction: f of the pair
+    float2 F;                   // restriction: f of the pair (half-rows 0, 1)
     float vm, rm, vp, rp;       // x-neighbours outside the pair (edge lanes)
 };
+
+__device__ __forceinline__ float2 ld_halves(const float* __restrict__ x, int os, int hx) {
+    return make_float2(__ldg(x + os), __ldg(x + os + hx));
+}
+// half-row entries (colour 0, colour 1) in cell order; c0: colour of cell i0
+__device__ __forceinline__ float2 cell_order(float2 v, int c0) {
+    return c0 ? make_float2(v.y, v.x) : v;
+}
 
 template <bool WITH_F>
 __device__ __forceinline__ void op_load(OpSlot& s, const PairCtx& q, const float* __restrict__ x,
                                         const float* __restrict__ rh, const float* __restrict__ f, int k) {
-    const int o = plane_at(k, q.nz, q.pl, q.cj);
-    s.X = ldc2(x, o);
+    const int o = plane_at(k, q.nz, q.pl, q.cj);    // rho/2, cell order
+    const int os = plane_at(k, q.nz, q.pl, q.jt);   // x and f, colour-split layout
+    const int c0 = (q.jpar + k) & 1;                // colour of cell i0 (nz, ny even)
+    s.X = ld_halves(x, os, q.hx);
     s.R = ldc2(rh, o);
-    s.Xym = ldc2(x, o + q.ym);
-    s.Xyp = ldc2(x, o + q.yp);
+    s.Xym = ld_halves(x, os + q.ym, q.hx);
+    s.Xyp = ld_halves(x, os + q.yp, q.hx);
     s.Rym = ldc2(rh, o + q.ym);
     s.Ryp = ldc2(rh, o + q.yp);
-    if (WITH_F) s.F = ldc2(f, o);
-    // unconditional (see pass_load)
-    s.vm = __ldg(x + o + q.xm_off);
+    if (WITH_F) s.F = ld_halves(f, os, q.hx);
+    // unconditional (see pass_load): cell i0-1 has colour 1-c0, cell i0+2 colour c0
+    s.vm = __ldg(x + os + (c0 ? 0 : q.hx) + q.tm);
     s.rm = __ldg(rh + o + q.xm_off);
-    s.vp = __ldg(x + o + q.xp_off);
+    s.vp = __ldg(x + os + (c0 ? q.hx : 0) + q.tp1);
     s.rp = __ldg(rh + o + q.xp_off);
 }
 
 // (A x) / scale for both cells of the pair in plane k: sum_f beta_f (x_c - x_nb)
 // in the face order x-, x+, y-, y+, z-, z+ of the face-array operator.
-// Xm: the pair one plane below; Bzm, Bzp: z-faces below and above.
-__device__ __forceinline__ float2 op_apply(const PairCtx& q, const OpSlot& S, float2 Xm, const OpSlot& S1,
-                                           float2 Bzm, float2 Bzp) {
+// X: the pair in cell order; Xm: the pair one plane below, Xp: the plane
+// above (cell order); Bzm, Bzp: z-faces below and above; c0: colour of cell i0.
+__device__ __forceinline__ float2 op_apply(const PairCtx& q, const OpSlot& S, float2 X, int c0, float2 Xm,
+                                           float2 Xp, float2 Bzm, float2 Bzp) {
     float2 vo, ro;
-    outer_x<true, true>(q, S.X, S.R, S.vm, S.rm, S.vp, S.rp, vo, ro);
+    outer_x<true, true>(q, X, S.R, S.vm, S.rm, S.vp, S.rp, vo, ro);
+    const float2 Xym = cell_order(S.Xym, c0 ^ 1), Xyp = cell_order(S.Xyp, c0 ^ 1);
     const float bxi = bface(S.R.x, S.R.y);
     const float bxm = q.xm_wall ? 0.f : bface(S.R.x, ro.x);
     const float bxp = q.xp_wall ? 0.f : bface(S.R.y, ro.y);
@@ -406,19 +453,18 @@ __device__ __forceinline__ float2 op_apply(const PairCtx& q, const OpSlot& S, fl
                                  : make_float2(bface(S.R.x, S.Rym.x), bface(S.R.y, S.Rym.y));
     const float2 Byp = q.yp_wall ? make_float2(0.f, 0.f)
                                  : make_float2(bface(S.R.x, S.Ryp.x), bface(S.R.y, S.Ryp.y));
-    const float2 X = S.X;
     float a0 = bxm * (X.x - vo.x);
     a0 = fmaf(bxi, X.x - X.y, a0);
-    a0 = fmaf(Bym.x, X.x - S.Xym.x, a0);
-    a0 = fmaf(Byp.x, X.x - S.Xyp.x, a0);
+    a0 = fmaf(Bym.x, X.x - Xym.x, a0);
+    a0 = fmaf(Byp.x, X.x - Xyp.x, a0);
     a0 = fmaf(Bzm.x, X.x - Xm.x, a0);
-    a0 = fmaf(Bzp.x, X.x - S1.X.x, a0);
+    a0 = fmaf(Bzp.x, X.x - Xp.x, a0);
     float a1 = bxi * (X.y - X.x);
     a1 = fmaf(bxp, X.y - vo.y, a1);
-    a1 = fmaf(Bym.y, X.y - S.Xym.y, a1);
-    a1 = fmaf(Byp.y, X.y - S.Xyp.y, a1);
+    a1 = fmaf(Bym.y, X.y - Xym.y, a1);
+    a1 = fmaf(Byp.y, X.y - Xyp.y, a1);
     a1 = fmaf(Bzm.y, X.y - Xm.y, a1);
-    a1 = fmaf(Bzp.y, X.y - S1.X.y, a1);
+    a1 = fmaf(Bzp.y, X.y - Xp.y, a1);
     return make_float2(a0, a1);
 }
 
@@ -436,7 +482,7 @@ __device__ __forceinline__ float2 zfaces(const PairCtx& q, int k, float2 Rlo, fl
 // level with every axis halved; the two fine rows of a coarse cell belong to
 // the warps 2m and 2m+1 of the block and are added through shared memory.
 template <bool RESTRICT>
-__global__ void __launch_bounds__(kBX* kVY) op_rho_kernel(Geo g, const float* __restrict__ rh, float ih2,
+__global__ void __launch_bounds__(kBX* kVY, 3) op_rho_kernel(Geo g, const float* __restrict__ rh, float ih2,
                                                         const float* __restrict__ x,
                                                         const float* __restrict__ f,
                                                         float* __restrict__ out, Geo cg,
@@ -459,25 +505,29 @@ __global__ void __launch_bounds__(kBX* kVY) op_rho_kernel(Geo g, const float* __
     op_load<RESTRICT>(B, q, x, rh, f, kb + 1);
     float2 Xm, Bzm;
     {
-        const int o = plane_at(kb - 1, q.nz, q.pl, q.cj);
-        Xm = ldc2(x, o);
-        Bzm = zfaces(q, kb - 1, ldc2(rh, o), A.R);
+        Xm = cell_order(ld_halves(x, plane_at(kb - 1, q.nz, q.pl, q.jt), q.hx), (q.jpar + kb - 1) & 1);
+        Bzm = zfaces(q, kb - 1, ldc2(rh, plane_at(kb - 1, q.nz, q.pl, q.cj)), A.R);
     }
     int buf = 0;
     auto plane = [&](int k, const OpSlot& S0, const OpSlot& S1) {
         plane_barrier();
-        const int c = k * q.pl + q.cj;
+        const int c0 = (q.jpar + k) & 1;
+        const float2 X = cell_order(S0.X, c0);
         const float2 Bzp = zfaces(q, k, S0.R, S1.R);
-        const float2 a = op_apply(q, S0, Xm, S1, Bzm, Bzp);
+        const float2 a = op_apply(q, S0, X, c0, Xm, cell_order(S1.X, c0 ^ 1), Bzm, Bzp);
         if (!RESTRICT) {
             const float2 Q = make_float2(ih2 * a.x, ih2 * a.y);
             if (store) {
-                st2(out, c, Q);
-                loc = fmaf(S0.X.x, Q.x, loc);
-                loc = fmaf(S0.X.y, Q.y, loc);
+                // q in the colour-split layout
+                const int os = k * q.pl + q.jt;
+                out[os + (c0 ? q.hx : 0)] = Q.x;
+                out[os + (c0 ? 0 : q.hx)] = Q.y;
+                loc = fmaf(X.x, Q.x, loc);
+                loc = fmaf(X.y, Q.y, loc);
             }
         } else {
-            acc += (S0.F.x - ih2 * a.x) + (S0.F.y - ih2 * a.y);
+            const float2 F = cell_order(S0.F, c0);
+            acc += (F.x - ih2 * a.x) + (F.y - ih2 * a.y);
             if ((k - kb) & 1) {  // planes 2K, 2K+1 done: add the row pair
                 sh[buf][ty][tx] = acc;
                 acc = 0.f;
@@ -488,7 +538,7 @@ __global__ void __launch_bounds__(kBX* kVY) op_rho_kernel(Geo g, const float* __
                 buf ^= 1;
             }
         }
-        Xm = S0.X;
+        Xm = X;
         Bzm = Bzp;
     };
     for (int k = kb; k < ke; k += 3) {
@@ -531,6 +581,46 @@ void launch_restrict_rho(const Geo& g, const float* rh, double h, const float* f
     dim3 gr(pair_blocks_x(g), (g.ny + kVY - 1) / kVY, (g.nz + seg - 1) / seg);
     op_rho_kernel<true><<<gr, dim3(kBX, kVY), 0, st>>>(g, rh, (float)(1.0 / (h * h)), x, f, fc, cg,
                                                        nullptr, seg, no_fin());
+    count_launch();
+}
+
+// ---------------------------------------------------------- prolongation ---
+
+// x += P xc onto a colour-split finest level from the level with every axis
+// halved (piecewise-constant P): entry t of both half-rows of row (j, k) is a
+// child of coarse cell (t, j/2, k/2).  V = 4: four entries per thread.
+template <int V>
+__global__ void prolong_split_kernel(Geo fg, Geo cg, const float* __restrict__ xc, float* __restrict__ x) {
+    const int hx = fg.nx / 2;
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (t >= hx || j >= fg.ny) return;
+    const int rb = (k * fg.ny + j) * fg.nx + t;
+    const int cb = ((k >> 1) * cg.ny + (j >> 1)) * cg.nx + t;
+    if (V == 4) {
+        const float4 a = *reinterpret_cast<const float4*>(xc + cb);
+        float4 u = *reinterpret_cast<const float4*>(x + rb);
+        float4 w = *reinterpret_cast<const float4*>(x + rb + hx);
+        u.x += a.x; u.y += a.y; u.z += a.z; u.w += a.w;
+        w.x += a.x; w.y += a.y; w.z += a.z; w.w += a.w;
+        *reinterpret_cast<float4*>(x + rb) = u;
+        *reinterpret_cast<float4*>(x + rb + hx) = w;
+    } else {
+        const float a = xc[cb];
+        x[rb] += a;
+        x[rb + hx] += a;
+    }
+}
+
+void launch_prolong_split(const Geo& fine, const Geo& coarse, const float* xc, float* x, cudaStream_t st) {
+    const int hx = fine.nx / 2;
+    const bool v4 = hx % 4 == 0 && ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(xc)) & 15) == 0;
+    const int per = v4 ? 4 : 1;
+    dim3 blk(32, 8);
+    dim3 gr((hx / per + 31) / 32, (fine.ny + 7) / 8, fine.nz);
+    if (v4) prolong_split_kernel<4><<<gr, blk, 0, st>>>(fine, coarse, xc, x);
+    else prolong_split_kernel<1><<<gr, blk, 0, st>>>(fine, coarse, xc, x);
     count_launch();
 }
 

@@ -496,7 +496,14 @@ void vup(paris_ctx* c, const Coef<T>& c0, const T* f0, T* x0, int l) {
     {
         const double n = (double)c->lv[l].g.ncell();
         ProfScope ps(c, l == 0 ? PARIS_K_PROLONG0 : -1, (2 * n + (double)C.g.ncell()) * sizeof(T));
-        launch_prolong_add<T>(c->lv[l].g, C.g, C.fac, Prec<T>::x(C), x, c->st);
+        bool split = false;
+        if constexpr (sizeof(T) == 4) {
+            if (l == 0 && c->rho0) {
+                launch_prolong_split(c->lv[l].g, C.g, (const float*)Prec<T>::x(C), (float*)x, c->st);
+                split = true;
+            }
+        }
+        if (!split) launch_prolong_add<T>(c->lv[l].g, C.g, C.fac, Prec<T>::x(C), x, c->st);
     }
     if (o.nu2 > 0) smooth<T>(c, l, cf, f, x, o.nu2, false, true);
 }
@@ -645,7 +652,7 @@ paris_status true_residual(paris_ctx* c, const Coef<double>& c64, const double* 
         const double n = (double)c->N;
         ProfScope ps(c, PARIS_K_RESID64, (16 * n + 8 * beta_count(c->g0)) + (r32 ? 4 : 8) * n);
         launch_residual64(c->g0, c64, c->f, x, (r32 && !keep_r64) ? nullptr : c->r, r32, c->scal, c->partials,
-                          zero_ok, c->st, FinSpec{c->scal, 3, 2, FIN_RNORMS, 0.0});
+                          zero_ok, c->st, FinSpec{c->scal, 3, 2, FIN_RNORMS, 0.0}, r32 && c->rho0);
     }
     ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
     CK(cudaGetLastError());
@@ -711,7 +718,7 @@ paris_status solve_fp64(paris_ctx* c, const Coef<double>& c64, double* x, SolveO
 bool rho0_usable(const paris_ctx* c) {
     const paris_opts& o = c->opts;
     if (!o.level0_density || o.precision != PARIS_MIXED || o.smoother != PARIS_SMOOTH_RBGS_2PASS ||
-        o.half_coefficients || !c->rh32 || c->lv.size() < 3)
+        o.half_coefficients || !c->rh32 || !c->rh2 || c->lv.size() < 3)
         return false;
     const Level& L1 = c->lv[1];
     return L1.fac[0] == 2 && L1.fac[1] == 2 && L1.fac[2] == 2;
@@ -744,8 +751,11 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
         setup_hierarchy<float>(c, c32);
     }
     // With the finest level from rho/2 the refinement step updates r in
-    // double-float (launch_refine_rho) after the first FP64 residual.
-    const bool refine = c->rho0 && c->rh2;
+    // double-float (launch_refine_rho) after the first FP64 residual; the
+    // level-0 FP32 vectors are then in the colour-split layout, which only
+    // the rho/2 kernels, the refinement step and the layout-free vector
+    // kernels (dot products, axpy forms) touch.
+    const bool refine = c->rho0;
     double prev_rr = INFINITY;
     int stalls = 0;
     for (bool first = true;; first = false) {
