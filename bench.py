@@ -35,17 +35,15 @@ sys.path.insert(0, ROOT)
 METRIC = "Projection solves/s at 256³, ρ ratio 1000, resid 1e-10: mixed vs FP64; % HBM"
 UNIT = "solves/s"
 
-# DRAM traffic of one launch of each instrumented kernel class, from an ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the
-# kernel source is unchanged (sha256 of csrc/kernels.cu at capture time).
 # DRAM bytes (read + write) per launch of the dominant kernel class, from one
 # ncu capture of "python bench.py --single mixed", valid while the source file
 # holding that kernel is unchanged (sha256 prefix); otherwise traffic is null.
 NCU_TRAFFIC = {
-    # finest-level colour pass, "ncu --set full -k regex:rbgs_rho -c 4" of the
-    # command above: 11 zero passes of 177.4 MB and 77 regular passes of 242.9 MB
-    # per solve
-    "smooth0": {"bytes_per_launch": 234.6e6, "source": "rho0.cu", "sha": "4ec254564df83070"},
+    # finest-level colour pass: DRAM read + write bytes per launch from
+    # "ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
+    #  -k regex:rbgs_rho|op_rho|... -c 24" of "bench.py --single mixed": zero-initial passes
+    # 133.2 MB, regular passes 184.9 MB; 11 and 77 of them per solve
+    "smooth0": {"bytes_per_launch": 178.4e6, "source": "rho0.cu", "sha": "40fd7f17f0558ae1"},
 }
 
 
@@ -223,7 +221,7 @@ def workload_config(n):
     return {"workload": f"drops{n}_walls_z: {n}^3 unit box, periodic x/y, walls z, 64 drops, "
                         f"rho 1000/1, dt 1e-4, tol 1e-10 (L2 and Linf)",
             "grid": [n, n, n], "precision": "mixed FP32 V-cycles in FP64 refinement (value) vs FP64",
-            "l2": "no flush: every step reads C and u*,v*,w* (4 x 134 MB > 129 MB L2)",
+            "l2": "no flush: each step projects its own copies of u*,v*,w* and p and reads C (5 x 134 MB > 129 MB L2)",
             "parallelism": "replicas"}
 
 
@@ -244,21 +242,26 @@ def run_paris(args, rank, world, local):
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     C = d(pr.C)
     u0, v0, w0 = d(pr.u), d(pr.v), d(pr.w)
-    u, v, w = u0.clone(), v0.clone(), w0.clone()
-    p = torch.zeros(g.shape, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
-    results = {}
+    # every timed step projects its own copy of u*, v*, w* from a zero initial
+    # pressure (the step corrects them in place): the copies are made before
+    # the timed region, which then holds the projection steps alone
+    nsets = max(args.steps, 1)
+    sets = [(u0.clone(), v0.clone(), w0.clone(), torch.zeros(g.shape, dtype=torch.float64, device=dev))
+            for _ in range(nsets)]
 
-    def step(ctx):
-        u.copy_(u0)
-        v.copy_(v0)
-        w.copy_(w0)
-        p.zero_()
-        return ctx.projection_step(C, pr.rho1, pr.rho2, pr.dt, u, v, w, p)
+    def refill(K):
+        for (u, v, w, p) in sets[:K]:
+            u.copy_(u0)
+            v.copy_(v0)
+            w.copy_(w0)
+            p.zero_()
 
     def timed(ctx, K, W, prof=False):
         for _ in range(W):
-            st = step(ctx)
+            refill(1)
+            st = ctx.projection_step(C, pr.rho1, pr.rho2, pr.dt, *sets[0])
+        refill(K)
         barrier(world)
         torch.cuda.synchronize(dev)
         if prof:
@@ -268,8 +271,8 @@ def run_paris(args, rank, world, local):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         sts = []
-        for _ in range(K):
-            sts.append(step(ctx))
+        for i in range(K):
+            sts.append(ctx.projection_step(C, pr.rho1, pr.rho2, pr.dt, *sets[i]))
         e1.record(stream)
         torch.cuda.synchronize(dev)
         barrier(world)
@@ -284,9 +287,12 @@ def run_paris(args, rank, world, local):
     # mixed precision (headline)
     ctx = paris.Context(g, opts=paris.default_opts(precision=paris.MIXED), device=dev)
     with ClockSampler(local) as clk:
-        ms_mixed, st_mixed, launches, prof = timed(ctx, args.steps, args.warmup, prof=True)
+        ms_mixed, st_mixed, launches, _ = timed(ctx, args.steps, args.warmup)
     clocks = clk.summary()
     ms_mixed = allreduce_max(ms_mixed, world, dev)
+    # the same steps again with an event pair around every launch of the
+    # instrumented kernel classes (kernel times and the roofline)
+    ms_prof, _, _, prof = timed(ctx, args.steps, 1, prof=True)
     # e2e through the host-buffer entry point (pinned host memory)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     hC, hu0, hv0, hw0 = pin(pr.C), pin(pr.u), pin(pr.v), pin(pr.w)
@@ -312,8 +318,9 @@ def run_paris(args, rank, world, local):
     # plain FP64 form
     ctx = paris.Context(g, opts=paris.default_opts(precision=paris.FP64), device=dev)
     k64 = max(3, args.steps // 2)
-    ms_fp64, st_fp64, _, prof64 = timed(ctx, k64, args.warmup, prof=True)
+    ms_fp64, st_fp64, _, _ = timed(ctx, k64, args.warmup)
     ms_fp64 = allreduce_max(ms_fp64, world, dev)
+    _, _, _, prof64 = timed(ctx, k64, 1, prof=True)
     ctx.close()
 
     # batched mode: 256 uneven periodic instances in one persistent launch
@@ -384,7 +391,9 @@ def run_paris(args, rank, world, local):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
                      "peak_kind": peak_kind, "launches": pk["timed"],
-                     "avg_launch_us": 1e3 * pk["ms"] / max(pk["timed"], 1)},
+                     "avg_launch_us": 1e3 * pk["ms"] / max(pk["timed"], 1),
+                     "timing": f"events around each launch of the class over {args.steps} further "
+                               f"steps ({ms_prof / args.steps:.2f} ms/step with the events)"},
         "kernel_classes": {k: {"launches": v["timed"], "ms": v["ms"],
                                "gbs": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else None}
                            for k, v in prof.items()},
