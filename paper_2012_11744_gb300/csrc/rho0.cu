@@ -43,6 +43,8 @@ constexpr int kVY = 8 / kWX;    // rows per block (8 warps per block)
 constexpr int kBX = kVX * kWX;  // threads along x per block
 constexpr bool kLockstep = false;  // barrier per plane: a block's warps advance together
 constexpr int kPassRing = 4;       // planes in the colour pass's load ring (even)
+constexpr int kTileV = 2;          // pairs per lane of the plane-tile colour pass (0: the ring kernel only)
+constexpr int kTileOpV = 2;        // pairs per lane of the plane-tile product and restriction (0: ring)
 constexpr unsigned kAll = 0xffffffffu;
 
 __device__ __forceinline__ float rcp_fast(float v) {
@@ -378,10 +380,206 @@ __global__ void __launch_bounds__(kBX* kVY) rbgs_rho_kernel(Geo g, const float* 
         pass_loop<ZERO, 1, kPassRing>(q, x, rh, f, h2, omega, color, kb, ke);
 }
 
+// ---- the colour pass over plane tiles, V pairs per lane
+//
+// A block updates one colour in an 8-row tile of one plane; blocks are
+// ordered plane by plane, so the GPU sweeps each array through z as a whole
+// and the planes above and below a tile (read again by the tiles of those
+// planes) come from L2.  Each lane owns V consecutive pairs of a row: its
+// loads are V-wide vectors of the half-rows (16 bytes for V = 4), which
+// streams the level faster than one pair per lane with any depth of
+// prefetch.  Same update, in the same arithmetic order, as pass_plane.
+
+namespace {
+
+template <int N>
+__device__ __forceinline__ void ldv(float (&d)[N], const float* p) {
+    static_assert(N == 2 || N == 4 || N == 8, "vector of 2, 4 or 8 floats");
+    if constexpr (N == 2) {
+        const float2 a = *reinterpret_cast<const float2*>(p);
+        d[0] = a.x;
+        d[1] = a.y;
+    } else {
+#pragma unroll
+        for (int h = 0; h < N / 4; ++h) {
+            const float4 a = *reinterpret_cast<const float4*>(p + 4 * h);
+            d[4 * h] = a.x;
+            d[4 * h + 1] = a.y;
+            d[4 * h + 2] = a.z;
+            d[4 * h + 3] = a.w;
+        }
+    }
+}
+template <int N>
+__device__ __forceinline__ void ldgv(float (&d)[N], const float* __restrict__ p) {
+    static_assert(N == 2 || N == 4 || N == 8, "vector of 2, 4 or 8 floats");
+    if constexpr (N == 2) {
+        const float2 a = __ldg(reinterpret_cast<const float2*>(p));
+        d[0] = a.x;
+        d[1] = a.y;
+    } else {
+#pragma unroll
+        for (int h = 0; h < N / 4; ++h) {
+            const float4 a = __ldg(reinterpret_cast<const float4*>(p + 4 * h));
+            d[4 * h] = a.x;
+            d[4 * h + 1] = a.y;
+            d[4 * h + 2] = a.z;
+            d[4 * h + 3] = a.w;
+        }
+    }
+}
+template <int N>
+__device__ __forceinline__ void stv(float* p, const float (&d)[N]) {
+    if constexpr (N == 2) {
+        *reinterpret_cast<float2*>(p) = make_float2(d[0], d[1]);
+    } else {
+        *reinterpret_cast<float4*>(p) = make_float4(d[0], d[1], d[2], d[3]);
+    }
+}
+
+// member M of the V pairs (2t0 + 2v + M) is updated; walls as in pass_plane
+template <bool ZERO, int V, int M>
+__device__ __forceinline__ void tile_update(const Geo& g, const float* __restrict__ rh,
+                                            const float* __restrict__ f, float* x, float h2, float omega,
+                                            int col, int j, int k, int t0, int lane, bool act) {
+    const int nx = g.nx, hx = nx / 2, pl = nx * g.ny;
+    const int rb = k * pl + j * nx;
+    const int su = rb + (col ? hx : 0) + t0;  // updated colour, entries t0 .. t0+V-1
+    const int so = rb + (col ? 0 : hx) + t0;  // the other colour
+    const int o = rb + 2 * t0;                // rho/2 of cells 2t0 .. 2t0+2V-1
+    const int ym = j > 0 ? -nx : (g.ny - 1) * nx, yp = j < g.ny - 1 ? nx : -(g.ny - 1) * nx;
+    const int zm = k > 0 ? -pl : (g.nz - 1) * pl, zp = k < g.nz - 1 ? pl : -(g.nz - 1) * pl;
+    float R[2 * V], F[V], Q[2 * V];
+    float rym[V], ryp[V], rzm[V], rzp[V];
+    ldgv<2 * V>(R, rh + o);
+    ldgv<V>(F, f + su);
+    ldgv<2 * V>(Q, rh + o + ym);
+#pragma unroll
+    for (int v = 0; v < V; ++v) rym[v] = Q[2 * v + M];
+    ldgv<2 * V>(Q, rh + o + yp);
+#pragma unroll
+    for (int v = 0; v < V; ++v) ryp[v] = Q[2 * v + M];
+    ldgv<2 * V>(Q, rh + o + zm);
+#pragma unroll
+    for (int v = 0; v < V; ++v) rzm[v] = Q[2 * v + M];
+    ldgv<2 * V>(Q, rh + o + zp);
+#pragma unroll
+    for (int v = 0; v < V; ++v) rzp[v] = Q[2 * v + M];
+    // the x-neighbour outside the lane's entries: cell 2t0-1 (M = 0) or
+    // 2t0+2V (M = 1), of the other colour, wrapped around the row
+    const int te = M == 0 ? (t0 > 0 ? -1 : hx - 1) : (t0 + V < hx ? V : V - hx);
+    const float re = __ldg(rh + o + (M == 0 ? (t0 > 0 ? -1 : nx - 1) : (t0 + V < hx ? 2 * V : 2 * V - nx)));
+    float xu[V], xo[V], xym[V], xyp[V], xzm[V], xzp[V], xe = 0.f;
+    if (ZERO) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) xu[v] = xo[v] = xym[v] = xyp[v] = xzm[v] = xzp[v] = 0.f;
+    } else {
+        ldv<V>(xu, x + su);
+        ldv<V>(xo, x + so);
+        ldv<V>(xym, x + so + ym);
+        ldv<V>(xyp, x + so + yp);
+        ldv<V>(xzm, x + so + zm);
+        ldv<V>(xzp, x + so + zp);
+        xe = x[so + te];
+    }
+    // neighbours outside the pair: within the lane's entries, from the
+    // adjacent lane, or (lane at the edge of the warp or of the row) loaded
+    float vo[V], ro[V];
+    if (M == 0) {
+        const float px = __shfl_up_sync(kAll, xo[V - 1], 1), pr = __shfl_up_sync(kAll, R[2 * V - 1], 1);
+        const bool from_lane = lane > 0 && t0 > 0;
+        vo[0] = from_lane ? px : xe;
+        ro[0] = from_lane ? pr : re;
+#pragma unroll
+        for (int v = 1; v < V; ++v) {
+            vo[v] = xo[v - 1];
+            ro[v] = R[2 * v - 1];
+        }
+    } else {
+        const float nxv = __shfl_down_sync(kAll, xo[0], 1), nr = __shfl_down_sync(kAll, R[0], 1);
+        const bool from_lane = lane < 31 && t0 + V < hx;
+#pragma unroll
+        for (int v = 0; v < V - 1; ++v) {
+            vo[v] = xo[v + 1];
+            ro[v] = R[2 * v + 2];
+        }
+        vo[V - 1] = from_lane ? nxv : xe;
+        ro[V - 1] = from_lane ? nr : re;
+    }
+    const bool ym_wall = g.wy && j == 0, yp_wall = g.wy && j == g.ny - 1;
+    const bool zm_wall = g.wz && k == 0, zp_wall = g.wz && k == g.nz - 1;
+    float xn[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const bool xwall = g.wx && (M == 0 ? (t0 + v == 0) : (t0 + v == hx - 1));
+        const float ru = R[2 * v + M], rin = R[2 * v + 1 - M];
+        const float b0 = xwall ? 0.f : bface(ru, ro[v]);
+        const float b1 = bface(ru, rin);
+        const float b2 = ym_wall ? 0.f : bface(ru, rym[v]);
+        const float b3 = yp_wall ? 0.f : bface(ru, ryp[v]);
+        const float b4 = zm_wall ? 0.f : bface(ru, rzm[v]);
+        const float b5 = zp_wall ? 0.f : bface(ru, rzp[v]);
+        const float w = rcp_fast(((b0 + b1) + (b2 + b3)) + (b4 + b5));
+        const float fc = F[v] * h2;
+        if (ZERO) {
+            xn[v] = omega * w * fc;
+        } else {
+            float acc = fmaf(b0, vo[v], fc);
+            acc = fmaf(b1, xo[v], acc);
+            acc = fmaf(b2, xym[v], acc);
+            acc = fmaf(b3, xyp[v], acc);
+            acc = fmaf(b4, xzm[v], acc);
+            acc = fmaf(b5, xzp[v], acc);
+            xn[v] = fmaf(omega, fmaf(w, acc, -xu[v]), xu[v]);
+        }
+    }
+    if (act) {
+        stv<V>(x + su, xn);
+        if (ZERO) {
+            float zr[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) zr[v] = 0.f;
+            stv<V>(x + so, zr);  // the other colour starts from zero
+        }
+    }
+}
+
+}  // namespace
+
+template <bool ZERO, int V>
+__global__ void __launch_bounds__(kBX* kVY) rbgs_rho_tile_kernel(Geo g, const float* __restrict__ rh, float h2,
+                                                               const float* __restrict__ f, float* x,
+                                                               int color, float omega, int k0) {
+    const int j = blockIdx.y * kVY + threadIdx.y;
+    if (j >= g.ny) return;  // uniform per warp
+    const int k = k0 + blockIdx.z;
+    const int lane = threadIdx.x & 31;
+    const int hx = g.nx / 2;
+    const int tv = (blockIdx.x * kBX + threadIdx.x) * V;
+    const bool act = tv < hx;
+    const int t0 = act ? tv : hx - V;  // idle lanes shadow the last entries (no stores)
+    // cell 2t0 has colour (j + k) & 1: the updated member is the same for the whole row
+    if (((j + k + color) & 1) == 0)
+        tile_update<ZERO, V, 0>(g, rh, f, x, h2, omega, color, j, k, t0, lane, act);
+    else
+        tile_update<ZERO, V, 1>(g, rh, f, x, h2, omega, color, j, k, t0, lane, act);
+}
+
 void launch_rbgs_rho(const Geo& g, const float* rh, double h, const float* f, float* x, int color,
                      double omega, bool zero_init, cudaStream_t st, int k0, int k1) {
     if (k1 < 0) k1 = g.nz;
     const float h2 = (float)(h * h);
+    const int hx = g.nx / 2;
+    if (kTileV > 0 && hx % kTileV == 0) {
+        constexpr int V = kTileV > 0 ? kTileV : 2;
+        dim3 gr((hx / V + kBX - 1) / kBX, (g.ny + kVY - 1) / kVY, k1 - k0);
+        if (zero_init)
+            rbgs_rho_tile_kernel<true, V><<<gr, dim3(kBX, kVY), 0, st>>>(g, rh, h2, f, x, color, (float)omega, k0);
+        else
+            rbgs_rho_tile_kernel<false, V><<<gr, dim3(kBX, kVY), 0, st>>>(g, rh, h2, f, x, color, (float)omega, k0);
+        count_launch();
+        return;
+    }
     if (zero_init) {
         const int seg = segment_planes(g, k1 - k0, (const void*)rbgs_rho_kernel<true>);
         dim3 gr(pair_blocks_x(g), (g.ny + kVY - 1) / kVY, (k1 - k0 + seg - 1) / seg);
@@ -560,13 +758,210 @@ __global__ void __launch_bounds__(kBX* kVY, 3) op_rho_kernel(Geo g, const float*
     }
 }
 
+// ---- the product and the restriction over plane tiles, V pairs per lane
+//
+// The layout of the colour pass over tiles (rbgs_rho_tile_kernel): a block
+// applies A to an 8-row tile of one plane (the restriction: of the two planes
+// of one coarse plane), every value a V-wide vector load of a half-row, the
+// planes above and below read again (from L2) by each plane's tiles.
+
+namespace {
+
+// (A x)/scale of the 2V cells 2t0 .. 2t0+2V-1 of row j, plane k, in cell
+// order; C0: colour of cell 2t0 ((j + k) & 1).  Faces in the order x-, x+,
+// y-, y+, z-, z+ of op_apply.  X, F: x (and f) of the cells in cell order.
+template <bool WITH_F, int V, int C0>
+__device__ __forceinline__ void tile_apply(const Geo& g, const float* __restrict__ rh, const float* __restrict__ x,
+                                           const float* __restrict__ f, int j, int k, int t0, int lane,
+                                           float (&a)[2 * V], float (&X)[2 * V], float (&F)[2 * V]) {
+    const int nx = g.nx, hx = nx / 2, pl = nx * g.ny;
+    const int rb = k * pl + j * nx;
+    const int o = rb + 2 * t0;
+    const int ym = j > 0 ? -nx : (g.ny - 1) * nx, yp = j < g.ny - 1 ? nx : -(g.ny - 1) * nx;
+    const int zm = k > 0 ? -pl : (g.nz - 1) * pl, zp = k < g.nz - 1 ? pl : -(g.nz - 1) * pl;
+    // half-rows h = 0, 1 at entries t0 .. t0+V-1; entry v of half h is cell
+    // 2(t0+v) + (h ^ C0) in this row, 2(t0+v) + (h ^ C0 ^ 1) in the rows and
+    // planes next to it
+    float h0[V], h1[V];
+    auto cells = [&](int off, int c0, float (&out)[2 * V]) {
+        ldgv<V>(h0, x + rb + off + t0);
+        ldgv<V>(h1, x + rb + off + hx + t0);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            out[2 * v] = c0 ? h1[v] : h0[v];
+            out[2 * v + 1] = c0 ? h0[v] : h1[v];
+        }
+    };
+    float R[2 * V], Rym[2 * V], Ryp[2 * V], Rzm[2 * V], Rzp[2 * V];
+    float Xym[2 * V], Xyp[2 * V], Xzm[2 * V], Xzp[2 * V];
+    ldgv<2 * V>(R, rh + o);
+    ldgv<2 * V>(Rym, rh + o + ym);
+    ldgv<2 * V>(Ryp, rh + o + yp);
+    ldgv<2 * V>(Rzm, rh + o + zm);
+    ldgv<2 * V>(Rzp, rh + o + zp);
+    cells(0, C0, X);
+    cells(ym, C0 ^ 1, Xym);
+    cells(yp, C0 ^ 1, Xyp);
+    cells(zm, C0 ^ 1, Xzm);
+    cells(zp, C0 ^ 1, Xzp);
+    if (WITH_F) {
+        ldgv<V>(h0, f + rb + t0);
+        ldgv<V>(h1, f + rb + hx + t0);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            F[2 * v] = C0 ? h1[v] : h0[v];
+            F[2 * v + 1] = C0 ? h0[v] : h1[v];
+        }
+    }
+    // cells 2t0-1 (colour C0^1) and 2t0+2V (colour C0) outside the lane's
+    // entries, wrapped around the row: from the adjacent lanes, or loaded
+    const int tl = t0 > 0 ? t0 - 1 : hx - 1, tr = t0 + V < hx ? t0 + V : t0 + V - hx;
+    const float xl_ld = __ldg(x + rb + (C0 ? 0 : hx) + tl), xr_ld = __ldg(x + rb + (C0 ? hx : 0) + tr);
+    const float rl_ld = __ldg(rh + o + (t0 > 0 ? -1 : nx - 1));
+    const float rr_ld = __ldg(rh + o + (t0 + V < hx ? 2 * V : 2 * V - nx));
+    const float xl_sh = __shfl_up_sync(kAll, X[2 * V - 1], 1), rl_sh = __shfl_up_sync(kAll, R[2 * V - 1], 1);
+    const float xr_sh = __shfl_down_sync(kAll, X[0], 1), rr_sh = __shfl_down_sync(kAll, R[0], 1);
+    const bool left_lane = lane > 0 && t0 > 0, right_lane = lane < 31 && t0 + V < hx;
+    const float xl = left_lane ? xl_sh : xl_ld, rl = left_lane ? rl_sh : rl_ld;
+    const float xr = right_lane ? xr_sh : xr_ld, rr = right_lane ? rr_sh : rr_ld;
+    const bool ym_wall = g.wy && j == 0, yp_wall = g.wy && j == g.ny - 1;
+    const bool zm_wall = g.wz && k == 0, zp_wall = g.wz && k == g.nz - 1;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const float bxi = bface(R[2 * v], R[2 * v + 1]);
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const int c = 2 * v + m;
+            float bxm, bxp, xm, xp;
+            if (m == 0) {
+                const bool wall = g.wx && t0 + v == 0;
+                const float xo = v > 0 ? X[c - 1] : xl, ro = v > 0 ? R[c - 1] : rl;
+                bxm = wall ? 0.f : bface(R[c], ro);
+                xm = xo;
+                bxp = bxi;
+                xp = X[c + 1];
+            } else {
+                const bool wall = g.wx && t0 + v == hx - 1;
+                const float xo = v < V - 1 ? X[c + 1] : xr, ro = v < V - 1 ? R[c + 1] : rr;
+                bxm = bxi;
+                xm = X[c - 1];
+                bxp = wall ? 0.f : bface(R[c], ro);
+                xp = xo;
+            }
+            const float bym = ym_wall ? 0.f : bface(R[c], Rym[c]);
+            const float byp = yp_wall ? 0.f : bface(R[c], Ryp[c]);
+            const float bzm = zm_wall ? 0.f : bface(Rzm[c], R[c]);
+            const float bzp = zp_wall ? 0.f : bface(R[c], Rzp[c]);
+            const float xc = X[c];
+            float s = bxm * (xc - xm);
+            s = fmaf(bxp, xc - xp, s);
+            s = fmaf(bym, xc - Xym[c], s);
+            s = fmaf(byp, xc - Xyp[c], s);
+            s = fmaf(bzm, xc - Xzm[c], s);
+            s = fmaf(bzp, xc - Xzp[c], s);
+            a[c] = s;
+        }
+    }
+}
+
+}  // namespace
+
+// RESTRICT = false: q = A d on the tiles of np consecutive planes and the
+// partial sums of d . q (several planes per block keep the blocks, and so
+// the ordered hand-overs of their partial sums, few).
+// RESTRICT = true: coarse f = mean over the 2x2x2 children of f - A x; a
+// block covers the two planes of one coarse plane (np = 2), and the two fine
+// rows of a coarse cell are the warps 2m, 2m+1 of the block, added through
+// shared memory.
+template <bool RESTRICT, int V>
+__global__ void __launch_bounds__(kBX* kVY, 3) op_rho_tile_kernel(Geo g, const float* __restrict__ rh, float ih2,
+                                                             const float* __restrict__ x,
+                                                             const float* __restrict__ f,
+                                                             float* __restrict__ out, Geo cg,
+                                                             double* partials, int np, FinSpec fin) {
+    __shared__ float sh[kVY][kBX * V];
+    const int ty = threadIdx.y, lane = threadIdx.x;
+    const int j = blockIdx.y * kVY + ty;
+    const bool row_ok = j < g.ny;
+    const int jc = row_ok ? j : g.ny - 1;  // idle rows shadow the last row (no stores)
+    const int hx = g.nx / 2;
+    const int tv = (blockIdx.x * kBX + lane) * V;
+    const bool act = row_ok && tv < hx;
+    const int t0 = tv < hx ? tv : hx - V;
+    float loc = 0.f;
+    float acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = 0.f;
+    for (int p = 0; p < np; ++p) {
+        const int k = blockIdx.z * np + p;
+        if (k >= g.nz) break;  // uniform per block
+        float a[2 * V], X[2 * V], F[2 * V];
+        if (((jc + k) & 1) == 0)
+            tile_apply<RESTRICT, V, 0>(g, rh, x, f, jc, k, t0, lane, a, X, F);
+        else
+            tile_apply<RESTRICT, V, 1>(g, rh, x, f, jc, k, t0, lane, a, X, F);
+        if (!RESTRICT) {
+            const int c0 = (jc + k) & 1;
+            float Q[2 * V], q0[V], q1[V];
+#pragma unroll
+            for (int c = 0; c < 2 * V; ++c) Q[c] = ih2 * a[c];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                q0[v] = c0 ? Q[2 * v + 1] : Q[2 * v];
+                q1[v] = c0 ? Q[2 * v] : Q[2 * v + 1];
+            }
+            if (act) {
+                const int rb = (k * g.ny + jc) * g.nx;
+                stv<V>(out + rb + t0, q0);
+                stv<V>(out + rb + hx + t0, q1);
+#pragma unroll
+                for (int c = 0; c < 2 * V; ++c) loc = fmaf(X[c], Q[c], loc);
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] += (F[2 * v] - ih2 * a[2 * v]) + (F[2 * v + 1] - ih2 * a[2 * v + 1]);
+        }
+    }
+    if (RESTRICT) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) sh[ty][lane * V + v] = acc[v];
+        __syncthreads();
+        if ((ty & 1) == 0 && act) {
+            float cf[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) cf[v] = (sh[ty][lane * V + v] + sh[ty + 1][lane * V + v]) * 0.125f;
+            stv<V>(out + ((int)blockIdx.z * cg.ny + (j >> 1)) * cg.nx + t0, cf);
+        }
+    } else {
+        double red[1] = {(double)loc};
+        const int op[1] = {0};
+        const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        block_reduce_store<1>(red, op, partials, blk, ty * kBX + lane);
+        finalize_last_block(partials, (int64_t)gridDim.x * gridDim.y * gridDim.z, fin, ty * kBX + lane);
+    }
+}
+
+constexpr int kTileOpPlanes = 8;  // planes per block of the tile product
+
 int64_t rho0_matvec_blocks(const Geo& g) {
-    // the most blocks any segment length (>= 2 planes) gives
-    return (int64_t)pair_blocks_x(g) * ((g.ny + kVY - 1) / kVY) * ((g.nz + 1) / 2);
+    // the most blocks any segment length (>= 2 planes) gives, or the plane tiles
+    const int64_t ring = (int64_t)pair_blocks_x(g) * ((g.ny + kVY - 1) / kVY) * ((g.nz + 1) / 2);
+    const int64_t tiles = (int64_t)((g.nx / 2 + 2 * kBX - 1) / (2 * kBX)) * ((g.ny + kVY - 1) / kVY) *
+                          ((g.nz + kTileOpPlanes - 1) / kTileOpPlanes);
+    return ring > tiles ? ring : tiles;
 }
 
 int64_t launch_matvec_rho(const Geo& g, const float* rh, double h, const float* d, float* q,
                           double* partials, cudaStream_t st, FinSpec fin) {
+    const int hx = g.nx / 2;
+    if (kTileOpV > 0 && hx % kTileOpV == 0) {
+        constexpr int V = kTileOpV > 0 ? kTileOpV : 2;
+        dim3 gr((hx / V + kBX - 1) / kBX, (g.ny + kVY - 1) / kVY, (g.nz + kTileOpPlanes - 1) / kTileOpPlanes);
+        op_rho_tile_kernel<false, V><<<gr, dim3(kBX, kVY), 0, st>>>(g, rh, (float)(1.0 / (h * h)), d, nullptr, q,
+                                                                    g, partials, kTileOpPlanes, fin);
+        count_launch();
+        return (int64_t)gr.x * gr.y * gr.z;
+    }
     const int seg = segment_planes(g, g.nz, (const void*)op_rho_kernel<false>);
     dim3 gr(pair_blocks_x(g), (g.ny + kVY - 1) / kVY, (g.nz + seg - 1) / seg);
     op_rho_kernel<false><<<gr, dim3(kBX, kVY), 0, st>>>(g, rh, (float)(1.0 / (h * h)), d, nullptr, q, g,
@@ -577,6 +972,15 @@ int64_t launch_matvec_rho(const Geo& g, const float* rh, double h, const float* 
 
 void launch_restrict_rho(const Geo& g, const float* rh, double h, const float* f, const float* x,
                          const Geo& cg, float* fc, cudaStream_t st) {
+    const int hx = g.nx / 2;
+    if (kTileOpV > 0 && hx % kTileOpV == 0) {
+        constexpr int V = kTileOpV > 0 ? kTileOpV : 2;
+        dim3 gr((hx / V + kBX - 1) / kBX, (g.ny + kVY - 1) / kVY, g.nz / 2);
+        op_rho_tile_kernel<true, V><<<gr, dim3(kBX, kVY), 0, st>>>(g, rh, (float)(1.0 / (h * h)), x, f, fc, cg,
+                                                                   nullptr, 2, no_fin());
+        count_launch();
+        return;
+    }
     const int seg = segment_planes(g, g.nz, (const void*)op_rho_kernel<true>);
     dim3 gr(pair_blocks_x(g), (g.ny + kVY - 1) / kVY, (g.nz + seg - 1) / seg);
     op_rho_kernel<true><<<gr, dim3(kBX, kVY), 0, st>>>(g, rh, (float)(1.0 / (h * h)), x, f, fc, cg,

@@ -238,7 +238,10 @@ def test_mixed_with_and_without_fp16_coefficients(paris, half):
 # rebuilds the finest level's FP32 operator from the volume fraction there
 VOF_GRIDS = [pi.Grid(32, 32, 32, 1 / 32), pi.Grid(64, 32, 16, 1 / 64, (P, P, W)),
              pi.Grid(24, 20, 16, 1 / 24, (W, P, W)), pi.Grid(20, 12, 8, 0.05, (W, W, P)),
-             pi.Grid(132, 20, 36, 1 / 132, (P, W, P)), pi.Grid(16, 8, 8, 1 / 16, (W, W, W))]
+             pi.Grid(132, 20, 36, 1 / 132, (P, W, P)), pi.Grid(16, 8, 8, 1 / 16, (W, W, W)),
+             # nx/2 odd: the finest level runs the plane-walking (ring) kernels
+             # instead of the plane-tile ones, which need an even nx/2
+             pi.Grid(30, 20, 12, 1 / 30, (P, W, P)), pi.Grid(22, 12, 16, 1 / 22, (W, P, W))]
 
 
 @pytest.mark.parametrize("vof", [0, 1])
