@@ -293,6 +293,11 @@ def run_paris(args, rank, world, local):
     # the same steps again with an event pair around every launch of the
     # instrumented kernel classes (kernel times and the roofline)
     ms_prof, _, _, prof = timed(ctx, args.steps, 1, prof=True)
+    # this device's streaming rates over four level-0-sized FP32 vectors
+    # (a read-only stream and a triad), the ceilings beside the copy peak
+    sv = [torch.zeros(N, dtype=torch.float32, device=dev) for _ in range(4)]
+    stream_read, stream_triad = paris.stream_rates(*sv, reps=5)
+    del sv
     # e2e through the host-buffer entry point (pinned host memory)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     hC, hu0, hv0, hw0 = pin(pr.C), pin(pr.u), pin(pr.v), pin(pr.w)
@@ -393,7 +398,8 @@ def run_paris(args, rank, world, local):
                      "peak_kind": peak_kind, "launches": pk["timed"],
                      "avg_launch_us": 1e3 * pk["ms"] / max(pk["timed"], 1),
                      "timing": f"events around each launch of the class over {args.steps} further "
-                               f"steps ({ms_prof / args.steps:.2f} ms/step with the events)"},
+                               f"steps ({ms_prof / args.steps:.2f} ms/step with the events)",
+                     "stream_read_only_gbs": stream_read, "stream_triad_gbs": stream_triad},
         "kernel_classes": {k: {"launches": v["timed"], "ms": v["ms"],
                                "gbs": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else None}
                            for k, v in prof.items()},

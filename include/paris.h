@@ -310,6 +310,20 @@ paris_status paris_max_divergence(paris_ctx* ctx, const double* u, const double*
 paris_status paris_check_arithmetic(const double* v, int64_t n, int shift, int64_t* mismatches,
                                     void* stream);
 
+/* Streaming rates of this device (context for roofline reports; no paper
+ * counterpart).  a, b, c, o: device arrays of n floats each (n a positive
+ * multiple of 4, 16-byte aligned), owned by the caller; a, b, c are only
+ * read, o is overwritten.  Two kernels of this library run reps + 1 times
+ * each on `stream` (a cudaStream_t, may be NULL; the call synchronises it),
+ * the first run of each untimed:
+ *   read_gbs  = 12 n bytes / best time of a read-only pass over a, b, c;
+ *   triad_gbs = 12 n bytes / best time of o = a + b/2 (8 n read, 4 n written).
+ * Use vectors larger than the L2 cache for DRAM rates.
+ * Errors: INVALID_ARG (null or misaligned pointers, n < 4 or not a multiple
+ * of 4, reps outside [1, 1000]), CUDA. */
+paris_status paris_stream_rates(const float* a, const float* b, const float* c, float* o, int64_t n, int reps,
+                                double* read_gbs, double* triad_gbs, void* stream);
+
 /* Kernel-class timing (diagnostics for roofline reports).  While enabled,
  * every launch of an instrumented level-0 kernel class is bracketed by a CUDA
  * event pair on the context's stream (a pool of 16384 pairs per enable;

@@ -98,6 +98,8 @@ SIGNATURES = {
     "paris_residual_norms": (ct.c_int, [_P, _P, _P, _P, _P, _P, ct.POINTER(_D), ct.POINTER(_D)]),
     "paris_max_divergence": (ct.c_int, [_P, _P, _P, _P, ct.POINTER(_D)]),
     "paris_check_arithmetic": (ct.c_int, [_P, ct.c_int64, ct.c_int, ct.POINTER(ct.c_int64), _P]),
+    "paris_stream_rates": (ct.c_int, [_P, _P, _P, _P, ct.c_int64, ct.c_int, ct.POINTER(ct.c_double),
+                                      ct.POINTER(ct.c_double), _P]),
     "paris_profile": (ct.c_int, [_P, ct.c_int]),
     "paris_profile_read": (ct.c_int, [_P, ct.c_int, ct.POINTER(KernelProf)]),
     "paris_launch_count": (ct.c_int64, []),

@@ -66,6 +66,21 @@ def check_arithmetic(v, shift: int = 0) -> int:
     return int(out.value)
 
 
+def stream_rates(a, b, c, o, reps: int = 5) -> tuple:
+    """paris_stream_rates on four contiguous float32 CUDA tensors of one size
+    (a, b, c read; o overwritten): (read-only GB/s, triad GB/s)."""
+    ts = (a, b, c, o)
+    if not all(isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+               and t.numel() == a.numel() for t in ts):
+        raise TypeError("a, b, c, o must be contiguous float32 CUDA tensors of one size")
+    rd, tr = ct.c_double(0.0), ct.c_double(0.0)
+    stream = torch.cuda.current_stream(a.device).cuda_stream
+    _abi.check(_abi.load().paris_stream_rates(*(ct.c_void_p(t.data_ptr()) for t in ts), a.numel(), int(reps),
+                                              ct.byref(rd), ct.byref(tr), ct.c_void_p(stream)),
+               "paris_stream_rates")
+    return rd.value, tr.value
+
+
 def _grid_struct(g) -> _abi.Grid:
     s = _abi.Grid()
     s.nx, s.ny, s.nz, s.h = int(g.nx), int(g.ny), int(g.nz), float(g.h)

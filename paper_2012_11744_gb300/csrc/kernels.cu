@@ -1147,6 +1147,67 @@ void launch_check_arithmetic(const double* v, int64_t n, int shift, unsigned lon
     count_launch();
 }
 
+// --------------------------------------------------- streaming probes ---
+
+// Reads a, b and c once (a.b + a.c per block, stored to o[block] so the
+// loads stay live): the rate of a read-only stream.
+__global__ void stream_read3_kernel(const float4* __restrict__ a, const float4* __restrict__ b,
+                                    const float4* __restrict__ c, float* __restrict__ o, int64_t nv) {
+    float s = 0.f;
+    PARIS_VEC_FOR(i, nv) {
+        const float4 x = a[i], y = b[i], z = c[i];
+        s = fmaf(x.x, y.x + z.x, s);
+        s = fmaf(x.y, y.y + z.y, s);
+        s = fmaf(x.z, y.z + z.z, s);
+        s = fmaf(x.w, y.w + z.w, s);
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+    if ((threadIdx.x & 31) == 0) atomicAdd(o + blockIdx.x, s);
+}
+
+// o = a + 0.5 b: two streams read, one written
+__global__ void stream_triad_kernel(const float4* __restrict__ a, const float4* __restrict__ b,
+                                    float4* __restrict__ o, int64_t nv) {
+    PARIS_VEC_FOR(i, nv) {
+        const float4 x = a[i], y = b[i];
+        o[i] = make_float4(fmaf(0.5f, y.x, x.x), fmaf(0.5f, y.y, x.y), fmaf(0.5f, y.z, x.z), fmaf(0.5f, y.w, x.w));
+    }
+}
+
+cudaError_t stream_rates(const float* a, const float* b, const float* c, float* o, int64_t n, int reps,
+                         double* read_gbs, double* triad_gbs, cudaStream_t st) {
+    const int64_t nv = n / 4;
+    // two waves of 8 resident blocks per SM: the fastest grid for these streams
+    const int nb = (int)std::min<int64_t>((nv + kRedThreads - 1) / kRedThreads, 152 * 16);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best_r = 1e30f, best_t = 1e30f;
+    for (int r = 0; e == cudaSuccess && r <= reps; ++r) {
+        float ms = 0.f;
+        cudaEventRecord(e0, st);
+        stream_read3_kernel<<<nb, kRedThreads, 0, st>>>((const float4*)a, (const float4*)b, (const float4*)c, o, nv);
+        cudaEventRecord(e1, st);
+        e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0 && ms < best_r) best_r = ms;  // the first run warms up
+        cudaEventRecord(e0, st);
+        stream_triad_kernel<<<nb, kRedThreads, 0, st>>>((const float4*)a, (const float4*)b, (float4*)o, nv);
+        cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0 && ms < best_t) best_t = ms;
+        count_launch(2);
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    *read_gbs = 3.0 * 16.0 * nv / (best_r * 1e-3) / 1e9;
+    *triad_gbs = 3.0 * 16.0 * nv / (best_t * 1e-3) / 1e9;
+    return e;
+}
+
 // ------------------------------------------------------ explicit instances ---
 
 #define PARIS_INSTANTIATE(T)                                                                  \

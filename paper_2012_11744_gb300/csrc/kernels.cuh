@@ -149,6 +149,12 @@ __device__ inline void finalize_last_block(const double* partials, int64_t nbloc
     if (tid == 0) f.s->ticket = 0u;
 }
 
+// Best-of-reps device rates of two streams over n-float vectors (n a
+// multiple of 4, 16-byte aligned): a, b, c read (read_gbs) and o = a + b/2
+// (triad_gbs, two read and one written), bytes moved over event time.
+cudaError_t stream_rates(const float* a, const float* b, const float* c, float* o, int64_t n, int reps,
+                         double* read_gbs, double* triad_gbs, cudaStream_t st);
+
 // Grid of the element-wise kernels (kEW elements per thread).
 int elementwise_blocks(int64_t n);
 // Most blocks any reducing kernel launches on a grid of this size (the

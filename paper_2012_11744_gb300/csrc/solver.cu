@@ -1217,6 +1217,20 @@ paris_status paris_check_arithmetic(const double* v, int64_t n, int shift, int64
     return PARIS_OK;
 }
 
+paris_status paris_stream_rates(const float* a, const float* b, const float* c, float* o, int64_t n, int reps,
+                                double* read_gbs, double* triad_gbs, void* stream) {
+    if (!a || !b || !c || !o || !read_gbs || !triad_gbs || n < 4 || n % 4 || reps < 1 || reps > 1000)
+        return PARIS_ERR_INVALID_ARG;
+    for (const void* p : {(const void*)a, (const void*)b, (const void*)c, (const void*)o})
+        if (reinterpret_cast<uintptr_t>(p) & 15) return PARIS_ERR_INVALID_ARG;
+    const cudaError_t e = stream_rates(a, b, c, o, n, reps, read_gbs, triad_gbs, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        paris_internal_note_cuda_error(e);
+        return PARIS_ERR_CUDA;
+    }
+    return PARIS_OK;
+}
+
 paris_status paris_max_divergence(paris_ctx* c, const double* u, const double* v,
                                   const double* w, double* max_abs_div) {
     if (!c || !u || !v || !w || !max_abs_div) return PARIS_ERR_INVALID_ARG;

@@ -322,3 +322,22 @@ def test_refinement_residual_matches_fp64_residual(paris, grid):
         print(f"reported {st['rel_res_l2']:.3e} {st['rel_res_linf']:.3e}  FP64 {l2:.3e} {linf:.3e}")
         assert abs(st["rel_res_l2"] - l2) <= 2e-12 and abs(st["rel_res_linf"] - linf) <= 2e-12
         assert l2 <= 1e-10 and linf <= 1e-10
+
+
+def test_stream_rates_probe(paris):
+    """The streaming probe returns positive rates below any plausible DRAM
+    figure for vectors larger than L2, leaves a, b, c untouched, writes
+    o = a + b/2, and rejects misaligned or mis-sized arguments."""
+    n = 40 * 1024 * 1024  # 160 MB per vector
+    g = torch.Generator(device="cuda").manual_seed(5)
+    a, b, c = (torch.rand(n, device="cuda", generator=g) for _ in range(3))
+    a0, b0, c0 = a.clone(), b.clone(), c.clone()
+    o = torch.empty(n, device="cuda")
+    rd, tr = paris.stream_rates(a, b, c, o, reps=3)
+    assert 100.0 < rd < 20000.0 and 100.0 < tr < 20000.0, (rd, tr)
+    assert torch.equal(a, a0) and torch.equal(b, b0) and torch.equal(c, c0)
+    assert torch.equal(o, torch.addcmul(a, b, torch.full_like(b, 0.5)))
+    with pytest.raises(paris.ParisError):
+        paris.stream_rates(a[1:], b[1:], c[1:], o[1:])  # 4-byte offset: not 16-byte aligned
+    with pytest.raises(paris.ParisError):
+        paris.stream_rates(a[:6], b[:6], c[:6], o[:6])  # not a multiple of 4
