@@ -42,8 +42,8 @@ NCU_TRAFFIC = {
     # finest-level colour pass: DRAM read + write bytes per launch from
     # "ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
     #  -k regex:rbgs_rho|op_rho|... -c 24" of "bench.py --single mixed": zero-initial passes
-    # 133.2 MB, regular passes 184.9 MB; 11 and 77 of them per solve
-    "smooth0": {"bytes_per_launch": 178.4e6, "source": "rho0.cu", "sha": "40fd7f17f0558ae1"},
+    # 134.3 MB, regular passes 186.8 MB; 11 and 77 of them per solve
+    "smooth0": {"bytes_per_launch": 180.2e6, "source": "rho0.cu", "sha": "41dc04c6d5902ba1"},
 }
 
 
