@@ -258,7 +258,8 @@ typedef struct paris_batch paris_batch;
 /* n grids (host array), options (precision is always mixed; smoother must be
  * PARIS_SMOOTH_RBGS or PARIS_SMOOTH_RBGS_2PASS, both run as red-black colour
  * passes here), stream.  Allocates all workspace.  INVALID_ARG also when n
- * exceeds the number of CTAs the GPU can keep resident. */
+ * exceeds the number of CTAs the GPU can keep resident, or when an instance
+ * has (nx+1)(ny+1)(nz+1) >= 2^31 (its arrays are indexed in 32 bits). */
 paris_status paris_batch_create(paris_batch** b, int n, const paris_grid* grids,
                                 const paris_opts* o, void* stream);
 paris_status paris_batch_destroy(paris_batch* b);

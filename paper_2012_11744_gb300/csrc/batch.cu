@@ -157,11 +157,14 @@ __device__ bool greduce(Grp& c, double (&v)[NV], const int (&op)[NV]) {
     for (int64_t c_ = (int64_t)cx.rank * kBT + threadIdx.x; c_ < (int64_t)(n_); \
          c_ += (int64_t)cx.ncta * kBT)
 
+// cell index -> (i, j, k) in 32-bit arithmetic (an instance has fewer than
+// 2^31 cells and faces, checked at creation)
 __device__ inline void decomp(const Geo& g, int64_t c, int& i, int& j, int& k) {
-    i = (int)(c % g.nx);
-    const int64_t t = c / g.nx;
-    j = (int)(t % g.ny);
-    k = (int)(t / g.ny);
+    const unsigned cu = (unsigned)c, nx = (unsigned)g.nx, ny = (unsigned)g.ny;
+    const unsigned t = cu / nx;
+    i = (int)(cu - t * nx);
+    k = (int)(t / ny);
+    j = (int)(t - (unsigned)k * ny);
 }
 
 // ------------------------------------------------------------ set-up ---
@@ -213,14 +216,16 @@ __device__ bool setup_rhs(Grp& cx, double& bnorm2, double& binf, double& nonfin)
     if (!greduce<1>(cx, acc, op1)) return false;
     const double mean = acc[0] / (double)g.ncell();
     double n3[3] = {0.0, 0.0, 0.0};
+    unsigned nf = 0;
     GLOOP(c, g.ncell()) {
         const double t = -(I.f64[c] - mean);
         I.f64[c] = t;
         I.p[c] = 0.0;
         n3[0] = fma(t, t, n3[0]);
         n3[1] = fmax(n3[1], fabs(t));
-        n3[2] += isfinite(t) ? 0.0 : 1.0;
+        nf += isfinite(t) ? 0u : 1u;
     }
+    n3[2] = (double)nf;
     const int op3[3] = {0, 1, 0};
     if (!greduce<3>(cx, n3, op3)) return false;
     bnorm2 = n3[0];
@@ -311,13 +316,21 @@ __device__ void rb_pass(Grp& cx, const BLevel& L, const float* f, float* x, int 
                         bool zero) {
     const Geo& g = L.g;
     Coef<float> cf{L.b[0], L.b[1], L.b[2], 1.0f};
-    GLOOP(c, g.ncell()) {
-        int i, j, k;
-        decomp(g, c, i, j, k);
-        if (((i + j + k) & 1) != color) {
-            if (zero) x[c] = 0.f;
-            continue;
+    // one iteration per x-pair (2t, 2t+1) of a row: the member of this colour
+    // is updated (the other one zeroed on a zero pass)
+    const unsigned npair = (unsigned)(g.nx + 1) / 2, ny = (unsigned)g.ny;
+    GLOOP(pp, (int64_t)npair * g.ny * g.nz) {
+        const unsigned pu = (unsigned)pp, row = pu / npair;
+        const int tp = (int)(pu - row * npair);
+        const int k = (int)(row / ny), j = (int)(row - (unsigned)k * ny);
+        const int i0 = 2 * tp;
+        const int i = i0 + ((i0 + j + k + color) & 1);
+        if (zero) {
+            const int io = 2 * i0 + 1 - i;
+            if (io < g.nx) x[g.cidx(io, j, k)] = 0.f;
         }
+        if (i >= g.nx) continue;
+        const int64_t c = g.cidx(i, j, k);
         Stencil<float> s;
         load_stencil(g, cf, i, j, k, s);
         const float d = ((s.b[0] + s.b[1]) + (s.b[2] + s.b[3])) + (s.b[4] + s.b[5]);
@@ -453,6 +466,7 @@ __device__ bool solve(Grp& cx, const BParams& P, double bnorm2, double binf, int
         // FP64 true residual, scaled FP32 copy for the inner solve
         const double scale = 1.0 / (rinf_prev > 1e-300 ? rinf_prev : 1.0);
         double n3[3] = {0.0, 0.0, 0.0};
+        unsigned nonfin = 0;
         GLOOP(c, N) {
             int i, j, k;
             decomp(g, c, i, j, k);
@@ -462,8 +476,9 @@ __device__ bool solve(Grp& cx, const BParams& P, double bnorm2, double binf, int
             I.r[c] = (float)(r * scale);
             n3[0] = fma(r, r, n3[0]);
             n3[1] = fmax(n3[1], fabs(r));
-            n3[2] += isfinite(r) ? 0.0 : 1.0;
+            nonfin += isfinite(r) ? 0u : 1u;
         }
+        n3[2] = (double)nonfin;
         const int op3[3] = {0, 1, 0};
         if (!greduce<3>(cx, n3, op3)) return false;
         rr = n3[0];
@@ -487,16 +502,19 @@ __device__ bool solve(Grp& cx, const BParams& P, double bnorm2, double binf, int
         // inner flexible CG on A e = r (FP32 vectors, FP64 group sums)
         GLOOP(c, N) I.e[c] = 0.f;
         if (!vcycle(cx, P, I.r, I.z)) return false;
-        double d2[2] = {0.0, 0.0};
+        // per-thread sums in FP32 (the element-wise products' precision),
+        // across threads and CTAs in FP64
+        float a0 = 0.f;
         GLOOP(c, N) {
-            d2[0] += (double)(I.r[c] * I.z[c]);
+            a0 = fmaf(I.r[c], I.z[c], a0);
             I.d[c] = I.z[c];
         }
+        double d2[2] = {(double)a0, 0.0};
         const int op2[2] = {0, 0};
         if (!greduce<2>(cx, d2, op2)) return false;
         double rho = d2[0];
         for (int jj = 0; jj < 50 && iters < P.max_iter; ++jj) {
-            double dq[1] = {0.0};
+            float aq = 0.f;
             GLOOP(c, N) {
                 int i, j, k;
                 decomp(g, c, i, j, k);
@@ -504,29 +522,33 @@ __device__ bool solve(Grp& cx, const BParams& P, double bnorm2, double binf, int
                 load_stencil(g, c32, i, j, k, s);
                 const float qc = apply_A(s, I.d, I.d[c], 1.0f);
                 I.q[c] = qc;
-                dq[0] += (double)(I.d[c] * qc);
+                aq = fmaf(I.d[c], qc, aq);
             }
+            double dq[1] = {(double)aq};
             const int op1[1] = {0};
             if (!greduce<1>(cx, dq, op1)) return false;
             const double alpha = dq[0] > 0.0 ? rho / dq[0] : 0.0;
             const float af = (float)alpha;
-            double rn[2] = {0.0, 0.0};
+            float ar = 0.f;
+            unsigned nonfin = 0;
             GLOOP(c, N) {
                 I.e[c] = fmaf(af, I.d[c], I.e[c]);
                 const float rc = fmaf(-af, I.q[c], I.r[c]);
                 I.r[c] = rc;
-                rn[0] += (double)(rc * rc);
-                rn[1] += isfinite(rc) ? 0.0 : 1.0;
+                ar = fmaf(rc, rc, ar);
+                nonfin += isfinite(rc) ? 0u : 1u;
             }
+            double rn[2] = {(double)ar, (double)nonfin};
             if (!greduce<2>(cx, rn, op2)) return false;
             ++iters;
             if (rn[1] > 0 || rn[0] <= target || rn[0] > 1e6 * rr32) break;
             if (!vcycle(cx, P, I.r, I.z)) return false;
-            double zz[2] = {0.0, 0.0};
+            float z0 = 0.f, z1 = 0.f;
             GLOOP(c, N) {
-                zz[0] += (double)(I.z[c] * I.r[c]);
-                zz[1] += (double)(I.z[c] * I.q[c]);
+                z0 = fmaf(I.z[c], I.r[c], z0);
+                z1 = fmaf(I.z[c], I.q[c], z1);
             }
+            double zz[2] = {(double)z0, (double)z1};
             if (!greduce<2>(cx, zz, op2)) return false;
             const double beta = rho != 0.0 ? -alpha * zz[1] / rho : 0.0;
             rho = zz[0];
@@ -786,6 +808,8 @@ paris_status paris_batch_create(paris_batch** out, int n, const paris_grid* grid
         if (g.nx < 2 || g.ny < 2 || g.nz < 2 || !(g.h > 0)) return PARIS_ERR_INVALID_ARG;
         for (int a = 0; a < 3; ++a)
             if (g.bc[a] != PARIS_PERIODIC && g.bc[a] != PARIS_WALL) return PARIS_ERR_INVALID_ARG;
+        // every array of an instance is indexed in 32 bits on the device
+        if ((int64_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1) >= ((int64_t)1 << 31)) return PARIS_ERR_INVALID_ARG;
     }
     paris_batch* b = new (std::nothrow) paris_batch();
     if (!b) return PARIS_ERR_NO_MEMORY;

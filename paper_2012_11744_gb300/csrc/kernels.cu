@@ -977,13 +977,13 @@ __global__ void update_xr_kernel(int64_t n, const Scal* s, const T* __restrict__
     constexpr int W = V16<T>::n;
     const T alpha = (T)s->alpha;
     T l2 = T(0), li = T(0);
-    double nf = 0.0;
+    unsigned nf = 0;  // an integer count: no FP64 add per element
     auto one = [&](T dv, T qv, T& xv, T& rv) {
         xv = fma(alpha, dv, xv);
         rv = fma(-alpha, qv, rv);
         l2 = fma(rv, rv, l2);
         li = fmax(li, fabs(rv));
-        nf += isfinite(rv) ? 0.0 : 1.0;
+        nf += isfinite(rv) ? 0u : 1u;
     };
     const int64_t nv = vec ? n / W : 0;
     PARIS_VEC_FOR(i, nv) {
@@ -1006,7 +1006,7 @@ __global__ void update_xr_kernel(int64_t n, const Scal* s, const T* __restrict__
         x[c] = xv;
         r[c] = rv;
     }
-    double acc[3] = {(double)l2, (double)li, nf};
+    double acc[3] = {(double)l2, (double)li, (double)nf};
     const int op[3] = {0, 1, 0};
     block_reduce_store<3>(acc, op, partials, blockIdx.x, threadIdx.x);
     finalize_last_block(partials, gridDim.x, fin, threadIdx.x);
