@@ -381,6 +381,16 @@ def run_paris(args, rank, world, local):
                          f"system ({s['sample_s']:.1f} s), extrapolated to the {s['cg_iters_full']} "
                          f"iterations of the full oracle solve"}
     its = [s["iters"] for s in st_mixed]
+
+    def solve_roofline(k, v_cycle, outer, ms):
+        # compulsory bytes of a solve: N (187 + k (V + outer)); 187 B/cell fixed
+        # (face coefficients 44, coarse coefficients ~15, divergence 32, mean 16,
+        # correction 80), V the bytes per cell of one V-cycle, outer those of one
+        # Krylov iteration outside it, k the iterations
+        b = N * (187.0 + k * (v_cycle + outer))
+        t = b / (hbm * 1e9) * 1e3
+        return {"model_bytes_per_solve": b, "iters": k, "roofline_ms": t, "measured_ms": ms,
+                "pct_hbm": t / ms}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_mixed / args.steps, "higher_is_better": True,
@@ -390,6 +400,11 @@ def run_paris(args, rank, world, local):
                  "iters": st_fp64[-1]["iters"], "rel_res_l2": st_fp64[-1]["rel_res_l2"],
                  "rel_res_linf": st_fp64[-1]["rel_res_linf"]},
         "mixed_over_fp64": value / fp64_value,
+        "solve_roofline": {
+            "model": "N (187 + k (V + outer)) bytes at the measured copy peak; V = 142.9 B/cell per FP32 "
+                     "V-cycle (285.7 FP64), outer = 132 B/cell per mixed FCG iteration (140 FP64)",
+            "mixed": solve_roofline(its[-1], 142.9, 132.0, ms_mixed / args.steps),
+            "fp64": solve_roofline(st_fp64[-1]["iters"], 285.7, 140.0, ms_fp64 / k64)},
         "solve": {"iters": its[-1], "outer_iters": st_mixed[-1]["outer_iters"],
                   "rel_res_l2": st_mixed[-1]["rel_res_l2"], "rel_res_linf": st_mixed[-1]["rel_res_linf"],
                   "levels": st_mixed[-1]["levels"], "fell_back": st_mixed[-1]["fell_back"]},
