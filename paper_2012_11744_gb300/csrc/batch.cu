@@ -272,7 +272,8 @@ __device__ bool setup_levels(Grp& cx) {
             const int i = c % L.g.nx, j = (c / L.g.nx) % L.g.ny, k = c / (L.g.nx * L.g.ny);
             Coef<float> cf{L.b[0], L.b[1], L.b[2], 1.0f};
             Stencil<float> s;
-            load_stencil(L.g, cf, i, j, k, s);
+            int c32_;
+            load_stencil_fast(L.g, cf.bx, cf.by, cf.bz, i, j, k, s, c32_);
             for (int q = 0; q < 6; ++q) {
                 M[(int64_t)c * n + c] += (double)s.b[q];
                 M[(int64_t)c * n + s.nb[q]] -= (double)s.b[q];
@@ -332,7 +333,8 @@ __device__ void rb_pass(Grp& cx, const BLevel& L, const float* f, float* x, int 
         if (i >= g.nx) continue;
         const int64_t c = g.cidx(i, j, k);
         Stencil<float> s;
-        load_stencil(g, cf, i, j, k, s);
+        int c32_;
+        load_stencil_fast(g, cf.bx, cf.by, cf.bz, i, j, k, s, c32_);
         const float d = ((s.b[0] + s.b[1]) + (s.b[2] + s.b[3])) + (s.b[4] + s.b[5]);
         const float wv = d > 0.f ? 1.f / d : 0.f;
         if (zero) {
@@ -376,7 +378,8 @@ __device__ bool vcycle(Grp& cx, const BParams& P, const float* f0, float* x0) {
                         const int i = I0 * Cl.fac[0] + di, j = J0 * Cl.fac[1] + dj, k = K0 * Cl.fac[2] + dk;
                         const int64_t c = L.g.cidx(i, j, k);
                         Stencil<float> s;
-                        load_stencil(L.g, cf, i, j, k, s);
+                        int c32_;
+                        load_stencil_fast(L.g, cf.bx, cf.by, cf.bz, i, j, k, s, c32_);
                         sum += f[c] - apply_A(s, x, x[c], 1.0f);
                     }
             Cl.f[cc] = sum / (float)(Cl.fac[0] * Cl.fac[1] * Cl.fac[2]);
@@ -430,7 +433,8 @@ __device__ bool vcycle(Grp& cx, const BParams& P, const float* f0, float* x0) {
         GLOOP(c, L.g.ncell()) {
             int i, j, k;
             decomp(L.g, c, i, j, k);
-            x[c] += Cl.x[Cl.g.cidx(i / Cl.fac[0], j / Cl.fac[1], k / Cl.fac[2])];
+            // coarsening factors are 1 or 2: halving is a shift
+            x[c] += Cl.x[Cl.g.cidx(i >> (Cl.fac[0] - 1), j >> (Cl.fac[1] - 1), k >> (Cl.fac[2] - 1))];
         }
         if (!gbar(cx)) return false;
         for (int s = 0; s < P.nu2; ++s) {
@@ -471,7 +475,8 @@ __device__ bool solve(Grp& cx, const BParams& P, double bnorm2, double binf, int
             int i, j, k;
             decomp(g, c, i, j, k);
             Stencil<double> s;
-            load_stencil(g, c64, i, j, k, s);
+            int c32_;
+            load_stencil_fast(g, c64.bx, c64.by, c64.bz, i, j, k, s, c32_);
             const double r = I.f64[c] - apply_A(s, I.p, I.p[c], c64.scale);
             I.r[c] = (float)(r * scale);
             n3[0] = fma(r, r, n3[0]);
@@ -519,7 +524,8 @@ __device__ bool solve(Grp& cx, const BParams& P, double bnorm2, double binf, int
                 int i, j, k;
                 decomp(g, c, i, j, k);
                 Stencil<float> s;
-                load_stencil(g, c32, i, j, k, s);
+                int c32_;
+                load_stencil_fast(g, c32.bx, c32.by, c32.bz, i, j, k, s, c32_);
                 const float qc = apply_A(s, I.d, I.d[c], 1.0f);
                 I.q[c] = qc;
                 aq = fmaf(I.d[c], qc, aq);

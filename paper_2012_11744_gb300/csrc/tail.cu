@@ -18,6 +18,18 @@ namespace {
 
 constexpr int kTailThreads = 1024;
 
+// One element from global to shared memory without a register round trip
+// (cp.async; completed by cp.async.wait_all).  Both addresses are aligned to
+// the element size.
+__device__ __forceinline__ void async_copy(float* dst, const float* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void async_copy(double* dst, const double* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+
 template <typename T>
 struct TailArgs {
     int n;                    // levels in the tail, the last one the dense coarsest
@@ -27,6 +39,30 @@ struct TailArgs {
     int nu1, nu2;
 };
 
+// t / d for the small counts of the tail levels (t < 2^14, d < 2^13): the
+// quotient of t times the FP32 reciprocal, truncated, is off by at most one
+// and corrected with one integer test each way (exhaustively checked over
+// those ranges, also with the reciprocal one ulp off).
+struct TailDiv {
+    unsigned d;
+    float inv;
+};
+__device__ __forceinline__ TailDiv tail_div(int d) { return TailDiv{(unsigned)d, 1.0f / (float)d}; }
+__device__ __forceinline__ unsigned operator/(unsigned t, TailDiv q) {
+    unsigned r = __float2uint_rz(__uint2float_rn(t) * q.inv);
+    if (r * q.d > t) --r;
+    else if ((r + 1) * q.d <= t) ++r;
+    return r;
+}
+// (i, j, k) of index t on an n0 x n1 x n2 box, x fastest
+__device__ __forceinline__ void tail_split(unsigned t, TailDiv n0, TailDiv n1, int& i, int& j, int& k) {
+    const unsigned row = t / n0;
+    i = (int)(t - row * n0.d);
+    const unsigned kk = row / n1;
+    j = (int)(row - kk * n1.d);
+    k = (int)kk;
+}
+
 // One colour pass of over-relaxed red-black Gauss-Seidel on a tail level (the
 // update of rbgs_kernel; zero: x taken as 0, the other colour zeroed).
 template <typename T, bool USEW>
@@ -35,8 +71,10 @@ __device__ void tail_pass(const TailLevel<T>& L, int color, bool zero, T omega) 
     const T hs = T(1) / L.scale;
     const int npair = (g.nx + 1) / 2;
     const int total = npair * g.ny * g.nz;
+    const TailDiv dp = tail_div(npair), dy = tail_div(g.ny);
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int tp = t % npair, j = (t / npair) % g.ny, k = t / (npair * g.ny);
+        int tp, j, k;
+        tail_split((unsigned)t, dp, dy, tp, j, k);
         const int i0 = 2 * tp;
         const int i = i0 + ((i0 + j + k + color) & 1);
         const int io = i0 + 1 - (i - i0);
@@ -79,8 +117,10 @@ __device__ void tail_restrict(const TailLevel<T>& F, const TailLevel<T>& C) {
     const Geo& cg = C.g;
     const int fa0 = C.fac[0], fa1 = C.fac[1], fa2 = C.fac[2];
     const int total = cg.nx * cg.ny * cg.nz;
+    const TailDiv dx = tail_div(cg.nx), dy = tail_div(cg.ny);
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int I = t % cg.nx, J = (t / cg.nx) % cg.ny, K = t / (cg.nx * cg.ny);
+        int I, J, K;
+        tail_split((unsigned)t, dx, dy, I, J, K);
         T sum = T(0);
         for (int dk = 0; dk < fa2; ++dk)
             for (int dj = 0; dj < fa1; ++dj)
@@ -101,8 +141,10 @@ __device__ void tail_prolong(const TailLevel<T>& C, const TailLevel<T>& F) {
     const Geo& fg = F.g;
     const Geo& cg = C.g;
     const int total = fg.nx * fg.ny * fg.nz;
+    const TailDiv dx = tail_div(fg.nx), dy = tail_div(fg.ny);
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int i = t % fg.nx, j = (t / fg.nx) % fg.ny, k = t / (fg.nx * fg.ny);
+        int i, j, k;
+        tail_split((unsigned)t, dx, dy, i, j, k);
         F.x[t] += C.x[cg.cidx(i >> (C.fac[0] - 1), j >> (C.fac[1] - 1), k >> (C.fac[2] - 1))];
     }
 }
@@ -165,8 +207,11 @@ __global__ void __launch_bounds__(kTailThreads) tail_vcycle_kernel(const __grid_
     }
     __syncthreads();
     if (SMEM) {
+        // every thread issues its share of the copies as asynchronous global ->
+        // shared copies and waits once, so the staging costs about one memory
+        // latency instead of one per element a thread moves
         auto copy = [&](const T* src, const T* dst, int64_t cnt) {
-            for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) const_cast<T*>(dst)[e] = src[e];
+            for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) async_copy(const_cast<T*>(dst) + e, src + e);
         };
         for (int l = 0; l < n; ++l) {
             const TailLevel<T>& G = a.L[l];
@@ -178,7 +223,8 @@ __global__ void __launch_bounds__(kTailThreads) tail_vcycle_kernel(const __grid_
         }
         copy(a.L[0].f, Ls[0].f, a.L[0].g.ncell());  // the other levels' f are restricted here
         const int64_t nc = a.L[n - 1].g.ncell();
-        for (int64_t e = threadIdx.x; e < nc * nc; e += blockDim.x) const_cast<double*>(Msh)[e] = a.Minv[e];
+        for (int64_t e = threadIdx.x; e < nc * nc; e += blockDim.x) async_copy(const_cast<double*>(Msh) + e, a.Minv + e);
+        asm volatile("cp.async.wait_all;" ::: "memory");
         __syncthreads();
     }
     for (int l = 0; l < n - 1; ++l) {
