@@ -511,7 +511,6 @@ void vup(paris_ctx* c, const Coef<T>& c0, const T* f0, T* x0, int l) {
 // Levels with at most this many cells, down to the dense coarsest level,
 // run as one single-block launch (launch_tail_vcycle).
 constexpr int64_t kTailCells = 4096;
-static_assert(kTailCells < (1 << 13), "the tail kernel splits indices below 2^13 with FP32 reciprocals");
 
 // First level of that tail, or -1 (the tail needs the two-pass red-black
 // smoother, a dense coarsest level and at least one level above it).

@@ -39,27 +39,12 @@ struct TailArgs {
     int nu1, nu2;
 };
 
-// t / d for the small counts of the tail levels (t < 2^14, d < 2^13): the
-// quotient of t times the FP32 reciprocal, truncated, is off by at most one
-// and corrected with one integer test each way (exhaustively checked over
-// those ranges, also with the reciprocal one ulp off).
-struct TailDiv {
-    unsigned d;
-    float inv;
-};
-__device__ __forceinline__ TailDiv tail_div(int d) { return TailDiv{(unsigned)d, 1.0f / (float)d}; }
-__device__ __forceinline__ unsigned operator/(unsigned t, TailDiv q) {
-    unsigned r = __float2uint_rz(__uint2float_rn(t) * q.inv);
-    if (r * q.d > t) --r;
-    else if ((r + 1) * q.d <= t) ++r;
-    return r;
-}
 // (i, j, k) of index t on an n0 x n1 x n2 box, x fastest
-__device__ __forceinline__ void tail_split(unsigned t, TailDiv n0, TailDiv n1, int& i, int& j, int& k) {
+__device__ __forceinline__ void tail_split(unsigned t, unsigned n0, unsigned n1, int& i, int& j, int& k) {
     const unsigned row = t / n0;
-    i = (int)(t - row * n0.d);
+    i = (int)(t - row * n0);
     const unsigned kk = row / n1;
-    j = (int)(row - kk * n1.d);
+    j = (int)(row - kk * n1);
     k = (int)kk;
 }
 
@@ -71,10 +56,9 @@ __device__ void tail_pass(const TailLevel<T>& L, int color, bool zero, T omega) 
     const T hs = T(1) / L.scale;
     const int npair = (g.nx + 1) / 2;
     const int total = npair * g.ny * g.nz;
-    const TailDiv dp = tail_div(npair), dy = tail_div(g.ny);
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
         int tp, j, k;
-        tail_split((unsigned)t, dp, dy, tp, j, k);
+        tail_split((unsigned)t, (unsigned)npair, (unsigned)g.ny, tp, j, k);
         const int i0 = 2 * tp;
         const int i = i0 + ((i0 + j + k + color) & 1);
         const int io = i0 + 1 - (i - i0);
@@ -117,10 +101,9 @@ __device__ void tail_restrict(const TailLevel<T>& F, const TailLevel<T>& C) {
     const Geo& cg = C.g;
     const int fa0 = C.fac[0], fa1 = C.fac[1], fa2 = C.fac[2];
     const int total = cg.nx * cg.ny * cg.nz;
-    const TailDiv dx = tail_div(cg.nx), dy = tail_div(cg.ny);
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
         int I, J, K;
-        tail_split((unsigned)t, dx, dy, I, J, K);
+        tail_split((unsigned)t, (unsigned)cg.nx, (unsigned)cg.ny, I, J, K);
         T sum = T(0);
         for (int dk = 0; dk < fa2; ++dk)
             for (int dj = 0; dj < fa1; ++dj)
@@ -141,10 +124,9 @@ __device__ void tail_prolong(const TailLevel<T>& C, const TailLevel<T>& F) {
     const Geo& fg = F.g;
     const Geo& cg = C.g;
     const int total = fg.nx * fg.ny * fg.nz;
-    const TailDiv dx = tail_div(fg.nx), dy = tail_div(fg.ny);
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
         int i, j, k;
-        tail_split((unsigned)t, dx, dy, i, j, k);
+        tail_split((unsigned)t, (unsigned)fg.nx, (unsigned)fg.ny, i, j, k);
         F.x[t] += C.x[cg.cidx(i >> (C.fac[0] - 1), j >> (C.fac[1] - 1), k >> (C.fac[2] - 1))];
     }
 }
