@@ -209,7 +209,11 @@ paris_status paris_projection_step(paris_ctx* ctx, const double* C, double rho1,
  * and p_host (in: initial guess, out: p) are copied to and from device
  * buffers the context owns (allocated on the first call of this function,
  * which should therefore not be the one being timed).  Pinned host memory
- * gives the fastest copies.  Synchronises the stream before returning. */
+ * gives the fastest copies.  The copies run on a second stream of the
+ * context, in the order the step needs the data, so that they overlap the
+ * face coefficients, the divergence and the velocity correction; the call
+ * synchronises both streams before returning (also on an error, so no copy
+ * into or out of the caller's buffers is left running). */
 paris_status paris_projection_step_host(paris_ctx* ctx, const double* C_host, double rho1,
                                         double rho2, double dt, double* u_host, double* v_host,
                                         double* w_host, double* p_host, paris_stats* st);

@@ -110,6 +110,9 @@ struct paris_ctx {
     double* rhs = nullptr;
     // host-call staging (allocated on first use)
     double *hC = nullptr, *hu = nullptr, *hv = nullptr, *hw = nullptr, *hp = nullptr;
+    // host-buffer step: a copy stream and its ordering events (created on first use)
+    cudaStream_t copy_st = nullptr;
+    cudaEvent_t copy_ev[5] = {};
     double last_mean_b = 0.0;
     Profiler prof;
     // CUDA graphs of the coarse part of the V-cycle (index 0: FP32, 1: FP64)
@@ -902,6 +905,12 @@ paris_status paris_destroy(paris_ctx* c) {
     cudaStreamSynchronize(c->st);
     drop_graphs(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->copy_st) {
+        cudaStreamSynchronize(c->copy_st);
+        cudaStreamDestroy(c->copy_st);
+    }
+    for (auto& e : c->copy_ev)
+        if (e) cudaEventDestroy(e);
     c->mem.release();
     if (c->scal_h) cudaFreeHost(c->scal_h);
     for (auto& e : c->prof.ev) cudaEventDestroy(e);
@@ -1082,6 +1091,54 @@ paris_status paris_project(paris_ctx* c, const double* bx, const double* by, con
     return PARIS_OK;
 }
 
+// Ordering against a copy stream for the host-buffer step: the compute
+// stream waits for C before the face coefficients, for u*, v*, w* before the
+// divergence and for p before the solve; p goes back to the host while the
+// correction runs.
+struct HostLink {
+    cudaStream_t cs;
+    cudaEvent_t c_ready, uvw_ready, p_ready, p_final;
+    double* p_host;
+};
+
+paris_status projection_step_impl(paris_ctx* c, const double* C, double rho1, double rho2, double dt,
+                                  double* u, double* v, double* w, double* p, paris_stats* st,
+                                  const HostLink* hl) {
+    const bool use_rho0 = rho0_usable(c);
+    {
+        ProfScope ps(c, PARIS_K_FIELD, 0.0);
+        if (hl) CK(cudaStreamWaitEvent(c->st, hl->c_ready, 0));
+        launch_face_coeffs(c->g0, C, rho1, rho2, c->beta[0], c->beta[1], c->beta[2],
+                           use_rho0 ? c->rh32 : nullptr, use_rho0 ? c->rh2 : nullptr, c->st);
+        CK(cudaGetLastError());
+        // rhs = div u*/dt and its mean; the solve's prologue forms the mean-free
+        // f = -(rhs - mean) directly (no separate mean removal pass)
+        CK(cudaMemsetAsync(c->scal, 0, sizeof(Scal), c->st));
+        if (hl) CK(cudaStreamWaitEvent(c->st, hl->uvw_ready, 0));
+        const int64_t nb =
+            launch_divergence(c->g0, u, v, w, 1.0 / (c->grid.h * dt), c->rhs, c->partials, c->st);
+        finalize(c->partials, nb, 3, 2, c->scal, FIN_MEAN_B, (double)c->N, c->st);
+        CK(cudaGetLastError());
+    }
+    if (hl) CK(cudaStreamWaitEvent(c->st, hl->p_ready, 0));
+    paris_status s;
+    paris_status solve =
+        poisson_solve(c, c->beta[0], c->beta[1], c->beta[2], c->rhs, p, st, use_rho0, true);
+    if (solve != PARIS_OK && solve != PARIS_ERR_NOT_CONVERGED) return solve;
+    if (hl) {
+        // the correction only reads p: copy it out meanwhile
+        CK(cudaEventRecord(hl->p_final, c->st));
+        CK(cudaStreamWaitEvent(hl->cs, hl->p_final, 0));
+        CK(cudaMemcpyAsync(hl->p_host, p, sizeof(double) * c->N, cudaMemcpyDeviceToHost, hl->cs));
+    }
+    {
+        ProfScope ps(c, PARIS_K_PROJECT, 0.0);
+        s = paris_project(c, c->beta[0], c->beta[1], c->beta[2], p, dt, u, v, w);
+    }
+    if (s != PARIS_OK) return s;
+    return solve;
+}
+
 paris_status paris_projection_step(paris_ctx* c, const double* C, double rho1, double rho2,
                                    double dt, double* u, double* v, double* w, double* p,
                                    paris_stats* st) {
@@ -1089,30 +1146,7 @@ paris_status paris_projection_step(paris_ctx* c, const double* C, double rho1, d
     if (!(rho1 > 0.0) || !(rho2 > 0.0) || !std::isfinite(rho1) || !std::isfinite(rho2))
         return PARIS_ERR_INVALID_ARG;
     if (!(dt > 0.0) || !std::isfinite(dt)) return PARIS_ERR_INVALID_ARG;
-    const bool use_rho0 = rho0_usable(c);
-    {
-        ProfScope ps(c, PARIS_K_FIELD, 0.0);
-        launch_face_coeffs(c->g0, C, rho1, rho2, c->beta[0], c->beta[1], c->beta[2],
-                           use_rho0 ? c->rh32 : nullptr, use_rho0 ? c->rh2 : nullptr, c->st);
-        CK(cudaGetLastError());
-        // rhs = div u*/dt and its mean; the solve's prologue forms the mean-free
-        // f = -(rhs - mean) directly (no separate mean removal pass)
-        CK(cudaMemsetAsync(c->scal, 0, sizeof(Scal), c->st));
-        const int64_t nb =
-            launch_divergence(c->g0, u, v, w, 1.0 / (c->grid.h * dt), c->rhs, c->partials, c->st);
-        finalize(c->partials, nb, 3, 2, c->scal, FIN_MEAN_B, (double)c->N, c->st);
-        CK(cudaGetLastError());
-    }
-    paris_status s;
-    paris_status solve =
-        poisson_solve(c, c->beta[0], c->beta[1], c->beta[2], c->rhs, p, st, use_rho0, true);
-    if (solve != PARIS_OK && solve != PARIS_ERR_NOT_CONVERGED) return solve;
-    {
-        ProfScope ps(c, PARIS_K_PROJECT, 0.0);
-        s = paris_project(c, c->beta[0], c->beta[1], c->beta[2], p, dt, u, v, w);
-    }
-    if (s != PARIS_OK) return s;
-    return solve;
+    return projection_step_impl(c, C, rho1, rho2, dt, u, v, w, p, st, nullptr);
 }
 
 paris_status paris_projection_step_host(paris_ctx* c, const double* C_host, double rho1,
@@ -1129,17 +1163,41 @@ paris_status paris_projection_step_host(paris_ctx* c, const double* C_host, doub
         c->hp = c->mem.get<double>(N);
         if (c->mem.err != cudaSuccess) return PARIS_ERR_NO_MEMORY;
     }
-    CK(cudaMemcpyAsync(c->hC, C_host, sizeof(double) * N, cudaMemcpyHostToDevice, c->st));
-    CK(cudaMemcpyAsync(c->hu, u_host, sizeof(double) * nf[0], cudaMemcpyHostToDevice, c->st));
-    CK(cudaMemcpyAsync(c->hv, v_host, sizeof(double) * nf[1], cudaMemcpyHostToDevice, c->st));
-    CK(cudaMemcpyAsync(c->hw, w_host, sizeof(double) * nf[2], cudaMemcpyHostToDevice, c->st));
-    CK(cudaMemcpyAsync(c->hp, p_host, sizeof(double) * N, cudaMemcpyHostToDevice, c->st));
-    paris_status s = paris_projection_step(c, c->hC, rho1, rho2, dt, c->hu, c->hv, c->hw, c->hp, st);
-    if (s != PARIS_OK && s != PARIS_ERR_NOT_CONVERGED) return s;
-    CK(cudaMemcpyAsync(u_host, c->hu, sizeof(double) * nf[0], cudaMemcpyDeviceToHost, c->st));
-    CK(cudaMemcpyAsync(v_host, c->hv, sizeof(double) * nf[1], cudaMemcpyDeviceToHost, c->st));
-    CK(cudaMemcpyAsync(w_host, c->hw, sizeof(double) * nf[2], cudaMemcpyDeviceToHost, c->st));
-    CK(cudaMemcpyAsync(p_host, c->hp, sizeof(double) * N, cudaMemcpyDeviceToHost, c->st));
+    if (!(rho1 > 0.0) || !(rho2 > 0.0) || !std::isfinite(rho1) || !std::isfinite(rho2))
+        return PARIS_ERR_INVALID_ARG;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return PARIS_ERR_INVALID_ARG;
+    if (!c->copy_st) {
+        CK(cudaStreamCreateWithFlags(&c->copy_st, cudaStreamNonBlocking));
+        for (auto& e : c->copy_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    cudaStream_t cs = c->copy_st;
+    // the copies start after the work already queued on the context's stream
+    CK(cudaEventRecord(c->copy_ev[4], c->st));
+    CK(cudaStreamWaitEvent(cs, c->copy_ev[4], 0));
+    HostLink hl{cs, c->copy_ev[0], c->copy_ev[1], c->copy_ev[2], c->copy_ev[3], p_host};
+    // inputs in the order the step needs them, each group announced by an event
+    CK(cudaMemcpyAsync(c->hC, C_host, sizeof(double) * N, cudaMemcpyHostToDevice, cs));
+    CK(cudaEventRecord(hl.c_ready, cs));
+    CK(cudaMemcpyAsync(c->hu, u_host, sizeof(double) * nf[0], cudaMemcpyHostToDevice, cs));
+    CK(cudaMemcpyAsync(c->hv, v_host, sizeof(double) * nf[1], cudaMemcpyHostToDevice, cs));
+    CK(cudaMemcpyAsync(c->hw, w_host, sizeof(double) * nf[2], cudaMemcpyHostToDevice, cs));
+    CK(cudaEventRecord(hl.uvw_ready, cs));
+    CK(cudaMemcpyAsync(c->hp, p_host, sizeof(double) * N, cudaMemcpyHostToDevice, cs));
+    CK(cudaEventRecord(hl.p_ready, cs));
+    paris_status s = projection_step_impl(c, c->hC, rho1, rho2, dt, c->hu, c->hv, c->hw, c->hp, st, &hl);
+    if (s != PARIS_OK && s != PARIS_ERR_NOT_CONVERGED) {
+        // leave no copy into or out of the caller's buffers running
+        cudaStreamSynchronize(cs);
+        cudaStreamSynchronize(c->st);
+        return s;
+    }
+    // u, v, w go back once the correction is done (p is already on its way)
+    CK(cudaEventRecord(c->copy_ev[4], c->st));
+    CK(cudaStreamWaitEvent(cs, c->copy_ev[4], 0));
+    CK(cudaMemcpyAsync(u_host, c->hu, sizeof(double) * nf[0], cudaMemcpyDeviceToHost, cs));
+    CK(cudaMemcpyAsync(v_host, c->hv, sizeof(double) * nf[1], cudaMemcpyDeviceToHost, cs));
+    CK(cudaMemcpyAsync(w_host, c->hw, sizeof(double) * nf[2], cudaMemcpyDeviceToHost, cs));
+    CK(cudaStreamSynchronize(cs));
     CK(cudaStreamSynchronize(c->st));
     return s;
 }

@@ -341,3 +341,27 @@ def test_stream_rates_probe(paris):
         paris.stream_rates(a[1:], b[1:], c[1:], o[1:])  # 4-byte offset: not 16-byte aligned
     with pytest.raises(paris.ParisError):
         paris.stream_rates(a[:6], b[:6], c[:6], o[:6])  # not a multiple of 4
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffer_step_matches_device_step(paris, pinned):
+    """paris_projection_step_host (copies on a second stream, overlapped with
+    the step) returns exactly what paris_projection_step returns on device
+    arrays, for pinned and pageable host buffers, twice in a row (reused
+    staging buffers, fresh inputs each call)."""
+    grid = pi.Grid(48, 32, 40, 1 / 48, (P, P, W))
+    pr = pi.random_problem(grid, seed=31, rho1=1000.0)
+    with ctx_for(paris, grid, precision=paris.MIXED) as ctx:
+        u, v, w = dev(pr.u), dev(pr.v), dev(pr.w)
+        p = torch.zeros(grid.shape, dtype=torch.float64, device="cuda")
+        st_d = ctx.projection_step(dev(pr.C), pr.rho1, pr.rho2, pr.dt, u, v, w, p)
+        ref = [host(t) for t in (u, v, w, p)]
+        for _ in range(2):
+            hs = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).clone()
+                  for a in (pr.C, pr.u, pr.v, pr.w, np.zeros(grid.shape))]
+            if pinned:
+                hs = [t.pin_memory() for t in hs]
+            st_h = ctx.projection_step_host(*hs[:1], pr.rho1, pr.rho2, pr.dt, *hs[1:])
+            assert st_h["iters"] == st_d["iters"] and st_h["converged"] == 1
+            for got, want in zip(hs[1:], ref):
+                np.testing.assert_array_equal(got.numpy(), want)
