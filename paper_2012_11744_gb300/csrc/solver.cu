@@ -110,6 +110,7 @@ struct paris_ctx {
     double* rhs = nullptr;
     // host-call staging (allocated on first use)
     double *hC = nullptr, *hu = nullptr, *hv = nullptr, *hw = nullptr, *hp = nullptr;
+    bool mixed_ready = false;  // mixed_setup already ran for the current coefficients
     // host-buffer step: a copy stream and its ordering events (created on first use)
     cudaStream_t copy_st = nullptr;
     cudaEvent_t copy_ev[5] = {};
@@ -736,23 +737,36 @@ struct Level0Mode {
     }
 };
 
+// The set-up of the mixed solve: FP32 copies of the finest coefficients (or
+// nothing, with the finest level from rho/2) and the FP32 hierarchy.  It
+// depends on the coefficients only, so the projection step runs it before
+// the right-hand side and the initial guess are needed (mixed_ready).
+void mixed_setup(paris_ctx* c, const Coef<double>& c64, bool rho0) {
+    const double ih2 = 1.0 / (c->grid.h * c->grid.h);
+    const double* b64[3] = {c64.bx, c64.by, c64.bz};
+    c->rho0 = rho0;
+    c->half0 = !rho0 && c->opts.half_coefficients != 0;
+    Coef<float> c32{c->b32_0[0], c->b32_0[1], c->b32_0[2], 1.0f};
+    ProfScope ps(c, PARIS_K_SETUP, 0.0);
+    if (!rho0) {
+        launch_convert_beta<float>(c->g0, b64, ih2, c->b32_0, c->st);
+        if (c->half0) launch_convert_beta_half(c->g0, b64, c->b16_0, c->st);
+    }
+    setup_hierarchy<float>(c, c32);
+}
+
 paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, SolveOut& out,
                          int max_iter, bool rho0) {
     const int64_t N = c->N;
-    const double ih2 = 1.0 / (c->grid.h * c->grid.h);
-    const double* b64[3] = {c64.bx, c64.by, c64.bz};
     Level0Mode mode_guard{c};
-    c->rho0 = rho0;
     Coef<float> c32{c->b32_0[0], c->b32_0[1], c->b32_0[2], 1.0f};
-    {
-        ProfScope ps(c, PARIS_K_SETUP, 0.0);
-        if (!rho0) {
-            launch_convert_beta<float>(c->g0, b64, ih2, c->b32_0, c->st);
-            c->half0 = c->opts.half_coefficients != 0;
-            if (c->half0) launch_convert_beta_half(c->g0, b64, c->b16_0, c->st);
-        }
-        setup_hierarchy<float>(c, c32);
+    if (c->mixed_ready) {
+        c->rho0 = rho0;
+        c->half0 = !rho0 && c->opts.half_coefficients != 0;
+    } else {
+        mixed_setup(c, c64, rho0);
     }
+    c->mixed_ready = false;
     // With the finest level from rho/2 the refinement step updates r in
     // double-float (launch_refine_rho) after the first FP64 residual; the
     // level-0 FP32 vectors are then in the colour-split layout, which only
@@ -1105,12 +1119,28 @@ paris_status projection_step_impl(paris_ctx* c, const double* C, double rho1, do
                                   double* u, double* v, double* w, double* p, paris_stats* st,
                                   const HostLink* hl) {
     const bool use_rho0 = rho0_usable(c);
+    // the set-up run ahead below is used by this step's solve only
+    struct ReadyGuard {
+        paris_ctx* c;
+        ~ReadyGuard() { c->mixed_ready = false; }
+    } ready_guard{c};
     {
         ProfScope ps(c, PARIS_K_FIELD, 0.0);
         if (hl) CK(cudaStreamWaitEvent(c->st, hl->c_ready, 0));
         launch_face_coeffs(c->g0, C, rho1, rho2, c->beta[0], c->beta[1], c->beta[2],
                            use_rho0 ? c->rh32 : nullptr, use_rho0 ? c->rh2 : nullptr, c->st);
         CK(cudaGetLastError());
+    }
+    if (c->opts.precision == PARIS_MIXED) {
+        // the hierarchy needs the coefficients only: build it while the host
+        // copies of u*, v*, w* and p may still be running
+        const Coef<double> c64{c->beta[0], c->beta[1], c->beta[2], 1.0 / (c->grid.h * c->grid.h)};
+        mixed_setup(c, c64, use_rho0);
+        c->mixed_ready = true;
+        CK(cudaGetLastError());
+    }
+    {
+        ProfScope ps(c, PARIS_K_FIELD, 0.0);
         // rhs = div u*/dt and its mean; the solve's prologue forms the mean-free
         // f = -(rhs - mean) directly (no separate mean removal pass)
         CK(cudaMemsetAsync(c->scal, 0, sizeof(Scal), c->st));
