@@ -43,7 +43,7 @@ NCU_TRAFFIC = {
     # "ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
     #  -k regex:rbgs_rho|op_rho|... -c 24" of "bench.py --single mixed": zero-initial passes
     # 134.3 MB, regular passes 186.8 MB; 11 and 77 of them per solve
-    "smooth0": {"bytes_per_launch": 180.2e6, "source": "rho0.cu", "sha": "41dc04c6d5902ba1"},
+    "smooth0": {"bytes_per_launch": 180.2e6, "source": "rho0.cu", "sha": "cde4a82403ac57f9"},
 }
 
 
@@ -336,8 +336,9 @@ def run_paris(args, rank, world, local):
             bC = b.pack([q.C for q in probs], "C")
             bu0, bv0, bw0 = (b.pack([getattr(q, k) for q in probs], k) for k in ("u", "v", "w"))
             r1, r2, dts = [q.rho1 for q in probs], [q.rho2 for q in probs], [q.dt for q in probs]
-            cache = os.path.join(ROOT, "gpurun_out", "batch_autotune.jsonl") if os.path.isdir(
-                os.path.join(ROOT, "gpurun_out")) else None
+            # the tuning is measured afresh on every run (a cache in the temporary
+            # directory only spares repeated trials within one machine session)
+            cache = os.path.join(tempfile.gettempdir(), f"paris_batch_autotune_{os.getuid()}.jsonl")
             b.autotune(bC, r1, r2, dts, bu0, bv0, bw0, cache_path=cache)
             bu, bv, bw = bu0.clone(), bv0.clone(), bw0.clone()
             bp = torch.zeros_like(bC)

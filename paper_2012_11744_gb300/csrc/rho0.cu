@@ -302,11 +302,11 @@ __device__ __forceinline__ void pass_plane(const PairCtx& q, float* x, float h2,
 }
 
 // A ring of R slots over the planes (R even: the updated member alternates
-// with the plane).  Step U of a round computes plane k + U from slot U (this
-// plane) and slot U+1 (the plane above) after loading plane k + U + R - 1 into
-// slot U-1, whose plane (k + U - 1) is done; the round is unrolled, so every
-// slot keeps its registers, and the plane above arrives R - 2 steps after its
-// load was issued.  A colour pass only reads cells of the other colour and
+// with the plane).  Step U of a turn of the ring computes plane k + U from
+// slot U (this plane) and slot U+1 (the plane above) after loading plane
+// k + U + R - 1 into slot U-1, whose plane (k + U - 1) is done; the turn is
+// unrolled, so every slot keeps its registers, and the plane above arrives
+// R - 2 steps after its load was issued.  A colour pass only reads cells of the other colour and
 // the updated cell itself before its update, so loading ahead is safe.
 template <bool ZERO, int M0, int R, int U>
 struct PassRing {
