@@ -311,41 +311,82 @@ __device__ bool setup_levels(Grp& cx) {
 
 // ------------------------------------------------------------ V-cycle ---
 
+// The colour-c cell of pair pp of a level (i >= nx: none; io: the other
+// member of the pair, or nx when it does not exist).
+struct PassCell {
+    int i, j, k, io;
+};
+__device__ inline PassCell pass_cell(const Geo& g, unsigned pp, unsigned npair, int color) {
+    const unsigned ny = (unsigned)g.ny, row = pp / npair;
+    PassCell p;
+    const int tp = (int)(pp - row * npair);
+    p.k = (int)(row / ny);
+    p.j = (int)(row - (unsigned)p.k * ny);
+    const int i0 = 2 * tp;
+    p.i = i0 + ((i0 + p.j + p.k + color) & 1);
+    p.io = 2 * i0 + 1 - p.i;
+    return p;
+}
+
+// The loaded values of one pass cell: face coefficients, f, x and the
+// neighbours' x.
+struct PassLoad {
+    float b[6];
+    int c;
+    float f, x, nb[6];
+    bool on;
+};
+__device__ __forceinline__ void pass_load(PassLoad& d, const BLevel& L, const float* f, const float* x,
+                                          const PassCell& p, bool zero) {
+    d.on = p.i < L.g.nx;
+    if (!d.on) return;
+    Stencil<float> s;
+    load_stencil_fast(L.g, L.b[0], L.b[1], L.b[2], p.i, p.j, p.k, s, d.c);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) d.b[q] = s.b[q];
+    d.f = f[d.c];
+    if (!zero) {
+        d.x = x[d.c];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) d.nb[q] = x[(int)s.nb[q]];
+    }
+}
+__device__ __forceinline__ void pass_store(const PassLoad& d, const Geo& g, float* x, const PassCell& p,
+                                           float omega, bool zero) {
+    if (zero && p.io < g.nx) x[g.cidx(p.io, p.j, p.k)] = 0.f;
+    if (!d.on) return;
+    const float sum = ((d.b[0] + d.b[1]) + (d.b[2] + d.b[3])) + (d.b[4] + d.b[5]);
+    const float wv = sum > 0.f ? 1.f / sum : 0.f;
+    if (zero) {
+        x[d.c] = omega * wv * d.f;
+    } else {
+        float acc = d.f;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) acc = fmaf(d.b[q], d.nb[q], acc);
+        x[d.c] = fmaf(omega, fmaf(wv, acc, -d.x), d.x);
+    }
+}
+
 // One red-black colour pass in place on level L (zero: x taken as 0 and the
 // other colour zeroed).  x_c <- x_c + omega (w (f + sum beta x_nb) - x_c).
-__device__ void rb_pass(Grp& cx, const BLevel& L, const float* f, float* x, int color, float omega,
+// A thread takes two pairs per iteration and loads both stencils before it
+// updates either: cells of the updated colour are never neighbours of one
+// another, so the two updates are independent.
+__device__ __noinline__ void rb_pass(Grp& cx, const BLevel& L, const float* f, float* x, int color, float omega,
                         bool zero) {
     const Geo& g = L.g;
-    Coef<float> cf{L.b[0], L.b[1], L.b[2], 1.0f};
-    // one iteration per x-pair (2t, 2t+1) of a row: the member of this colour
-    // is updated (the other one zeroed on a zero pass)
-    const unsigned npair = (unsigned)(g.nx + 1) / 2, ny = (unsigned)g.ny;
-    GLOOP(pp, (int64_t)npair * g.ny * g.nz) {
-        const unsigned pu = (unsigned)pp, row = pu / npair;
-        const int tp = (int)(pu - row * npair);
-        const int k = (int)(row / ny), j = (int)(row - (unsigned)k * ny);
-        const int i0 = 2 * tp;
-        const int i = i0 + ((i0 + j + k + color) & 1);
-        if (zero) {
-            const int io = 2 * i0 + 1 - i;
-            if (io < g.nx) x[g.cidx(io, j, k)] = 0.f;
-        }
-        if (i >= g.nx) continue;
-        const int64_t c = g.cidx(i, j, k);
-        Stencil<float> s;
-        int c32_;
-        load_stencil_fast(g, cf.bx, cf.by, cf.bz, i, j, k, s, c32_);
-        const float d = ((s.b[0] + s.b[1]) + (s.b[2] + s.b[3])) + (s.b[4] + s.b[5]);
-        const float wv = d > 0.f ? 1.f / d : 0.f;
-        if (zero) {
-            x[c] = omega * wv * f[c];
-        } else {
-            float acc = f[c];
-#pragma unroll
-            for (int q = 0; q < 6; ++q) acc = fmaf(s.b[q], x[s.nb[q]], acc);
-            const float xc = x[c];
-            x[c] = fmaf(omega, fmaf(wv, acc, -xc), xc);
-        }
+    const unsigned npair = (unsigned)(g.nx + 1) / 2;
+    const int64_t total = (int64_t)npair * g.ny * g.nz;
+    const int64_t stride = (int64_t)cx.ncta * kBT;
+    for (int64_t p0 = (int64_t)cx.rank * kBT + threadIdx.x; p0 < total; p0 += 2 * stride) {
+        const int64_t p1 = p0 + stride;
+        const PassCell a = pass_cell(g, (unsigned)p0, npair, color);
+        const PassCell b = p1 < total ? pass_cell(g, (unsigned)p1, npair, color) : PassCell{g.nx, 0, 0, g.nx};
+        PassLoad da, db;
+        pass_load(da, L, f, x, a, zero);
+        pass_load(db, L, f, x, b, zero);
+        pass_store(da, g, x, a, omega, zero);
+        pass_store(db, g, x, b, omega, zero);
     }
 }
 
