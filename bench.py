@@ -457,7 +457,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="paris", choices=["paris", "reference"])
-    ap.add_argument("--n", type=int, default=256, help="grid edge of the drop-field workload")
+    ap.add_argument("--edge", dest="n", type=int, default=256, help="grid edge of the drop-field workload")
     ap.add_argument("--ref-budget", type=float, default=2.0,
                     help="seconds of oracle CG iterations per --impl reference step")
     ap.add_argument("--cpu-budget", type=float, default=6.0,
