@@ -109,6 +109,12 @@ typedef struct {
                              the smoother is PARIS_SMOOTH_RBGS_2PASS and half_coefficients is
                              0; otherwise ignored.  The FP64 residual, the converged p and
                              the projection keep the FP64 beta (1) */
+    int level0_tiles;     /* with level0_density: the finest level's colour passes, inner CG
+                             product and residual restriction run on plane tiles, two pairs
+                             of cells per thread, when nx/2 is even (1), or always on the
+                             kernels that walk z-columns one pair per thread (0).  The colour
+                             passes give identical results; the product's dot products differ
+                             in summation order only (1) */
 } paris_opts;
 
 typedef struct {

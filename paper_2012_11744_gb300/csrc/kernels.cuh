@@ -255,15 +255,16 @@ void launch_prolong_add(const Geo& fine, const Geo& coarse, const int fac[3], co
 // holds its cells of colour (i+j+k) even in order of i, then the odd ones.
 // even nx, ny, nz and 32-bit offsets
 bool rho0_fits(const Geo& g);
+// tiles: plane-tile kernels where nx/2 is even (else the z-column kernels)
 void launch_rbgs_rho(const Geo& g, const float* rh, double h, const float* f, float* x, int color,
-                     double omega, bool zero_init, cudaStream_t st, int k0 = 0, int k1 = -1);
+                     double omega, bool zero_init, cudaStream_t st, int k0 = 0, int k1 = -1, bool tiles = true);
 // q = A d; partials (d . q); returns the number of blocks
 int64_t launch_matvec_rho(const Geo& g, const float* rh, double h, const float* d, float* q,
-                          double* partials, cudaStream_t st, FinSpec fin = no_fin());
+                          double* partials, cudaStream_t st, FinSpec fin = no_fin(), bool tiles = true);
 int64_t rho0_matvec_blocks(const Geo& g);
 // coarse f = mean over the 2x2x2 children of (f - A x); coarse = every axis halved
 void launch_restrict_rho(const Geo& g, const float* rh, double h, const float* f, const float* x,
-                         const Geo& coarse, float* fc, cudaStream_t st);
+                         const Geo& coarse, float* fc, cudaStream_t st, bool tiles = true);
 // x += P xc (piecewise constant) onto the split level 0 from the level with every axis halved
 void launch_prolong_split(const Geo& fine, const Geo& coarse, const float* xc, float* x, cudaStream_t st);
 // scaled FP32 coefficients of the level with every axis halved

@@ -566,11 +566,11 @@ __global__ void __launch_bounds__(kBX* kVY) rbgs_rho_tile_kernel(Geo g, const fl
 }
 
 void launch_rbgs_rho(const Geo& g, const float* rh, double h, const float* f, float* x, int color,
-                     double omega, bool zero_init, cudaStream_t st, int k0, int k1) {
+                     double omega, bool zero_init, cudaStream_t st, int k0, int k1, bool tiles) {
     if (k1 < 0) k1 = g.nz;
     const float h2 = (float)(h * h);
     const int hx = g.nx / 2;
-    if (kTileV > 0 && hx % kTileV == 0) {
+    if (tiles && kTileV > 0 && hx % kTileV == 0) {
         constexpr int V = kTileV > 0 ? kTileV : 2;
         dim3 gr((hx / V + kBX - 1) / kBX, (g.ny + kVY - 1) / kVY, k1 - k0);
         if (zero_init)
@@ -952,9 +952,9 @@ int64_t rho0_matvec_blocks(const Geo& g) {
 }
 
 int64_t launch_matvec_rho(const Geo& g, const float* rh, double h, const float* d, float* q,
-                          double* partials, cudaStream_t st, FinSpec fin) {
+                          double* partials, cudaStream_t st, FinSpec fin, bool tiles) {
     const int hx = g.nx / 2;
-    if (kTileOpV > 0 && hx % kTileOpV == 0) {
+    if (tiles && kTileOpV > 0 && hx % kTileOpV == 0) {
         constexpr int V = kTileOpV > 0 ? kTileOpV : 2;
         dim3 gr((hx / V + kBX - 1) / kBX, (g.ny + kVY - 1) / kVY, (g.nz + kTileOpPlanes - 1) / kTileOpPlanes);
         op_rho_tile_kernel<false, V><<<gr, dim3(kBX, kVY), 0, st>>>(g, rh, (float)(1.0 / (h * h)), d, nullptr, q,
@@ -971,9 +971,9 @@ int64_t launch_matvec_rho(const Geo& g, const float* rh, double h, const float* 
 }
 
 void launch_restrict_rho(const Geo& g, const float* rh, double h, const float* f, const float* x,
-                         const Geo& cg, float* fc, cudaStream_t st) {
+                         const Geo& cg, float* fc, cudaStream_t st, bool tiles) {
     const int hx = g.nx / 2;
-    if (kTileOpV > 0 && hx % kTileOpV == 0) {
+    if (tiles && kTileOpV > 0 && hx % kTileOpV == 0) {
         constexpr int V = kTileOpV > 0 ? kTileOpV : 2;
         dim3 gr((hx / V + kBX - 1) / kBX, (g.ny + kVY - 1) / kVY, g.nz / 2);
         op_rho_tile_kernel<true, V><<<gr, dim3(kBX, kVY), 0, st>>>(g, rh, (float)(1.0 / (h * h)), x, f, fc, cg,

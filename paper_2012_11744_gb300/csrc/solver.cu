@@ -154,6 +154,7 @@ bool valid_opts(const paris_opts* o) {
     if (!(o->inner_tol > 0.0 && o->inner_tol < 1.0)) return false;
     if (o->slab_planes < 0) return false;
     if (o->level0_density != 0 && o->level0_density != 1) return false;
+    if (o->level0_tiles != 0 && o->level0_tiles != 1) return false;
     return true;
 }
 
@@ -382,7 +383,7 @@ void smooth(paris_ctx* c, int l, const Coef<T>& cf, const T* f, T* x, int sweeps
                 if constexpr (sizeof(T) == 4) {
                     if (v0) {
                         launch_rbgs_rho(L.g, c->rh32, c->grid.h, (const float*)f, (float*)x, color, o.omega,
-                                        zero, c->st, a, b);
+                                        zero, c->st, a, b, o.level0_tiles != 0);
                         return;
                     }
                     if (h16) {
@@ -461,7 +462,7 @@ void vdown(paris_ctx* c, const Coef<T>& c0, const T* f0, T* x0, int l) {
     if constexpr (sizeof(T) == 4) {
         if (v0) {
             launch_restrict_rho(c->lv[l].g, c->rh32, c->grid.h, (const float*)f, (const float*)x, C.g,
-                                (float*)Prec<T>::f(C), c->st);
+                                (float*)Prec<T>::f(C), c->st, c->opts.level0_tiles != 0);
             return;
         }
         if (h16) {
@@ -807,7 +808,7 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
             if (c->rho0) {
                 ProfScope ps(c, PARIS_K_MATVEC0, 3.0 * N * 4);
                 launch_matvec_rho(c->g0, c->rh32, c->grid.h, c->d32, c->q32, c->partials, c->st,
-                                  FinSpec{c->scal, 1, 0, FIN_ALPHA, 0.0});
+                                  FinSpec{c->scal, 1, 0, FIN_ALPHA, 0.0}, c->opts.level0_tiles != 0);
             } else {
                 ProfScope ps(c, PARIS_K_MATVEC0, (2.0 * N + beta_count(c->g0)) * 4);
                 launch_matvec_dot<float>(c->g0, c32, c->d32, c->q32, c->partials, c->st,
@@ -871,6 +872,7 @@ void paris_default_opts(paris_opts* o) {
     o->slab_planes = 0;
     o->half_coefficients = 0;
     o->level0_density = 1;
+    o->level0_tiles = 1;
 }
 
 const char* paris_status_string(paris_status s) {

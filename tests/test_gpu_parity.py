@@ -365,3 +365,29 @@ def test_host_buffer_step_matches_device_step(paris, pinned):
             assert st_h["iters"] == st_d["iters"] and st_h["converged"] == 1
             for got, want in zip(hs[1:], ref):
                 np.testing.assert_array_equal(got.numpy(), want)
+
+
+@pytest.mark.parametrize("grid", [pi.Grid(48, 32, 40, 1 / 48, (P, P, W)), pi.Grid(64, 24, 16, 1 / 64, (W, P, P))],
+                         ids=["48x32x40_ppw", "64x24x16_wpp"])
+def test_level0_tiles_match_column_kernels(paris, grid):
+    """The plane-tile finest-level kernels (two pairs per thread) and the
+    z-column kernels (one pair per thread) compute the same operator: the
+    mixed projection step takes the same iterations with either and returns
+    the same p to the last few bits (the inner product's dot products are
+    summed in another order)."""
+    pr = pi.random_problem(grid, seed=33, rho1=1000.0)
+    out = []
+    for tiles in (1, 0):
+        with ctx_for(paris, grid, precision=paris.MIXED, level0_tiles=tiles) as ctx:
+            u, v, w = dev(pr.u), dev(pr.v), dev(pr.w)
+            p = torch.zeros(grid.shape, dtype=torch.float64, device="cuda")
+            ctx.profile(True)
+            st = ctx.projection_step(dev(pr.C), pr.rho1, pr.rho2, pr.dt, u, v, w, p)
+            prof = ctx.profile_read()["smooth0"]
+            ctx.profile(False)
+            assert st["converged"] == 1 and st["fell_back"] == 0
+            assert prof["bytes"] / prof["timed"] / grid.ncells <= 12.01
+            out.append((host(p), st["iters"], st["outer_iters"]))
+    assert out[0][1:] == out[1][1:]
+    p0, p1 = out
+    assert np.max(np.abs(p0[0] - p1[0])) <= 1e-9 * np.max(np.abs(p1[0]))
