@@ -43,7 +43,7 @@ NCU_TRAFFIC = {
     # "ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
     #  -k regex:rbgs_rho|op_rho|... -c 24" of "bench.py --single mixed": zero-initial passes
     # 134.3 MB, regular passes 186.8 MB; 11 and 77 of them per solve
-    "smooth0": {"bytes_per_launch": 180.2e6, "source": "rho0.cu", "sha": "cde4a82403ac57f9"},
+    "smooth0": {"bytes_per_launch": 180.2e6, "source": "rho0.cu", "sha": "95dae1dcc952a92f"},
 }
 
 
