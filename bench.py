@@ -42,8 +42,8 @@ NCU_TRAFFIC = {
     # finest-level colour pass: DRAM read + write bytes per launch from
     # "ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
     #  -k regex:rbgs_rho|op_rho|... -c 24" of "bench.py --single mixed": zero-initial passes
-    # 134.3 MB, regular passes 186.8 MB; 11 and 77 of them per solve
-    "smooth0": {"bytes_per_launch": 180.2e6, "source": "rho0.cu", "sha": "95dae1dcc952a92f"},
+    # 115.4 MB, the passes after them 153.0 MB, the others 186.7 MB; 11, 11 and 66 per solve
+    "smooth0": {"bytes_per_launch": 173.6e6, "source": "rho0.cu", "sha": "fb920ebe33b63029"},
 }
 
 

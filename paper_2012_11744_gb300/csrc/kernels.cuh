@@ -255,9 +255,16 @@ void launch_prolong_add(const Geo& fine, const Geo& coarse, const int fac[3], co
 // holds its cells of colour (i+j+k) even in order of i, then the odd ones.
 // even nx, ny, nz and 32-bit offsets
 bool rho0_fits(const Geo& g);
-// tiles: plane-tile kernels where nx/2 is even (else the z-column kernels)
+// tiles: plane-tile kernels where nx/2 is even (else the z-column kernels).
+// The plane-tile zero pass (zero_init) writes the updated colour only; the
+// pass of the other colour that follows it must be launched with own_zero,
+// which takes that colour as zero instead of reading it.  The z-column
+// kernels write both colours on the zero pass and ignore own_zero.
 void launch_rbgs_rho(const Geo& g, const float* rh, double h, const float* f, float* x, int color,
-                     double omega, bool zero_init, cudaStream_t st, int k0 = 0, int k1 = -1, bool tiles = true);
+                     double omega, bool zero_init, cudaStream_t st, int k0 = 0, int k1 = -1, bool tiles = true,
+                     bool own_zero = false);
+// whether launch_rbgs_rho runs the plane-tile kernels on this grid
+bool rho0_tile_pass(const Geo& g, bool tiles);
 // q = A d; partials (d . q); returns the number of blocks
 int64_t launch_matvec_rho(const Geo& g, const float* rh, double h, const float* d, float* q,
                           double* partials, cudaStream_t st, FinSpec fin = no_fin(), bool tiles = true);

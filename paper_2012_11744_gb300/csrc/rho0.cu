@@ -437,8 +437,11 @@ __device__ __forceinline__ void stv(float* p, const float (&d)[N]) {
     }
 }
 
-// member M of the V pairs (2t0 + 2v + M) is updated; walls as in pass_plane
-template <bool ZERO, int V, int M>
+// member M of the V pairs (2t0 + 2v + M) is updated; walls as in pass_plane.
+// ZERO: x is taken as 0 everywhere (nothing of x is read) and only the
+// updated colour is written; XZ: the updated colour is taken as 0 (the pass
+// after a ZERO pass of the other colour, which left it unwritten).
+template <bool ZERO, bool XZ, int V, int M>
 __device__ __forceinline__ void tile_update(const Geo& g, const float* __restrict__ rh,
                                             const float* __restrict__ f, float* x, float h2, float omega,
                                             int col, int j, int k, int t0, int lane, bool act) {
@@ -474,7 +477,12 @@ __device__ __forceinline__ void tile_update(const Geo& g, const float* __restric
 #pragma unroll
         for (int v = 0; v < V; ++v) xu[v] = xo[v] = xym[v] = xyp[v] = xzm[v] = xzp[v] = 0.f;
     } else {
-        ldv<V>(xu, x + su);
+        if (XZ) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) xu[v] = 0.f;
+        } else {
+            ldv<V>(xu, x + su);
+        }
         ldv<V>(xo, x + so);
         ldv<V>(xym, x + so + ym);
         ldv<V>(xyp, x + so + yp);
@@ -533,20 +541,12 @@ __device__ __forceinline__ void tile_update(const Geo& g, const float* __restric
             xn[v] = fmaf(omega, fmaf(w, acc, -xu[v]), xu[v]);
         }
     }
-    if (act) {
-        stv<V>(x + su, xn);
-        if (ZERO) {
-            float zr[V];
-#pragma unroll
-            for (int v = 0; v < V; ++v) zr[v] = 0.f;
-            stv<V>(x + so, zr);  // the other colour starts from zero
-        }
-    }
+    if (act) stv<V>(x + su, xn);
 }
 
 }  // namespace
 
-template <bool ZERO, int V>
+template <bool ZERO, bool XZ, int V>
 __global__ void __launch_bounds__(kBX* kVY) rbgs_rho_tile_kernel(Geo g, const float* __restrict__ rh, float h2,
                                                                const float* __restrict__ f, float* x,
                                                                int color, float omega, int k0) {
@@ -560,23 +560,30 @@ __global__ void __launch_bounds__(kBX* kVY) rbgs_rho_tile_kernel(Geo g, const fl
     const int t0 = act ? tv : hx - V;  // idle lanes shadow the last entries (no stores)
     // cell 2t0 has colour (j + k) & 1: the updated member is the same for the whole row
     if (((j + k + color) & 1) == 0)
-        tile_update<ZERO, V, 0>(g, rh, f, x, h2, omega, color, j, k, t0, lane, act);
+        tile_update<ZERO, XZ, V, 0>(g, rh, f, x, h2, omega, color, j, k, t0, lane, act);
     else
-        tile_update<ZERO, V, 1>(g, rh, f, x, h2, omega, color, j, k, t0, lane, act);
+        tile_update<ZERO, XZ, V, 1>(g, rh, f, x, h2, omega, color, j, k, t0, lane, act);
 }
 
+bool rho0_tile_pass(const Geo& g, bool tiles) { return tiles && kTileV > 0 && (g.nx / 2) % kTileV == 0; }
+
 void launch_rbgs_rho(const Geo& g, const float* rh, double h, const float* f, float* x, int color,
-                     double omega, bool zero_init, cudaStream_t st, int k0, int k1, bool tiles) {
+                     double omega, bool zero_init, cudaStream_t st, int k0, int k1, bool tiles, bool own_zero) {
     if (k1 < 0) k1 = g.nz;
     const float h2 = (float)(h * h);
     const int hx = g.nx / 2;
-    if (tiles && kTileV > 0 && hx % kTileV == 0) {
+    if (rho0_tile_pass(g, tiles)) {
         constexpr int V = kTileV > 0 ? kTileV : 2;
         dim3 gr((hx / V + kBX - 1) / kBX, (g.ny + kVY - 1) / kVY, k1 - k0);
         if (zero_init)
-            rbgs_rho_tile_kernel<true, V><<<gr, dim3(kBX, kVY), 0, st>>>(g, rh, h2, f, x, color, (float)omega, k0);
+            rbgs_rho_tile_kernel<true, false, V><<<gr, dim3(kBX, kVY), 0, st>>>(g, rh, h2, f, x, color,
+                                                                                (float)omega, k0);
+        else if (own_zero)
+            rbgs_rho_tile_kernel<false, true, V><<<gr, dim3(kBX, kVY), 0, st>>>(g, rh, h2, f, x, color,
+                                                                                (float)omega, k0);
         else
-            rbgs_rho_tile_kernel<false, V><<<gr, dim3(kBX, kVY), 0, st>>>(g, rh, h2, f, x, color, (float)omega, k0);
+            rbgs_rho_tile_kernel<false, false, V><<<gr, dim3(kBX, kVY), 0, st>>>(g, rh, h2, f, x, color,
+                                                                                 (float)omega, k0);
         count_launch();
         return;
     }

@@ -377,13 +377,19 @@ void smooth(paris_ctx* c, int l, const Coef<T>& cf, const T* f, T* x, int sweeps
             // f and the write of the updated colour, plus the coefficients
             // (three face arrays, or rho/2 once); a zero-initial pass reads no x
             // and writes both colours
-            const double b_first = v0 ? (z0 ? 2.5 : 3.0) * n * sz : (z0 ? 2 * n * sz : 2.5 * n * sz + nb * bsz);
-            const double b_second = v0 ? 3.0 * n * sz : 2.5 * n * sz + nb * bsz;
+            // (plane-tile zero pass: the updated colour only, and the pass after it
+            // reads neither colour's old value of its own cells)
+            const bool tile0 = v0 && rho0_tile_pass(L.g, o.level0_tiles != 0);
+            const double b_first = v0 ? (z0 ? (tile0 ? 2.0 : 2.5) : 3.0) * n * sz
+                                      : (z0 ? 2 * n * sz : 2.5 * n * sz + nb * bsz);
+            const double b_second = v0 ? ((z0 && tile0) ? 2.5 : 3.0) * n * sz : 2.5 * n * sz + nb * bsz;
             auto pass = [&](int color, bool zero, int a, int b) {
                 if constexpr (sizeof(T) == 4) {
                     if (v0) {
+                        // after a zero pass the other colour is still unwritten on the
+                        // plane-tile path: the second pass of that sweep takes it as zero
                         launch_rbgs_rho(L.g, c->rh32, c->grid.h, (const float*)f, (float*)x, color, o.omega,
-                                        zero, c->st, a, b, o.level0_tiles != 0);
+                                        zero, c->st, a, b, o.level0_tiles != 0, z0 && !zero);
                         return;
                     }
                     if (h16) {
