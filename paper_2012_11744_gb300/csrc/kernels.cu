@@ -648,10 +648,151 @@ __global__ void __launch_bounds__(kTX* kTY) rbgs_kernel(Geo g, const TB* __restr
     if (zero_init && io < g.nx) x[g.cidx(io, j, k)] = T(0);
 }
 
+// Four consecutive cells of a row as one 16-byte (FP32) or two 16-byte
+// (FP64) loads.
+template <typename T>
+__device__ __forceinline__ void ld4(T (&d)[4], const T* __restrict__ p) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+        d[0] = a.x; d[1] = a.y; d[2] = a.z; d[3] = a.w;
+    } else {
+        const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+        const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+        d[0] = a.x; d[1] = a.y; d[2] = b.x; d[3] = b.y;
+    }
+}
+template <typename T>
+__device__ __forceinline__ void ld4x(T (&d)[4], const T* p) {  // x: written in the same pass
+    if constexpr (sizeof(T) == 4) {
+        const float4 a = *reinterpret_cast<const float4*>(p);
+        d[0] = a.x; d[1] = a.y; d[2] = a.z; d[3] = a.w;
+    } else {
+        const double2 a = *reinterpret_cast<const double2*>(p);
+        const double2 b = *(reinterpret_cast<const double2*>(p) + 1);
+        d[0] = a.x; d[1] = a.y; d[2] = b.x; d[3] = b.y;
+    }
+}
+
+// The colour pass of rbgs_kernel with two pairs per thread: cells 4q..4q+3
+// of a row, of which the two of colour `color` are updated, every array read
+// as 16-byte vectors (the single-pair kernel's scalar loads stream the level
+// more slowly).  Same update, faces in the same order.  Needs nx % 4 == 0, no
+// walls along x, 32-bit offsets and 16-byte aligned arrays.
+// M: the updated member of both pairs ((j + k + color) & 1, uniform per warp)
+template <typename T, bool USEW, int M>
+__device__ __forceinline__ void rbgs4_row(const Geo& g, const T* __restrict__ bx, const T* __restrict__ by,
+                                          const T* __restrict__ bz, T scale, const T* __restrict__ w,
+                                          const T* __restrict__ f, T* __restrict__ x, T omega, int zero_init,
+                                          int j, int k, int i0, int lane, bool act) {
+    const int nx = g.nx, ny = g.ny, nz = g.nz, pl = nx * ny;
+    const int rowc = (k * ny + j) * nx;
+    const int c0 = rowc + i0;
+    const bool ylo = j == 0, yhi = j == ny - 1, zlo = k == 0, zhi = k == nz - 1;
+    const int ym = !ylo ? -nx : (g.wy ? 0 : (ny - 1) * nx), yp = !yhi ? nx : (g.wy ? 0 : -(ny - 1) * nx);
+    const int zm = !zlo ? -pl : (g.wz ? 0 : (nz - 1) * pl), zp = !zhi ? pl : (g.wz ? 0 : -(nz - 1) * pl);
+    const int fy0 = (k * (ny + g.wy) + j) * nx + i0;  // y-faces below the cells
+    const int fy1 = (!yhi || g.wy) ? fy0 + nx : fy0 - (ny - 1) * nx;
+    T X[4], F[4], W[4], XYM[4], XYP[4], XZM[4], XZP[4], BX[4], BY0[4], BY1[4], BZ0[4], BZ1[4];
+    ld4(F, f + c0);
+    if (USEW) ld4(W, w + c0);
+    ld4(BX, bx + c0);  // x-faces i0 .. i0+3 (no walls along x: the face row is the cell row)
+    ld4(BY0, by + fy0);
+    ld4(BY1, by + fy1);
+    ld4(BZ0, bz + c0);
+    ld4(BZ1, bz + ((!zhi || g.wz) ? c0 + pl : c0 - (nz - 1) * pl));
+    // face i0+4 (the + face of the last cell): the next lane's first, or loaded
+    const int ir = i0 + 4 < nx ? i0 + 4 : 0;
+    // (every lane takes part in the shuffle; the select comes after it)
+    const T bxr_ld = __ldg(bx + rowc + ir);
+    const T bxr_sh = __shfl_down_sync(0xffffffffu, BX[0], 1);
+    const T bxr = (lane < kTX - 1 && i0 + 4 < nx) ? bxr_sh : bxr_ld;
+    if (zero_init) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) X[u] = XYM[u] = XYP[u] = XZM[u] = XZP[u] = T(0);
+    } else {
+        ld4x(X, x + c0);
+        ld4x(XYM, x + c0 + ym);
+        ld4x(XYP, x + c0 + yp);
+        ld4x(XZM, x + c0 + zm);
+        ld4x(XZP, x + c0 + zp);
+    }
+    // x of the cells next to the quad (i0-1 and i0+4, wrapped around the row)
+    T xl = T(0), xr = T(0);
+    if (!zero_init) {
+        const T xl_ld = x[rowc + (i0 > 0 ? i0 - 1 : nx - 1)], xr_ld = x[rowc + ir];
+        const T xl_sh = __shfl_up_sync(0xffffffffu, X[3], 1), xr_sh = __shfl_down_sync(0xffffffffu, X[0], 1);
+        xl = (lane > 0 && i0 > 0) ? xl_sh : xl_ld;
+        xr = (lane < kTX - 1 && i0 + 4 < nx) ? xr_sh : xr_ld;
+    }
+    const T hs = T(1) / scale;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int li = 2 * u + M;  // the updated cell of pair u
+        T b[6];
+        b[0] = BX[li];
+        b[1] = li < 3 ? BX[li + 1] : bxr;
+        b[2] = (g.wy && ylo) ? T(0) : BY0[li];
+        b[3] = (g.wy && yhi) ? T(0) : BY1[li];
+        b[4] = (g.wz && zlo) ? T(0) : BZ0[li];
+        b[5] = (g.wz && zhi) ? T(0) : BZ1[li];
+        T xn;
+        if (zero_init) {
+            const T wc = USEW ? W[li] : inv_sum6(b);
+            xn = omega * wc * (F[li] * hs);
+        } else {
+            const T nb[6] = {li > 0 ? X[li - 1] : xl, li < 3 ? X[li + 1] : xr, XYM[li], XYP[li], XZM[li], XZP[li]};
+            T acc = F[li] * hs;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) acc = fma(b[q], nb[q], acc);
+            const T xc = X[li];
+            xn = fma(omega, fma(USEW ? W[li] : inv_sum6(b), acc, -xc), xc);
+        }
+        if (act) {
+            x[c0 + li] = xn;
+            if (zero_init) x[c0 + li + 1 - 2 * M] = T(0);  // the other member of the pair
+        }
+    }
+}
+
+template <typename T, bool USEW>
+__global__ void __launch_bounds__(kTX* kTY) rbgs4_kernel(Geo g, const T* __restrict__ bx,
+                                                        const T* __restrict__ by,
+                                                        const T* __restrict__ bz, T scale,
+                                                        const T* __restrict__ w,
+                                                        const T* __restrict__ f, T* __restrict__ x,
+                                                        int color, T omega, int zero_init, int k0) {
+    const int j = blockIdx.y * kTY + threadIdx.y;
+    if (j >= g.ny) return;  // uniform per warp
+    const int k = k0 + blockIdx.z;
+    const int nq = g.nx / 4;
+    const int lane = threadIdx.x;
+    const int qv = blockIdx.x * kTX + lane;
+    const bool act = qv < nq;
+    const int i0 = 4 * (act ? qv : nq - 1);  // idle lanes shadow the last quad (no stores)
+    if (((j + k + color) & 1) == 0)
+        rbgs4_row<T, USEW, 0>(g, bx, by, bz, scale, w, f, x, omega, zero_init, j, k, i0, lane, act);
+    else
+        rbgs4_row<T, USEW, 1>(g, bx, by, bz, scale, w, f, x, omega, zero_init, j, k, i0, lane, act);
+}
+
 template <typename T>
 void launch_rbgs(const Geo& g, const Coef<T>& cf, const T* w, const T* f, T* x, int color,
                  double omega, bool zero_init, cudaStream_t st, int k0, int k1) {
     if (k1 < 0) k1 = g.nz;
+    // four cells per thread where a row fills at least a warp (shorter rows
+    // would leave lanes idle: the single-pair kernel serves them)
+    if (g.nx % 4 == 0 && g.nx >= 4 * kTX && !g.wx && fits_i32(g) && aligned16(cf.bx, cf.by, cf.bz, f) &&
+        aligned16(x) && (sizeof(T) == 4 || aligned16(w))) {
+        dim3 gr((g.nx / 4 + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, k1 - k0);
+        if (sizeof(T) == 8)
+            rbgs4_kernel<T, true><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf.bx, cf.by, cf.bz, cf.scale, w, f, x, color,
+                                                                 (T)omega, zero_init ? 1 : 0, k0);
+        else
+            rbgs4_kernel<T, false><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf.bx, cf.by, cf.bz, cf.scale, w, f, x, color,
+                                                                  (T)omega, zero_init ? 1 : 0, k0);
+        count_launch();
+        return;
+    }
     const int npair = (g.nx + 1) / 2;
     dim3 gr((npair + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, k1 - k0);
     // FP32: recomputing 1/D from the coefficients already loaded is cheaper
