@@ -43,7 +43,7 @@ NCU_TRAFFIC = {
     # "ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
     #  -k regex:rbgs_rho|op_rho|... -c 24" of "bench.py --single mixed": zero-initial passes
     # 115.4 MB, the passes after them 153.0 MB, the others 186.7 MB; 11, 11 and 66 per solve
-    "smooth0": {"bytes_per_launch": 173.6e6, "source": "rho0.cu", "sha": "fb920ebe33b63029"},
+    "smooth0": {"bytes_per_launch": 173.6e6, "source": "rho0.cu", "sha": "f29994e75ed92a4f"},
 }
 
 

@@ -16,9 +16,17 @@
 // and every neighbour it needs from the other half, instead of moving whole
 // rows of which it updates half.  rho/2 stays in cell order.
 //
-// Thread layout: a thread owns the x-pair of cells (2t, 2t+1) of one row
-// (entry t of both half-rows) and walks a segment of z-planes (an even number
-// chosen per launch).  The pair's values of the planes above are loaded a few
+// Two kernel families apply the operator.  Where nx/2 is even, the
+// plane-tile kernels (rbgs_rho_tile_kernel, op_rho_tile_kernel, below) give a
+// thread two consecutive pairs of one row of one plane and read every
+// half-row as a vector; blocks sweep the planes in order, so the planes above
+// and below come from L2.  They stream the level faster and are the ones the
+// projection step uses.  The z-column kernels described next serve odd nx/2
+// (and paris_opts.level0_tiles = 0).
+//
+// Z-column thread layout: a thread owns the x-pair of cells (2t, 2t+1) of one
+// row (entry t of both half-rows) and walks a segment of z-planes (an even
+// number chosen per launch).  The pair's values of the planes above are loaded a few
 // planes ahead into a ring of registers, so each warp keeps several planes of
 // loads in flight while it computes; the values one plane below are carried
 // from the previous step.  The x-neighbours outside the pair are held by the
