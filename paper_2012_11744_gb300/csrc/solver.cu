@@ -1205,10 +1205,30 @@ paris_status paris_projection_step_host(paris_ctx* c, const double* C_host, doub
         return PARIS_ERR_INVALID_ARG;
     if (!(dt > 0.0) || !std::isfinite(dt)) return PARIS_ERR_INVALID_ARG;
     if (!c->copy_st) {
-        CK(cudaStreamCreateWithFlags(&c->copy_st, cudaStreamNonBlocking));
-        for (auto& e : c->copy_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        // all or nothing: a failed creation leaves the context as it was
+        cudaStream_t cs = nullptr;
+        cudaEvent_t ev[5] = {};
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            for (auto& x : ev)
+                if (x) cudaEventDestroy(x);
+            if (cs) cudaStreamDestroy(cs);
+            paris_internal_note_cuda_error(e);
+            return PARIS_ERR_CUDA;
+        }
+        c->copy_st = cs;
+        for (int i = 0; i < 5; ++i) c->copy_ev[i] = ev[i];
     }
     cudaStream_t cs = c->copy_st;
+    // on every way out, no copy into or out of the caller's buffers is left running
+    struct DrainGuard {
+        paris_ctx* c;
+        ~DrainGuard() {
+            cudaStreamSynchronize(c->copy_st);
+            cudaStreamSynchronize(c->st);
+        }
+    } drain{c};
     // the copies start after the work already queued on the context's stream
     CK(cudaEventRecord(c->copy_ev[4], c->st));
     CK(cudaStreamWaitEvent(cs, c->copy_ev[4], 0));
@@ -1223,12 +1243,7 @@ paris_status paris_projection_step_host(paris_ctx* c, const double* C_host, doub
     CK(cudaMemcpyAsync(c->hp, p_host, sizeof(double) * N, cudaMemcpyHostToDevice, cs));
     CK(cudaEventRecord(hl.p_ready, cs));
     paris_status s = projection_step_impl(c, c->hC, rho1, rho2, dt, c->hu, c->hv, c->hw, c->hp, st, &hl);
-    if (s != PARIS_OK && s != PARIS_ERR_NOT_CONVERGED) {
-        // leave no copy into or out of the caller's buffers running
-        cudaStreamSynchronize(cs);
-        cudaStreamSynchronize(c->st);
-        return s;
-    }
+    if (s != PARIS_OK && s != PARIS_ERR_NOT_CONVERGED) return s;
     // u, v, w go back once the correction is done (p is already on its way)
     CK(cudaEventRecord(c->copy_ev[4], c->st));
     CK(cudaStreamWaitEvent(cs, c->copy_ev[4], 0));
