@@ -15,6 +15,9 @@ Every function follows a passage of the PARIS paper (arXiv 2012.11744):
   projection_step  steps 1-6 in order, then mean(p) = 0
   project_adjoint / face_coeffs_adjoint: derivatives of the above (no paper
   counterpart; pinned against central finite differences in the tests)
+
+The implicit viscous step of Sec. 3.2.3 (Eq. muelliptic) is in ``viscous.py``
+(numpy and scipy.sparse, FP64).
 """
 from __future__ import annotations
 
