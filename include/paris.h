@@ -250,6 +250,50 @@ paris_status paris_face_coeffs_adjoint(paris_ctx* ctx, double rho1, double rho2,
                                        const double* gbeta_y, const double* gbeta_z, double* gC);
 
 /* ---------------------------------------------------------------------------
+ * IMPLICIT VISCOUS STEP (Sec. 3.2.3, Eq. muelliptic).  For one velocity
+ * component, u* - tau nu_f Lap_h u* = u^n on the component's own face grid,
+ * Lap_h the 7-point Laplacian with spacing h.  The unknowns are the
+ * component's faces except its wall faces (where it is zero).  Beyond the
+ * ends of an axis the Laplacian takes: the wrapped value (periodic axis),
+ * zero (the component's own wall faces), or minus the end value (a wall
+ * axis of a tangential component: no-slip, the velocity vanishes on the
+ * wall, half a cell beyond the last unknown).  nu_f is the kinematic
+ * viscosity at the face: the printed equation multiplies the Laplacian by
+ * the dynamic viscosity, which the predictor's form of the viscous term
+ * divides by the density. */
+
+/* nu_f = (mu_L + mu_R) / (rho_L + rho_R) on every face of component comp
+ * (0 = x-faces, 1 = y-faces, 2 = z-faces; face layout above), mu and rho
+ * from Eq. muH in the two cells sharing the face: mu = mu1 C + mu2 (1 - C),
+ * rho = rho1 C + rho2 (1 - C).  Wall faces of the component get 0.  C:
+ * cells; nu: the component's face array (output).  The products and sums are
+ * rounded one by one, in that order (no fused multiply-add).
+ * Errors: INVALID_ARG (null pointer, comp outside 0..2, a mu or rho that is
+ * not finite and > 0). */
+paris_status paris_face_viscosity(paris_ctx* ctx, int comp, const double* C, double mu1, double mu2,
+                                  double rho1, double rho2, double* nu);
+
+/* Solve Eq. muelliptic for component comp in its symmetric positive definite
+ * form (diag(1/(tau nu)) - Lap_h) u* = u^n / (tau nu) by conjugate gradients
+ * with the Jacobi preconditioner, in FP64, from the initial guess u* = u^n.
+ * nu, un (in) and us (out): the component's face arrays; entries on its wall
+ * faces are not read, and us gets 0 there.  nu must be finite and > 0 on the
+ * unknowns.  us must not overlap un or nu.  Stops when
+ * ||b - A u*||_2 <= tol ||b||_2 and ||b - A u*||_inf <= tol ||b||_inf, with
+ * b = u^n/(tau nu), checked on the true residual; max_iter bounds the CG
+ * iterations.  tau = 0 returns u* = u^n.  Uses the context's Krylov
+ * workspace (no allocation) and synchronises the stream.  st (host,
+ * optional): iters (CG iterations), outer_iters (restarts + 1), the relative
+ * residual norms of the SPD form, converged; the other fields 0.
+ * Errors: INVALID_ARG (null pointer, comp outside 0..2, us equal to un or nu,
+ * tau < 0 or not finite, tol outside (0,1), max_iter < 1), NONFINITE (a nu
+ * that is not > 0, or a NaN/Inf in the right-hand side or the residual),
+ * NOT_CONVERGED (us holds the last iterate), CUDA. */
+paris_status paris_viscous_solve(paris_ctx* ctx, int comp, const double* nu, double tau,
+                                 const double* un, double* us, double tol, int max_iter,
+                                 paris_stats* st);
+
+/* ---------------------------------------------------------------------------
  * BATCHED PROJECTIONS.  Many independent projection steps of uneven grid
  * sizes in one persistent cooperative launch (captured in a CUDA graph on the
  * first call and replayed afterwards).  Every instance runs the same step as

@@ -286,6 +286,33 @@ class Context:
             self._t(gbz, fs[2], "gbeta_z"), self._t(gC, g.shape, "gC")), "paris_face_coeffs_adjoint")
         return gC
 
+    def face_viscosity(self, comp, C, mu1, mu2, rho1, rho2, out=None):
+        """nu_f = (mu_L + mu_R)/(rho_L + rho_R) on the faces of component comp
+        (Eq. muH in both cells), 0 on its wall faces."""
+        g = self.grid
+        fs = g.face_shape(comp)
+        nu = out if out is not None else torch.empty(fs, dtype=torch.float64, device=self.device)
+        _abi.check(self.lib.paris_face_viscosity(self._ptr, int(comp), self._t(C, g.shape, "C"), float(mu1),
+                                                 float(mu2), float(rho1), float(rho2), self._t(nu, fs, "nu")),
+                   "paris_face_viscosity")
+        return nu
+
+    def viscous_solve(self, comp, nu, tau, un, us=None, tol=1e-12, max_iter=10000, check=True):
+        """u* - tau nu Lap_h u* = u^n for component comp (Eq. muelliptic) on its
+        face array; returns (us, stats dict)."""
+        g = self.grid
+        fs = g.face_shape(comp)
+        us = us if us is not None else torch.empty(fs, dtype=torch.float64, device=self.device)
+        st = _abi.Stats()
+        s = self.lib.paris_viscous_solve(self._ptr, int(comp), self._t(nu, fs, "nu"), float(tau),
+                                         self._t(un, fs, "un"), self._t(us, fs, "us"), float(tol),
+                                         int(max_iter), ct.byref(st))
+        if check:
+            _abi.check(s, "paris_viscous_solve", st.as_dict())
+        d = st.as_dict()
+        d["status"] = s
+        return us, d
+
     def residual_norms(self, bx, by, bz, rhs, p):
         """FP64 (||rhs - L p||_2/||rhs||_2, ||.||_inf/||rhs||_inf) on the device."""
         g = self.grid

@@ -38,7 +38,8 @@ enum FinalizeMode {
     FIN_FCG_BETA = 7,   // beta = -alpha * result1 / rho, rho = result0 (flexible CG)
     FIN_SCALE = 8,      // scale = 1/max(result1, tiny), rr0 = rr*scale^2 ... (mixed)
     FIN_INNER_INIT = 9, // rr0 = result0, rr = result0
-    FIN_REFINE = 10     // scale from the current rinf, then rr = result0 / scale^2, rinf = result1
+    FIN_REFINE = 10,    // scale from the current rinf, then rr = result0 / scale^2, rinf = result1
+    FIN_RNORMS_RHO = 11 // rr = result0, rinf = result1, beta = result3 / rho, rho = result3 (Jacobi PCG)
 };
 
 // Second stage of a reduction, by one block of kRedThreads threads: fold the
@@ -102,6 +103,11 @@ __device__ inline void finalize_block(const double* partials, int64_t nblocks, i
                 s->xmax = r[3];
                 break;
             case FIN_RNORMS: s->rr = r[0]; s->rinf = r[1]; s->nonfinite += r[2]; break;
+            case FIN_RNORMS_RHO:
+                s->rr = r[0]; s->rinf = r[1]; s->nonfinite += r[2];
+                s->beta = (s->rho != 0.0) ? r[3] / s->rho : 0.0;
+                s->rho = r[3];
+                break;
             case FIN_ALPHA: s->alpha = (r[0] > 0.0) ? s->rho / r[0] : 0.0; break;
             case FIN_RHO_BETA: s->beta = (s->rho != 0.0) ? r[0] / s->rho : 0.0; s->rho = r[0]; break;
             case FIN_RHO_INIT: s->rho = r[0]; s->beta = 0.0; break;
@@ -171,6 +177,42 @@ long long launch_count();
 
 void finalize(const double* partials, int64_t nblocks, int nv, int maxmask, Scal* s, int mode,
               double param, cudaStream_t st);
+
+// ------------------------------------------------- implicit viscous step ---
+// One velocity component of Sec. 3.2.3 (Eq. muelliptic) in SPD form,
+// (diag(1/(tau nu)) - Lap_h) u* = u^n/(tau nu), on its unknowns (viscous.cu).
+
+enum HelmKind { HELM_PERIODIC = 0, HELM_ZERO = 1, HELM_NOSLIP = 2 };
+
+struct HelmGeo {
+    int m[3];     // unknowns along x, y, z
+    int e[3];     // extents of the component's full face array
+    int kind[3];  // beyond the ends of each axis: wrap, zero, minus the end value
+    int comp;     // 0 = u (x-faces), 1 = v, 2 = w
+    int wall;     // the face array holds wall faces along the component's axis
+    int64_t off;  // face-array index of unknown (0,0,0)
+    double ih2;   // 1/h^2
+};
+HelmGeo helm_geo(const Geo& g0, int comp, double h);
+int64_t helm_unknowns(const HelmGeo& g);
+int64_t helm_faces(const HelmGeo& g);
+// us = un on the unknowns, 0 on the wall faces; partials (|b|^2, max|b|,
+// non-finite count, 0) of b = un/(tau nu)
+int64_t launch_helm_init(const HelmGeo& g, const double* un, const double* nu, double tau, double* us,
+                         double* partials, cudaStream_t st, FinSpec fin);
+// r = b - A x, z = r/diag(A); partials (r.r, max|r|, non-finite count, r.z)
+int64_t launch_helm_residual(const HelmGeo& g, const double* un, const double* nu, double tau, const double* x,
+                             double* r, double* z, double* partials, cudaStream_t st, FinSpec fin);
+// q = A d; partials d.q
+int64_t launch_helm_matvec_dot(const HelmGeo& g, const double* nu, double tau, const double* d, double* q,
+                               double* partials, cudaStream_t st, FinSpec fin);
+// x += alpha d, r -= alpha q, z = r/diag(A); partials as launch_helm_residual
+int64_t launch_helm_update(const HelmGeo& g, const double* nu, double tau, const Scal* s, const double* d,
+                           const double* q, double* x, double* r, double* z, double* partials, cudaStream_t st,
+                           FinSpec fin);
+// nu_f = (mu_L + mu_R)/(rho_L + rho_R) on the component's faces, 0 on its wall faces
+void launch_helm_face_nu(const HelmGeo& g, const Geo& g0, const double* C, double mu1, double mu2, double rho1,
+                         double rho2, double* nu, cudaStream_t st);
 
 // ---------------------------------------------------------- field steps ---
 // beta = 2/(rho_L + rho_R) (FP64); rh32 (may be null): FP32 copy of rho/2,

@@ -1342,6 +1342,80 @@ paris_status paris_stream_rates(const float* a, const float* b, const float* c, 
     return PARIS_OK;
 }
 
+paris_status paris_face_viscosity(paris_ctx* c, int comp, const double* C, double mu1, double mu2,
+                                  double rho1, double rho2, double* nu) {
+    if (!c || !C || !nu || comp < 0 || comp > 2) return PARIS_ERR_INVALID_ARG;
+    if (!(mu1 > 0.0) || !(mu2 > 0.0) || !(rho1 > 0.0) || !(rho2 > 0.0) || !std::isfinite(mu1) ||
+        !std::isfinite(mu2) || !std::isfinite(rho1) || !std::isfinite(rho2))
+        return PARIS_ERR_INVALID_ARG;
+    launch_helm_face_nu(helm_geo(c->g0, comp, c->grid.h), c->g0, C, mu1, mu2, rho1, rho2, nu, c->st);
+    CK(cudaGetLastError());
+    return PARIS_OK;
+}
+
+paris_status paris_viscous_solve(paris_ctx* c, int comp, const double* nu, double tau, const double* un,
+                                 double* us, double tol, int max_iter, paris_stats* st) {
+    if (!c || !nu || !un || !us || comp < 0 || comp > 2) return PARIS_ERR_INVALID_ARG;
+    if (us == un || us == nu) return PARIS_ERR_INVALID_ARG;
+    if (!(tau >= 0.0) || !std::isfinite(tau) || !(tol > 0.0 && tol < 1.0) || max_iter < 1)
+        return PARIS_ERR_INVALID_ARG;
+    if (st) *st = paris_stats{};
+    const HelmGeo g = helm_geo(c->g0, comp, c->grid.h);
+    CK(cudaMemsetAsync(c->scal, 0, sizeof(Scal), c->st));
+    if (tau == 0.0) {  // u* = u^n
+        launch_helm_init(g, un, nu, 1.0, us, c->partials, c->st, no_fin());
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(c->st));
+        if (st) st->converged = 1;
+        return PARIS_OK;
+    }
+    const auto met = [tol](const Scal& h) { return h.rr <= tol * tol * h.bnorm2 && h.rinf <= tol * h.binf; };
+    const FinSpec rnorms{c->scal, 4, 2, FIN_RNORMS_RHO, 0.0};
+    double *r = c->r, *z = c->z, *d = c->d, *q = c->q;
+    launch_helm_init(g, un, nu, tau, us, c->partials, c->st, FinSpec{c->scal, 4, 0xA, FIN_BNORMS, 0.0});
+    launch_helm_residual(g, un, nu, tau, us, r, z, c->partials, c->st, rnorms);
+    CK(cudaGetLastError());
+    paris_status s = read_scal(c);
+    if (s != PARIS_OK) return s;
+    int iters = 0, restarts = 0;
+    bool converged = c->scal_h->bnorm2 == 0.0 || met(*c->scal_h);
+    bool nonfinite = c->scal_h->nonfinite > 0;
+    while (!converged && !nonfinite && iters < max_iter) {
+        std::swap(d, z);  // first direction d = z: exchange the buffers
+        bool inner = false;
+        while (iters < max_iter) {
+            launch_helm_matvec_dot(g, nu, tau, d, q, c->partials, c->st, FinSpec{c->scal, 1, 0, FIN_ALPHA, 0.0});
+            launch_helm_update(g, nu, tau, c->scal, d, q, us, r, z, c->partials, c->st, rnorms);
+            CK(cudaGetLastError());
+            s = read_scal(c);
+            if (s != PARIS_OK) return s;
+            ++iters;
+            if (c->scal_h->nonfinite > 0) { nonfinite = true; break; }
+            if (met(*c->scal_h)) { inner = true; break; }
+            launch_xpby<double>(helm_unknowns(g), c->scal, z, d, c->st);  // d = z + beta d
+        }
+        if (nonfinite) break;
+        // verify with the true residual; restart from it if the recurrence drifted
+        launch_helm_residual(g, un, nu, tau, us, r, z, c->partials, c->st, rnorms);
+        CK(cudaGetLastError());
+        s = read_scal(c);
+        if (s != PARIS_OK) return s;
+        nonfinite = c->scal_h->nonfinite > 0;
+        converged = !nonfinite && met(*c->scal_h);
+        if (converged || !inner || ++restarts > 3) break;
+    }
+    const Scal& h = *c->scal_h;
+    if (st) {
+        st->iters = iters;
+        st->outer_iters = restarts + 1;
+        st->rel_res_l2 = h.bnorm2 > 0 ? std::sqrt(h.rr / h.bnorm2) : 0.0;
+        st->rel_res_linf = h.binf > 0 ? h.rinf / h.binf : 0.0;
+        st->converged = converged ? 1 : 0;
+    }
+    if (nonfinite) return PARIS_ERR_NONFINITE;
+    return converged ? PARIS_OK : PARIS_ERR_NOT_CONVERGED;
+}
+
 paris_status paris_max_divergence(paris_ctx* c, const double* u, const double* v,
                                   const double* w, double* max_abs_div) {
     if (!c || !u || !v || !w || !max_abs_div) return PARIS_ERR_INVALID_ARG;
