@@ -451,6 +451,71 @@ def run_single(args):
     print(json.dumps({"single": args.single, "smoother": args.smoother, "stats": st}))
 
 
+def run_viscous(args):
+    """Implicit viscous step (Eq. muelliptic) of the three velocity components
+    on the drop field, one JSON line.  nu_f from Eq. muH with water/air-like
+    viscosities (mu 1e-3 / 1.8e-5) and the workload's densities; tau =
+    4 h^2 / max nu_f (24 times the explicit stability limit of the viscous
+    term); tol 1e-10.  One step = the three component solves from u*, v*, w*
+    resident on the device.  Algorithmic bytes of one CG iteration per
+    unknown: q = A d (d, nu read, q written: 24 B), x, r, z update (d, q, x,
+    r, nu read; x, r, z written: 64 B), d = z + beta d (24 B)."""
+    import torch
+
+    import paper_2012_11744_gb300 as paris
+    import paris_inputs as pi
+    pr = pi.config2(n=args.n)
+    g = pr.grid
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    ctx = paris.Context(g)
+    C = d(pr.C)
+    uvw = [d(pr.u), d(pr.v), d(pr.w)]
+    nus = [ctx.face_viscosity(c, C, 1e-3, 1.8e-5, pr.rho1, pr.rho2) for c in range(3)]
+    numax = max(float(nu.max()) for nu in nus)
+    tau = 4.0 * g.h ** 2 / numax
+    outs = [torch.empty_like(x) for x in uvw]
+    st = ctx.stream
+    stats = []
+
+    def step():
+        stats.clear()
+        for c in range(3):
+            stats.append(ctx.viscous_solve(c, nus[c], tau, uvw[c], outs[c], tol=1e-10)[1])
+
+    for _ in range(args.warmup):
+        step()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        ev0.record(st)
+        for _ in range(args.steps):
+            step()
+        ev1.record(st)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    iters = [s["iters"] for s in stats]
+    # unknowns of component c: its face grid without the wall faces of its own axis
+    cells = (g.nx, g.ny, g.nz)
+    unknowns = [int(np.prod([cells[a] - (1 if a == c and g.bc[a] == pi.WALL else 0) for a in range(3)]))
+                for c in range(3)]
+    byt = sum(112.0 * n * k for n, k in zip(unknowns, iters))
+    hbm, kind = measured_peaks()
+    gbs = byt / (ms * 1e-3) / 1e9
+    print(json.dumps({
+        "metric": "implicit viscous solves/s (u, v, w each a solve) at %d^3, tol 1e-10" % args.n,
+        "value": 3.0 / (ms * 1e-3), "unit": "solves/s", "ms_per_step": ms, "steps": args.steps,
+        "warmup": args.warmup, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+        "iters": iters, "converged": [s["converged"] for s in stats],
+        "rel_res_l2": [s["rel_res_l2"] for s in stats], "tau_nu_max_over_h2": 4.0,
+        "cg_iteration_bytes": byt,
+        "iteration_roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                               "frac": gbs / hbm, "peak_kind": kind,
+                               "note": "whole iterations incl. the host read of the norms"},
+        "clocks": clk.summary(),
+        "config": {"workload": workload_config(args.n)["workload"] + ", mu 1e-3/1.8e-5",
+                   "l2": "no flush: each iteration streams 7 vectors of one component (> 129 MB L2)"}}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -466,11 +531,16 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-mode measurement")
     ap.add_argument("--single", choices=["mixed", "fp64"], default=None,
                     help="run one untimed projection (the target of ncu captures) and exit")
+    ap.add_argument("--viscous", action="store_true",
+                    help="time the implicit viscous step of the three components instead and exit")
     ap.add_argument("--smoother", type=int, default=None,
                     help="with --single: 0 fused red-black, 1 Jacobi, 2 two-pass red-black")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.viscous:
+        run_viscous(args)
+        return
     if args.single:
         run_single(args)
         return
