@@ -829,7 +829,7 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
             ++out.iters;
             if (s != PARIS_OK) return s;
             const double in_rr = c->scal_h->red[0];
-            if (!(in_rr == in_rr) || c->scal_h->red[2] > 0) break;  // non-finite: let the outer step judge
+            if (!(in_rr == in_rr) || c->scal_h->red[2] > 0) break;  // non-finite: the outer step decides
             if (in_rr <= target || in_rr > 1e6 * rr32) break;
             vcycle<float>(c, c32, c->r32, c->z32);
             ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
