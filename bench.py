@@ -32,6 +32,11 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# implicit viscous step of `--viscous`: mu of fluid 1 / fluid 2, and tau = this
+# factor times h^2 / max nu_f
+VISC_MU = (1.0e-3, 1.8e-5)
+VISC_TAU_NU_OVER_H2 = 4.0
+
 METRIC = "Projection solves/s at 256³, ρ ratio 1000, resid 1e-10: mixed vs FP64; % HBM"
 UNIT = "solves/s"
 
@@ -180,6 +185,52 @@ def oracle_sample(pr, budget_s: float, golden: dict | None):
     solve_s = setup + per_it * n_full
     return {"solve_s": solve_s, "setup_s": setup, "s_per_cg_iter": per_it, "cg_iters_sampled": res.iters,
             "cg_iters_full": n_full, "sample_s": t5 - t0}
+
+
+def viscous_oracle_sample(pr, budget_s: float, golden: dict | None):
+    """Time the viscous oracle (as it stands) on a bounded sample of the step
+    `run_viscous` times: face viscosities of the three components, then
+    oracle solves of the w component cut short after 1, 5 and m2 CG
+    iterations (each assembles its operator; m2 sized from the first two so
+    that the last one iterates for about `budget_s`).  The difference of the
+    first and last gives the time of one iteration, the rest the set-up;
+    extrapolated to the three components' iteration counts of the full oracle
+    solves (stored by tests/golden/make_viscous256_golden.py)."""
+    from oracle import viscous as V
+    g = pr.grid
+    t0 = time.perf_counter()
+    nus = [V.face_nu(g, c, pr.C, VISC_MU[0], VISC_MU[1], pr.rho1, pr.rho2) for c in range(3)]
+    tau = VISC_TAU_NU_OVER_H2 * g.h ** 2 / max(float(nu.max()) for nu in nus)
+    t1 = time.perf_counter()
+    un = V.interior(g, 2, pr.w)
+
+    def cut(m):
+        t = time.perf_counter()
+        try:
+            V.solve(g, 2, nus[2], tau, un, tol=1e-300, max_iter=m)
+        except RuntimeError:  # stopped after m iterations, as intended
+            pass
+        return time.perf_counter() - t
+
+    m1 = 1
+    s1 = cut(m1)
+    rough = max(cut(m1 + 4) - s1, 1e-6) / 4  # a first estimate of one iteration's time
+    m2 = m1 + max(8, int(budget_s / rough))
+    s2 = cut(m2)
+    per_it = max(s2 - s1, 0.0) / (m2 - m1)
+    setup = max(s1 - m1 * per_it, 0.0)
+    iters = [int(c["iters"]) for c in golden["components"]] if golden else [100, 100, 100]
+    step_s = (t1 - t0) + sum(setup + per_it * k for k in iters)
+    return {"step_s": step_s, "setup_s": setup, "s_per_cg_iter": per_it, "cg_iters_sampled": [m1, m2],
+            "cg_iters_full": iters, "sample_s": time.perf_counter() - t0}
+
+
+def load_visc_golden(n):
+    p = os.path.join(ROOT, "tests", "golden", f"viscous{n}_drops.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh)
+    return None
 
 
 def load_golden(n):
@@ -470,9 +521,9 @@ def run_viscous(args):
     ctx = paris.Context(g)
     C = d(pr.C)
     uvw = [d(pr.u), d(pr.v), d(pr.w)]
-    nus = [ctx.face_viscosity(c, C, 1e-3, 1.8e-5, pr.rho1, pr.rho2) for c in range(3)]
+    nus = [ctx.face_viscosity(c, C, VISC_MU[0], VISC_MU[1], pr.rho1, pr.rho2) for c in range(3)]
     numax = max(float(nu.max()) for nu in nus)
-    tau = 4.0 * g.h ** 2 / numax
+    tau = VISC_TAU_NU_OVER_H2 * g.h ** 2 / numax
     outs = [torch.empty_like(x) for x in uvw]
     st = ctx.stream
     stats = []
@@ -501,6 +552,15 @@ def run_viscous(args):
     byt = sum(112.0 * n * k for n, k in zip(unknowns, iters))
     hbm, kind = measured_peaks()
     gbs = byt / (ms * 1e-3) / 1e9
+    cpu = None
+    if not args.no_cpu:
+        gold = load_visc_golden(args.n)
+        smp = viscous_oracle_sample(pr, args.cpu_budget, gold)
+        cpu = {"value": 3.0 / smp["step_s"], "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"scipy CG (sparse products on one thread), face viscosities, then the w solve cut after "
+                         f"{smp['cg_iters_sampled'][0]}, 5 and {smp['cg_iters_sampled'][1]} iterations "
+                         f"(set-up {smp['setup_s']:.2f} s, {smp['s_per_cg_iter']:.3f} s per iteration), "
+                         f"extrapolated to the full oracle solves' {smp['cg_iters_full']} iterations"}
     print(json.dumps({
         "metric": "implicit viscous solves/s (u, v, w each a solve) at %d^3, tol 1e-10" % args.n,
         "value": 3.0 / (ms * 1e-3), "unit": "solves/s", "ms_per_step": ms, "steps": args.steps,
@@ -511,7 +571,7 @@ def run_viscous(args):
         "iteration_roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                                "frac": gbs / hbm, "peak_kind": kind,
                                "note": "whole iterations incl. the host read of the norms"},
-        "clocks": clk.summary(),
+        "clocks": clk.summary(), "cpu_baseline": cpu,
         "config": {"workload": workload_config(args.n)["workload"] + ", mu 1e-3/1.8e-5",
                    "l2": "no flush: each iteration streams 7 vectors of one component (> 129 MB L2)"}}))
 

@@ -136,17 +136,27 @@ def spd_operator(grid, comp, nu, tau):
     return (sp.diags(d) - laplacian(grid, comp)).tocsr()
 
 
-def solve(grid, comp, nu, tau, un, tol=1e-13, max_iter=100000):
+def solve(grid, comp, nu, tau, un, tol=1e-13, max_iter=100000, stats=None):
     """u* of Eq. muelliptic for component `comp`: `un` and the result are arrays
-    of the unknowns (unknown_shape).  tau = 0 returns u^n."""
+    of the unknowns (unknown_shape).  tau = 0 returns u^n.  `stats` (a dict,
+    optional) receives the number of CG iterations under "iters"."""
     un = np.asarray(un, dtype=np.float64)
     if tau == 0.0:
+        if stats is not None:
+            stats["iters"] = 0
         return un.copy()
     A = spd_operator(grid, comp, nu, tau)
     b = (un / (tau * np.asarray(nu, dtype=np.float64))).ravel()
-    x, info = spla.cg(A, b, x0=un.ravel().copy(), rtol=tol, atol=0.0, maxiter=max_iter)
+    count = [0]
+
+    def tick(_xk):
+        count[0] += 1
+
+    x, info = spla.cg(A, b, x0=un.ravel().copy(), rtol=tol, atol=0.0, maxiter=max_iter, callback=tick)
     if info != 0:
         raise RuntimeError(f"viscous CG did not converge (info {info})")
+    if stats is not None:
+        stats["iters"] = count[0]
     return x.reshape(un.shape)
 
 

@@ -10,6 +10,10 @@ number here stays below 1e3, so residuals of 1e-12 bound the error near 1e-9.
 Wall faces of the component are filled with NaN on input (never read) and must
 come back 0.
 """
+import hashlib
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -19,6 +23,7 @@ from oracle import viscous as V
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+HERE = os.path.dirname(os.path.abspath(__file__))
 P, W = pi.PERIODIC, pi.WALL
 MU1, MU2, RHO1, RHO2 = 1.0e-3, 1.8e-5, 1000.0, 1.2  # water-like and air-like phases
 
@@ -175,3 +180,39 @@ def test_viscous_errors(paris):
         assert s == 3 and st.iters == 2 and st.converged == 0
         assert lib.paris_face_viscosity(p, 0, ptr(dev(pr.C)), 0.0, MU2, RHO1, RHO2, ptr(us)) == 1
         assert lib.paris_face_viscosity(p, -1, ptr(dev(pr.C)), MU1, MU2, RHO1, RHO2, ptr(us)) == 1
+
+
+def test_viscous_fullsize_sampled(paris):
+    """256^3 drop field in the configuration `bench.py --viscous` times: u* of
+    each component at 2048 seeded unknowns against a stored full oracle solve
+    (golden/viscous256_drops.json, written by make_viscous256_golden.py from the
+    oracle alone).  Bar: the SPD form is a strictly diagonally dominant matrix
+    whose rows exceed their off-diagonal sums by 1/(tau nu), so (Varah)
+    ||A^-1||_inf <= tau max nu and ||u* - u*_oracle||_inf <= tau max nu
+    (||r_gpu||_inf + ||r_oracle||_inf): the GPU's stopping test bounds its
+    residual by 1e-10 ||b||_inf, the golden file records the oracle's."""
+    path = os.path.join(HERE, "golden", "viscous256_drops.json")
+    if not os.path.exists(path):
+        pytest.skip("golden/viscous256_drops.json not generated")
+    with open(path) as fh:
+        gold = json.load(fh)
+    pr = pi.config2(n=256)
+    assert hashlib.sha256(np.ascontiguousarray(pr.C).tobytes()).hexdigest() == gold["C_sha256"]
+    g = pr.grid
+    tau = gold["tau"]
+    with paris.Context(g) as ctx:
+        C = dev(pr.C)
+        nus = [ctx.face_viscosity(c, C, gold["mu1"], gold["mu2"], pr.rho1, pr.rho2) for c in range(3)]
+        numax = max(float(nu.max()) for nu in nus)
+        assert abs(gold["tau_nu_over_h2"] * g.h ** 2 / numax - tau) <= 1e-15 * tau
+        for c in range(3):
+            un = (pr.u, pr.v, pr.w)[c]
+            us, st = ctx.viscous_solve(c, nus[c], tau, dev(un), tol=1e-10)
+            assert st["converged"] == 1 and st["rel_res_l2"] <= 1e-10 and st["rel_res_linf"] <= 1e-10
+            x = V.interior(g, c, host(us)).ravel()
+            nu = V.interior(g, c, host(nus[c]))
+            binf = np.abs(V.interior(g, c, un) / (tau * nu)).max()
+            rec = gold["components"][c]
+            bound = tau * nu.max() * (1e-10 + rec["rel_res_linf"]) * binf + 1e-14 * rec["x_max_abs"]
+            err = np.abs(x[rec["unknowns"]] - np.asarray(rec["x"])).max()
+            assert err <= bound, (c, err, bound)
