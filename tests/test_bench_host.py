@@ -63,3 +63,13 @@ def test_traffic_record_points_at_a_kernel_source():
         assert cls in ("smooth0", "restrict0", "prolong0", "matvec0", "resid64")
         assert rec["bytes_per_launch"] > 0
         assert len(bench.kernel_source_sha(rec["source"])) == 16
+
+
+def test_viscous_oracle_sample_extrapolates_to_the_stored_counts():
+    import paris_inputs as pi
+    pr = pi.config2(n=16)
+    s = bench.viscous_oracle_sample(pr, 0.05, {"components": [{"iters": 10}, {"iters": 20}, {"iters": 30}]})
+    assert s["cg_iters_full"] == [10, 20, 30] and s["cg_iters_sampled"][0] == 1
+    assert s["cg_iters_sampled"][1] >= 9 and s["s_per_cg_iter"] >= 0.0 and s["setup_s"] >= 0.0
+    assert s["step_s"] >= 3 * s["setup_s"] + 60 * s["s_per_cg_iter"]
+    assert bench.viscous_oracle_sample(pr, 0.01, None)["cg_iters_full"] == [100, 100, 100]

@@ -170,3 +170,43 @@ def test_manufactured_solution_converges_at_second_order():
         errs.append(np.max(np.abs(us - u)))
     r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
     assert 3.4 < r1 < 4.6 and 3.4 < r2 < 4.6, errs
+
+
+def test_solve_reports_its_iterations():
+    grid = pi.Grid(8, 6, 4, 0.125, (P, W, P))
+    nu = np.full(V.unknown_shape(grid, 1), 1e-2)
+    un = np.random.default_rng(6).standard_normal(nu.shape)
+    info = {}
+    V.solve(grid, 1, nu, 0.1, un, stats=info)
+    assert info["iters"] >= 1
+    V.solve(grid, 1, nu, 0.0, un, stats=info)
+    assert info["iters"] == 0
+
+
+def test_viscous_golden_matches_its_inputs():
+    """The stored 256^3 oracle solves (golden/viscous256_drops.json) belong to
+    the current input generator and parameters, converged, and obey the
+    discrete maximum-norm bound |u*| <= tau max(nu) max|u^n/(tau nu)| of a
+    strictly diagonally dominant SPD form with margin 1/(tau nu)."""
+    import hashlib
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "viscous256_drops.json")
+    if not os.path.exists(path):
+        pytest.skip("golden/viscous256_drops.json not generated")
+    with open(path) as fh:
+        gold = json.load(fh)
+    pr = pi.config2(n=256)
+    g = pr.grid
+    assert hashlib.sha256(np.ascontiguousarray(pr.C).tobytes()).hexdigest() == gold["C_sha256"]
+    nus = [V.face_nu(g, c, pr.C, gold["mu1"], gold["mu2"], pr.rho1, pr.rho2) for c in range(3)]
+    tau = gold["tau_nu_over_h2"] * g.h ** 2 / max(float(nu.max()) for nu in nus)
+    assert tau == gold["tau"]
+    for c, rec in enumerate(gold["components"]):
+        n = int(np.prod(V.unknown_shape(g, c)))
+        assert rec["rel_res_l2"] <= 1e-12 and rec["rel_res_linf"] <= 1e-12 and rec["iters"] > 0
+        idx = np.asarray(rec["unknowns"])
+        assert idx.min() >= 0 and idx.max() < n and len(rec["x"]) == len(idx)
+        un = V.interior(g, c, (pr.u, pr.v, pr.w)[c])
+        bound = tau * nus[c].max() * np.abs(un / (tau * nus[c])).max()
+        assert np.abs(rec["x"]).max() <= rec["x_max_abs"] <= bound * (1 + 1e-12)
