@@ -324,8 +324,10 @@ static double max_abs(int64_t n, const double* a) {
 
 /* Unpreconditioned conjugate gradients for A x = rhs with A = -L symmetric
  * positive semi-definite and rhs mean-free (so the system is consistent).
- * x holds the initial guess on entry.  The textbook recurrence runs unchanged;
- * every `check` iterations, and whenever the recurrence residual reaches tol,
+ * x holds the initial guess on entry.  The textbook recurrence runs with one
+ * addition: after every update the residual r is projected to mean zero, i.e.
+ * kept orthogonal to the null space (the constants), where the consistent
+ * system's residual lies in exact arithmetic.  Every `check` iterations, and whenever the recurrence residual reaches tol,
  * x is projected to mean zero and the TRUE residual rhs - A x is computed.
  * The solve stops when ||rhs - A x||_2/||rhs||_2 <= tol.  If the recurrence
  * has converged but the true residual has not, CG restarts from the true
@@ -358,7 +360,9 @@ void oracle_cg(const or_csr* A, const double* rhs, double* x, double tol, int ma
     oracle_remove_mean(n, x);
     oracle_csr_matvec(A, x, q);
     #pragma omp parallel for schedule(static)
-    for (int64_t c = 0; c < n; ++c) { r[c] = rhs[c] - q[c]; d[c] = r[c]; }
+    for (int64_t c = 0; c < n; ++c) r[c] = rhs[c] - q[c];
+    oracle_remove_mean(n, r);
+    memcpy(d, r, sizeof(double) * n);
     double rr = det_dot(n, r, r);
     if (sqrt(rr) / bnorm > tol) {
         while (it < max_iter) {
@@ -368,6 +372,10 @@ void oracle_cg(const or_csr* A, const double* rhs, double* x, double tol, int ma
             double alpha = rr / dq;
             #pragma omp parallel for schedule(static)
             for (int64_t c = 0; c < n; ++c) { x[c] += alpha * d[c]; r[c] -= alpha * q[c]; }
+            /* keep the residual in the range of A (mean-free): the rounding of A d
+             * leaves a constant part in r that A cannot remove, and over many steps
+             * it grows until d . A d is no longer positive */
+            oracle_remove_mean(n, r);
             double rr_new = det_dot(n, r, r);
             double beta = rr_new / rr;
             if (coef && first_cycle && ncoef < max_coef) {
@@ -395,7 +403,9 @@ void oracle_cg(const or_csr* A, const double* rhs, double* x, double tol, int ma
                     at_restart = true_rel < at_restart ? true_rel : at_restart;
                     first_cycle = 0;
                     #pragma omp parallel for schedule(static)
-                    for (int64_t c = 0; c < n; ++c) { r[c] = t[c]; d[c] = t[c]; }
+                    for (int64_t c = 0; c < n; ++c) r[c] = t[c];
+                    oracle_remove_mean(n, r);
+                    memcpy(d, r, sizeof(double) * n);
                     rr = det_dot(n, r, r);
                 }
             }
