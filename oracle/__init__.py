@@ -17,7 +17,8 @@ Every function follows a passage of the PARIS paper (arXiv 2012.11744):
   counterpart; pinned against central finite differences in the tests)
 
 The implicit viscous step of Sec. 3.2.3 (Eq. muelliptic) is in ``viscous.py``
-(numpy and scipy.sparse, FP64).
+(numpy and scipy.sparse, FP64); the capillary (Eq. csf2) and gravity forcing
+of the predictor (Eq. nonconspredictedvel) in ``forcing.py`` (numpy, FP64).
 """
 from __future__ import annotations
 
