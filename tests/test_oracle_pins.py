@@ -387,6 +387,30 @@ def test_lanczos_extremes_match_dense_eigenvalues():
     assert abs(lmin - ev[1]) <= 0.05 * ev[1]
 
 
+@pytest.mark.parametrize("rho1", [10.0, 1000.0])
+def test_cg_on_layered_density_reaches_the_fp64_floor(rho1):
+    """Heavy fluid below a flat interface, walls in z, and the right-hand side
+    of a uniform vertical acceleration (a source in the bottom layer, a sink
+    in the top one): the CG either meets its tolerance or reports stagnation
+    at the FP64 floor (relative residual <= 1e-10 here), and the returned
+    residual is the true one.  Without its residual kept mean-free the CG
+    stopped at 1e-5 to 1e-2 on these systems with neither flag set."""
+    nz, h = 32, 1.0 / 32
+    grid = pi.Grid(8, 6, nz, h, (P, P, W))
+    zc = (np.arange(nz) + 0.5) * h
+    frac = np.clip((0.41 - (zc - h / 2)) / h, 0.0, 1.0)
+    C = np.broadcast_to(frac[:, None, None], grid.shape).copy()
+    beta = oracle.face_coeffs(grid, C, rho1, 1.2)
+    op = oracle.Operator(grid, *beta)
+    b = np.zeros(grid.shape)
+    b[0], b[-1] = 1.0 / h, -1.0 / h
+    res = oracle.cg(op, b, tol=1e-13)
+    assert res.rel_res_l2 <= 1e-13 or res.stagnated
+    assert res.rel_res_l2 <= 1e-10
+    r = b.ravel() - op.apply(res.x).ravel()
+    assert abs(np.linalg.norm(r) / np.linalg.norm(b) - res.rel_res_l2) <= 1e-3 * res.rel_res_l2 + 1e-16
+
+
 def test_cg_zero_rhs():
     grid = pi.Grid(4, 4, 4, 0.25)
     op = oracle.Operator(grid, *_rand_beta(grid, 0))
