@@ -45,11 +45,14 @@ def test_hand_computed_face_values():
 def test_predictor_adds_tau_a_and_zeroes_walls():
     grid = pi.Grid(5, 4, 3, 0.2, (W, P, W))
     pr = pi.random_problem(grid, seed=21)
+    un = [x.copy() for x in (pr.u, pr.v, pr.w)]
+    un[0][:, :, 0] = un[0][:, :, -1] = 5.0  # u^n on the wall faces is not carried over
+    un[2][0] = un[2][-1] = -5.0
     kappa = pi.random_field(grid.shape, seed=22, mean_free=False)
     acc = F.face_acceleration(grid, pr.C, kappa, 0.07, (0.0, -1.0, 2.0), pr.rho1, pr.rho2)
-    us = F.predictor(grid, pr.u, pr.v, pr.w, pr.C, kappa, 0.07, (0.0, -1.0, 2.0), pr.rho1, pr.rho2, 0.01)
+    us = F.predictor(grid, *un, pr.C, kappa, 0.07, (0.0, -1.0, 2.0), pr.rho1, pr.rho2, 0.01)
     for axis in range(3):
-        want = (pr.u, pr.v, pr.w)[axis] + 0.01 * acc[axis]
+        want = un[axis] + 0.01 * acc[axis]
         if grid.bc[axis] == W:
             sl = [slice(None)] * 3
             for end in (0, -1):
