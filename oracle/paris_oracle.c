@@ -334,11 +334,17 @@ static double max_abs(int64_t n, const double* a) {
  * residual.  The solve also stops (flagged "stagnated") when the true residual
  * has not halved over the last OR_STALL checks or after OR_MAX_RESTARTS
  * restarts without halving it: rounding then limits the attainable accuracy.
+ * A stall counts only once the true residual is at most OR_STALL_FLOOR
+ * relative: the FP64 floor of these systems lies far below it, while the
+ * residual of unpreconditioned CG (which minimises the A-norm of the error,
+ * not the residual) can sit on a plateau, or rise, for thousands of steps
+ * before it falls on strongly layered densities.
  * The CG step lengths alpha_k and ratios beta_k of the first cycle are stored
  * in coef[2k], coef[2k+1] (up to max_coef pairs): they define the Lanczos
  * tridiagonal matrix whose eigenvalues estimate the extreme eigenvalues of A. */
 #define OR_STALL 20
 #define OR_MAX_RESTARTS 3
+#define OR_STALL_FLOOR 1e-8
 void oracle_cg(const or_csr* A, const double* rhs, double* x, double tol, int max_iter,
                int check, double* coef, int max_coef, or_cg_stats* st) {
     int64_t n = A->n;
@@ -394,7 +400,10 @@ void oracle_cg(const or_csr* A, const double* rhs, double* x, double tol, int ma
                 double true_rel = sqrt(det_dot(n, t, t)) / bnorm;
                 if (true_rel <= tol) break;
                 /* hist[nhist % OR_STALL] holds the value of OR_STALL checks ago */
-                if (nhist >= OR_STALL && true_rel > 0.5 * hist[nhist % OR_STALL]) { stag = 1; break; }
+                if (nhist >= OR_STALL && true_rel <= OR_STALL_FLOOR && true_rel > 0.5 * hist[nhist % OR_STALL]) {
+                    stag = 1;
+                    break;
+                }
                 hist[nhist % OR_STALL] = true_rel;
                 ++nhist;
                 if (rec_done) {

@@ -437,3 +437,51 @@ def random_field(shape, seed: int, mean_free: bool = True) -> np.ndarray:
     if mean_free:
         f -= f.mean()
     return f
+
+
+def layered_problem(grid: Grid, z_frac: float = 0.41, rho1: float = 1000.0, rho2: float = 1.2,
+                    dt: float = 1e-3, g_z: float = -9.81, noise: float = 0.0, seed: int = 0) -> Problem:
+    """Fluid 1 below the flat plane z = z_frac * L_z, fluid 2 above (walls in z
+    expected), C the exact fraction of each cell below the plane.  u* = dt g_z
+    on every z-face off the walls (the predictor's uniform gravity from rest),
+    plus U[-noise, noise] on every component; wall-normal velocity zero."""
+    h = grid.h
+    zi = z_frac * grid.nz * h
+    zlo = np.arange(grid.nz) * h
+    frac = np.clip((zi - zlo) / h, 0.0, 1.0)
+    C = np.broadcast_to(frac[:, None, None], grid.shape).copy()
+    u = np.zeros(grid.face_shape(0))
+    v = np.zeros(grid.face_shape(1))
+    w = np.full(grid.face_shape(2), dt * g_z)
+    if noise > 0.0:
+        rng = np.random.default_rng([500, seed])
+        u += rng.uniform(-noise, noise, size=u.shape)
+        v += rng.uniform(-noise, noise, size=v.shape)
+        w += rng.uniform(-noise, noise, size=w.shape)
+    zero_wall_faces(grid, u, v, w)
+    return Problem(f"layered{grid.nx}x{grid.ny}x{grid.nz}", grid, C, u, v, w, rho1=rho1, rho2=rho2, dt=dt,
+                   extra={"z_interface": zi, "g_z": g_z})
+
+
+def drop_curvature(grid: Grid, spheres) -> np.ndarray:
+    """Cell curvature field of a set of spheres of fluid 1: kappa = -2/r of
+    the sphere whose surface is nearest to the cell centre (minimum image on
+    periodic axes), the sign that makes a sphere of fluid 1 of radius r carry
+    the Laplace jump 2 sigma / r.  Only its values next to interfaces enter
+    the capillary force; elsewhere grad C = 0."""
+    L = grid.lengths
+    c = [(np.arange(n) + 0.5) * grid.h for n in (grid.nx, grid.ny, grid.nz)]
+    best = np.full(grid.shape, np.inf)
+    kappa = np.zeros(grid.shape)
+    for centre, r in spheres:
+        d2 = np.zeros(grid.shape)
+        for a, ax in ((0, (None, None, slice(None))), (1, (None, slice(None), None)), (2, (slice(None), None, None))):
+            d = c[a] - centre[a]
+            if grid.bc[a] == PERIODIC:
+                d = d - L[a] * np.round(d / L[a])
+            d2 = d2 + (d * d)[ax]
+        dist = np.abs(np.sqrt(d2) - r)
+        closer = dist < best
+        best[closer] = dist[closer]
+        kappa[closer] = -2.0 / r
+    return kappa

@@ -411,6 +411,26 @@ def test_cg_on_layered_density_reaches_the_fp64_floor(rho1):
     assert abs(np.linalg.norm(r) / np.linalg.norm(b) - res.rel_res_l2) <= 1e-3 * res.rel_res_l2 + 1e-16
 
 
+@pytest.mark.parametrize("grid", [pi.Grid(16, 16, 64, 1 / 16, (P, P, W)), pi.Grid(32, 32, 128, 1 / 32, (P, P, W))],
+                         ids=["16x16x64", "32x32x128"])
+def test_projection_from_rest_is_hydrostatic(grid):
+    """Heavy fluid (1000) under light (1.2), walls in z, u* = dt g on the
+    z-faces: the exact discrete answer is u = 0 with p_{k+1} - p_k = g h rho_f
+    (rho_f the mean of the two cells), a closed form independent of the CG.
+    Catches a CG that stops on the residual plateau of unpreconditioned CG
+    (the 128-plane case stopped at relative residual 4 when a stall was
+    declared at any residual level) and a wrong face density."""
+    pr = pi.layered_problem(grid)
+    ref = oracle.projection_step(grid, pr.C, pr.rho1, pr.rho2, pr.dt, pr.u, pr.v, pr.w)
+    rho = pr.rho2 + (pr.rho1 - pr.rho2) * pr.C[:, 0, 0]
+    dp = pr.extra["g_z"] * grid.h * 0.5 * (rho[1:] + rho[:-1])
+    pz = np.concatenate([[0.0], np.cumsum(dp)])
+    pe = np.broadcast_to(pz[:, None, None], grid.shape) - pz.mean()
+    assert np.abs(ref.p - pe).max() <= 1e-9 * np.abs(pe).max()
+    assert max(np.abs(x).max() for x in ref.u) <= 1e-9 * abs(pr.dt * pr.extra["g_z"])
+    assert ref.cg.rel_res_l2 <= 1e-9
+
+
 def test_cg_zero_rhs():
     grid = pi.Grid(4, 4, 4, 0.25)
     op = oracle.Operator(grid, *_rand_beta(grid, 0))
