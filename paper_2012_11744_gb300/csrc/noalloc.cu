@@ -22,7 +22,7 @@ using paris::Geo;
 
 constexpr int kTX = 32, kTY = 8, kTZ = 8;  // one block covers a 32 x 8 x 8 box of cells
 constexpr int kMaxBlocks = 16384;          // 512 x 256 x 256 cells at most (16 x 32 x 32 blocks)
-constexpr int kNV = 3;                     // partials per block: sum, max |b|, non-finite count
+constexpr int kNV = 1;                     // partials per block: the sum of b
 
 // Shared scratch of every call on this device: block partials, then the
 // finalized mean.  Each call overwrites all of it before reading it.
@@ -31,22 +31,29 @@ static __device__ __align__(256) double g_noalloc_scratch[kNV * kMaxBlocks + 8];
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 double* g_scratch_addr[kMaxDevices] = {nullptr};
+int g_sms[kMaxDevices] = {0};
 
-// Address of the scratch array on the current device, looked up once per
-// device (the array's host-side name is not a device address).
-cudaError_t scratch_on_current_device(double** out) {
+// Address of the scratch array on the current device and that device's SM
+// count, looked up once per device with the device current (the array's
+// host-side name is not a device address).
+cudaError_t scratch_on_current_device(double** out, int* sms) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_mutex);
     if (!g_scratch_addr[dev]) {
+        int n = 0;
+        e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
+        g_sms[dev] = n > 0 ? n : 1;
         g_scratch_addr[dev] = (double*)p;
     }
     *out = g_scratch_addr[dev];
+    *sms = g_sms[dev];
     return cudaSuccess;
 }
 
@@ -71,18 +78,16 @@ __global__ void __launch_bounds__(kTX* kTY)
                        double* scratch) {
     const int i = blockIdx.x * kTX + threadIdx.x;
     const int j = blockIdx.y * kTY + threadIdx.y;
-    double acc[kNV] = {0.0, 0.0, 0.0};
+    double acc[kNV] = {0.0};
     if (i < g.nx && j < g.ny) {
         const int k0 = blockIdx.z * kTZ, k1 = min(k0 + kTZ, g.nz);
         for (int k = k0; k < k1; ++k) {
             double b = div_at(g, u, v, w, i, j, k) * inv_hdt;
             rhs[g.cidx(i, j, k)] = b;
             acc[0] += b;
-            acc[1] = fmax(acc[1], fabs(b));
-            acc[2] += isfinite(b) ? 0.0 : 1.0;
         }
     }
-    const int op[kNV] = {0, 1, 0};
+    const int op[kNV] = {0};
     const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     paris::block_reduce_store<kNV>(acc, op, scratch, blk, threadIdx.y * kTX + threadIdx.x);
 }
@@ -124,8 +129,14 @@ extern "C" paris_status paris_divergence_noalloc(const paris_grid* g, const doub
     const dim3 grid((g->nx + kTX - 1) / kTX, (g->ny + kTY - 1) / kTY, (g->nz + kTZ - 1) / kTZ);
     const int64_t nblocks = (int64_t)grid.x * grid.y * grid.z;
     if (nblocks > kMaxBlocks) return PARIS_ERR_INVALID_ARG;  // beyond the fixed scratch
+    // an error left pending by an unrelated earlier call is not this call's:
+    // consume it; one that persists (a sticky error) means the device context
+    // is unusable, and nothing is enqueued
+    cudaGetLastError();
+    if (cudaPeekAtLastError() != cudaSuccess) return PARIS_ERR_CUDA;
     double* scratch = nullptr;
-    if (scratch_on_current_device(&scratch) != cudaSuccess) return PARIS_ERR_CUDA;
+    int sms = 1;
+    if (scratch_on_current_device(&scratch, &sms) != cudaSuccess) return PARIS_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
     const Geo geo{g->nx, g->ny, g->nz, g->bc[0] == PARIS_WALL, g->bc[1] == PARIS_WALL,
                   g->bc[2] == PARIS_WALL};
@@ -134,7 +145,7 @@ extern "C" paris_status paris_divergence_noalloc(const paris_grid* g, const doub
                                                           mean_removed);
     const int64_t n = geo.ncell();
     int64_t nb = (n + 255) / 256;
-    if (nb > 152 * 8) nb = 152 * 8;
+    if (nb > (int64_t)sms * 8) nb = (int64_t)sms * 8;  // 8 resident 256-thread blocks per SM
     noalloc_sub_mean_kernel<<<(int)nb, 256, 0, st>>>(n, rhs, scratch);
     return cudaGetLastError() == cudaSuccess ? PARIS_OK : PARIS_ERR_CUDA;
 }
