@@ -109,12 +109,15 @@ typedef struct {
                              the smoother is PARIS_SMOOTH_RBGS_2PASS and half_coefficients is
                              0; otherwise ignored.  The FP64 residual, the converged p and
                              the projection keep the FP64 beta (1) */
-    int level0_tiles;     /* with level0_density: the finest level's colour passes, inner CG
-                             product and residual restriction run on plane tiles, two pairs
-                             of cells per thread, when nx/2 is even (1), or always on the
-                             kernels that walk z-columns one pair per thread (0).  The colour
-                             passes give identical results; the product's dot products differ
-                             in summation order only (1) */
+    int level0_tiles;     /* with level0_density: the finest level's colour passes run on
+                             plane tiles staged in shared memory by bulk asynchronous (TMA)
+                             copies when nx is a multiple of 8 and ny of 8 (2), or on plane
+                             tiles read straight into registers, two pairs of cells per
+                             thread, when nx/2 is even (1); the inner CG product and the
+                             residual restriction run on the register plane tiles for 1 and
+                             2.  0: always the kernels that walk z-columns one pair per
+                             thread.  The colour passes give identical results in all three;
+                             the product's dot products differ in summation order only (1) */
 } paris_opts;
 
 typedef struct {
@@ -170,13 +173,20 @@ paris_status paris_divergence(paris_ctx* ctx, const double* u, const double* v, 
  * (cells, output) and mean_removed (one double, output, may be NULL) are
  * DEVICE pointers owned by the caller; work is enqueued on `stream` and the
  * call returns without synchronising.  No device memory is allocated: the
- * block partial sums live in one static device array of 384 KB (16384 blocks
+ * block partial sums live in one static device array of 128 KB (16384 blocks
  * of 32x8x8 cells) that every GPU loading the library holds until the process
  * exits.  Grids needing more blocks than that (beyond 512x256x256 cells, i.e.
  * ceil(nx/32)*ceil(ny/8)*ceil(nz/8) > 16384) are rejected with
  * PARIS_ERR_INVALID_ARG before any work is enqueued.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  Every call
+ * device current; make that first call before any stream capture.  The
+ * address is kept for the life of the process: after cudaDeviceReset (or any
+ * other teardown of the device's primary context) it is stale, so this entry
+ * point must not be called again in that process.  An error left pending by
+ * an unrelated earlier CUDA call is cleared on entry; one that persists (a
+ * sticky error of the device context) is returned as PARIS_ERR_CUDA before
+ * anything is enqueued.  The call does not synchronise, so it reports launch
+ * errors only; a NaN or Inf in u, v or w passes into rhs.  Every call
  * overwrites the whole scratch it reads, so nothing needs clearing, but all
  * calls share the one array: calls that overlap on the GPU (other streams,
  * other threads) race and must be serialised by the caller. */
@@ -248,6 +258,42 @@ paris_status paris_face_coeffs_adjoint(paris_ctx* ctx, double rho1, double rho2,
                                        const double* beta_x, const double* beta_y,
                                        const double* beta_z, const double* gbeta_x,
                                        const double* gbeta_y, const double* gbeta_z, double* gC);
+
+/* ---------------------------------------------------------------------------
+ * PREDICTOR FORCING (Sec. 3.2, Eq. nonconspredictedvel; Sec. 3.6.1, Eq. csf2).
+ * The capillary force in CSF form, -sigma kappa grad^h C, and gravity enter
+ * the predictor as an acceleration on the faces.  On every face that is not
+ * a wall face, between cells L and R along its axis a,
+ *   a_f = g_a - (sigma/h) kappa_f (C_R - C_L) beta_f,   kappa_f = (kappa_L + kappa_R)/2,
+ * beta_f = 2/(rho_L + rho_R) the face coefficient of paris_face_coeffs (rho
+ * from Eq. muH), and u*_f = u^n_f + tau a_f; wall faces get u* = 0.  Because
+ * a_f uses the projection's own beta_f, a constant kappa gives a discrete
+ * gradient that the projection removes exactly (to rounding): the balance of
+ * a drop at rest (Laplace pressure) and of fluid layers at rest
+ * (hydrostatic pressure) is kept.  kappa follows the sign convention in
+ * which a sphere of fluid 1 (C = 1) of radius R has kappa = -2/R.  The
+ * advection and viscous terms of the predictor are not part of this call
+ * (the viscous one is paris_viscous_solve). */
+
+/* u, v, w (in u^n, out u*, in place) and beta_x/y/z (out, as
+ * paris_face_coeffs) in one pass over the faces.  C, kappa: cells (kappa may
+ * be NULL: kappa = 0, gravity only).  sigma >= 0, g = (gx, gy, gz) and
+ * tau >= 0 finite.  Asynchronous.
+ * Errors: INVALID_ARG (null pointer, rho <= 0, sigma < 0, a non-finite
+ * sigma, g or tau, tau < 0). */
+paris_status paris_predictor_forcing(paris_ctx* ctx, const double* C, const double* kappa, double rho1,
+                                     double rho2, double sigma, double gx, double gy, double gz,
+                                     double tau, double* u, double* v, double* w, double* beta_x,
+                                     double* beta_y, double* beta_z);
+
+/* The forcing above with tau = dt, then the projection step: u, v, w in:
+ * u^n, out: u^{n+1} = P(u^n + dt a); p in: initial guess, out: the pressure.
+ * Fused: the forcing is applied by the face-coefficient pass of the step.
+ * Errors: as paris_projection_step and paris_predictor_forcing. */
+paris_status paris_projection_step_forced(paris_ctx* ctx, const double* C, const double* kappa,
+                                          double rho1, double rho2, double sigma, double gx, double gy,
+                                          double gz, double dt, double* u, double* v, double* w, double* p,
+                                          paris_stats* st);
 
 /* ---------------------------------------------------------------------------
  * IMPLICIT VISCOUS STEP (Sec. 3.2.3, Eq. muelliptic).  For one velocity

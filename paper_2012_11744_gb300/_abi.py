@@ -85,6 +85,9 @@ SIGNATURES = {
     "paris_project_adjoint": (ct.c_int, [_P, _P, _P, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P, _P,
                                          _P, _P, ct.POINTER(Stats)]),
     "paris_face_coeffs_adjoint": (ct.c_int, [_P, _D, _D, _P, _P, _P, _P, _P, _P, _P]),
+    "paris_predictor_forcing": (ct.c_int, [_P, _P, _P, _D, _D, _D, _D, _D, _D, _D, _P, _P, _P, _P, _P, _P]),
+    "paris_projection_step_forced": (ct.c_int, [_P, _P, _P, _D, _D, _D, _D, _D, _D, _D, _P, _P, _P, _P,
+                                                ct.POINTER(Stats)]),
     "paris_face_viscosity": (ct.c_int, [_P, ct.c_int, _P, _D, _D, _D, _D, _P]),
     "paris_viscous_solve": (ct.c_int, [_P, ct.c_int, _P, _D, _P, _P, _D, ct.c_int, ct.POINTER(Stats)]),
     "paris_batch_create": (ct.c_int, [ct.POINTER(_P), ct.c_int, ct.POINTER(Grid), ct.POINTER(Opts), _P]),

@@ -220,6 +220,44 @@ class Context:
         d["status"] = s
         return d
 
+    def predictor_forcing(self, C, kappa, rho1, rho2, sigma, gravity, tau, u, v, w, beta=None):
+        """Capillary (CSF) and gravity forcing of the predictor: u, v, w (in
+        u^n, out u* = u^n + tau a_f) in place; returns the face coefficients
+        (written to ``beta`` when given).  kappa may be None (0)."""
+        g = self.grid
+        bx, by, bz = beta if beta is not None else self.empty_faces()
+        kp = ct.c_void_p(None) if kappa is None else self._t(kappa, g.shape, "kappa")
+        gx, gy, gz = (float(x) for x in gravity)
+        _abi.check(self.lib.paris_predictor_forcing(self._ptr, self._t(C, g.shape, "C"), kp, float(rho1),
+                                                    float(rho2), float(sigma), gx, gy, gz, float(tau),
+                                                    self._t(u, g.face_shape(0), "u"),
+                                                    self._t(v, g.face_shape(1), "v"),
+                                                    self._t(w, g.face_shape(2), "w"),
+                                                    self._t(bx, g.face_shape(0), "beta_x"),
+                                                    self._t(by, g.face_shape(1), "beta_y"),
+                                                    self._t(bz, g.face_shape(2), "beta_z")),
+                   "paris_predictor_forcing")
+        return bx, by, bz
+
+    def projection_step_forced(self, C, kappa, rho1, rho2, sigma, gravity, dt, u, v, w, p, check=True):
+        """Forcing (tau = dt) fused into the projection step: u, v, w in u^n,
+        out u^{n+1}; p in: initial guess, out: the pressure."""
+        g = self.grid
+        st = _abi.Stats()
+        kp = ct.c_void_p(None) if kappa is None else self._t(kappa, g.shape, "kappa")
+        gx, gy, gz = (float(x) for x in gravity)
+        s = self.lib.paris_projection_step_forced(self._ptr, self._t(C, g.shape, "C"), kp, float(rho1),
+                                                  float(rho2), float(sigma), gx, gy, gz, float(dt),
+                                                  self._t(u, g.face_shape(0), "u"),
+                                                  self._t(v, g.face_shape(1), "v"),
+                                                  self._t(w, g.face_shape(2), "w"),
+                                                  self._t(p, g.shape, "p"), ct.byref(st))
+        if check:
+            _abi.check(s, "paris_projection_step_forced", st.as_dict())
+        d = st.as_dict()
+        d["status"] = s
+        return d
+
     def projection_step_host(self, C, rho1, rho2, dt, u, v, w, p, check=True):
         """The four steps on HOST arrays (numpy float64 or CPU torch tensors,
         ideally pinned); u, v, w, p updated in place."""

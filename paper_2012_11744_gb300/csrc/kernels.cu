@@ -97,9 +97,27 @@ inline bool fits_i32(const Geo& g) {
     return g.nface(0) < big && g.nface(1) < big && g.nface(2) < big;
 }
 
+int device_sms() {
+    constexpr int kMaxDev = 64;
+    static std::atomic<int> cache[kMaxDev];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+        cudaGetLastError();
+        return 1;
+    }
+    int n = cache[dev].load(std::memory_order_relaxed);
+    if (n > 0) return n;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        return 1;
+    }
+    cache[dev].store(n, std::memory_order_relaxed);
+    return n;
+}
+
 int elementwise_blocks(int64_t n) {
     int64_t b = (n + kRedThreads - 1) / kRedThreads;
-    const int64_t cap = 152 * 8;  // 8 resident 256-thread blocks on each of the 152 SMs
+    const int64_t cap = (int64_t)device_sms() * 8;  // 8 resident 256-thread blocks per SM
     if (b > cap) b = cap;
     if (b < 1) b = 1;
     return (int)b;
@@ -163,14 +181,34 @@ constexpr int kFSeg = 16;  // planes per thread of the face-coefficient kernel
 // a register, the x- and y-neighbours' come through a shared-memory tile
 // whose halo row and column are evaluated by one warp each.  Optionally
 // writes the FP32 copy of rho/2 that the mixed solve's finest level reads.
+//
+// With FORCE (the predictor's capillary and gravity forcing, Eq.
+// nonconspredictedvel with the CSF term of Eq. csf2), the same pass also
+// writes u* = u^n + tau a_f in place on every face it owns, with
+//   a_f = g_a - (sigma/h) kappa_f (C_R - C_L) beta_f,  kappa_f = (kappa_L + kappa_R)/2,
+// beta_f the coefficient it has just formed (so a constant kappa gives
+// beta_f times a face gradient of -sigma kappa C: exactly what the projection
+// removes); wall faces get u* = 0.  C and kappa of the neighbours come
+// through shared-memory tiles like rh.
+struct ForceArgs {
+    const double* kappa;  // cells; null: kappa = 0
+    double s_over_h;      // sigma / h
+    double g[3];          // gravity (acceleration) per axis
+    double tau;           // time step of the predictor
+    double* u[3];         // face arrays: in u^n, out u*
+};
+
+template <bool FORCE>
 __global__ void __launch_bounds__(kTX* kTY) face_coeffs_kernel(Geo g, const double* __restrict__ C,
                                                               double r1h, double r2h,
                                                               double* __restrict__ bx,
                                                               double* __restrict__ by,
                                                               double* __restrict__ bz,
                                                               float* __restrict__ rh32,
-                                                              float2* __restrict__ rh2) {
+                                                              float2* __restrict__ rh2, ForceArgs fa) {
     __shared__ double sh[2][kTY + 1][kTX + 1];  // [plane parity][1 + row][1 + column]
+    __shared__ double shc[FORCE ? 2 : 1][kTY + 1][kTX + 1];  // C (FORCE)
+    __shared__ double shk[FORCE ? 2 : 1][kTY + 1][kTX + 1];  // kappa (FORCE)
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const int i = blockIdx.x * kTX + tx, j = blockIdx.y * kTY + ty;
@@ -179,6 +217,7 @@ __global__ void __launch_bounds__(kTX* kTY) face_coeffs_kernel(Geo g, const doub
     const int kb = blockIdx.z * kFSeg, ke = min(kb + kFSeg, nz);
     const int64_t pl = (int64_t)nx * ny;
     auto rho = [&](double c) { return fma(r1h, c, r2h * (1.0 - c)); };
+    auto kap = [&](int64_t c) { return fa.kappa ? fa.kappa[c] : 0.0; };
     // halo cells: row j0-1 (warp 0) and column i0-1 (lanes 0..7 of warp 1)
     const int i0 = blockIdx.x * kTX, j0 = blockIdx.y * kTY;
     const int hx = i0 > 0 ? i0 - 1 : nx - 1;  // periodic wrap (walls: beta 0, value unused)
@@ -186,24 +225,72 @@ __global__ void __launch_bounds__(kTX* kTY) face_coeffs_kernel(Geo g, const doub
     const int hrow = min(j0 + tx, ny - 1);       // row of the column-halo cell of lane tx
     const int hcol = min(i0 + tx, nx - 1);       // column of the row-halo cell of lane tx
     const bool xw = g.wx && i == 0, yw = g.wy && j == 0;
-    double rzm = rho(C[(int64_t)(kb > 0 ? kb - 1 : nz - 1) * pl + (int64_t)jc * nx + ic]);
+    const int64_t czm_at = (int64_t)(kb > 0 ? kb - 1 : nz - 1) * pl + (int64_t)jc * nx + ic;
+    double czm = C[czm_at];
+    double rzm = rho(czm);
+    double kzm = FORCE ? kap(czm_at) : 0.0;
     for (int k = kb; k < ke; ++k) {
         const int64_t plane = (int64_t)k * pl;
         const int64_t c = plane + (int64_t)jc * nx + ic;
-        const double rc = rho(C[c]);
+        const double cc = C[c];
+        const double rc = rho(cc);
         const int b = k & 1;
         sh[b][ty + 1][tx + 1] = rc;
-        if (ty == 0) sh[b][0][tx + 1] = rho(C[plane + (int64_t)hy * nx + hcol]);
-        if (ty == 1 && tx < kTY) sh[b][tx + 1][0] = rho(C[plane + (int64_t)hrow * nx + hx]);
+        const int64_t crow = plane + (int64_t)hy * nx + hcol, ccol = plane + (int64_t)hrow * nx + hx;
+        double kc = 0.0;
+        if (ty == 0) {
+            const double ch = C[crow];
+            sh[b][0][tx + 1] = rho(ch);
+            if (FORCE) {
+                shc[b][0][tx + 1] = ch;
+                shk[b][0][tx + 1] = kap(crow);
+            }
+        }
+        if (ty == 1 && tx < kTY) {
+            const double ch = C[ccol];
+            sh[b][tx + 1][0] = rho(ch);
+            if (FORCE) {
+                shc[b][tx + 1][0] = ch;
+                shk[b][tx + 1][0] = kap(ccol);
+            }
+        }
+        if (FORCE) {
+            kc = kap(c);
+            shc[b][ty + 1][tx + 1] = cc;
+            shk[b][ty + 1][tx + 1] = kc;
+        }
         __syncthreads();
         const double rxm = sh[b][ty + 1][tx], rym = sh[b][ty][tx + 1];
         if (in) {
-            bx[g.fx(i, j, k)] = xw ? 0.0 : recip64(rxm + rc);
-            by[g.fy(i, j, k)] = yw ? 0.0 : recip64(rym + rc);
-            bz[g.fz(i, j, k)] = (g.wz && k == 0) ? 0.0 : recip64(rzm + rc);
+            const double bxv = xw ? 0.0 : recip64(rxm + rc);
+            const double byv = yw ? 0.0 : recip64(rym + rc);
+            const bool zw = g.wz && k == 0;
+            const double bzv = zw ? 0.0 : recip64(rzm + rc);
+            const int64_t fxi = g.fx(i, j, k), fyi = g.fy(i, j, k), fzi = g.fz(i, j, k);
+            bx[fxi] = bxv;
+            by[fyi] = byv;
+            bz[fzi] = bzv;
             if (g.wx && i == nx - 1) bx[g.fx(nx, j, k)] = 0.0;
             if (g.wy && j == ny - 1) by[g.fy(i, ny, k)] = 0.0;
             if (g.wz && k == nz - 1) bz[g.fz(i, j, nz)] = 0.0;
+            if (FORCE) {
+                // u*_f = u^n_f + tau (g_a - (sigma/h) kappa_f (C_R - C_L) beta_f); 0 on walls
+                auto star = [&](double* u, int64_t f, bool wall, double cl, double kl, double bf, double ga) {
+                    if (wall) {
+                        u[f] = 0.0;
+                        return;
+                    }
+                    const double kf = 0.5 * (kl + kc);
+                    const double a = ga - fa.s_over_h * kf * (cc - cl) * bf;
+                    u[f] = fma(fa.tau, a, u[f]);
+                };
+                star(fa.u[0], fxi, xw, shc[b][ty + 1][tx], shk[b][ty + 1][tx], bxv, fa.g[0]);
+                star(fa.u[1], fyi, yw, shc[b][ty][tx + 1], shk[b][ty][tx + 1], byv, fa.g[1]);
+                star(fa.u[2], fzi, zw, czm, kzm, bzv, fa.g[2]);
+                if (g.wx && i == nx - 1) fa.u[0][g.fx(nx, j, k)] = 0.0;
+                if (g.wy && j == ny - 1) fa.u[1][g.fy(i, ny, k)] = 0.0;
+                if (g.wz && k == nz - 1) fa.u[2][g.fz(i, j, nz)] = 0.0;
+            }
             if (rh32) {
                 const float hi = d2f_scaled(rc, 0);
                 rh32[c] = hi;
@@ -212,14 +299,26 @@ __global__ void __launch_bounds__(kTX* kTY) face_coeffs_kernel(Geo g, const doub
             }
         }
         rzm = rc;
+        if (FORCE) {
+            czm = cc;
+            kzm = kc;
+        }
     }
 }
 
 void launch_face_coeffs(const Geo& g, const double* C, double rho1, double rho2, double* bx,
-                        double* by, double* bz, float* rh32, float2* rh2, cudaStream_t st) {
+                        double* by, double* bz, float* rh32, float2* rh2, cudaStream_t st,
+                        const Forcing* force) {
     dim3 gr((g.nx + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, (g.nz + kFSeg - 1) / kFSeg);
-    face_coeffs_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(g, C, 0.5 * rho1, 0.5 * rho2, bx, by, bz, rh32,
-                                                      rh2);
+    if (force) {
+        ForceArgs fa{force->kappa, force->sigma / force->h, {force->g[0], force->g[1], force->g[2]},
+                     force->tau, {force->u[0], force->u[1], force->u[2]}};
+        face_coeffs_kernel<true><<<gr, dim3(kTX, kTY), 0, st>>>(g, C, 0.5 * rho1, 0.5 * rho2, bx, by, bz, rh32,
+                                                                rh2, fa);
+    } else {
+        face_coeffs_kernel<false><<<gr, dim3(kTX, kTY), 0, st>>>(g, C, 0.5 * rho1, 0.5 * rho2, bx, by, bz, rh32,
+                                                                 rh2, ForceArgs{});
+    }
     count_launch();
 }
 
@@ -1290,13 +1389,37 @@ void launch_check_arithmetic(const double* v, int64_t n, int shift, unsigned lon
 
 // --------------------------------------------------- streaming probes ---
 
-// Reads a, b and c once (a.b + a.c per block, stored to o[block] so the
-// loads stay live): the rate of a read-only stream.
-__global__ void stream_read3_kernel(const float4* __restrict__ a, const float4* __restrict__ b,
-                                    const float4* __restrict__ c, float* __restrict__ o, int64_t nv) {
+// Reads a, b and c once: the rate of a read-only stream.  Each thread keeps
+// kReadUnroll independent 16-byte loads of every array in flight (12 loads
+// per iteration), so the grid holds enough bytes in flight to cover the
+// memory latency; the sum a.(b + c) per warp goes to o[warp] so that the
+// loads stay live.
+constexpr int kReadUnroll = 4;
+__global__ void __launch_bounds__(kRedThreads) stream_read3_kernel(const float4* __restrict__ a,
+                                                                   const float4* __restrict__ b,
+                                                                   const float4* __restrict__ c,
+                                                                   float* __restrict__ o, int64_t nv) {
     float s = 0.f;
-    PARIS_VEC_FOR(i, nv) {
-        const float4 x = a[i], y = b[i], z = c[i];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + (kReadUnroll - 1) * stride < nv; i += kReadUnroll * stride) {
+        float4 x[kReadUnroll], y[kReadUnroll], z[kReadUnroll];
+#pragma unroll
+        for (int u = 0; u < kReadUnroll; ++u) {
+            x[u] = __ldcs(a + i + u * stride);
+            y[u] = __ldcs(b + i + u * stride);
+            z[u] = __ldcs(c + i + u * stride);
+        }
+#pragma unroll
+        for (int u = 0; u < kReadUnroll; ++u) {
+            s = fmaf(x[u].x, y[u].x + z[u].x, s);
+            s = fmaf(x[u].y, y[u].y + z[u].y, s);
+            s = fmaf(x[u].z, y[u].z + z[u].z, s);
+            s = fmaf(x[u].w, y[u].w + z[u].w, s);
+        }
+    }
+    for (; i < nv; i += stride) {
+        const float4 x = __ldcs(a + i), y = __ldcs(b + i), z = __ldcs(c + i);
         s = fmaf(x.x, y.x + z.x, s);
         s = fmaf(x.y, y.y + z.y, s);
         s = fmaf(x.z, y.z + z.z, s);
@@ -1304,7 +1427,7 @@ __global__ void stream_read3_kernel(const float4* __restrict__ a, const float4* 
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
-    if ((threadIdx.x & 31) == 0) atomicAdd(o + blockIdx.x, s);
+    if ((threadIdx.x & 31) == 0) o[((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5] = s;
 }
 
 // o = a + 0.5 b: two streams read, one written
@@ -1319,8 +1442,16 @@ __global__ void stream_triad_kernel(const float4* __restrict__ a, const float4* 
 cudaError_t stream_rates(const float* a, const float* b, const float* c, float* o, int64_t n, int reps,
                          double* read_gbs, double* triad_gbs, cudaStream_t st) {
     const int64_t nv = n / 4;
-    // two waves of 8 resident blocks per SM: the fastest grid for these streams
-    const int nb = (int)std::min<int64_t>((nv + kRedThreads - 1) / kRedThreads, 152 * 16);
+    // every SM full of resident blocks, one wave (the loops stride over the rest)
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_read3_kernel, kRedThreads, 0) !=
+            cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    // o receives one float per warp of the read kernel: at most n/4 of them
+    const int64_t cap = std::max<int64_t>(1, nv * 32 / kRedThreads);
+    const int nb = (int)std::min<int64_t>((int64_t)device_sms() * per_sm, cap);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);

@@ -24,7 +24,7 @@ struct Scal {
     double nonfinite;    // > 0 if a NaN/Inf was seen
     double xmax;         // max |x| of the initial guess (0: the first residual is f)
     unsigned ticket;     // blocks of the running reduction that stored their partials
-    unsigned pad_;
+    unsigned wait_fail;  // a bounded device-side wait gave up (staged kernels)
 };
 
 enum FinalizeMode {
@@ -161,6 +161,8 @@ __device__ inline void finalize_last_block(const double* partials, int64_t nbloc
 cudaError_t stream_rates(const float* a, const float* b, const float* c, float* o, int64_t n, int reps,
                          double* read_gbs, double* triad_gbs, cudaStream_t st);
 
+// Streaming multiprocessors of the current device (queried once per device).
+int device_sms();
 // Grid of the element-wise kernels (kEW elements per thread).
 int elementwise_blocks(int64_t n);
 // Most blocks any reducing kernel launches on a grid of this size (the
@@ -217,8 +219,18 @@ void launch_helm_face_nu(const HelmGeo& g, const Geo& g0, const double* C, doubl
 // ---------------------------------------------------------- field steps ---
 // beta = 2/(rho_L + rho_R) (FP64); rh32 (may be null): FP32 copy of rho/2,
 // rh2 (may be null): rho/2 as (hi, lo) FP32 pairs, hi = rh32
+// The predictor's capillary and gravity forcing fused into the face
+// coefficients (Eqs. nonconspredictedvel, csf2): u* = u^n + tau a_f in place.
+struct Forcing {
+    const double* kappa;  // cell curvature (null: 0)
+    double sigma, h;      // surface tension, cell size
+    double g[3];          // gravity per axis
+    double tau;           // predictor time step
+    double* u[3];         // face arrays: in u^n, out u*
+};
 void launch_face_coeffs(const Geo& g, const double* C, double rho1, double rho2, double* bx,
-                        double* by, double* bz, float* rh32, float2* rh2, cudaStream_t st);
+                        double* by, double* bz, float* rh32, float2* rh2, cudaStream_t st,
+                        const Forcing* force = nullptr);
 // rhs = div(u)/(h dt); partials: (sum rhs, max |rhs|, nonfinite count)
 int64_t launch_divergence(const Geo& g, const double* u, const double* v, const double* w,
                           double inv_hdt, double* rhs, double* partials, cudaStream_t st,
@@ -297,16 +309,24 @@ void launch_prolong_add(const Geo& fine, const Geo& coarse, const int fac[3], co
 // holds its cells of colour (i+j+k) even in order of i, then the odd ones.
 // even nx, ny, nz and 32-bit offsets
 bool rho0_fits(const Geo& g);
-// tiles: plane-tile kernels where nx/2 is even (else the z-column kernels).
-// The plane-tile zero pass (zero_init) writes the updated colour only; the
-// pass of the other colour that follows it must be launched with own_zero,
-// which takes that colour as zero instead of reading it.  The z-column
-// kernels write both colours on the zero pass and ignore own_zero.
+// tiles: 2 = the TMA-staged plane kernel (stage.cu) where rho0_stage_fits,
+// else 1 = the register plane-tile kernels where nx/2 is even, else (0) the
+// z-column kernels.  The staged and plane-tile zero pass (zero_init) writes
+// the updated colour only; the pass of the other colour that follows it must
+// be launched with own_zero, which takes that colour as zero instead of
+// reading it.  The z-column kernels write both colours on the zero pass and
+// ignore own_zero.  fail: a word the staged kernel sets when one of its
+// bounded waits gives up (may be null for the other kernels).
 void launch_rbgs_rho(const Geo& g, const float* rh, double h, const float* f, float* x, int color,
-                     double omega, bool zero_init, cudaStream_t st, int k0 = 0, int k1 = -1, bool tiles = true,
-                     bool own_zero = false);
-// whether launch_rbgs_rho runs the plane-tile kernels on this grid
-bool rho0_tile_pass(const Geo& g, bool tiles);
+                     double omega, bool zero_init, cudaStream_t st, int k0 = 0, int k1 = -1, int tiles = 1,
+                     bool own_zero = false, unsigned* fail = nullptr);
+// whether launch_rbgs_rho runs a plane kernel (staged or register tiles) on this grid
+bool rho0_tile_pass(const Geo& g, int tiles);
+// the staged colour pass (stage.cu): nx a multiple of 8, ny of its tile height
+bool rho0_stage_fits(const Geo& g);
+cudaError_t launch_rbgs_rho_stage(const Geo& g, const float* rh, double h, const float* f, float* x, int color,
+                                  double omega, bool zero_init, bool own_zero, int k0, int k1, unsigned* fail,
+                                  cudaStream_t st);
 // q = A d; partials (d . q); returns the number of blocks
 int64_t launch_matvec_rho(const Geo& g, const float* rh, double h, const float* d, float* q,
                           double* partials, cudaStream_t st, FinSpec fin = no_fin(), bool tiles = true);

@@ -554,8 +554,11 @@ __device__ __forceinline__ void tile_update(const Geo& g, const float* __restric
 
 }  // namespace
 
+#ifndef PARIS_TILE_MINB
+#define PARIS_TILE_MINB 1
+#endif
 template <bool ZERO, bool XZ, int V>
-__global__ void __launch_bounds__(kBX* kVY) rbgs_rho_tile_kernel(Geo g, const float* __restrict__ rh, float h2,
+__global__ void __launch_bounds__(kBX* kVY, PARIS_TILE_MINB) rbgs_rho_tile_kernel(Geo g, const float* __restrict__ rh, float h2,
                                                                const float* __restrict__ f, float* x,
                                                                int color, float omega, int k0) {
     const int j = blockIdx.y * kVY + threadIdx.y;
@@ -573,14 +576,23 @@ __global__ void __launch_bounds__(kBX* kVY) rbgs_rho_tile_kernel(Geo g, const fl
         tile_update<ZERO, XZ, V, 1>(g, rh, f, x, h2, omega, color, j, k, t0, lane, act);
 }
 
-bool rho0_tile_pass(const Geo& g, bool tiles) { return tiles && kTileV > 0 && (g.nx / 2) % kTileV == 0; }
+bool rho0_tile_pass(const Geo& g, int tiles) {
+    return (tiles == 2 && rho0_stage_fits(g)) || (tiles != 0 && kTileV > 0 && (g.nx / 2) % kTileV == 0);
+}
 
 void launch_rbgs_rho(const Geo& g, const float* rh, double h, const float* f, float* x, int color,
-                     double omega, bool zero_init, cudaStream_t st, int k0, int k1, bool tiles, bool own_zero) {
+                     double omega, bool zero_init, cudaStream_t st, int k0, int k1, int tiles, bool own_zero,
+                     unsigned* fail) {
     if (k1 < 0) k1 = g.nz;
+    const bool al16 = (((uintptr_t)rh | (uintptr_t)f | (uintptr_t)x) & 15u) == 0;  // bulk copies: 16-byte aligned
+    if (tiles == 2 && fail && al16 && rho0_stage_fits(g)) {
+        const cudaError_t e = launch_rbgs_rho_stage(g, rh, h, f, x, color, omega, zero_init, own_zero, k0, k1, fail, st);
+        if (e != cudaSuccess) paris_internal_note_cuda_error(e);
+        return;
+    }
     const float h2 = (float)(h * h);
     const int hx = g.nx / 2;
-    if (rho0_tile_pass(g, tiles)) {
+    if (tiles != 0 && kTileV > 0 && (g.nx / 2) % kTileV == 0) {
         constexpr int V = kTileV > 0 ? kTileV : 2;
         dim3 gr((hx / V + kBX - 1) / kBX, (g.ny + kVY - 1) / kVY, k1 - k0);
         if (zero_init)

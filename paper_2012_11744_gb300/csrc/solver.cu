@@ -154,7 +154,7 @@ bool valid_opts(const paris_opts* o) {
     if (!(o->inner_tol > 0.0 && o->inner_tol < 1.0)) return false;
     if (o->slab_planes < 0) return false;
     if (o->level0_density != 0 && o->level0_density != 1) return false;
-    if (o->level0_tiles != 0 && o->level0_tiles != 1) return false;
+    if (o->level0_tiles < 0 || o->level0_tiles > 2) return false;
     return true;
 }
 
@@ -261,6 +261,10 @@ void drop_graphs(paris_ctx* c) {
 paris_status read_scal(paris_ctx* c) {
     CK(cudaMemcpyAsync(c->scal_h, c->scal, sizeof(Scal), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
+    if (c->scal_h->wait_fail) {  // a staged kernel's bounded wait gave up: clear the word, report it
+        CK(cudaMemsetAsync(&c->scal->wait_fail, 0, sizeof(unsigned), c->st));
+        return PARIS_ERR_TIMEOUT;
+    }
     return PARIS_OK;
 }
 
@@ -379,7 +383,7 @@ void smooth(paris_ctx* c, int l, const Coef<T>& cf, const T* f, T* x, int sweeps
             // and writes both colours
             // (plane-tile zero pass: the updated colour only, and the pass after it
             // reads neither colour's old value of its own cells)
-            const bool tile0 = v0 && rho0_tile_pass(L.g, o.level0_tiles != 0);
+            const bool tile0 = v0 && rho0_tile_pass(L.g, o.level0_tiles);
             const double b_first = v0 ? (z0 ? (tile0 ? 2.0 : 2.5) : 3.0) * n * sz
                                       : (z0 ? 2 * n * sz : 2.5 * n * sz + nb * bsz);
             const double b_second = v0 ? ((z0 && tile0) ? 2.5 : 3.0) * n * sz : 2.5 * n * sz + nb * bsz;
@@ -389,7 +393,7 @@ void smooth(paris_ctx* c, int l, const Coef<T>& cf, const T* f, T* x, int sweeps
                         // after a zero pass the other colour is still unwritten on the
                         // plane-tile path: the second pass of that sweep takes it as zero
                         launch_rbgs_rho(L.g, c->rh32, c->grid.h, (const float*)f, (float*)x, color, o.omega,
-                                        zero, c->st, a, b, o.level0_tiles != 0, z0 && !zero);
+                                        zero, c->st, a, b, o.level0_tiles, z0 && !zero, &c->scal->wait_fail);
                         return;
                     }
                     if (h16) {
@@ -1125,7 +1129,7 @@ struct HostLink {
 
 paris_status projection_step_impl(paris_ctx* c, const double* C, double rho1, double rho2, double dt,
                                   double* u, double* v, double* w, double* p, paris_stats* st,
-                                  const HostLink* hl) {
+                                  const HostLink* hl, const Forcing* force = nullptr) {
     const bool use_rho0 = rho0_usable(c);
     // the set-up run ahead below is used by this step's solve only
     struct ReadyGuard {
@@ -1136,7 +1140,7 @@ paris_status projection_step_impl(paris_ctx* c, const double* C, double rho1, do
         ProfScope ps(c, PARIS_K_FIELD, 0.0);
         if (hl) CK(cudaStreamWaitEvent(c->st, hl->c_ready, 0));
         launch_face_coeffs(c->g0, C, rho1, rho2, c->beta[0], c->beta[1], c->beta[2],
-                           use_rho0 ? c->rh32 : nullptr, use_rho0 ? c->rh2 : nullptr, c->st);
+                           use_rho0 ? c->rh32 : nullptr, use_rho0 ? c->rh2 : nullptr, c->st, force);
         CK(cudaGetLastError());
     }
     if (c->opts.precision == PARIS_MIXED) {
@@ -1185,6 +1189,35 @@ paris_status paris_projection_step(paris_ctx* c, const double* C, double rho1, d
         return PARIS_ERR_INVALID_ARG;
     if (!(dt > 0.0) || !std::isfinite(dt)) return PARIS_ERR_INVALID_ARG;
     return projection_step_impl(c, C, rho1, rho2, dt, u, v, w, p, st, nullptr);
+}
+
+static bool valid_forcing(double sigma, double gx, double gy, double gz) {
+    return std::isfinite(sigma) && sigma >= 0.0 && std::isfinite(gx) && std::isfinite(gy) && std::isfinite(gz);
+}
+
+paris_status paris_predictor_forcing(paris_ctx* c, const double* C, const double* kappa, double rho1,
+                                     double rho2, double sigma, double gx, double gy, double gz, double tau,
+                                     double* u, double* v, double* w, double* bx, double* by, double* bz) {
+    if (!c || !C || !u || !v || !w || !bx || !by || !bz) return PARIS_ERR_INVALID_ARG;
+    if (!(rho1 > 0.0) || !(rho2 > 0.0) || !std::isfinite(rho1) || !std::isfinite(rho2))
+        return PARIS_ERR_INVALID_ARG;
+    if (!valid_forcing(sigma, gx, gy, gz) || !std::isfinite(tau) || tau < 0.0) return PARIS_ERR_INVALID_ARG;
+    const Forcing fo{kappa, sigma, c->grid.h, {gx, gy, gz}, tau, {u, v, w}};
+    launch_face_coeffs(c->g0, C, rho1, rho2, bx, by, bz, nullptr, nullptr, c->st, &fo);
+    CK(cudaGetLastError());
+    return PARIS_OK;
+}
+
+paris_status paris_projection_step_forced(paris_ctx* c, const double* C, const double* kappa, double rho1,
+                                          double rho2, double sigma, double gx, double gy, double gz,
+                                          double dt, double* u, double* v, double* w, double* p,
+                                          paris_stats* st) {
+    if (!c || !C || !u || !v || !w || !p) return PARIS_ERR_INVALID_ARG;
+    if (!(rho1 > 0.0) || !(rho2 > 0.0) || !std::isfinite(rho1) || !std::isfinite(rho2))
+        return PARIS_ERR_INVALID_ARG;
+    if (!(dt > 0.0) || !std::isfinite(dt) || !valid_forcing(sigma, gx, gy, gz)) return PARIS_ERR_INVALID_ARG;
+    const Forcing fo{kappa, sigma, c->grid.h, {gx, gy, gz}, dt, {u, v, w}};
+    return projection_step_impl(c, C, rho1, rho2, dt, u, v, w, p, st, nullptr, &fo);
 }
 
 paris_status paris_projection_step_host(paris_ctx* c, const double* C_host, double rho1,
