@@ -6,12 +6,17 @@ dominant kernel.
 One step = one whole projection (face coefficients from C, divergence of u*,
 multigrid-preconditioned Poisson solve to 1e-10 in the L2 and L-infinity norms,
 velocity correction) of the 256^3 drop field: 64 drops, periodic x/y, walls
-in z, rho1/rho2 = 1000, dt = 1e-4, seeded synthetic input.  Before every step
-u*, v*, w* are restored from device-resident copies and p is reset to zero
-(both inside the timed region; ~1 % of a step).  Each step reads more than the
-129 MB L2 (C plus u*, v*, w*: 537 MB), so no flush is needed.
+in z, rho1/rho2 = 1000, dt = 1e-4, seeded synthetic input.  Every timed step
+projects its own device-resident copy of u*, v*, w* from a zero initial
+pressure; those copies are made before the timed region, which holds the
+projection steps alone.  Each step reads more than the 129 MB L2 (C plus u*,
+v*, w*, p: 671 MB), so no flush is needed.  Each step is bracketed by its own
+CUDA event pair on the launching stream: value = steps / summed step time,
+and the median, p10 and p90 of the step times are reported beside it.  Every
+timed step must converge, or the run fails.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl paris|reference]
+       python bench.py --jet | --adjoint | --viscous   (other workloads, one line each)
 Multi-GPU (torchrun): every rank runs an independent replica ("replicas
 only": one projection does not shard here), value = all ranks' solves / max time.
 """
@@ -39,6 +44,7 @@ VISC_TAU_NU_OVER_H2 = 4.0
 
 METRIC = "Projection solves/s at 256³, ρ ratio 1000, resid 1e-10: mixed vs FP64; % HBM"
 UNIT = "solves/s"
+STREAM_FLOATS = 1 << 27  # FP32 elements per vector of the streaming-rate probe (512 MB)
 
 # DRAM bytes (read + write) per launch of the dominant kernel class, from one
 # ncu capture of "python bench.py --single mixed", valid while the source file
@@ -65,6 +71,47 @@ def measured_peaks():
             d = json.load(fh)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine() or "unknown"
+
+
+def oracle_threads() -> int:
+    """Threads the oracle's OpenMP loops run on (OMP_NUM_THREADS, else every core)."""
+    try:
+        return int(os.environ["OMP_NUM_THREADS"])
+    except (KeyError, ValueError):
+        return os.cpu_count() or 1
+
+
+def step_stats(ms_list):
+    """Median, p10 and p90 of per-step times (ms), nearest-rank percentiles."""
+    a = sorted(ms_list)
+    pick = lambda q: a[min(len(a) - 1, max(0, int(round(q * (len(a) - 1)))))]
+    return {"median": statistics.median(a), "p10": pick(0.1), "p90": pick(0.9), "n": len(a)}
+
+
+def require_converged(stats, what):
+    bad = [i for i, s in enumerate(stats) if s.get("converged") != 1]
+    if bad:
+        raise RuntimeError(f"{what}: timed steps {bad} did not converge: {[stats[i] for i in bad]}")
 
 
 class ClockSampler:
@@ -161,6 +208,8 @@ def oracle_sample(pr, budget_s: float, golden: dict | None):
     count of the full oracle solve (stored by tests/golden/make_drops256_golden.py)."""
     import oracle
     g = pr.grid
+    if golden is None and g.ncells > SMALL_CELLS:
+        raise FileNotFoundError(f"no stored oracle solve for {g.nx}x{g.ny}x{g.nz}")
     t0 = time.perf_counter()
     beta = oracle.face_coeffs(g, pr.C, pr.rho1, pr.rho2)
     b = oracle.divergence(g, pr.u, pr.v, pr.w, pr.dt)
@@ -176,12 +225,15 @@ def oracle_sample(pr, budget_s: float, golden: dict | None):
     res = oracle.cg(op, -b0, tol=1e-300, max_iter=m2, check=50)
     t4 = time.perf_counter()
     per_it = (t4 - t3) / max(res.iters, 1)
-    n_full = int(golden["oracle"]["cg_iters"]) if golden else None
+    if golden is not None:
+        n_full = int(golden["oracle"]["cg_iters"])
+    else:  # no stored full solve: small grids only, whose full solve is measured here
+        if g.ncells > SMALL_CELLS:
+            raise FileNotFoundError(f"no stored oracle solve for {g.nx}x{g.ny}x{g.nz}")
+        n_full = oracle.cg(op, -b0, tol=1e-13).iters
     proj = oracle.project(g, *beta, res.x, pr.dt, pr.u, pr.v, pr.w)  # noqa: F841 (timed below)
     t5 = time.perf_counter()
     setup = (t1 - t0) + (t5 - t4)
-    if n_full is None:
-        n_full = 12000  # order of magnitude when the stored count is missing
     solve_s = setup + per_it * n_full
     return {"solve_s": solve_s, "setup_s": setup, "s_per_cg_iter": per_it, "cg_iters_sampled": res.iters,
             "cg_iters_full": n_full, "sample_s": t5 - t0}
@@ -198,6 +250,8 @@ def viscous_oracle_sample(pr, budget_s: float, golden: dict | None):
     solves (stored by tests/golden/make_viscous256_golden.py)."""
     from oracle import viscous as V
     g = pr.grid
+    if golden is None and g.ncells > SMALL_CELLS:
+        raise FileNotFoundError(f"no stored viscous oracle solves for {g.nx}x{g.ny}x{g.nz}")
     t0 = time.perf_counter()
     nus = [V.face_nu(g, c, pr.C, VISC_MU[0], VISC_MU[1], pr.rho1, pr.rho2) for c in range(3)]
     tau = VISC_TAU_NU_OVER_H2 * g.h ** 2 / max(float(nu.max()) for nu in nus)
@@ -219,7 +273,16 @@ def viscous_oracle_sample(pr, budget_s: float, golden: dict | None):
     s2 = cut(m2)
     per_it = max(s2 - s1, 0.0) / (m2 - m1)
     setup = max(s1 - m1 * per_it, 0.0)
-    iters = [int(c["iters"]) for c in golden["components"]] if golden else [100, 100, 100]
+    if golden is not None:
+        iters = [int(c["iters"]) for c in golden["components"]]
+    else:  # no stored full solves: small grids only, whose full solves are counted here
+        if g.ncells > SMALL_CELLS:
+            raise FileNotFoundError(f"no stored viscous oracle solves for {g.nx}x{g.ny}x{g.nz}")
+        iters = []
+        for c in range(3):
+            st = {}
+            V.solve(g, c, nus[c], tau, V.interior(g, c, (pr.u, pr.v, pr.w)[c]), tol=1e-13, stats=st)
+            iters.append(int(st["iters"]))
     step_s = (t1 - t0) + sum(setup + per_it * k for k in iters)
     return {"step_s": step_s, "setup_s": setup, "s_per_cg_iter": per_it, "cg_iters_sampled": [m1, m2],
             "cg_iters_full": iters, "sample_s": time.perf_counter() - t0}
@@ -233,12 +296,20 @@ def load_visc_golden(n):
     return None
 
 
-def load_golden(n):
-    p = os.path.join(ROOT, "tests", "golden", f"drops{n}_walls_z.json")
-    if os.path.exists(p):
-        with open(p) as fh:
-            return json.load(fh)
-    return None
+SMALL_CELLS = 64 ** 3  # grids whose full oracle solve is cheap enough to run in a CPU-baseline sample
+
+
+def load_golden(name, required=True):
+    """A stored oracle solve (tests/golden/<name>.json), whose iteration count
+    the CPU baseline extrapolates to.  Missing: an error when required, else
+    None (the sample then solves small grids in full to count)."""
+    p = os.path.join(ROOT, "tests", "golden", f"{name}.json")
+    if not os.path.exists(p):
+        if required:
+            raise FileNotFoundError(f"{p} is missing: run tests/golden/make_*_golden.py first")
+        return None
+    with open(p) as fh:
+        return json.load(fh)
 
 
 def run_reference(args, rank, world):
@@ -247,8 +318,8 @@ def run_reference(args, rank, world):
         return
     import paris_inputs as pi
     pr = pi.config2(n=args.n)
-    golden = load_golden(args.n)
-    cores = os.cpu_count()
+    golden = load_golden(f"drops{args.n}_walls_z", required=args.n > 64)
+    cores = oracle_threads()
     for _ in range(args.warmup):
         oracle_sample(pr, 0.5, golden)
     samples = [oracle_sample(pr, args.ref_budget, golden) for _ in range(args.steps)]
@@ -259,7 +330,7 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": workload_config(args.n),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "cpu_model": cpu_model(), "kind": "oracle",
                          "sample": f"per step: oracle set-up + ~{args.ref_budget:.0f} s of CG iterations "
                                    f"on the {args.n}^3 system, extrapolated to the "
                                    f"{samples[0]['cg_iters_full']} iterations of the full oracle solve"},
@@ -309,6 +380,9 @@ def run_paris(args, rank, world, local):
             p.zero_()
 
     def timed(ctx, K, W, prof=False):
+        """K projection steps, each between its own event pair on the
+        launching stream; returns the summed ms, the per-step ms, the stats,
+        the library's launches and (prof) the kernel-class profile."""
         for _ in range(W):
             refill(1)
             st = ctx.projection_step(C, pr.rho1, pr.rho2, pr.dt, *sets[0])
@@ -318,35 +392,36 @@ def run_paris(args, rank, world, local):
         if prof:
             ctx.profile(True)
         l0 = api.launch_count()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
         sts = []
         for i in range(K):
+            ev[i][0].record(stream)
             sts.append(ctx.projection_step(C, pr.rho1, pr.rho2, pr.dt, *sets[i]))
-        e1.record(stream)
+            ev[i][1].record(stream)
         torch.cuda.synchronize(dev)
         barrier(world)
         launches = api.launch_count() - l0
-        ms = e0.elapsed_time(e1)
+        per = [a.elapsed_time(b) for a, b in ev]
         prof_d = ctx.profile_read() if prof else None
         if prof:
             ctx.profile(False)
-        return ms, sts, launches, prof_d
+        return sum(per), per, sts, launches, prof_d
 
     hbm, peak_kind = measured_peaks()
     # mixed precision (headline)
     ctx = paris.Context(g, opts=paris.default_opts(precision=paris.MIXED), device=dev)
     with ClockSampler(local) as clk:
-        ms_mixed, st_mixed, launches, _ = timed(ctx, args.steps, args.warmup)
+        ms_mixed, per_mixed, st_mixed, launches, _ = timed(ctx, args.steps, args.warmup)
     clocks = clk.summary()
+    require_converged(st_mixed, "mixed")
     ms_mixed = allreduce_max(ms_mixed, world, dev)
     # the same steps again with an event pair around every launch of the
     # instrumented kernel classes (kernel times and the roofline)
-    ms_prof, _, _, prof = timed(ctx, args.steps, 1, prof=True)
-    # this device's streaming rates over four level-0-sized FP32 vectors
-    # (a read-only stream and a triad), the ceilings beside the copy peak
-    sv = [torch.zeros(N, dtype=torch.float32, device=dev) for _ in range(4)]
+    ms_prof, _, st_prof, _, prof = timed(ctx, args.steps, 1, prof=True)
+    require_converged(st_prof, "mixed, profiled run")
+    # this device's streaming rates over four FP32 vectors of 512 MB (a
+    # read-only stream of 1.5 GB and a triad), the ceilings beside the copy peak
+    sv = [torch.zeros(STREAM_FLOATS, dtype=torch.float32, device=dev) for _ in range(4)]
     stream_read, stream_triad = paris.stream_rates(*sv, reps=5)
     del sv
     # e2e through the host-buffer entry point (pinned host memory)
@@ -363,8 +438,9 @@ def run_paris(args, rank, world, local):
         hw.copy_(hw0)
         hp.zero_()
         t0 = time.perf_counter()
-        ctx.projection_step_host(hC, pr.rho1, pr.rho2, pr.dt, hu, hv, hw, hp)
+        ste = ctx.projection_step_host(hC, pr.rho1, pr.rho2, pr.dt, hu, hv, hw, hp)
         t1 = time.perf_counter()
+        require_converged([ste], "e2e")
         if i >= args.warmup:
             e2e_s += t1 - t0
     e2e_s = allreduce_max(e2e_s, world, dev)
@@ -374,9 +450,11 @@ def run_paris(args, rank, world, local):
     # plain FP64 form
     ctx = paris.Context(g, opts=paris.default_opts(precision=paris.FP64), device=dev)
     k64 = max(3, args.steps // 2)
-    ms_fp64, st_fp64, _, _ = timed(ctx, k64, args.warmup)
+    ms_fp64, per_fp64, st_fp64, _, _ = timed(ctx, k64, args.warmup)
+    require_converged(st_fp64, "fp64")
     ms_fp64 = allreduce_max(ms_fp64, world, dev)
-    _, _, _, prof64 = timed(ctx, k64, 1, prof=True)
+    _, _, st64p, _, prof64 = timed(ctx, k64, 1, prof=True)
+    require_converged(st64p, "fp64, profiled run")
     ctx.close()
 
     # batched mode: 256 uneven periodic instances in one persistent launch
@@ -426,9 +504,10 @@ def run_paris(args, rank, world, local):
     cpu = None
     if world == 1 and not args.no_cpu:
         import paris_inputs as pi2  # noqa: F401
-        golden = load_golden(args.n)
+        golden = load_golden(f"drops{args.n}_walls_z", required=args.n > 64)
         s = oracle_sample(pr, args.cpu_budget, golden)
-        cpu = {"value": 1.0 / s["solve_s"], "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+        cpu = {"value": 1.0 / s["solve_s"], "unit": UNIT, "cores": oracle_threads(), "cpu_model": cpu_model(),
+               "kind": "oracle",
                "sample": f"oracle set-up + {s['cg_iters_sampled']} CG iterations of the {args.n}^3 "
                          f"system ({s['sample_s']:.1f} s), extrapolated to the {s['cg_iters_full']} "
                          f"iterations of the full oracle solve"}
@@ -448,7 +527,11 @@ def run_paris(args, rank, world, local):
         "warmup": args.warmup, "ms_per_step": ms_mixed / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": workload_config(args.n),
+        "step_ms": step_stats(per_mixed),
+        "all_steps_converged": True,
+        "iters_per_step": [x["iters"] for x in st_mixed],
         "fp64": {"value": fp64_value, "unit": UNIT, "ms_per_step": ms_fp64 / k64, "steps": k64,
+                 "step_ms": step_stats(per_fp64), "all_steps_converged": True,
                  "iters": st_fp64[-1]["iters"], "rel_res_l2": st_fp64[-1]["rel_res_l2"],
                  "rel_res_linf": st_fp64[-1]["rel_res_linf"]},
         "mixed_over_fp64": value / fp64_value,
@@ -556,7 +639,8 @@ def run_viscous(args):
     if not args.no_cpu:
         gold = load_visc_golden(args.n)
         smp = viscous_oracle_sample(pr, args.cpu_budget, gold)
-        cpu = {"value": 3.0 / smp["step_s"], "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+        cpu = {"value": 3.0 / smp["step_s"], "unit": "solves/s", "cores": oracle_threads(),
+               "cpu_model": cpu_model(), "kind": "oracle",
                "sample": f"scipy CG (sparse products on one thread), face viscosities, then the w solve cut after "
                          f"{smp['cg_iters_sampled'][0]}, 5 and {smp['cg_iters_sampled'][1]} iterations "
                          f"(set-up {smp['setup_s']:.2f} s, {smp['s_per_cg_iter']:.3f} s per iteration), "
@@ -576,6 +660,236 @@ def run_viscous(args):
                    "l2": "no flush: each iteration streams 7 vectors of one component (> 129 MB L2)"}}))
 
 
+def event_steps(step, K, stream):
+    """Run step() K times, each between its own event pair on `stream`;
+    returns the per-step ms and the step results."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    out = []
+    torch.cuda.synchronize()
+    for i in range(K):
+        ev[i][0].record(stream)
+        out.append(step(i))
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev], out
+
+
+def class_roofline(prof, hbm, kind):
+    """Roofline of the dominant single-kernel class of a kernel-class profile."""
+    from paper_2012_11744_gb300 import _abi as pabi
+    dom = max(pabi.K_BYTES, key=lambda k: prof[k]["ms"])
+    pk = prof[dom]
+    ach = pk["bytes"] / (pk["ms"] / 1e3) / 1e9 if pk["ms"] > 0 else None
+    return {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
+            "frac": ach / hbm if ach else None, "traffic": None, "peak_kind": kind,
+            "launches": pk["timed"], "avg_launch_us": 1e3 * pk["ms"] / max(pk["timed"], 1)}
+
+
+def run_jet(args):
+    """The 512x256x256 jet (periodic x, walls y/z, ratio 1000, dt 5e-5),
+    mixed form to 1e-10: solves/s, and the pointwise error of the last
+    step's p and u against the stored full FP64 oracle solve
+    (tests/golden/jet512x256x256.json) at its sampled cells and faces."""
+    import hashlib
+
+    import torch
+
+    import paper_2012_11744_gb300 as paris
+    import paris_inputs as pi
+    pr = pi.config3()
+    g = pr.grid
+    gold = load_golden("jet512x256x256")
+    assert gold["C_sha256"] == hashlib.sha256(np.ascontiguousarray(pr.C).tobytes()).hexdigest()
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    C, u0, v0, w0 = d(pr.C), d(pr.u), d(pr.v), d(pr.w)
+    K = args.steps
+    sets = [(u0.clone(), v0.clone(), w0.clone(), torch.zeros(g.shape, dtype=torch.float64, device="cuda"))
+            for _ in range(K)]
+    ctx = paris.Context(g, opts=paris.default_opts(precision=paris.MIXED))
+    for _ in range(args.warmup):
+        uu, vv, ww, pp = u0.clone(), v0.clone(), w0.clone(), torch.zeros_like(sets[0][3])
+        ctx.projection_step(C, pr.rho1, pr.rho2, pr.dt, uu, vv, ww, pp)
+    with ClockSampler(0) as clk:
+        per, sts = event_steps(lambda i: ctx.projection_step(C, pr.rho1, pr.rho2, pr.dt, *sets[i]), K, ctx.stream)
+    require_converged(sts, "jet")
+    uu, vv, ww, pp = u0.clone(), v0.clone(), w0.clone(), torch.zeros_like(sets[0][3])
+    ctx.profile(True)
+    ctx.projection_step(C, pr.rho1, pr.rho2, pr.dt, uu, vv, ww, pp)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    ctx.close()
+    p = sets[-1][3].cpu().numpy().ravel()
+    uvw = [x.cpu().numpy().ravel() for x in sets[-1][:3]]
+    cells = np.asarray(gold["cells"])
+    p_err = float(np.abs(p[cells] - np.asarray(gold["p"])).max() / gold["p_max_abs"])
+    umax = gold["ustar_max_abs"]
+    u_err = max(float(np.abs(uvw[a][np.asarray(gold["faces"][a])] - np.asarray(gold["u"][a])).max())
+                for a in range(3)) / umax
+    hbm, kind = measured_peaks()
+    total = sum(per)
+    cpu = None
+    if not args.no_cpu:
+        smp = oracle_sample(pr, args.cpu_budget, gold)
+        cpu = {"value": 1.0 / smp["solve_s"], "unit": UNIT, "cores": oracle_threads(), "cpu_model": cpu_model(),
+               "kind": "oracle",
+               "sample": f"oracle set-up + {smp['cg_iters_sampled']} CG iterations of the jet system "
+                         f"({smp['sample_s']:.1f} s), extrapolated to the {smp['cg_iters_full']} iterations "
+                         f"of the full oracle solve"}
+    print(json.dumps({
+        "metric": "jet projection solves/s at 512x256x256, rho ratio 1000, resid 1e-10 (mixed)",
+        "value": K / (total / 1e3), "unit": UNIT, "steps": K, "warmup": args.warmup, "ms_per_step": total / K,
+        "step_ms": step_stats(per), "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+        "iters_per_step": [x["iters"] for x in sts], "rel_res_l2": sts[-1]["rel_res_l2"],
+        "rel_res_linf": sts[-1]["rel_res_linf"], "all_steps_converged": True,
+        "vs_oracle": {"p_rel_err_inf": p_err, "u_err_inf_over_max_ustar": u_err,
+                      "samples": [len(cells), sum(len(f) for f in gold["faces"])],
+                      "oracle_rel_res_l2": gold["oracle"]["rel_res_l2"],
+                      "oracle_p_rel_err_bound": gold["bound"]["p_rel_err_bound"]},
+        "roofline": class_roofline(prof, hbm, kind), "clocks": clk.summary(), "cpu_baseline": cpu,
+        "config": {"workload": "jet512x256x256: L = (2,1,1), periodic x, walls y/z, cylinder R = 0.08 with 4 "
+                               "sine modes, u_x = 1 in the liquid + U[-0.1,0.1] noise, rho 1000/1, dt 5e-5, "
+                               "tol 1e-10 (L2 and Linf)",
+                   "l2": "no flush: each step projects its own u*, v*, w*, p (4 x 268 MB > 129 MB L2)"}}),
+        flush=True)
+
+
+def run_adjoint(args):
+    """The adjoint configuration: 128^3 periodic tanh drop (rho 100/1), loss
+    L = 1/2 ||u - u_target||^2.  One step = the forward projection step plus
+    the adjoint (paris_project_adjoint and paris_face_coeffs_adjoint) giving
+    dL/du* and dL/dC, in FP64 and in the mixed form; value = gradients/s of
+    the mixed form.  The two forms' gradients are compared with each other
+    here; against the oracle adjoint and finite differences in the tests."""
+    import torch
+
+    import paper_2012_11744_gb300 as paris
+    import paris_inputs as pi
+    pr = pi.config5()
+    g = pr.grid
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    C, u0, v0, w0 = d(pr.C), d(pr.u), d(pr.v), d(pr.w)
+    tgt = [d(x) for x in pr.extra["target"]]
+    res = {}
+    for name, prec in (("mixed", paris.MIXED), ("fp64", paris.FP64)):
+        ctx = paris.Context(g, opts=paris.default_opts(precision=prec))
+        beta = ctx.empty_faces()
+        p = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+
+        def step(i):
+            u, v, w = u0.clone(), v0.clone(), w0.clone()
+            p.zero_()
+            st = ctx.projection_step(C, pr.rho1, pr.rho2, pr.dt, u, v, w, p)
+            ctx.face_coeffs(C, pr.rho1, pr.rho2, beta)
+            gu = [(x - t).contiguous() for x, t in zip((u, v, w), tgt)]
+            gus, gb, _, sta = ctx.project_adjoint(*beta, p, pr.dt, *gu)
+            gC = ctx.face_coeffs_adjoint(pr.rho1, pr.rho2, *beta, *gb)
+            return st, sta, gus, gC
+
+        for _ in range(args.warmup):
+            step(0)
+        per, outs = event_steps(step, args.steps, ctx.stream)
+        require_converged([o[0] for o in outs] + [o[1] for o in outs], f"adjoint {name}")
+        res[name] = {"per": per, "gus": [x.cpu().numpy() for x in outs[-1][2]], "gC": outs[-1][3].cpu().numpy(),
+                     "iters": [outs[-1][0]["iters"], outs[-1][1]["iters"]]}
+        ctx.close()
+    rel = lambda a, b: float(np.abs(a - b).max() / np.abs(b).max())
+    tot = sum(res["mixed"]["per"])
+    print(json.dumps({
+        "metric": "adjoint gradients/s (forward projection + dL/du*, dL/dC) at 128^3, rho ratio 100",
+        "value": args.steps / (tot / 1e3), "unit": "gradients/s", "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tot / args.steps, "step_ms": step_stats(res["mixed"]["per"]), "higher_is_better": True,
+        "dtype": "f32+f64", "data": "synthetic",
+        "fp64": {"value": args.steps / (sum(res["fp64"]["per"]) / 1e3), "step_ms": step_stats(res["fp64"]["per"]),
+                 "iters_forward_adjoint": res["fp64"]["iters"]},
+        "iters_forward_adjoint": res["mixed"]["iters"],
+        "mixed_vs_fp64": {"dL_du_star": max(rel(a, b) for a, b in zip(res["mixed"]["gus"], res["fp64"]["gus"])),
+                          "dL_dC": rel(res["mixed"]["gC"], res["fp64"]["gC"])},
+        "config": {"workload": "adjoint_drop128: 128^3 periodic, tanh drop r = 0.2 (w = 1.5h), rho 100/1, "
+                               "u* ~ U[-1,1], divergence-free target, dt 1e-3, tol 1e-10",
+                   "l2": "each step reads C, u*, target and writes the gradients (> 129 MB L2)"}}), flush=True)
+
+
+def run_forcing(args):
+    """The predictor forcing (capillary CSF term with the drops' curvature,
+    sigma 0.07, and gravity -9.81 in z) fused into the projection step of the
+    256^3 drop field, against the same step without forcing: solves/s of the
+    forced step and the time of the face pass that carries the forcing."""
+    import torch
+
+    import paper_2012_11744_gb300 as paris
+    import paris_inputs as pi
+    pr = pi.config2(n=args.n)
+    g = pr.grid
+    kappa = pi.drop_curvature(g, pr.extra["spheres"])
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    C, K_, u0, v0, w0 = d(pr.C), d(kappa), d(pr.u), d(pr.v), d(pr.w)
+    sigma, grav = 0.07, (0.0, 0.0, -9.81)
+    K = args.steps
+    sets = [(u0.clone(), v0.clone(), w0.clone(), torch.zeros(g.shape, dtype=torch.float64, device="cuda"))
+            for _ in range(K)]
+
+    def refill():
+        for (u, v, w, p) in sets:
+            u.copy_(u0)
+            v.copy_(v0)
+            w.copy_(w0)
+            p.zero_()
+
+    ctx = paris.Context(g, opts=paris.default_opts(precision=paris.MIXED))
+    forced = lambda i: ctx.projection_step_forced(C, K_, pr.rho1, pr.rho2, sigma, grav, pr.dt, *sets[i])
+    plain = lambda i: ctx.projection_step(C, pr.rho1, pr.rho2, pr.dt, *sets[i])
+    for _ in range(args.warmup):
+        refill()
+        forced(0)
+        plain(0)
+    refill()
+    with ClockSampler(0) as clk:
+        per_f, st_f = event_steps(forced, K, ctx.stream)
+    require_converged(st_f, "forced")
+    refill()
+    per_p, st_p = event_steps(plain, K, ctx.stream)
+    require_converged(st_p, "plain")
+    # the face pass alone, with and without the forcing (events around each launch)
+    N = g.ncells
+    beta = ctx.empty_faces()
+    uu, vv, ww = u0.clone(), v0.clone(), w0.clone()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    reps = 20
+    t = {}
+    for name, fn in (("forcing", lambda: ctx.predictor_forcing(C, K_, pr.rho1, pr.rho2, sigma, grav, pr.dt,
+                                                               uu, vv, ww, beta)),
+                     ("face_coeffs", lambda: ctx.face_coeffs(C, pr.rho1, pr.rho2, beta))):
+        fn()
+        e0, e1 = ev(), ev()
+        e0.record(ctx.stream)
+        for _ in range(reps):
+            fn()
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        t[name] = e0.elapsed_time(e1) / reps
+    ctx.close()
+    nf = sum(int(np.prod(g.face_shape(a))) for a in range(3))
+    byt_f = 8.0 * (2 * N + 3 * nf)  # C, kappa read; beta written, u^n read and u* written (8 B per face each)
+    hbm, kind = measured_peaks()
+    ach = byt_f / (t["forcing"] * 1e-3) / 1e9
+    print(json.dumps({
+        "metric": "forced projection solves/s at 256^3 (CSF + gravity in the face pass), rho 1000, resid 1e-10",
+        "value": K / (sum(per_f) / 1e3), "unit": UNIT, "steps": K, "warmup": args.warmup,
+        "ms_per_step": sum(per_f) / K, "step_ms": step_stats(per_f), "higher_is_better": True,
+        "dtype": "f32+f64", "data": "synthetic", "all_steps_converged": True,
+        "iters_per_step": [x["iters"] for x in st_f],
+        "unforced": {"value": K / (sum(per_p) / 1e3), "step_ms": step_stats(per_p)},
+        "face_pass_ms": {"with_forcing": t["forcing"], "face_coeffs_only": t["face_coeffs"]},
+        "roofline": {"bound": "hbm", "kernel": "face_coeffs_kernel<FORCE>", "achieved": ach, "peak": hbm,
+                     "unit": "GB/s", "frac": ach / hbm, "traffic": None, "peak_kind": kind,
+                     "bytes_per_launch": byt_f,
+                     "note": "C, kappa read (16 B/cell), beta written, u^n read, u* written (24 B/face each)"},
+        "clocks": clk.summary(),
+        "config": {"workload": workload_config(args.n)["workload"] + ", sigma 0.07, kappa = -2/r of the nearest "
+                               "drop, g = -9.81 z", "l2": "no flush: fields > 129 MB L2"}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -593,6 +907,10 @@ def main():
                     help="run one untimed projection (the target of ncu captures) and exit")
     ap.add_argument("--viscous", action="store_true",
                     help="time the implicit viscous step of the three components instead and exit")
+    ap.add_argument("--jet", action="store_true", help="time the 512x256x256 jet (mixed) instead and exit")
+    ap.add_argument("--adjoint", action="store_true", help="time the 128^3 adjoint step instead and exit")
+    ap.add_argument("--forcing", action="store_true",
+                    help="time the projection step with the predictor forcing fused in instead and exit")
     ap.add_argument("--smoother", type=int, default=None,
                     help="with --single: 0 fused red-black, 1 Jacobi, 2 two-pass red-black")
     args = ap.parse_args()
@@ -600,6 +918,15 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.viscous:
         run_viscous(args)
+        return
+    if args.jet:
+        run_jet(args)
+        return
+    if args.adjoint:
+        run_adjoint(args)
+        return
+    if args.forcing:
+        run_forcing(args)
         return
     if args.single:
         run_single(args)

@@ -4,6 +4,8 @@ import json
 import os
 import sys
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 
@@ -72,4 +74,16 @@ def test_viscous_oracle_sample_extrapolates_to_the_stored_counts():
     assert s["cg_iters_full"] == [10, 20, 30] and s["cg_iters_sampled"][0] == 1
     assert s["cg_iters_sampled"][1] >= 9 and s["s_per_cg_iter"] >= 0.0 and s["setup_s"] >= 0.0
     assert s["step_s"] >= 3 * s["setup_s"] + 60 * s["s_per_cg_iter"]
-    assert bench.viscous_oracle_sample(pr, 0.01, None)["cg_iters_full"] == [100, 100, 100]
+    # no stored solves: a small grid's full oracle solves are run and counted
+    full = bench.viscous_oracle_sample(pr, 0.01, None)["cg_iters_full"]
+    assert len(full) == 3 and all(k > 0 for k in full)
+    with pytest.raises(FileNotFoundError):
+        bench.viscous_oracle_sample(pi.config2(n=80), 0.01, None)
+
+
+def test_oracle_sample_counts_small_grids_and_refuses_large_ones_without_a_stored_solve():
+    import paris_inputs as pi
+    s = bench.oracle_sample(pi.config2(n=16), 0.05, None)
+    assert s["cg_iters_full"] > 0 and s["solve_s"] > 0
+    with pytest.raises(FileNotFoundError):
+        bench.oracle_sample(pi.config2(n=80), 0.01, None)
