@@ -16,7 +16,9 @@ Every function follows a passage of the PARIS paper (arXiv 2012.11744):
   project_adjoint / face_coeffs_adjoint: derivatives of the above (no paper
   counterpart; pinned against central finite differences in the tests)
 
-The implicit viscous step of Sec. 3.2.3 (Eq. muelliptic) is in ``viscous.py``
+Solid cells (the "Lego" solids of Sec. 3.8: link flags that block the
+velocity and zero the pressure coefficients on the solid and its boundary)
+are in ``solid.py``.  The implicit viscous step of Sec. 3.2.3 (Eq. muelliptic) is in ``viscous.py``
 (numpy and scipy.sparse, FP64); the capillary (Eq. csf2) and gravity forcing
 of the predictor (Eq. nonconspredictedvel) in ``forcing.py`` (numpy, FP64).
 """
@@ -86,6 +88,9 @@ def _load():
             lib.oracle_project.argtypes = [G, _D, _D, _D, _D, ct.c_double, _D, _D, _D]
             lib.oracle_face_gradient.argtypes = [G, _D, _D, _D, _D]
             lib.oracle_remove_mean.argtypes = [ct.c_int64, _D]
+            lib.oracle_null_project.argtypes = [ct.c_int64, _D, ct.c_void_p]
+            lib.oracle_cg_masked.argtypes = [P, _D, _D, ct.c_double, ct.c_int, ct.c_int, _D, ct.c_int,
+                                             ct.c_void_p, ct.POINTER(_CGStats)]
             lib.oracle_sum.argtypes = [ct.c_int64, _D]
             lib.oracle_sum.restype = ct.c_double
             lib.oracle_dot.argtypes = [ct.c_int64, _D, _D]
@@ -239,15 +244,28 @@ class CGResult:
         return float(ev[0]), float(ev[-1])
 
 
-def cg(op: Operator, rhs, x0=None, tol=1e-13, max_iter=200000, check=50, keep_coef=4000):
-    """Unpreconditioned CG on A x = rhs (rhs must be mean-free)."""
+def null_project(x, fluid=None):
+    """Remove the null-space part of x: the mean (no solid), or with a solid
+    mask (fluid = 1 outside the solid, Sec. 3.8) the mean over the fluid
+    cells, and 0 in the solid cells."""
+    lib = _load()
+    x = _c(x).copy()
+    fl = None if fluid is None else np.ascontiguousarray(fluid, dtype=np.uint8)
+    lib.oracle_null_project(x.size, _p(x), None if fl is None else fl.ctypes.data)
+    return x
+
+
+def cg(op: Operator, rhs, x0=None, tol=1e-13, max_iter=200000, check=50, keep_coef=4000, fluid=None):
+    """Unpreconditioned CG on A x = rhs (rhs must be orthogonal to the null
+    space: mean-free, and with a solid mask zero in the solid cells)."""
     lib = op.lib
     rhs = _c(rhs)
     x = np.zeros_like(rhs) if x0 is None else _c(x0).copy()
     coef = np.zeros(2 * keep_coef)
     st = _CGStats()
-    lib.oracle_cg(op.ptr, _p(rhs), _p(x), float(tol), int(max_iter), int(check), _p(coef),
-                  int(keep_coef), ct.byref(st))
+    fl = None if fluid is None else np.ascontiguousarray(fluid, dtype=np.uint8)
+    lib.oracle_cg_masked(op.ptr, _p(rhs), _p(x), float(tol), int(max_iter), int(check), _p(coef),
+                         int(keep_coef), None if fl is None else fl.ctypes.data, ct.byref(st))
     nc = st.n_coef
     return CGResult(x, st.iters, bool(st.stagnated), st.rel_res_l2, st.rel_res_linf,
                     coef[0:2 * nc:2].copy(), coef[1:2 * nc:2].copy())

@@ -159,6 +159,37 @@ void oracle_remove_mean(int64_t n, double* x) {
     for (int64_t q = 0; q < n; ++q) x[q] -= m;
 }
 
+/* Projection onto the complement of the null space of the operator with
+ * solid cells (Sec. 3.8): every coefficient of a solid cell is zeroed, so each
+ * solid cell is a null vector on its own, and the constants on the fluid
+ * cells are the other one (a connected fluid region).  fluid[c] = 1 outside
+ * the solid (the paper's flag s), 0 inside; NULL means no solid, and the
+ * projection is the mean removal above.  Fluid cells lose their mean over
+ * the fluid cells, solid cells are set to 0. */
+void oracle_null_project(int64_t n, double* x, const unsigned char* fluid) {
+    if (!fluid) {
+        oracle_remove_mean(n, x);
+        return;
+    }
+    int64_t nb = (n + OR_BLOCK - 1) / OR_BLOCK;
+    double* part = (double*)malloc(sizeof(double) * 2 * (nb > 0 ? nb : 1));
+    #pragma omp parallel for schedule(static)
+    for (int64_t blk = 0; blk < nb; ++blk) {
+        int64_t s = blk * OR_BLOCK, e = s + OR_BLOCK < n ? s + OR_BLOCK : n;
+        double acc = 0.0, cnt = 0.0;
+        for (int64_t q = s; q < e; ++q)
+            if (fluid[q]) { acc += x[q]; cnt += 1.0; }
+        part[2 * blk] = acc;
+        part[2 * blk + 1] = cnt;
+    }
+    double t = 0.0, c = 0.0;
+    for (int64_t blk = 0; blk < nb; ++blk) { t += part[2 * blk]; c += part[2 * blk + 1]; }
+    free(part);
+    double m = c > 0.0 ? t / c : 0.0;
+    #pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < n; ++q) x[q] = fluid[q] ? x[q] - m : 0.0;
+}
+
 /* ------------------------------------------------ face coefficients --- */
 
 /* Eq. muH gives the cell density from the volume fraction; the paper builds
@@ -339,14 +370,17 @@ static double max_abs(int64_t n, const double* a) {
  * residual of unpreconditioned CG (which minimises the A-norm of the error,
  * not the residual) can sit on a plateau, or rise, for thousands of steps
  * before it falls on strongly layered densities.
+ * With solid cells (fluid != NULL, Sec. 3.8) the projections above are onto
+ * the complement of the masked operator's null space (oracle_null_project).
  * The CG step lengths alpha_k and ratios beta_k of the first cycle are stored
  * in coef[2k], coef[2k+1] (up to max_coef pairs): they define the Lanczos
  * tridiagonal matrix whose eigenvalues estimate the extreme eigenvalues of A. */
 #define OR_STALL 20
 #define OR_MAX_RESTARTS 3
 #define OR_STALL_FLOOR 1e-8
-void oracle_cg(const or_csr* A, const double* rhs, double* x, double tol, int max_iter,
-               int check, double* coef, int max_coef, or_cg_stats* st) {
+void oracle_cg_masked(const or_csr* A, const double* rhs, double* x, double tol, int max_iter,
+                      int check, double* coef, int max_coef, const unsigned char* fluid,
+                      or_cg_stats* st) {
     int64_t n = A->n;
     double* r = (double*)malloc(sizeof(double) * n);
     double* d = (double*)malloc(sizeof(double) * n);
@@ -363,11 +397,11 @@ void oracle_cg(const or_csr* A, const double* rhs, double* x, double tol, int ma
         free(r); free(d); free(q); free(t);
         return;
     }
-    oracle_remove_mean(n, x);
+    oracle_null_project(n, x, fluid);
     oracle_csr_matvec(A, x, q);
     #pragma omp parallel for schedule(static)
     for (int64_t c = 0; c < n; ++c) r[c] = rhs[c] - q[c];
-    oracle_remove_mean(n, r);
+    oracle_null_project(n, r, fluid);
     memcpy(d, r, sizeof(double) * n);
     double rr = det_dot(n, r, r);
     if (sqrt(rr) / bnorm > tol) {
@@ -381,7 +415,7 @@ void oracle_cg(const or_csr* A, const double* rhs, double* x, double tol, int ma
             /* keep the residual in the range of A (mean-free): the rounding of A d
              * leaves a constant part in r that A cannot remove, and over many steps
              * it grows until d . A d is no longer positive */
-            oracle_remove_mean(n, r);
+            oracle_null_project(n, r, fluid);
             double rr_new = det_dot(n, r, r);
             double beta = rr_new / rr;
             if (coef && first_cycle && ncoef < max_coef) {
@@ -393,7 +427,7 @@ void oracle_cg(const or_csr* A, const double* rhs, double* x, double tol, int ma
             ++it;
             int rec_done = sqrt(rr) / bnorm <= tol;
             if (it % check == 0 || rec_done) {
-                oracle_remove_mean(n, x);
+                oracle_null_project(n, x, fluid);
                 oracle_csr_matvec(A, x, q);
                 #pragma omp parallel for schedule(static)
                 for (int64_t c = 0; c < n; ++c) t[c] = rhs[c] - q[c];
@@ -413,7 +447,7 @@ void oracle_cg(const or_csr* A, const double* rhs, double* x, double tol, int ma
                     first_cycle = 0;
                     #pragma omp parallel for schedule(static)
                     for (int64_t c = 0; c < n; ++c) r[c] = t[c];
-                    oracle_remove_mean(n, r);
+                    oracle_null_project(n, r, fluid);
                     memcpy(d, r, sizeof(double) * n);
                     rr = det_dot(n, r, r);
                 }
@@ -421,7 +455,7 @@ void oracle_cg(const or_csr* A, const double* rhs, double* x, double tol, int ma
         }
     }
     /* final true residual */
-    oracle_remove_mean(n, x);
+    oracle_null_project(n, x, fluid);
     oracle_csr_matvec(A, x, q);
     for (int64_t c = 0; c < n; ++c) r[c] = rhs[c] - q[c];
     st->iters = it;
@@ -430,6 +464,11 @@ void oracle_cg(const or_csr* A, const double* rhs, double* x, double tol, int ma
     st->rel_res_linf = max_abs(n, r) / binf;
     st->n_coef = ncoef;
     free(r); free(d); free(q); free(t);
+}
+
+void oracle_cg(const or_csr* A, const double* rhs, double* x, double tol, int max_iter,
+               int check, double* coef, int max_coef, or_cg_stats* st) {
+    oracle_cg_masked(A, rhs, x, tol, max_iter, check, coef, max_coef, NULL, st);
 }
 
 /* ------------------------------------------------ velocity correction --- */
