@@ -842,6 +842,7 @@ def run_forcing(args):
     for _ in range(args.warmup):
         refill()
         forced(0)
+        refill()
         plain(0)
     refill()
     with ClockSampler(0) as clk:

@@ -296,6 +296,31 @@ paris_status paris_projection_step_forced(paris_ctx* ctx, const double* C, const
                                           paris_stats* st);
 
 /* ---------------------------------------------------------------------------
+ * SOLID CELLS (Sec. 3.8, "Lego" solids).  A cell flag s, 1 outside the
+ * solid and 0 inside, makes every face whose two cells are not both fluid a
+ * closed link: its face coefficient is zeroed (a Neumann condition for p on
+ * the solid's boundary), it carries no flux in the divergence, and the
+ * velocity correction leaves u = 0 there.  (The paper's printed
+ * initialisation takes a face's flag from one of its cells; its text asks
+ * that the solid region and its boundary be blocked, which needs both.)
+ * Solid cells have no open face, so their pressure is not determined: the
+ * solve reports p = 0 there and makes p mean-free over the fluid cells.  The
+ * fluid region should be connected: a region cut into parts leaves one free
+ * constant per part (the paper's warning that a solid must not make the
+ * system ill-posed).
+ *
+ * paris_set_solid(ctx, s): s is a DEVICE array of nx*ny*nz bytes owned by
+ * the caller (cell layout, nonzero = fluid) that must stay valid and
+ * unchanged while it is set; NULL clears it.  While set, paris_face_coeffs,
+ * paris_divergence, paris_poisson_solve, paris_project and the projection
+ * steps apply it; the mixed form then runs its finest level from FP32 face
+ * coefficients (level0_density is not used).  paris_project_adjoint returns
+ * INVALID_ARG while a solid is set.  The call counts the fluid cells and
+ * synchronises the stream.  Errors: INVALID_ARG (null ctx, no fluid cell),
+ * CUDA. */
+paris_status paris_set_solid(paris_ctx* ctx, const unsigned char* s);
+
+/* ---------------------------------------------------------------------------
  * IMPLICIT VISCOUS STEP (Sec. 3.2.3, Eq. muelliptic).  For one velocity
  * component, u* - tau nu_f Lap_h u* = u^n on the component's own face grid,
  * Lap_h the 7-point Laplacian with spacing h.  The unknowns are the
@@ -338,6 +363,22 @@ paris_status paris_face_viscosity(paris_ctx* ctx, int comp, const double* C, dou
 paris_status paris_viscous_solve(paris_ctx* ctx, int comp, const double* nu, double tau,
                                  const double* un, double* us, double tol, int max_iter,
                                  paris_stats* st);
+
+/* The same solve (same arguments, stopping test and outputs) by flexible
+ * CG in FP64 preconditioned by an FP32 geometric-multigrid V-cycle of the
+ * component's operator: every axis halved per level (cell-centred along
+ * periodic and no-slip axes, vertex-centred along the component's own wall
+ * axis, with linear interpolation and full weighting there), rediscretised
+ * coarse operators with the restricted mass term 1/(tau nu), red-black
+ * Gauss-Seidel with the context's nu1/nu2 sweeps and omega (damped Jacobi on
+ * a level with an odd periodic extent), 8 sweeps on the coarsest level.
+ * The first call on a context allocates the multigrid's work arrays (about
+ * 4 x 4 x 8/7 bytes per cell plus 8 per cell); later calls allocate
+ * nothing.  st->levels: the multigrid levels.  Errors: as
+ * paris_viscous_solve, and NO_MEMORY on the first call. */
+paris_status paris_viscous_solve_mg(paris_ctx* ctx, int comp, const double* nu, double tau,
+                                    const double* un, double* us, double tol, int max_iter,
+                                    paris_stats* st);
 
 /* ---------------------------------------------------------------------------
  * BATCHED PROJECTIONS.  Many independent projection steps of uneven grid

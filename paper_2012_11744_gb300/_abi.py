@@ -88,8 +88,10 @@ SIGNATURES = {
     "paris_predictor_forcing": (ct.c_int, [_P, _P, _P, _D, _D, _D, _D, _D, _D, _D, _P, _P, _P, _P, _P, _P]),
     "paris_projection_step_forced": (ct.c_int, [_P, _P, _P, _D, _D, _D, _D, _D, _D, _D, _P, _P, _P, _P,
                                                 ct.POINTER(Stats)]),
+    "paris_set_solid": (ct.c_int, [_P, _P]),
     "paris_face_viscosity": (ct.c_int, [_P, ct.c_int, _P, _D, _D, _D, _D, _P]),
     "paris_viscous_solve": (ct.c_int, [_P, ct.c_int, _P, _D, _P, _P, _D, ct.c_int, ct.POINTER(Stats)]),
+    "paris_viscous_solve_mg": (ct.c_int, [_P, ct.c_int, _P, _D, _P, _P, _D, ct.c_int, ct.POINTER(Stats)]),
     "paris_batch_create": (ct.c_int, [ct.POINTER(_P), ct.c_int, ct.POINTER(Grid), ct.POINTER(Opts), _P]),
     "paris_batch_destroy": (ct.c_int, [_P]),
     "paris_batch_layout": (ct.c_int, [_P, ct.POINTER(ct.c_int64), ct.POINTER(ct.c_int64),

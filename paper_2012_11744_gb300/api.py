@@ -220,6 +220,21 @@ class Context:
         d["status"] = s
         return d
 
+    def set_solid(self, s):
+        """Solid cells (Sec. 3.8): s a uint8 tensor of the cell shape on the
+        context's device, nonzero = fluid, or None to clear.  The context
+        keeps a reference to s while it is set."""
+        g = self.grid
+        if s is None:
+            _abi.check(self.lib.paris_set_solid(self._ptr, ct.c_void_p(None)), "paris_set_solid")
+            self._solid = None
+            return
+        n = int(np.prod(g.shape))
+        if s.dtype != torch.uint8 or not s.is_contiguous() or s.device != self.device or s.numel() != n:
+            raise ValueError(f"s: need a contiguous uint8 tensor of {n} cells on {self.device}")
+        _abi.check(self.lib.paris_set_solid(self._ptr, ct.c_void_p(s.data_ptr())), "paris_set_solid")
+        self._solid = s
+
     def predictor_forcing(self, C, kappa, rho1, rho2, sigma, gravity, tau, u, v, w, beta=None):
         """Capillary (CSF) and gravity forcing of the predictor: u, v, w (in
         u^n, out u* = u^n + tau a_f) in place; returns the face coefficients
@@ -335,18 +350,20 @@ class Context:
                    "paris_face_viscosity")
         return nu
 
-    def viscous_solve(self, comp, nu, tau, un, us=None, tol=1e-12, max_iter=10000, check=True):
+    def viscous_solve(self, comp, nu, tau, un, us=None, tol=1e-12, max_iter=10000, check=True, multigrid=False):
         """u* - tau nu Lap_h u* = u^n for component comp (Eq. muelliptic) on its
-        face array; returns (us, stats dict)."""
+        face array; returns (us, stats dict).  multigrid: the V-cycle-
+        preconditioned flexible CG (paris_viscous_solve_mg) instead of the
+        Jacobi-preconditioned CG."""
         g = self.grid
         fs = g.face_shape(comp)
         us = us if us is not None else torch.empty(fs, dtype=torch.float64, device=self.device)
         st = _abi.Stats()
-        s = self.lib.paris_viscous_solve(self._ptr, int(comp), self._t(nu, fs, "nu"), float(tau),
-                                         self._t(un, fs, "un"), self._t(us, fs, "us"), float(tol),
-                                         int(max_iter), ct.byref(st))
+        fn = self.lib.paris_viscous_solve_mg if multigrid else self.lib.paris_viscous_solve
+        s = fn(self._ptr, int(comp), self._t(nu, fs, "nu"), float(tau), self._t(un, fs, "un"),
+               self._t(us, fs, "us"), float(tol), int(max_iter), ct.byref(st))
         if check:
-            _abi.check(s, "paris_viscous_solve", st.as_dict())
+            _abi.check(s, "paris_viscous_solve_mg" if multigrid else "paris_viscous_solve", st.as_dict())
         d = st.as_dict()
         d["status"] = s
         return us, d

@@ -401,16 +401,18 @@ int64_t launch_max_divergence(const Geo& g, const double* u, const double* v, co
     return nblocks_of(gr);
 }
 
-// f = -(rhs - mean_b): the right-hand side of the SPD system A p = f.
+// f = -(rhs - mean_b): the right-hand side of the SPD system A p = f; with
+// solid cells (solid[c] == 0, Sec. 3.8) f = 0 there, each such cell being a
+// null direction of the masked operator on its own.
 __global__ void make_rhs_kernel(int64_t n, const double* __restrict__ rhs, const Scal* s,
                                 double* __restrict__ f, const double* __restrict__ x0,
-                                double* partials, FinSpec fin) {
+                                double* partials, FinSpec fin, const unsigned char* __restrict__ solid) {
     const double mb = s->mean_b;
     double l2 = 0.0;
     unsigned long long fmax_k = 0, xmax_k = 0;
     unsigned nf = 0;
     PARIS_EW_FOR(c, n) {
-        const double t = -(rhs[c] - mb);
+        const double t = (solid && !solid[c]) ? 0.0 : -(rhs[c] - mb);
         f[c] = t;
         l2 = fma(t, t, l2);
         const unsigned long long k = abs_key(t);
@@ -429,9 +431,9 @@ __global__ void make_rhs_kernel(int64_t n, const double* __restrict__ rhs, const
 }
 
 int64_t launch_make_rhs(int64_t n, const double* rhs, const Scal* s, double* f, const double* x0,
-                        double* partials, cudaStream_t st, FinSpec fin) {
+                        double* partials, cudaStream_t st, FinSpec fin, const unsigned char* solid) {
     int nb = elementwise_blocks(n);
-    make_rhs_kernel<<<nb, kRedThreads, 0, st>>>(n, rhs, s, f, x0, partials, fin);
+    make_rhs_kernel<<<nb, kRedThreads, 0, st>>>(n, rhs, s, f, x0, partials, fin, solid);
     count_launch();
     return nb;
 }
@@ -634,8 +636,18 @@ __global__ void __launch_bounds__(1024) coarse_inverse_kernel(Geo g, Coef<T> cf,
         dsum = t;
     }
     __syncthreads();
+    // a cell with no open face (inside a solid, Sec. 3.8) has a zero row and
+    // column: it is decoupled as an identity row and kept out of the
+    // regularisation, which then acts on the constants of the other cells
     const double a = dsum / ((double)n * (double)n);
-    for (int e = tid; e < n * n; e += nt) M[e] += a;
+    for (int e = tid; e < n * n; e += nt) {
+        const int r = e / n, cc = e % n;
+        const bool ir = M[r * n + r] == 0.0, ic = M[cc * n + cc] == 0.0;
+        if (!ir && !ic) M[e] += a;
+    }
+    __syncthreads();
+    for (int c = tid; c < n; c += nt)
+        if (M[c * n + c] == 0.0) M[c * n + c] = 1.0;
     __syncthreads();
     for (int kk = 0; kk < n; ++kk) {
         if (tid == 0) piv = 1.0 / M[kk * n + kk];

@@ -39,7 +39,8 @@ enum FinalizeMode {
     FIN_SCALE = 8,      // scale = 1/max(result1, tiny), rr0 = rr*scale^2 ... (mixed)
     FIN_INNER_INIT = 9, // rr0 = result0, rr = result0
     FIN_REFINE = 10,    // scale from the current rinf, then rr = result0 / scale^2, rinf = result1
-    FIN_RNORMS_RHO = 11 // rr = result0, rinf = result1, beta = result3 / rho, rho = result3 (Jacobi PCG)
+    FIN_RNORMS_RHO = 11, // rr = result0, rinf = result1, beta = result3 / rho, rho = result3 (Jacobi PCG)
+    FIN_MEAN_FLUID = 12  // mean_b = result0 / result1 (a sum and a count over the fluid cells)
 };
 
 // Second stage of a reduction, by one block of kRedThreads threads: fold the
@@ -111,6 +112,7 @@ __device__ inline void finalize_block(const double* partials, int64_t nblocks, i
             case FIN_ALPHA: s->alpha = (r[0] > 0.0) ? s->rho / r[0] : 0.0; break;
             case FIN_RHO_BETA: s->beta = (s->rho != 0.0) ? r[0] / s->rho : 0.0; s->rho = r[0]; break;
             case FIN_RHO_INIT: s->rho = r[0]; s->beta = 0.0; break;
+            case FIN_MEAN_FLUID: s->mean_b = r[1] > 0.0 ? r[0] / r[1] : 0.0; break;
             case FIN_FCG_BETA:
                 s->beta = (s->rho != 0.0) ? -s->alpha * r[1] / s->rho : 0.0;
                 s->rho = r[0];
@@ -180,6 +182,29 @@ long long launch_count();
 void finalize(const double* partials, int64_t nblocks, int nv, int maxmask, Scal* s, int mode,
               double param, cudaStream_t st);
 
+// ------------------------------------------------------------ solid cells ---
+// Sec. 3.8 "Lego" solids (solid.cu): s = 1 outside the solid, 0 inside; a
+// face is open when both of its cells are fluid.
+// beta and/or u zeroed on every closed face (pointers may be null)
+void launch_link_block(const Geo& g, const unsigned char* s, double* bx, double* by, double* bz, double* u,
+                       double* v, double* w, cudaStream_t st);
+// rhs = div u/(h dt) with closed faces carrying no flux, 0 in solid cells;
+// partials (sum, max |rhs|, non-finite count) on the divergence's grid
+int64_t launch_masked_divergence(const Geo& g, const unsigned char* s, const double* u, const double* v,
+                                 const double* w, double inv_hdt, double* rhs, double* partials, cudaStream_t st,
+                                 FinSpec fin);
+// x <- x - (mean over the fluid cells), 0 in solid cells (the gauge)
+void launch_fluid_gauge(int64_t n, const unsigned char* s, double* x, double* partials, Scal* sc, cudaStream_t st);
+// x <- x - sc->mean_b on fluid cells, 0 in solid cells
+void launch_fluid_sub_mean(int64_t n, const unsigned char* s, double* x, const Scal* sc, cudaStream_t st);
+// sc->mean_b = mean of x over the fluid cells
+void launch_fluid_mean(int64_t n, const unsigned char* s, const double* x, double* partials, Scal* sc,
+                       cudaStream_t st);
+// x <- 0 in solid cells
+void launch_solid_zero(int64_t n, const unsigned char* s, double* x, cudaStream_t st);
+// sc->red[1] = number of fluid cells; returns the blocks used
+int64_t launch_fluid_count(int64_t n, const unsigned char* s, double* partials, Scal* sc, cudaStream_t st);
+
 // ------------------------------------------------- implicit viscous step ---
 // One velocity component of Sec. 3.2.3 (Eq. muelliptic) in SPD form,
 // (diag(1/(tau nu)) - Lap_h) u* = u^n/(tau nu), on its unknowns (viscous.cu).
@@ -196,6 +221,48 @@ struct HelmGeo {
     double ih2;   // 1/h^2
 };
 HelmGeo helm_geo(const Geo& g0, int comp, double h);
+
+// Multigrid preconditioner of the viscous step (helmmg.cu): per level the
+// unknowns per axis, the axis kinds and 1/h_l^2; the FP32 work arrays.
+constexpr int kHelmMaxLevels = 10;
+struct HelmLevelDesc {
+    int m[3];
+    int kind[3];
+    double ih2;
+};
+struct HelmPlan {
+    int nl;
+    HelmLevelDesc lv[kHelmMaxLevels];
+};
+struct HelmWork {
+    float* x[kHelmMaxLevels];
+    float* f[kHelmMaxLevels];
+    float* r[kHelmMaxLevels];
+    float* sig[kHelmMaxLevels];
+    double* sig64;
+};
+// coarsen every axis together while each can (periodic / no-slip: even and
+// >= 4; the component's own wall axis: odd and >= 5)
+HelmPlan helm_plan(const HelmGeo& g, int max_levels);
+// sigma = 1/(tau nu) (FP64 and level-0 FP32), u* = u^n on the unknowns and 0
+// on the own wall faces; partials of |b|^2, max |b|, non-finite (b = sigma u^n)
+int64_t launch_hmg_setup(const HelmGeo& g, const double* un, const double* nu, double tau, double* sig64,
+                         float* sig32, double* us, double* partials, cudaStream_t st, FinSpec fin);
+// the coarse levels' sigma by restriction
+void launch_hmg_sigma(const HelmPlan& P, float* const* sig, cudaStream_t st);
+// r = sigma u^n - A u*; partials (|r|^2, max |r|, non-finite)
+int64_t launch_hmg_residual64(const HelmGeo& g, const double* un, const double* sig, const double* us, double* r,
+                              double* partials, cudaStream_t st, FinSpec fin);
+// q = A d; partials (d . q)
+int64_t launch_hmg_matvec64(const HelmGeo& g, const double* sig, const double* d, double* q, double* partials,
+                            cudaStream_t st, FinSpec fin);
+// u* += alpha d, r -= alpha q; partials (|r|^2, max |r|, non-finite)
+int64_t launch_hmg_update64(const HelmGeo& g, const Scal* s, const double* d, const double* q, double* us, double* r,
+                            double* partials, cudaStream_t st, FinSpec fin);
+// z = V r (FP32 V-cycle; nu1/nu2 sweeps down/up, coarse_sweeps on the coarsest)
+void launch_hmg_vcycle(const HelmPlan& P, const HelmWork& W, const double* r, double* z, int nu1, int nu2,
+                       int coarse_sweeps, float omega, cudaStream_t st);
+int64_t helm_max_blocks(const HelmGeo& g);
 int64_t helm_unknowns(const HelmGeo& g);
 int64_t helm_faces(const HelmGeo& g);
 // us = un on the unknowns, 0 on the wall faces; partials (|b|^2, max|b|,
@@ -238,7 +305,7 @@ int64_t launch_divergence(const Geo& g, const double* u, const double* v, const 
 // f = -(rhs - mean_b), partials: (||f||^2, max|f|, nonfinite, max|x0|); x0 (the
 // initial guess) may be null
 int64_t launch_make_rhs(int64_t n, const double* rhs, const Scal* s, double* f, const double* x0,
-                        double* partials, cudaStream_t st, FinSpec fin = no_fin());
+                        double* partials, cudaStream_t st, FinSpec fin = no_fin(), const unsigned char* solid = nullptr);
 void launch_sub_mean(int64_t n, double* x, const Scal* s, cudaStream_t st);
 int64_t launch_sum(int64_t n, const double* x, double* partials, cudaStream_t st);
 void launch_project(const Geo& g, const double* bx, const double* by, const double* bz,

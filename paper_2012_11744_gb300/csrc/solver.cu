@@ -102,6 +102,12 @@ struct paris_ctx {
     float* rh32 = nullptr;
     float2* rh2 = nullptr;  // rho/2 as (hi, lo) FP32 pairs for the refinement step
     bool rho0 = false;  // the current solve's level-0 FP32 kernels read rh32 instead of b32_0
+    // solid cells (Sec. 3.8): the caller's cell flags (1 fluid, 0 solid), or null
+    const unsigned char* solid = nullptr;
+    double n_fluid = 0.0;  // fluid cells (with solid set)
+    // viscous-step multigrid work arrays (allocated on the first paris_viscous_solve_mg)
+    HelmWork hmg{};
+    std::vector<void*> hw_mem;
     double* partials = nullptr;
     Scal* scal = nullptr;
     Scal* scal_h = nullptr;  // pinned host mirror
@@ -649,11 +655,15 @@ bool meets(const paris_ctx* c, const Scal& s) {
 paris_status prologue(paris_ctx* c, const double* rhs, const double* x0, bool mean_known) {
     int64_t nb;
     if (!mean_known) {
-        nb = launch_sum(c->N, rhs, c->partials, c->st);
-        finalize(c->partials, nb, 3, 2, c->scal, FIN_MEAN_B, (double)c->N, c->st);
+        if (c->solid) {  // the mean over the fluid cells (the masked operator's constant mode)
+            launch_fluid_mean(c->N, c->solid, rhs, c->partials, c->scal, c->st);
+        } else {
+            nb = launch_sum(c->N, rhs, c->partials, c->st);
+            finalize(c->partials, nb, 3, 2, c->scal, FIN_MEAN_B, (double)c->N, c->st);
+        }
     }
-    launch_make_rhs(c->N, rhs, c->scal, c->f, x0, c->partials, c->st,
-                    FinSpec{c->scal, 4, 0xA, FIN_BNORMS, 0.0});
+    launch_make_rhs(c->N, rhs, c->scal, c->f, x0, c->partials, c->st, FinSpec{c->scal, 4, 0xA, FIN_BNORMS, 0.0},
+                    c->solid);
     CK(cudaGetLastError());
     return PARIS_OK;
 }
@@ -733,7 +743,7 @@ paris_status solve_fp64(paris_ctx* c, const Coef<double>& c64, double* x, SolveO
 bool rho0_usable(const paris_ctx* c) {
     const paris_opts& o = c->opts;
     if (!o.level0_density || o.precision != PARIS_MIXED || o.smoother != PARIS_SMOOTH_RBGS_2PASS ||
-        o.half_coefficients || !c->rh32 || !c->rh2 || c->lv.size() < 3)
+        o.half_coefficients || !c->rh32 || !c->rh2 || c->lv.size() < 3 || c->solid)
         return false;
     const Level& L1 = c->lv[1];
     return L1.fac[0] == 2 && L1.fac[1] == 2 && L1.fac[2] == 2;
@@ -938,6 +948,7 @@ paris_status paris_destroy(paris_ctx* c) {
     for (auto& e : c->copy_ev)
         if (e) cudaEventDestroy(e);
     c->mem.release();
+    for (void* q : c->hw_mem) cudaFree(q);
     if (c->scal_h) cudaFreeHost(c->scal_h);
     for (auto& e : c->prof.ev) cudaEventDestroy(e);
     delete c;
@@ -1016,6 +1027,7 @@ paris_status paris_face_coeffs(paris_ctx* c, const double* C, double rho1, doubl
     if (!(rho1 > 0.0) || !(rho2 > 0.0) || !std::isfinite(rho1) || !std::isfinite(rho2))
         return PARIS_ERR_INVALID_ARG;
     launch_face_coeffs(c->g0, C, rho1, rho2, bx, by, bz, nullptr, nullptr, c->st);
+    if (c->solid) launch_link_block(c->g0, c->solid, bx, by, bz, nullptr, nullptr, nullptr, c->st);
     CK(cudaGetLastError());
     return PARIS_OK;
 }
@@ -1024,9 +1036,16 @@ paris_status paris_divergence(paris_ctx* c, const double* u, const double* v, co
                               double dt, double* rhs, double* mean_removed) {
     if (!c || !u || !v || !w || !rhs) return PARIS_ERR_INVALID_ARG;
     if (!(dt > 0.0) || !std::isfinite(dt)) return PARIS_ERR_INVALID_ARG;
-    int64_t nb = launch_divergence(c->g0, u, v, w, 1.0 / (c->grid.h * dt), rhs, c->partials, c->st);
-    finalize(c->partials, nb, 3, 2, c->scal, FIN_MEAN_B, (double)c->N, c->st);
-    launch_sub_mean(c->N, rhs, c->scal, c->st);
+    if (c->solid) {  // closed faces carry no flux; the mean over the fluid cells
+        int64_t nb = launch_masked_divergence(c->g0, c->solid, u, v, w, 1.0 / (c->grid.h * dt), rhs, c->partials,
+                                              c->st, no_fin());
+        finalize(c->partials, nb, 3, 2, c->scal, FIN_MEAN_B, c->n_fluid, c->st);
+        launch_fluid_sub_mean(c->N, c->solid, rhs, c->scal, c->st);
+    } else {
+        int64_t nb = launch_divergence(c->g0, u, v, w, 1.0 / (c->grid.h * dt), rhs, c->partials, c->st);
+        finalize(c->partials, nb, 3, 2, c->scal, FIN_MEAN_B, (double)c->N, c->st);
+        launch_sub_mean(c->N, rhs, c->scal, c->st);
+    }
     CK(cudaGetLastError());
     if (mean_removed) {
         paris_status s = read_scal(c);
@@ -1077,7 +1096,13 @@ paris_status poisson_solve(paris_ctx* c, const double* bx, const double* by, con
     }
     {
         ProfScope ps(c, PARIS_K_PROJECT, 0.0);
-        s = remove_mean(c, p, c->N);
+        if (c->solid) {  // fluid mean 0, solid cells 0 (their p is not determined)
+            launch_fluid_gauge(c->N, c->solid, p, c->partials, c->scal, c->st);
+            CK(cudaGetLastError());
+            s = PARIS_OK;
+        } else {
+            s = remove_mean(c, p, c->N);
+        }
     }
     if (s != PARIS_OK) return s;
     s = read_scal(c);
@@ -1113,6 +1138,7 @@ paris_status paris_project(paris_ctx* c, const double* bx, const double* by, con
     if (!c || !bx || !by || !bz || !p || !u || !v || !w) return PARIS_ERR_INVALID_ARG;
     if (!(dt > 0.0) || !std::isfinite(dt)) return PARIS_ERR_INVALID_ARG;
     launch_project(c->g0, bx, by, bz, p, dt / c->grid.h, u, v, w, c->st);
+    if (c->solid) launch_link_block(c->g0, c->solid, nullptr, nullptr, nullptr, u, v, w, c->st);  // blocked
     CK(cudaGetLastError());
     return PARIS_OK;
 }
@@ -1141,6 +1167,8 @@ paris_status projection_step_impl(paris_ctx* c, const double* C, double rho1, do
         if (hl) CK(cudaStreamWaitEvent(c->st, hl->c_ready, 0));
         launch_face_coeffs(c->g0, C, rho1, rho2, c->beta[0], c->beta[1], c->beta[2],
                            use_rho0 ? c->rh32 : nullptr, use_rho0 ? c->rh2 : nullptr, c->st, force);
+        if (c->solid)
+            launch_link_block(c->g0, c->solid, c->beta[0], c->beta[1], c->beta[2], nullptr, nullptr, nullptr, c->st);
         CK(cudaGetLastError());
     }
     if (c->opts.precision == PARIS_MIXED) {
@@ -1157,9 +1185,15 @@ paris_status projection_step_impl(paris_ctx* c, const double* C, double rho1, do
         // f = -(rhs - mean) directly (no separate mean removal pass)
         CK(cudaMemsetAsync(c->scal, 0, sizeof(Scal), c->st));
         if (hl) CK(cudaStreamWaitEvent(c->st, hl->uvw_ready, 0));
-        const int64_t nb =
-            launch_divergence(c->g0, u, v, w, 1.0 / (c->grid.h * dt), c->rhs, c->partials, c->st);
-        finalize(c->partials, nb, 3, 2, c->scal, FIN_MEAN_B, (double)c->N, c->st);
+        if (c->solid) {  // closed faces carry no flux; the mean over the fluid cells
+            const int64_t nb = launch_masked_divergence(c->g0, c->solid, u, v, w, 1.0 / (c->grid.h * dt), c->rhs,
+                                                        c->partials, c->st, no_fin());
+            finalize(c->partials, nb, 3, 2, c->scal, FIN_MEAN_B, c->n_fluid, c->st);
+        } else {
+            const int64_t nb =
+                launch_divergence(c->g0, u, v, w, 1.0 / (c->grid.h * dt), c->rhs, c->partials, c->st);
+            finalize(c->partials, nb, 3, 2, c->scal, FIN_MEAN_B, (double)c->N, c->st);
+        }
         CK(cudaGetLastError());
     }
     if (hl) CK(cudaStreamWaitEvent(c->st, hl->p_ready, 0));
@@ -1189,6 +1223,24 @@ paris_status paris_projection_step(paris_ctx* c, const double* C, double rho1, d
         return PARIS_ERR_INVALID_ARG;
     if (!(dt > 0.0) || !std::isfinite(dt)) return PARIS_ERR_INVALID_ARG;
     return projection_step_impl(c, C, rho1, rho2, dt, u, v, w, p, st, nullptr);
+}
+
+paris_status paris_set_solid(paris_ctx* c, const unsigned char* s) {
+    if (!c) return PARIS_ERR_INVALID_ARG;
+    if (!s) {
+        c->solid = nullptr;
+        c->n_fluid = 0.0;
+        return PARIS_OK;
+    }
+    launch_fluid_count(c->N, s, c->partials, c->scal, c->st);
+    CK(cudaGetLastError());
+    paris_status st = read_scal(c);
+    if (st != PARIS_OK) return st;
+    const double n = c->scal_h->red[1];
+    if (!(n >= 1.0)) return PARIS_ERR_INVALID_ARG;  // no fluid cell
+    c->solid = s;
+    c->n_fluid = n;
+    return PARIS_OK;
 }
 
 static bool valid_forcing(double sigma, double gx, double gy, double gz) {
@@ -1297,6 +1349,7 @@ paris_status paris_project_adjoint(paris_ctx* c, const double* bx, const double*
         !gbz || !q)
         return PARIS_ERR_INVALID_ARG;
     if (!(dt > 0.0) || !std::isfinite(dt)) return PARIS_ERR_INVALID_ARG;
+    if (c->solid) return PARIS_ERR_INVALID_ARG;  // the adjoint of the blocking is not built
     const double inv_h = 1.0 / c->grid.h;
     // right-hand side of the adjoint solve: D (B g)
     launch_weighted_div(c->g0, bx, by, bz, gu, gv, gw, inv_h, c->rhs, c->partials, c->st);
@@ -1444,6 +1497,109 @@ paris_status paris_viscous_solve(paris_ctx* c, int comp, const double* nu, doubl
         st->rel_res_l2 = h.bnorm2 > 0 ? std::sqrt(h.rr / h.bnorm2) : 0.0;
         st->rel_res_linf = h.binf > 0 ? h.rinf / h.binf : 0.0;
         st->converged = converged ? 1 : 0;
+    }
+    if (nonfinite) return PARIS_ERR_NONFINITE;
+    return converged ? PARIS_OK : PARIS_ERR_NOT_CONVERGED;
+}
+
+// The viscous multigrid's work arrays, allocated once per context: level l
+// holds at most N / 8^l unknowns of any component (every axis is at least
+// halved from one level to the next).
+static paris_status helm_work(paris_ctx* c) {
+    if (!c->hw_mem.empty()) return PARIS_OK;
+    auto get = [&](size_t bytes, void** out) {
+        if (cudaMalloc(out, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        c->hw_mem.push_back(*out);
+        return true;
+    };
+    bool ok = get(sizeof(double) * (size_t)c->N, (void**)&c->hmg.sig64);
+    int64_t n = c->N;
+    for (int l = 0; ok && l < kHelmMaxLevels; ++l) {
+        const size_t b = sizeof(float) * (size_t)std::max<int64_t>(n, 1);
+        ok = get(b, (void**)&c->hmg.x[l]) && get(b, (void**)&c->hmg.f[l]) && get(b, (void**)&c->hmg.r[l]) &&
+             get(b, (void**)&c->hmg.sig[l]);
+        n = (n + 7) / 8;
+    }
+    if (!ok) {
+        for (void* q : c->hw_mem) cudaFree(q);
+        c->hw_mem.clear();
+        c->hmg = HelmWork{};
+        return PARIS_ERR_NO_MEMORY;
+    }
+    return PARIS_OK;
+}
+
+paris_status paris_viscous_solve_mg(paris_ctx* c, int comp, const double* nu, double tau, const double* un,
+                                    double* us, double tol, int max_iter, paris_stats* st) {
+    if (!c || !nu || !un || !us || comp < 0 || comp > 2) return PARIS_ERR_INVALID_ARG;
+    if (us == un || us == nu) return PARIS_ERR_INVALID_ARG;
+    if (!(tau >= 0.0) || !std::isfinite(tau) || !(tol > 0.0 && tol < 1.0) || max_iter < 1)
+        return PARIS_ERR_INVALID_ARG;
+    if (tau == 0.0) return paris_viscous_solve(c, comp, nu, tau, un, us, tol, max_iter, st);
+    if (st) *st = paris_stats{};
+    paris_status s = helm_work(c);
+    if (s != PARIS_OK) return s;
+    const HelmGeo g = helm_geo(c->g0, comp, c->grid.h);
+    const HelmPlan P = helm_plan(g, kHelmMaxLevels);
+    const int64_t n = helm_unknowns(g);
+    const paris_opts& o = c->opts;
+    const int nu1 = std::max(1, o.nu1), nu2 = std::max(1, o.nu2);
+    const float omega = o.smoother == PARIS_SMOOTH_JACOBI ? 1.15f : (float)o.omega;
+    CK(cudaMemsetAsync(c->scal, 0, sizeof(Scal), c->st));
+    const auto met = [tol](const Scal& h) { return h.rr <= tol * tol * h.bnorm2 && h.rinf <= tol * h.binf; };
+    const FinSpec rnorms{c->scal, 3, 2, FIN_RNORMS, 0.0};
+    double *r = c->r, *z = c->z, *d = c->d, *q = c->q;
+    launch_hmg_setup(g, un, nu, tau, c->hmg.sig64, c->hmg.sig[0], us, c->partials, c->st,
+                     FinSpec{c->scal, 3, 2, FIN_BNORMS, 0.0});
+    launch_hmg_sigma(P, c->hmg.sig, c->st);
+    launch_hmg_residual64(g, un, c->hmg.sig64, us, r, c->partials, c->st, rnorms);
+    CK(cudaGetLastError());
+    s = read_scal(c);
+    if (s != PARIS_OK) return s;
+    int iters = 0, restarts = 0;
+    bool converged = c->scal_h->bnorm2 == 0.0 || met(*c->scal_h);
+    bool nonfinite = c->scal_h->nonfinite > 0;
+    auto precondition = [&]() { launch_hmg_vcycle(P, c->hmg, r, z, nu1, nu2, 8, omega, c->st); };
+    while (!converged && !nonfinite && iters < max_iter) {
+        precondition();
+        launch_dot2<double>(n, r, z, nullptr, c->partials, c->st, FinSpec{c->scal, 2, 0, FIN_RHO_INIT, 0.0});
+        std::swap(d, z);  // first direction d = z
+        bool inner = false;
+        while (iters < max_iter) {
+            launch_hmg_matvec64(g, c->hmg.sig64, d, q, c->partials, c->st, FinSpec{c->scal, 1, 0, FIN_ALPHA, 0.0});
+            launch_hmg_update64(g, c->scal, d, q, us, r, c->partials, c->st, rnorms);
+            CK(cudaGetLastError());
+            s = read_scal(c);
+            if (s != PARIS_OK) return s;
+            ++iters;
+            if (c->scal_h->nonfinite > 0) { nonfinite = true; break; }
+            if (met(*c->scal_h)) { inner = true; break; }
+            precondition();
+            // flexible CG(1): beta = -(z . q) / (d . q) with the new z
+            launch_dot2<double>(n, z, r, q, c->partials, c->st, FinSpec{c->scal, 2, 0, FIN_FCG_BETA, 0.0});
+            launch_xpby<double>(n, c->scal, z, d, c->st);
+        }
+        if (nonfinite) break;
+        // verify with the true residual; restart from it if the recurrence drifted
+        launch_hmg_residual64(g, un, c->hmg.sig64, us, r, c->partials, c->st, rnorms);
+        CK(cudaGetLastError());
+        s = read_scal(c);
+        if (s != PARIS_OK) return s;
+        nonfinite = c->scal_h->nonfinite > 0;
+        converged = !nonfinite && met(*c->scal_h);
+        if (converged || !inner || ++restarts > 3) break;
+    }
+    const Scal& h = *c->scal_h;
+    if (st) {
+        st->iters = iters;
+        st->outer_iters = restarts + 1;
+        st->rel_res_l2 = h.bnorm2 > 0 ? std::sqrt(h.rr / h.bnorm2) : 0.0;
+        st->rel_res_linf = h.binf > 0 ? h.rinf / h.binf : 0.0;
+        st->converged = converged ? 1 : 0;
+        st->levels = P.nl;
     }
     if (nonfinite) return PARIS_ERR_NONFINITE;
     return converged ? PARIS_OK : PARIS_ERR_NOT_CONVERGED;

@@ -89,14 +89,15 @@ def test_face_viscosity_matches_oracle(paris, grid, comp):
     assert np.all(got[_walls(grid, comp)] == 0.0)
 
 
+@pytest.mark.parametrize("multigrid", [False, True], ids=["jacobi", "mg"])
 @pytest.mark.parametrize("grid", GRIDS, ids=GID)
 @pytest.mark.parametrize("comp", [0, 1, 2])
-def test_viscous_solve_matches_oracle(paris, grid, comp):
+def test_viscous_solve_matches_oracle(paris, grid, comp, multigrid):
     pr, nu, tau, un = _problem(grid, comp, seed=12)
     ref = V.solve(grid, comp, nu, tau, un)
     with paris.Context(grid) as ctx:
         us, st = ctx.viscous_solve(comp, dev(_full(grid, comp, nu)), tau, dev(_full(grid, comp, un)),
-                                   tol=1e-12)
+                                   tol=1e-12, multigrid=multigrid)
         us = host(us)
     assert st["converged"] == 1 and st["iters"] >= 1
     assert np.all(us[_walls(grid, comp)] == 0.0)
@@ -182,7 +183,54 @@ def test_viscous_errors(paris):
         assert lib.paris_face_viscosity(p, -1, ptr(dev(pr.C)), MU1, MU2, RHO1, RHO2, ptr(us)) == 1
 
 
-def test_viscous_fullsize_sampled(paris):
+@pytest.mark.parametrize("tnu", [4.0, 40.0, 400.0])
+@pytest.mark.parametrize("comp", [0, 2])
+def test_multigrid_needs_few_iterations(paris, comp, tnu):
+    """64^3 drop field with walls in z (the 256^3 recipe), tau nu/h^2 = tnu:
+    the V-cycle-preconditioned solve meets tol 1e-10 in at most 10 iterations
+    where Jacobi-PCG needs tens to hundreds, and both reach the same u*."""
+    pr = pi.config2(n=64)
+    g = pr.grid
+    with paris.Context(g) as ctx:
+        C = dev(pr.C)
+        nu_d = ctx.face_viscosity(comp, C, MU1, MU2, pr.rho1, pr.rho2)
+        tau = tnu * g.h ** 2 / float(nu_d.max())
+        un = dev((pr.u, pr.v, pr.w)[comp])
+        um, sm = ctx.viscous_solve(comp, nu_d, tau, un, tol=1e-10, multigrid=True)
+        uj, sj = ctx.viscous_solve(comp, nu_d, tau, un, tol=1e-10, max_iter=5000)
+        assert sm["converged"] == 1 and sj["converged"] == 1
+        assert sm["iters"] <= 10, sm
+        assert sj["iters"] > 2 * sm["iters"], (sj, sm)
+        a, b = V.interior(g, comp, host(um)), V.interior(g, comp, host(uj))
+        assert np.abs(a - b).max() <= 1e-8 * np.abs(b).max()
+
+
+def test_viscous_mg_errors(paris):
+    import ctypes as ct
+    from paper_2012_11744_gb300 import _abi
+    grid = pi.Grid(8, 6, 4, 0.125, (P, W, P))
+    pr, nu, tau, un = _problem(grid, 0, seed=15)
+    with paris.Context(grid) as ctx:
+        nu_d, un_d = dev(_full(grid, 0, nu)), dev(_full(grid, 0, un))
+        us = torch.empty_like(un_d)
+        lib, p = ctx.lib, ctx._ptr
+        ptr = lambda t: ct.c_void_p(t.data_ptr())  # noqa: E731
+        call = lambda comp, nu_, t, un_, us_, tol, it: lib.paris_viscous_solve_mg(  # noqa: E731
+            p, comp, nu_, t, un_, us_, tol, it, None)
+        assert call(3, ptr(nu_d), tau, ptr(un_d), ptr(us), 1e-10, 10) == 1
+        assert call(0, ptr(nu_d), -1.0, ptr(un_d), ptr(us), 1e-10, 10) == 1
+        assert call(0, ptr(nu_d), tau, ptr(un_d), ptr(un_d), 1e-10, 10) == 1
+        assert call(0, ptr(nu_d), tau, ptr(un_d), ptr(us), 1e-10, 0) == 1
+        bad = nu.copy()
+        bad[1, 2, 3] = 0.0
+        assert call(0, ptr(dev(_full(grid, 0, bad))), tau, ptr(un_d), ptr(us), 1e-10, 10) == 4
+        st = _abi.Stats()
+        s = lib.paris_viscous_solve_mg(p, 0, ptr(nu_d), tau, ptr(un_d), ptr(us), 1e-14, 1, ct.byref(st))
+        assert s == 3 and st.iters == 1 and st.converged == 0
+
+
+@pytest.mark.parametrize("multigrid", [False, True], ids=["jacobi", "mg"])
+def test_viscous_fullsize_sampled(paris, multigrid):
     """256^3 drop field in the configuration `bench.py --viscous` times: u* of
     each component at 2048 seeded unknowns against a stored full oracle solve
     (golden/viscous256_drops.json, written by make_viscous256_golden.py from the
@@ -207,7 +255,7 @@ def test_viscous_fullsize_sampled(paris):
         assert abs(gold["tau_nu_over_h2"] * g.h ** 2 / numax - tau) <= 1e-15 * tau
         for c in range(3):
             un = (pr.u, pr.v, pr.w)[c]
-            us, st = ctx.viscous_solve(c, nus[c], tau, dev(un), tol=1e-10)
+            us, st = ctx.viscous_solve(c, nus[c], tau, dev(un), tol=1e-10, multigrid=multigrid)
             assert st["converged"] == 1 and st["rel_res_l2"] <= 1e-10 and st["rel_res_linf"] <= 1e-10
             x = V.interior(g, c, host(us)).ravel()
             nu = V.interior(g, c, host(nus[c]))
