@@ -591,9 +591,15 @@ def run_viscous(args):
     viscosities (mu 1e-3 / 1.8e-5) and the workload's densities; tau =
     4 h^2 / max nu_f (24 times the explicit stability limit of the viscous
     term); tol 1e-10.  One step = the three component solves from u*, v*, w*
-    resident on the device.  Algorithmic bytes of one CG iteration per
-    unknown: q = A d (d, nu read, q written: 24 B), x, r, z update (d, q, x,
-    r, nu read; x, r, z written: 64 B), d = z + beta d (24 B)."""
+    resident on the device, by the multigrid-preconditioned flexible CG
+    (value) and by the Jacobi-preconditioned CG (beside it).  Algorithmic
+    bytes per unknown and iteration: Jacobi-PCG 112 (q = A d: 24; x, r, z
+    update: 64; d = z + beta d: 24); multigrid FCG 144 in FP64 (q = A d with
+    the stored 1/(tau nu): 24; x, r update: 48; z.r, z.q: 24; d update: 24;
+    the FP64/FP32 conversions at the V-cycle's ends: 24) plus the V-cycle,
+    8/7 x 110 in FP32 (four colour sweeps of 20, the residual 16, the
+    restriction 4.5, the prolongation 8.5 and the zeroing of x 4 on the
+    finest level)."""
     import torch
 
     import paper_2012_11744_gb300 as paris
@@ -608,33 +614,34 @@ def run_viscous(args):
     numax = max(float(nu.max()) for nu in nus)
     tau = VISC_TAU_NU_OVER_H2 * g.h ** 2 / numax
     outs = [torch.empty_like(x) for x in uvw]
-    st = ctx.stream
-    stats = []
-
-    def step():
-        stats.clear()
-        for c in range(3):
-            stats.append(ctx.viscous_solve(c, nus[c], tau, uvw[c], outs[c], tol=1e-10)[1])
-
-    for _ in range(args.warmup):
-        step()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    with ClockSampler(0) as clk:
-        ev0.record(st)
-        for _ in range(args.steps):
-            step()
-        ev1.record(st)
-        torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    iters = [s["iters"] for s in stats]
     # unknowns of component c: its face grid without the wall faces of its own axis
     cells = (g.nx, g.ny, g.nz)
     unknowns = [int(np.prod([cells[a] - (1 if a == c and g.bc[a] == pi.WALL else 0) for a in range(3)]))
                 for c in range(3)]
-    byt = sum(112.0 * n * k for n, k in zip(unknowns, iters))
     hbm, kind = measured_peaks()
-    gbs = byt / (ms * 1e-3) / 1e9
+    res = {}
+    for name, mg, per_it in (("multigrid", True, 144.0 + 110.0 * 8.0 / 7.0), ("jacobi", False, 112.0)):
+        def step(i):
+            return [ctx.viscous_solve(c, nus[c], tau, uvw[c], outs[c], tol=1e-10, multigrid=mg)[1] for c in range(3)]
+
+        for _ in range(args.warmup):
+            step(0)
+        K = args.steps if mg else max(1, args.steps // 2)
+        with ClockSampler(0) as clk:
+            per, sts = event_steps(step, K, ctx.stream)
+        last = sts[-1]
+        require_converged([x for s3 in sts for x in s3], f"viscous {name}")
+        iters = [x["iters"] for x in last]
+        byt = sum(per_it * n * k for n, k in zip(unknowns, iters))
+        ms = sum(per) / K
+        gbs = byt / (ms * 1e-3) / 1e9
+        res[name] = {"value": 3.0 / (ms * 1e-3), "ms_per_step": ms, "step_ms": step_stats(per), "steps": K,
+                     "iters": iters, "levels": [x["levels"] for x in last],
+                     "rel_res_l2": [x["rel_res_l2"] for x in last], "bytes_per_unknown_iteration": per_it,
+                     "iteration_roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                            "frac": gbs / hbm, "peak_kind": kind,
+                                            "note": "whole iterations incl. the host read of the norms"},
+                     "clocks": clk.summary()}
     cpu = None
     if not args.no_cpu:
         gold = load_visc_golden(args.n)
@@ -645,19 +652,19 @@ def run_viscous(args):
                          f"{smp['cg_iters_sampled'][0]}, 5 and {smp['cg_iters_sampled'][1]} iterations "
                          f"(set-up {smp['setup_s']:.2f} s, {smp['s_per_cg_iter']:.3f} s per iteration), "
                          f"extrapolated to the full oracle solves' {smp['cg_iters_full']} iterations"}
+    m = res["multigrid"]
     print(json.dumps({
         "metric": "implicit viscous solves/s (u, v, w each a solve) at %d^3, tol 1e-10" % args.n,
-        "value": 3.0 / (ms * 1e-3), "unit": "solves/s", "ms_per_step": ms, "steps": args.steps,
-        "warmup": args.warmup, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-        "iters": iters, "converged": [s["converged"] for s in stats],
-        "rel_res_l2": [s["rel_res_l2"] for s in stats], "tau_nu_max_over_h2": 4.0,
-        "cg_iteration_bytes": byt,
-        "iteration_roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
-                               "frac": gbs / hbm, "peak_kind": kind,
-                               "note": "whole iterations incl. the host read of the norms"},
-        "clocks": clk.summary(), "cpu_baseline": cpu,
+        "value": m["value"], "unit": "solves/s", "ms_per_step": m["ms_per_step"], "step_ms": m["step_ms"],
+        "steps": m["steps"], "warmup": args.warmup, "higher_is_better": True, "dtype": "f64+f32",
+        "data": "synthetic", "method": "flexible CG (FP64) with an FP32 geometric-multigrid V-cycle",
+        "iters": m["iters"], "levels": m["levels"], "rel_res_l2": m["rel_res_l2"], "all_steps_converged": True,
+        "tau_nu_max_over_h2": VISC_TAU_NU_OVER_H2, "iteration_roofline": m["iteration_roofline"],
+        "jacobi_pcg": res["jacobi"], "multigrid_over_jacobi": m["value"] / res["jacobi"]["value"],
+        "clocks": m["clocks"], "cpu_baseline": cpu,
         "config": {"workload": workload_config(args.n)["workload"] + ", mu 1e-3/1.8e-5",
-                   "l2": "no flush: each iteration streams 7 vectors of one component (> 129 MB L2)"}}))
+                   "l2": "no flush: each iteration streams several vectors of one component (> 129 MB L2)"}}),
+        flush=True)
 
 
 def event_steps(step, K, stream):
