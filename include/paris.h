@@ -321,6 +321,23 @@ paris_status paris_projection_step_forced(paris_ctx* ctx, const double* C, const
 paris_status paris_set_solid(paris_ctx* ctx, const unsigned char* s);
 
 /* ---------------------------------------------------------------------------
+ * MARKER FUNCTION (Sec. 3.4.2, Eq. FrontMarker3).  The front-tracking
+ * method spreads the gradient of the marker function I from the front onto
+ * the grid as a face field G (Eq. gradI) and integrates it by solving
+ *   Lap_h I = grad^h . G
+ * on the whole grid: the projection's operator with beta = 1 on every face
+ * (0 on wall faces, which carry no flux of G).  I is fixed up to a constant;
+ * the paper does not say how it is chosen, so the caller gives mean_I (for a
+ * front: the volume it encloses over the domain's volume).  gx, gy, gz: face
+ * arrays (device); I: cells, in: initial guess, out: the marker.  The
+ * context's coefficient arrays are overwritten (beta = 1) and its solver
+ * options apply (the mixed form runs on FP32 face coefficients).
+ * Synchronises.  Errors: INVALID_ARG (null pointer, non-finite mean_I, a
+ * solid set on the context), NOT_CONVERGED, NONFINITE, CUDA. */
+paris_status paris_marker_function(paris_ctx* ctx, const double* gx, const double* gy, const double* gz,
+                                   double mean_I, double* I, paris_stats* st);
+
+/* ---------------------------------------------------------------------------
  * IMPLICIT VISCOUS STEP (Sec. 3.2.3, Eq. muelliptic).  For one velocity
  * component, u* - tau nu_f Lap_h u* = u^n on the component's own face grid,
  * Lap_h the 7-point Laplacian with spacing h.  The unknowns are the

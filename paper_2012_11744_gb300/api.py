@@ -235,6 +235,23 @@ class Context:
         _abi.check(self.lib.paris_set_solid(self._ptr, ct.c_void_p(s.data_ptr())), "paris_set_solid")
         self._solid = s
 
+    def marker_function(self, gx, gy, gz, mean_I, I=None, check=True):
+        """Front-tracking marker function (Eq. FrontMarker3): Lap_h I = D G with
+        mean(I) = mean_I; I (cells) is the initial guess when given.  Returns
+        (I, stats dict)."""
+        g = self.grid
+        I = I if I is not None else torch.zeros(g.shape, dtype=torch.float64, device=self.device)
+        st = _abi.Stats()
+        s = self.lib.paris_marker_function(self._ptr, self._t(gx, g.face_shape(0), "gx"),
+                                           self._t(gy, g.face_shape(1), "gy"),
+                                           self._t(gz, g.face_shape(2), "gz"), float(mean_I),
+                                           self._t(I, g.shape, "I"), ct.byref(st))
+        if check:
+            _abi.check(s, "paris_marker_function", st.as_dict())
+        d = st.as_dict()
+        d["status"] = s
+        return I, d
+
     def predictor_forcing(self, C, kappa, rho1, rho2, sigma, gravity, tau, u, v, w, beta=None):
         """Capillary (CSF) and gravity forcing of the predictor: u, v, w (in
         u^n, out u* = u^n + tau a_f) in place; returns the face coefficients

@@ -205,6 +205,11 @@ void launch_solid_zero(int64_t n, const unsigned char* s, double* x, cudaStream_
 // sc->red[1] = number of fluid cells; returns the blocks used
 int64_t launch_fluid_count(int64_t n, const unsigned char* s, double* partials, Scal* sc, cudaStream_t st);
 
+// marker function (Eq. FrontMarker3): beta = 1 on every face, 0 on walls;
+// x += a on n entries
+void launch_unit_beta(const Geo& g, double* bx, double* by, double* bz, cudaStream_t st);
+void launch_add_constant(int64_t n, double* x, double a, cudaStream_t st);
+
 // ------------------------------------------------- implicit viscous step ---
 // One velocity component of Sec. 3.2.3 (Eq. muelliptic) in SPD form,
 // (diag(1/(tau nu)) - Lap_h) u* = u^n/(tau nu), on its unknowns (viscous.cu).

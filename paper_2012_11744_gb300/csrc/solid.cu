@@ -199,3 +199,46 @@ void launch_fluid_mean(int64_t n, const unsigned char* s, const double* x, doubl
 }
 
 }  // namespace paris
+
+// ------------------------------------------------------ marker function ---
+// Sec. 3.4.2, Eq. FrontMarker3: Lap_h I = D G_f is the projection's operator
+// with beta = 1 on every face (0 on the wall faces).
+
+namespace paris {
+
+namespace {
+
+__global__ void unit_beta_kernel(Geo g, int axis, int64_t n, double* __restrict__ b) {
+    const int e0 = g.nx + (axis == 0 ? g.wx : 0), e1 = g.ny + (axis == 1 ? g.wy : 0);
+    const int wall = axis == 0 ? g.wx : (axis == 1 ? g.wy : g.wz);
+    const int na = axis == 0 ? g.nx : (axis == 1 ? g.ny : g.nz);
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n; f += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = f / e0;
+        const int i = (int)(f - t * e0), j = (int)(t % e1), k = (int)(t / e1);
+        const int p = axis == 0 ? i : (axis == 1 ? j : k);
+        b[f] = (wall && (p == 0 || p == na)) ? 0.0 : 1.0;
+    }
+}
+
+__global__ void add_constant_kernel(int64_t n, double* __restrict__ x, double a) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
+        x[c] += a;
+}
+
+}  // namespace
+
+void launch_unit_beta(const Geo& g, double* bx, double* by, double* bz, cudaStream_t st) {
+    double* b[3] = {bx, by, bz};
+    for (int a = 0; a < 3; ++a) {
+        const int64_t n = g.nface(a);
+        unit_beta_kernel<<<elementwise_blocks(n), kRedThreads, 0, st>>>(g, a, n, b[a]);
+    }
+    count_launch(3);
+}
+
+void launch_add_constant(int64_t n, double* x, double a, cudaStream_t st) {
+    add_constant_kernel<<<elementwise_blocks(n), kRedThreads, 0, st>>>(n, x, a);
+    count_launch();
+}
+
+}  // namespace paris

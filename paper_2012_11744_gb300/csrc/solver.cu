@@ -1243,6 +1243,24 @@ paris_status paris_set_solid(paris_ctx* c, const unsigned char* s) {
     return PARIS_OK;
 }
 
+paris_status paris_marker_function(paris_ctx* c, const double* gx, const double* gy, const double* gz,
+                                   double mean_I, double* I, paris_stats* st) {
+    if (!c || !gx || !gy || !gz || !I || !std::isfinite(mean_I)) return PARIS_ERR_INVALID_ARG;
+    if (c->solid) return PARIS_ERR_INVALID_ARG;  // the marker is integrated on the whole grid
+    // beta = 1 in the context's coefficient arrays, b = D G (h dt = h: dt = 1) and its mean
+    launch_unit_beta(c->g0, c->beta[0], c->beta[1], c->beta[2], c->st);
+    CK(cudaMemsetAsync(c->scal, 0, sizeof(Scal), c->st));
+    const int64_t nb = launch_divergence(c->g0, gx, gy, gz, 1.0 / c->grid.h, c->rhs, c->partials, c->st);
+    finalize(c->partials, nb, 3, 2, c->scal, FIN_MEAN_B, (double)c->N, c->st);
+    CK(cudaGetLastError());
+    const paris_status s = poisson_solve(c, c->beta[0], c->beta[1], c->beta[2], c->rhs, I, st, false, true);
+    if (s != PARIS_OK && s != PARIS_ERR_NOT_CONVERGED) return s;
+    launch_add_constant(c->N, I, mean_I, c->st);  // the solve left I mean-free
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->st));
+    return s;
+}
+
 static bool valid_forcing(double sigma, double gx, double gy, double gz) {
     return std::isfinite(sigma) && sigma >= 0.0 && std::isfinite(gx) && std::isfinite(gy) && std::isfinite(gz);
 }
