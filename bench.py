@@ -52,9 +52,9 @@ STREAM_FLOATS = 1 << 27  # FP32 elements per vector of the streaming-rate probe 
 NCU_TRAFFIC = {
     # finest-level colour pass: DRAM read + write bytes per launch from
     # "ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
-    #  -k regex:rbgs_rho|op_rho|... -c 24" of "bench.py --single mixed": zero-initial passes
-    # 115.4 MB, the passes after them 153.0 MB, the others 186.7 MB; 11, 11 and 66 per solve
-    "smooth0": {"bytes_per_launch": 173.6e6, "source": "rho0.cu", "sha": "f29994e75ed92a4f"},
+    #  -k regex:rbgs_rho_tile -c 24" of "bench.py --single mixed": zero-initial passes
+    # 115.2 MB, the passes after them 152.9 MB, the others 186.7 MB; 11, 11 and 66 per solve
+    "smooth0": {"bytes_per_launch": 173.5e6, "source": "rho0.cu", "sha": "6e7a9fcff9c59395"},
 }
 
 
