@@ -1221,24 +1221,56 @@ int64_t launch_matvec_dot(const Geo& g, const Coef<T>& cf, const T* d, T* q, dou
     return nblocks_of(gr);
 }
 
+// The streaming Krylov kernels keep several independent 16-byte loads per
+// array in flight per thread (kKU iterations of the grid-stride loop at once,
+// each with its own partial sums), which the memory system needs to stream
+// at its rate; the partial sums are folded in a fixed order.
+constexpr int kKU = 4;
+
 template <typename T>
 __global__ void update_xr_kernel(int64_t n, const Scal* s, const T* __restrict__ d,
                                  const T* __restrict__ q, T* __restrict__ x, T* __restrict__ r,
                                  double* partials, int vec, FinSpec fin) {
     using VT = typename V16<T>::type;
     constexpr int W = V16<T>::n;
+    constexpr int U = kKU / 2;  // four arrays per element: two iterations at once
     const T alpha = (T)s->alpha;
-    T l2 = T(0), li = T(0);
+    T l2[U], li[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) l2[u] = li[u] = T(0);
     unsigned nf = 0;  // an integer count: no FP64 add per element
-    auto one = [&](T dv, T qv, T& xv, T& rv) {
+    auto one = [&](T dv, T qv, T& xv, T& rv, T& l2u, T& liu) {
         xv = fma(alpha, dv, xv);
         rv = fma(-alpha, qv, rv);
-        l2 = fma(rv, rv, l2);
-        li = fmax(li, fabs(rv));
+        l2u = fma(rv, rv, l2u);
+        liu = fmax(liu, fabs(rv));
         nf += isfinite(rv) ? 0u : 1u;
     };
     const int64_t nv = vec ? n / W : 0;
-    PARIS_VEC_FOR(i, nv) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + (U - 1) * stride < nv; i += U * stride) {
+        VT dv[U], qv[U], xv[U], rv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            dv[u] = reinterpret_cast<const VT*>(d)[i + u * stride];
+            qv[u] = reinterpret_cast<const VT*>(q)[i + u * stride];
+            xv[u] = reinterpret_cast<VT*>(x)[i + u * stride];
+            rv[u] = reinterpret_cast<VT*>(r)[i + u * stride];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const T* de = reinterpret_cast<const T*>(&dv[u]);
+            const T* qe = reinterpret_cast<const T*>(&qv[u]);
+            T* xe = reinterpret_cast<T*>(&xv[u]);
+            T* re = reinterpret_cast<T*>(&rv[u]);
+#pragma unroll
+            for (int w = 0; w < W; ++w) one(de[w], qe[w], xe[w], re[w], l2[u], li[u]);
+            reinterpret_cast<VT*>(x)[i + u * stride] = xv[u];
+            reinterpret_cast<VT*>(r)[i + u * stride] = rv[u];
+        }
+    }
+    for (; i < nv; i += stride) {
         const VT dv = reinterpret_cast<const VT*>(d)[i];
         const VT qv = reinterpret_cast<const VT*>(q)[i];
         VT xv = reinterpret_cast<VT*>(x)[i];
@@ -1248,17 +1280,23 @@ __global__ void update_xr_kernel(int64_t n, const Scal* s, const T* __restrict__
         T* xe = reinterpret_cast<T*>(&xv);
         T* re = reinterpret_cast<T*>(&rv);
 #pragma unroll
-        for (int w = 0; w < W; ++w) one(de[w], qe[w], xe[w], re[w]);
+        for (int w = 0; w < W; ++w) one(de[w], qe[w], xe[w], re[w], l2[0], li[0]);
         reinterpret_cast<VT*>(x)[i] = xv;
         reinterpret_cast<VT*>(r)[i] = rv;
     }
     PARIS_TAIL_FOR(c, nv * W, n) {
         T xv = x[c], rv = r[c];
-        one(d[c], q[c], xv, rv);
+        one(d[c], q[c], xv, rv, l2[0], li[0]);
         x[c] = xv;
         r[c] = rv;
     }
-    double acc[3] = {(double)l2, (double)li, (double)nf};
+    T l2s = l2[0], lis = li[0];
+#pragma unroll
+    for (int u = 1; u < U; ++u) {
+        l2s += l2[u];
+        lis = fmax(lis, li[u]);
+    }
+    double acc[3] = {(double)l2s, (double)lis, (double)nf};
     const int op[3] = {0, 1, 0};
     block_reduce_store<3>(acc, op, partials, blockIdx.x, threadIdx.x);
     finalize_last_block(partials, gridDim.x, fin, threadIdx.x);
@@ -1279,27 +1317,54 @@ __global__ void dot2_kernel(int64_t n, const T* __restrict__ a, const T* __restr
                             const T* __restrict__ c, double* partials, int vec, FinSpec fin) {
     using VT = typename V16<T>::type;
     constexpr int W = V16<T>::n;
-    T s0 = T(0), s1 = T(0);
+    constexpr int U = kKU;
+    T s0[U], s1[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) s0[u] = s1[u] = T(0);
     const int64_t nv = vec ? n / W : 0;
-    PARIS_VEC_FOR(i, nv) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + (U - 1) * stride < nv; i += U * stride) {
+        VT av[U], bv[U], cv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            av[u] = __ldcs(reinterpret_cast<const VT*>(a) + i + u * stride);
+            bv[u] = __ldcs(reinterpret_cast<const VT*>(b) + i + u * stride);
+            if (c) cv[u] = __ldcs(reinterpret_cast<const VT*>(c) + i + u * stride);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const T* ae = reinterpret_cast<const T*>(&av[u]);
+            const T* be = reinterpret_cast<const T*>(&bv[u]);
+#pragma unroll
+            for (int w = 0; w < W; ++w) s0[u] = fma(ae[w], be[w], s0[u]);
+            if (c) {
+                const T* ce = reinterpret_cast<const T*>(&cv[u]);
+#pragma unroll
+                for (int w = 0; w < W; ++w) s1[u] = fma(ae[w], ce[w], s1[u]);
+            }
+        }
+    }
+    for (; i < nv; i += stride) {
         const VT av = reinterpret_cast<const VT*>(a)[i];
         const VT bv = reinterpret_cast<const VT*>(b)[i];
         const T* ae = reinterpret_cast<const T*>(&av);
         const T* be = reinterpret_cast<const T*>(&bv);
 #pragma unroll
-        for (int w = 0; w < W; ++w) s0 = fma(ae[w], be[w], s0);
+        for (int w = 0; w < W; ++w) s0[0] = fma(ae[w], be[w], s0[0]);
         if (c) {
             const VT cv = reinterpret_cast<const VT*>(c)[i];
             const T* ce = reinterpret_cast<const T*>(&cv);
 #pragma unroll
-            for (int w = 0; w < W; ++w) s1 = fma(ae[w], ce[w], s1);
+            for (int w = 0; w < W; ++w) s1[0] = fma(ae[w], ce[w], s1[0]);
         }
     }
     PARIS_TAIL_FOR(e, nv * W, n) {
-        s0 = fma(a[e], b[e], s0);
-        if (c) s1 = fma(a[e], c[e], s1);
+        s0[0] = fma(a[e], b[e], s0[0]);
+        if (c) s1[0] = fma(a[e], c[e], s1[0]);
     }
-    double acc[2] = {(double)s0, (double)s1};
+    T t0 = (s0[0] + s0[1]) + (s0[2] + s0[3]), t1 = (s1[0] + s1[1]) + (s1[2] + s1[3]);
+    double acc[2] = {(double)t0, (double)t1};
     const int op[2] = {0, 0};
     block_reduce_store<2>(acc, op, partials, blockIdx.x, threadIdx.x);
     finalize_last_block(partials, gridDim.x, fin, threadIdx.x);
