@@ -567,7 +567,9 @@ def run_paris(args, rank, world, local):
 
 
 def run_single(args):
-    """One projection of the workload, untimed: the target of ncu captures."""
+    """One projection of the workload (or, with --single viscous, the three
+    multigrid component solves of --viscous), untimed: the target of ncu
+    captures."""
     import torch
 
     import paper_2012_11744_gb300 as paris
@@ -575,6 +577,16 @@ def run_single(args):
     pr = pi.config2(n=args.n)
     g = pr.grid
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    if args.single == "viscous":
+        ctx = paris.Context(g)
+        C = d(pr.C)
+        nus = [ctx.face_viscosity(c, C, VISC_MU[0], VISC_MU[1], pr.rho1, pr.rho2) for c in range(3)]
+        tau = VISC_TAU_NU_OVER_H2 * g.h ** 2 / max(float(nu.max()) for nu in nus)
+        sts = [ctx.viscous_solve(c, nus[c], tau, d((pr.u, pr.v, pr.w)[c]), tol=1e-10, multigrid=True)[1]
+               for c in range(3)]
+        torch.cuda.synchronize()
+        print(json.dumps({"single": "viscous", "stats": sts}))
+        return
     prec = paris.MIXED if args.single == "mixed" else paris.FP64
     kw = {} if args.smoother is None else {"smoother": args.smoother}
     ctx = paris.Context(g, opts=paris.default_opts(precision=prec, **kw))
@@ -911,7 +923,7 @@ def main():
                     help="seconds of oracle CG iterations in the cpu_baseline sample")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-mode measurement")
-    ap.add_argument("--single", choices=["mixed", "fp64"], default=None,
+    ap.add_argument("--single", choices=["mixed", "fp64", "viscous"], default=None,
                     help="run one untimed projection (the target of ncu captures) and exit")
     ap.add_argument("--viscous", action="store_true",
                     help="time the implicit viscous step of the three components instead and exit")

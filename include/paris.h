@@ -381,18 +381,21 @@ paris_status paris_viscous_solve(paris_ctx* ctx, int comp, const double* nu, dou
                                  const double* un, double* us, double tol, int max_iter,
                                  paris_stats* st);
 
-/* The same solve (same arguments, stopping test and outputs) by flexible
- * CG in FP64 preconditioned by an FP32 geometric-multigrid V-cycle of the
+/* The same solve (same arguments, stopping test and outputs) by FP64
+ * iterative refinement around FP32 flexible CG (each refinement step
+ * reduces its residual by paris_opts.inner_tol, or by what the tolerance
+ * still needs), preconditioned by an FP32 geometric-multigrid V-cycle of the
  * component's operator: every axis halved per level (cell-centred along
  * periodic and no-slip axes, vertex-centred along the component's own wall
  * axis, with linear interpolation and full weighting there), rediscretised
  * coarse operators with the restricted mass term 1/(tau nu), red-black
  * Gauss-Seidel with the context's nu1/nu2 sweeps and omega (damped Jacobi on
  * a level with an odd periodic extent), 8 sweeps on the coarsest level.
- * The first call on a context allocates the multigrid's work arrays (about
- * 4 x 4 x 8/7 bytes per cell plus 8 per cell); later calls allocate
- * nothing.  st->levels: the multigrid levels.  Errors: as
- * paris_viscous_solve, and NO_MEMORY on the first call. */
+ * The stopping test is on the FP64 residual.  The first call on a context
+ * allocates the multigrid's work arrays (about 4 x 4 x 8/7 bytes per cell
+ * plus 8 per cell); later calls allocate nothing.  st->iters: FP32 inner
+ * iterations; st->outer_iters: refinement steps; st->levels: the multigrid
+ * levels.  Errors: as paris_viscous_solve, and NO_MEMORY on the first call. */
 paris_status paris_viscous_solve_mg(paris_ctx* ctx, int comp, const double* nu, double tau,
                                     const double* un, double* us, double tol, int max_iter,
                                     paris_stats* st);

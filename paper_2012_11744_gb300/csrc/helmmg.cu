@@ -1,5 +1,5 @@
 // Multigrid preconditioner of the implicit viscous step (Sec. 3.2.3, Eq.
-// muelliptic) and the FP64 kernels of the flexible CG around it.
+// muelliptic) and the kernels of the mixed-precision solve around it.
 //
 // One velocity component's SPD operator on its unknowns (the component's
 // face grid without its own wall faces),
@@ -21,9 +21,11 @@
 // boundary kinds; the coarse sigma is the restricted fine sigma.  Smoother:
 // red-black Gauss-Seidel with over-relaxation where every periodic extent of
 // the level is even, damped Jacobi otherwise (a periodic axis of odd length
-// would give a cell two neighbours of its own colour).  The V-cycle is not
-// exactly linear (FP32, Gauss-Seidel), so the outer FP64 iteration is the
-// flexible CG of the Poisson solve's mixed form.
+// would give a cell two neighbours of its own colour).  The solve around it
+// has the structure of the Poisson solve's mixed form: FP64 iterative
+// refinement (the FP64 residual of the SPD form, the accumulation of u*)
+// around an FP32 flexible CG (the V-cycle is not exactly linear: FP32,
+// Gauss-Seidel) on the finest level's operator with FP32 sigma.
 #include "kernels.cuh"
 
 namespace paris {
@@ -296,67 +298,63 @@ __global__ void __launch_bounds__(kTX* kTY) hmg_residual64_kernel(HelmGeo g, con
     finalize_last_block(partials, (int64_t)gridDim.x * gridDim.y * gridDim.z, fin, tid);
 }
 
-// q = A d and the partials of d . q
-__global__ void __launch_bounds__(kTX* kTY) hmg_matvec64_kernel(HelmGeo g, const double* __restrict__ sig,
-                                                               const double* __restrict__ d, double* __restrict__ q,
+// FP32 inner iteration: q = A d on the finest level (FP32 sigma) and the
+// partials of d . q
+__global__ void __launch_bounds__(kTX* kTY) hmg_matvec32_kernel(HLev L, const float* __restrict__ sig,
+                                                               const float* __restrict__ d, float* __restrict__ q,
                                                                double* partials, FinSpec fin) {
     const int i = blockIdx.x * kTX + threadIdx.x, j = blockIdx.y * kTY + threadIdx.y;
     const int tid = threadIdx.y * kTX + threadIdx.x;
-    double dq = 0.0;
-    const int64_t su[3] = {1, g.m[0], (int64_t)g.m[0] * g.m[1]};
-    if (i < g.m[0] && j < g.m[1]) {
-        const int k0 = blockIdx.z * kZ, k1 = min(k0 + kZ, g.m[2]);
+    float dq = 0.f;
+    if (i < L.m[0] && j < L.m[1]) {
+        const int k0 = blockIdx.z * kZ, k1 = min(k0 + kZ, L.m[2]);
         for (int k = k0; k < k1; ++k) {
-            const int64_t p = ((int64_t)k * g.m[1] + j) * g.m[0] + i;
-            const double qp = hop64(g, d, p, su, i, j, k, sig[p]);
-            q[p] = qp;
-            dq = fma(d[p], qp, dq);
+            const int c = hidx(L, i, j, k);
+            float acc, dg;
+            hnb<float>(L, d, i, j, k, acc, dg);
+            const float dc = d[c];
+            const float qc = fmaf(dg, L.ih2, sig[c]) * dc - acc * L.ih2;
+            q[c] = qc;
+            dq = fmaf(dc, qc, dq);
         }
     }
-    double acc[1] = {dq};
+    double accd[1] = {(double)dq};
     const int op[1] = {0};
-    block_reduce_store<1>(acc, op, partials, ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x,
+    block_reduce_store<1>(accd, op, partials, ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x,
                           tid);
     finalize_last_block(partials, (int64_t)gridDim.x * gridDim.y * gridDim.z, fin, tid);
 }
 
-// u* += alpha d (face array), r -= alpha q; partials (|r|^2, max |r|, non-finite count)
-__global__ void __launch_bounds__(kTX* kTY) hmg_update64_kernel(HelmGeo g, const Scal* __restrict__ s,
-                                                               const double* __restrict__ d,
-                                                               const double* __restrict__ q, double* __restrict__ us,
-                                                               double* __restrict__ r, double* partials, FinSpec fin) {
-    const int i = blockIdx.x * kTX + threadIdx.x, j = blockIdx.y * kTY + threadIdx.y;
-    const int tid = threadIdx.y * kTX + threadIdx.x;
-    const double alpha = s->alpha;
-    double l2 = 0.0;
-    unsigned long long rk = 0;
-    unsigned nf = 0;
-    if (i < g.m[0] && j < g.m[1]) {
-        const int k0 = blockIdx.z * kZ, k1 = min(k0 + kZ, g.m[2]);
-        for (int k = k0; k < k1; ++k) {
-            const int64_t p = ((int64_t)k * g.m[1] + j) * g.m[0] + i;
-            const int64_t f = g.off + i + (int64_t)g.e[0] * (j + (int64_t)g.e[1] * k);
-            us[f] = fma(alpha, d[p], us[f]);
-            const double rp = fma(-alpha, q[p], r[p]);
-            r[p] = rp;
-            l2 = fma(rp, rp, l2);
-            const unsigned long long kr = abs_key(rp);
-            rk = kr > rk ? kr : rk;
-            nf += key_nonfinite(kr);
-        }
+// r32 = scale r64 (scale a power of two from the context's scalar block,
+// kept until the correction is accumulated); partials of |r32|^2, max |r32|
+__global__ void hmg_scale_d2f_kernel(int64_t n, const double* __restrict__ r, const Scal* __restrict__ s,
+                                     float* __restrict__ r32, double* partials, FinSpec fin) {
+    const double sc = s->scale;
+    float l2 = 0.f, mx = 0.f;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        const float v = (float)(sc * r[c]);
+        r32[c] = v;
+        l2 = fmaf(v, v, l2);
+        mx = fmaxf(mx, fabsf(v));
     }
-    block_reduce_skc<double>(l2, rk, nf, partials, ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x,
-                             tid);
-    finalize_last_block(partials, (int64_t)gridDim.x * gridDim.y * gridDim.z, fin, tid);
+    double acc[2] = {(double)l2, (double)mx};
+    const int op[2] = {0, 1};
+    block_reduce_store<2>(acc, op, partials, blockIdx.x, threadIdx.x);
+    finalize_last_block(partials, gridDim.x, fin, threadIdx.x);
 }
 
-__global__ void hmg_d2f_kernel(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
-        b[c] = (float)a[c];
-}
-__global__ void hmg_f2d_kernel(int64_t n, const float* __restrict__ a, double* __restrict__ b) {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
-        b[c] = (double)a[c];
+// u* += e / scale on the unknowns of the face array
+__global__ void __launch_bounds__(kTX* kTY) hmg_accumulate_kernel(HelmGeo g, const float* __restrict__ e,
+                                                                 const Scal* __restrict__ s, double* __restrict__ us) {
+    const int i = blockIdx.x * kTX + threadIdx.x, j = blockIdx.y * kTY + threadIdx.y;
+    if (i >= g.m[0] || j >= g.m[1]) return;
+    const double inv = s->inv_scale;
+    const int k0 = blockIdx.z * kZ, k1 = min(k0 + kZ, g.m[2]);
+    for (int k = k0; k < k1; ++k) {
+        const int64_t p = ((int64_t)k * g.m[1] + j) * g.m[0] + i;
+        const int64_t f = g.off + i + (int64_t)g.e[0] * (j + (int64_t)g.e[1] * k);
+        us[f] = fma((double)e[p], inv, us[f]);
+    }
 }
 
 inline dim3 hgrid(const int (&m)[3], int zper) {
@@ -447,28 +445,20 @@ int64_t launch_hmg_residual64(const HelmGeo& g, const double* un, const double* 
     return (int64_t)gr.x * gr.y * gr.z;
 }
 
-int64_t launch_hmg_matvec64(const HelmGeo& g, const double* sig, const double* d, double* q, double* partials,
-                            cudaStream_t st, FinSpec fin) {
-    const dim3 gr = hgrid(g.m, kZ);
-    hmg_matvec64_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(g, sig, d, q, partials, fin);
-    count_launch();
-    return (int64_t)gr.x * gr.y * gr.z;
+// z32 = V f32 on FP32 vectors of the finest level (f32 and z32 are not
+// the work arrays of level 0, which the V-cycle uses for its own x and f)
+static void hmg_vcycle_core(const HelmPlan& P, const HelmWork& W, const float* f0, float* x0, int nu1, int nu2,
+                            int coarse_sweeps, float omega, cudaStream_t st);
+
+void launch_hmg_vcycle32(const HelmPlan& P, const HelmWork& W, const float* r32, float* z32, int nu1, int nu2,
+                         int coarse_sweeps, float omega, cudaStream_t st) {
+    hmg_vcycle_core(P, W, r32, z32, nu1, nu2, coarse_sweeps, omega, st);
 }
 
-int64_t launch_hmg_update64(const HelmGeo& g, const Scal* s, const double* d, const double* q, double* us, double* r,
-                            double* partials, cudaStream_t st, FinSpec fin) {
-    const dim3 gr = hgrid(g.m, kZ);
-    hmg_update64_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(g, s, d, q, us, r, partials, fin);
-    count_launch();
-    return (int64_t)gr.x * gr.y * gr.z;
-}
-
-// z = V r: FP32 V-cycle from the FP64 residual r (unknown layout) into z
-void launch_hmg_vcycle(const HelmPlan& P, const HelmWork& W, const double* r, double* z, int nu1, int nu2,
-                       int coarse_sweeps, float omega, cudaStream_t st) {
-    const int64_t n0 = hcount(P.lv[0]);
-    hmg_d2f_kernel<<<elementwise_blocks(n0), kRedThreads, 0, st>>>(n0, r, W.f[0]);
-    count_launch();
+static void hmg_vcycle_core(const HelmPlan& P, const HelmWork& W, const float* f0, float* x0, int nu1, int nu2,
+                            int coarse_sweeps, float omega, cudaStream_t st) {
+    auto F = [&](int l) { return l == 0 ? f0 : (const float*)W.f[l]; };
+    auto X = [&](int l) { return l == 0 ? x0 : W.x[l]; };
     auto smooth = [&](int l, int sweeps, bool reverse) {
         const HLev L = hlev(P.lv[l]);
         const dim3 gr = hgrid(P.lv[l].m, kZ);
@@ -476,29 +466,29 @@ void launch_hmg_vcycle(const HelmPlan& P, const HelmWork& W, const double* r, do
             for (int s = 0; s < sweeps; ++s)
                 for (int h = 0; h < 2; ++h) {
                     const int color = reverse ? 1 - h : h;
-                    hmg_smooth_kernel<false><<<gr, dim3(kTX, kTY), 0, st>>>(L, W.f[l], W.sig[l], W.x[l], W.x[l],
+                    hmg_smooth_kernel<false><<<gr, dim3(kTX, kTY), 0, st>>>(L, F(l), W.sig[l], X(l), X(l),
                                                                            color, omega);
                     count_launch();
                 }
         } else {  // damped Jacobi, ping-pong through the level's residual buffer, ending in x
             const int64_t n = hcount(P.lv[l]);
             for (int s = 0; s < sweeps; ++s) {
-                hmg_smooth_kernel<true><<<gr, dim3(kTX, kTY), 0, st>>>(L, W.f[l], W.sig[l], W.x[l], W.r[l], 0,
+                hmg_smooth_kernel<true><<<gr, dim3(kTX, kTY), 0, st>>>(L, F(l), W.sig[l], X(l), W.r[l], 0,
                                                                       0.8f);
-                cudaMemcpyAsync(W.x[l], W.r[l], sizeof(float) * n, cudaMemcpyDeviceToDevice, st);
+                cudaMemcpyAsync(X(l), W.r[l], sizeof(float) * n, cudaMemcpyDeviceToDevice, st);
                 count_launch();
             }
         }
     };
     for (int l = 0; l < P.nl; ++l) {
-        cudaMemsetAsync(W.x[l], 0, sizeof(float) * hcount(P.lv[l]), st);
+        cudaMemsetAsync(X(l), 0, sizeof(float) * hcount(P.lv[l]), st);
         if (l == P.nl - 1) {
             smooth(l, coarse_sweeps, false);
             break;
         }
         smooth(l, nu1, false);
         const HLev L = hlev(P.lv[l]), Cg = hlev(P.lv[l + 1]);
-        hmg_residual_kernel<<<hgrid(P.lv[l].m, kZ), dim3(kTX, kTY), 0, st>>>(L, W.f[l], W.sig[l], W.x[l], W.r[l]);
+        hmg_residual_kernel<<<hgrid(P.lv[l].m, kZ), dim3(kTX, kTY), 0, st>>>(L, F(l), W.sig[l], X(l), W.r[l]);
         dim3 gr((Cg.m[0] + kTX - 1) / kTX, (Cg.m[1] + kTY - 1) / kTY, Cg.m[2]);
         hmg_restrict_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(L, Cg, W.r[l], W.f[l + 1]);
         count_launch(2);
@@ -506,17 +496,41 @@ void launch_hmg_vcycle(const HelmPlan& P, const HelmWork& W, const double* r, do
     for (int l = P.nl - 2; l >= 0; --l) {
         const HLev L = hlev(P.lv[l]), Cg = hlev(P.lv[l + 1]);
         dim3 gr((L.m[0] + kTX - 1) / kTX, (L.m[1] + kTY - 1) / kTY, L.m[2]);
-        hmg_prolong_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(L, Cg, W.x[l + 1], W.x[l]);
+        hmg_prolong_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(L, Cg, X(l + 1), X(l));
         count_launch();
         smooth(l, nu2, true);
     }
-    hmg_f2d_kernel<<<elementwise_blocks(n0), kRedThreads, 0, st>>>(n0, W.x[0], z);
-    count_launch();
 }
 
 int64_t helm_max_blocks(const HelmGeo& g) {
     const dim3 gr = hgrid(g.m, kZ);
     return (int64_t)gr.x * gr.y * gr.z;
+}
+
+}  // namespace paris
+
+namespace paris {
+
+int64_t launch_hmg_matvec32(const HelmPlan& P, const float* sig, const float* d, float* q, double* partials,
+                            cudaStream_t st, FinSpec fin) {
+    const HLev L = hlev(P.lv[0]);
+    const dim3 gr = hgrid(P.lv[0].m, kZ);
+    hmg_matvec32_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(L, sig, d, q, partials, fin);
+    count_launch();
+    return (int64_t)gr.x * gr.y * gr.z;
+}
+
+int64_t launch_hmg_scale_d2f(int64_t n, const double* r, const Scal* s, float* r32, double* partials,
+                             cudaStream_t st, FinSpec fin) {
+    const int nb = elementwise_blocks(n);
+    hmg_scale_d2f_kernel<<<nb, kRedThreads, 0, st>>>(n, r, s, r32, partials, fin);
+    count_launch();
+    return nb;
+}
+
+void launch_hmg_accumulate(const HelmGeo& g, const float* e, const Scal* s, double* us, cudaStream_t st) {
+    hmg_accumulate_kernel<<<hgrid(g.m, kZ), dim3(kTX, kTY), 0, st>>>(g, e, s, us);
+    count_launch();
 }
 
 }  // namespace paris

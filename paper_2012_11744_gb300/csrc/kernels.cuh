@@ -258,16 +258,17 @@ void launch_hmg_sigma(const HelmPlan& P, float* const* sig, cudaStream_t st);
 // r = sigma u^n - A u*; partials (|r|^2, max |r|, non-finite)
 int64_t launch_hmg_residual64(const HelmGeo& g, const double* un, const double* sig, const double* us, double* r,
                               double* partials, cudaStream_t st, FinSpec fin);
-// q = A d; partials (d . q)
-int64_t launch_hmg_matvec64(const HelmGeo& g, const double* sig, const double* d, double* q, double* partials,
-                            cudaStream_t st, FinSpec fin);
-// u* += alpha d, r -= alpha q; partials (|r|^2, max |r|, non-finite)
-int64_t launch_hmg_update64(const HelmGeo& g, const Scal* s, const double* d, const double* q, double* us, double* r,
-                            double* partials, cudaStream_t st, FinSpec fin);
-// z = V r (FP32 V-cycle; nu1/nu2 sweeps down/up, coarse_sweeps on the coarsest)
-void launch_hmg_vcycle(const HelmPlan& P, const HelmWork& W, const double* r, double* z, int nu1, int nu2,
-                       int coarse_sweeps, float omega, cudaStream_t st);
 int64_t helm_max_blocks(const HelmGeo& g);
+// FP32 inner iteration of the mixed form: z32 = V r32 (finest-level vectors
+// given, not the work arrays); q = A d in FP32 and d . q; r32 = scale r64 and
+// its norms (scale from the scalar block); u* += e / scale
+void launch_hmg_vcycle32(const HelmPlan& P, const HelmWork& W, const float* r32, float* z32, int nu1, int nu2,
+                         int coarse_sweeps, float omega, cudaStream_t st);
+int64_t launch_hmg_matvec32(const HelmPlan& P, const float* sig, const float* d, float* q, double* partials,
+                            cudaStream_t st, FinSpec fin);
+int64_t launch_hmg_scale_d2f(int64_t n, const double* r, const Scal* s, float* r32, double* partials,
+                             cudaStream_t st, FinSpec fin);
+void launch_hmg_accumulate(const HelmGeo& g, const float* e, const Scal* s, double* us, cudaStream_t st);
 int64_t helm_unknowns(const HelmGeo& g);
 int64_t helm_faces(const HelmGeo& g);
 // us = un on the unknowns, 0 on the wall faces; partials (|b|^2, max|b|,

@@ -1569,51 +1569,65 @@ paris_status paris_viscous_solve_mg(paris_ctx* c, int comp, const double* nu, do
     CK(cudaMemsetAsync(c->scal, 0, sizeof(Scal), c->st));
     const auto met = [tol](const Scal& h) { return h.rr <= tol * tol * h.bnorm2 && h.rinf <= tol * h.binf; };
     const FinSpec rnorms{c->scal, 3, 2, FIN_RNORMS, 0.0};
-    double *r = c->r, *z = c->z, *d = c->d, *q = c->q;
+    // FP64 iterative refinement around FP32 flexible CG: the FP64 residual of
+    // the SPD form decides convergence; each refinement step solves A e = r
+    // in FP32 with r scaled by a power of two (exact in both directions) to a
+    // relative reduction inner_tol (or what the outer tolerance still needs)
+    double* r = c->r;
+    float *r32 = c->r32, *z32 = c->z32, *d32 = c->d32, *q32 = c->q32, *e32 = c->e32;
     launch_hmg_setup(g, un, nu, tau, c->hmg.sig64, c->hmg.sig[0], us, c->partials, c->st,
                      FinSpec{c->scal, 3, 2, FIN_BNORMS, 0.0});
     launch_hmg_sigma(P, c->hmg.sig, c->st);
-    launch_hmg_residual64(g, un, c->hmg.sig64, us, r, c->partials, c->st, rnorms);
-    CK(cudaGetLastError());
-    s = read_scal(c);
-    if (s != PARIS_OK) return s;
-    int iters = 0, restarts = 0;
-    bool converged = c->scal_h->bnorm2 == 0.0 || met(*c->scal_h);
-    bool nonfinite = c->scal_h->nonfinite > 0;
-    auto precondition = [&]() { launch_hmg_vcycle(P, c->hmg, r, z, nu1, nu2, 8, omega, c->st); };
-    while (!converged && !nonfinite && iters < max_iter) {
-        precondition();
-        launch_dot2<double>(n, r, z, nullptr, c->partials, c->st, FinSpec{c->scal, 2, 0, FIN_RHO_INIT, 0.0});
-        std::swap(d, z);  // first direction d = z
-        bool inner = false;
-        while (iters < max_iter) {
-            launch_hmg_matvec64(g, c->hmg.sig64, d, q, c->partials, c->st, FinSpec{c->scal, 1, 0, FIN_ALPHA, 0.0});
-            launch_hmg_update64(g, c->scal, d, q, us, r, c->partials, c->st, rnorms);
-            CK(cudaGetLastError());
-            s = read_scal(c);
-            if (s != PARIS_OK) return s;
-            ++iters;
-            if (c->scal_h->nonfinite > 0) { nonfinite = true; break; }
-            if (met(*c->scal_h)) { inner = true; break; }
-            precondition();
-            // flexible CG(1): beta = -(z . q) / (d . q) with the new z
-            launch_dot2<double>(n, z, r, q, c->partials, c->st, FinSpec{c->scal, 2, 0, FIN_FCG_BETA, 0.0});
-            launch_xpby<double>(n, c->scal, z, d, c->st);
-        }
-        if (nonfinite) break;
-        // verify with the true residual; restart from it if the recurrence drifted
+    int iters = 0, outer = 0, stalls = 0;
+    bool converged = false, nonfinite = false;
+    double prev_rr = INFINITY;
+    for (;;) {
         launch_hmg_residual64(g, un, c->hmg.sig64, us, r, c->partials, c->st, rnorms);
         CK(cudaGetLastError());
         s = read_scal(c);
         if (s != PARIS_OK) return s;
-        nonfinite = c->scal_h->nonfinite > 0;
-        converged = !nonfinite && met(*c->scal_h);
-        if (converged || !inner || ++restarts > 3) break;
+        const Scal& h = *c->scal_h;
+        if (h.nonfinite > 0) { nonfinite = true; break; }
+        if (h.bnorm2 == 0.0 || met(h)) { converged = true; break; }
+        if (iters >= max_iter) break;
+        if (h.rr > 0.25 * prev_rr) { if (++stalls >= 2) break; } else stalls = 0;
+        prev_rr = h.rr;
+        ++outer;
+        finalize(c->partials, 0, 1, 0, c->scal, FIN_SCALE, 0.0, c->st);  // scale from max |r|
+        launch_hmg_scale_d2f(n, r, c->scal, r32, c->partials, c->st, FinSpec{c->scal, 2, 2, FIN_STORE, 0.0});
+        CK(cudaMemsetAsync(e32, 0, sizeof(float) * n, c->st));
+        s = read_scal(c);
+        if (s != PARIS_OK) return s;
+        const double rr32 = c->scal_h->red[0];
+        const double need2 = (tol * tol * h.bnorm2) / std::max(h.rr, 1e-300) * 1e-2;
+        const double it2 = o.inner_tol * o.inner_tol;
+        const double target = rr32 * std::max(it2, std::min(need2, 1.0));
+        launch_hmg_vcycle32(P, c->hmg, r32, z32, nu1, nu2, 8, omega, c->st);
+        launch_dot2<float>(n, r32, z32, nullptr, c->partials, c->st, FinSpec{c->scal, 2, 0, FIN_RHO_INIT, 0.0});
+        std::swap(d32, z32);  // first direction d = z
+        for (int j = 0; j < 50 && iters < max_iter; ++j) {
+            launch_hmg_matvec32(P, c->hmg.sig[0], d32, q32, c->partials, c->st, FinSpec{c->scal, 1, 0, FIN_ALPHA, 0.0});
+            launch_update_xr<float>(n, c->scal, d32, q32, e32, r32, c->partials, c->st,
+                                    FinSpec{c->scal, 3, 2, FIN_STORE, 0.0});
+            CK(cudaGetLastError());
+            s = read_scal(c);
+            if (s != PARIS_OK) return s;
+            ++iters;
+            const double in_rr = c->scal_h->red[0];
+            if (!(in_rr == in_rr) || c->scal_h->red[2] > 0) break;  // non-finite: the FP64 residual decides
+            if (in_rr <= target || in_rr > 1e6 * rr32) break;
+            launch_hmg_vcycle32(P, c->hmg, r32, z32, nu1, nu2, 8, omega, c->st);
+            // flexible CG(1): beta = -(z . q) / (d . q) with the new z
+            launch_dot2<float>(n, z32, r32, q32, c->partials, c->st, FinSpec{c->scal, 2, 0, FIN_FCG_BETA, 0.0});
+            launch_xpby<float>(n, c->scal, z32, d32, c->st);
+        }
+        launch_hmg_accumulate(g, e32, c->scal, us, c->st);  // u* += e / scale
+        CK(cudaGetLastError());
     }
     const Scal& h = *c->scal_h;
     if (st) {
         st->iters = iters;
-        st->outer_iters = restarts + 1;
+        st->outer_iters = outer;
         st->rel_res_l2 = h.bnorm2 > 0 ? std::sqrt(h.rr / h.bnorm2) : 0.0;
         st->rel_res_linf = h.binf > 0 ? h.rinf / h.binf : 0.0;
         st->converged = converged ? 1 : 0;
