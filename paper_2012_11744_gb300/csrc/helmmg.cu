@@ -89,6 +89,104 @@ __global__ void __launch_bounds__(kTX* kTY) hmg_smooth_kernel(HLev L, const floa
     }
 }
 
+// One colour of red-black Gauss-Seidel with a thread per pair of cells
+// (2t, 2t+1) of a row: the member of the pass's colour is updated, so every
+// thread works on every plane of its z-segment.  Same update as the
+// column kernel above.
+__global__ void __launch_bounds__(kTX* kTY) hmg_rbgs_pair_kernel(HLev L, const float* __restrict__ f,
+                                                                const float* __restrict__ sig, float* x, int color,
+                                                                float omega) {
+    const int t = blockIdx.x * kTX + threadIdx.x, j = blockIdx.y * kTY + threadIdx.y;
+    if (2 * t >= L.m[0] || j >= L.m[1]) return;
+    const int k0 = blockIdx.z * kZ, k1 = min(k0 + kZ, L.m[2]);
+    for (int k = k0; k < k1; ++k) {
+        const int i = 2 * t + ((j + k + color) & 1);
+        if (i >= L.m[0]) continue;
+        const int c = hidx(L, i, j, k);
+        float acc, dg;
+        hnb<float>(L, x, i, j, k, acc, dg);
+        const float xc = x[c];
+        const float gs = fmaf(acc, L.ih2, f[c]) / fmaf(dg, L.ih2, sig[c]);
+        x[c] = fmaf(omega, gs - xc, xc);
+    }
+}
+
+// The same colour pass with a thread per four cells 4q .. 4q+3 of a row
+// (rows of m0 % 4 == 0 cells, at least a warp's worth): every array read as
+// 16-byte vectors, the two cells of the pass's colour updated, the
+// x-neighbours outside the quad from the adjacent lanes (or loaded at the
+// edges of the warp), the quad stored back whole (the other two cells
+// unchanged: no thread writes them in this pass).  M: the updated member of
+// both pairs of the quad ((j + k + color) & 1, uniform per row).
+template <int M>
+__device__ __forceinline__ void hrb4_row(const HLev& L, const float* __restrict__ f, const float* __restrict__ sig,
+                                         float* x, float omega, int j, int k, int i0, int lane, bool act) {
+    const int m0 = L.m[0], m1 = L.m[1], m2 = L.m[2], pl = m0 * m1;
+    const int rowc = (k * m1 + j) * m0, c0 = rowc + i0;
+    const bool py = L.kind[1] == HELM_PERIODIC, pz = L.kind[2] == HELM_PERIODIC;
+    // neighbour rows and planes: present (or wrapped) and their offsets
+    const bool hym = py ? m1 > 1 : j > 0, hyp = py ? m1 > 1 : j < m1 - 1;
+    const bool hzm = pz ? m2 > 1 : k > 0, hzp = pz ? m2 > 1 : k < m2 - 1;
+    const int oym = j > 0 ? -m0 : (m1 - 1) * m0, oyp = j < m1 - 1 ? m0 : -(m1 - 1) * m0;
+    const int ozm = k > 0 ? -pl : (m2 - 1) * pl, ozp = k < m2 - 1 ? pl : -(m2 - 1) * pl;
+    float X[4], F[4], S[4], YM[4] = {0.f, 0.f, 0.f, 0.f}, YP[4] = {0.f, 0.f, 0.f, 0.f},
+                                ZM[4] = {0.f, 0.f, 0.f, 0.f}, ZP[4] = {0.f, 0.f, 0.f, 0.f};
+    auto ld = [](float (&d)[4], const float* p) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        d[0] = v.x;
+        d[1] = v.y;
+        d[2] = v.z;
+        d[3] = v.w;
+    };
+    ld(X, x + c0);
+    ld(F, f + c0);
+    ld(S, sig + c0);
+    if (hym) ld(YM, x + c0 + oym);
+    if (hyp) ld(YP, x + c0 + oyp);
+    if (hzm) ld(ZM, x + c0 + ozm);
+    if (hzp) ld(ZP, x + c0 + ozp);
+    // x of the cells next to the quad (i0-1 and i0+4): wrapped along a periodic
+    // axis, absent (0) beyond the ends of the other kinds
+    const bool px = L.kind[0] == HELM_PERIODIC;
+    const int il = i0 > 0 ? i0 - 1 : m0 - 1, ir = i0 + 4 < m0 ? i0 + 4 : 0;
+    const bool hxl = px ? m0 > 1 : i0 > 0, hxr = px ? m0 > 1 : i0 + 4 < m0;
+    const float xl_sh = __shfl_up_sync(0xffffffffu, X[3], 1), xr_sh = __shfl_down_sync(0xffffffffu, X[0], 1);
+    const float xl_ld = hxl ? x[rowc + il] : 0.f, xr_ld = hxr ? x[rowc + ir] : 0.f;
+    const float xl = (lane > 0 && i0 > 0) ? xl_sh : xl_ld;
+    const float xr = (lane < kTX - 1 && i0 + 4 < m0) ? xr_sh : xr_ld;
+    // Laplacian diagonal counts of the y and z axes (uniform per row)
+    auto ends = [](int kind, int m, int p) {
+        if (kind == HELM_PERIODIC) return m > 1 ? 2.f : 0.f;
+        return kind == HELM_NOSLIP ? 2.f + (float)((p == 0) + (p == m - 1)) : 2.f;
+    };
+    const float dyz = ends(L.kind[1], m1, j) + ends(L.kind[2], m2, k);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int li = 2 * u + M, i = i0 + li;
+        const float lo = li > 0 ? X[li - 1] : xl, hi = li < 3 ? X[li + 1] : xr;
+        const float acc = ((lo + hi) + (YM[li] + YP[li])) + (ZM[li] + ZP[li]);
+        const float dg = ends(L.kind[0], m0, i) + dyz;
+        const float gs = fmaf(acc, L.ih2, F[li]) / fmaf(dg, L.ih2, S[li]);
+        X[li] = fmaf(omega, gs - X[li], X[li]);
+    }
+    if (act) *reinterpret_cast<float4*>(x + c0) = make_float4(X[0], X[1], X[2], X[3]);
+}
+
+__global__ void __launch_bounds__(kTX* kTY) hmg_rb4_kernel(HLev L, const float* __restrict__ f,
+                                                          const float* __restrict__ sig, float* x, int color,
+                                                          float omega) {
+    const int j = blockIdx.y * kTY + threadIdx.y;
+    if (j >= L.m[1]) return;  // uniform per warp
+    const int k = blockIdx.z, lane = threadIdx.x;
+    const int nq = L.m[0] / 4, q = blockIdx.x * kTX + lane;
+    const bool act = q < nq;
+    const int i0 = 4 * (act ? q : nq - 1);  // idle lanes shadow the last quad (no stores)
+    if (((j + k + color) & 1) == 0)
+        hrb4_row<0>(L, f, sig, x, omega, j, k, i0, lane, act);
+    else
+        hrb4_row<1>(L, f, sig, x, omega, j, k, i0, lane, act);
+}
+
 // r = f - A x on a level (FP32)
 __global__ void __launch_bounds__(kTX* kTY) hmg_residual_kernel(HLev L, const float* __restrict__ f,
                                                                const float* __restrict__ sig,
@@ -96,6 +194,7 @@ __global__ void __launch_bounds__(kTX* kTY) hmg_residual_kernel(HLev L, const fl
     const int i = blockIdx.x * kTX + threadIdx.x, j = blockIdx.y * kTY + threadIdx.y;
     if (i >= L.m[0] || j >= L.m[1]) return;
     const int k0 = blockIdx.z * kZ, k1 = min(k0 + kZ, L.m[2]);
+#pragma unroll 4
     for (int k = k0; k < k1; ++k) {
         const int c = hidx(L, i, j, k);
         float acc, dg;
@@ -308,6 +407,7 @@ __global__ void __launch_bounds__(kTX* kTY) hmg_matvec32_kernel(HLev L, const fl
     float dq = 0.f;
     if (i < L.m[0] && j < L.m[1]) {
         const int k0 = blockIdx.z * kZ, k1 = min(k0 + kZ, L.m[2]);
+#pragma unroll 4
         for (int k = k0; k < k1; ++k) {
             const int c = hidx(L, i, j, k);
             float acc, dg;
@@ -462,12 +562,22 @@ static void hmg_vcycle_core(const HelmPlan& P, const HelmWork& W, const float* f
     auto smooth = [&](int l, int sweeps, bool reverse) {
         const HLev L = hlev(P.lv[l]);
         const dim3 gr = hgrid(P.lv[l].m, kZ);
-        if (rb_ok(P.lv[l])) {
+        const bool quads = P.lv[l].m[0] % 4 == 0 && P.lv[l].m[0] >= 4 * kTX &&
+                           ((uintptr_t)F(l) | (uintptr_t)W.sig[l] | (uintptr_t)X(l)) % 16 == 0;
+        if (rb_ok(P.lv[l]) && quads) {
+            const dim3 g4((P.lv[l].m[0] / 4 + kTX - 1) / kTX, (P.lv[l].m[1] + kTY - 1) / kTY, P.lv[l].m[2]);
             for (int s = 0; s < sweeps; ++s)
                 for (int h = 0; h < 2; ++h) {
                     const int color = reverse ? 1 - h : h;
-                    hmg_smooth_kernel<false><<<gr, dim3(kTX, kTY), 0, st>>>(L, F(l), W.sig[l], X(l), X(l),
-                                                                           color, omega);
+                    hmg_rb4_kernel<<<g4, dim3(kTX, kTY), 0, st>>>(L, F(l), W.sig[l], X(l), color, omega);
+                    count_launch();
+                }
+        } else if (rb_ok(P.lv[l])) {
+            const dim3 gp(((P.lv[l].m[0] + 1) / 2 + kTX - 1) / kTX, gr.y, gr.z);
+            for (int s = 0; s < sweeps; ++s)
+                for (int h = 0; h < 2; ++h) {
+                    const int color = reverse ? 1 - h : h;
+                    hmg_rbgs_pair_kernel<<<gp, dim3(kTX, kTY), 0, st>>>(L, F(l), W.sig[l], X(l), color, omega);
                     count_launch();
                 }
         } else {  // damped Jacobi, ping-pong through the level's residual buffer, ending in x

@@ -900,8 +900,11 @@ __device__ __forceinline__ void tile_apply(const Geo& g, const float* __restrict
 // block covers the two planes of one coarse plane (np = 2), and the two fine
 // rows of a coarse cell are the warps 2m, 2m+1 of the block, added through
 // shared memory.
+#ifndef PARIS_OP_MINB
+#define PARIS_OP_MINB 3
+#endif
 template <bool RESTRICT, int V>
-__global__ void __launch_bounds__(kBX* kVY, 3) op_rho_tile_kernel(Geo g, const float* __restrict__ rh, float ih2,
+__global__ void __launch_bounds__(kBX* kVY, PARIS_OP_MINB) op_rho_tile_kernel(Geo g, const float* __restrict__ rh, float ih2,
                                                              const float* __restrict__ x,
                                                              const float* __restrict__ f,
                                                              float* __restrict__ out, Geo cg,
@@ -968,7 +971,10 @@ __global__ void __launch_bounds__(kBX* kVY, 3) op_rho_tile_kernel(Geo g, const f
     }
 }
 
-constexpr int kTileOpPlanes = 8;  // planes per block of the tile product
+#ifndef PARIS_OP_PLANES
+#define PARIS_OP_PLANES 8
+#endif
+constexpr int kTileOpPlanes = PARIS_OP_PLANES;  // planes per block of the tile product
 
 int64_t rho0_matvec_blocks(const Geo& g) {
     // the most blocks any segment length (>= 2 planes) gives, or the plane tiles
