@@ -172,6 +172,99 @@ __device__ __forceinline__ void hrb4_row(const HLev& L, const float* __restrict_
     if (act) *reinterpret_cast<float4*>(x + c0) = make_float4(X[0], X[1], X[2], X[3]);
 }
 
+// (A x) of the four cells 4q .. 4q+3 of a row (the quad layout of
+// hrb4_row: 16-byte vectors, x-neighbours from the adjacent lanes); X: x of
+// the quad as loaded.  Same per-cell arithmetic as hmg_residual_kernel.
+__device__ __forceinline__ void hop4(const HLev& L, const float* __restrict__ x, const float* __restrict__ sig,
+                                     int j, int k, int i0, int lane, float (&X)[4], float (&AX)[4]) {
+    const int m0 = L.m[0], m1 = L.m[1], m2 = L.m[2], pl = m0 * m1;
+    const int rowc = (k * m1 + j) * m0, c0 = rowc + i0;
+    const bool py = L.kind[1] == HELM_PERIODIC, pz = L.kind[2] == HELM_PERIODIC, px = L.kind[0] == HELM_PERIODIC;
+    const bool hym = py ? m1 > 1 : j > 0, hyp = py ? m1 > 1 : j < m1 - 1;
+    const bool hzm = pz ? m2 > 1 : k > 0, hzp = pz ? m2 > 1 : k < m2 - 1;
+    const int oym = j > 0 ? -m0 : (m1 - 1) * m0, oyp = j < m1 - 1 ? m0 : -(m1 - 1) * m0;
+    const int ozm = k > 0 ? -pl : (m2 - 1) * pl, ozp = k < m2 - 1 ? pl : -(m2 - 1) * pl;
+    float S[4], YM[4] = {0.f, 0.f, 0.f, 0.f}, YP[4] = {0.f, 0.f, 0.f, 0.f}, ZM[4] = {0.f, 0.f, 0.f, 0.f},
+                ZP[4] = {0.f, 0.f, 0.f, 0.f};
+    auto ld = [](float (&d)[4], const float* p) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+        d[0] = v.x;
+        d[1] = v.y;
+        d[2] = v.z;
+        d[3] = v.w;
+    };
+    ld(X, x + c0);
+    ld(S, sig + c0);
+    if (hym) ld(YM, x + c0 + oym);
+    if (hyp) ld(YP, x + c0 + oyp);
+    if (hzm) ld(ZM, x + c0 + ozm);
+    if (hzp) ld(ZP, x + c0 + ozp);
+    const int il = i0 > 0 ? i0 - 1 : m0 - 1, ir = i0 + 4 < m0 ? i0 + 4 : 0;
+    const bool hxl = px ? m0 > 1 : i0 > 0, hxr = px ? m0 > 1 : i0 + 4 < m0;
+    const float xl_sh = __shfl_up_sync(0xffffffffu, X[3], 1), xr_sh = __shfl_down_sync(0xffffffffu, X[0], 1);
+    const float xl_ld = hxl ? __ldg(x + rowc + il) : 0.f, xr_ld = hxr ? __ldg(x + rowc + ir) : 0.f;
+    const float xl = (lane > 0 && i0 > 0) ? xl_sh : xl_ld;
+    const float xr = (lane < kTX - 1 && i0 + 4 < m0) ? xr_sh : xr_ld;
+    auto ends = [](int kind, int m, int p) {
+        if (kind == HELM_PERIODIC) return m > 1 ? 2.f : 0.f;
+        return kind == HELM_NOSLIP ? 2.f + (float)((p == 0) + (p == m - 1)) : 2.f;
+    };
+    const float dyz = ends(L.kind[1], m1, j) + ends(L.kind[2], m2, k);
+#pragma unroll
+    for (int li = 0; li < 4; ++li) {
+        const float lo = li > 0 ? X[li - 1] : xl, hi = li < 3 ? X[li + 1] : xr;
+        const float acc = ((lo + hi) + (YM[li] + YP[li])) + (ZM[li] + ZP[li]);
+        const float dg = ends(L.kind[0], m0, i0 + li) + dyz;
+        AX[li] = fmaf(dg, L.ih2, S[li]) * X[li] - acc * L.ih2;
+    }
+}
+
+// r = f - A x (quads)
+__global__ void __launch_bounds__(kTX* kTY) hmg_residual4_kernel(HLev L, const float* __restrict__ f,
+                                                                const float* __restrict__ sig,
+                                                                const float* __restrict__ x, float* __restrict__ r) {
+    const int j = blockIdx.y * kTY + threadIdx.y;
+    if (j >= L.m[1]) return;
+    const int k = blockIdx.z, lane = threadIdx.x;
+    const int nq = L.m[0] / 4, q = blockIdx.x * kTX + lane;
+    const bool act = q < nq;
+    const int i0 = 4 * (act ? q : nq - 1);
+    float X[4], AX[4];
+    hop4(L, x, sig, j, k, i0, lane, X, AX);
+    if (act) {
+        const int c0 = (k * L.m[1] + j) * L.m[0] + i0;
+        const float4 fv = __ldg(reinterpret_cast<const float4*>(f + c0));
+        *reinterpret_cast<float4*>(r + c0) = make_float4(fv.x - AX[0], fv.y - AX[1], fv.z - AX[2], fv.w - AX[3]);
+    }
+}
+
+// q = A d (quads) and the partials of d . q
+__global__ void __launch_bounds__(kTX* kTY) hmg_matvec4_kernel(HLev L, const float* __restrict__ sig,
+                                                              const float* __restrict__ d, float* __restrict__ q,
+                                                              double* partials, FinSpec fin) {
+    const int j = blockIdx.y * kTY + threadIdx.y;
+    const int tid = threadIdx.y * kTX + threadIdx.x;
+    const int jc = j < L.m[1] ? j : L.m[1] - 1;  // idle rows shadow the last row (no stores)
+    const int k = blockIdx.z, lane = threadIdx.x;
+    const int nq = L.m[0] / 4, qq = blockIdx.x * kTX + lane;
+    const bool act = qq < nq && j < L.m[1];
+    const int i0 = 4 * (qq < nq ? qq : nq - 1);
+    float X[4], AX[4];
+    hop4(L, d, sig, jc, k, i0, lane, X, AX);
+    float dq = 0.f;
+    if (act) {
+        const int c0 = (k * L.m[1] + jc) * L.m[0] + i0;
+        *reinterpret_cast<float4*>(q + c0) = make_float4(AX[0], AX[1], AX[2], AX[3]);
+#pragma unroll
+        for (int li = 0; li < 4; ++li) dq = fmaf(X[li], AX[li], dq);
+    }
+    double accd[1] = {(double)dq};
+    const int op[1] = {0};
+    block_reduce_store<1>(accd, op, partials, ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x,
+                          tid);
+    finalize_last_block(partials, (int64_t)gridDim.x * gridDim.y * gridDim.z, fin, tid);
+}
+
 __global__ void __launch_bounds__(kTX* kTY) hmg_rb4_kernel(HLev L, const float* __restrict__ f,
                                                           const float* __restrict__ sig, float* x, int color,
                                                           float omega) {
@@ -598,7 +691,14 @@ static void hmg_vcycle_core(const HelmPlan& P, const HelmWork& W, const float* f
         }
         smooth(l, nu1, false);
         const HLev L = hlev(P.lv[l]), Cg = hlev(P.lv[l + 1]);
-        hmg_residual_kernel<<<hgrid(P.lv[l].m, kZ), dim3(kTX, kTY), 0, st>>>(L, F(l), W.sig[l], X(l), W.r[l]);
+        const bool q4 = P.lv[l].m[0] % 4 == 0 && P.lv[l].m[0] >= 4 * kTX &&
+                        ((uintptr_t)F(l) | (uintptr_t)W.sig[l] | (uintptr_t)X(l) | (uintptr_t)W.r[l]) % 16 == 0;
+        if (q4)
+            hmg_residual4_kernel<<<dim3((P.lv[l].m[0] / 4 + kTX - 1) / kTX, (P.lv[l].m[1] + kTY - 1) / kTY,
+                                        P.lv[l].m[2]),
+                                   dim3(kTX, kTY), 0, st>>>(L, F(l), W.sig[l], X(l), W.r[l]);
+        else
+            hmg_residual_kernel<<<hgrid(P.lv[l].m, kZ), dim3(kTX, kTY), 0, st>>>(L, F(l), W.sig[l], X(l), W.r[l]);
         dim3 gr((Cg.m[0] + kTX - 1) / kTX, (Cg.m[1] + kTY - 1) / kTY, Cg.m[2]);
         hmg_restrict_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(L, Cg, W.r[l], W.f[l + 1]);
         count_launch(2);
@@ -624,6 +724,17 @@ namespace paris {
 int64_t launch_hmg_matvec32(const HelmPlan& P, const float* sig, const float* d, float* q, double* partials,
                             cudaStream_t st, FinSpec fin) {
     const HLev L = hlev(P.lv[0]);
+    // quads where the rows fill a warp; one partial per block, within the
+    // context's partial slots (four per block of the z-loop grid)
+    const int64_t blocks4 = (int64_t)((L.m[0] / 4 + kTX - 1) / kTX) * ((L.m[1] + kTY - 1) / kTY) * L.m[2];
+    const dim3 gz = hgrid(P.lv[0].m, kZ);
+    if (L.m[0] % 4 == 0 && L.m[0] >= 4 * kTX && ((uintptr_t)sig | (uintptr_t)d | (uintptr_t)q) % 16 == 0 &&
+        blocks4 <= 4 * (int64_t)gz.x * gz.y * gz.z) {
+        const dim3 g4((L.m[0] / 4 + kTX - 1) / kTX, (L.m[1] + kTY - 1) / kTY, L.m[2]);
+        hmg_matvec4_kernel<<<g4, dim3(kTX, kTY), 0, st>>>(L, sig, d, q, partials, fin);
+        count_launch();
+        return blocks4;
+    }
     const dim3 gr = hgrid(P.lv[0].m, kZ);
     hmg_matvec32_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(L, sig, d, q, partials, fin);
     count_launch();
