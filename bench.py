@@ -547,8 +547,10 @@ def run_paris(args, rank, world, local):
                      "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
                      "peak_kind": peak_kind, "launches": pk["timed"],
                      "avg_launch_us": 1e3 * pk["ms"] / max(pk["timed"], 1),
-                     "timing": f"events around each launch of the class over {args.steps} further "
-                               f"steps ({ms_prof / args.steps:.2f} ms/step with the events)",
+                     "timing": f"CUDA events on the launching stream over {args.steps} further steps "
+                               f"({ms_prof / args.steps:.2f} ms/step with the events): one pair around each "
+                               f"smoothing phase's back-to-back finest-level passes (smooth0, 4 launches), "
+                               f"one around each launch of the other classes",
                      "stream_read_only_gbs": stream_read, "stream_triad_gbs": stream_triad},
         "kernel_classes": {k: {"launches": v["timed"], "ms": v["ms"],
                                "gbs": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else None}

@@ -72,6 +72,7 @@ struct Profiler {
     std::vector<cudaEvent_t> ev;  // 2 per slot
     std::vector<int> slot_cls;
     std::vector<double> slot_bytes;
+    std::vector<int> slot_n;  // launches bracketed by the slot's event pair
     int used = 0;
     int64_t launches[PARIS_K_COUNT] = {};
 };
@@ -279,14 +280,17 @@ paris_status read_scal(paris_ctx* c) {
 struct ProfScope {
     paris_ctx* c;
     int slot = -1;
-    ProfScope(paris_ctx* c_, int cls, double bytes) : c(c_) {
+    // n: the launches the pair brackets (consecutive launches of one class
+    // share a pair, so that the pair's own cost is spread over them)
+    ProfScope(paris_ctx* c_, int cls, double bytes, int n = 1) : c(c_) {
         Profiler& P = c->prof;
         if (!P.on || cls < 0) return;
-        P.launches[cls]++;
+        P.launches[cls] += n;
         if (P.used < kProfPool) {
             slot = P.used++;
             P.slot_cls[slot] = cls;
             P.slot_bytes[slot] = bytes;
+            P.slot_n[slot] = n;
             cudaEventRecord(P.ev[2 * slot], c->st);
         }
     }
@@ -374,7 +378,32 @@ void smooth(paris_ctx* c, int l, const Coef<T>& cf, const T* f, T* x, int sweeps
         const int S = o.slab_planes > 0 ? o.slab_planes : nz;
         const int m = (nz + S - 1) / S;
         const bool slabs = o.slab_planes > 0 && m >= 4;
-        const double per_plane = 1.0 / nz;
+        // the finest level's passes of this smoothing phase run back to back:
+        // one event pair brackets all of them (their bytes and launch count
+        // summed), so that the pair's own cost is spread over the phase
+        int phase_cls = -1;
+        double phase_bytes = 0.0;
+        int phase_n = 0;
+        if (cls >= 0) {
+            // bytes per pass: x at every cell (neighbours and the updated colour),
+            // f and the write of the updated colour, plus the coefficients
+            // (three face arrays, or rho/2 once); a zero-initial pass reads no x
+            // and writes both colours (plane-tile zero pass: the updated colour
+            // only, and the pass after it reads neither colour's old value of its
+            // own cells)
+            for (int s = 0; s < sweeps; ++s) {
+                const bool z0 = first_zero && s == 0;
+                const bool v0 = sizeof(T) == 4 && l == 0 && c->rho0;
+                const bool h16 = sizeof(T) == 4 && l == 0 && c->half0;
+                const double bsz = h16 ? 2.0 : (double)sz;
+                const bool tile0 = v0 && rho0_tile_pass(L.g, o.level0_tiles);
+                phase_bytes += v0 ? (z0 ? (tile0 ? 2.0 : 2.5) : 3.0) * n * sz : (z0 ? 2 * n * sz : 2.5 * n * sz + nb * bsz);
+                phase_bytes += v0 ? ((z0 && tile0) ? 2.5 : 3.0) * n * sz : 2.5 * n * sz + nb * bsz;
+                phase_n += slabs ? 2 * m : 2;
+            }
+            phase_cls = cls;
+        }
+        ProfScope phase(c, phase_cls, phase_bytes, phase_n);
         for (int s = 0; s < sweeps; ++s) {
             const bool z0 = first_zero && s == 0;
             const int c0 = reverse ? 1 : 0;
@@ -383,16 +412,6 @@ void smooth(paris_ctx* c, int l, const Coef<T>& cf, const T* f, T* x, int sweeps
             const bool h16 = sizeof(T) == 4 && l == 0 && c->half0;
             const bool v0 = sizeof(T) == 4 && l == 0 && c->rho0;
             const double bsz = h16 ? 2.0 : (double)sz;
-            // bytes per pass: x at every cell (neighbours and the updated colour),
-            // f and the write of the updated colour, plus the coefficients
-            // (three face arrays, or rho/2 once); a zero-initial pass reads no x
-            // and writes both colours
-            // (plane-tile zero pass: the updated colour only, and the pass after it
-            // reads neither colour's old value of its own cells)
-            const bool tile0 = v0 && rho0_tile_pass(L.g, o.level0_tiles);
-            const double b_first = v0 ? (z0 ? (tile0 ? 2.0 : 2.5) : 3.0) * n * sz
-                                      : (z0 ? 2 * n * sz : 2.5 * n * sz + nb * bsz);
-            const double b_second = v0 ? ((z0 && tile0) ? 2.5 : 3.0) * n * sz : 2.5 * n * sz + nb * bsz;
             auto pass = [&](int color, bool zero, int a, int b) {
                 if constexpr (sizeof(T) == 4) {
                     if (v0) {
@@ -411,14 +430,8 @@ void smooth(paris_ctx* c, int l, const Coef<T>& cf, const T* f, T* x, int sweeps
                 }
                 launch_rbgs<T>(L.g, cf, Prec<T>::w(L), f, x, color, o.omega, zero, c->st, a, b);
             };
-            auto first = [&](int a, int b) {
-                ProfScope ps(c, cls, b_first * (b - a) * per_plane);
-                pass(c0, z0, a, b);
-            };
-            auto second = [&](int a, int b) {
-                ProfScope ps(c, cls, b_second * (b - a) * per_plane);
-                pass(1 - c0, false, a, b);
-            };
+            auto first = [&](int a, int b) { pass(c0, z0, a, b); };
+            auto second = [&](int a, int b) { pass(1 - c0, false, a, b); };
             if (!slabs) {
                 first(0, nz);
                 second(0, nz);
@@ -981,6 +994,7 @@ paris_status paris_profile(paris_ctx* c, int enable) {
         for (auto& e : P.ev) CK(cudaEventCreate(&e));
         P.slot_cls.resize(kProfPool);
         P.slot_bytes.resize(kProfPool);
+        P.slot_n.resize(kProfPool);
     }
     if (enable) {
         CK(cudaStreamSynchronize(c->st));
@@ -1003,7 +1017,7 @@ paris_status paris_profile_read(paris_ctx* c, int cls, paris_kernel_prof* out) {
         if (P.slot_cls[s] != cls) continue;
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, P.ev[2 * s], P.ev[2 * s + 1]));
-        out->timed += 1;
+        out->timed += P.slot_n[s];
         out->ms += ms;
         out->bytes += P.slot_bytes[s];
     }
