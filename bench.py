@@ -54,7 +54,7 @@ NCU_TRAFFIC = {
     # "ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
     #  -k regex:rbgs_rho_tile -c 24" of "bench.py --single mixed": zero-initial passes
     # 115.2 MB, the passes after them 152.9 MB, the others 186.7 MB; 11, 11 and 66 per solve
-    "smooth0": {"bytes_per_launch": 173.5e6, "source": "rho0.cu", "sha": "6e7a9fcff9c59395"},
+    "smooth0": {"bytes_per_launch": 173.5e6, "source": "rho0.cu", "sha": "2ed75e0262fbb7aa"},
 }
 
 

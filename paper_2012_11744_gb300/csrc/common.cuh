@@ -217,6 +217,13 @@ __device__ inline double f2d_scaled(float v, int s) {
     return __hiloint2double((int)(sign | ((unsigned)de << 20) | (frac >> 3)), (int)(frac << 29));
 }
 
+// Programmatic dependent launch: a kernel launched with launch_pdl may start
+// while the kernel before it on the stream is finishing; it waits here for
+// that kernel's completion (and its memory) before touching anything the
+// earlier kernel writes.  Without the launch attribute the wait returns at
+// once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ------------------------------------------------------------ reductions ---
 
 __device__ inline double warp_sum(double v) {

@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(kTX* kTY) hmg_smooth_kernel(HLev L, const floa
 __global__ void __launch_bounds__(kTX* kTY) hmg_rbgs_pair_kernel(HLev L, const float* __restrict__ f,
                                                                 const float* __restrict__ sig, float* x, int color,
                                                                 float omega) {
+    pdl_wait();
     const int t = blockIdx.x * kTX + threadIdx.x, j = blockIdx.y * kTY + threadIdx.y;
     if (2 * t >= L.m[0] || j >= L.m[1]) return;
     const int k0 = blockIdx.z * kZ, k1 = min(k0 + kZ, L.m[2]);
@@ -223,6 +224,7 @@ __device__ __forceinline__ void hop4(const HLev& L, const float* __restrict__ x,
 __global__ void __launch_bounds__(kTX* kTY) hmg_residual4_kernel(HLev L, const float* __restrict__ f,
                                                                 const float* __restrict__ sig,
                                                                 const float* __restrict__ x, float* __restrict__ r) {
+    pdl_wait();
     const int j = blockIdx.y * kTY + threadIdx.y;
     if (j >= L.m[1]) return;
     const int k = blockIdx.z, lane = threadIdx.x;
@@ -242,6 +244,7 @@ __global__ void __launch_bounds__(kTX* kTY) hmg_residual4_kernel(HLev L, const f
 __global__ void __launch_bounds__(kTX* kTY) hmg_matvec4_kernel(HLev L, const float* __restrict__ sig,
                                                               const float* __restrict__ d, float* __restrict__ q,
                                                               double* partials, FinSpec fin) {
+    pdl_wait();
     const int j = blockIdx.y * kTY + threadIdx.y;
     const int tid = threadIdx.y * kTX + threadIdx.x;
     const int jc = j < L.m[1] ? j : L.m[1] - 1;  // idle rows shadow the last row (no stores)
@@ -268,6 +271,7 @@ __global__ void __launch_bounds__(kTX* kTY) hmg_matvec4_kernel(HLev L, const flo
 __global__ void __launch_bounds__(kTX* kTY) hmg_rb4_kernel(HLev L, const float* __restrict__ f,
                                                           const float* __restrict__ sig, float* x, int color,
                                                           float omega) {
+    pdl_wait();
     const int j = blockIdx.y * kTY + threadIdx.y;
     if (j >= L.m[1]) return;  // uniform per warp
     const int k = blockIdx.z, lane = threadIdx.x;
@@ -284,6 +288,7 @@ __global__ void __launch_bounds__(kTX* kTY) hmg_rb4_kernel(HLev L, const float* 
 __global__ void __launch_bounds__(kTX* kTY) hmg_residual_kernel(HLev L, const float* __restrict__ f,
                                                                const float* __restrict__ sig,
                                                                const float* __restrict__ x, float* __restrict__ r) {
+    pdl_wait();
     const int i = blockIdx.x * kTX + threadIdx.x, j = blockIdx.y * kTY + threadIdx.y;
     if (i >= L.m[0] || j >= L.m[1]) return;
     const int k0 = blockIdx.z * kZ, k1 = min(k0 + kZ, L.m[2]);
@@ -327,6 +332,7 @@ __device__ __forceinline__ Kids kids(int kind, int I) {
 // coarse = R fine (tensor product of the per-axis weights)
 __global__ void __launch_bounds__(kTX* kTY) hmg_restrict_kernel(HLev F, HLev Cg, const float* __restrict__ fine,
                                                                float* __restrict__ coarse) {
+    pdl_wait();
     const int I = blockIdx.x * kTX + threadIdx.x, J = blockIdx.y * kTY + threadIdx.y, K = blockIdx.z;
     if (I >= Cg.m[0] || J >= Cg.m[1]) return;
     const Kids a = kids(F.kind[0], I), b = kids(F.kind[1], J), c = kids(F.kind[2], K);
@@ -372,6 +378,7 @@ __device__ __forceinline__ Pars parents(int kind, int i, int mc) {
 // x += P e (tensor product)
 __global__ void __launch_bounds__(kTX* kTY) hmg_prolong_kernel(HLev F, HLev Cg, const float* __restrict__ e,
                                                               float* __restrict__ x) {
+    pdl_wait();
     const int i = blockIdx.x * kTX + threadIdx.x, j = blockIdx.y * kTY + threadIdx.y, k = blockIdx.z;
     if (i >= F.m[0] || j >= F.m[1]) return;
     const Pars a = parents(F.kind[0], i, Cg.m[0]), b = parents(F.kind[1], j, Cg.m[1]),
@@ -465,6 +472,7 @@ __global__ void __launch_bounds__(kTX* kTY) hmg_residual64_kernel(HelmGeo g, con
                                                                  const double* __restrict__ us,
                                                                  double* __restrict__ r, double* partials,
                                                                  FinSpec fin) {
+    pdl_wait();
     const int i = blockIdx.x * kTX + threadIdx.x, j = blockIdx.y * kTY + threadIdx.y;
     const int tid = threadIdx.y * kTX + threadIdx.x;
     double l2 = 0.0;
@@ -495,6 +503,7 @@ __global__ void __launch_bounds__(kTX* kTY) hmg_residual64_kernel(HelmGeo g, con
 __global__ void __launch_bounds__(kTX* kTY) hmg_matvec32_kernel(HLev L, const float* __restrict__ sig,
                                                                const float* __restrict__ d, float* __restrict__ q,
                                                                double* partials, FinSpec fin) {
+    pdl_wait();
     const int i = blockIdx.x * kTX + threadIdx.x, j = blockIdx.y * kTY + threadIdx.y;
     const int tid = threadIdx.y * kTX + threadIdx.x;
     float dq = 0.f;
@@ -522,6 +531,7 @@ __global__ void __launch_bounds__(kTX* kTY) hmg_matvec32_kernel(HLev L, const fl
 // kept until the correction is accumulated); partials of |r32|^2, max |r32|
 __global__ void hmg_scale_d2f_kernel(int64_t n, const double* __restrict__ r, const Scal* __restrict__ s,
                                      float* __restrict__ r32, double* partials, FinSpec fin) {
+    pdl_wait();
     const double sc = s->scale;
     float l2 = 0.f, mx = 0.f;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
@@ -539,6 +549,7 @@ __global__ void hmg_scale_d2f_kernel(int64_t n, const double* __restrict__ r, co
 // u* += e / scale on the unknowns of the face array
 __global__ void __launch_bounds__(kTX* kTY) hmg_accumulate_kernel(HelmGeo g, const float* __restrict__ e,
                                                                  const Scal* __restrict__ s, double* __restrict__ us) {
+    pdl_wait();
     const int i = blockIdx.x * kTX + threadIdx.x, j = blockIdx.y * kTY + threadIdx.y;
     if (i >= g.m[0] || j >= g.m[1]) return;
     const double inv = s->inv_scale;
@@ -625,7 +636,7 @@ void launch_hmg_sigma(const HelmPlan& P, float* const* sig, cudaStream_t st) {
     for (int l = 0; l + 1 < P.nl; ++l) {
         const HLev F = hlev(P.lv[l]), Cg = hlev(P.lv[l + 1]);
         dim3 gr((Cg.m[0] + kTX - 1) / kTX, (Cg.m[1] + kTY - 1) / kTY, Cg.m[2]);
-        hmg_restrict_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(F, Cg, sig[l], sig[l + 1]);
+        launch_pdl(hmg_restrict_kernel, gr, dim3(kTX, kTY), 0, st, F, Cg, sig[l], sig[l + 1]);
         count_launch();
     }
 }
@@ -633,7 +644,7 @@ void launch_hmg_sigma(const HelmPlan& P, float* const* sig, cudaStream_t st) {
 int64_t launch_hmg_residual64(const HelmGeo& g, const double* un, const double* sig, const double* us, double* r,
                               double* partials, cudaStream_t st, FinSpec fin) {
     const dim3 gr = hgrid(g.m, kZ);
-    hmg_residual64_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(g, un, sig, us, r, partials, fin);
+    launch_pdl(hmg_residual64_kernel, gr, dim3(kTX, kTY), 0, st, g, un, sig, us, r, partials, fin);
     count_launch();
     return (int64_t)gr.x * gr.y * gr.z;
 }
@@ -662,7 +673,8 @@ static void hmg_vcycle_core(const HelmPlan& P, const HelmWork& W, const float* f
             for (int s = 0; s < sweeps; ++s)
                 for (int h = 0; h < 2; ++h) {
                     const int color = reverse ? 1 - h : h;
-                    hmg_rb4_kernel<<<g4, dim3(kTX, kTY), 0, st>>>(L, F(l), W.sig[l], X(l), color, omega);
+                    launch_pdl(hmg_rb4_kernel, g4, dim3(kTX, kTY), 0, st, L, F(l), W.sig[l], X(l), color,
+                        omega);
                     count_launch();
                 }
         } else if (rb_ok(P.lv[l])) {
@@ -670,7 +682,8 @@ static void hmg_vcycle_core(const HelmPlan& P, const HelmWork& W, const float* f
             for (int s = 0; s < sweeps; ++s)
                 for (int h = 0; h < 2; ++h) {
                     const int color = reverse ? 1 - h : h;
-                    hmg_rbgs_pair_kernel<<<gp, dim3(kTX, kTY), 0, st>>>(L, F(l), W.sig[l], X(l), color, omega);
+                    launch_pdl(hmg_rbgs_pair_kernel, gp, dim3(kTX, kTY), 0, st, L, F(l), W.sig[l], X(l), color,
+                        omega);
                     count_launch();
                 }
         } else {  // damped Jacobi, ping-pong through the level's residual buffer, ending in x
@@ -694,19 +707,20 @@ static void hmg_vcycle_core(const HelmPlan& P, const HelmWork& W, const float* f
         const bool q4 = P.lv[l].m[0] % 4 == 0 && P.lv[l].m[0] >= 4 * kTX &&
                         ((uintptr_t)F(l) | (uintptr_t)W.sig[l] | (uintptr_t)X(l) | (uintptr_t)W.r[l]) % 16 == 0;
         if (q4)
-            hmg_residual4_kernel<<<dim3((P.lv[l].m[0] / 4 + kTX - 1) / kTX, (P.lv[l].m[1] + kTY - 1) / kTY,
-                                        P.lv[l].m[2]),
-                                   dim3(kTX, kTY), 0, st>>>(L, F(l), W.sig[l], X(l), W.r[l]);
+            launch_pdl(hmg_residual4_kernel,
+                       dim3((P.lv[l].m[0] / 4 + kTX - 1) / kTX, (P.lv[l].m[1] + kTY - 1) / kTY, P.lv[l].m[2]),
+                       dim3(kTX, kTY), 0, st, L, F(l), W.sig[l], X(l), W.r[l]);
         else
-            hmg_residual_kernel<<<hgrid(P.lv[l].m, kZ), dim3(kTX, kTY), 0, st>>>(L, F(l), W.sig[l], X(l), W.r[l]);
+            launch_pdl(hmg_residual_kernel, hgrid(P.lv[l].m, kZ), dim3(kTX, kTY), 0, st, L, F(l), W.sig[l],
+                X(l), W.r[l]);
         dim3 gr((Cg.m[0] + kTX - 1) / kTX, (Cg.m[1] + kTY - 1) / kTY, Cg.m[2]);
-        hmg_restrict_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(L, Cg, W.r[l], W.f[l + 1]);
+        launch_pdl(hmg_restrict_kernel, gr, dim3(kTX, kTY), 0, st, L, Cg, W.r[l], W.f[l + 1]);
         count_launch(2);
     }
     for (int l = P.nl - 2; l >= 0; --l) {
         const HLev L = hlev(P.lv[l]), Cg = hlev(P.lv[l + 1]);
         dim3 gr((L.m[0] + kTX - 1) / kTX, (L.m[1] + kTY - 1) / kTY, L.m[2]);
-        hmg_prolong_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(L, Cg, X(l + 1), X(l));
+        launch_pdl(hmg_prolong_kernel, gr, dim3(kTX, kTY), 0, st, L, Cg, X(l + 1), X(l));
         count_launch();
         smooth(l, nu2, true);
     }
@@ -731,12 +745,12 @@ int64_t launch_hmg_matvec32(const HelmPlan& P, const float* sig, const float* d,
     if (L.m[0] % 4 == 0 && L.m[0] >= 4 * kTX && ((uintptr_t)sig | (uintptr_t)d | (uintptr_t)q) % 16 == 0 &&
         blocks4 <= 4 * (int64_t)gz.x * gz.y * gz.z) {
         const dim3 g4((L.m[0] / 4 + kTX - 1) / kTX, (L.m[1] + kTY - 1) / kTY, L.m[2]);
-        hmg_matvec4_kernel<<<g4, dim3(kTX, kTY), 0, st>>>(L, sig, d, q, partials, fin);
+        launch_pdl(hmg_matvec4_kernel, g4, dim3(kTX, kTY), 0, st, L, sig, d, q, partials, fin);
         count_launch();
         return blocks4;
     }
     const dim3 gr = hgrid(P.lv[0].m, kZ);
-    hmg_matvec32_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(L, sig, d, q, partials, fin);
+    launch_pdl(hmg_matvec32_kernel, gr, dim3(kTX, kTY), 0, st, L, sig, d, q, partials, fin);
     count_launch();
     return (int64_t)gr.x * gr.y * gr.z;
 }
@@ -744,13 +758,13 @@ int64_t launch_hmg_matvec32(const HelmPlan& P, const float* sig, const float* d,
 int64_t launch_hmg_scale_d2f(int64_t n, const double* r, const Scal* s, float* r32, double* partials,
                              cudaStream_t st, FinSpec fin) {
     const int nb = elementwise_blocks(n);
-    hmg_scale_d2f_kernel<<<nb, kRedThreads, 0, st>>>(n, r, s, r32, partials, fin);
+    launch_pdl(hmg_scale_d2f_kernel, nb, kRedThreads, 0, st, n, r, s, r32, partials, fin);
     count_launch();
     return nb;
 }
 
 void launch_hmg_accumulate(const HelmGeo& g, const float* e, const Scal* s, double* us, cudaStream_t st) {
-    hmg_accumulate_kernel<<<hgrid(g.m, kZ), dim3(kTX, kTY), 0, st>>>(g, e, s, us);
+    launch_pdl(hmg_accumulate_kernel, hgrid(g.m, kZ), dim3(kTX, kTY), 0, st, g, e, s, us);
     count_launch();
 }
 

@@ -724,6 +724,7 @@ __global__ void __launch_bounds__(kTX* kTY) rbgs_kernel(Geo g, const TB* __restr
                                                        const T* __restrict__ w,
                                                        const T* __restrict__ f, T* __restrict__ x,
                                                        int color, T omega, int zero_init, int k0) {
+    pdl_wait();
     const int t = blockIdx.x * kTX + threadIdx.x;
     const int j = blockIdx.y * kTY + threadIdx.y;
     const int k = k0 + blockIdx.z;
@@ -872,6 +873,7 @@ __global__ void __launch_bounds__(kTX* kTY) rbgs4_kernel(Geo g, const T* __restr
                                                         const T* __restrict__ w,
                                                         const T* __restrict__ f, T* __restrict__ x,
                                                         int color, T omega, int zero_init, int k0) {
+    pdl_wait();
     const int j = blockIdx.y * kTY + threadIdx.y;
     if (j >= g.ny) return;  // uniform per warp
     const int k = k0 + blockIdx.z;
@@ -896,11 +898,11 @@ void launch_rbgs(const Geo& g, const Coef<T>& cf, const T* w, const T* f, T* x, 
         aligned16(x) && (sizeof(T) == 4 || aligned16(w))) {
         dim3 gr((g.nx / 4 + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, k1 - k0);
         if (sizeof(T) == 8)
-            rbgs4_kernel<T, true><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf.bx, cf.by, cf.bz, cf.scale, w, f, x, color,
-                                                                 (T)omega, zero_init ? 1 : 0, k0);
+            launch_pdl(rbgs4_kernel<T, true>, gr, dim3(kTX, kTY), 0, st, g, cf.bx, cf.by, cf.bz, cf.scale, w, f,
+                x, color, (T)omega, zero_init ? 1 : 0, k0);
         else
-            rbgs4_kernel<T, false><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf.bx, cf.by, cf.bz, cf.scale, w, f, x, color,
-                                                                  (T)omega, zero_init ? 1 : 0, k0);
+            launch_pdl(rbgs4_kernel<T, false>, gr, dim3(kTX, kTY), 0, st, g, cf.bx, cf.by, cf.bz, cf.scale, w,
+                f, x, color, (T)omega, zero_init ? 1 : 0, k0);
         count_launch();
         return;
     }
@@ -911,18 +913,18 @@ void launch_rbgs(const Geo& g, const Coef<T>& cf, const T* w, const T* f, T* x, 
     const bool i32 = fits_i32(g);
     if (sizeof(T) == 8) {
         if (i32)
-            rbgs_kernel<T, T, true, true><<<gr, dim3(kTX, kTY), 0, st>>>(
-                g, cf.bx, cf.by, cf.bz, cf.scale, w, f, x, color, (T)omega, zero_init ? 1 : 0, k0);
+            launch_pdl(rbgs_kernel<T, T, true, true>, gr, dim3(kTX, kTY), 0, st, g, cf.bx, cf.by, cf.bz,
+                cf.scale, w, f, x, color, (T)omega, zero_init ? 1 : 0, k0);
         else
-            rbgs_kernel<T, T, true, false><<<gr, dim3(kTX, kTY), 0, st>>>(
-                g, cf.bx, cf.by, cf.bz, cf.scale, w, f, x, color, (T)omega, zero_init ? 1 : 0, k0);
+            launch_pdl(rbgs_kernel<T, T, true, false>, gr, dim3(kTX, kTY), 0, st, g, cf.bx, cf.by, cf.bz,
+                cf.scale, w, f, x, color, (T)omega, zero_init ? 1 : 0, k0);
     } else {
         if (i32)
-            rbgs_kernel<T, T, false, true><<<gr, dim3(kTX, kTY), 0, st>>>(
-                g, cf.bx, cf.by, cf.bz, cf.scale, w, f, x, color, (T)omega, zero_init ? 1 : 0, k0);
+            launch_pdl(rbgs_kernel<T, T, false, true>, gr, dim3(kTX, kTY), 0, st, g, cf.bx, cf.by, cf.bz,
+                cf.scale, w, f, x, color, (T)omega, zero_init ? 1 : 0, k0);
         else
-            rbgs_kernel<T, T, false, false><<<gr, dim3(kTX, kTY), 0, st>>>(
-                g, cf.bx, cf.by, cf.bz, cf.scale, w, f, x, color, (T)omega, zero_init ? 1 : 0, k0);
+            launch_pdl(rbgs_kernel<T, T, false, false>, gr, dim3(kTX, kTY), 0, st, g, cf.bx, cf.by, cf.bz,
+                cf.scale, w, f, x, color, (T)omega, zero_init ? 1 : 0, k0);
     }
     count_launch();
 }
@@ -933,11 +935,11 @@ void launch_rbgs_h(const Geo& g, const __half* const b[3], float scale, const fl
     const int npair = (g.nx + 1) / 2;
     dim3 gr((npair + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, k1 - k0);
     if (fits_i32(g))
-        rbgs_kernel<float, __half, false, true><<<gr, dim3(kTX, kTY), 0, st>>>(
-            g, b[0], b[1], b[2], scale, nullptr, f, x, color, (float)omega, zero_init ? 1 : 0, k0);
+        launch_pdl(rbgs_kernel<float, __half, false, true>, gr, dim3(kTX, kTY), 0, st, g, b[0], b[1], b[2],
+            scale, nullptr, f, x, color, (float)omega, zero_init ? 1 : 0, k0);
     else
-        rbgs_kernel<float, __half, false, false><<<gr, dim3(kTX, kTY), 0, st>>>(
-            g, b[0], b[1], b[2], scale, nullptr, f, x, color, (float)omega, zero_init ? 1 : 0, k0);
+        launch_pdl(rbgs_kernel<float, __half, false, false>, gr, dim3(kTX, kTY), 0, st, g, b[0], b[1], b[2],
+            scale, nullptr, f, x, color, (float)omega, zero_init ? 1 : 0, k0);
     count_launch();
 }
 
@@ -987,6 +989,7 @@ __global__ void restrict_residual_kernel(Geo fg, const TB* __restrict__ bx, cons
                                          const TB* __restrict__ bz, T scale, const T* __restrict__ f,
                                          const T* __restrict__ x, Geo cg, int fa0, int fa1,
                                          int fa2, T* __restrict__ fc) {
+    pdl_wait();
     const int I = blockIdx.x * kTX + threadIdx.x;
     const int J = blockIdx.y * kTY + threadIdx.y;
     const int K = blockIdx.z;
@@ -1016,11 +1019,11 @@ void launch_restrict_residual(const Geo& fine, const Coef<T>& cf, const T* f, co
                              const Geo& coarse, const int fac[3], T* fc, cudaStream_t st) {
     dim3 gr((coarse.nx + kTX - 1) / kTX, (coarse.ny + kTY - 1) / kTY, coarse.nz);
     if (fits_i32(fine))
-        restrict_residual_kernel<T, T, true><<<gr, dim3(kTX, kTY), 0, st>>>(
-            fine, cf.bx, cf.by, cf.bz, cf.scale, f, x, coarse, fac[0], fac[1], fac[2], fc);
+        launch_pdl(restrict_residual_kernel<T, T, true>, gr, dim3(kTX, kTY), 0, st, fine, cf.bx, cf.by, cf.bz,
+            cf.scale, f, x, coarse, fac[0], fac[1], fac[2], fc);
     else
-        restrict_residual_kernel<T, T, false><<<gr, dim3(kTX, kTY), 0, st>>>(
-            fine, cf.bx, cf.by, cf.bz, cf.scale, f, x, coarse, fac[0], fac[1], fac[2], fc);
+        launch_pdl(restrict_residual_kernel<T, T, false>, gr, dim3(kTX, kTY), 0, st, fine, cf.bx, cf.by, cf.bz,
+            cf.scale, f, x, coarse, fac[0], fac[1], fac[2], fc);
     count_launch();
 }
 
@@ -1029,11 +1032,11 @@ void launch_restrict_residual_h(const Geo& fine, const __half* const b[3], float
                                 cudaStream_t st) {
     dim3 gr((coarse.nx + kTX - 1) / kTX, (coarse.ny + kTY - 1) / kTY, coarse.nz);
     if (fits_i32(fine))
-        restrict_residual_kernel<float, __half, true><<<gr, dim3(kTX, kTY), 0, st>>>(
-            fine, b[0], b[1], b[2], scale, f, x, coarse, fac[0], fac[1], fac[2], fc);
+        launch_pdl(restrict_residual_kernel<float, __half, true>, gr, dim3(kTX, kTY), 0, st, fine, b[0], b[1],
+            b[2], scale, f, x, coarse, fac[0], fac[1], fac[2], fc);
     else
-        restrict_residual_kernel<float, __half, false><<<gr, dim3(kTX, kTY), 0, st>>>(
-            fine, b[0], b[1], b[2], scale, f, x, coarse, fac[0], fac[1], fac[2], fc);
+        launch_pdl(restrict_residual_kernel<float, __half, false>, gr, dim3(kTX, kTY), 0, st, fine, b[0], b[1],
+            b[2], scale, f, x, coarse, fac[0], fac[1], fac[2], fc);
     count_launch();
 }
 
@@ -1054,6 +1057,7 @@ void launch_convert_beta_half(const Geo& g, const double* const b64[3], __half* 
 template <typename T>
 __global__ void prolong_add_kernel(Geo fg, Geo cg, int fa0, int fa1, int fa2,
                                    const T* __restrict__ xc, T* __restrict__ x) {
+    pdl_wait();
     const int i = blockIdx.x * kTX + threadIdx.x;
     const int j = blockIdx.y * kTY + threadIdx.y;
     const int k = blockIdx.z;
@@ -1065,6 +1069,7 @@ __global__ void prolong_add_kernel(Geo fg, Geo cg, int fa0, int fa1, int fa2,
 // x_fine += x_coarse[parent] for four x-consecutive fine cells per thread
 // (all axes halved, nx % 4 == 0, 16-byte aligned x)
 __global__ void prolong_add4_kernel(Geo fg, Geo cg, const float* __restrict__ xc, float* __restrict__ x) {
+    pdl_wait();
     const int q = blockIdx.x * kTX + threadIdx.x;  // quad index along x
     const int j = blockIdx.y * kTY + threadIdx.y;
     const int k = blockIdx.z;
@@ -1086,14 +1091,14 @@ void launch_prolong_add(const Geo& fine, const Geo& coarse, const int fac[3], co
     if constexpr (sizeof(T) == 4) {
         if (fac[0] == 2 && fac[1] == 2 && fac[2] == 2 && fine.nx % 4 == 0 && aligned16(x)) {
             dim3 gr((fine.nx / 4 + kTX - 1) / kTX, (fine.ny + kTY - 1) / kTY, fine.nz);
-            prolong_add4_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(fine, coarse, (const float*)xc, (float*)x);
+            launch_pdl(prolong_add4_kernel, gr, dim3(kTX, kTY), 0, st, fine, coarse, (const float*)xc,
+                (float*)x);
             count_launch();
             return;
         }
     }
     dim3 gr((fine.nx + kTX - 1) / kTX, (fine.ny + kTY - 1) / kTY, fine.nz);
-    prolong_add_kernel<T><<<gr, dim3(kTX, kTY), 0, st>>>(fine, coarse, fac[0], fac[1], fac[2], xc,
-                                                         x);
+    launch_pdl(prolong_add_kernel<T>, gr, dim3(kTX, kTY), 0, st, fine, coarse, fac[0], fac[1], fac[2], xc, x);
     count_launch();
 }
 
@@ -1111,6 +1116,7 @@ __global__ void __launch_bounds__(kTX* kTY) residual64_kernel(Geo g, Coef<double
                                                               float* __restrict__ r32,
                                                               const Scal* s, double* partials,
                                                               int zero_ok, int split, FinSpec fin) {
+    pdl_wait();
     const int i = blockIdx.x * kTX + threadIdx.x;
     const int j = blockIdx.y * kTY + threadIdx.y;
     double l2 = 0.0;
@@ -1165,11 +1171,11 @@ int64_t launch_residual64(const Geo& g, const Coef<double>& cf, const double* f,
                           cudaStream_t st, FinSpec fin, bool split) {
     dim3 gr = tile_grid(g, kZ);
     if (fits_i32(g))
-        residual64_kernel<true><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, f, x, r64, r32, s, partials,
-                                                               zero_ok ? 1 : 0, split ? 1 : 0, fin);
+        launch_pdl(residual64_kernel<true>, gr, dim3(kTX, kTY), 0, st, g, cf, f, x, r64, r32, s, partials,
+            zero_ok ? 1 : 0, split ? 1 : 0, fin);
     else
-        residual64_kernel<false><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, f, x, r64, r32, s, partials,
-                                                                zero_ok ? 1 : 0, split ? 1 : 0, fin);
+        launch_pdl(residual64_kernel<false>, gr, dim3(kTX, kTY), 0, st, g, cf, f, x, r64, r32, s, partials,
+            zero_ok ? 1 : 0, split ? 1 : 0, fin);
     count_launch();
     return nblocks_of(gr);
 }
@@ -1234,6 +1240,7 @@ __global__ void update_xr_kernel(int64_t n, const Scal* s, const T* __restrict__
     using VT = typename V16<T>::type;
     constexpr int W = V16<T>::n;
     constexpr int U = kKU / 2;  // four arrays per element: two iterations at once
+    pdl_wait();
     const T alpha = (T)s->alpha;
     T l2[U], li[U];
 #pragma unroll
@@ -1306,8 +1313,8 @@ template <typename T>
 int64_t launch_update_xr(int64_t n, const Scal* s, const T* d, const T* q, T* x, T* r,
                          double* partials, cudaStream_t st, FinSpec fin) {
     int nb = elementwise_blocks(n);
-    update_xr_kernel<T><<<nb, kRedThreads, 0, st>>>(n, s, d, q, x, r, partials,
-                                                    aligned16(d, q, x, r) ? 1 : 0, fin);
+    launch_pdl(update_xr_kernel<T>, dim3(nb), dim3(kRedThreads), 0, st, n, s, d, q, x, r, partials,
+               aligned16(d, q, x, r) ? 1 : 0, fin);
     count_launch();
     return nb;
 }
@@ -1318,6 +1325,7 @@ __global__ void dot2_kernel(int64_t n, const T* __restrict__ a, const T* __restr
     using VT = typename V16<T>::type;
     constexpr int W = V16<T>::n;
     constexpr int U = kKU;
+    pdl_wait();
     T s0[U], s1[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) s0[u] = s1[u] = T(0);
@@ -1374,7 +1382,8 @@ template <typename T>
 int64_t launch_dot2(int64_t n, const T* a, const T* b, const T* c, double* partials,
                     cudaStream_t st, FinSpec fin) {
     int nb = elementwise_blocks(n);
-    dot2_kernel<T><<<nb, kRedThreads, 0, st>>>(n, a, b, c, partials, aligned16(a, b, c) ? 1 : 0, fin);
+    launch_pdl(dot2_kernel<T>, dim3(nb), dim3(kRedThreads), 0, st, n, a, b, c, partials,
+               aligned16(a, b, c) ? 1 : 0, fin);
     count_launch();
     return nb;
 }
@@ -1384,6 +1393,7 @@ __global__ void xpby_kernel(int64_t n, const Scal* s, const T* __restrict__ z, T
                             int vec) {
     using VT = typename V16<T>::type;
     constexpr int W = V16<T>::n;
+    pdl_wait();
     const T beta = (T)s->beta;
     const int64_t nv = vec ? n / W : 0;
     PARIS_VEC_FOR(i, nv) {
@@ -1400,7 +1410,8 @@ __global__ void xpby_kernel(int64_t n, const Scal* s, const T* __restrict__ z, T
 
 template <typename T>
 void launch_xpby(int64_t n, const Scal* s, const T* z, T* d, cudaStream_t st) {
-    xpby_kernel<T><<<elementwise_blocks(n), kRedThreads, 0, st>>>(n, s, z, d, aligned16(z, d) ? 1 : 0);
+    launch_pdl(xpby_kernel<T>, dim3(elementwise_blocks(n)), dim3(kRedThreads), 0, st, n, s, z, d,
+               aligned16(z, d) ? 1 : 0);
     count_launch();
 }
 
@@ -1408,6 +1419,7 @@ void launch_xpby(int64_t n, const Scal* s, const T* z, T* d, cudaStream_t st) {
 // conversion with an exponent shift, then one FP64 addition.
 __global__ void accumulate_kernel(int64_t n, const Scal* s, const float* __restrict__ e,
                                   double* __restrict__ x, int vec) {
+    pdl_wait();
     const int sh = -(int)s->scale_exp;
     const int64_t nv = vec ? n / 4 : 0;
     PARIS_VEC_FOR(i, nv) {
@@ -1425,7 +1437,8 @@ __global__ void accumulate_kernel(int64_t n, const Scal* s, const float* __restr
 }
 
 void launch_accumulate(int64_t n, const Scal* s, const float* e, double* x, cudaStream_t st) {
-    accumulate_kernel<<<elementwise_blocks(n), kRedThreads, 0, st>>>(n, s, e, x, aligned16(e, x) ? 1 : 0);
+    launch_pdl(accumulate_kernel, elementwise_blocks(n), kRedThreads, 0, st, n, s, e, x,
+               aligned16(e, x) ? 1 : 0);
     count_launch();
 }
 

@@ -1,6 +1,8 @@
 // Host-side launchers of the projection kernels (internal to the library).
 #pragma once
 
+#include <utility>
+
 #include "common.cuh"
 
 namespace paris {
@@ -162,6 +164,26 @@ __device__ inline void finalize_last_block(const double* partials, int64_t nbloc
 // (triad_gbs, two read and one written), bytes moved over event time.
 cudaError_t stream_rates(const float* a, const float* b, const float* c, float* o, int64_t n, int reps,
                          double* read_gbs, double* triad_gbs, cudaStream_t st);
+
+// Launch with programmatic stream serialization: the launch is processed
+// while the preceding kernel on the stream runs, and the kernel (which must
+// call pdl_wait() before reading that kernel's results) starts as soon as
+// the preceding kernel completes.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Streaming multiprocessors of the current device (queried once per device).
 int device_sms();

@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(kTX* kTY) refine_rho_kernel(Geo g, const float
                                                             const double* r_old, double* r_new,
                                                             double* __restrict__ x, float* __restrict__ r32,
                                                             const Scal* s, double* partials, FinSpec fin) {
+    pdl_wait();
     const int i = blockIdx.x * kTX + threadIdx.x;
     const int j = blockIdx.y * kTY + threadIdx.y;
     float l2 = 0.f;
@@ -157,8 +158,8 @@ void launch_refine_rho(const Geo& g, const float2* rh2, double h, const float* e
     const float hi = (float)ih2d;
     const float lo = (float)(ih2d - (double)hi);
     dim3 gr((g.nx + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, (g.nz + kZ - 1) / kZ);
-    refine_rho_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(g, rh2, hi, lo, e, r_old, r_new, x, r32, s, partials,
-                                                     FinSpec{s, 3, 2, FIN_REFINE, 0.0});
+    launch_pdl(refine_rho_kernel, gr, dim3(kTX, kTY), 0, st, g, rh2, hi, lo, e, r_old, r_new, x, r32, s,
+        partials, FinSpec{s, 3, 2, FIN_REFINE, 0.0});
     count_launch();
 }
 

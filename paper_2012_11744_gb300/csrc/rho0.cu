@@ -561,6 +561,7 @@ template <bool ZERO, bool XZ, int V>
 __global__ void __launch_bounds__(kBX* kVY, PARIS_TILE_MINB) rbgs_rho_tile_kernel(Geo g, const float* __restrict__ rh, float h2,
                                                                const float* __restrict__ f, float* x,
                                                                int color, float omega, int k0) {
+    pdl_wait();
     const int j = blockIdx.y * kVY + threadIdx.y;
     if (j >= g.ny) return;  // uniform per warp
     const int k = k0 + blockIdx.z;
@@ -596,14 +597,14 @@ void launch_rbgs_rho(const Geo& g, const float* rh, double h, const float* f, fl
         constexpr int V = kTileV > 0 ? kTileV : 2;
         dim3 gr((hx / V + kBX - 1) / kBX, (g.ny + kVY - 1) / kVY, k1 - k0);
         if (zero_init)
-            rbgs_rho_tile_kernel<true, false, V><<<gr, dim3(kBX, kVY), 0, st>>>(g, rh, h2, f, x, color,
-                                                                                (float)omega, k0);
+            launch_pdl(rbgs_rho_tile_kernel<true, false, V>, gr, dim3(kBX, kVY), 0, st, g, rh, h2, f, x, color,
+                (float)omega, k0);
         else if (own_zero)
-            rbgs_rho_tile_kernel<false, true, V><<<gr, dim3(kBX, kVY), 0, st>>>(g, rh, h2, f, x, color,
-                                                                                (float)omega, k0);
+            launch_pdl(rbgs_rho_tile_kernel<false, true, V>, gr, dim3(kBX, kVY), 0, st, g, rh, h2, f, x, color,
+                (float)omega, k0);
         else
-            rbgs_rho_tile_kernel<false, false, V><<<gr, dim3(kBX, kVY), 0, st>>>(g, rh, h2, f, x, color,
-                                                                                 (float)omega, k0);
+            launch_pdl(rbgs_rho_tile_kernel<false, false, V>, gr, dim3(kBX, kVY), 0, st, g, rh, h2, f, x, color,
+                (float)omega, k0);
         count_launch();
         return;
     }
@@ -910,6 +911,7 @@ __global__ void __launch_bounds__(kBX* kVY, PARIS_OP_MINB) op_rho_tile_kernel(Ge
                                                              float* __restrict__ out, Geo cg,
                                                              double* partials, int np, FinSpec fin) {
     __shared__ float sh[kVY][kBX * V];
+    pdl_wait();
     const int ty = threadIdx.y, lane = threadIdx.x;
     const int j = blockIdx.y * kVY + ty;
     const bool row_ok = j < g.ny;
@@ -990,8 +992,8 @@ int64_t launch_matvec_rho(const Geo& g, const float* rh, double h, const float* 
     if (tiles && kTileOpV > 0 && hx % kTileOpV == 0) {
         constexpr int V = kTileOpV > 0 ? kTileOpV : 2;
         dim3 gr((hx / V + kBX - 1) / kBX, (g.ny + kVY - 1) / kVY, (g.nz + kTileOpPlanes - 1) / kTileOpPlanes);
-        op_rho_tile_kernel<false, V><<<gr, dim3(kBX, kVY), 0, st>>>(g, rh, (float)(1.0 / (h * h)), d, nullptr, q,
-                                                                    g, partials, kTileOpPlanes, fin);
+        launch_pdl(op_rho_tile_kernel<false, V>, gr, dim3(kBX, kVY), 0, st, g, rh, (float)(1.0 / (h * h)), d,
+            (const float*)nullptr, q, g, partials, kTileOpPlanes, fin);
         count_launch();
         return (int64_t)gr.x * gr.y * gr.z;
     }
@@ -1009,8 +1011,8 @@ void launch_restrict_rho(const Geo& g, const float* rh, double h, const float* f
     if (tiles && kTileOpV > 0 && hx % kTileOpV == 0) {
         constexpr int V = kTileOpV > 0 ? kTileOpV : 2;
         dim3 gr((hx / V + kBX - 1) / kBX, (g.ny + kVY - 1) / kVY, g.nz / 2);
-        op_rho_tile_kernel<true, V><<<gr, dim3(kBX, kVY), 0, st>>>(g, rh, (float)(1.0 / (h * h)), x, f, fc, cg,
-                                                                   nullptr, 2, no_fin());
+        launch_pdl(op_rho_tile_kernel<true, V>, gr, dim3(kBX, kVY), 0, st, g, rh, (float)(1.0 / (h * h)), x, f,
+            fc, cg, (double*)nullptr, 2, no_fin());
         count_launch();
         return;
     }
@@ -1028,6 +1030,7 @@ void launch_restrict_rho(const Geo& g, const float* rh, double h, const float* f
 // child of coarse cell (t, j/2, k/2).  V = 4: four entries per thread.
 template <int V>
 __global__ void prolong_split_kernel(Geo fg, Geo cg, const float* __restrict__ xc, float* __restrict__ x) {
+    pdl_wait();
     const int hx = fg.nx / 2;
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) * V;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -1056,8 +1059,8 @@ void launch_prolong_split(const Geo& fine, const Geo& coarse, const float* xc, f
     const int per = v4 ? 4 : 1;
     dim3 blk(32, 8);
     dim3 gr((hx / per + 31) / 32, (fine.ny + 7) / 8, fine.nz);
-    if (v4) prolong_split_kernel<4><<<gr, blk, 0, st>>>(fine, coarse, xc, x);
-    else prolong_split_kernel<1><<<gr, blk, 0, st>>>(fine, coarse, xc, x);
+    if (v4) launch_pdl(prolong_split_kernel<4>, gr, blk, 0, st, fine, coarse, xc, x);
+    else launch_pdl(prolong_split_kernel<1>, gr, blk, 0, st, fine, coarse, xc, x);
     count_launch();
 }
 

@@ -157,6 +157,7 @@ __device__ void tail_coarse_solve(const TailLevel<T>& L, const double* __restric
 // The level table itself lives in shared memory (Ls), pointing at either copy.
 template <typename T, bool USEW, bool SMEM>
 __global__ void __launch_bounds__(kTailThreads) tail_vcycle_kernel(const __grid_constant__ TailArgs<T> a) {
+    pdl_wait();
     __shared__ double fs[kMaxDenseCells];
     __shared__ double mean;
     __shared__ TailLevel<T> Ls[kMaxTail];
@@ -275,13 +276,13 @@ void launch_tail_vcycle(const TailLevel<T>* levels, int n, const double* Minv, d
             opted[use_w ? 1 : 0] = true;
         }
         if (use_w)
-            tail_vcycle_kernel<T, true, true><<<1, kTailThreads, smem, st>>>(a);
+            launch_pdl(tail_vcycle_kernel<T, true, true>, 1, kTailThreads, smem, st, a);
         else
-            tail_vcycle_kernel<T, false, true><<<1, kTailThreads, smem, st>>>(a);
+            launch_pdl(tail_vcycle_kernel<T, false, true>, 1, kTailThreads, smem, st, a);
     } else if (use_w) {
-        tail_vcycle_kernel<T, true, false><<<1, kTailThreads, 0, st>>>(a);
+        launch_pdl(tail_vcycle_kernel<T, true, false>, 1, kTailThreads, 0, st, a);
     } else {
-        tail_vcycle_kernel<T, false, false><<<1, kTailThreads, 0, st>>>(a);
+        launch_pdl(tail_vcycle_kernel<T, false, false>, 1, kTailThreads, 0, st, a);
     }
     count_launch();
 }
