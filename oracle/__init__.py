@@ -20,7 +20,10 @@ Solid cells (the "Lego" solids of Sec. 3.8: link flags that block the
 velocity and zero the pressure coefficients on the solid and its boundary)
 are in ``solid.py``.  The implicit viscous step of Sec. 3.2.3 (Eq. muelliptic) is in ``viscous.py``
 (numpy and scipy.sparse, FP64); the capillary (Eq. csf2) and gravity forcing
-of the predictor (Eq. nonconspredictedvel) in ``forcing.py`` (numpy, FP64).
+of the predictor (Eq. nonconspredictedvel) in ``forcing.py`` (numpy, FP64);
+the free-surface projections of Sec. 3.7.5 (the ghost-fluid Dirichlet solve
+in the liquid and the phantom projection in two gas layers) in
+``freesurf.py`` (numpy and scipy.sparse, FP64).
 """
 from __future__ import annotations
 
