@@ -338,6 +338,59 @@ paris_status paris_marker_function(paris_ctx* ctx, const double* gx, const doubl
                                    double mean_I, double* I, paris_stats* st);
 
 /* ---------------------------------------------------------------------------
+ * FREE-SURFACE PROJECTIONS (Sec. 3.7.5 "Free-surface flow solver", with the
+ * boundary condition of Eq. free_surf_norm_bc).  Only the liquid is solved;
+ * here C is the GAS volume fraction, as in that section (C = 0 in the
+ * liquid), and the liquid cells are those with C < 1/2.
+ *
+ * paris_free_surface_step: the projection in the liquid with the liquid
+ * density rho_l alone (beta = 1/rho_l).  A face between a liquid cell c and
+ * a gas cell g takes the gradient of Eq. mod_branches, (p_s - p_c)/(theta h),
+ * theta h the distance along the face's axis from c's node to the interface
+ * (theta in (0, 1], from the height function or a plane reconstruction; the
+ * caller's), and p_s the interface pressure of Eq. Laplace_num,
+ *     p_s = p_gas[g] + sigma (kappa[c] + kappa[g]) / 2,
+ * p_gas the gas pressure per cell (the polytropic law of Eq. polygas per gas
+ * pocket; the caller's).  The step forms rhs = (div u*) / dt in the liquid (wall
+ * faces carry no flux), solves the SPD system (no null space: every liquid
+ * region must touch the gas) in the FP64 form of the multigrid-preconditioned
+ * CG whatever opts.precision says, and corrects u = u* - dt beta grad p
+ * (Eq. fotm) on every face touching the liquid with the same gradients.
+ * Faces between two gas cells keep their values (the caller extrapolates
+ * them); wall faces are set to 0.  p: in, the initial guess in the liquid;
+ * out, the solution in the liquid and p_gas in the gas (0 without p_gas).
+ *   C, kappa, p_gas, p  cells (nx*ny*nz); kappa and p_gas may be NULL (0)
+ *   theta_x/y/z         face arrays (the layout of u, v, w), read on the
+ *                       liquid-gas faces only; all three NULL: theta = 1
+ *   u, v, w             face arrays, in u*, out the projected velocity
+ * All device pointers; the context must have no solid set.  Synchronises.
+ * Errors: INVALID_ARG (null C/u/v/w/p, rho_l or dt not finite and positive,
+ * sigma not finite, one or two theta arrays NULL, a solid set), NO_MEMORY
+ * (the free-surface work arrays, 9 bytes per cell plus the coarse levels,
+ * are allocated on the first call), NOT_CONVERGED, NONFINITE, CUDA.
+ *
+ * paris_phantom_projection: the second ("phantom") projection of "Ensuring
+ * volume conservation".  The unknowns are the first two layers of gas cells
+ * (layer 1: gas cells with a liquid face neighbour; layer 2: the other gas
+ * cells with a face neighbour in layer 1); the faces to the liquid keep
+ * their (solved) velocities and carry no gradient; the gas beyond the two
+ * layers holds phat = 0 (a Dirichlet condition at its cell centres).  It
+ * solves div grad phat = div u on the layers (no density, no dt; wall faces
+ * closed) and corrects u -= grad phat on the faces between two gas cells at
+ * least one of which is in the layers; every other face (wall faces
+ * included) is left as it is.  phat: in, the initial guess on the layers;
+ * out, phat on the layers and 0 elsewhere.  Each gas pocket must reach
+ * beyond two layers (else the system has no Dirichlet cell and, in general,
+ * no solution: NOT_CONVERGED).  Synchronises.  Errors: INVALID_ARG (a NULL
+ * pointer, a solid set), NO_MEMORY, NOT_CONVERGED, NONFINITE, CUDA. */
+paris_status paris_free_surface_step(paris_ctx* ctx, const double* C, double rho_l, double dt,
+                                     const double* theta_x, const double* theta_y, const double* theta_z,
+                                     const double* kappa, double sigma, const double* p_gas, double* u,
+                                     double* v, double* w, double* p, paris_stats* st);
+paris_status paris_phantom_projection(paris_ctx* ctx, const double* C, double* u, double* v, double* w,
+                                      double* phat, paris_stats* st);
+
+/* ---------------------------------------------------------------------------
  * IMPLICIT VISCOUS STEP (Sec. 3.2.3, Eq. muelliptic).  For one velocity
  * component, u* - tau nu_f Lap_h u* = u^n on the component's own face grid,
  * Lap_h the 7-point Laplacian with spacing h.  The unknowns are the

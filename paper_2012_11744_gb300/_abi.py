@@ -90,6 +90,9 @@ SIGNATURES = {
                                                 ct.POINTER(Stats)]),
     "paris_set_solid": (ct.c_int, [_P, _P]),
     "paris_marker_function": (ct.c_int, [_P, _P, _P, _P, _D, _P, ct.POINTER(Stats)]),
+    "paris_free_surface_step": (ct.c_int, [_P, _P, _D, _D, _P, _P, _P, _P, _D, _P, _P, _P, _P, _P,
+                                           ct.POINTER(Stats)]),
+    "paris_phantom_projection": (ct.c_int, [_P, _P, _P, _P, _P, _P, ct.POINTER(Stats)]),
     "paris_face_viscosity": (ct.c_int, [_P, ct.c_int, _P, _D, _D, _D, _D, _P]),
     "paris_viscous_solve": (ct.c_int, [_P, ct.c_int, _P, _D, _P, _P, _D, ct.c_int, ct.POINTER(Stats)]),
     "paris_viscous_solve_mg": (ct.c_int, [_P, ct.c_int, _P, _D, _P, _P, _D, ct.c_int, ct.POINTER(Stats)]),

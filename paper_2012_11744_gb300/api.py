@@ -252,6 +252,46 @@ class Context:
         d["status"] = s
         return I, d
 
+    def free_surface_step(self, C, rho_l, dt, u, v, w, p, p_gas=None, theta=None, kappa=None, sigma=0.0,
+                          check=True):
+        """Free-surface projection (Sec. 3.7.5): solved in the liquid (C < 1/2,
+        C the gas fraction), the gas a Dirichlet condition p_s = p_gas +
+        sigma (kappa_c + kappa_g)/2 at theta h from the liquid node (theta: three
+        face tensors or None for 1).  u, v, w, p in place; p_gas, kappa may be
+        None (0).  Returns the stats dict."""
+        g = self.grid
+        st = _abi.Stats()
+        none = ct.c_void_p(None)
+        th = [none] * 3 if theta is None else [self._t(t, g.face_shape(a), f"theta_{'xyz'[a]}")
+                                               for a, t in enumerate(theta)]
+        pg = none if p_gas is None else self._t(p_gas, g.shape, "p_gas")
+        kp = none if kappa is None else self._t(kappa, g.shape, "kappa")
+        s = self.lib.paris_free_surface_step(self._ptr, self._t(C, g.shape, "C"), float(rho_l), float(dt), *th, kp,
+                                             float(sigma), pg, self._t(u, g.face_shape(0), "u"),
+                                             self._t(v, g.face_shape(1), "v"), self._t(w, g.face_shape(2), "w"),
+                                             self._t(p, g.shape, "p"), ct.byref(st))
+        if check:
+            _abi.check(s, "paris_free_surface_step", st.as_dict())
+        d = st.as_dict()
+        d["status"] = s
+        return d
+
+    def phantom_projection(self, C, u, v, w, phat=None, check=True):
+        """Phantom projection in the first two gas layers (Sec. 3.7.5,
+        "Ensuring volume conservation"): u, v, w in place; returns (phat,
+        stats dict)."""
+        g = self.grid
+        phat = phat if phat is not None else torch.zeros(g.shape, dtype=torch.float64, device=self.device)
+        st = _abi.Stats()
+        s = self.lib.paris_phantom_projection(self._ptr, self._t(C, g.shape, "C"), self._t(u, g.face_shape(0), "u"),
+                                              self._t(v, g.face_shape(1), "v"), self._t(w, g.face_shape(2), "w"),
+                                              self._t(phat, g.shape, "phat"), ct.byref(st))
+        if check:
+            _abi.check(s, "paris_phantom_projection", st.as_dict())
+        d = st.as_dict()
+        d["status"] = s
+        return phat, d
+
     def predictor_forcing(self, C, kappa, rho1, rho2, sigma, gravity, tau, u, v, w, beta=None):
         """Capillary (CSF) and gravity forcing of the predictor: u, v, w (in
         u^n, out u* = u^n + tau a_f) in place; returns the face coefficients

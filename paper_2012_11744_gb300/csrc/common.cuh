@@ -38,13 +38,17 @@ struct Geo {
 };
 
 // Coefficient set of one level: face arrays and a uniform scale (1/h^2 for
-// arrays holding beta itself, 1 for arrays that are already scaled).
+// arrays holding beta itself, 1 for arrays that are already scaled), and an
+// optional per-cell diagonal excess sig in the units of the face arrays: the
+// operator is  (A x)_c = scale (sum_f beta_f (x_c - x_nb) + sig_c x_c),  the
+// form a Dirichlet condition at a cut face takes (Sec. 3.7.5); null: none.
 template <typename T>
 struct Coef {
     const T* bx;
     const T* by;
     const T* bz;
     T scale;
+    const T* sig = nullptr;
 };
 
 // Neighbour indices and + face index along one axis of length n.  Along a

@@ -580,9 +580,37 @@ void launch_coarse_beta(const Geo& fine, const Coef<T>& cf, const Geo& coarse, c
     }
 }
 
+// Coarse diagonal excess: the mean over the children of the fine one times
+// the fine level's scale (the coarse levels hold absolute coefficients), the
+// restriction of the fine equations (an average) applied to sig x with x
+// constant over the children.
+template <typename T>
+__global__ void coarse_sig_kernel(Geo fg, const T* __restrict__ sf, double scale, Geo cg, int fa0, int fa1,
+                                  int fa2, T* __restrict__ out) {
+    const int64_t total = cg.ncell();
+    PARIS_EW_FOR(t, total) {
+        const int I = (int)(t % cg.nx);
+        const int J = (int)((t / cg.nx) % cg.ny);
+        const int K = (int)(t / ((int64_t)cg.nx * cg.ny));
+        double sum = 0.0;
+        for (int dk = 0; dk < fa2; ++dk)
+            for (int dj = 0; dj < fa1; ++dj)
+                for (int di = 0; di < fa0; ++di)
+                    sum += (double)sf[fg.cidx(I * fa0 + di, J * fa1 + dj, K * fa2 + dk)];
+        out[t] = (T)(sum / (double)(fa0 * fa1 * fa2) * scale);
+    }
+}
 
-// w = 1 / sum_f beta_f (unscaled inverse diagonal; the smoother divides the
-// right-hand side by the level's scale).
+template <typename T>
+void launch_coarse_sig(const Geo& fine, const T* sig, double scale, const Geo& coarse, const int f[3], T* out,
+                       cudaStream_t st) {
+    coarse_sig_kernel<T><<<elementwise_blocks(coarse.ncell()), kRedThreads, 0, st>>>(fine, sig, scale, coarse,
+                                                                                      f[0], f[1], f[2], out);
+    count_launch();
+}
+
+// w = 1 / (sum_f beta_f + sig_c) (unscaled inverse diagonal; the smoother
+// divides the right-hand side by the level's scale).
 template <typename T>
 __global__ void inv_diag_kernel(Geo g, Coef<T> cf, T* __restrict__ w) {
     const int i = blockIdx.x * kTX + threadIdx.x;
@@ -591,7 +619,13 @@ __global__ void inv_diag_kernel(Geo g, Coef<T> cf, T* __restrict__ w) {
     if (i >= g.nx || j >= g.ny) return;
     Stencil<T> s;
     load_stencil(g, cf, i, j, k, s);
-    w[g.cidx(i, j, k)] = inv_sum6(s.b);
+    const int64_t c = g.cidx(i, j, k);
+    if (cf.sig) {  // the diagonal of a Dirichlet-coupled cell includes its excess
+        const T d = (((s.b[0] + s.b[1]) + (s.b[2] + s.b[3])) + (s.b[4] + s.b[5])) + cf.sig[c];
+        w[c] = d > T(0) ? rcp_rn(d) : T(0);
+    } else {
+        w[c] = inv_sum6(s.b);
+    }
 }
 
 template <typename T>
@@ -603,7 +637,7 @@ void launch_inv_diag(const Geo& g, const Coef<T>& cf, T* w, cudaStream_t st) {
 
 // Dense inverse of the coarsest operator regularised on its null space:
 // (A + a 1 1^T)^{-1} with a = mean(diag)/n, which maps a mean-free f to the
-// mean-free solution of A x = f.  FP64 Gauss-Jordan without pivoting (the
+// mean-free solution of A x = f (with a diagonal excess, cf.sig: A^{-1}).  FP64 Gauss-Jordan without pivoting (the
 // regularised matrix is SPD) by one CTA of 32 x 32 threads on a copy of the
 // matrix in shared memory (n <= 128: at most 129 KB); the elimination step
 // maps rows to threadIdx.y and columns to threadIdx.x.
@@ -628,6 +662,7 @@ __global__ void __launch_bounds__(1024) coarse_inverse_kernel(Geo g, Coef<T> cf,
             M[c * n + c] += b;
             M[c * n + (int)s.nb[q]] -= b;  // a self-neighbour (n = 1) cancels
         }
+        if (cf.sig) M[c * n + c] += (double)cf.sig[c] * (double)cf.scale;
     }
     __syncthreads();
     if (tid == 0) {
@@ -639,7 +674,8 @@ __global__ void __launch_bounds__(1024) coarse_inverse_kernel(Geo g, Coef<T> cf,
     // a cell with no open face (inside a solid, Sec. 3.8) has a zero row and
     // column: it is decoupled as an identity row and kept out of the
     // regularisation, which then acts on the constants of the other cells
-    const double a = dsum / ((double)n * (double)n);
+    // (a Dirichlet-coupled operator, cf.sig set, has no null space: no term)
+    const double a = cf.sig ? 0.0 : dsum / ((double)n * (double)n);
     for (int e = tid; e < n * n; e += nt) {
         const int r = e / n, cc = e % n;
         const bool ir = M[r * n + r] == 0.0, ic = M[cc * n + cc] == 0.0;
@@ -680,10 +716,11 @@ void launch_coarse_inverse(const Geo& g, const Coef<T>& cf, double* inv, cudaStr
     count_launch();
 }
 
-// x = M (f - mean f) on the coarsest level (FP64 arithmetic).
+// x = M (f - mean f) on the coarsest level (FP64 arithmetic); without the
+// mean when the operator has no null space (keep_mean).
 template <typename T>
 __global__ void coarse_solve_kernel(int n, const double* __restrict__ M, const T* __restrict__ f,
-                                    T* __restrict__ x) {
+                                    T* __restrict__ x, int keep_mean) {
     extern __shared__ double fs[];
     __shared__ double mean;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -692,7 +729,7 @@ __global__ void coarse_solve_kernel(int n, const double* __restrict__ M, const T
     if (tid == 0) {
         double t = 0.0;
         for (int c = 0; c < n; ++c) t += fs[c];
-        mean = t / (double)n;
+        mean = keep_mean ? 0.0 : t / (double)n;
     }
     __syncthreads();
     for (int r = tid; r < n; r += nt) {
@@ -703,9 +740,9 @@ __global__ void coarse_solve_kernel(int n, const double* __restrict__ M, const T
 }
 
 template <typename T>
-void launch_coarse_solve(const Geo& g, const double* inv, const T* f, T* x, cudaStream_t st) {
+void launch_coarse_solve(const Geo& g, const double* inv, const T* f, T* x, cudaStream_t st, bool keep_mean) {
     int n = (int)g.ncell();
-    coarse_solve_kernel<T><<<1, 128, sizeof(double) * n, st>>>(n, inv, f, x);
+    coarse_solve_kernel<T><<<1, 128, sizeof(double) * n, st>>>(n, inv, f, x, keep_mean ? 1 : 0);
     count_launch();
 }
 
@@ -988,7 +1025,7 @@ template <typename T, typename TB, bool I32>
 __global__ void restrict_residual_kernel(Geo fg, const TB* __restrict__ bx, const TB* __restrict__ by,
                                          const TB* __restrict__ bz, T scale, const T* __restrict__ f,
                                          const T* __restrict__ x, Geo cg, int fa0, int fa1,
-                                         int fa2, T* __restrict__ fc) {
+                                         int fa2, T* __restrict__ fc, const T* __restrict__ sig) {
     pdl_wait();
     const int I = blockIdx.x * kTX + threadIdx.x;
     const int J = blockIdx.y * kTY + threadIdx.y;
@@ -1009,7 +1046,9 @@ __global__ void restrict_residual_kernel(Geo fg, const TB* __restrict__ bx, cons
                     c = fg.cidx(i, j, k);
                     load_stencil_as<T>(fg, bx, by, bz, i, j, k, s);
                 }
-                sum += f[c] - apply_A(s, x, x[c], scale);
+                T ax = apply_A(s, x, x[c], scale);
+                if (sig) ax = fma(scale * sig[c], x[c], ax);
+                sum += f[c] - ax;
             }
     fc[cg.cidx(I, J, K)] = sum / T(fa0 * fa1 * fa2);
 }
@@ -1020,10 +1059,10 @@ void launch_restrict_residual(const Geo& fine, const Coef<T>& cf, const T* f, co
     dim3 gr((coarse.nx + kTX - 1) / kTX, (coarse.ny + kTY - 1) / kTY, coarse.nz);
     if (fits_i32(fine))
         launch_pdl(restrict_residual_kernel<T, T, true>, gr, dim3(kTX, kTY), 0, st, fine, cf.bx, cf.by, cf.bz,
-            cf.scale, f, x, coarse, fac[0], fac[1], fac[2], fc);
+            cf.scale, f, x, coarse, fac[0], fac[1], fac[2], fc, cf.sig);
     else
         launch_pdl(restrict_residual_kernel<T, T, false>, gr, dim3(kTX, kTY), 0, st, fine, cf.bx, cf.by, cf.bz,
-            cf.scale, f, x, coarse, fac[0], fac[1], fac[2], fc);
+            cf.scale, f, x, coarse, fac[0], fac[1], fac[2], fc, cf.sig);
     count_launch();
 }
 
@@ -1033,10 +1072,10 @@ void launch_restrict_residual_h(const Geo& fine, const __half* const b[3], float
     dim3 gr((coarse.nx + kTX - 1) / kTX, (coarse.ny + kTY - 1) / kTY, coarse.nz);
     if (fits_i32(fine))
         launch_pdl(restrict_residual_kernel<float, __half, true>, gr, dim3(kTX, kTY), 0, st, fine, b[0], b[1],
-            b[2], scale, f, x, coarse, fac[0], fac[1], fac[2], fc);
+            b[2], scale, f, x, coarse, fac[0], fac[1], fac[2], fc, (const float*)nullptr);
     else
         launch_pdl(restrict_residual_kernel<float, __half, false>, gr, dim3(kTX, kTY), 0, st, fine, b[0], b[1],
-            b[2], scale, f, x, coarse, fac[0], fac[1], fac[2], fc);
+            b[2], scale, f, x, coarse, fac[0], fac[1], fac[2], fc, (const float*)nullptr);
     count_launch();
 }
 
@@ -1147,6 +1186,7 @@ __global__ void __launch_bounds__(kTX* kTY) residual64_kernel(Geo g, Coef<double
                 double a = st.b[0] * (xc - x[st.nb[0]]);
 #pragma unroll
                 for (int q = 1; q < 6; ++q) a = fma(st.b[q], xc - x[st.nb[q]], a);
+                if (cf.sig) a = fma(cf.sig[c], xc, a);
                 r = fma(-cf.scale, a, f[c]);
             }
             if (r64) r64[c] = r;
@@ -1204,7 +1244,8 @@ __global__ void __launch_bounds__(kTX* kTY) matvec_dot_kernel(Geo g, Coef<T> cf,
                 load_stencil(g, cf, i, j, k, st);
             }
             const T dc = d[c];
-            const T qc = apply_A(st, d, dc, cf.scale);
+            T qc = apply_A(st, d, dc, cf.scale);
+            if (cf.sig) qc = fma(cf.scale * cf.sig[c], dc, qc);
             q[c] = qc;
             loc = fma(dc, qc, loc);
         })
@@ -1579,7 +1620,9 @@ cudaError_t stream_rates(const float* a, const float* b, const float* c, float* 
                                         const double[3], T* [3], cudaStream_t);                \
     template void launch_inv_diag<T>(const Geo&, const Coef<T>&, T*, cudaStream_t);            \
     template void launch_coarse_inverse<T>(const Geo&, const Coef<T>&, double*, cudaStream_t); \
-    template void launch_coarse_solve<T>(const Geo&, const double*, const T*, T*, cudaStream_t); \
+    template void launch_coarse_solve<T>(const Geo&, const double*, const T*, T*, cudaStream_t, bool); \
+    template void launch_coarse_sig<T>(const Geo&, const T*, double, const Geo&, const int[3], T*,     \
+                                       cudaStream_t);                                                  \
     template void launch_rbgs<T>(const Geo&, const Coef<T>&, const T*, const T*, T*, int,     \
                                  double, bool, cudaStream_t, int, int);                        \
     template void launch_jacobi<T>(const Geo&, const Coef<T>&, const T*, const T*, const T*,  \

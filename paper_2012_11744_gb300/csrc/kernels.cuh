@@ -232,6 +232,29 @@ int64_t launch_fluid_count(int64_t n, const unsigned char* s, double* partials, 
 void launch_unit_beta(const Geo& g, double* bx, double* by, double* bz, cudaStream_t st);
 void launch_add_constant(int64_t n, double* x, double a, cudaStream_t st);
 
+// free-surface projections (Sec. 3.7.5, freesurf.cu).  Cell classes: 1
+// unknown, 2 Dirichlet, 0 excluded.
+// liquid (C < 1/2) unknown, gas Dirichlet
+void launch_fs_liquid_classes(const Geo& g, const double* C, unsigned char* cls, cudaStream_t st);
+// the first two gas layers unknown, the liquid excluded, the gas beyond Dirichlet (tmp: scratch)
+void launch_fs_gas_layers(const Geo& g, const double* C, unsigned char* tmp, unsigned char* cls, cudaStream_t st);
+// beta on the faces between unknown cells (0 elsewhere), the diagonal excess
+// sig (sum of beta/theta over the Dirichlet faces) and gd = sum of
+// beta/(theta h^2) p_s, p_s = pd[d] + sigma (kappa_c + kappa_d)/2 (null pd,
+// kappa, theta: 0, 0, 1)
+void launch_fs_setup(const Geo& g, const unsigned char* cls, double beta, const double* const theta[3],
+                     const double* pd, const double* kappa, double sigma, double h, double* bx, double* by,
+                     double* bz, double* sig, double* gd, cudaStream_t st);
+// rhs = div u/(h dt) - gd on the unknown cells, 0 elsewhere (gd read from rhs)
+void launch_fs_rhs(const Geo& g, const unsigned char* cls, const double* u, const double* v, const double* w,
+                   double inv_hdt, double* rhs, cudaStream_t st);
+// u -= coef (cut-face gradient) on the faces touching an unknown cell
+void launch_fs_project(const Geo& g, const unsigned char* cls, const double* const theta[3], const double* p,
+                       const double* pd, const double* kappa, double sigma, double coef, bool zero_walls,
+                       double* u, double* v, double* w, cudaStream_t st);
+// p = pd (Dirichlet cells; 0 without pd) or 0 (excluded cells)
+void launch_fs_fill(const Geo& g, const unsigned char* cls, const double* pd, double* p, cudaStream_t st);
+
 // ------------------------------------------------- implicit viscous step ---
 // One velocity component of Sec. 3.2.3 (Eq. muelliptic) in SPD form,
 // (diag(1/(tau nu)) - Lap_h) u* = u^n/(tau nu), on its unknowns (viscous.cu).
@@ -354,8 +377,13 @@ void launch_inv_diag(const Geo& g, const Coef<T>& cf, T* w, cudaStream_t st);
 // dense (A + a 1 1^T)^{-1} of the coarsest operator, FP64, one CTA
 template <typename T>
 void launch_coarse_inverse(const Geo& g, const Coef<T>& cf, double* inv, cudaStream_t st);
+// x = inv (f - mean f); keep_mean: x = inv f (an operator without null space)
 template <typename T>
-void launch_coarse_solve(const Geo& g, const double* inv, const T* f, T* x, cudaStream_t st);
+void launch_coarse_solve(const Geo& g, const double* inv, const T* f, T* x, cudaStream_t st, bool keep_mean);
+// coarse diagonal excess (Coef::sig) from the fine one of a level with the given scale
+template <typename T>
+void launch_coarse_sig(const Geo& fine, const T* sig, double scale, const Geo& coarse, const int f[3], T* out,
+                       cudaStream_t st);
 
 // ------------------------------------------------------------ V-cycle -----
 // One red-black colour pass of over-relaxed Gauss-Seidel on A x = f, in

@@ -43,6 +43,7 @@ struct Level {
     double* x64 = nullptr;
     double* f64 = nullptr;
     double* t64 = nullptr;
+    double* sig64 = nullptr;  // diagonal excess of a Dirichlet-coupled operator (levels >= 1, on first use)
 };
 
 struct Alloc {
@@ -106,6 +107,13 @@ struct paris_ctx {
     // solid cells (Sec. 3.8): the caller's cell flags (1 fluid, 0 solid), or null
     const unsigned char* solid = nullptr;
     double n_fluid = 0.0;  // fluid cells (with solid set)
+    // free-surface projections (Sec. 3.7.5; allocated on first use): the
+    // finest level's diagonal excess and the cell classes; dirichlet: the
+    // current solve's operator carries the excess (no null space, FP64 form)
+    double* sig0 = nullptr;
+    unsigned char* fs_cls = nullptr;
+    unsigned char* fs_tmp = nullptr;
+    bool dirichlet = false;
     // viscous-step multigrid work arrays (allocated on the first paris_viscous_solve_mg)
     HelmWork hmg{};
     std::vector<void*> hw_mem;
@@ -326,7 +334,11 @@ template <typename T>
 Coef<T> level_coef(paris_ctx* c, int l, const Coef<T>& c0) {
     if (l == 0) return c0;
     Level& L = c->lv[l];
-    return Coef<T>{Prec<T>::b(L, 0), Prec<T>::b(L, 1), Prec<T>::b(L, 2), T(1)};
+    Coef<T> cf{Prec<T>::b(L, 0), Prec<T>::b(L, 1), Prec<T>::b(L, 2), T(1)};
+    if constexpr (sizeof(T) == 8) {
+        if (c->dirichlet) cf.sig = L.sig64;
+    }
+    return cf;
 }
 
 // Per-solve set-up of the hierarchy in precision T: coarse coefficients,
@@ -348,6 +360,9 @@ void setup_hierarchy(paris_ctx* c, const Coef<T>& c0) {
             }
         }
         launch_coarse_beta<T>(F.g, cf, L.g, L.fac, ratio2, out, c->st);
+        if constexpr (sizeof(T) == 8) {
+            if (c->dirichlet) launch_coarse_sig<T>(F.g, cf.sig, (double)cf.scale, L.g, L.fac, L.sig64, c->st);
+        }
     }
     // inverse diagonals: read by the FP64 smoothers and by Jacobi; the FP32
     // red-black sweeps recompute them from the coefficients they load
@@ -511,7 +526,7 @@ void vcoarse(paris_ctx* c, const Coef<T>& c0, const T* f0, T* x0) {
     const T* f = nl == 1 ? f0 : Prec<T>::f(C);
     T* x = nl == 1 ? x0 : Prec<T>::x(C);
     if (c->dense_coarse) {
-        launch_coarse_solve<T>(C.g, c->coarse_inv, f, x, c->st);
+        launch_coarse_solve<T>(C.g, c->coarse_inv, f, x, c->st, c->dirichlet);
     } else {
         Coef<T> cf = level_coef<T>(c, nl - 1, c0);
         smooth<T>(c, nl - 1, cf, f, x, 8, true, false);
@@ -550,7 +565,7 @@ constexpr int64_t kTailCells = 4096;
 // smoother, a dense coarsest level and at least one level above it).
 int tail_start(const paris_ctx* c) {
     const int nl = (int)c->lv.size();
-    if (!c->dense_coarse || c->opts.smoother != PARIS_SMOOTH_RBGS_2PASS || nl < 3) return -1;
+    if (!c->dense_coarse || c->opts.smoother != PARIS_SMOOTH_RBGS_2PASS || nl < 3 || c->dirichlet) return -1;
     int t = nl - 1;
     while (t - 1 >= 1 && c->lv[t - 1].g.ncell() <= kTailCells) --t;
     if (t >= nl - 1 || nl - t > kMaxTail) return -1;
@@ -636,7 +651,7 @@ bool coarse_graph_launch(paris_ctx* c, const Coef<T>& c0) {
 template <typename T>
 void vcycle(paris_ctx* c, const Coef<T>& c0, const T* f0, T* x0) {
     const int nl = (int)c->lv.size();
-    if (nl >= 3 && !c->cap_stream_broken) {
+    if (nl >= 3 && !c->cap_stream_broken && !c->dirichlet) {
         vdown<T>(c, c0, f0, x0, 0);
         {
             ProfScope ps(c, PARIS_K_COARSE, 0.0);
@@ -1082,6 +1097,7 @@ paris_status poisson_solve(paris_ctx* c, const double* bx, const double* by, con
                            bool mean_known) {
     const double ih2 = 1.0 / (c->grid.h * c->grid.h);
     Coef<double> c64{bx, by, bz, ih2};
+    if (c->dirichlet) c64.sig = c->sig0;
     if (!mean_known) CK(cudaMemsetAsync(c->scal, 0, sizeof(Scal), c->st));
     paris_status s;
     {
@@ -1091,7 +1107,7 @@ paris_status poisson_solve(paris_ctx* c, const double* bx, const double* by, con
     if (s != PARIS_OK) return s;
     SolveOut out;
     int fell_back = 0;
-    if (c->opts.precision == PARIS_MIXED) {
+    if (c->opts.precision == PARIS_MIXED && !c->dirichlet) {
         s = solve_mixed(c, c64, p, out, c->opts.max_iter, rho0);
         if (s != PARIS_OK) return s;
         if (!out.converged && !out.nonfinite && c->opts.fallback) {
@@ -1110,7 +1126,9 @@ paris_status poisson_solve(paris_ctx* c, const double* bx, const double* by, con
     }
     {
         ProfScope ps(c, PARIS_K_PROJECT, 0.0);
-        if (c->solid) {  // fluid mean 0, solid cells 0 (their p is not determined)
+        if (c->dirichlet) {  // no null space: no gauge
+            s = PARIS_OK;
+        } else if (c->solid) {  // fluid mean 0, solid cells 0 (their p is not determined)
             launch_fluid_gauge(c->N, c->solid, p, c->partials, c->scal, c->st);
             CK(cudaGetLastError());
             s = PARIS_OK;
@@ -1273,6 +1291,92 @@ paris_status paris_marker_function(paris_ctx* c, const double* gx, const double*
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(c->st));
     return s;
+}
+
+}  // extern "C"
+
+namespace {
+
+// The free-surface work arrays (all or nothing): the finest diagonal excess,
+// one per coarse level, and two byte arrays of cell classes.
+paris_status fs_alloc(paris_ctx* c) {
+    if (c->sig0) return PARIS_OK;
+    Alloc a;
+    double* s0 = a.get<double>(c->N);
+    std::vector<double*> sl(c->lv.size(), nullptr);
+    for (size_t l = 1; l < c->lv.size(); ++l) sl[l] = a.get<double>(c->lv[l].g.ncell());
+    unsigned char* cls = a.get<unsigned char>(c->N);
+    unsigned char* tmp = a.get<unsigned char>(c->N);
+    if (a.err != cudaSuccess) {
+        a.release();
+        return PARIS_ERR_NO_MEMORY;
+    }
+    c->sig0 = s0;
+    for (size_t l = 1; l < c->lv.size(); ++l) c->lv[l].sig64 = sl[l];
+    c->fs_cls = cls;
+    c->fs_tmp = tmp;
+    c->mem.ptrs.insert(c->mem.ptrs.end(), a.ptrs.begin(), a.ptrs.end());
+    return PARIS_OK;
+}
+
+// The projection on the unknown cells of c->fs_cls (1 unknown, 2 Dirichlet,
+// 0 excluded): coefficients, diagonal excess and Dirichlet right-hand side,
+// rhs = div u/dt - gd, the FP64 solve without null space, the cut-face
+// velocity correction with coef = dt beta / h, the Dirichlet values into p.
+paris_status fs_project_step(paris_ctx* c, const double* const theta[3], const double* pd, const double* kappa,
+                             double sigma, double beta, double dt, bool zero_walls, double* u, double* v, double* w,
+                             double* p, paris_stats* st) {
+    launch_fs_setup(c->g0, c->fs_cls, beta, theta, pd, kappa, sigma, c->grid.h, c->beta[0], c->beta[1], c->beta[2],
+                    c->sig0, c->rhs, c->st);
+    launch_fs_rhs(c->g0, c->fs_cls, u, v, w, 1.0 / (c->grid.h * dt), c->rhs, c->st);
+    CK(cudaMemsetAsync(c->scal, 0, sizeof(Scal), c->st));  // mean_b = 0: nothing is removed
+    CK(cudaGetLastError());
+    struct DirichletMode {
+        paris_ctx* c;
+        ~DirichletMode() { c->dirichlet = false; }
+    } mode{c};
+    c->dirichlet = true;
+    c->mixed_ready = false;
+    const paris_status solve = poisson_solve(c, c->beta[0], c->beta[1], c->beta[2], c->rhs, p, st, false, true);
+    if (solve != PARIS_OK && solve != PARIS_ERR_NOT_CONVERGED) return solve;
+    launch_fs_project(c->g0, c->fs_cls, theta, p, pd, kappa, sigma, dt * beta / c->grid.h, zero_walls, u, v, w,
+                      c->st);
+    launch_fs_fill(c->g0, c->fs_cls, pd, p, c->st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->st));
+    return solve;
+}
+
+}  // namespace
+
+extern "C" {
+
+paris_status paris_free_surface_step(paris_ctx* c, const double* C, double rho_l, double dt, const double* theta_x,
+                                     const double* theta_y, const double* theta_z, const double* kappa,
+                                     double sigma, const double* p_gas, double* u, double* v, double* w, double* p,
+                                     paris_stats* st) {
+    if (!c || !C || !u || !v || !w || !p) return PARIS_ERR_INVALID_ARG;
+    if (!(rho_l > 0.0) || !std::isfinite(rho_l) || !(dt > 0.0) || !std::isfinite(dt) || !std::isfinite(sigma))
+        return PARIS_ERR_INVALID_ARG;
+    const bool any_t = theta_x || theta_y || theta_z, all_t = theta_x && theta_y && theta_z;
+    if (any_t && !all_t) return PARIS_ERR_INVALID_ARG;
+    if (c->solid) return PARIS_ERR_INVALID_ARG;
+    paris_status s = fs_alloc(c);
+    if (s != PARIS_OK) return s;
+    launch_fs_liquid_classes(c->g0, C, c->fs_cls, c->st);
+    const double* theta[3] = {theta_x, theta_y, theta_z};
+    return fs_project_step(c, theta, p_gas, kappa, sigma, 1.0 / rho_l, dt, true, u, v, w, p, st);
+}
+
+paris_status paris_phantom_projection(paris_ctx* c, const double* C, double* u, double* v, double* w, double* phat,
+                                      paris_stats* st) {
+    if (!c || !C || !u || !v || !w || !phat) return PARIS_ERR_INVALID_ARG;
+    if (c->solid) return PARIS_ERR_INVALID_ARG;
+    paris_status s = fs_alloc(c);
+    if (s != PARIS_OK) return s;
+    launch_fs_gas_layers(c->g0, C, c->fs_tmp, c->fs_cls, c->st);
+    const double* theta[3] = {nullptr, nullptr, nullptr};
+    return fs_project_step(c, theta, nullptr, nullptr, 0.0, 1.0, 1.0, false, u, v, w, phat, st);
 }
 
 static bool valid_forcing(double sigma, double gx, double gy, double gz) {
