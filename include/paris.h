@@ -91,7 +91,7 @@ typedef struct {
     int nu1, nu2;         /* pre/post smoothing sweeps per level (2, 2) */
     double omega;         /* over-relaxation factor of the smoother (1.15; Jacobi: 0.8) */
     int smoother;         /* paris_smoother (PARIS_SMOOTH_RBGS_2PASS) */
-    int coarse_max_cells; /* coarsen until the coarsest grid has at most this many cells (64) */
+    int coarse_max_cells; /* coarsen until the coarsest grid has at most this many cells (8) */
     double inner_tol;     /* MIXED: relative residual reduction of each FP32 inner solve (1e-5) */
     int fallback;         /* MIXED: on failure redo the solve in FP64 (1) */
     int slab_planes;      /* two-pass red-black: run each colour pass in z-slabs of this

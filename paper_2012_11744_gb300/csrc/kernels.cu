@@ -306,6 +306,97 @@ __global__ void __launch_bounds__(kTX* kTY) face_coeffs_kernel(Geo g, const doub
     }
 }
 
+// a + b = s.x + s.y exactly (Knuth's two-sum, FP32)
+__device__ __forceinline__ float2 two_sum_f(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s, a);
+    return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp)));
+}
+
+// 1/(a + b) for two (hi, lo) FP32 pairs in FP32 arithmetic, returned in FP64:
+// the pair sum S (leading part by two-sum, the rest added), y0 the
+// approximate reciprocal of its leading part (1 ulp), t = 1 - S y0 (to about
+// 2^-47), 1/S = y0 (1 + t + t^2 + ...) kept to second order: y0 + y0 (t + t^2)
+// as an FP64 sum of two FP32 numbers, about 46 significant bits.
+__device__ __forceinline__ double recip_pair_sum(float2 a, float2 b) {
+    const float2 s = two_sum_f(a.x, b.x);
+    const float slo = __fadd_rn(s.y, __fadd_rn(a.y, b.y));
+    float y0;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(s.x));
+    float t = __fmaf_rn(-s.x, y0, 1.0f);
+    t = __fmaf_rn(-slo, y0, t);
+    const float blo = __fmul_rn(y0, __fmaf_rn(t, t, t));
+    return f2d_scaled(y0, 0) + f2d_scaled(blo, 0);
+}
+
+// The face coefficients of the mixed form's projection step, with the FP64
+// pipe (1/64 of the FP32 rate on this GPU) used for three operations per
+// cell instead of about seventeen: rh = rho/2 = rh2 + C (rh1 - rh2) by one
+// FMA, its (hi, lo) FP32 split (one FP64 subtraction), and per face beta_f =
+// 1/(rh_L + rh_R) from the two pairs in FP32 arithmetic (recip_pair_sum) with
+// one FP64 addition.  beta_f is then within about 2^-46 of 1/rho_f (the exact
+// form, face_coeffs_kernel, is within one ulp): the operator the mixed form's
+// double-float refinement step already applies.  Same tiling as
+// face_coeffs_kernel; writes rh32 and rh2 too.
+__global__ void __launch_bounds__(kTX* kTY) face_coeffs_fast_kernel(Geo g, const double* __restrict__ C,
+                                                                   double d12h, double r2h,
+                                                                   double* __restrict__ bx,
+                                                                   double* __restrict__ by,
+                                                                   double* __restrict__ bz,
+                                                                   float* __restrict__ rh32,
+                                                                   float2* __restrict__ rh2) {
+    __shared__ float2 sh[2][kTY + 1][kTX + 1];  // [plane parity][1 + row][1 + column]
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int i = blockIdx.x * kTX + tx, j = blockIdx.y * kTY + ty;
+    const bool in = i < nx && j < ny;
+    const int ic = min(i, nx - 1), jc = min(j, ny - 1);  // idle threads shadow a cell
+    const int kb = blockIdx.z * kFSeg, ke = min(kb + kFSeg, nz);
+    const int64_t pl = (int64_t)nx * ny;
+    auto pair = [&](double c) {
+        const double rh = fma(d12h, c, r2h);
+        const float hi = d2f_scaled(rh, 0);
+        return make_float2(hi, d2f_scaled(rh - f2d_scaled(hi, 0), 0));
+    };
+    const int i0 = blockIdx.x * kTX, j0 = blockIdx.y * kTY;
+    const int hx = i0 > 0 ? i0 - 1 : nx - 1;  // periodic wrap (walls: beta 0, value unused)
+    const int hy = j0 > 0 ? j0 - 1 : ny - 1;
+    const int hrow = min(j0 + tx, ny - 1);
+    const int hcol = min(i0 + tx, nx - 1);
+    const bool xw = g.wx && i == 0, yw = g.wy && j == 0;
+    float2 rzm = pair(C[(int64_t)(kb > 0 ? kb - 1 : nz - 1) * pl + (int64_t)jc * nx + ic]);
+    for (int k = kb; k < ke; ++k) {
+        const int64_t plane = (int64_t)k * pl;
+        const int64_t c = plane + (int64_t)jc * nx + ic;
+        const float2 rc = pair(C[c]);
+        const int b = k & 1;
+        sh[b][ty + 1][tx + 1] = rc;
+        if (ty == 0) sh[b][0][tx + 1] = pair(C[plane + (int64_t)hy * nx + hcol]);
+        if (ty == 1 && tx < kTY) sh[b][tx + 1][0] = pair(C[plane + (int64_t)hrow * nx + hx]);
+        __syncthreads();
+        if (in) {
+            const bool zw = g.wz && k == 0;
+            bx[g.fx(i, j, k)] = xw ? 0.0 : recip_pair_sum(sh[b][ty + 1][tx], rc);
+            by[g.fy(i, j, k)] = yw ? 0.0 : recip_pair_sum(sh[b][ty][tx + 1], rc);
+            bz[g.fz(i, j, k)] = zw ? 0.0 : recip_pair_sum(rzm, rc);
+            if (g.wx && i == nx - 1) bx[g.fx(nx, j, k)] = 0.0;
+            if (g.wy && j == ny - 1) by[g.fy(i, ny, k)] = 0.0;
+            if (g.wz && k == nz - 1) bz[g.fz(i, j, nz)] = 0.0;
+            rh32[c] = rc.x;
+            rh2[c] = rc;
+        }
+        rzm = rc;
+    }
+}
+
+void launch_face_coeffs_fast(const Geo& g, const double* C, double rho1, double rho2, double* bx, double* by,
+                             double* bz, float* rh32, float2* rh2, cudaStream_t st) {
+    dim3 gr((g.nx + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, (g.nz + kFSeg - 1) / kFSeg);
+    face_coeffs_fast_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(g, C, 0.5 * rho1 - 0.5 * rho2, 0.5 * rho2, bx, by, bz,
+                                                           rh32, rh2);
+    count_launch();
+}
+
 void launch_face_coeffs(const Geo& g, const double* C, double rho1, double rho2, double* bx,
                         double* by, double* bz, float* rh32, float2* rh2, cudaStream_t st,
                         const Forcing* force) {
@@ -1021,7 +1112,7 @@ void launch_jacobi(const Geo& g, const Coef<T>& cf, const T* w, const T* f, cons
 
 // Coarse right-hand side: the average over the children of the fine residual
 // f - A x (restriction R = P^T / #children for the piecewise-constant P).
-template <typename T, typename TB, bool I32>
+template <typename T, typename TB, bool I32, bool SIG = false>
 __global__ void restrict_residual_kernel(Geo fg, const TB* __restrict__ bx, const TB* __restrict__ by,
                                          const TB* __restrict__ bz, T scale, const T* __restrict__ f,
                                          const T* __restrict__ x, Geo cg, int fa0, int fa1,
@@ -1047,7 +1138,7 @@ __global__ void restrict_residual_kernel(Geo fg, const TB* __restrict__ bx, cons
                     load_stencil_as<T>(fg, bx, by, bz, i, j, k, s);
                 }
                 T ax = apply_A(s, x, x[c], scale);
-                if (sig) ax = fma(scale * sig[c], x[c], ax);
+                if (SIG) ax = fma(scale * sig[c], x[c], ax);
                 sum += f[c] - ax;
             }
     fc[cg.cidx(I, J, K)] = sum / T(fa0 * fa1 * fa2);
@@ -1057,12 +1148,11 @@ template <typename T>
 void launch_restrict_residual(const Geo& fine, const Coef<T>& cf, const T* f, const T* x,
                              const Geo& coarse, const int fac[3], T* fc, cudaStream_t st) {
     dim3 gr((coarse.nx + kTX - 1) / kTX, (coarse.ny + kTY - 1) / kTY, coarse.nz);
-    if (fits_i32(fine))
-        launch_pdl(restrict_residual_kernel<T, T, true>, gr, dim3(kTX, kTY), 0, st, fine, cf.bx, cf.by, cf.bz,
-            cf.scale, f, x, coarse, fac[0], fac[1], fac[2], fc, cf.sig);
-    else
-        launch_pdl(restrict_residual_kernel<T, T, false>, gr, dim3(kTX, kTY), 0, st, fine, cf.bx, cf.by, cf.bz,
-            cf.scale, f, x, coarse, fac[0], fac[1], fac[2], fc, cf.sig);
+    // the diagonal excess as a template flag: the plain operator's kernels are unchanged
+    auto* k = fits_i32(fine) ? (cf.sig ? restrict_residual_kernel<T, T, true, true> : restrict_residual_kernel<T, T, true>)
+                             : (cf.sig ? restrict_residual_kernel<T, T, false, true> : restrict_residual_kernel<T, T, false>);
+    launch_pdl(k, gr, dim3(kTX, kTY), 0, st, fine, cf.bx, cf.by, cf.bz, cf.scale, f, x, coarse, fac[0], fac[1],
+               fac[2], fc, cf.sig);
     count_launch();
 }
 
@@ -1147,7 +1237,7 @@ void launch_prolong_add(const Geo& fine, const Geo& coarse, const int fac[3], co
 // scaled FP32 copy r32 = scale * r that the inner solve starts from.  With
 // zero_ok and an initial guess that is zero everywhere (s->xmax == 0, a value
 // every thread reads alike) A x vanishes and r = f is copied.
-template <bool I32>
+template <bool I32, bool SIG = false>
 __global__ void __launch_bounds__(kTX* kTY) residual64_kernel(Geo g, Coef<double> cf,
                                                               const double* __restrict__ f,
                                                               const double* __restrict__ x,
@@ -1186,7 +1276,7 @@ __global__ void __launch_bounds__(kTX* kTY) residual64_kernel(Geo g, Coef<double
                 double a = st.b[0] * (xc - x[st.nb[0]]);
 #pragma unroll
                 for (int q = 1; q < 6; ++q) a = fma(st.b[q], xc - x[st.nb[q]], a);
-                if (cf.sig) a = fma(cf.sig[c], xc, a);
+                if (SIG) a = fma(cf.sig[c], xc, a);
                 r = fma(-cf.scale, a, f[c]);
             }
             if (r64) r64[c] = r;
@@ -1210,19 +1300,17 @@ int64_t launch_residual64(const Geo& g, const Coef<double>& cf, const double* f,
                           double* r64, float* r32, const Scal* s, double* partials, bool zero_ok,
                           cudaStream_t st, FinSpec fin, bool split) {
     dim3 gr = tile_grid(g, kZ);
-    if (fits_i32(g))
-        launch_pdl(residual64_kernel<true>, gr, dim3(kTX, kTY), 0, st, g, cf, f, x, r64, r32, s, partials,
-            zero_ok ? 1 : 0, split ? 1 : 0, fin);
-    else
-        launch_pdl(residual64_kernel<false>, gr, dim3(kTX, kTY), 0, st, g, cf, f, x, r64, r32, s, partials,
-            zero_ok ? 1 : 0, split ? 1 : 0, fin);
+    auto* k = fits_i32(g) ? (cf.sig ? residual64_kernel<true, true> : residual64_kernel<true>)
+                          : (cf.sig ? residual64_kernel<false, true> : residual64_kernel<false>);
+    launch_pdl(k, gr, dim3(kTX, kTY), 0, st, g, cf, f, x, r64, r32, s, partials, zero_ok ? 1 : 0, split ? 1 : 0,
+               fin);
     count_launch();
     return nblocks_of(gr);
 }
 
 // q = A d and the partial sums of d . q (accumulated per thread in T,
 // across threads and blocks in FP64).
-template <typename T, bool I32>
+template <typename T, bool I32, bool SIG = false>
 __global__ void __launch_bounds__(kTX* kTY) matvec_dot_kernel(Geo g, Coef<T> cf,
                                                              const T* __restrict__ d,
                                                              T* __restrict__ q,
@@ -1245,7 +1333,7 @@ __global__ void __launch_bounds__(kTX* kTY) matvec_dot_kernel(Geo g, Coef<T> cf,
             }
             const T dc = d[c];
             T qc = apply_A(st, d, dc, cf.scale);
-            if (cf.sig) qc = fma(cf.scale * cf.sig[c], dc, qc);
+            if (SIG) qc = fma(cf.scale * cf.sig[c], dc, qc);
             q[c] = qc;
             loc = fma(dc, qc, loc);
         })
@@ -1260,10 +1348,9 @@ template <typename T>
 int64_t launch_matvec_dot(const Geo& g, const Coef<T>& cf, const T* d, T* q, double* partials,
                           cudaStream_t st, FinSpec fin) {
     dim3 gr = tile_grid(g, kZ);
-    if (fits_i32(g))
-        matvec_dot_kernel<T, true><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, d, q, partials, fin);
-    else
-        matvec_dot_kernel<T, false><<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, d, q, partials, fin);
+    auto* k = fits_i32(g) ? (cf.sig ? matvec_dot_kernel<T, true, true> : matvec_dot_kernel<T, true>)
+                          : (cf.sig ? matvec_dot_kernel<T, false, true> : matvec_dot_kernel<T, false>);
+    k<<<gr, dim3(kTX, kTY), 0, st>>>(g, cf, d, q, partials, fin);
     count_launch();
     return nblocks_of(gr);
 }

@@ -349,6 +349,10 @@ struct Forcing {
 void launch_face_coeffs(const Geo& g, const double* C, double rho1, double rho2, double* bx,
                         double* by, double* bz, float* rh32, float2* rh2, cudaStream_t st,
                         const Forcing* force = nullptr);
+// the same outputs (rh32, rh2 required) with beta from the rho/2 pairs in FP32
+// arithmetic: within about 2^-46 of 1/rho_f (the mixed form's step)
+void launch_face_coeffs_fast(const Geo& g, const double* C, double rho1, double rho2, double* bx, double* by,
+                             double* bz, float* rh32, float2* rh2, cudaStream_t st);
 // rhs = div(u)/(h dt); partials: (sum rhs, max |rhs|, nonfinite count)
 int64_t launch_divergence(const Geo& g, const double* u, const double* v, const double* w,
                           double inv_hdt, double* rhs, double* partials, cudaStream_t st,
@@ -453,6 +457,12 @@ cudaError_t launch_rbgs_rho_stage(const Geo& g, const float* rh, double h, const
 // q = A d; partials (d . q); returns the number of blocks
 int64_t launch_matvec_rho(const Geo& g, const float* rh, double h, const float* d, float* q,
                           double* partials, cudaStream_t st, FinSpec fin = no_fin(), bool tiles = true);
+// the plane-tile product with the flexible CG's direction update fused in:
+// dnew = z + beta d (beta from s) and q = A dnew, d . q partials as above
+// (dnew must not alias z or d); only where rho0_product_fuses
+bool rho0_product_fuses(const Geo& g, bool tiles);
+int64_t launch_matvec_rho_xpby(const Geo& g, const float* rh, double h, const float* z, const float* d, float* dnew,
+                               float* q, const Scal* s, double* partials, cudaStream_t st, FinSpec fin);
 int64_t rho0_matvec_blocks(const Geo& g);
 // coarse f = mean over the 2x2x2 children of (f - A x); coarse = every axis halved
 void launch_restrict_rho(const Geo& g, const float* rh, double h, const float* f, const float* x,

@@ -798,10 +798,14 @@ namespace {
 // (A x)/scale of the 2V cells 2t0 .. 2t0+2V-1 of row j, plane k, in cell
 // order; C0: colour of cell 2t0 ((j + k) & 1).  Faces in the order x-, x+,
 // y-, y+, z-, z+ of op_apply.  X, F: x (and f) of the cells in cell order.
-template <bool WITH_F, int V, int C0>
+// XP: x is formed on the fly as z + beta x (the flexible CG's direction
+// update d = z + beta d fused into the product that reads it; same FMA as
+// the separate update, so the same values).
+template <bool WITH_F, int V, int C0, bool XP = false>
 __device__ __forceinline__ void tile_apply(const Geo& g, const float* __restrict__ rh, const float* __restrict__ x,
                                            const float* __restrict__ f, int j, int k, int t0, int lane,
-                                           float (&a)[2 * V], float (&X)[2 * V], float (&F)[2 * V]) {
+                                           float (&a)[2 * V], float (&X)[2 * V], float (&F)[2 * V],
+                                           const float* __restrict__ z = nullptr, float beta = 0.f) {
     const int nx = g.nx, hx = nx / 2, pl = nx * g.ny;
     const int rb = k * pl + j * nx;
     const int o = rb + 2 * t0;
@@ -814,6 +818,16 @@ __device__ __forceinline__ void tile_apply(const Geo& g, const float* __restrict
     auto cells = [&](int off, int c0, float (&out)[2 * V]) {
         ldgv<V>(h0, x + rb + off + t0);
         ldgv<V>(h1, x + rb + off + hx + t0);
+        if (XP) {
+            float g0[V], g1[V];
+            ldgv<V>(g0, z + rb + off + t0);
+            ldgv<V>(g1, z + rb + off + hx + t0);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                h0[v] = fmaf(beta, h0[v], g0[v]);
+                h1[v] = fmaf(beta, h1[v], g1[v]);
+            }
+        }
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             out[2 * v] = c0 ? h1[v] : h0[v];
@@ -844,7 +858,11 @@ __device__ __forceinline__ void tile_apply(const Geo& g, const float* __restrict
     // cells 2t0-1 (colour C0^1) and 2t0+2V (colour C0) outside the lane's
     // entries, wrapped around the row: from the adjacent lanes, or loaded
     const int tl = t0 > 0 ? t0 - 1 : hx - 1, tr = t0 + V < hx ? t0 + V : t0 + V - hx;
-    const float xl_ld = __ldg(x + rb + (C0 ? 0 : hx) + tl), xr_ld = __ldg(x + rb + (C0 ? hx : 0) + tr);
+    float xl_ld = __ldg(x + rb + (C0 ? 0 : hx) + tl), xr_ld = __ldg(x + rb + (C0 ? hx : 0) + tr);
+    if (XP) {
+        xl_ld = fmaf(beta, xl_ld, __ldg(z + rb + (C0 ? 0 : hx) + tl));
+        xr_ld = fmaf(beta, xr_ld, __ldg(z + rb + (C0 ? hx : 0) + tr));
+    }
     const float rl_ld = __ldg(rh + o + (t0 > 0 ? -1 : nx - 1));
     const float rr_ld = __ldg(rh + o + (t0 + V < hx ? 2 * V : 2 * V - nx));
     const float xl_sh = __shfl_up_sync(kAll, X[2 * V - 1], 1), rl_sh = __shfl_up_sync(kAll, R[2 * V - 1], 1);
@@ -904,14 +922,18 @@ __device__ __forceinline__ void tile_apply(const Geo& g, const float* __restrict
 #ifndef PARIS_OP_MINB
 #define PARIS_OP_MINB 3
 #endif
-template <bool RESTRICT, int V>
+template <bool RESTRICT, int V, bool XP = false>
 __global__ void __launch_bounds__(kBX* kVY, PARIS_OP_MINB) op_rho_tile_kernel(Geo g, const float* __restrict__ rh, float ih2,
                                                              const float* __restrict__ x,
                                                              const float* __restrict__ f,
                                                              float* __restrict__ out, Geo cg,
-                                                             double* partials, int np, FinSpec fin) {
+                                                             double* partials, int np, FinSpec fin,
+                                                             const float* __restrict__ z = nullptr,
+                                                             const Scal* s = nullptr,
+                                                             float* __restrict__ xnew = nullptr) {
     __shared__ float sh[kVY][kBX * V];
     pdl_wait();
+    const float beta = XP ? (float)s->beta : 0.f;  // XP: x = z + beta x, written to xnew
     const int ty = threadIdx.y, lane = threadIdx.x;
     const int j = blockIdx.y * kVY + ty;
     const bool row_ok = j < g.ny;
@@ -929,9 +951,9 @@ __global__ void __launch_bounds__(kBX* kVY, PARIS_OP_MINB) op_rho_tile_kernel(Ge
         if (k >= g.nz) break;  // uniform per block
         float a[2 * V], X[2 * V], F[2 * V];
         if (((jc + k) & 1) == 0)
-            tile_apply<RESTRICT, V, 0>(g, rh, x, f, jc, k, t0, lane, a, X, F);
+            tile_apply<RESTRICT, V, 0, XP>(g, rh, x, f, jc, k, t0, lane, a, X, F, z, beta);
         else
-            tile_apply<RESTRICT, V, 1>(g, rh, x, f, jc, k, t0, lane, a, X, F);
+            tile_apply<RESTRICT, V, 1, XP>(g, rh, x, f, jc, k, t0, lane, a, X, F, z, beta);
         if (!RESTRICT) {
             const int c0 = (jc + k) & 1;
             float Q[2 * V], q0[V], q1[V];
@@ -946,6 +968,16 @@ __global__ void __launch_bounds__(kBX* kVY, PARIS_OP_MINB) op_rho_tile_kernel(Ge
                 const int rb = (k * g.ny + jc) * g.nx;
                 stv<V>(out + rb + t0, q0);
                 stv<V>(out + rb + hx + t0, q1);
+                if (XP) {
+                    float d0[V], d1[V];
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        d0[v] = c0 ? X[2 * v + 1] : X[2 * v];
+                        d1[v] = c0 ? X[2 * v] : X[2 * v + 1];
+                    }
+                    stv<V>(xnew + rb + t0, d0);
+                    stv<V>(xnew + rb + hx + t0, d1);
+                }
 #pragma unroll
                 for (int c = 0; c < 2 * V; ++c) loc = fmaf(X[c], Q[c], loc);
             }
@@ -986,6 +1018,19 @@ int64_t rho0_matvec_blocks(const Geo& g) {
     return ring > tiles ? ring : tiles;
 }
 
+bool rho0_product_fuses(const Geo& g, bool tiles) { return tiles && kTileOpV > 0 && (g.nx / 2) % kTileOpV == 0; }
+
+int64_t launch_matvec_rho_xpby(const Geo& g, const float* rh, double h, const float* z, const float* d, float* dnew,
+                               float* q, const Scal* s, double* partials, cudaStream_t st, FinSpec fin) {
+    constexpr int V = kTileOpV > 0 ? kTileOpV : 2;
+    const int hx = g.nx / 2;
+    dim3 gr((hx / V + kBX - 1) / kBX, (g.ny + kVY - 1) / kVY, (g.nz + kTileOpPlanes - 1) / kTileOpPlanes);
+    launch_pdl(op_rho_tile_kernel<false, V, true>, gr, dim3(kBX, kVY), 0, st, g, rh, (float)(1.0 / (h * h)), d,
+               (const float*)nullptr, q, g, partials, kTileOpPlanes, fin, z, s, dnew);
+    count_launch();
+    return (int64_t)gr.x * gr.y * gr.z;
+}
+
 int64_t launch_matvec_rho(const Geo& g, const float* rh, double h, const float* d, float* q,
                           double* partials, cudaStream_t st, FinSpec fin, bool tiles) {
     const int hx = g.nx / 2;
@@ -993,7 +1038,8 @@ int64_t launch_matvec_rho(const Geo& g, const float* rh, double h, const float* 
         constexpr int V = kTileOpV > 0 ? kTileOpV : 2;
         dim3 gr((hx / V + kBX - 1) / kBX, (g.ny + kVY - 1) / kVY, (g.nz + kTileOpPlanes - 1) / kTileOpPlanes);
         launch_pdl(op_rho_tile_kernel<false, V>, gr, dim3(kBX, kVY), 0, st, g, rh, (float)(1.0 / (h * h)), d,
-            (const float*)nullptr, q, g, partials, kTileOpPlanes, fin);
+            (const float*)nullptr, q, g, partials, kTileOpPlanes, fin, (const float*)nullptr, (const Scal*)nullptr,
+            (float*)nullptr);
         count_launch();
         return (int64_t)gr.x * gr.y * gr.z;
     }
@@ -1012,7 +1058,7 @@ void launch_restrict_rho(const Geo& g, const float* rh, double h, const float* f
         constexpr int V = kTileOpV > 0 ? kTileOpV : 2;
         dim3 gr((hx / V + kBX - 1) / kBX, (g.ny + kVY - 1) / kVY, g.nz / 2);
         launch_pdl(op_rho_tile_kernel<true, V>, gr, dim3(kBX, kVY), 0, st, g, rh, (float)(1.0 / (h * h)), x, f,
-            fc, cg, (double*)nullptr, 2, no_fin());
+            fc, cg, (double*)nullptr, 2, no_fin(), (const float*)nullptr, (const Scal*)nullptr, (float*)nullptr);
         count_launch();
         return;
     }

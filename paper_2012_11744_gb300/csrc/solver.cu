@@ -94,6 +94,7 @@ struct paris_ctx {
     double *f = nullptr, *r = nullptr, *z = nullptr, *d = nullptr, *q = nullptr;
     // FP32 inner vectors
     float *r32 = nullptr, *z32 = nullptr, *d32 = nullptr, *q32 = nullptr, *e32 = nullptr;
+    float* d32b = nullptr;  // the next direction of the fused direction update and product
     // level-0 FP32 coefficient copies (beta/h^2) and FP16 copies (beta) for
     // the V-cycle's finest-level passes
     float* b32_0[3] = {nullptr, nullptr, nullptr};
@@ -246,6 +247,7 @@ paris_status alloc_ctx(paris_ctx* c) {
     c->d32 = m.get<float>(N);
     c->q32 = m.get<float>(N);
     c->e32 = m.get<float>(N);
+    if (rho0_fits(c->g0)) c->d32b = m.get<float>(N);
     for (int a = 0; a < 3; ++a) {
         c->b32_0[a] = m.get<float>(c->g0.nface(a));
         c->b16_0[a] = m.get<__half>(c->g0.nface(a));
@@ -852,8 +854,17 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
                                FinSpec{c->scal, 2, 0, FIN_RHO_INIT, 0.0});
             std::swap(c->d32, c->z32);  // first direction d = z: exchange the buffers
         }
+        // with the finest level from rho/2 the direction update d = z + beta d
+        // rides in the next product (fuse_next: beta is pending)
+        const bool fuse = c->rho0 && c->d32b && rho0_product_fuses(c->g0, c->opts.level0_tiles != 0);
+        bool fuse_next = false;
         for (int j = 0; j < 50 && out.iters < max_iter; ++j) {
-            if (c->rho0) {
+            if (fuse_next) {
+                ProfScope ps(c, PARIS_K_MATVEC0, 5.0 * N * 4);
+                launch_matvec_rho_xpby(c->g0, c->rh32, c->grid.h, c->z32, c->d32, c->d32b, c->q32, c->scal,
+                                       c->partials, c->st, FinSpec{c->scal, 1, 0, FIN_ALPHA, 0.0});
+                std::swap(c->d32, c->d32b);
+            } else if (c->rho0) {
                 ProfScope ps(c, PARIS_K_MATVEC0, 3.0 * N * 4);
                 launch_matvec_rho(c->g0, c->rh32, c->grid.h, c->d32, c->q32, c->partials, c->st,
                                   FinSpec{c->scal, 1, 0, FIN_ALPHA, 0.0}, c->opts.level0_tiles != 0);
@@ -877,7 +888,10 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
             ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
             launch_dot2<float>(N, c->z32, c->r32, c->q32, c->partials, c->st,  // (z.r, z.q)
                                FinSpec{c->scal, 2, 0, FIN_FCG_BETA, 0.0});
-            launch_xpby<float>(N, c->scal, c->z32, c->d32, c->st);
+            if (fuse)
+                fuse_next = true;
+            else
+                launch_xpby<float>(N, c->scal, c->z32, c->d32, c->st);
         }
         if (refine) {
             ProfScope ps(c, PARIS_K_RESID64, 48.0 * N);
@@ -914,7 +928,7 @@ void paris_default_opts(paris_opts* o) {
     o->nu2 = 2;
     o->omega = 1.15;
     o->smoother = PARIS_SMOOTH_RBGS_2PASS;
-    o->coarse_max_cells = 64;
+    o->coarse_max_cells = 8;
     o->inner_tol = 1e-5;
     o->fallback = 1;
     o->slab_planes = 0;
@@ -1188,7 +1202,9 @@ struct HostLink {
 paris_status projection_step_impl(paris_ctx* c, const double* C, double rho1, double rho2, double dt,
                                   double* u, double* v, double* w, double* p, paris_stats* st,
                                   const HostLink* hl, const Forcing* force = nullptr) {
-    const bool use_rho0 = rho0_usable(c);
+    // the FP32 pairs of rho/2 need both half-densities well inside the FP32 range
+    const double rlo = 0.5 * std::min(rho1, rho2), rhi = 0.5 * std::max(rho1, rho2);
+    const bool use_rho0 = rho0_usable(c) && rlo >= 1e-30 && rhi <= 1e30;
     // the set-up run ahead below is used by this step's solve only
     struct ReadyGuard {
         paris_ctx* c;
@@ -1197,8 +1213,12 @@ paris_status projection_step_impl(paris_ctx* c, const double* C, double rho1, do
     {
         ProfScope ps(c, PARIS_K_FIELD, 0.0);
         if (hl) CK(cudaStreamWaitEvent(c->st, hl->c_ready, 0));
-        launch_face_coeffs(c->g0, C, rho1, rho2, c->beta[0], c->beta[1], c->beta[2],
-                           use_rho0 ? c->rh32 : nullptr, use_rho0 ? c->rh2 : nullptr, c->st, force);
+        if (use_rho0 && !force)  // beta to about 2^-46: the operator of the double-float refinement
+            launch_face_coeffs_fast(c->g0, C, rho1, rho2, c->beta[0], c->beta[1], c->beta[2], c->rh32, c->rh2,
+                                    c->st);
+        else
+            launch_face_coeffs(c->g0, C, rho1, rho2, c->beta[0], c->beta[1], c->beta[2],
+                               use_rho0 ? c->rh32 : nullptr, use_rho0 ? c->rh2 : nullptr, c->st, force);
         if (c->solid)
             launch_link_block(c->g0, c->solid, c->beta[0], c->beta[1], c->beta[2], nullptr, nullptr, nullptr, c->st);
         CK(cudaGetLastError());
