@@ -118,6 +118,13 @@ typedef struct {
                              2.  0: always the kernels that walk z-columns one pair per
                              thread.  The colour passes give identical results in all three;
                              the product's dot products differ in summation order only (1) */
+    int level0_half_rho;  /* with level0_density and level0_tiles 1: the V-cycle's finest
+                             colour passes and residual restriction read rho/2 in FP16 (2
+                             instead of 4 bytes per cell and pass; 11 bits of rho are
+                             plenty for a preconditioner), when rho1/2 and rho2/2 lie in
+                             [1e-4, 6e4]; the inner CG product, the refinement step and the
+                             projection keep full precision, so this changes the V-cycle,
+                             not the converged p (1) */
 } paris_opts;
 
 typedef struct {

@@ -344,7 +344,8 @@ __global__ void __launch_bounds__(kTX* kTY) face_coeffs_fast_kernel(Geo g, const
                                                                    double* __restrict__ by,
                                                                    double* __restrict__ bz,
                                                                    float* __restrict__ rh32,
-                                                                   float2* __restrict__ rh2) {
+                                                                   float2* __restrict__ rh2,
+                                                                   __half* __restrict__ rh16) {
     __shared__ float2 sh[2][kTY + 1][kTX + 1];  // [plane parity][1 + row][1 + column]
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -384,16 +385,17 @@ __global__ void __launch_bounds__(kTX* kTY) face_coeffs_fast_kernel(Geo g, const
             if (g.wz && k == nz - 1) bz[g.fz(i, j, nz)] = 0.0;
             rh32[c] = rc.x;
             rh2[c] = rc;
+            if (rh16) rh16[c] = __float2half_rn(rc.x);
         }
         rzm = rc;
     }
 }
 
 void launch_face_coeffs_fast(const Geo& g, const double* C, double rho1, double rho2, double* bx, double* by,
-                             double* bz, float* rh32, float2* rh2, cudaStream_t st) {
+                             double* bz, float* rh32, float2* rh2, __half* rh16, cudaStream_t st) {
     dim3 gr((g.nx + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, (g.nz + kFSeg - 1) / kFSeg);
     face_coeffs_fast_kernel<<<gr, dim3(kTX, kTY), 0, st>>>(g, C, 0.5 * rho1 - 0.5 * rho2, 0.5 * rho2, bx, by, bz,
-                                                           rh32, rh2);
+                                                           rh32, rh2, rh16);
     count_launch();
 }
 

@@ -350,9 +350,10 @@ void launch_face_coeffs(const Geo& g, const double* C, double rho1, double rho2,
                         double* by, double* bz, float* rh32, float2* rh2, cudaStream_t st,
                         const Forcing* force = nullptr);
 // the same outputs (rh32, rh2 required) with beta from the rho/2 pairs in FP32
-// arithmetic: within about 2^-46 of 1/rho_f (the mixed form's step)
+// arithmetic: within about 2^-46 of 1/rho_f (the mixed form's step); rh16 (may
+// be null): rho/2 in FP16 (rounded from rh32)
 void launch_face_coeffs_fast(const Geo& g, const double* C, double rho1, double rho2, double* bx, double* by,
-                             double* bz, float* rh32, float2* rh2, cudaStream_t st);
+                             double* bz, float* rh32, float2* rh2, __half* rh16, cudaStream_t st);
 // rhs = div(u)/(h dt); partials: (sum rhs, max |rhs|, nonfinite count)
 int64_t launch_divergence(const Geo& g, const double* u, const double* v, const double* w,
                           double inv_hdt, double* rhs, double* partials, cudaStream_t st,
@@ -444,9 +445,11 @@ bool rho0_fits(const Geo& g);
 // reading it.  The z-column kernels write both colours on the zero pass and
 // ignore own_zero.  fail: a word the staged kernel sets when one of its
 // bounded waits gives up (may be null for the other kernels).
+// rh16 (may be null): rho/2 in FP16, read instead of rh by the register
+// plane-tile pass (tiles == 1)
 void launch_rbgs_rho(const Geo& g, const float* rh, double h, const float* f, float* x, int color,
                      double omega, bool zero_init, cudaStream_t st, int k0 = 0, int k1 = -1, int tiles = 1,
-                     bool own_zero = false, unsigned* fail = nullptr);
+                     bool own_zero = false, unsigned* fail = nullptr, const __half* rh16 = nullptr);
 // whether launch_rbgs_rho runs a plane kernel (staged or register tiles) on this grid
 bool rho0_tile_pass(const Geo& g, int tiles);
 // the staged colour pass (stage.cu): nx a multiple of 8, ny of its tile height
@@ -466,7 +469,8 @@ int64_t launch_matvec_rho_xpby(const Geo& g, const float* rh, double h, const fl
 int64_t rho0_matvec_blocks(const Geo& g);
 // coarse f = mean over the 2x2x2 children of (f - A x); coarse = every axis halved
 void launch_restrict_rho(const Geo& g, const float* rh, double h, const float* f, const float* x,
-                         const Geo& coarse, float* fc, cudaStream_t st, bool tiles = true);
+                         const Geo& coarse, float* fc, cudaStream_t st, bool tiles = true,
+                         const __half* rh16 = nullptr);
 // x += P xc (piecewise constant) onto the split level 0 from the level with every axis halved
 void launch_prolong_split(const Geo& fine, const Geo& coarse, const float* xc, float* x, cudaStream_t st);
 // scaled FP32 coefficients of the level with every axis halved

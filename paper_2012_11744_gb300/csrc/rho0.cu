@@ -436,6 +436,30 @@ __device__ __forceinline__ void ldgv(float (&d)[N], const float* __restrict__ p)
         }
     }
 }
+// N FP16 values widened to FP32 (N = 4: one 8-byte load, aligned to 8 bytes)
+template <int N>
+__device__ __forceinline__ void ldgv(float (&d)[N], const __half* __restrict__ p) {
+    static_assert(N == 2 || N == 4 || N == 8, "vector of 2, 4 or 8 halves");
+    if constexpr (N == 2) {
+        const float2 a = __half22float2(__ldg(reinterpret_cast<const __half2*>(p)));
+        d[0] = a.x;
+        d[1] = a.y;
+    } else {
+#pragma unroll
+        for (int h = 0; h < N / 4; ++h) {
+            const uint2 raw = __ldg(reinterpret_cast<const uint2*>(p + 4 * h));
+            const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&raw.x));
+            const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&raw.y));
+            d[4 * h] = a.x;
+            d[4 * h + 1] = a.y;
+            d[4 * h + 2] = b.x;
+            d[4 * h + 3] = b.y;
+        }
+    }
+}
+__device__ __forceinline__ float ldr(const float* __restrict__ p) { return __ldg(p); }
+__device__ __forceinline__ float ldr(const __half* __restrict__ p) { return __half2float(__ldg(p)); }
+
 template <int N>
 __device__ __forceinline__ void stv(float* p, const float (&d)[N]) {
     if constexpr (N == 2) {
@@ -449,8 +473,8 @@ __device__ __forceinline__ void stv(float* p, const float (&d)[N]) {
 // ZERO: x is taken as 0 everywhere (nothing of x is read) and only the
 // updated colour is written; XZ: the updated colour is taken as 0 (the pass
 // after a ZERO pass of the other colour, which left it unwritten).
-template <bool ZERO, bool XZ, int V, int M>
-__device__ __forceinline__ void tile_update(const Geo& g, const float* __restrict__ rh,
+template <bool ZERO, bool XZ, int V, int M, typename RT>
+__device__ __forceinline__ void tile_update(const Geo& g, const RT* __restrict__ rh,
                                             const float* __restrict__ f, float* x, float h2, float omega,
                                             int col, int j, int k, int t0, int lane, bool act) {
     const int nx = g.nx, hx = nx / 2, pl = nx * g.ny;
@@ -479,7 +503,7 @@ __device__ __forceinline__ void tile_update(const Geo& g, const float* __restric
     // the x-neighbour outside the lane's entries: cell 2t0-1 (M = 0) or
     // 2t0+2V (M = 1), of the other colour, wrapped around the row
     const int te = M == 0 ? (t0 > 0 ? -1 : hx - 1) : (t0 + V < hx ? V : V - hx);
-    const float re = __ldg(rh + o + (M == 0 ? (t0 > 0 ? -1 : nx - 1) : (t0 + V < hx ? 2 * V : 2 * V - nx)));
+    const float re = ldr(rh + o + (M == 0 ? (t0 > 0 ? -1 : nx - 1) : (t0 + V < hx ? 2 * V : 2 * V - nx)));
     float xu[V], xo[V], xym[V], xyp[V], xzm[V], xzp[V], xe = 0.f;
     if (ZERO) {
 #pragma unroll
@@ -557,8 +581,8 @@ __device__ __forceinline__ void tile_update(const Geo& g, const float* __restric
 #ifndef PARIS_TILE_MINB
 #define PARIS_TILE_MINB 1
 #endif
-template <bool ZERO, bool XZ, int V>
-__global__ void __launch_bounds__(kBX* kVY, PARIS_TILE_MINB) rbgs_rho_tile_kernel(Geo g, const float* __restrict__ rh, float h2,
+template <bool ZERO, bool XZ, int V, typename RT = float>
+__global__ void __launch_bounds__(kBX* kVY, PARIS_TILE_MINB) rbgs_rho_tile_kernel(Geo g, const RT* __restrict__ rh, float h2,
                                                                const float* __restrict__ f, float* x,
                                                                int color, float omega, int k0) {
     pdl_wait();
@@ -572,9 +596,9 @@ __global__ void __launch_bounds__(kBX* kVY, PARIS_TILE_MINB) rbgs_rho_tile_kerne
     const int t0 = act ? tv : hx - V;  // idle lanes shadow the last entries (no stores)
     // cell 2t0 has colour (j + k) & 1: the updated member is the same for the whole row
     if (((j + k + color) & 1) == 0)
-        tile_update<ZERO, XZ, V, 0>(g, rh, f, x, h2, omega, color, j, k, t0, lane, act);
+        tile_update<ZERO, XZ, V, 0, RT>(g, rh, f, x, h2, omega, color, j, k, t0, lane, act);
     else
-        tile_update<ZERO, XZ, V, 1>(g, rh, f, x, h2, omega, color, j, k, t0, lane, act);
+        tile_update<ZERO, XZ, V, 1, RT>(g, rh, f, x, h2, omega, color, j, k, t0, lane, act);
 }
 
 bool rho0_tile_pass(const Geo& g, int tiles) {
@@ -583,7 +607,7 @@ bool rho0_tile_pass(const Geo& g, int tiles) {
 
 void launch_rbgs_rho(const Geo& g, const float* rh, double h, const float* f, float* x, int color,
                      double omega, bool zero_init, cudaStream_t st, int k0, int k1, int tiles, bool own_zero,
-                     unsigned* fail) {
+                     unsigned* fail, const __half* rh16) {
     if (k1 < 0) k1 = g.nz;
     const bool al16 = (((uintptr_t)rh | (uintptr_t)f | (uintptr_t)x) & 15u) == 0;  // bulk copies: 16-byte aligned
     if (tiles == 2 && fail && al16 && rho0_stage_fits(g)) {
@@ -596,6 +620,19 @@ void launch_rbgs_rho(const Geo& g, const float* rh, double h, const float* f, fl
     if (tiles != 0 && kTileV > 0 && (g.nx / 2) % kTileV == 0) {
         constexpr int V = kTileV > 0 ? kTileV : 2;
         dim3 gr((hx / V + kBX - 1) / kBX, (g.ny + kVY - 1) / kVY, k1 - k0);
+        if (rh16 && tiles == 1) {  // the V-cycle's passes from FP16 rho/2
+            if (zero_init)
+                launch_pdl(rbgs_rho_tile_kernel<true, false, V, __half>, gr, dim3(kBX, kVY), 0, st, g, rh16, h2, f,
+                           x, color, (float)omega, k0);
+            else if (own_zero)
+                launch_pdl(rbgs_rho_tile_kernel<false, true, V, __half>, gr, dim3(kBX, kVY), 0, st, g, rh16, h2, f,
+                           x, color, (float)omega, k0);
+            else
+                launch_pdl(rbgs_rho_tile_kernel<false, false, V, __half>, gr, dim3(kBX, kVY), 0, st, g, rh16, h2, f,
+                           x, color, (float)omega, k0);
+            count_launch();
+            return;
+        }
         if (zero_init)
             launch_pdl(rbgs_rho_tile_kernel<true, false, V>, gr, dim3(kBX, kVY), 0, st, g, rh, h2, f, x, color,
                 (float)omega, k0);
@@ -801,8 +838,8 @@ namespace {
 // XP: x is formed on the fly as z + beta x (the flexible CG's direction
 // update d = z + beta d fused into the product that reads it; same FMA as
 // the separate update, so the same values).
-template <bool WITH_F, int V, int C0, bool XP = false>
-__device__ __forceinline__ void tile_apply(const Geo& g, const float* __restrict__ rh, const float* __restrict__ x,
+template <bool WITH_F, int V, int C0, bool XP = false, typename RT = float>
+__device__ __forceinline__ void tile_apply(const Geo& g, const RT* __restrict__ rh, const float* __restrict__ x,
                                            const float* __restrict__ f, int j, int k, int t0, int lane,
                                            float (&a)[2 * V], float (&X)[2 * V], float (&F)[2 * V],
                                            const float* __restrict__ z = nullptr, float beta = 0.f) {
@@ -863,8 +900,8 @@ __device__ __forceinline__ void tile_apply(const Geo& g, const float* __restrict
         xl_ld = fmaf(beta, xl_ld, __ldg(z + rb + (C0 ? 0 : hx) + tl));
         xr_ld = fmaf(beta, xr_ld, __ldg(z + rb + (C0 ? hx : 0) + tr));
     }
-    const float rl_ld = __ldg(rh + o + (t0 > 0 ? -1 : nx - 1));
-    const float rr_ld = __ldg(rh + o + (t0 + V < hx ? 2 * V : 2 * V - nx));
+    const float rl_ld = ldr(rh + o + (t0 > 0 ? -1 : nx - 1));
+    const float rr_ld = ldr(rh + o + (t0 + V < hx ? 2 * V : 2 * V - nx));
     const float xl_sh = __shfl_up_sync(kAll, X[2 * V - 1], 1), rl_sh = __shfl_up_sync(kAll, R[2 * V - 1], 1);
     const float xr_sh = __shfl_down_sync(kAll, X[0], 1), rr_sh = __shfl_down_sync(kAll, R[0], 1);
     const bool left_lane = lane > 0 && t0 > 0, right_lane = lane < 31 && t0 + V < hx;
@@ -922,8 +959,8 @@ __device__ __forceinline__ void tile_apply(const Geo& g, const float* __restrict
 #ifndef PARIS_OP_MINB
 #define PARIS_OP_MINB 3
 #endif
-template <bool RESTRICT, int V, bool XP = false>
-__global__ void __launch_bounds__(kBX* kVY, PARIS_OP_MINB) op_rho_tile_kernel(Geo g, const float* __restrict__ rh, float ih2,
+template <bool RESTRICT, int V, bool XP = false, typename RT = float>
+__global__ void __launch_bounds__(kBX* kVY, PARIS_OP_MINB) op_rho_tile_kernel(Geo g, const RT* __restrict__ rh, float ih2,
                                                              const float* __restrict__ x,
                                                              const float* __restrict__ f,
                                                              float* __restrict__ out, Geo cg,
@@ -951,9 +988,9 @@ __global__ void __launch_bounds__(kBX* kVY, PARIS_OP_MINB) op_rho_tile_kernel(Ge
         if (k >= g.nz) break;  // uniform per block
         float a[2 * V], X[2 * V], F[2 * V];
         if (((jc + k) & 1) == 0)
-            tile_apply<RESTRICT, V, 0, XP>(g, rh, x, f, jc, k, t0, lane, a, X, F, z, beta);
+            tile_apply<RESTRICT, V, 0, XP, RT>(g, rh, x, f, jc, k, t0, lane, a, X, F, z, beta);
         else
-            tile_apply<RESTRICT, V, 1, XP>(g, rh, x, f, jc, k, t0, lane, a, X, F, z, beta);
+            tile_apply<RESTRICT, V, 1, XP, RT>(g, rh, x, f, jc, k, t0, lane, a, X, F, z, beta);
         if (!RESTRICT) {
             const int c0 = (jc + k) & 1;
             float Q[2 * V], q0[V], q1[V];
@@ -1052,13 +1089,18 @@ int64_t launch_matvec_rho(const Geo& g, const float* rh, double h, const float* 
 }
 
 void launch_restrict_rho(const Geo& g, const float* rh, double h, const float* f, const float* x,
-                         const Geo& cg, float* fc, cudaStream_t st, bool tiles) {
+                         const Geo& cg, float* fc, cudaStream_t st, bool tiles, const __half* rh16) {
     const int hx = g.nx / 2;
     if (tiles && kTileOpV > 0 && hx % kTileOpV == 0) {
         constexpr int V = kTileOpV > 0 ? kTileOpV : 2;
         dim3 gr((hx / V + kBX - 1) / kBX, (g.ny + kVY - 1) / kVY, g.nz / 2);
-        launch_pdl(op_rho_tile_kernel<true, V>, gr, dim3(kBX, kVY), 0, st, g, rh, (float)(1.0 / (h * h)), x, f,
-            fc, cg, (double*)nullptr, 2, no_fin(), (const float*)nullptr, (const Scal*)nullptr, (float*)nullptr);
+        if (rh16)  // the V-cycle's restriction from FP16 rho/2
+            launch_pdl(op_rho_tile_kernel<true, V, false, __half>, gr, dim3(kBX, kVY), 0, st, g, rh16,
+                       (float)(1.0 / (h * h)), x, f, fc, cg, (double*)nullptr, 2, no_fin(), (const float*)nullptr,
+                       (const Scal*)nullptr, (float*)nullptr);
+        else
+            launch_pdl(op_rho_tile_kernel<true, V>, gr, dim3(kBX, kVY), 0, st, g, rh, (float)(1.0 / (h * h)), x, f,
+                fc, cg, (double*)nullptr, 2, no_fin(), (const float*)nullptr, (const Scal*)nullptr, (float*)nullptr);
         count_launch();
         return;
     }

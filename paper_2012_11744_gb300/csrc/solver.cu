@@ -104,6 +104,8 @@ struct paris_ctx {
     // rebuild their coefficients (paris_opts.level0_density)
     float* rh32 = nullptr;
     float2* rh2 = nullptr;  // rho/2 as (hi, lo) FP32 pairs for the refinement step
+    __half* rh16 = nullptr;  // rho/2 in FP16 for the V-cycle's finest passes (paris_opts.level0_half_rho)
+    bool half_rho = false;   // the current solve's V-cycle reads rh16
     bool rho0 = false;  // the current solve's level-0 FP32 kernels read rh32 instead of b32_0
     // solid cells (Sec. 3.8): the caller's cell flags (1 fluid, 0 solid), or null
     const unsigned char* solid = nullptr;
@@ -171,6 +173,7 @@ bool valid_opts(const paris_opts* o) {
     if (o->slab_planes < 0) return false;
     if (o->level0_density != 0 && o->level0_density != 1) return false;
     if (o->level0_tiles < 0 || o->level0_tiles > 2) return false;
+    if (o->level0_half_rho != 0 && o->level0_half_rho != 1) return false;
     return true;
 }
 
@@ -257,6 +260,7 @@ paris_status alloc_ctx(paris_ctx* c) {
     if (rho0_fits(c->g0)) {
         c->rh32 = m.get<float>(N);
         c->rh2 = m.get<float2>(N);
+        c->rh16 = m.get<__half>(N);
     }
     // block partials: up to 4 values per block of the largest reducing grid
     c->partials = m.get<double>(std::max(max_reduce_blocks(c->g0), rho0_matvec_blocks(c->g0)) * 4);
@@ -404,18 +408,20 @@ void smooth(paris_ctx* c, int l, const Coef<T>& cf, const T* f, T* x, int sweeps
         if (cls >= 0) {
             // bytes per pass: x at every cell (neighbours and the updated colour),
             // f and the write of the updated colour, plus the coefficients
-            // (three face arrays, or rho/2 once); a zero-initial pass reads no x
-            // and writes both colours (plane-tile zero pass: the updated colour
-            // only, and the pass after it reads neither colour's old value of its
-            // own cells)
+            // (three face arrays, or rho/2 once, 4 or 2 bytes a cell); a
+            // zero-initial pass reads no x and writes both colours (plane-tile
+            // zero pass: the updated colour only, and the pass after it reads
+            // neither colour's old value of its own cells)
             for (int s = 0; s < sweeps; ++s) {
                 const bool z0 = first_zero && s == 0;
                 const bool v0 = sizeof(T) == 4 && l == 0 && c->rho0;
                 const bool h16 = sizeof(T) == 4 && l == 0 && c->half0;
                 const double bsz = h16 ? 2.0 : (double)sz;
                 const bool tile0 = v0 && rho0_tile_pass(L.g, o.level0_tiles);
-                phase_bytes += v0 ? (z0 ? (tile0 ? 2.0 : 2.5) : 3.0) * n * sz : (z0 ? 2 * n * sz : 2.5 * n * sz + nb * bsz);
-                phase_bytes += v0 ? ((z0 && tile0) ? 2.5 : 3.0) * n * sz : 2.5 * n * sz + nb * bsz;
+                const double rhb = c->half_rho ? 2.0 : 4.0;  // bytes of rho/2 per cell
+                phase_bytes += v0 ? (z0 ? (tile0 ? 1.0 : 1.5) : 2.0) * n * sz + rhb * n
+                                  : (z0 ? 2 * n * sz : 2.5 * n * sz + nb * bsz);
+                phase_bytes += v0 ? ((z0 && tile0) ? 1.5 : 2.0) * n * sz + rhb * n : 2.5 * n * sz + nb * bsz;
                 phase_n += slabs ? 2 * m : 2;
             }
             phase_cls = cls;
@@ -435,7 +441,8 @@ void smooth(paris_ctx* c, int l, const Coef<T>& cf, const T* f, T* x, int sweeps
                         // after a zero pass the other colour is still unwritten on the
                         // plane-tile path: the second pass of that sweep takes it as zero
                         launch_rbgs_rho(L.g, c->rh32, c->grid.h, (const float*)f, (float*)x, color, o.omega,
-                                        zero, c->st, a, b, o.level0_tiles, z0 && !zero, &c->scal->wait_fail);
+                                        zero, c->st, a, b, o.level0_tiles, z0 && !zero, &c->scal->wait_fail,
+                                        c->half_rho ? c->rh16 : nullptr);
                         return;
                     }
                     if (h16) {
@@ -504,11 +511,12 @@ void vdown(paris_ctx* c, const Coef<T>& c0, const T* f0, T* x0, int l) {
     const bool v0 = sizeof(T) == 4 && l == 0 && c->rho0;
     ProfScope ps(c, l == 0 ? PARIS_K_RESTRICT0 : -1,
                  (2 * n + (double)C.g.ncell()) * sizeof(T) +
-                     (v0 ? n * sizeof(T) : beta_count(c->lv[l].g) * (h16 ? 2 : sizeof(T))));
+                     (v0 ? n * (c->half_rho ? 2.0 : (double)sizeof(T)) : beta_count(c->lv[l].g) * (h16 ? 2 : sizeof(T))));
     if constexpr (sizeof(T) == 4) {
         if (v0) {
             launch_restrict_rho(c->lv[l].g, c->rh32, c->grid.h, (const float*)f, (const float*)x, C.g,
-                                (float*)Prec<T>::f(C), c->st, c->opts.level0_tiles != 0);
+                                (float*)Prec<T>::f(C), c->st, c->opts.level0_tiles != 0,
+                                c->half_rho ? c->rh16 : nullptr);
             return;
         }
         if (h16) {
@@ -561,7 +569,10 @@ void vup(paris_ctx* c, const Coef<T>& c0, const T* f0, T* x0, int l) {
 
 // Levels with at most this many cells, down to the dense coarsest level,
 // run as one single-block launch (launch_tail_vcycle).
-constexpr int64_t kTailCells = 4096;
+#ifndef PARIS_TAIL_CELLS
+#define PARIS_TAIL_CELLS 4096
+#endif
+constexpr int64_t kTailCells = PARIS_TAIL_CELLS;
 
 // First level of that tail, or -1 (the tail needs the two-pass red-black
 // smoother, a dense coarsest level and at least one level above it).
@@ -785,6 +796,7 @@ struct Level0Mode {
     ~Level0Mode() {
         c->rho0 = false;
         c->half0 = false;
+        c->half_rho = false;
     }
 };
 
@@ -807,7 +819,7 @@ void mixed_setup(paris_ctx* c, const Coef<double>& c64, bool rho0) {
 }
 
 paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, SolveOut& out,
-                         int max_iter, bool rho0) {
+                         int max_iter, bool rho0, bool half_rho) {
     const int64_t N = c->N;
     Level0Mode mode_guard{c};
     Coef<float> c32{c->b32_0[0], c->b32_0[1], c->b32_0[2], 1.0f};
@@ -817,6 +829,7 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
     } else {
         mixed_setup(c, c64, rho0);
     }
+    c->half_rho = c->rho0 && half_rho && c->rh16 && c->opts.level0_tiles == 1;
     c->mixed_ready = false;
     // With the finest level from rho/2 the refinement step updates r in
     // double-float (launch_refine_rho) after the first FP64 residual; the
@@ -935,6 +948,7 @@ void paris_default_opts(paris_opts* o) {
     o->half_coefficients = 0;
     o->level0_density = 1;
     o->level0_tiles = 1;
+    o->level0_half_rho = 1;
 }
 
 const char* paris_status_string(paris_status s) {
@@ -1108,7 +1122,7 @@ namespace {
 // mean_known: the caller reset scal and left the mean of rhs in scal->mean_b.
 paris_status poisson_solve(paris_ctx* c, const double* bx, const double* by, const double* bz,
                            const double* rhs, double* p, paris_stats* st, bool rho0,
-                           bool mean_known) {
+                           bool mean_known, bool half_rho = false) {
     const double ih2 = 1.0 / (c->grid.h * c->grid.h);
     Coef<double> c64{bx, by, bz, ih2};
     if (c->dirichlet) c64.sig = c->sig0;
@@ -1122,7 +1136,7 @@ paris_status poisson_solve(paris_ctx* c, const double* bx, const double* by, con
     SolveOut out;
     int fell_back = 0;
     if (c->opts.precision == PARIS_MIXED && !c->dirichlet) {
-        s = solve_mixed(c, c64, p, out, c->opts.max_iter, rho0);
+        s = solve_mixed(c, c64, p, out, c->opts.max_iter, rho0, half_rho);
         if (s != PARIS_OK) return s;
         if (!out.converged && !out.nonfinite && c->opts.fallback) {
             SolveOut o2;
@@ -1205,6 +1219,8 @@ paris_status projection_step_impl(paris_ctx* c, const double* C, double rho1, do
     // the FP32 pairs of rho/2 need both half-densities well inside the FP32 range
     const double rlo = 0.5 * std::min(rho1, rho2), rhi = 0.5 * std::max(rho1, rho2);
     const bool use_rho0 = rho0_usable(c) && rlo >= 1e-30 && rhi <= 1e30;
+    // FP16 rho/2 for the V-cycle (normal FP16 numbers with room to spare)
+    const bool use_half = use_rho0 && !force && c->opts.level0_half_rho && c->rh16 && rlo >= 1e-4 && rhi <= 6e4;
     // the set-up run ahead below is used by this step's solve only
     struct ReadyGuard {
         paris_ctx* c;
@@ -1215,7 +1231,7 @@ paris_status projection_step_impl(paris_ctx* c, const double* C, double rho1, do
         if (hl) CK(cudaStreamWaitEvent(c->st, hl->c_ready, 0));
         if (use_rho0 && !force)  // beta to about 2^-46: the operator of the double-float refinement
             launch_face_coeffs_fast(c->g0, C, rho1, rho2, c->beta[0], c->beta[1], c->beta[2], c->rh32, c->rh2,
-                                    c->st);
+                                    use_half ? c->rh16 : nullptr, c->st);
         else
             launch_face_coeffs(c->g0, C, rho1, rho2, c->beta[0], c->beta[1], c->beta[2],
                                use_rho0 ? c->rh32 : nullptr, use_rho0 ? c->rh2 : nullptr, c->st, force);
@@ -1251,7 +1267,7 @@ paris_status projection_step_impl(paris_ctx* c, const double* C, double rho1, do
     if (hl) CK(cudaStreamWaitEvent(c->st, hl->p_ready, 0));
     paris_status s;
     paris_status solve =
-        poisson_solve(c, c->beta[0], c->beta[1], c->beta[2], c->rhs, p, st, use_rho0, true);
+        poisson_solve(c, c->beta[0], c->beta[1], c->beta[2], c->rhs, p, st, use_rho0, true, use_half);
     if (solve != PARIS_OK && solve != PARIS_ERR_NOT_CONVERGED) return solve;
     if (hl) {
         // the correction only reads p: copy it out meanwhile

@@ -414,7 +414,7 @@ def test_level0_tiles_match_column_kernels(paris, grid):
     pr = pi.random_problem(grid, seed=33, rho1=1000.0)
     out = []
     for tiles in (1, 0):
-        with ctx_for(paris, grid, precision=paris.MIXED, level0_tiles=tiles) as ctx:
+        with ctx_for(paris, grid, precision=paris.MIXED, level0_tiles=tiles, level0_half_rho=0) as ctx:
             u, v, w = dev(pr.u), dev(pr.v), dev(pr.w)
             p = torch.zeros(grid.shape, dtype=torch.float64, device="cuda")
             ctx.profile(True)
@@ -443,7 +443,7 @@ def test_staged_colour_pass_bit_identical_to_register_tiles(paris, grid):
     pr = pi.random_problem(grid, seed=35, rho1=1000.0)
     out = []
     for tiles in (2, 1):
-        with ctx_for(paris, grid, precision=paris.MIXED, level0_tiles=tiles) as ctx:
+        with ctx_for(paris, grid, precision=paris.MIXED, level0_tiles=tiles, level0_half_rho=0) as ctx:
             u, v, w = dev(pr.u), dev(pr.v), dev(pr.w)
             p = torch.zeros(grid.shape, dtype=torch.float64, device="cuda")
             st = ctx.projection_step(dev(pr.C), pr.rho1, pr.rho2, pr.dt, u, v, w, p)
@@ -452,3 +452,37 @@ def test_staged_colour_pass_bit_identical_to_register_tiles(paris, grid):
     assert out[0][4:] == out[1][4:]
     for a, b in zip(out[0][:4], out[1][:4]):
         np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("grid", [pi.Grid(64, 64, 64, 1 / 64, (P, P, W)), pi.Grid(96, 48, 40, 1 / 96, (W, P, P))],
+                         ids=["64_ppw", "96x48x40_wpp"])
+@pytest.mark.parametrize("rho1,rho2", [(1000.0, 1.0), (1.0, 1e-4)], ids=["ratio1000", "rho_below_fp16"])
+def test_half_density_v_cycle(paris, grid, rho1, rho2):
+    """The V-cycle's finest passes reading rho/2 in FP16 (level0_half_rho)
+    change the preconditioner only: the step converges in at most one more
+    iteration than with FP32 rho/2 and returns p within 1e-8 of it, both
+    within the oracle's bar; densities outside FP16's comfortable range
+    (rho/2 below 1e-4 here) keep FP32."""
+    pr = pi.random_problem(grid, seed=37, rho1=rho1, rho2=rho2)
+    ref = oracle.projection_step(grid, pr.C, pr.rho1, pr.rho2, pr.dt, pr.u, pr.v, pr.w)
+    out = []
+    for half in (1, 0):
+        with ctx_for(paris, grid, precision=paris.MIXED, level0_half_rho=half) as ctx:
+            u, v, w = dev(pr.u), dev(pr.v), dev(pr.w)
+            p = torch.zeros(grid.shape, dtype=torch.float64, device="cuda")
+            ctx.profile(True)
+            st = ctx.projection_step(dev(pr.C), pr.rho1, pr.rho2, pr.dt, u, v, w, p)
+            prof = ctx.profile_read()["smooth0"]
+            ctx.profile(False)
+            assert st["converged"] == 1 and st["fell_back"] == 0, (half, st)
+            out.append((host(p), st["iters"], prof["bytes"] / prof["timed"] / grid.ncells))
+    (ph, ih, bh), (pf, i_f, bf) = out
+    assert ih <= i_f + 1, (ih, i_f)
+    scale = np.abs(ref.p).max()
+    assert np.abs(ph - pf).max() <= 1e-8 * scale
+    assert np.abs(ph - ref.p).max() <= 1e-8 * scale
+    # the bytes the class counts: 2 B of rho/2 a cell fewer per regular pass in the FP16 mode
+    if min(rho1, rho2) >= 2e-4:
+        assert bh < bf - 1.0
+    else:
+        assert bh == bf
