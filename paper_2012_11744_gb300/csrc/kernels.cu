@@ -1366,7 +1366,7 @@ constexpr int kKU = 4;
 template <typename T>
 __global__ void update_xr_kernel(int64_t n, const Scal* s, const T* __restrict__ d,
                                  const T* __restrict__ q, T* __restrict__ x, T* __restrict__ r,
-                                 double* partials, int vec, FinSpec fin) {
+                                 double* partials, int vec, FinSpec fin, int rev) {
     using VT = typename V16<T>::type;
     constexpr int W = V16<T>::n;
     constexpr int U = kKU / 2;  // four arrays per element: two iterations at once
@@ -1385,15 +1385,17 @@ __global__ void update_xr_kernel(int64_t n, const Scal* s, const T* __restrict__
     };
     const int64_t nv = vec ? n / W : 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // rev: the vectors from the end (a pass that starts where the previous one ended)
+    auto at = [&](int64_t e) { return rev ? nv - 1 - e : e; };
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (; i + (U - 1) * stride < nv; i += U * stride) {
         VT dv[U], qv[U], xv[U], rv[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            dv[u] = reinterpret_cast<const VT*>(d)[i + u * stride];
-            qv[u] = reinterpret_cast<const VT*>(q)[i + u * stride];
-            xv[u] = reinterpret_cast<VT*>(x)[i + u * stride];
-            rv[u] = reinterpret_cast<VT*>(r)[i + u * stride];
+            dv[u] = reinterpret_cast<const VT*>(d)[at(i + u * stride)];
+            qv[u] = reinterpret_cast<const VT*>(q)[at(i + u * stride)];
+            xv[u] = reinterpret_cast<VT*>(x)[at(i + u * stride)];
+            rv[u] = reinterpret_cast<VT*>(r)[at(i + u * stride)];
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -1403,23 +1405,23 @@ __global__ void update_xr_kernel(int64_t n, const Scal* s, const T* __restrict__
             T* re = reinterpret_cast<T*>(&rv[u]);
 #pragma unroll
             for (int w = 0; w < W; ++w) one(de[w], qe[w], xe[w], re[w], l2[u], li[u]);
-            reinterpret_cast<VT*>(x)[i + u * stride] = xv[u];
-            reinterpret_cast<VT*>(r)[i + u * stride] = rv[u];
+            reinterpret_cast<VT*>(x)[at(i + u * stride)] = xv[u];
+            reinterpret_cast<VT*>(r)[at(i + u * stride)] = rv[u];
         }
     }
     for (; i < nv; i += stride) {
-        const VT dv = reinterpret_cast<const VT*>(d)[i];
-        const VT qv = reinterpret_cast<const VT*>(q)[i];
-        VT xv = reinterpret_cast<VT*>(x)[i];
-        VT rv = reinterpret_cast<VT*>(r)[i];
+        const VT dv = reinterpret_cast<const VT*>(d)[at(i)];
+        const VT qv = reinterpret_cast<const VT*>(q)[at(i)];
+        VT xv = reinterpret_cast<VT*>(x)[at(i)];
+        VT rv = reinterpret_cast<VT*>(r)[at(i)];
         const T* de = reinterpret_cast<const T*>(&dv);
         const T* qe = reinterpret_cast<const T*>(&qv);
         T* xe = reinterpret_cast<T*>(&xv);
         T* re = reinterpret_cast<T*>(&rv);
 #pragma unroll
         for (int w = 0; w < W; ++w) one(de[w], qe[w], xe[w], re[w], l2[0], li[0]);
-        reinterpret_cast<VT*>(x)[i] = xv;
-        reinterpret_cast<VT*>(r)[i] = rv;
+        reinterpret_cast<VT*>(x)[at(i)] = xv;
+        reinterpret_cast<VT*>(r)[at(i)] = rv;
     }
     PARIS_TAIL_FOR(c, nv * W, n) {
         T xv = x[c], rv = r[c];
@@ -1441,17 +1443,17 @@ __global__ void update_xr_kernel(int64_t n, const Scal* s, const T* __restrict__
 
 template <typename T>
 int64_t launch_update_xr(int64_t n, const Scal* s, const T* d, const T* q, T* x, T* r,
-                         double* partials, cudaStream_t st, FinSpec fin) {
+                         double* partials, cudaStream_t st, FinSpec fin, bool rev) {
     int nb = elementwise_blocks(n);
     launch_pdl(update_xr_kernel<T>, dim3(nb), dim3(kRedThreads), 0, st, n, s, d, q, x, r, partials,
-               aligned16(d, q, x, r) ? 1 : 0, fin);
+               aligned16(d, q, x, r) ? 1 : 0, fin, rev ? 1 : 0);
     count_launch();
     return nb;
 }
 
 template <typename T>
 __global__ void dot2_kernel(int64_t n, const T* __restrict__ a, const T* __restrict__ b,
-                            const T* __restrict__ c, double* partials, int vec, FinSpec fin) {
+                            const T* __restrict__ c, double* partials, int vec, FinSpec fin, int rev) {
     using VT = typename V16<T>::type;
     constexpr int W = V16<T>::n;
     constexpr int U = kKU;
@@ -1461,14 +1463,15 @@ __global__ void dot2_kernel(int64_t n, const T* __restrict__ a, const T* __restr
     for (int u = 0; u < U; ++u) s0[u] = s1[u] = T(0);
     const int64_t nv = vec ? n / W : 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    auto at = [&](int64_t e) { return rev ? nv - 1 - e : e; };  // rev: from the end
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (; i + (U - 1) * stride < nv; i += U * stride) {
         VT av[U], bv[U], cv[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            av[u] = __ldcs(reinterpret_cast<const VT*>(a) + i + u * stride);
-            bv[u] = __ldcs(reinterpret_cast<const VT*>(b) + i + u * stride);
-            if (c) cv[u] = __ldcs(reinterpret_cast<const VT*>(c) + i + u * stride);
+            av[u] = __ldg(reinterpret_cast<const VT*>(a) + at(i + u * stride));
+            bv[u] = __ldg(reinterpret_cast<const VT*>(b) + at(i + u * stride));
+            if (c) cv[u] = __ldg(reinterpret_cast<const VT*>(c) + at(i + u * stride));
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -1484,14 +1487,14 @@ __global__ void dot2_kernel(int64_t n, const T* __restrict__ a, const T* __restr
         }
     }
     for (; i < nv; i += stride) {
-        const VT av = reinterpret_cast<const VT*>(a)[i];
-        const VT bv = reinterpret_cast<const VT*>(b)[i];
+        const VT av = reinterpret_cast<const VT*>(a)[at(i)];
+        const VT bv = reinterpret_cast<const VT*>(b)[at(i)];
         const T* ae = reinterpret_cast<const T*>(&av);
         const T* be = reinterpret_cast<const T*>(&bv);
 #pragma unroll
         for (int w = 0; w < W; ++w) s0[0] = fma(ae[w], be[w], s0[0]);
         if (c) {
-            const VT cv = reinterpret_cast<const VT*>(c)[i];
+            const VT cv = reinterpret_cast<const VT*>(c)[at(i)];
             const T* ce = reinterpret_cast<const T*>(&cv);
 #pragma unroll
             for (int w = 0; w < W; ++w) s1[0] = fma(ae[w], ce[w], s1[0]);
@@ -1510,10 +1513,10 @@ __global__ void dot2_kernel(int64_t n, const T* __restrict__ a, const T* __restr
 
 template <typename T>
 int64_t launch_dot2(int64_t n, const T* a, const T* b, const T* c, double* partials,
-                    cudaStream_t st, FinSpec fin) {
+                    cudaStream_t st, FinSpec fin, bool rev) {
     int nb = elementwise_blocks(n);
     launch_pdl(dot2_kernel<T>, dim3(nb), dim3(kRedThreads), 0, st, n, a, b, c, partials,
-               aligned16(a, b, c) ? 1 : 0, fin);
+               aligned16(a, b, c) ? 1 : 0, fin, rev ? 1 : 0);
     count_launch();
     return nb;
 }
@@ -1723,9 +1726,9 @@ cudaError_t stream_rates(const float* a, const float* b, const float* c, float* 
     template int64_t launch_matvec_dot<T>(const Geo&, const Coef<T>&, const T*, T*, double*,   \
                                           cudaStream_t, FinSpec);                              \
     template int64_t launch_update_xr<T>(int64_t, const Scal*, const T*, const T*, T*, T*,     \
-                                         double*, cudaStream_t, FinSpec);                      \
+                                         double*, cudaStream_t, FinSpec, bool);                \
     template int64_t launch_dot2<T>(int64_t, const T*, const T*, const T*, double*,            \
-                                    cudaStream_t, FinSpec);                                    \
+                                    cudaStream_t, FinSpec, bool);                              \
     template void launch_xpby<T>(int64_t, const Scal*, const T*, T*, cudaStream_t);
 
 PARIS_INSTANTIATE(float)

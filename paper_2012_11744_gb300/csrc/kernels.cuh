@@ -449,7 +449,8 @@ bool rho0_fits(const Geo& g);
 // plane-tile pass (tiles == 1)
 void launch_rbgs_rho(const Geo& g, const float* rh, double h, const float* f, float* x, int color,
                      double omega, bool zero_init, cudaStream_t st, int k0 = 0, int k1 = -1, int tiles = 1,
-                     bool own_zero = false, unsigned* fail = nullptr, const __half* rh16 = nullptr);
+                     bool own_zero = false, unsigned* fail = nullptr, const __half* rh16 = nullptr,
+                     bool rev = false);
 // whether launch_rbgs_rho runs a plane kernel (staged or register tiles) on this grid
 bool rho0_tile_pass(const Geo& g, int tiles);
 // the staged colour pass (stage.cu): nx a multiple of 8, ny of its tile height
@@ -459,20 +460,20 @@ cudaError_t launch_rbgs_rho_stage(const Geo& g, const float* rh, double h, const
                                   cudaStream_t st);
 // q = A d; partials (d . q); returns the number of blocks
 int64_t launch_matvec_rho(const Geo& g, const float* rh, double h, const float* d, float* q,
-                          double* partials, cudaStream_t st, FinSpec fin = no_fin(), bool tiles = true);
+                          double* partials, cudaStream_t st, FinSpec fin = no_fin(), bool tiles = true, bool rev = false);
 // the plane-tile product with the flexible CG's direction update fused in:
 // dnew = z + beta d (beta from s) and q = A dnew, d . q partials as above
 // (dnew must not alias z or d); only where rho0_product_fuses
 bool rho0_product_fuses(const Geo& g, bool tiles);
 int64_t launch_matvec_rho_xpby(const Geo& g, const float* rh, double h, const float* z, const float* d, float* dnew,
-                               float* q, const Scal* s, double* partials, cudaStream_t st, FinSpec fin);
+                               float* q, const Scal* s, double* partials, cudaStream_t st, FinSpec fin, bool rev = false);
 int64_t rho0_matvec_blocks(const Geo& g);
 // coarse f = mean over the 2x2x2 children of (f - A x); coarse = every axis halved
 void launch_restrict_rho(const Geo& g, const float* rh, double h, const float* f, const float* x,
                          const Geo& coarse, float* fc, cudaStream_t st, bool tiles = true,
-                         const __half* rh16 = nullptr);
+                         const __half* rh16 = nullptr, bool rev = false);
 // x += P xc (piecewise constant) onto the split level 0 from the level with every axis halved
-void launch_prolong_split(const Geo& fine, const Geo& coarse, const float* xc, float* x, cudaStream_t st);
+void launch_prolong_split(const Geo& fine, const Geo& coarse, const float* xc, float* x, cudaStream_t st, bool rev = false);
 // scaled FP32 coefficients of the level with every axis halved
 void launch_coarse_beta_rho(const Geo& fine, const float* rh, double h, const Geo& coarse, float* out[3],
                             cudaStream_t st);
@@ -482,7 +483,7 @@ void launch_coarse_beta_rho(const Geo& fine, const float* rh, double h, const Ge
 // r32 = 2^b r_new (2^a: s->scale, 2^b from s->rinf), norms (FIN_REFINE fused);
 // e and r32 in the colour-split layout
 void launch_refine_rho(const Geo& g, const float2* rh2, double h, const float* e, const double* r_old,
-                       double* r_new, double* x, float* r32, Scal* s, double* partials, cudaStream_t st);
+                       double* r_new, double* x, float* r32, Scal* s, double* partials, cudaStream_t st, bool rev = false);
 
 // ------------------------------------------------ single-launch V-cycle tail ---
 // One level of the tail: coefficients (scaled by `scale`), inverse diagonal
@@ -523,11 +524,11 @@ int64_t launch_matvec_dot(const Geo& g, const Coef<T>& cf, const T* d, T* q, dou
 // x += alpha d; r -= alpha q; partials (||r||^2, max|r|, nonfinite)
 template <typename T>
 int64_t launch_update_xr(int64_t n, const Scal* s, const T* d, const T* q, T* x, T* r,
-                         double* partials, cudaStream_t st, FinSpec fin = no_fin());
+                         double* partials, cudaStream_t st, FinSpec fin = no_fin(), bool rev = false);
 // partials (a . b, a . c)  (c may be null -> 0); fin: fused second stage
 template <typename T>
 int64_t launch_dot2(int64_t n, const T* a, const T* b, const T* c, double* partials,
-                    cudaStream_t st, FinSpec fin = no_fin());
+                    cudaStream_t st, FinSpec fin = no_fin(), bool rev = false);
 // d = z + beta d
 template <typename T>
 void launch_xpby(int64_t n, const Scal* s, const T* z, T* d, cudaStream_t st);

@@ -82,8 +82,9 @@ __global__ void __launch_bounds__(kTX* kTY) refine_rho_kernel(Geo g, const float
                                                             const float* __restrict__ e,
                                                             const double* r_old, double* r_new,
                                                             double* __restrict__ x, float* __restrict__ r32,
-                                                            const Scal* s, double* partials, FinSpec fin) {
+                                                            const Scal* s, double* partials, FinSpec fin, int rev) {
     pdl_wait();
+    const int zb = rev ? (int)(gridDim.z - 1 - blockIdx.z) : (int)blockIdx.z;  // rev: descending plane chunks
     const int i = blockIdx.x * kTX + threadIdx.x;
     const int j = blockIdx.y * kTY + threadIdx.y;
     float l2 = 0.f;
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(kTX* kTY) refine_rho_kernel(Geo g, const float
         const int hx = nx / 2;
         const int tx = i >> 1;
         const int txm = (xlo ? nx - 1 : i - 1) >> 1, txp = (xhi ? 0 : i + 1) >> 1;
-        const int k0 = blockIdx.z * kZ, k1 = min(k0 + kZ, nz);
+        const int k0 = zb * kZ, k1 = min(k0 + kZ, nz);
         for (int k = k0; k < k1; ++k) {
             const int c = (k * ny + j) * nx + i;
             const bool zlo = k == 0, zhi = k == nz - 1;
@@ -146,20 +147,20 @@ __global__ void __launch_bounds__(kTX* kTY) refine_rho_kernel(Geo g, const float
         }
     }
     const int tid = threadIdx.y * kTX + threadIdx.x;
-    const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    const int64_t blk = ((int64_t)zb * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     block_reduce_skc<float>(l2, rmax_k, nf, partials, blk, tid);
     finalize_last_block(partials, (int64_t)gridDim.x * gridDim.y * gridDim.z, fin, tid);
 }
 
 void launch_refine_rho(const Geo& g, const float2* rh2, double h, const float* e, const double* r_old,
-                       double* r_new, double* x, float* r32, Scal* s, double* partials, cudaStream_t st) {
+                       double* r_new, double* x, float* r32, Scal* s, double* partials, cudaStream_t st, bool rev) {
     // 1/h^2 as an FP32 pair
     const double ih2d = 1.0 / (h * h);
     const float hi = (float)ih2d;
     const float lo = (float)(ih2d - (double)hi);
     dim3 gr((g.nx + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, (g.nz + kZ - 1) / kZ);
     launch_pdl(refine_rho_kernel, gr, dim3(kTX, kTY), 0, st, g, rh2, hi, lo, e, r_old, r_new, x, r32, s,
-        partials, FinSpec{s, 3, 2, FIN_REFINE, 0.0});
+        partials, FinSpec{s, 3, 2, FIN_REFINE, 0.0}, rev ? 1 : 0);
     count_launch();
 }
 

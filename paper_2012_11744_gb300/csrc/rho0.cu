@@ -584,11 +584,15 @@ __device__ __forceinline__ void tile_update(const Geo& g, const RT* __restrict__
 template <bool ZERO, bool XZ, int V, typename RT = float>
 __global__ void __launch_bounds__(kBX* kVY, PARIS_TILE_MINB) rbgs_rho_tile_kernel(Geo g, const RT* __restrict__ rh, float h2,
                                                                const float* __restrict__ f, float* x,
-                                                               int color, float omega, int k0) {
+                                                               int color, float omega, int k0, int rev) {
     pdl_wait();
     const int j = blockIdx.y * kVY + threadIdx.y;
     if (j >= g.ny) return;  // uniform per warp
-    const int k = k0 + blockIdx.z;
+    // rev: the planes in descending order (the blocks of a grid start in
+    // ascending blockIdx order, so a pass that runs against the previous one
+    // begins where that one ended, on planes still in L2; the cells of one
+    // colour are independent, so the order changes no value)
+    const int k = k0 + (rev ? (int)(gridDim.z - 1 - blockIdx.z) : (int)blockIdx.z);
     const int lane = threadIdx.x & 31;
     const int hx = g.nx / 2;
     const int tv = (blockIdx.x * kBX + threadIdx.x) * V;
@@ -607,7 +611,7 @@ bool rho0_tile_pass(const Geo& g, int tiles) {
 
 void launch_rbgs_rho(const Geo& g, const float* rh, double h, const float* f, float* x, int color,
                      double omega, bool zero_init, cudaStream_t st, int k0, int k1, int tiles, bool own_zero,
-                     unsigned* fail, const __half* rh16) {
+                     unsigned* fail, const __half* rh16, bool rev) {
     if (k1 < 0) k1 = g.nz;
     const bool al16 = (((uintptr_t)rh | (uintptr_t)f | (uintptr_t)x) & 15u) == 0;  // bulk copies: 16-byte aligned
     if (tiles == 2 && fail && al16 && rho0_stage_fits(g)) {
@@ -623,25 +627,25 @@ void launch_rbgs_rho(const Geo& g, const float* rh, double h, const float* f, fl
         if (rh16 && tiles == 1) {  // the V-cycle's passes from FP16 rho/2
             if (zero_init)
                 launch_pdl(rbgs_rho_tile_kernel<true, false, V, __half>, gr, dim3(kBX, kVY), 0, st, g, rh16, h2, f,
-                           x, color, (float)omega, k0);
+                           x, color, (float)omega, k0, rev ? 1 : 0);
             else if (own_zero)
                 launch_pdl(rbgs_rho_tile_kernel<false, true, V, __half>, gr, dim3(kBX, kVY), 0, st, g, rh16, h2, f,
-                           x, color, (float)omega, k0);
+                           x, color, (float)omega, k0, rev ? 1 : 0);
             else
                 launch_pdl(rbgs_rho_tile_kernel<false, false, V, __half>, gr, dim3(kBX, kVY), 0, st, g, rh16, h2, f,
-                           x, color, (float)omega, k0);
+                           x, color, (float)omega, k0, rev ? 1 : 0);
             count_launch();
             return;
         }
         if (zero_init)
             launch_pdl(rbgs_rho_tile_kernel<true, false, V>, gr, dim3(kBX, kVY), 0, st, g, rh, h2, f, x, color,
-                (float)omega, k0);
+                (float)omega, k0, rev ? 1 : 0);
         else if (own_zero)
             launch_pdl(rbgs_rho_tile_kernel<false, true, V>, gr, dim3(kBX, kVY), 0, st, g, rh, h2, f, x, color,
-                (float)omega, k0);
+                (float)omega, k0, rev ? 1 : 0);
         else
             launch_pdl(rbgs_rho_tile_kernel<false, false, V>, gr, dim3(kBX, kVY), 0, st, g, rh, h2, f, x, color,
-                (float)omega, k0);
+                (float)omega, k0, rev ? 1 : 0);
         count_launch();
         return;
     }
@@ -967,9 +971,13 @@ __global__ void __launch_bounds__(kBX* kVY, PARIS_OP_MINB) op_rho_tile_kernel(Ge
                                                              double* partials, int np, FinSpec fin,
                                                              const float* __restrict__ z = nullptr,
                                                              const Scal* s = nullptr,
-                                                             float* __restrict__ xnew = nullptr) {
+                                                             float* __restrict__ xnew = nullptr, int rev = 0) {
     __shared__ float sh[kVY][kBX * V];
     pdl_wait();
+    // rev: the plane groups in descending order (starting where a previous
+    // pass ended); a block's work, and its slot of partial sums, follow its
+    // plane group, so the result does not depend on the order
+    const int zb = rev ? (int)(gridDim.z - 1 - blockIdx.z) : (int)blockIdx.z;
     const float beta = XP ? (float)s->beta : 0.f;  // XP: x = z + beta x, written to xnew
     const int ty = threadIdx.y, lane = threadIdx.x;
     const int j = blockIdx.y * kVY + ty;
@@ -984,7 +992,7 @@ __global__ void __launch_bounds__(kBX* kVY, PARIS_OP_MINB) op_rho_tile_kernel(Ge
 #pragma unroll
     for (int v = 0; v < V; ++v) acc[v] = 0.f;
     for (int p = 0; p < np; ++p) {
-        const int k = blockIdx.z * np + p;
+        const int k = zb * np + p;
         if (k >= g.nz) break;  // uniform per block
         float a[2 * V], X[2 * V], F[2 * V];
         if (((jc + k) & 1) == 0)
@@ -1031,12 +1039,12 @@ __global__ void __launch_bounds__(kBX* kVY, PARIS_OP_MINB) op_rho_tile_kernel(Ge
             float cf[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) cf[v] = (sh[ty][lane * V + v] + sh[ty + 1][lane * V + v]) * 0.125f;
-            stv<V>(out + ((int)blockIdx.z * cg.ny + (j >> 1)) * cg.nx + t0, cf);
+            stv<V>(out + (zb * cg.ny + (j >> 1)) * cg.nx + t0, cf);
         }
     } else {
         double red[1] = {(double)loc};
         const int op[1] = {0};
-        const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        const int64_t blk = ((int64_t)zb * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
         block_reduce_store<1>(red, op, partials, blk, ty * kBX + lane);
         finalize_last_block(partials, (int64_t)gridDim.x * gridDim.y * gridDim.z, fin, ty * kBX + lane);
     }
@@ -1058,25 +1066,25 @@ int64_t rho0_matvec_blocks(const Geo& g) {
 bool rho0_product_fuses(const Geo& g, bool tiles) { return tiles && kTileOpV > 0 && (g.nx / 2) % kTileOpV == 0; }
 
 int64_t launch_matvec_rho_xpby(const Geo& g, const float* rh, double h, const float* z, const float* d, float* dnew,
-                               float* q, const Scal* s, double* partials, cudaStream_t st, FinSpec fin) {
+                               float* q, const Scal* s, double* partials, cudaStream_t st, FinSpec fin, bool rev) {
     constexpr int V = kTileOpV > 0 ? kTileOpV : 2;
     const int hx = g.nx / 2;
     dim3 gr((hx / V + kBX - 1) / kBX, (g.ny + kVY - 1) / kVY, (g.nz + kTileOpPlanes - 1) / kTileOpPlanes);
     launch_pdl(op_rho_tile_kernel<false, V, true>, gr, dim3(kBX, kVY), 0, st, g, rh, (float)(1.0 / (h * h)), d,
-               (const float*)nullptr, q, g, partials, kTileOpPlanes, fin, z, s, dnew);
+               (const float*)nullptr, q, g, partials, kTileOpPlanes, fin, z, s, dnew, rev ? 1 : 0);
     count_launch();
     return (int64_t)gr.x * gr.y * gr.z;
 }
 
 int64_t launch_matvec_rho(const Geo& g, const float* rh, double h, const float* d, float* q,
-                          double* partials, cudaStream_t st, FinSpec fin, bool tiles) {
+                          double* partials, cudaStream_t st, FinSpec fin, bool tiles, bool rev) {
     const int hx = g.nx / 2;
     if (tiles && kTileOpV > 0 && hx % kTileOpV == 0) {
         constexpr int V = kTileOpV > 0 ? kTileOpV : 2;
         dim3 gr((hx / V + kBX - 1) / kBX, (g.ny + kVY - 1) / kVY, (g.nz + kTileOpPlanes - 1) / kTileOpPlanes);
         launch_pdl(op_rho_tile_kernel<false, V>, gr, dim3(kBX, kVY), 0, st, g, rh, (float)(1.0 / (h * h)), d,
             (const float*)nullptr, q, g, partials, kTileOpPlanes, fin, (const float*)nullptr, (const Scal*)nullptr,
-            (float*)nullptr);
+            (float*)nullptr, rev ? 1 : 0);
         count_launch();
         return (int64_t)gr.x * gr.y * gr.z;
     }
@@ -1089,7 +1097,7 @@ int64_t launch_matvec_rho(const Geo& g, const float* rh, double h, const float* 
 }
 
 void launch_restrict_rho(const Geo& g, const float* rh, double h, const float* f, const float* x,
-                         const Geo& cg, float* fc, cudaStream_t st, bool tiles, const __half* rh16) {
+                         const Geo& cg, float* fc, cudaStream_t st, bool tiles, const __half* rh16, bool rev) {
     const int hx = g.nx / 2;
     if (tiles && kTileOpV > 0 && hx % kTileOpV == 0) {
         constexpr int V = kTileOpV > 0 ? kTileOpV : 2;
@@ -1097,10 +1105,11 @@ void launch_restrict_rho(const Geo& g, const float* rh, double h, const float* f
         if (rh16)  // the V-cycle's restriction from FP16 rho/2
             launch_pdl(op_rho_tile_kernel<true, V, false, __half>, gr, dim3(kBX, kVY), 0, st, g, rh16,
                        (float)(1.0 / (h * h)), x, f, fc, cg, (double*)nullptr, 2, no_fin(), (const float*)nullptr,
-                       (const Scal*)nullptr, (float*)nullptr);
+                       (const Scal*)nullptr, (float*)nullptr, rev ? 1 : 0);
         else
             launch_pdl(op_rho_tile_kernel<true, V>, gr, dim3(kBX, kVY), 0, st, g, rh, (float)(1.0 / (h * h)), x, f,
-                fc, cg, (double*)nullptr, 2, no_fin(), (const float*)nullptr, (const Scal*)nullptr, (float*)nullptr);
+                fc, cg, (double*)nullptr, 2, no_fin(), (const float*)nullptr, (const Scal*)nullptr, (float*)nullptr,
+                rev ? 1 : 0);
         count_launch();
         return;
     }
@@ -1117,12 +1126,12 @@ void launch_restrict_rho(const Geo& g, const float* rh, double h, const float* f
 // halved (piecewise-constant P): entry t of both half-rows of row (j, k) is a
 // child of coarse cell (t, j/2, k/2).  V = 4: four entries per thread.
 template <int V>
-__global__ void prolong_split_kernel(Geo fg, Geo cg, const float* __restrict__ xc, float* __restrict__ x) {
+__global__ void prolong_split_kernel(Geo fg, Geo cg, const float* __restrict__ xc, float* __restrict__ x, int rev) {
     pdl_wait();
     const int hx = fg.nx / 2;
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) * V;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
+    const int k = rev ? (int)(gridDim.z - 1 - blockIdx.z) : (int)blockIdx.z;  // rev: descending planes
     if (t >= hx || j >= fg.ny) return;
     const int rb = (k * fg.ny + j) * fg.nx + t;
     const int cb = ((k >> 1) * cg.ny + (j >> 1)) * cg.nx + t;
@@ -1141,14 +1150,14 @@ __global__ void prolong_split_kernel(Geo fg, Geo cg, const float* __restrict__ x
     }
 }
 
-void launch_prolong_split(const Geo& fine, const Geo& coarse, const float* xc, float* x, cudaStream_t st) {
+void launch_prolong_split(const Geo& fine, const Geo& coarse, const float* xc, float* x, cudaStream_t st, bool rev) {
     const int hx = fine.nx / 2;
     const bool v4 = hx % 4 == 0 && ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(xc)) & 15) == 0;
     const int per = v4 ? 4 : 1;
     dim3 blk(32, 8);
     dim3 gr((hx / per + 31) / 32, (fine.ny + 7) / 8, fine.nz);
-    if (v4) launch_pdl(prolong_split_kernel<4>, gr, blk, 0, st, fine, coarse, xc, x);
-    else launch_pdl(prolong_split_kernel<1>, gr, blk, 0, st, fine, coarse, xc, x);
+    if (v4) launch_pdl(prolong_split_kernel<4>, gr, blk, 0, st, fine, coarse, xc, x, rev ? 1 : 0);
+    else launch_pdl(prolong_split_kernel<1>, gr, blk, 0, st, fine, coarse, xc, x, rev ? 1 : 0);
     count_launch();
 }
 

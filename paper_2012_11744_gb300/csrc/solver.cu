@@ -106,6 +106,10 @@ struct paris_ctx {
     float2* rh2 = nullptr;  // rho/2 as (hi, lo) FP32 pairs for the refinement step
     __half* rh16 = nullptr;  // rho/2 in FP16 for the V-cycle's finest passes (paris_opts.level0_half_rho)
     bool half_rho = false;   // the current solve's V-cycle reads rh16
+    // plane order of the finest level's passes in the mixed form: each pass
+    // starts where the one before it ended (its data still in L2), so
+    // successive passes alternate; lz: the next one runs from the last plane
+    bool lz = false;
     bool rho0 = false;  // the current solve's level-0 FP32 kernels read rh32 instead of b32_0
     // solid cells (Sec. 3.8): the caller's cell flags (1 fluid, 0 solid), or null
     const unsigned char* solid = nullptr;
@@ -379,6 +383,19 @@ void setup_hierarchy(paris_ctx* c, const Coef<T>& c0) {
         launch_coarse_inverse<T>(c->lv[nl - 1].g, level_coef<T>(c, nl - 1, c0), c->coarse_inv, c->st);
 }
 
+#ifndef PARIS_ZREV
+#define PARIS_ZREV 1
+#endif
+constexpr bool kZrev = PARIS_ZREV != 0;
+
+// the plane order of the next finest-level pass of the mixed form (see
+// paris_ctx::lz), and the order of the one after it
+bool take_dir(paris_ctx* c) {
+    const bool r = kZrev && c->lz;
+    c->lz = !c->lz;
+    return r;
+}
+
 template <typename T>
 void smooth(paris_ctx* c, int l, const Coef<T>& cf, const T* f, T* x, int sweeps, bool first_zero,
             bool reverse) {
@@ -440,9 +457,11 @@ void smooth(paris_ctx* c, int l, const Coef<T>& cf, const T* f, T* x, int sweeps
                     if (v0) {
                         // after a zero pass the other colour is still unwritten on the
                         // plane-tile path: the second pass of that sweep takes it as zero
+                        // successive passes alternate their plane order, each starting
+                        // where the previous one ended (planes still in L2)
                         launch_rbgs_rho(L.g, c->rh32, c->grid.h, (const float*)f, (float*)x, color, o.omega,
                                         zero, c->st, a, b, o.level0_tiles, z0 && !zero, &c->scal->wait_fail,
-                                        c->half_rho ? c->rh16 : nullptr);
+                                        c->half_rho ? c->rh16 : nullptr, take_dir(c));
                         return;
                     }
                     if (h16) {
@@ -516,7 +535,7 @@ void vdown(paris_ctx* c, const Coef<T>& c0, const T* f0, T* x0, int l) {
         if (v0) {
             launch_restrict_rho(c->lv[l].g, c->rh32, c->grid.h, (const float*)f, (const float*)x, C.g,
                                 (float*)Prec<T>::f(C), c->st, c->opts.level0_tiles != 0,
-                                c->half_rho ? c->rh16 : nullptr);
+                                c->half_rho ? c->rh16 : nullptr, take_dir(c));
             return;
         }
         if (h16) {
@@ -558,7 +577,7 @@ void vup(paris_ctx* c, const Coef<T>& c0, const T* f0, T* x0, int l) {
         bool split = false;
         if constexpr (sizeof(T) == 4) {
             if (l == 0 && c->rho0) {
-                launch_prolong_split(c->lv[l].g, C.g, (const float*)Prec<T>::x(C), (float*)x, c->st);
+                launch_prolong_split(c->lv[l].g, C.g, (const float*)Prec<T>::x(C), (float*)x, c->st, take_dir(c));
                 split = true;
             }
         }
@@ -830,6 +849,7 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
         mixed_setup(c, c64, rho0);
     }
     c->half_rho = c->rho0 && half_rho && c->rh16 && c->opts.level0_tiles == 1;
+    c->lz = false;  // the same plane orders in every solve (the same sums)
     c->mixed_ready = false;
     // With the finest level from rho/2 the refinement step updates r in
     // double-float (launch_refine_rho) after the first FP64 residual; the
@@ -842,6 +862,7 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
     for (bool first = true;; first = false) {
         // r32 = scale * (f - A x); x is the untouched initial guess on the first pass
         paris_status s = (first || !refine) ? true_residual(c, c64, x, c->r32, first, refine) : read_scal(c);
+        if (first || !refine) c->lz = true;  // the residual ran through the planes in ascending order
         if (s != PARIS_OK) return s;
         const Scal& h = *c->scal_h;
         if (h.nonfinite > 0) { out.nonfinite = true; return PARIS_OK; }
@@ -864,7 +885,7 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
         {
             ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
             launch_dot2<float>(N, c->r32, c->z32, nullptr, c->partials, c->st,
-                               FinSpec{c->scal, 2, 0, FIN_RHO_INIT, 0.0});
+                               FinSpec{c->scal, 2, 0, FIN_RHO_INIT, 0.0}, c->rho0 && take_dir(c));
             std::swap(c->d32, c->z32);  // first direction d = z: exchange the buffers
         }
         // with the finest level from rho/2 the direction update d = z + beta d
@@ -875,12 +896,12 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
             if (fuse_next) {
                 ProfScope ps(c, PARIS_K_MATVEC0, 5.0 * N * 4);
                 launch_matvec_rho_xpby(c->g0, c->rh32, c->grid.h, c->z32, c->d32, c->d32b, c->q32, c->scal,
-                                       c->partials, c->st, FinSpec{c->scal, 1, 0, FIN_ALPHA, 0.0});
+                                       c->partials, c->st, FinSpec{c->scal, 1, 0, FIN_ALPHA, 0.0}, take_dir(c));
                 std::swap(c->d32, c->d32b);
             } else if (c->rho0) {
                 ProfScope ps(c, PARIS_K_MATVEC0, 3.0 * N * 4);
                 launch_matvec_rho(c->g0, c->rh32, c->grid.h, c->d32, c->q32, c->partials, c->st,
-                                  FinSpec{c->scal, 1, 0, FIN_ALPHA, 0.0}, c->opts.level0_tiles != 0);
+                                  FinSpec{c->scal, 1, 0, FIN_ALPHA, 0.0}, c->opts.level0_tiles != 0, take_dir(c));
             } else {
                 ProfScope ps(c, PARIS_K_MATVEC0, (2.0 * N + beta_count(c->g0)) * 4);
                 launch_matvec_dot<float>(c->g0, c32, c->d32, c->q32, c->partials, c->st,
@@ -889,7 +910,7 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
             {
                 ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
                 launch_update_xr<float>(N, c->scal, c->d32, c->q32, c->e32, c->r32, c->partials, c->st,
-                                        FinSpec{c->scal, 3, 2, FIN_STORE, 0.0});
+                                        FinSpec{c->scal, 3, 2, FIN_STORE, 0.0}, c->rho0 && take_dir(c));
                 s = read_scal(c);
             }
             ++out.iters;
@@ -900,16 +921,18 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
             vcycle<float>(c, c32, c->r32, c->z32);
             ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
             launch_dot2<float>(N, c->z32, c->r32, c->q32, c->partials, c->st,  // (z.r, z.q)
-                               FinSpec{c->scal, 2, 0, FIN_FCG_BETA, 0.0});
-            if (fuse)
+                               FinSpec{c->scal, 2, 0, FIN_FCG_BETA, 0.0}, c->rho0 && take_dir(c));
+            if (fuse) {
                 fuse_next = true;
-            else
+            } else {
                 launch_xpby<float>(N, c->scal, c->z32, c->d32, c->st);
+                c->lz = true;
+            }
         }
         if (refine) {
             ProfScope ps(c, PARIS_K_RESID64, 48.0 * N);
             launch_refine_rho(c->g0, c->rh2, c->grid.h, c->e32, c->r, c->r, x, c->r32, c->scal, c->partials,
-                              c->st);
+                              c->st, take_dir(c));
         } else {
             ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
             launch_accumulate(N, c->scal, c->e32, x, c->st);
