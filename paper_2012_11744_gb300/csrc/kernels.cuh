@@ -493,6 +493,9 @@ template <typename T>
 struct TailLevel {
     Geo g;
     int fac[3];
+    // multipliers of the divisions by nx, ny and the pairs per row (nx + 1)/2:
+    // t / n = umulhi(t, m) for t, n < 2^16 with m = ceil(2^32 / n) (n > 1)
+    unsigned mx, my, mp;
     T scale;
     const T* bx;
     const T* by;

@@ -351,6 +351,8 @@ Coef<T> level_coef(paris_ctx* c, int l, const Coef<T>& c0) {
     return cf;
 }
 
+int tail_start(const paris_ctx* c);
+
 // Per-solve set-up of the hierarchy in precision T: coarse coefficients,
 // inverse diagonals, dense coarsest inverse.
 template <typename T>
@@ -374,11 +376,17 @@ void setup_hierarchy(paris_ctx* c, const Coef<T>& c0) {
             if (c->dirichlet) launch_coarse_sig<T>(F.g, cf.sig, (double)cf.scale, L.g, L.fac, L.sig64, c->st);
         }
     }
-    // inverse diagonals: read by the FP64 smoothers and by Jacobi; the FP32
-    // red-black sweeps recompute them from the coefficients they load
-    if (sizeof(T) == 8 || c->opts.smoother == PARIS_SMOOTH_JACOBI)
+    // inverse diagonals: read by the FP64 smoothers, by Jacobi and by the
+    // single-block tail; the FP32 red-black sweeps of the other levels
+    // recompute them from the coefficients they load (the same value)
+    const int t = tail_start(c);
+    if (sizeof(T) == 8 || c->opts.smoother == PARIS_SMOOTH_JACOBI) {
         for (int l = 0; l < nl; ++l)
             launch_inv_diag<T>(c->lv[l].g, level_coef<T>(c, l, c0), Prec<T>::w(c->lv[l]), c->st);
+    } else if (t > 0) {
+        for (int l = t; l < nl; ++l)
+            launch_inv_diag<T>(c->lv[l].g, level_coef<T>(c, l, c0), Prec<T>::w(c->lv[l]), c->st);
+    }
     if (c->dense_coarse)
         launch_coarse_inverse<T>(c->lv[nl - 1].g, level_coef<T>(c, nl - 1, c0), c->coarse_inv, c->st);
 }
@@ -613,16 +621,20 @@ void launch_tail(paris_ctx* c, int t) {
         TailLevel<T>& d = tl[l - t];
         d.g = L.g;
         for (int a = 0; a < 3; ++a) d.fac[a] = L.fac[a];
+        // multipliers of the index divisions (ceil(2^32 / n); n = 1 is special-cased in the kernel)
+        auto mul = [](int n) { return n > 1 ? (unsigned)((0x100000000ull + (unsigned)n - 1) / (unsigned)n) : 0u; };
+        d.mx = mul(L.g.nx);
+        d.my = mul(L.g.ny);
+        d.mp = mul((L.g.nx + 1) / 2);
         d.scale = T(1);
         d.bx = Prec<T>::b(L, 0);
         d.by = Prec<T>::b(L, 1);
         d.bz = Prec<T>::b(L, 2);
-        d.w = sizeof(T) == 8 ? Prec<T>::w(L) : nullptr;
+        d.w = Prec<T>::w(L);  // the inverse diagonals (set up with the hierarchy)
         d.x = Prec<T>::x(L);
         d.f = Prec<T>::f(L);
     }
-    launch_tail_vcycle<T>(tl, nl - t, c->coarse_inv, c->opts.omega, c->opts.nu1, c->opts.nu2, sizeof(T) == 8,
-                          c->st);
+    launch_tail_vcycle<T>(tl, nl - t, c->coarse_inv, c->opts.omega, c->opts.nu1, c->opts.nu2, true, c->st);
 }
 
 // Levels 1 .. L-1 of the V-cycle (level 0's restriction already done).

@@ -39,11 +39,15 @@ struct TailArgs {
     int nu1, nu2;
 };
 
-// (i, j, k) of index t on an n0 x n1 x n2 box, x fastest
-__device__ __forceinline__ void tail_split(unsigned t, unsigned n0, unsigned n1, int& i, int& j, int& k) {
-    const unsigned row = t / n0;
+// t / n by the multiplier m of TailLevel (exact for t, n < 2^16)
+__device__ __forceinline__ unsigned udiv(unsigned t, unsigned n, unsigned m) { return n == 1 ? t : __umulhi(t, m); }
+
+// (i, j, k) of index t on an n0 x n1 x n2 box, x fastest (m0, m1: the multipliers of n0, n1)
+__device__ __forceinline__ void tail_split(unsigned t, unsigned n0, unsigned n1, unsigned m0, unsigned m1, int& i,
+                                           int& j, int& k) {
+    const unsigned row = udiv(t, n0, m0);
     i = (int)(t - row * n0);
-    const unsigned kk = row / n1;
+    const unsigned kk = udiv(row, n1, m1);
     j = (int)(row - kk * n1);
     k = (int)kk;
 }
@@ -51,14 +55,14 @@ __device__ __forceinline__ void tail_split(unsigned t, unsigned n0, unsigned n1,
 // One colour pass of over-relaxed red-black Gauss-Seidel on a tail level (the
 // update of rbgs_kernel; zero: x taken as 0, the other colour zeroed).
 template <typename T, bool USEW>
-__device__ void tail_pass(const TailLevel<T>& L, int color, bool zero, T omega) {
-    const Geo& g = L.g;
+__device__ void tail_pass(const TailLevel<T> L, int color, bool zero, T omega) {
+    const Geo g = L.g;
     const T hs = T(1) / L.scale;
     const int npair = (g.nx + 1) / 2;
     const int total = npair * g.ny * g.nz;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
         int tp, j, k;
-        tail_split((unsigned)t, (unsigned)npair, (unsigned)g.ny, tp, j, k);
+        tail_split((unsigned)t, (unsigned)npair, (unsigned)g.ny, L.mp, L.my, tp, j, k);
         const int i0 = 2 * tp;
         const int i = i0 + ((i0 + j + k + color) & 1);
         const int io = i0 + 1 - (i - i0);
@@ -84,7 +88,7 @@ __device__ void tail_pass(const TailLevel<T>& L, int color, bool zero, T omega) 
 }
 
 template <typename T, bool USEW>
-__device__ void tail_smooth(const TailLevel<T>& L, int sweeps, bool first_zero, bool reverse, T omega) {
+__device__ void tail_smooth(const TailLevel<T> L, int sweeps, bool first_zero, bool reverse, T omega) {
     const int c0 = reverse ? 1 : 0;
     for (int s = 0; s < sweeps; ++s) {
         tail_pass<T, USEW>(L, c0, first_zero && s == 0, omega);
@@ -96,14 +100,14 @@ __device__ void tail_smooth(const TailLevel<T>& L, int sweeps, bool first_zero, 
 
 // coarse f = average over the children of the fine residual f - A x
 template <typename T>
-__device__ void tail_restrict(const TailLevel<T>& F, const TailLevel<T>& C) {
-    const Geo& fg = F.g;
-    const Geo& cg = C.g;
+__device__ void tail_restrict(const TailLevel<T> F, const TailLevel<T> C) {
+    const Geo fg = F.g;
+    const Geo cg = C.g;
     const int fa0 = C.fac[0], fa1 = C.fac[1], fa2 = C.fac[2];
     const int total = cg.nx * cg.ny * cg.nz;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
         int I, J, K;
-        tail_split((unsigned)t, (unsigned)cg.nx, (unsigned)cg.ny, I, J, K);
+        tail_split((unsigned)t, (unsigned)cg.nx, (unsigned)cg.ny, C.mx, C.my, I, J, K);
         T sum = T(0);
         for (int dk = 0; dk < fa2; ++dk)
             for (int dj = 0; dj < fa1; ++dj)
@@ -120,20 +124,20 @@ __device__ void tail_restrict(const TailLevel<T>& F, const TailLevel<T>& C) {
 
 // x_fine += x_coarse[parent]
 template <typename T>
-__device__ void tail_prolong(const TailLevel<T>& C, const TailLevel<T>& F) {
-    const Geo& fg = F.g;
-    const Geo& cg = C.g;
+__device__ void tail_prolong(const TailLevel<T> C, const TailLevel<T> F) {
+    const Geo fg = F.g;
+    const Geo cg = C.g;
     const int total = fg.nx * fg.ny * fg.nz;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
         int i, j, k;
-        tail_split((unsigned)t, (unsigned)fg.nx, (unsigned)fg.ny, i, j, k);
+        tail_split((unsigned)t, (unsigned)fg.nx, (unsigned)fg.ny, F.mx, F.my, i, j, k);
         F.x[t] += C.x[cg.cidx(i >> (C.fac[0] - 1), j >> (C.fac[1] - 1), k >> (C.fac[2] - 1))];
     }
 }
 
 // x = M (f - mean f) on the coarsest level (FP64 arithmetic)
 template <typename T>
-__device__ void tail_coarse_solve(const TailLevel<T>& L, const double* __restrict__ M, double* fs,
+__device__ void tail_coarse_solve(const TailLevel<T> L, const double* __restrict__ M, double* fs,
                                   double* mean) {
     const int n = L.g.nx * L.g.ny * L.g.nz;
     for (int c = threadIdx.x; c < n; c += blockDim.x) fs[c] = (double)L.f[c];
@@ -211,7 +215,7 @@ __global__ void __launch_bounds__(kTailThreads) tail_vcycle_kernel(const __grid_
         __syncthreads();
     }
     for (int l = 0; l < n - 1; ++l) {
-        const TailLevel<T>& L = Ls[l];
+        const TailLevel<T> L = Ls[l];  // in registers: the loops below store through its pointers
         if (a.nu1 > 0) {
             tail_smooth<T, USEW>(L, a.nu1, true, false, a.omega);
         } else {
