@@ -903,6 +903,20 @@ __device__ __forceinline__ void ld4(T (&d)[4], const T* __restrict__ p) {
         d[0] = a.x; d[1] = a.y; d[2] = b.x; d[3] = b.y;
     }
 }
+// four FP16 values widened to FP32 (one 8-byte load)
+__device__ __forceinline__ void ld4(float (&d)[4], const __half* __restrict__ p) {
+    const uint2 raw = __ldg(reinterpret_cast<const uint2*>(p));
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&raw.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&raw.y));
+    d[0] = a.x;
+    d[1] = a.y;
+    d[2] = b.x;
+    d[3] = b.y;
+}
+__device__ __forceinline__ float ldb(const float* __restrict__ p) { return __ldg(p); }
+__device__ __forceinline__ double ldb(const double* __restrict__ p) { return __ldg(p); }
+__device__ __forceinline__ float ldb(const __half* __restrict__ p) { return __half2float(__ldg(p)); }
+
 template <typename T>
 __device__ __forceinline__ void ld4x(T (&d)[4], const T* p) {  // x: written in the same pass
     if constexpr (sizeof(T) == 4) {
@@ -921,9 +935,9 @@ __device__ __forceinline__ void ld4x(T (&d)[4], const T* p) {  // x: written in 
 // more slowly).  Same update, faces in the same order.  Needs nx % 4 == 0, no
 // walls along x, 32-bit offsets and 16-byte aligned arrays.
 // M: the updated member of both pairs ((j + k + color) & 1, uniform per warp)
-template <typename T, bool USEW, int M>
-__device__ __forceinline__ void rbgs4_row(const Geo& g, const T* __restrict__ bx, const T* __restrict__ by,
-                                          const T* __restrict__ bz, T scale, const T* __restrict__ w,
+template <typename T, typename TB, bool USEW, int M>
+__device__ __forceinline__ void rbgs4_row(const Geo& g, const TB* __restrict__ bx, const TB* __restrict__ by,
+                                          const TB* __restrict__ bz, T scale, const T* __restrict__ w,
                                           const T* __restrict__ f, T* __restrict__ x, T omega, int zero_init,
                                           int j, int k, int i0, int lane, bool act) {
     const int nx = g.nx, ny = g.ny, nz = g.nz, pl = nx * ny;
@@ -945,7 +959,7 @@ __device__ __forceinline__ void rbgs4_row(const Geo& g, const T* __restrict__ bx
     // face i0+4 (the + face of the last cell): the next lane's first, or loaded
     const int ir = i0 + 4 < nx ? i0 + 4 : 0;
     // (every lane takes part in the shuffle; the select comes after it)
-    const T bxr_ld = __ldg(bx + rowc + ir);
+    const T bxr_ld = (T)ldb(bx + rowc + ir);
     const T bxr_sh = __shfl_down_sync(0xffffffffu, BX[0], 1);
     const T bxr = (lane < kTX - 1 && i0 + 4 < nx) ? bxr_sh : bxr_ld;
     if (zero_init) {
@@ -996,10 +1010,10 @@ __device__ __forceinline__ void rbgs4_row(const Geo& g, const T* __restrict__ bx
     }
 }
 
-template <typename T, bool USEW>
-__global__ void __launch_bounds__(kTX* kTY) rbgs4_kernel(Geo g, const T* __restrict__ bx,
-                                                        const T* __restrict__ by,
-                                                        const T* __restrict__ bz, T scale,
+template <typename T, bool USEW, typename TB = T>
+__global__ void __launch_bounds__(kTX* kTY) rbgs4_kernel(Geo g, const TB* __restrict__ bx,
+                                                        const TB* __restrict__ by,
+                                                        const TB* __restrict__ bz, T scale,
                                                         const T* __restrict__ w,
                                                         const T* __restrict__ f, T* __restrict__ x,
                                                         int color, T omega, int zero_init, int k0) {
@@ -1013,9 +1027,9 @@ __global__ void __launch_bounds__(kTX* kTY) rbgs4_kernel(Geo g, const T* __restr
     const bool act = qv < nq;
     const int i0 = 4 * (act ? qv : nq - 1);  // idle lanes shadow the last quad (no stores)
     if (((j + k + color) & 1) == 0)
-        rbgs4_row<T, USEW, 0>(g, bx, by, bz, scale, w, f, x, omega, zero_init, j, k, i0, lane, act);
+        rbgs4_row<T, TB, USEW, 0>(g, bx, by, bz, scale, w, f, x, omega, zero_init, j, k, i0, lane, act);
     else
-        rbgs4_row<T, USEW, 1>(g, bx, by, bz, scale, w, f, x, omega, zero_init, j, k, i0, lane, act);
+        rbgs4_row<T, TB, USEW, 1>(g, bx, by, bz, scale, w, f, x, omega, zero_init, j, k, i0, lane, act);
 }
 
 template <typename T>
@@ -1062,6 +1076,15 @@ void launch_rbgs(const Geo& g, const Coef<T>& cf, const T* w, const T* f, T* x, 
 void launch_rbgs_h(const Geo& g, const __half* const b[3], float scale, const float* f, float* x,
                    int color, double omega, bool zero_init, cudaStream_t st, int k0, int k1) {
     if (k1 < 0) k1 = g.nz;
+    // four cells per thread where a row fills a warp (the update of the pair kernel)
+    if (g.nx % 4 == 0 && g.nx >= 4 * kTX && !g.wx && fits_i32(g) && aligned16(f, x) &&
+        ((((uintptr_t)b[0] | (uintptr_t)b[1] | (uintptr_t)b[2]) & 7u) == 0)) {
+        dim3 gr((g.nx / 4 + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, k1 - k0);
+        launch_pdl(rbgs4_kernel<float, false, __half>, gr, dim3(kTX, kTY), 0, st, g, b[0], b[1], b[2], scale,
+                   (const float*)nullptr, f, x, color, (float)omega, zero_init ? 1 : 0, k0);
+        count_launch();
+        return;
+    }
     const int npair = (g.nx + 1) / 2;
     dim3 gr((npair + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, k1 - k0);
     if (fits_i32(g))

@@ -474,9 +474,11 @@ void launch_restrict_rho(const Geo& g, const float* rh, double h, const float* f
                          const __half* rh16 = nullptr, bool rev = false);
 // x += P xc (piecewise constant) onto the split level 0 from the level with every axis halved
 void launch_prolong_split(const Geo& fine, const Geo& coarse, const float* xc, float* x, cudaStream_t st, bool rev = false);
-// scaled FP32 coefficients of the level with every axis halved
+// scaled FP32 coefficients of the level with every axis halved; out16 (may be
+// null): FP16 copies of the sums of the four fine faces' coefficients times s16
+// (the FP32 coefficient is that sum times 1/(16 h^2))
 void launch_coarse_beta_rho(const Geo& fine, const float* rh, double h, const Geo& coarse, float* out[3],
-                            cudaStream_t st);
+                            cudaStream_t st, __half* const out16[3] = nullptr, float s16 = 1.f);
 
 // FP64 refinement step of the mixed form on the finest level, A d in
 // double-float from the rho/2 pairs rh2: x += 2^-a e, r_new = r_old - A 2^-a e,

@@ -1168,7 +1168,7 @@ void launch_prolong_split(const Geo& fine, const Geo& coarse, const float* xc, f
 // 1/h0^2 (the coarse arrays hold scaled coefficients).
 template <int AXIS>
 __global__ void coarse_beta_rho_kernel(Geo fg, const float* __restrict__ rh, float scale, Geo cg,
-                                       float* __restrict__ out) {
+                                       float* __restrict__ out, __half* __restrict__ out16, float s16) {
     const int n0 = cg.nx + (AXIS == 0 ? cg.wx : 0);
     const int n1 = cg.ny + (AXIS == 1 ? cg.wy : 0);
     const int n2 = cg.nz + (AXIS == 2 ? cg.wz : 0);
@@ -1185,6 +1185,7 @@ __global__ void coarse_beta_rho_kernel(Geo fg, const float* __restrict__ rh, flo
         const int F = AXIS == 0 ? I : (AXIS == 1 ? J : K);
         if (wall && (F == 0 || F == cn)) {
             out[t] = 0.f;
+            if (out16) out16[t] = __float2half_rn(0.f);
             continue;
         }
         // fine cells on either side of the face plane 2F along AXIS; the
@@ -1201,16 +1202,21 @@ __global__ void coarse_beta_rho_kernel(Geo fg, const float* __restrict__ rh, flo
                 s += bface(__ldg(rh + cl), __ldg(rh + cl + dhi));
             }
         out[t] = s * scale;
+        if (out16) out16[t] = __float2half_rn(s * s16);  // the sum times a power of two
     }
 }
 
 void launch_coarse_beta_rho(const Geo& fine, const float* rh, double h, const Geo& coarse, float* out[3],
-                            cudaStream_t st) {
+                            cudaStream_t st, __half* const out16[3], float s16) {
     // mean of 4 faces (1/4) x (h0/h1)^2 (1/4) x 1/h0^2
     const float scale = (float)(1.0 / (16.0 * h * h));
-    coarse_beta_rho_kernel<0><<<elementwise_blocks(coarse.nface(0)), kRedThreads, 0, st>>>(fine, rh, scale, coarse, out[0]);
-    coarse_beta_rho_kernel<1><<<elementwise_blocks(coarse.nface(1)), kRedThreads, 0, st>>>(fine, rh, scale, coarse, out[1]);
-    coarse_beta_rho_kernel<2><<<elementwise_blocks(coarse.nface(2)), kRedThreads, 0, st>>>(fine, rh, scale, coarse, out[2]);
+    for (int a = 0; a < 3; ++a) {
+        const unsigned nb = (unsigned)elementwise_blocks(coarse.nface(a));
+        __half* o16 = out16 ? out16[a] : nullptr;
+        if (a == 0) coarse_beta_rho_kernel<0><<<nb, kRedThreads, 0, st>>>(fine, rh, scale, coarse, out[0], o16, s16);
+        if (a == 1) coarse_beta_rho_kernel<1><<<nb, kRedThreads, 0, st>>>(fine, rh, scale, coarse, out[1], o16, s16);
+        if (a == 2) coarse_beta_rho_kernel<2><<<nb, kRedThreads, 0, st>>>(fine, rh, scale, coarse, out[2], o16, s16);
+    }
     count_launch(3);
 }
 

@@ -44,6 +44,8 @@ struct Level {
     double* f64 = nullptr;
     double* t64 = nullptr;
     double* sig64 = nullptr;  // diagonal excess of a Dirichlet-coupled operator (levels >= 1, on first use)
+    __half* b16[3] = {nullptr, nullptr, nullptr};  // level 1 of the mixed step: FP16 coefficients (see half1)
+    float scale16 = 1.f;                           // their scale (the coefficient is b16 * scale16)
 };
 
 struct Alloc {
@@ -105,7 +107,8 @@ struct paris_ctx {
     float* rh32 = nullptr;
     float2* rh2 = nullptr;  // rho/2 as (hi, lo) FP32 pairs for the refinement step
     __half* rh16 = nullptr;  // rho/2 in FP16 for the V-cycle's finest passes (paris_opts.level0_half_rho)
-    bool half_rho = false;   // the current solve's V-cycle reads rh16
+    bool half_rho = false;   // the current solve's V-cycle reads rh16, and level 1 its FP16 coefficients
+    double rho_min = 1.0;    // the smaller density of the current projection step
     // plane order of the finest level's passes in the mixed form: each pass
     // starts where the one before it ended (its data still in L2), so
     // successive passes alternate; lz: the next one runs from the last plane
@@ -141,8 +144,8 @@ struct paris_ctx {
     // CUDA graphs of the coarse part of the V-cycle (index 0: FP32, 1: FP64)
     cudaStream_t cap_stream = nullptr;
     bool cap_stream_broken = false;
-    cudaGraphExec_t cg_exec[2] = {nullptr, nullptr};
-    int cg_kernels[2] = {0, 0};
+    cudaGraphExec_t cg_exec[3] = {nullptr, nullptr, nullptr};
+    int cg_kernels[3] = {0, 0, 0};
 };
 
 namespace {
@@ -265,6 +268,8 @@ paris_status alloc_ctx(paris_ctx* c) {
         c->rh32 = m.get<float>(N);
         c->rh2 = m.get<float2>(N);
         c->rh16 = m.get<__half>(N);
+        if (c->lv.size() > 1)
+            for (int a = 0; a < 3; ++a) c->lv[1].b16[a] = m.get<__half>(c->lv[1].g.nface(a));
     }
     // block partials: up to 4 values per block of the largest reducing grid
     c->partials = m.get<double>(std::max(max_reduce_blocks(c->g0), rho0_matvec_blocks(c->g0)) * 4);
@@ -367,7 +372,15 @@ void setup_hierarchy(paris_ctx* c, const Coef<T>& c0) {
         T* out[3] = {Prec<T>::b(L, 0), Prec<T>::b(L, 1), Prec<T>::b(L, 2)};
         if constexpr (sizeof(T) == 4) {
             if (l == 1 && c->rho0) {
-                launch_coarse_beta_rho(F.g, c->rh32, c->grid.h, L.g, out, c->st);
+                // with the FP16 rho/2 of the V-cycle, level 1 gets FP16 coefficients too: the
+                // sums of four fine faces' 1/(rh_L + rh_R) times a power of two s16 that puts
+                // them below 2^14 (all between 2^14 rho_min/rho_max / 2 and 2^14)
+                float s16 = 1.f;
+                if (c->half_rho) {
+                    s16 = std::ldexp(1.0f, (int)std::floor(std::log2(4096.0 * c->rho_min)));
+                    L.scale16 = (float)(1.0 / (16.0 * c->grid.h * c->grid.h * (double)s16));
+                }
+                launch_coarse_beta_rho(F.g, c->rh32, c->grid.h, L.g, out, c->st, c->half_rho ? L.b16 : nullptr, s16);
                 continue;
             }
         }
@@ -478,6 +491,10 @@ void smooth(paris_ctx* c, int l, const Coef<T>& cf, const T* f, T* x, int sweeps
                                       o.omega, zero, c->st, a, b);
                         return;
                     }
+                    if (l == 1 && c->rho0 && c->half_rho) {  // level 1 of the mixed step: FP16 coefficients
+                        launch_rbgs_h(L.g, L.b16, L.scale16, f, x, color, o.omega, zero, c->st, a, b);
+                        return;
+                    }
                 }
                 launch_rbgs<T>(L.g, cf, Prec<T>::w(L), f, x, color, o.omega, zero, c->st, a, b);
             };
@@ -549,6 +566,11 @@ void vdown(paris_ctx* c, const Coef<T>& c0, const T* f0, T* x0, int l) {
         if (h16) {
             launch_restrict_residual_h(c->lv[l].g, c->b16_0, (float)(1.0 / (c->grid.h * c->grid.h)), f, x, C.g,
                                        C.fac, Prec<T>::f(C), c->st);
+            return;
+        }
+        if (l == 1 && c->rho0 && c->half_rho) {
+            const Level& L1 = c->lv[1];
+            launch_restrict_residual_h(L1.g, L1.b16, L1.scale16, f, x, C.g, C.fac, Prec<T>::f(C), c->st);
             return;
         }
     }
@@ -662,7 +684,8 @@ void coarse_part(paris_ctx* c, const Coef<T>& c0) {
 template <typename T>
 bool coarse_graph_launch(paris_ctx* c, const Coef<T>& c0) {
     const int nl = (int)c->lv.size();
-    const int slot = sizeof(T) == 8 ? 1 : 0;
+    // FP32 graphs with level 1 from the FP32 or from the FP16 coefficients, FP64
+    const int slot = sizeof(T) == 8 ? 1 : ((c->rho0 && c->half_rho) ? 2 : 0);
     if (nl < 3 || !c->cap_stream) return false;
     if (!c->cg_exec[slot]) {
         cudaStream_t user = c->st;
@@ -1255,7 +1278,10 @@ paris_status projection_step_impl(paris_ctx* c, const double* C, double rho1, do
     const double rlo = 0.5 * std::min(rho1, rho2), rhi = 0.5 * std::max(rho1, rho2);
     const bool use_rho0 = rho0_usable(c) && rlo >= 1e-30 && rhi <= 1e30;
     // FP16 rho/2 for the V-cycle (normal FP16 numbers with room to spare)
-    const bool use_half = use_rho0 && !force && c->opts.level0_half_rho && c->rh16 && rlo >= 1e-4 && rhi <= 6e4;
+    const bool use_half = use_rho0 && !force && c->opts.level0_half_rho && c->rh16 && rlo >= 1e-4 && rhi <= 6e4 &&
+                          rhi / rlo <= 1e7;
+    c->rho_min = 2.0 * rlo;
+    c->half_rho = use_half && c->opts.level0_tiles == 1;  // the set-up below writes level 1's FP16 copies
     // the set-up run ahead below is used by this step's solve only
     struct ReadyGuard {
         paris_ctx* c;
