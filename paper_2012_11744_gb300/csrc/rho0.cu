@@ -581,8 +581,13 @@ __device__ __forceinline__ void tile_update(const Geo& g, const RT* __restrict__
 #ifndef PARIS_TILE_MINB
 #define PARIS_TILE_MINB 1
 #endif
+// with rho/2 in FP16 the pass is closer to issue-bound: six blocks per SM
+// (40 registers) measured 2 % faster than the register-unbounded five
+#ifndef PARIS_TILE_MINB_H
+#define PARIS_TILE_MINB_H 6
+#endif
 template <bool ZERO, bool XZ, int V, typename RT = float>
-__global__ void __launch_bounds__(kBX* kVY, PARIS_TILE_MINB) rbgs_rho_tile_kernel(Geo g, const RT* __restrict__ rh, float h2,
+__global__ void __launch_bounds__(kBX* kVY, sizeof(RT) == 2 ? PARIS_TILE_MINB_H : PARIS_TILE_MINB) rbgs_rho_tile_kernel(Geo g, const RT* __restrict__ rh, float h2,
                                                                const float* __restrict__ f, float* x,
                                                                int color, float omega, int k0, int rev) {
     pdl_wait();
@@ -960,11 +965,17 @@ __device__ __forceinline__ void tile_apply(const Geo& g, const RT* __restrict__ 
 // block covers the two planes of one coarse plane (np = 2), and the two fine
 // rows of a coarse cell are the warps 2m, 2m+1 of the block, added through
 // shared memory.
+// blocks per SM the register allocation must allow: the product (with the
+// fused direction update) at 4 (64 registers, a few spilled) measured 3 %
+// faster than at 3; the restriction is fastest at 3 (80 registers)
 #ifndef PARIS_OP_MINB
-#define PARIS_OP_MINB 3
+#define PARIS_OP_MINB 4
+#endif
+#ifndef PARIS_OP_MINB_R
+#define PARIS_OP_MINB_R 3
 #endif
 template <bool RESTRICT, int V, bool XP = false, typename RT = float>
-__global__ void __launch_bounds__(kBX* kVY, PARIS_OP_MINB) op_rho_tile_kernel(Geo g, const RT* __restrict__ rh, float ih2,
+__global__ void __launch_bounds__(kBX* kVY, RESTRICT ? PARIS_OP_MINB_R : PARIS_OP_MINB) op_rho_tile_kernel(Geo g, const RT* __restrict__ rh, float ih2,
                                                              const float* __restrict__ x,
                                                              const float* __restrict__ f,
                                                              float* __restrict__ out, Geo cg,
