@@ -125,6 +125,11 @@ typedef struct {
                              [1e-4, 6e4]; the inner CG product, the refinement step and the
                              projection keep full precision, so this changes the V-cycle,
                              not the converged p (1) */
+    int coarse_tail;      /* the small levels of the V-cycle (two-pass red-black smoother,
+                             dense coarsest level): 1 the levels of at most 4096 cells, down
+                             to the coarsest and back, in one launch of one block; 0 one
+                             launch per step and level.  The same arithmetic in the same
+                             order in both: identical results (1) */
 } paris_opts;
 
 typedef struct {

@@ -39,7 +39,8 @@ class Opts(ct.Structure):
                 ("smoother", ct.c_int), ("coarse_max_cells", ct.c_int),
                 ("inner_tol", ct.c_double), ("fallback", ct.c_int), ("slab_planes", ct.c_int),
                 ("half_coefficients", ct.c_int), ("level0_density", ct.c_int),
-                ("level0_tiles", ct.c_int), ("level0_half_rho", ct.c_int)]
+                ("level0_tiles", ct.c_int), ("level0_half_rho", ct.c_int),
+                ("coarse_tail", ct.c_int)]
 
 
 class KernelProf(ct.Structure):

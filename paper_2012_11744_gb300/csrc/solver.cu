@@ -181,6 +181,7 @@ bool valid_opts(const paris_opts* o) {
     if (o->level0_density != 0 && o->level0_density != 1) return false;
     if (o->level0_tiles < 0 || o->level0_tiles > 2) return false;
     if (o->level0_half_rho != 0 && o->level0_half_rho != 1) return false;
+    if (o->coarse_tail != 0 && o->coarse_tail != 1) return false;
     return true;
 }
 
@@ -390,7 +391,7 @@ void setup_hierarchy(paris_ctx* c, const Coef<T>& c0) {
         }
     }
     // inverse diagonals: read by the FP64 smoothers, by Jacobi and by the
-    // single-block tail; the FP32 red-black sweeps of the other levels
+    // tail launch; the FP32 red-black sweeps of the other levels
     // recompute them from the coefficients they load (the same value)
     const int t = tail_start(c);
     if (sizeof(T) == 8 || c->opts.smoother == PARIS_SMOOTH_JACOBI) {
@@ -627,9 +628,13 @@ constexpr int64_t kTailCells = PARIS_TAIL_CELLS;
 // smoother, a dense coarsest level and at least one level above it).
 int tail_start(const paris_ctx* c) {
     const int nl = (int)c->lv.size();
-    if (!c->dense_coarse || c->opts.smoother != PARIS_SMOOTH_RBGS_2PASS || nl < 3 || c->dirichlet) return -1;
+    if (c->opts.coarse_tail == 0 || !c->dense_coarse || c->opts.smoother != PARIS_SMOOTH_RBGS_2PASS || nl < 3 ||
+        c->dirichlet)
+        return -1;
+    // level 1 with FP16 coefficients (the mixed step's FP16 rho/2) keeps its own kernels
+    const int lo = (c->rho0 && c->half_rho) ? 2 : 1;
     int t = nl - 1;
-    while (t - 1 >= 1 && c->lv[t - 1].g.ncell() <= kTailCells) --t;
+    while (t - 1 >= lo && c->lv[t - 1].g.ncell() <= kTailCells) --t;
     if (t >= nl - 1 || nl - t > kMaxTail) return -1;
     return t;
 }
@@ -1007,6 +1012,7 @@ void paris_default_opts(paris_opts* o) {
     o->level0_density = 1;
     o->level0_tiles = 1;
     o->level0_half_rho = 1;
+    o->coarse_tail = 1;
 }
 
 const char* paris_status_string(paris_status s) {
