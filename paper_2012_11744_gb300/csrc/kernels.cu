@@ -1143,7 +1143,10 @@ void launch_jacobi(const Geo& g, const Coef<T>& cf, const T* w, const T* f, cons
 
 // Coarse right-hand side: the average over the children of the fine residual
 // f - A x (restriction R = P^T / #children for the piecewise-constant P).
-template <typename T, typename TB, bool I32, bool SIG = false>
+// FULL: the 2 x 2 x 2 children of full coarsening, the loops unrolled so
+// that the loads of all eight stencils are in flight together (the sum keeps
+// its order).
+template <typename T, typename TB, bool I32, bool SIG = false, bool FULL = false>
 __global__ void restrict_residual_kernel(Geo fg, const TB* __restrict__ bx, const TB* __restrict__ by,
                                          const TB* __restrict__ bz, T scale, const T* __restrict__ f,
                                          const T* __restrict__ x, Geo cg, int fa0, int fa1,
@@ -1153,10 +1156,14 @@ __global__ void restrict_residual_kernel(Geo fg, const TB* __restrict__ bx, cons
     const int J = blockIdx.y * kTY + threadIdx.y;
     const int K = blockIdx.z;
     if (I >= cg.nx || J >= cg.ny) return;
+    if (FULL) fa0 = fa1 = fa2 = 2;
     T sum = T(0);
-    for (int dk = 0; dk < fa2; ++dk)
-        for (int dj = 0; dj < fa1; ++dj)
-            for (int di = 0; di < fa0; ++di) {
+#pragma unroll
+    for (int dk = 0; dk < (FULL ? 2 : fa2); ++dk)
+#pragma unroll
+        for (int dj = 0; dj < (FULL ? 2 : fa1); ++dj)
+#pragma unroll
+            for (int di = 0; di < (FULL ? 2 : fa0); ++di) {
                 const int i = I * fa0 + di, j = J * fa1 + dj, k = K * fa2 + dk;
                 Stencil<T> s;
                 int64_t c;
@@ -1180,8 +1187,11 @@ void launch_restrict_residual(const Geo& fine, const Coef<T>& cf, const T* f, co
                              const Geo& coarse, const int fac[3], T* fc, cudaStream_t st) {
     dim3 gr((coarse.nx + kTX - 1) / kTX, (coarse.ny + kTY - 1) / kTY, coarse.nz);
     // the diagonal excess as a template flag: the plain operator's kernels are unchanged
-    auto* k = fits_i32(fine) ? (cf.sig ? restrict_residual_kernel<T, T, true, true> : restrict_residual_kernel<T, T, true>)
-                             : (cf.sig ? restrict_residual_kernel<T, T, false, true> : restrict_residual_kernel<T, T, false>);
+    const bool full = fac[0] == 2 && fac[1] == 2 && fac[2] == 2;
+    auto* k = fits_i32(fine)
+                  ? (cf.sig ? restrict_residual_kernel<T, T, true, true>
+                            : (full ? restrict_residual_kernel<T, T, true, false, true> : restrict_residual_kernel<T, T, true>))
+                  : (cf.sig ? restrict_residual_kernel<T, T, false, true> : restrict_residual_kernel<T, T, false>);
     launch_pdl(k, gr, dim3(kTX, kTY), 0, st, fine, cf.bx, cf.by, cf.bz, cf.scale, f, x, coarse, fac[0], fac[1],
                fac[2], fc, cf.sig);
     count_launch();
@@ -1191,7 +1201,10 @@ void launch_restrict_residual_h(const Geo& fine, const __half* const b[3], float
                                 const float* x, const Geo& coarse, const int fac[3], float* fc,
                                 cudaStream_t st) {
     dim3 gr((coarse.nx + kTX - 1) / kTX, (coarse.ny + kTY - 1) / kTY, coarse.nz);
-    if (fits_i32(fine))
+    if (fits_i32(fine) && fac[0] == 2 && fac[1] == 2 && fac[2] == 2)
+        launch_pdl(restrict_residual_kernel<float, __half, true, false, true>, gr, dim3(kTX, kTY), 0, st, fine,
+                   b[0], b[1], b[2], scale, f, x, coarse, fac[0], fac[1], fac[2], fc, (const float*)nullptr);
+    else if (fits_i32(fine))
         launch_pdl(restrict_residual_kernel<float, __half, true>, gr, dim3(kTX, kTY), 0, st, fine, b[0], b[1],
             b[2], scale, f, x, coarse, fac[0], fac[1], fac[2], fc, (const float*)nullptr);
     else
