@@ -1408,7 +1408,8 @@ int64_t launch_matvec_dot(const Geo& g, const Coef<T>& cf, const T* d, T* q, dou
 #endif
 constexpr int kKU = PARIS_KU;
 
-template <typename T>
+// NOX: r only (d and x not touched), the same loops and partial sums
+template <typename T, bool NOX = false>
 __global__ void update_xr_kernel(int64_t n, const Scal* s, const T* __restrict__ d,
                                  const T* __restrict__ q, T* __restrict__ x, T* __restrict__ r,
                                  double* partials, int vec, FinSpec fin, int rev) {
@@ -1422,7 +1423,7 @@ __global__ void update_xr_kernel(int64_t n, const Scal* s, const T* __restrict__
     for (int u = 0; u < U; ++u) l2[u] = li[u] = T(0);
     unsigned nf = 0;  // an integer count: no FP64 add per element
     auto one = [&](T dv, T qv, T& xv, T& rv, T& l2u, T& liu) {
-        xv = fma(alpha, dv, xv);
+        if (!NOX) xv = fma(alpha, dv, xv);
         rv = fma(-alpha, qv, rv);
         l2u = fma(rv, rv, l2u);
         liu = fmax(liu, fabs(rv));
@@ -1437,9 +1438,9 @@ __global__ void update_xr_kernel(int64_t n, const Scal* s, const T* __restrict__
         VT dv[U], qv[U], xv[U], rv[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            dv[u] = reinterpret_cast<const VT*>(d)[at(i + u * stride)];
+            if (!NOX) dv[u] = reinterpret_cast<const VT*>(d)[at(i + u * stride)];
             qv[u] = reinterpret_cast<const VT*>(q)[at(i + u * stride)];
-            xv[u] = reinterpret_cast<VT*>(x)[at(i + u * stride)];
+            if (!NOX) xv[u] = reinterpret_cast<VT*>(x)[at(i + u * stride)];
             rv[u] = reinterpret_cast<VT*>(r)[at(i + u * stride)];
         }
 #pragma unroll
@@ -1450,14 +1451,17 @@ __global__ void update_xr_kernel(int64_t n, const Scal* s, const T* __restrict__
             T* re = reinterpret_cast<T*>(&rv[u]);
 #pragma unroll
             for (int w = 0; w < W; ++w) one(de[w], qe[w], xe[w], re[w], l2[u], li[u]);
-            reinterpret_cast<VT*>(x)[at(i + u * stride)] = xv[u];
+            if (!NOX) reinterpret_cast<VT*>(x)[at(i + u * stride)] = xv[u];
             reinterpret_cast<VT*>(r)[at(i + u * stride)] = rv[u];
         }
     }
     for (; i < nv; i += stride) {
-        const VT dv = reinterpret_cast<const VT*>(d)[at(i)];
+        VT dv, xv;
+        if (!NOX) {
+            dv = reinterpret_cast<const VT*>(d)[at(i)];
+            xv = reinterpret_cast<VT*>(x)[at(i)];
+        }
         const VT qv = reinterpret_cast<const VT*>(q)[at(i)];
-        VT xv = reinterpret_cast<VT*>(x)[at(i)];
         VT rv = reinterpret_cast<VT*>(r)[at(i)];
         const T* de = reinterpret_cast<const T*>(&dv);
         const T* qe = reinterpret_cast<const T*>(&qv);
@@ -1465,13 +1469,13 @@ __global__ void update_xr_kernel(int64_t n, const Scal* s, const T* __restrict__
         T* re = reinterpret_cast<T*>(&rv);
 #pragma unroll
         for (int w = 0; w < W; ++w) one(de[w], qe[w], xe[w], re[w], l2[0], li[0]);
-        reinterpret_cast<VT*>(x)[at(i)] = xv;
+        if (!NOX) reinterpret_cast<VT*>(x)[at(i)] = xv;
         reinterpret_cast<VT*>(r)[at(i)] = rv;
     }
     PARIS_TAIL_FOR(c, nv * W, n) {
-        T xv = x[c], rv = r[c];
-        one(d[c], q[c], xv, rv, l2[0], li[0]);
-        x[c] = xv;
+        T xv = NOX ? T(0) : x[c], rv = r[c];
+        one(NOX ? T(0) : d[c], q[c], xv, rv, l2[0], li[0]);
+        if (!NOX) x[c] = xv;
         r[c] = rv;
     }
     T l2s = l2[0], lis = li[0];
@@ -1492,6 +1496,16 @@ int64_t launch_update_xr(int64_t n, const Scal* s, const T* d, const T* q, T* x,
     int nb = elementwise_blocks(n);
     launch_pdl(update_xr_kernel<T>, dim3(nb), dim3(kRedThreads), 0, st, n, s, d, q, x, r, partials,
                aligned16(d, q, x, r) ? 1 : 0, fin, rev ? 1 : 0);
+    count_launch();
+    return nb;
+}
+
+template <typename T>
+int64_t launch_update_r(int64_t n, const Scal* s, const T* q, T* r, double* partials, cudaStream_t st, FinSpec fin,
+                        bool rev) {
+    int nb = elementwise_blocks(n);
+    launch_pdl(update_xr_kernel<T, true>, dim3(nb), dim3(kRedThreads), 0, st, n, s, (const T*)nullptr, q, (T*)nullptr,
+               r, partials, aligned16(q, r) ? 1 : 0, fin, rev ? 1 : 0);
     count_launch();
     return nb;
 }
@@ -1784,6 +1798,8 @@ cudaError_t stream_rates(const float* a, const float* b, const float* c, float* 
                                           cudaStream_t, FinSpec);                              \
     template int64_t launch_update_xr<T>(int64_t, const Scal*, const T*, const T*, T*, T*,     \
                                          double*, cudaStream_t, FinSpec, bool);                \
+    template int64_t launch_update_r<T>(int64_t, const Scal*, const T*, T*, double*,           \
+                                        cudaStream_t, FinSpec, bool);                          \
     template int64_t launch_dot2<T>(int64_t, const T*, const T*, const T*, double*,            \
                                     cudaStream_t, FinSpec, bool);                              \
     template void launch_xpby<T>(int64_t, const Scal*, const T*, T*, cudaStream_t);

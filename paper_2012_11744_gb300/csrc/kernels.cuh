@@ -463,10 +463,14 @@ int64_t launch_matvec_rho(const Geo& g, const float* rh, double h, const float* 
                           double* partials, cudaStream_t st, FinSpec fin = no_fin(), bool tiles = true, bool rev = false);
 // the plane-tile product with the flexible CG's direction update fused in:
 // dnew = z + beta d (beta from s) and q = A dnew, d . q partials as above
-// (dnew must not alias z or d); only where rho0_product_fuses
+// (dnew must not alias z or d); only where rho0_product_fuses.  e (may be
+// null): the previous iteration's solution update e += alpha d rides along
+// (alpha from s, read before this launch's finalize replaces it; emem false:
+// e taken as 0, not read)
 bool rho0_product_fuses(const Geo& g, bool tiles);
 int64_t launch_matvec_rho_xpby(const Geo& g, const float* rh, double h, const float* z, const float* d, float* dnew,
-                               float* q, const Scal* s, double* partials, cudaStream_t st, FinSpec fin, bool rev = false);
+                               float* q, const Scal* s, double* partials, cudaStream_t st, FinSpec fin, bool rev = false,
+                               float* e = nullptr, bool emem = true);
 int64_t rho0_matvec_blocks(const Geo& g);
 // coarse f = mean over the 2x2x2 children of (f - A x); coarse = every axis halved
 void launch_restrict_rho(const Geo& g, const float* rh, double h, const float* f, const float* x,
@@ -483,9 +487,12 @@ void launch_coarse_beta_rho(const Geo& fine, const float* rh, double h, const Ge
 // FP64 refinement step of the mixed form on the finest level, A d in
 // double-float from the rho/2 pairs rh2: x += 2^-a e, r_new = r_old - A 2^-a e,
 // r32 = 2^b r_new (2^a: s->scale, 2^b from s->rinf), norms (FIN_REFINE fused);
-// e and r32 in the colour-split layout
+// e and r32 in the colour-split layout.  emem false: e taken as 0 (not read);
+// dpend (may be null): the inner solve's last update e += alpha dpend (alpha
+// from s) applied first
 void launch_refine_rho(const Geo& g, const float2* rh2, double h, const float* e, const double* r_old,
-                       double* r_new, double* x, float* r32, Scal* s, double* partials, cudaStream_t st, bool rev = false);
+                       double* r_new, double* x, float* r32, Scal* s, double* partials, cudaStream_t st, bool rev = false,
+                       bool emem = true, const float* dpend = nullptr);
 
 // ------------------------------------------------ single-launch V-cycle tail ---
 // One level of the tail: coefficients (scaled by `scale`), inverse diagonal
@@ -530,6 +537,10 @@ int64_t launch_matvec_dot(const Geo& g, const Coef<T>& cf, const T* d, T* q, dou
 template <typename T>
 int64_t launch_update_xr(int64_t n, const Scal* s, const T* d, const T* q, T* x, T* r,
                          double* partials, cudaStream_t st, FinSpec fin = no_fin(), bool rev = false);
+// r -= alpha q and the partials of launch_update_xr (x's update left to the caller)
+template <typename T>
+int64_t launch_update_r(int64_t n, const Scal* s, const T* q, T* r, double* partials, cudaStream_t st,
+                        FinSpec fin = no_fin(), bool rev = false);
 // partials (a . b, a . c)  (c may be null -> 0); fin: fused second stage
 template <typename T>
 int64_t launch_dot2(int64_t n, const T* a, const T* b, const T* c, double* partials,

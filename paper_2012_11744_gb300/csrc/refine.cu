@@ -82,7 +82,8 @@ __global__ void __launch_bounds__(kTX* kTY) refine_rho_kernel(Geo g, const float
                                                             const float* __restrict__ e,
                                                             const double* r_old, double* r_new,
                                                             double* __restrict__ x, float* __restrict__ r32,
-                                                            const Scal* s, double* partials, FinSpec fin, int rev) {
+                                                            const Scal* s, double* partials, FinSpec fin, int rev,
+                                                            int emem, const float* __restrict__ dpend) {
     pdl_wait();
     const int zb = rev ? (int)(gridDim.z - 1 - blockIdx.z) : (int)blockIdx.z;  // rev: descending plane chunks
     const int i = blockIdx.x * kTX + threadIdx.x;
@@ -92,6 +93,14 @@ __global__ void __launch_bounds__(kTX* kTY) refine_rho_kernel(Geo g, const float
     unsigned nf = 0;
     if (i < g.nx && j < g.ny) {
         const int sa = (int)s->scale_exp;  // r32 of this inner solve = 2^sa r
+        // the inner solution at entry p: e (0 when not yet written), plus the
+        // pending last update alpha dpend (the same FMA the inner loop's update
+        // would have made)
+        const float ap = dpend ? (float)s->alpha : 0.f;
+        auto ev = [&](int p) {
+            const float v = emem ? __ldg(e + p) : 0.f;
+            return dpend ? __fmaf_rn(ap, __ldg(dpend + p), v) : v;
+        };
         const int sb = -exponent_of(s->rinf);  // next r32 = 2^sb r (the scale of FIN_SCALE)
         const int nx = g.nx, ny = g.ny, nz = g.nz, pl = nx * ny;
         // neighbour offsets along x and y (periodic wrap; a wall side points at
@@ -118,17 +127,17 @@ __global__ void __launch_bounds__(kTX* kTY) refine_rho_kernel(Geo g, const float
             const int so = rb + (odd ? 0 : hx);                // other colour's half of this row
             const int sn = so + tx;                            // y and z neighbours: same entry, other half
             const float2 rc = __ldg(rh2 + c);
-            const float ec = __ldg(e + sc);
+            const float ec = ev(sc);
             // sum over the faces of beta_f (e_c - e_nb) as S + E: S the running
             // FP32 sum of the leading products (two-sum), E every rounding
             // error and low part (faces x-, x+, y-, y+, z-, z+)
             float S = 0.f, E = 0.f;
-            if (!wxm) face_term(rc, __ldg(rh2 + c + oxm), ec, __ldg(e + so + txm), S, E);
-            if (!wxp) face_term(rc, __ldg(rh2 + c + oxp), ec, __ldg(e + so + txp), S, E);
-            if (!wym) face_term(rc, __ldg(rh2 + c + oym), ec, __ldg(e + sn + oym), S, E);
-            if (!wyp) face_term(rc, __ldg(rh2 + c + oyp), ec, __ldg(e + sn + oyp), S, E);
-            if (!wzm) face_term(rc, __ldg(rh2 + c + ozm), ec, __ldg(e + sn + ozm), S, E);
-            if (!wzp) face_term(rc, __ldg(rh2 + c + ozp), ec, __ldg(e + sn + ozp), S, E);
+            if (!wxm) face_term(rc, __ldg(rh2 + c + oxm), ec, ev(so + txm), S, E);
+            if (!wxp) face_term(rc, __ldg(rh2 + c + oxp), ec, ev(so + txp), S, E);
+            if (!wym) face_term(rc, __ldg(rh2 + c + oym), ec, ev(sn + oym), S, E);
+            if (!wyp) face_term(rc, __ldg(rh2 + c + oyp), ec, ev(sn + oyp), S, E);
+            if (!wzm) face_term(rc, __ldg(rh2 + c + ozm), ec, ev(sn + ozm), S, E);
+            if (!wzp) face_term(rc, __ldg(rh2 + c + ozp), ec, ev(sn + ozp), S, E);
             // A d = 2^-sa (S + E) ih2, the product as a pair, the power of two
             // applied exactly on the FP64 side
             const float qh = __fmul_rn(S, ih2_hi);
@@ -153,14 +162,15 @@ __global__ void __launch_bounds__(kTX* kTY) refine_rho_kernel(Geo g, const float
 }
 
 void launch_refine_rho(const Geo& g, const float2* rh2, double h, const float* e, const double* r_old,
-                       double* r_new, double* x, float* r32, Scal* s, double* partials, cudaStream_t st, bool rev) {
+                       double* r_new, double* x, float* r32, Scal* s, double* partials, cudaStream_t st, bool rev,
+                       bool emem, const float* dpend) {
     // 1/h^2 as an FP32 pair
     const double ih2d = 1.0 / (h * h);
     const float hi = (float)ih2d;
     const float lo = (float)(ih2d - (double)hi);
     dim3 gr((g.nx + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, (g.nz + kZ - 1) / kZ);
     launch_pdl(refine_rho_kernel, gr, dim3(kTX, kTY), 0, st, g, rh2, hi, lo, e, r_old, r_new, x, r32, s,
-        partials, FinSpec{s, 3, 2, FIN_REFINE, 0.0}, rev ? 1 : 0);
+        partials, FinSpec{s, 3, 2, FIN_REFINE, 0.0}, rev ? 1 : 0, emem ? 1 : 0, dpend);
     count_launch();
 }
 

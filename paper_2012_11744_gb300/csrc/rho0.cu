@@ -982,7 +982,8 @@ __global__ void __launch_bounds__(kBX* kVY, RESTRICT ? PARIS_OP_MINB_R : PARIS_O
                                                              double* partials, int np, FinSpec fin,
                                                              const float* __restrict__ z = nullptr,
                                                              const Scal* s = nullptr,
-                                                             float* __restrict__ xnew = nullptr, int rev = 0) {
+                                                             float* __restrict__ xnew = nullptr, int rev = 0,
+                                                             float* __restrict__ eacc = nullptr, int emem = 0) {
     __shared__ float sh[kVY][kBX * V];
     pdl_wait();
     // rev: the plane groups in descending order (starting where a previous
@@ -990,6 +991,10 @@ __global__ void __launch_bounds__(kBX* kVY, RESTRICT ? PARIS_OP_MINB_R : PARIS_O
     // plane group, so the result does not depend on the order
     const int zb = rev ? (int)(gridDim.z - 1 - blockIdx.z) : (int)blockIdx.z;
     const float beta = XP ? (float)s->beta : 0.f;  // XP: x = z + beta x, written to xnew
+    // XP with eacc: the inner solution's update e += alpha x of the previous
+    // iteration (alpha read before this launch's own finalize replaces it;
+    // emem = 0: e not yet written, taken as +0)
+    const float alpha_p = (XP && eacc) ? (float)s->alpha : 0.f;
     const int ty = threadIdx.y, lane = threadIdx.x;
     const int j = blockIdx.y * kVY + ty;
     const bool row_ok = j < g.ny;
@@ -1005,6 +1010,27 @@ __global__ void __launch_bounds__(kBX* kVY, RESTRICT ? PARIS_OP_MINB_R : PARIS_O
     for (int p = 0; p < np; ++p) {
         const int k = zb * np + p;
         if (k >= g.nz) break;  // uniform per block
+        if (XP && eacc && act) {
+            // e += alpha_p x on this tile row (both colours, in memory order)
+            const int rb = (k * g.ny + jc) * g.nx;
+            float o0[V], o1[V], e0[V], e1[V];
+            ldgv<V>(o0, x + rb + t0);
+            ldgv<V>(o1, x + rb + hx + t0);
+            if (emem) {
+                ldgv<V>(e0, eacc + rb + t0);
+                ldgv<V>(e1, eacc + rb + hx + t0);
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) e0[v] = e1[v] = 0.f;
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                e0[v] = fmaf(alpha_p, o0[v], e0[v]);
+                e1[v] = fmaf(alpha_p, o1[v], e1[v]);
+            }
+            stv<V>(eacc + rb + t0, e0);
+            stv<V>(eacc + rb + hx + t0, e1);
+        }
         float a[2 * V], X[2 * V], F[2 * V];
         if (((jc + k) & 1) == 0)
             tile_apply<RESTRICT, V, 0, XP, RT>(g, rh, x, f, jc, k, t0, lane, a, X, F, z, beta);
@@ -1077,12 +1103,13 @@ int64_t rho0_matvec_blocks(const Geo& g) {
 bool rho0_product_fuses(const Geo& g, bool tiles) { return tiles && kTileOpV > 0 && (g.nx / 2) % kTileOpV == 0; }
 
 int64_t launch_matvec_rho_xpby(const Geo& g, const float* rh, double h, const float* z, const float* d, float* dnew,
-                               float* q, const Scal* s, double* partials, cudaStream_t st, FinSpec fin, bool rev) {
+                               float* q, const Scal* s, double* partials, cudaStream_t st, FinSpec fin, bool rev,
+                               float* e, bool emem) {
     constexpr int V = kTileOpV > 0 ? kTileOpV : 2;
     const int hx = g.nx / 2;
     dim3 gr((hx / V + kBX - 1) / kBX, (g.ny + kVY - 1) / kVY, (g.nz + kTileOpPlanes - 1) / kTileOpPlanes);
     launch_pdl(op_rho_tile_kernel<false, V, true>, gr, dim3(kBX, kVY), 0, st, g, rh, (float)(1.0 / (h * h)), d,
-               (const float*)nullptr, q, g, partials, kTileOpPlanes, fin, z, s, dnew, rev ? 1 : 0);
+               (const float*)nullptr, q, g, partials, kTileOpPlanes, fin, z, s, dnew, rev ? 1 : 0, e, emem ? 1 : 0);
     count_launch();
     return (int64_t)gr.x * gr.y * gr.z;
 }
@@ -1095,7 +1122,7 @@ int64_t launch_matvec_rho(const Geo& g, const float* rh, double h, const float* 
         dim3 gr((hx / V + kBX - 1) / kBX, (g.ny + kVY - 1) / kVY, (g.nz + kTileOpPlanes - 1) / kTileOpPlanes);
         launch_pdl(op_rho_tile_kernel<false, V>, gr, dim3(kBX, kVY), 0, st, g, rh, (float)(1.0 / (h * h)), d,
             (const float*)nullptr, q, g, partials, kTileOpPlanes, fin, (const float*)nullptr, (const Scal*)nullptr,
-            (float*)nullptr, rev ? 1 : 0);
+            (float*)nullptr, rev ? 1 : 0, (float*)nullptr, 0);
         count_launch();
         return (int64_t)gr.x * gr.y * gr.z;
     }
@@ -1116,11 +1143,11 @@ void launch_restrict_rho(const Geo& g, const float* rh, double h, const float* f
         if (rh16)  // the V-cycle's restriction from FP16 rho/2
             launch_pdl(op_rho_tile_kernel<true, V, false, __half>, gr, dim3(kBX, kVY), 0, st, g, rh16,
                        (float)(1.0 / (h * h)), x, f, fc, cg, (double*)nullptr, 2, no_fin(), (const float*)nullptr,
-                       (const Scal*)nullptr, (float*)nullptr, rev ? 1 : 0);
+                       (const Scal*)nullptr, (float*)nullptr, rev ? 1 : 0, (float*)nullptr, 0);
         else
             launch_pdl(op_rho_tile_kernel<true, V>, gr, dim3(kBX, kVY), 0, st, g, rh, (float)(1.0 / (h * h)), x, f,
                 fc, cg, (double*)nullptr, 2, no_fin(), (const float*)nullptr, (const Scal*)nullptr, (float*)nullptr,
-                rev ? 1 : 0);
+                rev ? 1 : 0, (float*)nullptr, 0);
         count_launch();
         return;
     }

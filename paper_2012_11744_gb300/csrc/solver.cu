@@ -917,7 +917,14 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
         double need2 = (c->opts.tol * c->opts.tol * h.bnorm2) / std::max(h.rr, 1e-300) * 1e-2;
         double it2 = c->opts.inner_tol * c->opts.inner_tol;
         const double target = rr32 * std::max(it2, std::min(need2, 1.0));
-        {
+        // with the finest level from rho/2 the direction update d = z + beta d
+        // rides in the next product (fuse_next: beta is pending), and so does
+        // the previous iteration's update e += alpha d (e_pend), the last one
+        // in the refinement step; e is written first by the second product
+        // (e_mem), so it needs no clearing
+        const bool fuse = c->rho0 && c->d32b && rho0_product_fuses(c->g0, c->opts.level0_tiles != 0);
+        bool e_mem = !fuse, e_pend = false;
+        if (!fuse) {
             ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
             CK(cudaMemsetAsync(c->e32, 0, sizeof(float) * N, c->st));
         }
@@ -928,15 +935,16 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
                                FinSpec{c->scal, 2, 0, FIN_RHO_INIT, 0.0}, c->rho0 && take_dir(c));
             std::swap(c->d32, c->z32);  // first direction d = z: exchange the buffers
         }
-        // with the finest level from rho/2 the direction update d = z + beta d
-        // rides in the next product (fuse_next: beta is pending)
-        const bool fuse = c->rho0 && c->d32b && rho0_product_fuses(c->g0, c->opts.level0_tiles != 0);
         bool fuse_next = false;
         for (int j = 0; j < 50 && out.iters < max_iter; ++j) {
             if (fuse_next) {
-                ProfScope ps(c, PARIS_K_MATVEC0, 5.0 * N * 4);
+                // z, d, rho/2 and e (after the first) read; d, q and e written
+                ProfScope ps(c, PARIS_K_MATVEC0, (5.0 + (e_pend ? (e_mem ? 3.0 : 2.0) : 0.0)) * N * 4);
                 launch_matvec_rho_xpby(c->g0, c->rh32, c->grid.h, c->z32, c->d32, c->d32b, c->q32, c->scal,
-                                       c->partials, c->st, FinSpec{c->scal, 1, 0, FIN_ALPHA, 0.0}, take_dir(c));
+                                       c->partials, c->st, FinSpec{c->scal, 1, 0, FIN_ALPHA, 0.0}, take_dir(c),
+                                       e_pend ? c->e32 : nullptr, e_mem);
+                if (e_pend) e_mem = true;
+                e_pend = false;
                 std::swap(c->d32, c->d32b);
             } else if (c->rho0) {
                 ProfScope ps(c, PARIS_K_MATVEC0, 3.0 * N * 4);
@@ -949,8 +957,14 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
             }
             {
                 ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
-                launch_update_xr<float>(N, c->scal, c->d32, c->q32, c->e32, c->r32, c->partials, c->st,
-                                        FinSpec{c->scal, 3, 2, FIN_STORE, 0.0}, c->rho0 && take_dir(c));
+                if (fuse) {
+                    launch_update_r<float>(N, c->scal, c->q32, c->r32, c->partials, c->st,
+                                           FinSpec{c->scal, 3, 2, FIN_STORE, 0.0}, take_dir(c));
+                    e_pend = true;  // e += alpha d, d = c->d32
+                } else {
+                    launch_update_xr<float>(N, c->scal, c->d32, c->q32, c->e32, c->r32, c->partials, c->st,
+                                            FinSpec{c->scal, 3, 2, FIN_STORE, 0.0}, c->rho0 && take_dir(c));
+                }
                 s = read_scal(c);
             }
             ++out.iters;
@@ -972,7 +986,7 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
         if (refine) {
             ProfScope ps(c, PARIS_K_RESID64, 48.0 * N);
             launch_refine_rho(c->g0, c->rh2, c->grid.h, c->e32, c->r, c->r, x, c->r32, c->scal, c->partials,
-                              c->st, take_dir(c));
+                              c->st, take_dir(c), e_mem, e_pend ? c->d32 : nullptr);
         } else {
             ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
             launch_accumulate(N, c->scal, c->e32, x, c->st);
