@@ -41,6 +41,8 @@
 // restriction a coarse level with every axis halved.
 #include "kernels.cuh"
 
+#include <type_traits>
+
 namespace paris {
 
 namespace {
@@ -576,6 +578,139 @@ __device__ __forceinline__ void tile_update(const Geo& g, const RT* __restrict__
     if (act) stv<V>(x + su, xn);
 }
 
+// The regular colour pass (x read) on two consecutive planes k and k+1 of
+// row j: plane k updates member M of its pairs, plane k+1 member 1 - M.  The
+// rows the two share are loaded once: rho/2 of row j in both planes (each
+// plane's z-neighbour row is the other's centre row) and x of the other
+// colour in both planes (plane k's x above is plane k+1's other colour, and
+// plane k+1's x below is plane k's).  Each cell's update is that of
+// tile_update, faces in the same order.
+template <int V, int M, typename RT>
+__device__ __forceinline__ void tile_update2(const Geo& g, const RT* __restrict__ rh,
+                                             const float* __restrict__ f, float* x, float h2, float omega,
+                                             int col, int j, int k, int t0, int lane, bool act) {
+    const int nx = g.nx, hx = nx / 2, pl = nx * g.ny;
+    const int rb = k * pl + j * nx;
+    const int su = rb + (col ? hx : 0) + t0;  // updated colour of plane k (plane k+1: + pl)
+    const int so = rb + (col ? 0 : hx) + t0;  // the other colour of plane k (plane k+1: + pl)
+    const int o = rb + 2 * t0;                // rho/2 of cells 2t0 .. 2t0+2V-1 of plane k (k+1: + pl)
+    const int ym = j > 0 ? -nx : (g.ny - 1) * nx, yp = j < g.ny - 1 ? nx : -(g.ny - 1) * nx;
+    const int zm = k > 0 ? -pl : (g.nz - 1) * pl;                      // below plane k
+    const int zp1 = k + 1 < g.nz - 1 ? pl : -(g.nz - 1) * pl;          // above plane k+1
+    float R0[2 * V], R1[2 * V], Q[2 * V];
+    ldgv<2 * V>(R0, rh + o);
+    ldgv<2 * V>(R1, rh + o + pl);
+    float F0[V], F1[V];
+    ldgv<V>(F0, f + su);
+    ldgv<V>(F1, f + su + pl);
+    float rym0[V], ryp0[V], rzm0[V], rym1[V], ryp1[V], rzp1[V];
+    ldgv<2 * V>(Q, rh + o + ym);
+#pragma unroll
+    for (int v = 0; v < V; ++v) rym0[v] = Q[2 * v + M];
+    ldgv<2 * V>(Q, rh + o + yp);
+#pragma unroll
+    for (int v = 0; v < V; ++v) ryp0[v] = Q[2 * v + M];
+    ldgv<2 * V>(Q, rh + o + zm);
+#pragma unroll
+    for (int v = 0; v < V; ++v) rzm0[v] = Q[2 * v + M];
+    ldgv<2 * V>(Q, rh + o + pl + ym);
+#pragma unroll
+    for (int v = 0; v < V; ++v) rym1[v] = Q[2 * v + 1 - M];
+    ldgv<2 * V>(Q, rh + o + pl + yp);
+#pragma unroll
+    for (int v = 0; v < V; ++v) ryp1[v] = Q[2 * v + 1 - M];
+    ldgv<2 * V>(Q, rh + o + pl + zp1);
+#pragma unroll
+    for (int v = 0; v < V; ++v) rzp1[v] = Q[2 * v + 1 - M];
+    // edge neighbours (plane k: member M's side; plane k+1: the other side)
+    const int teL = t0 > 0 ? -1 : hx - 1, teR = t0 + V < hx ? V : V - hx;
+    const int reL = t0 > 0 ? -1 : nx - 1, reR = t0 + V < hx ? 2 * V : 2 * V - nx;
+    const float re0 = ldr(rh + o + (M == 0 ? reL : reR));
+    const float re1 = ldr(rh + o + pl + (M == 0 ? reR : reL));
+    float xu0[V], xo0[V], xym0[V], xyp0[V], xzm0[V];
+    float xu1[V], xo1[V], xym1[V], xyp1[V], xzp1[V];
+    ldv<V>(xu0, x + su);
+    ldv<V>(xo0, x + so);
+    ldv<V>(xym0, x + so + ym);
+    ldv<V>(xyp0, x + so + yp);
+    ldv<V>(xzm0, x + so + zm);
+    ldv<V>(xu1, x + su + pl);
+    ldv<V>(xo1, x + so + pl);
+    ldv<V>(xym1, x + so + pl + ym);
+    ldv<V>(xyp1, x + so + pl + yp);
+    ldv<V>(xzp1, x + so + pl + zp1);
+    const float xe0 = x[so + (M == 0 ? teL : teR)];
+    const float xe1 = x[so + pl + (M == 0 ? teR : teL)];
+    const bool ym_wall = g.wy && j == 0, yp_wall = g.wy && j == g.ny - 1;
+    const bool zm_wall = g.wz && k == 0, zp_wall = g.wz && k + 1 == g.nz - 1;
+    // one plane's update: member MM, its rows and neighbours; rzm / xzm the
+    // plane below, rzp / xzp the plane above (the other plane's rows where
+    // they are shared)
+    auto update = [&](auto mm, const float (&R)[2 * V], const float (&F)[V], const float (&rym)[V],
+                      const float (&ryp)[V], const float (&rzm)[V], const float (&rzp)[V], const float (&xu)[V],
+                      const float (&xo)[V], const float (&xym)[V], const float (&xyp)[V], const float (&xzm)[V],
+                      const float (&xzp)[V], float xe, float re, bool zmw, bool zpw, float (&xn)[V]) {
+        constexpr int MM = decltype(mm)::value;
+        float vo[V], ro[V];
+        if (MM == 0) {
+            const float px = __shfl_up_sync(kAll, xo[V - 1], 1), pr = __shfl_up_sync(kAll, R[2 * V - 1], 1);
+            const bool from_lane = lane > 0 && t0 > 0;
+            vo[0] = from_lane ? px : xe;
+            ro[0] = from_lane ? pr : re;
+#pragma unroll
+            for (int v = 1; v < V; ++v) {
+                vo[v] = xo[v - 1];
+                ro[v] = R[2 * v - 1];
+            }
+        } else {
+            const float nxv = __shfl_down_sync(kAll, xo[0], 1), nr = __shfl_down_sync(kAll, R[0], 1);
+            const bool from_lane = lane < 31 && t0 + V < hx;
+#pragma unroll
+            for (int v = 0; v < V - 1; ++v) {
+                vo[v] = xo[v + 1];
+                ro[v] = R[2 * v + 2];
+            }
+            vo[V - 1] = from_lane ? nxv : xe;
+            ro[V - 1] = from_lane ? nr : re;
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const bool xwall = g.wx && (MM == 0 ? (t0 + v == 0) : (t0 + v == hx - 1));
+            const float ru = R[2 * v + MM], rin = R[2 * v + 1 - MM];
+            const float b0 = xwall ? 0.f : bface(ru, ro[v]);
+            const float b1 = bface(ru, rin);
+            const float b2 = ym_wall ? 0.f : bface(ru, rym[v]);
+            const float b3 = yp_wall ? 0.f : bface(ru, ryp[v]);
+            const float b4 = zmw ? 0.f : bface(ru, rzm[v]);
+            const float b5 = zpw ? 0.f : bface(ru, rzp[v]);
+            const float w = rcp_fast(((b0 + b1) + (b2 + b3)) + (b4 + b5));
+            const float fc = F[v] * h2;
+            float acc = fmaf(b0, vo[v], fc);
+            acc = fmaf(b1, xo[v], acc);
+            acc = fmaf(b2, xym[v], acc);
+            acc = fmaf(b3, xyp[v], acc);
+            acc = fmaf(b4, xzm[v], acc);
+            acc = fmaf(b5, xzp[v], acc);
+            xn[v] = fmaf(omega, fmaf(w, acc, -xu[v]), xu[v]);
+        }
+    };
+    // plane k: above it plane k+1's row (rho/2 of member M, x of the other colour of plane k+1)
+    float rzp0[V], rzm1[V], xn0[V], xn1[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        rzp0[v] = R1[2 * v + M];
+        rzm1[v] = R0[2 * v + 1 - M];
+    }
+    update(std::integral_constant<int, M>{}, R0, F0, rym0, ryp0, rzm0, rzp0, xu0, xo0, xym0, xyp0, xzm0, xo1, xe0,
+           re0, zm_wall, false, xn0);
+    update(std::integral_constant<int, 1 - M>{}, R1, F1, rym1, ryp1, rzm1, rzp1, xu1, xo1, xym1, xyp1, xo0, xzp1,
+           xe1, re1, false, zp_wall, xn1);
+    if (act) {
+        stv<V>(x + su, xn0);
+        stv<V>(x + su + pl, xn1);
+    }
+}
+
 }  // namespace
 
 #ifndef PARIS_TILE_MINB
@@ -585,6 +720,13 @@ __device__ __forceinline__ void tile_update(const Geo& g, const RT* __restrict__
 // (40 registers) measured 2 % faster than the register-unbounded five
 #ifndef PARIS_TILE_MINB_H
 #define PARIS_TILE_MINB_H 6
+#endif
+// the regular pass of the V-cycle on two planes per block (1: one plane per block)
+#ifndef PARIS_TILE_NP
+#define PARIS_TILE_NP 2
+#endif
+#ifndef PARIS_TILE2_MINB
+#define PARIS_TILE2_MINB 4
 #endif
 template <bool ZERO, bool XZ, int V, typename RT = float>
 __global__ void __launch_bounds__(kBX* kVY, sizeof(RT) == 2 ? PARIS_TILE_MINB_H : PARIS_TILE_MINB) rbgs_rho_tile_kernel(Geo g, const RT* __restrict__ rh, float h2,
@@ -608,6 +750,29 @@ __global__ void __launch_bounds__(kBX* kVY, sizeof(RT) == 2 ? PARIS_TILE_MINB_H 
         tile_update<ZERO, XZ, V, 0, RT>(g, rh, f, x, h2, omega, color, j, k, t0, lane, act);
     else
         tile_update<ZERO, XZ, V, 1, RT>(g, rh, f, x, h2, omega, color, j, k, t0, lane, act);
+}
+
+// The regular pass over pairs of planes (tile_update2): block z covers planes
+// k0 + 2 zb and k0 + 2 zb + 1 (rev: zb descending).
+template <int V, typename RT>
+__global__ void __launch_bounds__(kBX* kVY, PARIS_TILE2_MINB) rbgs_rho_tile2_kernel(Geo g, const RT* __restrict__ rh,
+                                                                                  float h2, const float* __restrict__ f,
+                                                                                  float* x, int color, float omega,
+                                                                                  int k0, int rev) {
+    pdl_wait();
+    const int j = blockIdx.y * kVY + threadIdx.y;
+    if (j >= g.ny) return;  // uniform per warp
+    const int zb = rev ? (int)(gridDim.z - 1 - blockIdx.z) : (int)blockIdx.z;
+    const int k = k0 + 2 * zb;
+    const int lane = threadIdx.x & 31;
+    const int hx = g.nx / 2;
+    const int tv = (blockIdx.x * kBX + threadIdx.x) * V;
+    const bool act = tv < hx;
+    const int t0 = act ? tv : hx - V;  // idle lanes shadow the last entries (no stores)
+    if (((j + k + color) & 1) == 0)
+        tile_update2<V, 0, RT>(g, rh, f, x, h2, omega, color, j, k, t0, lane, act);
+    else
+        tile_update2<V, 1, RT>(g, rh, f, x, h2, omega, color, j, k, t0, lane, act);
 }
 
 bool rho0_tile_pass(const Geo& g, int tiles) {
@@ -636,6 +801,9 @@ void launch_rbgs_rho(const Geo& g, const float* rh, double h, const float* f, fl
             else if (own_zero)
                 launch_pdl(rbgs_rho_tile_kernel<false, true, V, __half>, gr, dim3(kBX, kVY), 0, st, g, rh16, h2, f,
                            x, color, (float)omega, k0, rev ? 1 : 0);
+            else if (PARIS_TILE_NP == 2 && (k1 - k0) % 2 == 0)
+                launch_pdl(rbgs_rho_tile2_kernel<V, __half>, dim3(gr.x, gr.y, (k1 - k0) / 2), dim3(kBX, kVY), 0, st,
+                           g, rh16, h2, f, x, color, (float)omega, k0, rev ? 1 : 0);
             else
                 launch_pdl(rbgs_rho_tile_kernel<false, false, V, __half>, gr, dim3(kBX, kVY), 0, st, g, rh16, h2, f,
                            x, color, (float)omega, k0, rev ? 1 : 0);
