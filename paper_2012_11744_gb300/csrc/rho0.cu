@@ -585,7 +585,7 @@ __device__ __forceinline__ void tile_update(const Geo& g, const RT* __restrict__
 // colour in both planes (plane k's x above is plane k+1's other colour, and
 // plane k+1's x below is plane k's).  Each cell's update is that of
 // tile_update, faces in the same order.
-template <int V, int M, typename RT>
+template <bool ZERO, bool XZ, int V, int M, typename RT>
 __device__ __forceinline__ void tile_update2(const Geo& g, const RT* __restrict__ rh,
                                              const float* __restrict__ f, float* x, float h2, float omega,
                                              int col, int j, int k, int t0, int lane, bool act) {
@@ -629,18 +629,30 @@ __device__ __forceinline__ void tile_update2(const Geo& g, const RT* __restrict_
     const float re1 = ldr(rh + o + pl + (M == 0 ? reR : reL));
     float xu0[V], xo0[V], xym0[V], xyp0[V], xzm0[V];
     float xu1[V], xo1[V], xym1[V], xyp1[V], xzp1[V];
-    ldv<V>(xu0, x + su);
-    ldv<V>(xo0, x + so);
-    ldv<V>(xym0, x + so + ym);
-    ldv<V>(xyp0, x + so + yp);
-    ldv<V>(xzm0, x + so + zm);
-    ldv<V>(xu1, x + su + pl);
-    ldv<V>(xo1, x + so + pl);
-    ldv<V>(xym1, x + so + pl + ym);
-    ldv<V>(xyp1, x + so + pl + yp);
-    ldv<V>(xzp1, x + so + pl + zp1);
-    const float xe0 = x[so + (M == 0 ? teL : teR)];
-    const float xe1 = x[so + pl + (M == 0 ? teR : teL)];
+    float xe0 = 0.f, xe1 = 0.f;
+    if (ZERO) {
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+            xu0[v] = xo0[v] = xym0[v] = xyp0[v] = xzm0[v] = xu1[v] = xo1[v] = xym1[v] = xyp1[v] = xzp1[v] = 0.f;
+    } else {
+        if (XZ) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) xu0[v] = xu1[v] = 0.f;
+        } else {
+            ldv<V>(xu0, x + su);
+            ldv<V>(xu1, x + su + pl);
+        }
+        ldv<V>(xo0, x + so);
+        ldv<V>(xym0, x + so + ym);
+        ldv<V>(xyp0, x + so + yp);
+        ldv<V>(xzm0, x + so + zm);
+        ldv<V>(xo1, x + so + pl);
+        ldv<V>(xym1, x + so + pl + ym);
+        ldv<V>(xyp1, x + so + pl + yp);
+        ldv<V>(xzp1, x + so + pl + zp1);
+        xe0 = x[so + (M == 0 ? teL : teR)];
+        xe1 = x[so + pl + (M == 0 ? teR : teL)];
+    }
     const bool ym_wall = g.wy && j == 0, yp_wall = g.wy && j == g.ny - 1;
     const bool zm_wall = g.wz && k == 0, zp_wall = g.wz && k + 1 == g.nz - 1;
     // one plane's update: member MM, its rows and neighbours; rzm / xzm the
@@ -685,13 +697,17 @@ __device__ __forceinline__ void tile_update2(const Geo& g, const RT* __restrict_
             const float b5 = zpw ? 0.f : bface(ru, rzp[v]);
             const float w = rcp_fast(((b0 + b1) + (b2 + b3)) + (b4 + b5));
             const float fc = F[v] * h2;
-            float acc = fmaf(b0, vo[v], fc);
-            acc = fmaf(b1, xo[v], acc);
-            acc = fmaf(b2, xym[v], acc);
-            acc = fmaf(b3, xyp[v], acc);
-            acc = fmaf(b4, xzm[v], acc);
-            acc = fmaf(b5, xzp[v], acc);
-            xn[v] = fmaf(omega, fmaf(w, acc, -xu[v]), xu[v]);
+            if (ZERO) {
+                xn[v] = omega * w * fc;
+            } else {
+                float acc = fmaf(b0, vo[v], fc);
+                acc = fmaf(b1, xo[v], acc);
+                acc = fmaf(b2, xym[v], acc);
+                acc = fmaf(b3, xyp[v], acc);
+                acc = fmaf(b4, xzm[v], acc);
+                acc = fmaf(b5, xzp[v], acc);
+                xn[v] = fmaf(omega, fmaf(w, acc, -xu[v]), xu[v]);
+            }
         }
     };
     // plane k: above it plane k+1's row (rho/2 of member M, x of the other colour of plane k+1)
@@ -728,6 +744,13 @@ __device__ __forceinline__ void tile_update2(const Geo& g, const RT* __restrict_
 #ifndef PARIS_TILE2_MINB
 #define PARIS_TILE2_MINB 4
 #endif
+// the zero-initial pass and the pass after it on two planes per block
+#ifndef PARIS_TILE_NP_ZERO
+#define PARIS_TILE_NP_ZERO 2
+#endif
+#ifndef PARIS_TILE_NP_XZ
+#define PARIS_TILE_NP_XZ 2
+#endif
 template <bool ZERO, bool XZ, int V, typename RT = float>
 __global__ void __launch_bounds__(kBX* kVY, sizeof(RT) == 2 ? PARIS_TILE_MINB_H : PARIS_TILE_MINB) rbgs_rho_tile_kernel(Geo g, const RT* __restrict__ rh, float h2,
                                                                const float* __restrict__ f, float* x,
@@ -752,9 +775,10 @@ __global__ void __launch_bounds__(kBX* kVY, sizeof(RT) == 2 ? PARIS_TILE_MINB_H 
         tile_update<ZERO, XZ, V, 1, RT>(g, rh, f, x, h2, omega, color, j, k, t0, lane, act);
 }
 
-// The regular pass over pairs of planes (tile_update2): block z covers planes
-// k0 + 2 zb and k0 + 2 zb + 1 (rev: zb descending).
-template <int V, typename RT>
+// The colour pass over pairs of planes (tile_update2; ZERO, XZ as in
+// tile_update): block z covers planes k0 + 2 zb and k0 + 2 zb + 1 (rev: zb
+// descending).
+template <bool ZERO, bool XZ, int V, typename RT>
 __global__ void __launch_bounds__(kBX* kVY, PARIS_TILE2_MINB) rbgs_rho_tile2_kernel(Geo g, const RT* __restrict__ rh,
                                                                                   float h2, const float* __restrict__ f,
                                                                                   float* x, int color, float omega,
@@ -770,9 +794,9 @@ __global__ void __launch_bounds__(kBX* kVY, PARIS_TILE2_MINB) rbgs_rho_tile2_ker
     const bool act = tv < hx;
     const int t0 = act ? tv : hx - V;  // idle lanes shadow the last entries (no stores)
     if (((j + k + color) & 1) == 0)
-        tile_update2<V, 0, RT>(g, rh, f, x, h2, omega, color, j, k, t0, lane, act);
+        tile_update2<ZERO, XZ, V, 0, RT>(g, rh, f, x, h2, omega, color, j, k, t0, lane, act);
     else
-        tile_update2<V, 1, RT>(g, rh, f, x, h2, omega, color, j, k, t0, lane, act);
+        tile_update2<ZERO, XZ, V, 1, RT>(g, rh, f, x, h2, omega, color, j, k, t0, lane, act);
 }
 
 bool rho0_tile_pass(const Geo& g, int tiles) {
@@ -795,15 +819,23 @@ void launch_rbgs_rho(const Geo& g, const float* rh, double h, const float* f, fl
         constexpr int V = kTileV > 0 ? kTileV : 2;
         dim3 gr((hx / V + kBX - 1) / kBX, (g.ny + kVY - 1) / kVY, k1 - k0);
         if (rh16 && tiles == 1) {  // the V-cycle's passes from FP16 rho/2
-            if (zero_init)
+            const dim3 gr2(gr.x, gr.y, (k1 - k0) / 2);
+            const bool two = (k1 - k0) % 2 == 0;
+            if (zero_init && two && PARIS_TILE_NP_ZERO == 2)
+                launch_pdl(rbgs_rho_tile2_kernel<true, false, V, __half>, gr2, dim3(kBX, kVY), 0, st, g, rh16, h2, f,
+                           x, color, (float)omega, k0, rev ? 1 : 0);
+            else if (zero_init)
                 launch_pdl(rbgs_rho_tile_kernel<true, false, V, __half>, gr, dim3(kBX, kVY), 0, st, g, rh16, h2, f,
+                           x, color, (float)omega, k0, rev ? 1 : 0);
+            else if (own_zero && two && PARIS_TILE_NP_XZ == 2)
+                launch_pdl(rbgs_rho_tile2_kernel<false, true, V, __half>, gr2, dim3(kBX, kVY), 0, st, g, rh16, h2, f,
                            x, color, (float)omega, k0, rev ? 1 : 0);
             else if (own_zero)
                 launch_pdl(rbgs_rho_tile_kernel<false, true, V, __half>, gr, dim3(kBX, kVY), 0, st, g, rh16, h2, f,
                            x, color, (float)omega, k0, rev ? 1 : 0);
-            else if (PARIS_TILE_NP == 2 && (k1 - k0) % 2 == 0)
-                launch_pdl(rbgs_rho_tile2_kernel<V, __half>, dim3(gr.x, gr.y, (k1 - k0) / 2), dim3(kBX, kVY), 0, st,
-                           g, rh16, h2, f, x, color, (float)omega, k0, rev ? 1 : 0);
+            else if (PARIS_TILE_NP == 2 && two)
+                launch_pdl(rbgs_rho_tile2_kernel<false, false, V, __half>, gr2, dim3(kBX, kVY), 0, st, g, rh16, h2, f,
+                           x, color, (float)omega, k0, rev ? 1 : 0);
             else
                 launch_pdl(rbgs_rho_tile_kernel<false, false, V, __half>, gr, dim3(kBX, kVY), 0, st, g, rh16, h2, f,
                            x, color, (float)omega, k0, rev ? 1 : 0);
@@ -1175,11 +1207,9 @@ __global__ void __launch_bounds__(kBX* kVY, RESTRICT ? PARIS_OP_MINB_R : PARIS_O
     float acc[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) acc[v] = 0.f;
-    for (int p = 0; p < np; ++p) {
-        const int k = zb * np + p;
-        if (k >= g.nz) break;  // uniform per block
+    // e += alpha_p x on the tile row of plane k (both colours, in memory order)
+    auto eupd = [&](int k) {
         if (XP && eacc && act) {
-            // e += alpha_p x on this tile row (both colours, in memory order)
             const int rb = (k * g.ny + jc) * g.nx;
             float o0[V], o1[V], e0[V], e1[V];
             ldgv<V>(o0, x + rb + t0);
@@ -1199,11 +1229,9 @@ __global__ void __launch_bounds__(kBX* kVY, RESTRICT ? PARIS_OP_MINB_R : PARIS_O
             stv<V>(eacc + rb + t0, e0);
             stv<V>(eacc + rb + hx + t0, e1);
         }
-        float a[2 * V], X[2 * V], F[2 * V];
-        if (((jc + k) & 1) == 0)
-            tile_apply<RESTRICT, V, 0, XP, RT>(g, rh, x, f, jc, k, t0, lane, a, X, F, z, beta);
-        else
-            tile_apply<RESTRICT, V, 1, XP, RT>(g, rh, x, f, jc, k, t0, lane, a, X, F, z, beta);
+    };
+    // plane k's results: q (and the new x) stored, d . q, or the restriction sums
+    auto post = [&](int k, const float (&a)[2 * V], const float (&X)[2 * V], const float (&F)[2 * V]) {
         if (!RESTRICT) {
             const int c0 = (jc + k) & 1;
             float Q[2 * V], q0[V], q1[V];
@@ -1235,6 +1263,17 @@ __global__ void __launch_bounds__(kBX* kVY, RESTRICT ? PARIS_OP_MINB_R : PARIS_O
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[v] += (F[2 * v] - ih2 * a[2 * v]) + (F[2 * v + 1] - ih2 * a[2 * v + 1]);
         }
+    };
+    for (int p = 0; p < np; ++p) {
+        const int k = zb * np + p;
+        if (k >= g.nz) break;  // uniform per block
+        eupd(k);
+        float a[2 * V], X[2 * V], F[2 * V];
+        if (((jc + k) & 1) == 0)
+            tile_apply<RESTRICT, V, 0, XP, RT>(g, rh, x, f, jc, k, t0, lane, a, X, F, z, beta);
+        else
+            tile_apply<RESTRICT, V, 1, XP, RT>(g, rh, x, f, jc, k, t0, lane, a, X, F, z, beta);
+        post(k, a, X, F);
     }
     if (RESTRICT) {
 #pragma unroll
