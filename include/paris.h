@@ -365,8 +365,10 @@ paris_status paris_marker_function(paris_ctx* ctx, const double* gx, const doubl
  * p_gas the gas pressure per cell (the polytropic law of Eq. polygas per gas
  * pocket; the caller's).  The step forms rhs = (div u*) / dt in the liquid (wall
  * faces carry no flux), solves the SPD system (no null space: every liquid
- * region must touch the gas) in the FP64 form of the multigrid-preconditioned
- * CG whatever opts.precision says, and corrects u = u* - dt beta grad p
+ * region must touch the gas) in opts.precision (the mixed form: FP64
+ * refinement around the FP32 V-cycle-preconditioned CG, the diagonal excess
+ * on every FP32 level; fallback to FP64 as for paris_poisson_solve), and
+ * corrects u = u* - dt beta grad p
  * (Eq. fotm) on every face touching the liquid with the same gradients.
  * Faces between two gas cells keep their values (the caller extrapolates
  * them); wall faces are set to 0.  p: in, the initial guess in the liquid;

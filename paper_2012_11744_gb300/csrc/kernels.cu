@@ -630,6 +630,11 @@ void launch_convert_beta(const Geo& g, const double* b64[3], double scale, T* ou
     }
 }
 
+void launch_convert_scaled(int64_t n, const double* in, double scale, float* out, cudaStream_t st) {
+    convert_beta_kernel<float><<<elementwise_blocks(n), kRedThreads, 0, st>>>(n, in, scale, out);
+    count_launch();
+}
+
 // Rediscretised coarse coefficients (the paper gives no coarsening rule,
 // Sec. 3.7.3): a coarse face normal to axis a is covered by the fine faces
 // at fine index f_a*I_a along a and f_b*I_b + {0..f_b-1} along the other
@@ -1056,9 +1061,9 @@ void launch_rbgs(const Geo& g, const Coef<T>& cf, const T* w, const T* f, T* x, 
     // four cells per thread where a row fills at least a warp (shorter rows
     // would leave lanes idle: the single-pair kernel serves them)
     if (g.nx % 4 == 0 && g.nx >= 4 * kTX && !g.wx && fits_i32(g) && aligned16(cf.bx, cf.by, cf.bz, f) &&
-        aligned16(x) && (sizeof(T) == 4 || aligned16(w))) {
+        aligned16(x) && ((sizeof(T) == 4 && !cf.sig) || aligned16(w))) {
         dim3 gr((g.nx / 4 + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, k1 - k0);
-        if (sizeof(T) == 8)
+        if (sizeof(T) == 8 || cf.sig)  // w read (FP64, or a diagonal excess the coefficients do not hold)
             launch_pdl(rbgs4_kernel<T, true>, gr, dim3(kTX, kTY), 0, st, g, cf.bx, cf.by, cf.bz, cf.scale, w, f,
                 x, color, (T)omega, zero_init ? 1 : 0, k0);
         else
@@ -1072,7 +1077,7 @@ void launch_rbgs(const Geo& g, const Coef<T>& cf, const T* w, const T* f, T* x, 
     // FP32: recomputing 1/D from the coefficients already loaded is cheaper
     // than reading it; FP64: the division costs more than the read
     const bool i32 = fits_i32(g);
-    if (sizeof(T) == 8) {
+    if (sizeof(T) == 8 || cf.sig) {
         if (i32)
             launch_pdl(rbgs_kernel<T, T, true, true>, gr, dim3(kTX, kTY), 0, st, g, cf.bx, cf.by, cf.bz,
                 cf.scale, w, f, x, color, (T)omega, zero_init ? 1 : 0, k0);

@@ -374,6 +374,8 @@ int64_t launch_max_divergence(const Geo& g, const double* u, const double* v, co
 template <typename T>
 void launch_convert_beta(const Geo& g, const double* b64[3], double scale, T* out[3],
                          cudaStream_t st);
+// out = float(in * scale) over n cells (the FP32 copy of a diagonal excess)
+void launch_convert_scaled(int64_t n, const double* in, double scale, float* out, cudaStream_t st);
 template <typename T>
 void launch_coarse_beta(const Geo& fine, const Coef<T>& cf, const Geo& coarse, const int f[3],
                         const double hc2_over_hf2[3], T* out[3], cudaStream_t st);

@@ -44,6 +44,7 @@ struct Level {
     double* f64 = nullptr;
     double* t64 = nullptr;
     double* sig64 = nullptr;  // diagonal excess of a Dirichlet-coupled operator (levels >= 1, on first use)
+    float* sig32 = nullptr;   // its FP32 copy for the mixed form's V-cycle
     __half* b16[3] = {nullptr, nullptr, nullptr};  // level 1 of the mixed step: FP16 coefficients (see half1)
     float scale16 = 1.f;                           // their scale (the coefficient is b16 * scale16)
 };
@@ -119,8 +120,9 @@ struct paris_ctx {
     double n_fluid = 0.0;  // fluid cells (with solid set)
     // free-surface projections (Sec. 3.7.5; allocated on first use): the
     // finest level's diagonal excess and the cell classes; dirichlet: the
-    // current solve's operator carries the excess (no null space, FP64 form)
+    // current solve's operator carries the excess (no null space)
     double* sig0 = nullptr;
+    float* sig32_0 = nullptr;  // FP32 copy of sig0 times 1/h^2 (the mixed form's finest level)
     unsigned char* fs_cls = nullptr;
     unsigned char* fs_tmp = nullptr;
     bool dirichlet = false;
@@ -336,6 +338,7 @@ struct Prec<float> {
     static float* x(Level& L) { return L.x32; }
     static float* f(Level& L) { return L.f32; }
     static float* t(Level& L) { return L.t32; }
+    static float* sig(Level& L) { return L.sig32; }
 };
 template <>
 struct Prec<double> {
@@ -344,6 +347,7 @@ struct Prec<double> {
     static double* x(Level& L) { return L.x64; }
     static double* f(Level& L) { return L.f64; }
     static double* t(Level& L) { return L.t64; }
+    static double* sig(Level& L) { return L.sig64; }
 };
 
 template <typename T>
@@ -351,9 +355,7 @@ Coef<T> level_coef(paris_ctx* c, int l, const Coef<T>& c0) {
     if (l == 0) return c0;
     Level& L = c->lv[l];
     Coef<T> cf{Prec<T>::b(L, 0), Prec<T>::b(L, 1), Prec<T>::b(L, 2), T(1)};
-    if constexpr (sizeof(T) == 8) {
-        if (c->dirichlet) cf.sig = L.sig64;
-    }
+    if (c->dirichlet) cf.sig = Prec<T>::sig(L);
     return cf;
 }
 
@@ -386,15 +388,14 @@ void setup_hierarchy(paris_ctx* c, const Coef<T>& c0) {
             }
         }
         launch_coarse_beta<T>(F.g, cf, L.g, L.fac, ratio2, out, c->st);
-        if constexpr (sizeof(T) == 8) {
-            if (c->dirichlet) launch_coarse_sig<T>(F.g, cf.sig, (double)cf.scale, L.g, L.fac, L.sig64, c->st);
-        }
+        if (c->dirichlet) launch_coarse_sig<T>(F.g, cf.sig, (double)cf.scale, L.g, L.fac, Prec<T>::sig(L), c->st);
     }
-    // inverse diagonals: read by the FP64 smoothers, by Jacobi and by the
-    // tail launch; the FP32 red-black sweeps of the other levels
-    // recompute them from the coefficients they load (the same value)
+    // inverse diagonals: read by the FP64 smoothers, by Jacobi, by the tail
+    // launch and by every smoother of an operator with a diagonal excess; the
+    // other FP32 red-black sweeps recompute them from the coefficients they
+    // load (the same value)
     const int t = tail_start(c);
-    if (sizeof(T) == 8 || c->opts.smoother == PARIS_SMOOTH_JACOBI) {
+    if (sizeof(T) == 8 || c->opts.smoother == PARIS_SMOOTH_JACOBI || c->dirichlet) {
         for (int l = 0; l < nl; ++l)
             launch_inv_diag<T>(c->lv[l].g, level_coef<T>(c, l, c0), Prec<T>::w(c->lv[l]), c->st);
     } else if (t > 0) {
@@ -425,7 +426,8 @@ void smooth(paris_ctx* c, int l, const Coef<T>& cf, const T* f, T* x, int sweeps
     const paris_opts& o = c->opts;
     const double n = (double)L.g.ncell(), sz = sizeof(T), nb = beta_count(L.g);
     const int cls = l == 0 ? PARIS_K_SMOOTH0 : -1;
-    const bool use_w = sizeof(T) == 8;  // FP64: a division costs more than reading 1/D
+    // FP64: a division costs more than reading 1/D; a diagonal excess is only in 1/D
+    const bool use_w = sizeof(T) == 8 || cf.sig != nullptr;
     if (o.smoother == PARIS_SMOOTH_RBGS_2PASS ||
         (o.smoother == PARIS_SMOOTH_RBGS && !rbgs_fused_fits(L.g))) {
         // Large levels run each colour pass slab by slab: the second colour of
@@ -867,12 +869,16 @@ void mixed_setup(paris_ctx* c, const Coef<double>& c64, bool rho0) {
     const double ih2 = 1.0 / (c->grid.h * c->grid.h);
     const double* b64[3] = {c64.bx, c64.by, c64.bz};
     c->rho0 = rho0;
-    c->half0 = !rho0 && c->opts.half_coefficients != 0;
+    c->half0 = !rho0 && c->opts.half_coefficients != 0 && !c->dirichlet;
     Coef<float> c32{c->b32_0[0], c->b32_0[1], c->b32_0[2], 1.0f};
     ProfScope ps(c, PARIS_K_SETUP, 0.0);
     if (!rho0) {
         launch_convert_beta<float>(c->g0, b64, ih2, c->b32_0, c->st);
         if (c->half0) launch_convert_beta_half(c->g0, b64, c->b16_0, c->st);
+    }
+    if (c->dirichlet) {  // the diagonal excess, scaled like the FP32 coefficients
+        launch_convert_scaled(c->N, c64.sig, ih2, c->sig32_0, c->st);
+        c32.sig = c->sig32_0;
     }
     setup_hierarchy<float>(c, c32);
 }
@@ -882,9 +888,10 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
     const int64_t N = c->N;
     Level0Mode mode_guard{c};
     Coef<float> c32{c->b32_0[0], c->b32_0[1], c->b32_0[2], 1.0f};
+    if (c->dirichlet) c32.sig = c->sig32_0;
     if (c->mixed_ready) {
         c->rho0 = rho0;
-        c->half0 = !rho0 && c->opts.half_coefficients != 0;
+        c->half0 = !rho0 && c->opts.half_coefficients != 0 && !c->dirichlet;
     } else {
         mixed_setup(c, c64, rho0);
     }
@@ -1213,7 +1220,7 @@ paris_status poisson_solve(paris_ctx* c, const double* bx, const double* by, con
     if (s != PARIS_OK) return s;
     SolveOut out;
     int fell_back = 0;
-    if (c->opts.precision == PARIS_MIXED && !c->dirichlet) {
+    if (c->opts.precision == PARIS_MIXED && (!c->dirichlet || c->sig32_0)) {
         s = solve_mixed(c, c64, p, out, c->opts.max_iter, rho0, half_rho);
         if (s != PARIS_OK) return s;
         if (!out.converged && !out.nonfinite && c->opts.fallback) {
@@ -1420,8 +1427,13 @@ paris_status fs_alloc(paris_ctx* c) {
     if (c->sig0) return PARIS_OK;
     Alloc a;
     double* s0 = a.get<double>(c->N);
+    float* s0f = a.get<float>(c->N);
     std::vector<double*> sl(c->lv.size(), nullptr);
-    for (size_t l = 1; l < c->lv.size(); ++l) sl[l] = a.get<double>(c->lv[l].g.ncell());
+    std::vector<float*> slf(c->lv.size(), nullptr);
+    for (size_t l = 1; l < c->lv.size(); ++l) {
+        sl[l] = a.get<double>(c->lv[l].g.ncell());
+        slf[l] = a.get<float>(c->lv[l].g.ncell());
+    }
     unsigned char* cls = a.get<unsigned char>(c->N);
     unsigned char* tmp = a.get<unsigned char>(c->N);
     if (a.err != cudaSuccess) {
@@ -1429,7 +1441,11 @@ paris_status fs_alloc(paris_ctx* c) {
         return PARIS_ERR_NO_MEMORY;
     }
     c->sig0 = s0;
-    for (size_t l = 1; l < c->lv.size(); ++l) c->lv[l].sig64 = sl[l];
+    c->sig32_0 = s0f;
+    for (size_t l = 1; l < c->lv.size(); ++l) {
+        c->lv[l].sig64 = sl[l];
+        c->lv[l].sig32 = slf[l];
+    }
     c->fs_cls = cls;
     c->fs_tmp = tmp;
     c->mem.ptrs.insert(c->mem.ptrs.end(), a.ptrs.begin(), a.ptrs.end());
