@@ -1156,6 +1156,92 @@ __device__ __forceinline__ void tile_apply(const Geo& g, const RT* __restrict__ 
     }
 }
 
+// The residual restriction's operator sums over the 2 x 2 x 2 children of
+// a coarse cell.  Summed over the children, A x keeps only the faces on the
+// coarse cell's surface: a face between two children enters once from each
+// side with opposite signs.  So each child takes only its faces on that
+// surface: along x the pair's outer face (the pairs are the coarse cells'
+// x-extents), along y the face away from the other row of the coarse cell
+// (row j even: y-, odd: y+), along z likewise (plane k even: z-, odd: z+).
+// a: (A x)/scale restricted to those faces for the 2V cells of row j, plane
+// k, in cell order; F: f of the same cells.  Three faces a cell instead of
+// six, and one y- and one z-neighbour row instead of two.
+template <int V, int C0, typename RT>
+__device__ __forceinline__ void tile_restrict_faces(const Geo& g, const RT* __restrict__ rh,
+                                                    const float* __restrict__ x, const float* __restrict__ f,
+                                                    int j, int k, int t0, int lane, float (&a)[2 * V],
+                                                    float (&F)[2 * V]) {
+    const int nx = g.nx, hx = nx / 2, pl = nx * g.ny;
+    const int rb = k * pl + j * nx;
+    const int o = rb + 2 * t0;
+    const bool jodd = j & 1, kodd = k & 1;
+    const int oy = !jodd ? (j > 0 ? -nx : (g.ny - 1) * nx) : (j < g.ny - 1 ? nx : -(g.ny - 1) * nx);
+    const int oz = !kodd ? (k > 0 ? -pl : (g.nz - 1) * pl) : (k < g.nz - 1 ? pl : -(g.nz - 1) * pl);
+    const bool ywall = g.wy && (!jodd ? j == 0 : j == g.ny - 1);
+    const bool zwall = g.wz && (!kodd ? k == 0 : k == g.nz - 1);
+    float h0[V], h1[V];
+    auto cells = [&](int off, int c0, float (&out)[2 * V]) {
+        ldgv<V>(h0, x + rb + off + t0);
+        ldgv<V>(h1, x + rb + off + hx + t0);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            out[2 * v] = c0 ? h1[v] : h0[v];
+            out[2 * v + 1] = c0 ? h0[v] : h1[v];
+        }
+    };
+    float R[2 * V], Ry[2 * V], Rz[2 * V], X[2 * V], Xy[2 * V], Xz[2 * V];
+    ldgv<2 * V>(R, rh + o);
+    ldgv<2 * V>(Ry, rh + o + oy);
+    ldgv<2 * V>(Rz, rh + o + oz);
+    cells(0, C0, X);
+    cells(oy, C0 ^ 1, Xy);
+    cells(oz, C0 ^ 1, Xz);
+    ldgv<V>(h0, f + rb + t0);
+    ldgv<V>(h1, f + rb + hx + t0);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        F[2 * v] = C0 ? h1[v] : h0[v];
+        F[2 * v + 1] = C0 ? h0[v] : h1[v];
+    }
+    // cells 2t0-1 and 2t0+2V outside the lane's entries, wrapped around the
+    // row: from the adjacent lanes, or loaded
+    const int tl = t0 > 0 ? t0 - 1 : hx - 1, tr = t0 + V < hx ? t0 + V : t0 + V - hx;
+    const float xl_ld = __ldg(x + rb + (C0 ? 0 : hx) + tl), xr_ld = __ldg(x + rb + (C0 ? hx : 0) + tr);
+    const float rl_ld = ldr(rh + o + (t0 > 0 ? -1 : nx - 1));
+    const float rr_ld = ldr(rh + o + (t0 + V < hx ? 2 * V : 2 * V - nx));
+    const float xl_sh = __shfl_up_sync(kAll, X[2 * V - 1], 1), rl_sh = __shfl_up_sync(kAll, R[2 * V - 1], 1);
+    const float xr_sh = __shfl_down_sync(kAll, X[0], 1), rr_sh = __shfl_down_sync(kAll, R[0], 1);
+    const bool left_lane = lane > 0 && t0 > 0, right_lane = lane < 31 && t0 + V < hx;
+    const float xl = left_lane ? xl_sh : xl_ld, rl = left_lane ? rl_sh : rl_ld;
+    const float xr = right_lane ? xr_sh : xr_ld, rr = right_lane ? rr_sh : rr_ld;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const int c = 2 * v + m;
+            float xo, ro;
+            bool xwall;
+            if (m == 0) {
+                xwall = g.wx && t0 + v == 0;
+                xo = v > 0 ? X[c - 1] : xl;
+                ro = v > 0 ? R[c - 1] : rl;
+            } else {
+                xwall = g.wx && t0 + v == hx - 1;
+                xo = v < V - 1 ? X[c + 1] : xr;
+                ro = v < V - 1 ? R[c + 1] : rr;
+            }
+            const float bx = xwall ? 0.f : bface(R[c], ro);
+            const float by = ywall ? 0.f : bface(R[c], Ry[c]);
+            const float bz = zwall ? 0.f : bface(R[c], Rz[c]);
+            const float xc = X[c];
+            float sum = bx * (xc - xo);
+            sum = fmaf(by, xc - Xy[c], sum);
+            sum = fmaf(bz, xc - Xz[c], sum);
+            a[c] = sum;
+        }
+    }
+}
+
 }  // namespace
 
 // RESTRICT = false: q = A d on the tiles of np consecutive planes and the
@@ -1167,13 +1253,20 @@ __device__ __forceinline__ void tile_apply(const Geo& g, const RT* __restrict__ 
 // shared memory.
 // blocks per SM the register allocation must allow: the product (with the
 // fused direction update) at 4 (64 registers, a few spilled) measured 3 %
-// faster than at 3; the restriction is fastest at 3 (80 registers)
+// faster than at 3; the restriction on the coarse cells' surface faces at 4
+// (64 registers: 43 us against 50 at 3)
 #ifndef PARIS_OP_MINB
 #define PARIS_OP_MINB 4
 #endif
 #ifndef PARIS_OP_MINB_R
-#define PARIS_OP_MINB_R 3
+#define PARIS_OP_MINB_R 4
 #endif
+// the restriction's operator on the coarse cells' surface faces only (0: the
+// full stencil of every child)
+#ifndef PARIS_RESTRICT_SURFACE
+#define PARIS_RESTRICT_SURFACE 1
+#endif
+constexpr bool kRestrictSurface = PARIS_RESTRICT_SURFACE != 0;
 template <bool RESTRICT, int V, bool XP = false, typename RT = float>
 __global__ void __launch_bounds__(kBX* kVY, RESTRICT ? PARIS_OP_MINB_R : PARIS_OP_MINB) op_rho_tile_kernel(Geo g, const RT* __restrict__ rh, float ih2,
                                                              const float* __restrict__ x,
@@ -1269,10 +1362,17 @@ __global__ void __launch_bounds__(kBX* kVY, RESTRICT ? PARIS_OP_MINB_R : PARIS_O
         if (k >= g.nz) break;  // uniform per block
         eupd(k);
         float a[2 * V], X[2 * V], F[2 * V];
-        if (((jc + k) & 1) == 0)
-            tile_apply<RESTRICT, V, 0, XP, RT>(g, rh, x, f, jc, k, t0, lane, a, X, F, z, beta);
-        else
-            tile_apply<RESTRICT, V, 1, XP, RT>(g, rh, x, f, jc, k, t0, lane, a, X, F, z, beta);
+        if constexpr (RESTRICT && kRestrictSurface) {
+            if (((jc + k) & 1) == 0)
+                tile_restrict_faces<V, 0, RT>(g, rh, x, f, jc, k, t0, lane, a, F);
+            else
+                tile_restrict_faces<V, 1, RT>(g, rh, x, f, jc, k, t0, lane, a, F);
+        } else {
+            if (((jc + k) & 1) == 0)
+                tile_apply<RESTRICT, V, 0, XP, RT>(g, rh, x, f, jc, k, t0, lane, a, X, F, z, beta);
+            else
+                tile_apply<RESTRICT, V, 1, XP, RT>(g, rh, x, f, jc, k, t0, lane, a, X, F, z, beta);
+        }
         post(k, a, X, F);
     }
     if (RESTRICT) {
