@@ -163,6 +163,27 @@ __device__ inline T apply_A(const Stencil<T>& s, const T* __restrict__ x, T xc, 
     return scale * acc;
 }
 
+// The faces of apply_A selected by mask (bit q: face q), in the same order.
+// Summed over the children of a coarse cell, A x keeps only the faces on the
+// coarse cell's surface (a face between two children enters once from each
+// side with opposite signs): the restrictions take those faces only.
+template <typename T>
+__device__ inline T apply_A_faces(const Stencil<T>& s, const T* __restrict__ x, T xc, T scale, unsigned mask) {
+    T acc = T(0);
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+        if ((mask >> q) & 1u) acc = fma(s.b[q], xc - x[s.nb[q]], acc);
+    return scale * acc;
+}
+
+// the faces of child (di, dj, dk) of a coarse cell with factors (f0, f1, f2)
+// on the coarse cell's surface: - face of the first child along an axis, +
+// face of the last
+__device__ inline unsigned surface_faces(int di, int dj, int dk, int f0, int f1, int f2) {
+    return (di == 0 ? 1u : 0u) | (di == f0 - 1 ? 2u : 0u) | (dj == 0 ? 4u : 0u) | (dj == f1 - 1 ? 8u : 0u) |
+           (dk == 0 ? 16u : 0u) | (dk == f2 - 1 ? 32u : 0u);
+}
+
 // 1 / sum of the six face coefficients (the red-black sweeps' inverse diagonal)
 __device__ inline float rcp_rn(float d) { return __frcp_rn(d); }  // == 1.0f / d
 __device__ inline double rcp_rn(double d) { return 1.0 / d; }

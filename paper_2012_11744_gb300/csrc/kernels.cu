@@ -1158,10 +1158,12 @@ void launch_jacobi(const Geo& g, const Coef<T>& cf, const T* w, const T* f, cons
 // ------------------------------------------------- restriction / prolongation ---
 
 // Coarse right-hand side: the average over the children of the fine residual
-// f - A x (restriction R = P^T / #children for the piecewise-constant P).
-// FULL: the 2 x 2 x 2 children of full coarsening, the loops unrolled so
-// that the loads of all eight stencils are in flight together (the sum keeps
-// its order).
+// f - A x (restriction R = P^T / #children for the piecewise-constant P),
+// each child's A x on its faces on the coarse cell's surface only (the
+// faces between children cancel in the sum; apply_A_faces).  FULL: the
+// 2 x 2 x 2 children of full coarsening, the loops unrolled so that the
+// loads of all eight children are in flight together (the sum keeps its
+// order).
 template <typename T, typename TB, bool I32, bool SIG = false, bool FULL = false>
 __global__ void restrict_residual_kernel(Geo fg, const TB* __restrict__ bx, const TB* __restrict__ by,
                                          const TB* __restrict__ bz, T scale, const T* __restrict__ f,
@@ -1191,7 +1193,7 @@ __global__ void restrict_residual_kernel(Geo fg, const TB* __restrict__ bx, cons
                     c = fg.cidx(i, j, k);
                     load_stencil_as<T>(fg, bx, by, bz, i, j, k, s);
                 }
-                T ax = apply_A(s, x, x[c], scale);
+                T ax = apply_A_faces(s, x, x[c], scale, surface_faces(di, dj, dk, fa0, fa1, fa2));
                 if (SIG) ax = fma(scale * sig[c], x[c], ax);
                 sum += f[c] - ax;
             }

@@ -98,7 +98,8 @@ __device__ void tail_smooth(const TailLevel<T> L, int sweeps, bool first_zero, b
     }
 }
 
-// coarse f = average over the children of the fine residual f - A x
+// coarse f = average over the children of the fine residual f - A x (A x on
+// the coarse cell's surface faces, as restrict_residual_kernel)
 template <typename T>
 __device__ void tail_restrict(const TailLevel<T> F, const TailLevel<T> C) {
     const Geo fg = F.g;
@@ -116,7 +117,7 @@ __device__ void tail_restrict(const TailLevel<T> F, const TailLevel<T> C) {
                     Stencil<T> s;
                     int c;
                     load_stencil_fast<T>(fg, F.bx, F.by, F.bz, i, j, k, s, c);
-                    sum += F.f[c] - apply_A(s, F.x, F.x[c], F.scale);
+                    sum += F.f[c] - apply_A_faces(s, F.x, F.x[c], F.scale, surface_faces(di, dj, dk, fa0, fa1, fa2));
                 }
         C.f[t] = sum / T(fa0 * fa1 * fa2);
     }
