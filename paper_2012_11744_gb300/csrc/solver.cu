@@ -141,6 +141,7 @@ struct paris_ctx {
     // host-buffer step: a copy stream and its ordering events (created on first use)
     cudaStream_t copy_st = nullptr;
     cudaEvent_t copy_ev[5] = {};
+    cudaEvent_t scal_ev = nullptr;  // the host copy of scal of the inner loop's norms (read_scal_async)
     double last_mean_b = 0.0;
     Profiler prof;
     // CUDA graphs of the coarse part of the V-cycle (index 0: FP32, 1: FP64)
@@ -295,6 +296,23 @@ paris_status read_scal(paris_ctx* c) {
     CK(cudaMemcpyAsync(c->scal_h, c->scal, sizeof(Scal), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     if (c->scal_h->wait_fail) {  // a staged kernel's bounded wait gave up: clear the word, report it
+        CK(cudaMemsetAsync(&c->scal->wait_fail, 0, sizeof(unsigned), c->st));
+        return PARIS_ERR_TIMEOUT;
+    }
+    return PARIS_OK;
+}
+
+// read_scal in two halves: the copy queued (and an event after it), so that
+// more work can be queued behind it, then the wait for that copy only
+paris_status read_scal_async(paris_ctx* c) {
+    if (!c->scal_ev) CK(cudaEventCreateWithFlags(&c->scal_ev, cudaEventDisableTiming));
+    CK(cudaMemcpyAsync(c->scal_h, c->scal, sizeof(Scal), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaEventRecord(c->scal_ev, c->st));
+    return PARIS_OK;
+}
+paris_status read_scal_wait(paris_ctx* c) {
+    CK(cudaEventSynchronize(c->scal_ev));
+    if (c->scal_h->wait_fail) {
         CK(cudaMemsetAsync(&c->scal->wait_fail, 0, sizeof(unsigned), c->st));
         return PARIS_ERR_TIMEOUT;
     }
@@ -943,6 +961,7 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
             std::swap(c->d32, c->z32);  // first direction d = z: exchange the buffers
         }
         bool fuse_next = false;
+        double prev_in_rr = rr32;  // ||r32||^2 before the last iteration
         for (int j = 0; j < 50 && out.iters < max_iter; ++j) {
             if (fuse_next) {
                 // z, d, rho/2 and e (after the first) read; d, q and e written
@@ -972,23 +991,39 @@ paris_status solve_mixed(paris_ctx* c, const Coef<double>& c64, double* x, Solve
                     launch_update_xr<float>(N, c->scal, c->d32, c->q32, c->e32, c->r32, c->partials, c->st,
                                             FinSpec{c->scal, 3, 2, FIN_STORE, 0.0}, c->rho0 && take_dir(c));
                 }
-                s = read_scal(c);
+                s = read_scal_async(c);
+                if (s != PARIS_OK) return s;
+            }
+            // the next iteration's V-cycle and dot products go in behind the
+            // norms' copy while the host waits for it, when even a reduction
+            // of ||r||^2 by 1000 in this iteration would leave it above the
+            // target (the reduction per iteration is about 60 here); if the
+            // iteration converges all the same, their results go unused
+            const bool ahead = fuse && prev_in_rr * 1e-3 > target;
+            auto next_direction = [&]() {
+                vcycle<float>(c, c32, c->r32, c->z32);
+                ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
+                launch_dot2<float>(N, c->z32, c->r32, c->q32, c->partials, c->st,  // (z.r, z.q)
+                                   FinSpec{c->scal, 2, 0, FIN_FCG_BETA, 0.0}, c->rho0 && take_dir(c));
+                if (fuse) {
+                    fuse_next = true;
+                } else {
+                    launch_xpby<float>(N, c->scal, c->z32, c->d32, c->st);
+                    c->lz = true;
+                }
+            };
+            if (ahead) next_direction();
+            {
+                ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
+                s = read_scal_wait(c);
             }
             ++out.iters;
             if (s != PARIS_OK) return s;
             const double in_rr = c->scal_h->red[0];
             if (!(in_rr == in_rr) || c->scal_h->red[2] > 0) break;  // non-finite: the outer step decides
             if (in_rr <= target || in_rr > 1e6 * rr32) break;
-            vcycle<float>(c, c32, c->r32, c->z32);
-            ProfScope ps(c, PARIS_K_KRYLOV, 0.0);
-            launch_dot2<float>(N, c->z32, c->r32, c->q32, c->partials, c->st,  // (z.r, z.q)
-                               FinSpec{c->scal, 2, 0, FIN_FCG_BETA, 0.0}, c->rho0 && take_dir(c));
-            if (fuse) {
-                fuse_next = true;
-            } else {
-                launch_xpby<float>(N, c->scal, c->z32, c->d32, c->st);
-                c->lz = true;
-            }
+            prev_in_rr = in_rr;
+            if (!ahead) next_direction();
         }
         if (refine) {
             ProfScope ps(c, PARIS_K_RESID64, 48.0 * N);
@@ -1088,6 +1123,7 @@ paris_status paris_destroy(paris_ctx* c) {
     }
     for (auto& e : c->copy_ev)
         if (e) cudaEventDestroy(e);
+    if (c->scal_ev) cudaEventDestroy(c->scal_ev);
     c->mem.release();
     for (void* q : c->hw_mem) cudaFree(q);
     if (c->scal_h) cudaFreeHost(c->scal_h);
