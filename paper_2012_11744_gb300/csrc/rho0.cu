@@ -741,8 +741,15 @@ __device__ __forceinline__ void tile_update2(const Geo& g, const RT* __restrict_
 #ifndef PARIS_TILE_NP
 #define PARIS_TILE_NP 2
 #endif
+// rows per block of the two-plane pass: blocks of two rows (64 threads, 16
+// per SM at 64 registers) measured 28.6 us a pass against 30.3 with eight
+// rows and 32.4 with sixteen
+#ifndef PARIS_TILE2_VY
+#define PARIS_TILE2_VY 2
+#endif
+constexpr int kVY2 = PARIS_TILE2_VY;
 #ifndef PARIS_TILE2_MINB
-#define PARIS_TILE2_MINB 4
+#define PARIS_TILE2_MINB (32 / PARIS_TILE2_VY)
 #endif
 // the zero-initial pass and the pass after it on two planes per block
 #ifndef PARIS_TILE_NP_ZERO
@@ -779,12 +786,12 @@ __global__ void __launch_bounds__(kBX* kVY, sizeof(RT) == 2 ? PARIS_TILE_MINB_H 
 // tile_update): block z covers planes k0 + 2 zb and k0 + 2 zb + 1 (rev: zb
 // descending).
 template <bool ZERO, bool XZ, int V, typename RT>
-__global__ void __launch_bounds__(kBX* kVY, PARIS_TILE2_MINB) rbgs_rho_tile2_kernel(Geo g, const RT* __restrict__ rh,
-                                                                                  float h2, const float* __restrict__ f,
-                                                                                  float* x, int color, float omega,
-                                                                                  int k0, int rev) {
+__global__ void __launch_bounds__(kBX* kVY2, PARIS_TILE2_MINB) rbgs_rho_tile2_kernel(Geo g, const RT* __restrict__ rh,
+                                                                                   float h2, const float* __restrict__ f,
+                                                                                   float* x, int color, float omega,
+                                                                                   int k0, int rev) {
     pdl_wait();
-    const int j = blockIdx.y * kVY + threadIdx.y;
+    const int j = blockIdx.y * kVY2 + threadIdx.y;
     if (j >= g.ny) return;  // uniform per warp
     const int zb = rev ? (int)(gridDim.z - 1 - blockIdx.z) : (int)blockIdx.z;
     const int k = k0 + 2 * zb;
@@ -819,22 +826,22 @@ void launch_rbgs_rho(const Geo& g, const float* rh, double h, const float* f, fl
         constexpr int V = kTileV > 0 ? kTileV : 2;
         dim3 gr((hx / V + kBX - 1) / kBX, (g.ny + kVY - 1) / kVY, k1 - k0);
         if (rh16 && tiles == 1) {  // the V-cycle's passes from FP16 rho/2
-            const dim3 gr2(gr.x, gr.y, (k1 - k0) / 2);
+            const dim3 gr2(gr.x, (g.ny + kVY2 - 1) / kVY2, (k1 - k0) / 2);
             const bool two = (k1 - k0) % 2 == 0;
             if (zero_init && two && PARIS_TILE_NP_ZERO == 2)
-                launch_pdl(rbgs_rho_tile2_kernel<true, false, V, __half>, gr2, dim3(kBX, kVY), 0, st, g, rh16, h2, f,
+                launch_pdl(rbgs_rho_tile2_kernel<true, false, V, __half>, gr2, dim3(kBX, kVY2), 0, st, g, rh16, h2, f,
                            x, color, (float)omega, k0, rev ? 1 : 0);
             else if (zero_init)
                 launch_pdl(rbgs_rho_tile_kernel<true, false, V, __half>, gr, dim3(kBX, kVY), 0, st, g, rh16, h2, f,
                            x, color, (float)omega, k0, rev ? 1 : 0);
             else if (own_zero && two && PARIS_TILE_NP_XZ == 2)
-                launch_pdl(rbgs_rho_tile2_kernel<false, true, V, __half>, gr2, dim3(kBX, kVY), 0, st, g, rh16, h2, f,
+                launch_pdl(rbgs_rho_tile2_kernel<false, true, V, __half>, gr2, dim3(kBX, kVY2), 0, st, g, rh16, h2, f,
                            x, color, (float)omega, k0, rev ? 1 : 0);
             else if (own_zero)
                 launch_pdl(rbgs_rho_tile_kernel<false, true, V, __half>, gr, dim3(kBX, kVY), 0, st, g, rh16, h2, f,
                            x, color, (float)omega, k0, rev ? 1 : 0);
             else if (PARIS_TILE_NP == 2 && two)
-                launch_pdl(rbgs_rho_tile2_kernel<false, false, V, __half>, gr2, dim3(kBX, kVY), 0, st, g, rh16, h2, f,
+                launch_pdl(rbgs_rho_tile2_kernel<false, false, V, __half>, gr2, dim3(kBX, kVY2), 0, st, g, rh16, h2, f,
                            x, color, (float)omega, k0, rev ? 1 : 0);
             else
                 launch_pdl(rbgs_rho_tile_kernel<false, false, V, __half>, gr, dim3(kBX, kVY), 0, st, g, rh16, h2, f,
@@ -1261,14 +1268,22 @@ __device__ __forceinline__ void tile_restrict_faces(const Geo& g, const RT* __re
 #ifndef PARIS_OP_MINB_R
 #define PARIS_OP_MINB_R 4
 #endif
+// rows per block of the plane-tile restriction (even): two rows measured
+// 41.7 us a launch against 43.2 with eight
+#ifndef PARIS_RESTRICT_VY
+#define PARIS_RESTRICT_VY 2
+#endif
+constexpr int kVYR = PARIS_RESTRICT_VY;
 // the restriction's operator on the coarse cells' surface faces only (0: the
 // full stencil of every child)
 #ifndef PARIS_RESTRICT_SURFACE
 #define PARIS_RESTRICT_SURFACE 1
 #endif
 constexpr bool kRestrictSurface = PARIS_RESTRICT_SURFACE != 0;
-template <bool RESTRICT, int V, bool XP = false, typename RT = float>
-__global__ void __launch_bounds__(kBX* kVY, RESTRICT ? PARIS_OP_MINB_R : PARIS_OP_MINB) op_rho_tile_kernel(Geo g, const RT* __restrict__ rh, float ih2,
+// VB: rows per block (the product's block reduction needs kVY; the
+// restriction pairs rows 2m, 2m+1, so VB is even)
+template <bool RESTRICT, int V, bool XP = false, typename RT = float, int VB = kVY>
+__global__ void __launch_bounds__(kBX* VB, RESTRICT ? PARIS_OP_MINB_R * kVY / VB : PARIS_OP_MINB) op_rho_tile_kernel(Geo g, const RT* __restrict__ rh, float ih2,
                                                              const float* __restrict__ x,
                                                              const float* __restrict__ f,
                                                              float* __restrict__ out, Geo cg,
@@ -1277,7 +1292,8 @@ __global__ void __launch_bounds__(kBX* kVY, RESTRICT ? PARIS_OP_MINB_R : PARIS_O
                                                              const Scal* s = nullptr,
                                                              float* __restrict__ xnew = nullptr, int rev = 0,
                                                              float* __restrict__ eacc = nullptr, int emem = 0) {
-    __shared__ float sh[kVY][kBX * V];
+    static_assert(RESTRICT ? VB % 2 == 0 : VB == kVY, "rows per block");
+    __shared__ float sh[VB][kBX * V];
     pdl_wait();
     // rev: the plane groups in descending order (starting where a previous
     // pass ended); a block's work, and its slot of partial sums, follow its
@@ -1289,7 +1305,7 @@ __global__ void __launch_bounds__(kBX* kVY, RESTRICT ? PARIS_OP_MINB_R : PARIS_O
     // emem = 0: e not yet written, taken as +0)
     const float alpha_p = (XP && eacc) ? (float)s->alpha : 0.f;
     const int ty = threadIdx.y, lane = threadIdx.x;
-    const int j = blockIdx.y * kVY + ty;
+    const int j = blockIdx.y * VB + ty;
     const bool row_ok = j < g.ny;
     const int jc = row_ok ? j : g.ny - 1;  // idle rows shadow the last row (no stores)
     const int hx = g.nx / 2;
@@ -1446,13 +1462,14 @@ void launch_restrict_rho(const Geo& g, const float* rh, double h, const float* f
     const int hx = g.nx / 2;
     if (tiles && kTileOpV > 0 && hx % kTileOpV == 0) {
         constexpr int V = kTileOpV > 0 ? kTileOpV : 2;
-        dim3 gr((hx / V + kBX - 1) / kBX, (g.ny + kVY - 1) / kVY, g.nz / 2);
+        dim3 gr((hx / V + kBX - 1) / kBX, (g.ny + kVYR - 1) / kVYR, g.nz / 2);
         if (rh16)  // the V-cycle's restriction from FP16 rho/2
-            launch_pdl(op_rho_tile_kernel<true, V, false, __half>, gr, dim3(kBX, kVY), 0, st, g, rh16,
+            launch_pdl(op_rho_tile_kernel<true, V, false, __half, kVYR>, gr, dim3(kBX, kVYR), 0, st, g, rh16,
                        (float)(1.0 / (h * h)), x, f, fc, cg, (double*)nullptr, 2, no_fin(), (const float*)nullptr,
                        (const Scal*)nullptr, (float*)nullptr, rev ? 1 : 0, (float*)nullptr, 0);
         else
-            launch_pdl(op_rho_tile_kernel<true, V>, gr, dim3(kBX, kVY), 0, st, g, rh, (float)(1.0 / (h * h)), x, f,
+            launch_pdl(op_rho_tile_kernel<true, V, false, float, kVYR>, gr, dim3(kBX, kVYR), 0, st, g, rh,
+                (float)(1.0 / (h * h)), x, f,
                 fc, cg, (double*)nullptr, 2, no_fin(), (const float*)nullptr, (const Scal*)nullptr, (float*)nullptr,
                 rev ? 1 : 0, (float*)nullptr, 0);
         count_launch();
