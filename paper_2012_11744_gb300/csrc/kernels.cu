@@ -22,6 +22,20 @@ namespace paris {
 namespace {
 
 constexpr int kTX = 32, kTY = 8;  // 2-D tile of the stencil kernels (x fastest)
+// rows per block of the colour passes of the face-array levels (rbgs_kernel,
+// rbgs4_kernel), by precision: small blocks schedule at finer grain; the
+// FP64 step measured 33.6 ms with two rows against 35.9 with eight, the
+// mixed one 8.84 ms with four against 8.87 (and 8.92 with two)
+#ifndef PARIS_PASS_TY32
+#define PARIS_PASS_TY32 4
+#endif
+#ifndef PARIS_PASS_TY64
+#define PARIS_PASS_TY64 2
+#endif
+template <typename T>
+__host__ __device__ constexpr int pass_rows() {
+    return sizeof(T) == 8 ? PARIS_PASS_TY64 : PARIS_PASS_TY32;
+}
 constexpr int kZ = 8;             // cells per thread along z in reducing stencil kernels
 
 // Element-wise grid-stride loop over [0, n).
@@ -859,7 +873,7 @@ void launch_coarse_solve(const Geo& g, const double* inv, const T* f, T* x, cuda
 // incoming x is taken as zero and the other member of the pair is zeroed.
 
 template <typename T, typename TB, bool USEW, bool I32>
-__global__ void __launch_bounds__(kTX* kTY) rbgs_kernel(Geo g, const TB* __restrict__ bx,
+__global__ void __launch_bounds__(kTX* pass_rows<T>()) rbgs_kernel(Geo g, const TB* __restrict__ bx,
                                                        const TB* __restrict__ by,
                                                        const TB* __restrict__ bz, T scale,
                                                        const T* __restrict__ w,
@@ -867,7 +881,7 @@ __global__ void __launch_bounds__(kTX* kTY) rbgs_kernel(Geo g, const TB* __restr
                                                        int color, T omega, int zero_init, int k0) {
     pdl_wait();
     const int t = blockIdx.x * kTX + threadIdx.x;
-    const int j = blockIdx.y * kTY + threadIdx.y;
+    const int j = blockIdx.y * pass_rows<T>() + threadIdx.y;
     const int k = k0 + blockIdx.z;
     const int i0 = 2 * t;
     if (i0 >= g.nx || j >= g.ny) return;
@@ -1023,14 +1037,14 @@ __device__ __forceinline__ void rbgs4_row(const Geo& g, const TB* __restrict__ b
 // form's passes measured 4 % faster so than with the stores inside the
 // update).
 template <typename T, bool USEW, typename TB = T>
-__global__ void __launch_bounds__(kTX* kTY) rbgs4_kernel(Geo g, const TB* __restrict__ bx,
+__global__ void __launch_bounds__(kTX* pass_rows<T>()) rbgs4_kernel(Geo g, const TB* __restrict__ bx,
                                                         const TB* __restrict__ by,
                                                         const TB* __restrict__ bz, T scale,
                                                         const T* __restrict__ w,
                                                         const T* __restrict__ f, T* __restrict__ x,
                                                         int color, T omega, int zero_init, int k0) {
     pdl_wait();
-    const int j = blockIdx.y * kTY + threadIdx.y;
+    const int j = blockIdx.y * pass_rows<T>() + threadIdx.y;
     if (j >= g.ny) return;  // uniform per warp
     const int k = k0 + blockIdx.z;
     const int nq = g.nx / 4;
@@ -1062,34 +1076,34 @@ void launch_rbgs(const Geo& g, const Coef<T>& cf, const T* w, const T* f, T* x, 
     // would leave lanes idle: the single-pair kernel serves them)
     if (g.nx % 4 == 0 && g.nx >= 4 * kTX && !g.wx && fits_i32(g) && aligned16(cf.bx, cf.by, cf.bz, f) &&
         aligned16(x) && ((sizeof(T) == 4 && !cf.sig) || aligned16(w))) {
-        dim3 gr((g.nx / 4 + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, k1 - k0);
+        dim3 gr((g.nx / 4 + kTX - 1) / kTX, (g.ny + pass_rows<T>() - 1) / pass_rows<T>(), k1 - k0);
         if (sizeof(T) == 8 || cf.sig)  // w read (FP64, or a diagonal excess the coefficients do not hold)
-            launch_pdl(rbgs4_kernel<T, true>, gr, dim3(kTX, kTY), 0, st, g, cf.bx, cf.by, cf.bz, cf.scale, w, f,
+            launch_pdl(rbgs4_kernel<T, true>, gr, dim3(kTX, pass_rows<T>()), 0, st, g, cf.bx, cf.by, cf.bz, cf.scale, w, f,
                 x, color, (T)omega, zero_init ? 1 : 0, k0);
         else
-            launch_pdl(rbgs4_kernel<T, false>, gr, dim3(kTX, kTY), 0, st, g, cf.bx, cf.by, cf.bz, cf.scale, w,
+            launch_pdl(rbgs4_kernel<T, false>, gr, dim3(kTX, pass_rows<T>()), 0, st, g, cf.bx, cf.by, cf.bz, cf.scale, w,
                 f, x, color, (T)omega, zero_init ? 1 : 0, k0);
         count_launch();
         return;
     }
     const int npair = (g.nx + 1) / 2;
-    dim3 gr((npair + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, k1 - k0);
+    dim3 gr((npair + kTX - 1) / kTX, (g.ny + pass_rows<T>() - 1) / pass_rows<T>(), k1 - k0);
     // FP32: recomputing 1/D from the coefficients already loaded is cheaper
     // than reading it; FP64: the division costs more than the read
     const bool i32 = fits_i32(g);
     if (sizeof(T) == 8 || cf.sig) {
         if (i32)
-            launch_pdl(rbgs_kernel<T, T, true, true>, gr, dim3(kTX, kTY), 0, st, g, cf.bx, cf.by, cf.bz,
+            launch_pdl(rbgs_kernel<T, T, true, true>, gr, dim3(kTX, pass_rows<T>()), 0, st, g, cf.bx, cf.by, cf.bz,
                 cf.scale, w, f, x, color, (T)omega, zero_init ? 1 : 0, k0);
         else
-            launch_pdl(rbgs_kernel<T, T, true, false>, gr, dim3(kTX, kTY), 0, st, g, cf.bx, cf.by, cf.bz,
+            launch_pdl(rbgs_kernel<T, T, true, false>, gr, dim3(kTX, pass_rows<T>()), 0, st, g, cf.bx, cf.by, cf.bz,
                 cf.scale, w, f, x, color, (T)omega, zero_init ? 1 : 0, k0);
     } else {
         if (i32)
-            launch_pdl(rbgs_kernel<T, T, false, true>, gr, dim3(kTX, kTY), 0, st, g, cf.bx, cf.by, cf.bz,
+            launch_pdl(rbgs_kernel<T, T, false, true>, gr, dim3(kTX, pass_rows<T>()), 0, st, g, cf.bx, cf.by, cf.bz,
                 cf.scale, w, f, x, color, (T)omega, zero_init ? 1 : 0, k0);
         else
-            launch_pdl(rbgs_kernel<T, T, false, false>, gr, dim3(kTX, kTY), 0, st, g, cf.bx, cf.by, cf.bz,
+            launch_pdl(rbgs_kernel<T, T, false, false>, gr, dim3(kTX, pass_rows<T>()), 0, st, g, cf.bx, cf.by, cf.bz,
                 cf.scale, w, f, x, color, (T)omega, zero_init ? 1 : 0, k0);
     }
     count_launch();
@@ -1101,19 +1115,19 @@ void launch_rbgs_h(const Geo& g, const __half* const b[3], float scale, const fl
     // four cells per thread where a row fills a warp (the update of the pair kernel)
     if (g.nx % 4 == 0 && g.nx >= 4 * kTX && !g.wx && fits_i32(g) && aligned16(f, x) &&
         ((((uintptr_t)b[0] | (uintptr_t)b[1] | (uintptr_t)b[2]) & 7u) == 0)) {
-        dim3 gr((g.nx / 4 + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, k1 - k0);
-        launch_pdl(rbgs4_kernel<float, false, __half>, gr, dim3(kTX, kTY), 0, st, g, b[0], b[1], b[2], scale,
+        dim3 gr((g.nx / 4 + kTX - 1) / kTX, (g.ny + pass_rows<float>() - 1) / pass_rows<float>(), k1 - k0);
+        launch_pdl(rbgs4_kernel<float, false, __half>, gr, dim3(kTX, pass_rows<float>()), 0, st, g, b[0], b[1], b[2], scale,
                    (const float*)nullptr, f, x, color, (float)omega, zero_init ? 1 : 0, k0);
         count_launch();
         return;
     }
     const int npair = (g.nx + 1) / 2;
-    dim3 gr((npair + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, k1 - k0);
+    dim3 gr((npair + kTX - 1) / kTX, (g.ny + pass_rows<float>() - 1) / pass_rows<float>(), k1 - k0);
     if (fits_i32(g))
-        launch_pdl(rbgs_kernel<float, __half, false, true>, gr, dim3(kTX, kTY), 0, st, g, b[0], b[1], b[2],
+        launch_pdl(rbgs_kernel<float, __half, false, true>, gr, dim3(kTX, pass_rows<float>()), 0, st, g, b[0], b[1], b[2],
             scale, nullptr, f, x, color, (float)omega, zero_init ? 1 : 0, k0);
     else
-        launch_pdl(rbgs_kernel<float, __half, false, false>, gr, dim3(kTX, kTY), 0, st, g, b[0], b[1], b[2],
+        launch_pdl(rbgs_kernel<float, __half, false, false>, gr, dim3(kTX, pass_rows<float>()), 0, st, g, b[0], b[1], b[2],
             scale, nullptr, f, x, color, (float)omega, zero_init ? 1 : 0, k0);
     count_launch();
 }
