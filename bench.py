@@ -53,9 +53,9 @@ NCU_TRAFFIC = {
     # finest-level colour pass: DRAM read + write bytes per launch from
     # "ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
     #  -k regex:rbgs_rho_tile|... -c 60" of "bench.py --single mixed" (caches flushed
-    # between launches): zero-initial passes 72.6 MB, the passes after them 113.4 MB,
+    # between launches): zero-initial passes 72.6 MB, the passes after them 113.5 MB,
     # the others 147.7 MB (rho/2 in FP16, two planes per block); 11, 11 and 66 per solve
-    "smooth0": {"bytes_per_launch": 134.0e6, "source": "rho0.cu", "sha": "c2c73a9817a6d0c9"},
+    "smooth0": {"bytes_per_launch": 134.1e6, "source": "rho0.cu", "sha": "08c283ebe42f14f7"},
 }
 
 
