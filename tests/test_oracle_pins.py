@@ -110,6 +110,53 @@ def test_assembled_operator_equals_D_B_G(grid):
     np.testing.assert_allclose(-A, L, rtol=1e-14, atol=1e-14 * np.abs(L).max())
 
 
+def _surface_restriction(grid, beta, x):
+    """Sum over the 2 x 2 x 2 children of each coarse cell of the faces on
+    the coarse cell's surface only, beta_f (x_c - x_nb) / h^2, written out face
+    by face from the face arrays (wall faces carry no flux)."""
+    terms = []
+    for a, ax in ((0, 2), (1, 1), (2, 0)):  # x, y, z faces; array axes (z, y, x)
+        b = np.array(beta[a], dtype=np.float64)
+        n = grid.shape[ax]
+        if grid.bc[a] == W:
+            bm = np.take(b, range(0, n), axis=ax).copy()
+            bp = np.take(b, range(1, n + 1), axis=ax).copy()
+            idx = [slice(None)] * 3
+            idx[ax] = 0
+            bm[tuple(idx)] = 0.0
+            idx[ax] = n - 1
+            bp[tuple(idx)] = 0.0
+        else:
+            bm, bp = b, np.roll(b, -1, axis=ax)
+        even = (np.arange(n) % 2 == 0).reshape([-1 if d == ax else 1 for d in range(3)])
+        terms.append(np.where(even, bm * (x - np.roll(x, 1, axis=ax)), bp * (x - np.roll(x, -1, axis=ax))))
+    s = (terms[0] + terms[1] + terms[2]) / grid.h ** 2
+    nz, ny, nx = grid.shape
+    return s.reshape(nz // 2, 2, ny // 2, 2, nx // 2, 2).sum(axis=(1, 3, 5))
+
+
+@pytest.mark.parametrize("grid", [pi.Grid(8, 8, 8, 0.125), pi.Grid(8, 6, 4, 0.1, (W, P, W)),
+                                  pi.Grid(4, 8, 6, 0.2, (P, W, P)), pi.Grid(6, 4, 2, 0.25, (W, W, W)),
+                                  pi.Grid(2, 4, 2, 0.5, (P, P, W))],
+                         ids=lambda g: f"{g.nx}x{g.ny}x{g.nz}_{g.bc}")
+def test_children_sum_keeps_only_the_coarse_cell_surface(grid):
+    """Summed over the children of a coarse cell, A x equals the sum over the
+    faces on the coarse cell's surface only: a face between two children
+    enters once from each side with opposite signs.  The residual
+    restrictions use this identity; it is checked against the assembled
+    operator.  Catches a surface face taken from the wrong child, a wall face
+    counted, and a periodic wrap face between two children (n = 2) taken as
+    a surface face."""
+    beta = _rand_beta(grid, 7)
+    x = np.random.default_rng(8).uniform(-1, 1, size=grid.shape)
+    op = oracle.Operator(grid, *beta)
+    ax = op.apply(x)
+    nz, ny, nx = grid.shape
+    full = ax.reshape(nz // 2, 2, ny // 2, 2, nx // 2, 2).sum(axis=(1, 3, 5))
+    surf = _surface_restriction(grid, beta, x)
+    np.testing.assert_allclose(surf, full, rtol=1e-12, atol=1e-12 * np.abs(full).max())
+
+
 @pytest.mark.parametrize("grid", SMALL_GRIDS, ids=lambda g: f"{g.nx}x{g.ny}x{g.nz}_{g.bc}")
 def test_divergence_and_gradient_match_definitions(grid):
     """oracle.divergence == D u/dt and oracle.face_gradient == G p; D = -G^T on
